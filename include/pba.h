@@ -1,0 +1,191 @@
+/*
+ * pba.h — C ABI of the GB300 (sm_103a) photometric bundle adjustment library.
+ *
+ * Inverse compositional photometric bundle adjustment with proxy templates
+ * (IC) and the forwards compositional form (FC) beside it, after Ham, Lucey
+ * and Singh, "Proxy Templates for Inverse Compositional Photometric Bundle
+ * Adjustment", ICCV 2017 (arXiv 1704.06967).
+ *
+ * Model (Sec. 3, Eq. energy and Eq. warp). Frame 0 is the reference (template)
+ * with the identity pose. Every point n has an integer pixel u_n in frame 0,
+ * one inverse depth d_n shared by its P pattern pixels u_n + o_j, and a
+ * visibility flag per target frame f = 1..F-1. With normalised coordinates
+ * x = ((u - c_x)/f_x, (v - c_y)/f_y) the warp is W(x; p_fn) = <R_f x~ + d_n t_f>
+ * and each residual is r = I_0(x) - I_f(W(x; p_fn)), sampled bilinearly.
+ * The energy is the Huber norm of the residuals over (point, pattern pixel,
+ * target frame).
+ *
+ * Poses are 12 doubles per frame, row-major [R | t] with R the 3x3 rotation
+ * (row-major, 9 values) followed by t (3 values), mapping reference-frame
+ * points X to frame-f points R X + t. Frame 0 must be the identity.
+ * Inverse depths are doubles. All arrays passed from the host use the
+ * caller's point order; the library reorders internally and maps back.
+ *
+ * Memory. The library allocates no device memory. The caller asks for the
+ * workspace size (pba_workspace_size) once frames and points are set and
+ * hands over one device buffer (pba_set_workspace) that must outlive the
+ * context or the next pba_set_workspace. Device images passed with
+ * PBA_MEM_DEVICE are borrowed and must outlive the context; host images
+ * (PBA_MEM_HOST) are copied into the workspace by pba_set_workspace. All
+ * device work is enqueued on the configured CUDA stream; a call returns
+ * before its kernels finish unless it returns data to the host (statistics,
+ * parameters, updates, systems), in which case it synchronises that stream.
+ *
+ * Errors. Every call returns a pba_status; no exception or exit crosses the
+ * ABI. On failure pba_last_error() describes it. Kernels never trap; they set
+ * a device error word that the next synchronising call reports
+ * (PBA_ERR_NOT_PD for a non-positive pivot of the reduced camera system,
+ * PBA_ERR_NONFINITE for a non-finite update). A context is not thread safe;
+ * distinct contexts are independent.
+ */
+#ifndef PBA_H
+#define PBA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PBA_MAX_PATTERN 16
+
+typedef struct pba_ctx pba_ctx;
+
+typedef enum {
+    PBA_OK = 0,
+    PBA_ERR_ARG = 1,        /* invalid argument (null pointer, size, range) */
+    PBA_ERR_STATE = 2,      /* call out of order (e.g. iterate before precompute) */
+    PBA_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+    PBA_ERR_NOMEM = 4,      /* workspace too small / host allocation failed */
+    PBA_ERR_NOT_PD = 5,     /* reduced camera system not positive definite */
+    PBA_ERR_NONFINITE = 6,  /* non-finite update or statistic */
+    PBA_ERR_TIMEOUT = 7     /* a bounded device wait gave up */
+} pba_status;
+
+typedef enum { PBA_F32 = 0, PBA_F16 = 1, PBA_BF16 = 2 } pba_dtype;
+
+typedef enum { PBA_MEM_DEVICE = 0, PBA_MEM_HOST = 1 } pba_memory;
+
+typedef struct {
+    double huber_k;          /* Huber constant k of ||.||_gamma (Eq. energy); > 0 */
+    int pattern_size;        /* P, 1..PBA_MAX_PATTERN */
+    const int32_t* pattern;  /* host, P*2 pixel offsets (dx, dy), copied at create */
+    double gauge_anchor_w;   /* scale-gauge prior weight relative to mean diag(S); 0 -> 1 */
+    double conv_px;          /* convergence threshold of Sec. 4.1 in pixels; 0 -> 5e-3 */
+    int n_bundles;           /* independent bundles in this context; must be 1 */
+    void* cuda_stream;       /* cudaStream_t for all work; NULL = legacy default stream */
+    int use_graphs;          /* non-zero: replay iteration loops from captured CUDA graphs */
+    int max_stats_iters;     /* capacity of the per-iteration statistics; 0 -> 256 */
+} pba_config;
+
+/* Statistics of one iteration (Sec. 4.1): Huber energy, RMS and count of the
+ * residuals valid at the iteration's parameters, the largest pattern-centre
+ * reprojection displacement of the step (pixels), and the norms of the update. */
+typedef struct {
+    double energy;
+    double rms;
+    double n_valid;
+    double max_disp_px;
+    double dtheta_norm;
+    double dd_norm;
+} pba_iter_stats;
+
+/* Creates a context. cfg and cfg->pattern are copied. */
+pba_status pba_create(const pba_config* cfg, pba_ctx** out);
+
+/* Destroys a context (synchronises its stream; NULL is a no-op). */
+void pba_destroy(pba_ctx* ctx);
+
+/* Text of the last error of this context (never NULL; valid until the next call). */
+const char* pba_last_error(const pba_ctx* ctx);
+
+/* Sets the images, the initial poses p_0 and the pinhole intrinsics.
+ * images: F frames of height h, row pitch pitch_elems >= w elements of dtype,
+ *   frame-major (frame f at images + f*h*pitch_elems elements); frame 0 is the
+ *   template I_0. Device pointer (borrowed) or host pointer (copied by
+ *   pba_set_workspace) according to mem.
+ * poses: host, F*12 doubles (p_0), frame 0 = identity. Copied.
+ * intrinsics: host, {f_x, f_y, c_x, c_y}. Copied.
+ * Requires bundle == 0, F >= 2, w, h >= 4. Invalidates the precompute and the
+ * workspace layout. */
+pba_status pba_set_frames(pba_ctx* ctx, int bundle, int n_frames, int w, int h, int pitch_elems,
+                          pba_dtype dtype, pba_memory mem, const void* images,
+                          const double* poses, const double* intrinsics);
+
+/* Sets the points (Sec. 3: one inverse depth per point in the reference frame).
+ * uv: host, N*2 int32 pixel centres in frame 0; every pattern pixel and its
+ *   central-difference neighbours must lie inside frame 0.
+ * inv_depth: host, N doubles (d_0), > 0.
+ * vis: host, N*F bytes (vis[n*F + f] != 0: point n observed in frame f;
+ *   column 0 ignored), or NULL for all visible. Copied.
+ * Invalidates the precompute and the workspace layout. */
+pba_status pba_set_points(pba_ctx* ctx, int bundle, int n_points, const int32_t* uv,
+                          const double* inv_depth, const uint8_t* vis);
+
+/* Device workspace bytes needed for the current frames and points. */
+pba_status pba_workspace_size(pba_ctx* ctx, size_t* bytes);
+
+/* Hands over the device workspace (>= pba_workspace_size bytes, 256-byte
+ * aligned) and uploads frames, points and parameters into it. */
+pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* IC precompute at the current parameters, which become p_0 (Sec. 3.5):
+ * per residual the proxy-template Jacobian row J = grad I_0 dphi/dDelta p
+ * (Sec. 3.4), initial residual and Huber weight W_0; H = J^T W_0 J in frame,
+ * frame-point and point blocks; the Schur complement S of the point block
+ * with the scale-gauge prior, its FP64 Cholesky factor and inverse. */
+pba_status pba_precompute_ic(pba_ctx* ctx);
+
+/* Runs n_iters IC iterations (Sec. 3.5 steps 1-4 with the Sec. 3.6 update):
+ * Huber weights from the current residuals, g = J^T W r, Delta p = -H^-1 g by
+ * the Schur complement, then R <- R R0^T exp(omega)^T R0, t <- t - R R0^T Dt,
+ * d <- d (d0 - Dd)/d0. stats (host, nullable): n_iters+1 entries, entry k for
+ * the parameters p_k (the last one has no update). PBA_ERR_STATE before
+ * pba_precompute_ic. */
+pba_status pba_iterate(pba_ctx* ctx, int n_iters, pba_iter_stats* stats);
+
+/* Runs n_iters FC iterations: Jacobians from the target-image gradients, the
+ * Hessian blocks, the Schur complement and its FP64 Cholesky factor rebuilt
+ * every iteration, then T <- exp([upsilon, omega]) T, d <- d + Dd (Sec. 3,
+ * the boxplus operator). stats as for pba_iterate. Needs no precompute. */
+pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats);
+
+/* Current parameters: poses F*12 doubles, inv_depth N doubles (host, nullable each). */
+pba_status pba_get_params(pba_ctx* ctx, int bundle, double* poses, double* inv_depth);
+
+/* Replaces the current parameters (not p_0; the IC precompute is kept). */
+pba_status pba_set_params(pba_ctx* ctx, int bundle, const double* poses, const double* inv_depth);
+
+/* Update of the last iteration: dtheta F*6 doubles ([Dt, omega] for IC,
+ * [upsilon, omega] for FC; frame 0 zero), dd N doubles (host, nullable each). */
+pba_status pba_get_last_update(pba_ctx* ctx, int bundle, double* dtheta, double* dd);
+
+/* The last linear system: Hff F*36 (row-major 6x6 per frame, frame 0 zero),
+ * Hfd N*F*6 (caller point order), Hdd N, and S (6(F-1))^2 row-major as
+ * factorised (with the gauge prior). fc != 0 selects the last FC system.
+ * Host arrays, nullable each. */
+pba_status pba_get_system(pba_ctx* ctx, int bundle, int fc, double* Hff, double* Hfd,
+                          double* Hdd, double* S);
+
+/* Residual count of the bundle (visible (point, frame) pairs times P). */
+pba_status pba_num_residuals(pba_ctx* ctx, int bundle, int64_t* n);
+
+/* Kernel timing. pba_enable_timing(ctx, 1) starts recording a CUDA event pair
+ * on the context's stream around every kernel launch (and resets the
+ * counters); 0 stops recording. pba_last_timing synchronises the stream and
+ * fills out[2 * PBA_TIMING_SLOTS + 1]: out[s] = accumulated device ms of slot
+ * s, out[PBA_TIMING_SLOTS] = kernel launches since the reset (counted whether
+ * or not timing is on), out[PBA_TIMING_SLOTS + 1 + s] = timed launches of
+ * slot s. Slots: 0 setup / IC precompute, 1 residual pass, 2 per-frame
+ * reduction, 3 Schur complement + assembly (FC), 4 factorisation / solve /
+ * pose update, 5 final evaluation pass. */
+#define PBA_TIMING_SLOTS 6
+pba_status pba_enable_timing(pba_ctx* ctx, int on);
+pba_status pba_last_timing(pba_ctx* ctx, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBA_H */

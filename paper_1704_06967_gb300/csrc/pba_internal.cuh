@@ -1,0 +1,236 @@
+// Internal device layout and helpers of the GB300 photometric bundle
+// adjustment library (IC with proxy templates, FC beside it).
+//
+// Data layout in HBM (all inside the caller's workspace):
+//  * points are reordered (Morton order of their reference pixel) and grouped
+//    in tiles of 32: lane l of tile t is sorted point 32 t + l. A CTA of the
+//    pass kernels owns one tile, so a point's sums over frames complete on chip.
+//  * an "entry" is a (tile, target frame) pair with at least one visible lane;
+//    entries are stored tile-major. Entry e owns the pairs pair_off .. pair_off
+//    + popc(mask) - 1 (visible lanes in lane order, "rank" = popc below lane).
+//  * per pair: the IC Jacobian rows of its P pattern pixels (7 floats each,
+//    pattern-major, packed into float4 chunks and stored chunk-major inside
+//    the entry so a warp's loads are contiguous) and the 6-float frame-point
+//    Hessian block H_fd (component-major inside the entry).
+//  * per frame: FP64 master pose, FP32 constants for the pass (R, t and the
+//    pattern offsets rotated into the frame).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pba.h"
+
+namespace pba {
+
+constexpr int kTile = 32;             // points per tile (= lanes of a warp)
+constexpr int kPassWarps = 4;         // warps per CTA of the pass kernels
+constexpr int kFrameConst = 64;       // floats of FP32 constants per frame
+constexpr int kEntryPartial = 32;     // floats of partial sums per entry
+constexpr int kStats = 8;             // doubles per statistics slot
+
+// device error word values (bit flags)
+constexpr int kErrNotPD = 1;
+constexpr int kErrNonFinite = 2;
+
+struct Entry {
+    int f;          // target frame (1..F-1)
+    unsigned mask;  // visible lanes
+    int pair_off;   // first pair of the entry
+    int tile;
+};
+
+// Per-tile statistics partials (FP32 sums of one tile).
+struct TileStats {
+    float energy, sumsq, count, maxdisp, ddsq, pad0, pad1, pad2;
+};
+
+// Everything the kernels need, passed by value.
+struct DevProblem {
+    int F, N, Npad, T, E, P, W, H, pitch, dtype;
+    float fx, fy, cx, cy, huber_k;
+    const void* img;            // F frames, H rows of `pitch` elements
+    const float* gx;            // FC gradient images (F*H*W), nullable for IC
+    const float* gy;
+    const int* pat;             // P*2 offsets (device copy)
+    const Entry* entries;       // E, tile-major
+    const int* tile_entry;      // T+1 offsets into entries
+    const int* frame_entry;     // F+1 offsets into frame_entries
+    const int* frame_entries;   // E entry ids grouped by frame, tile order
+    const int* ent_of;          // T*F entry id of (tile, frame) or -1
+    const int* uvs;             // Npad*2 sorted pixels (pad: copy of a real point)
+    const float2* xn;           // Npad normalised centre coordinates
+    const float* I0p;           // T*P*32 template intensities [tile][j][lane]
+    unsigned char* valid_pt;    // Npad (1 = real point)
+};
+
+// ---------------------------------------------------------------------------
+// image access
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float load_px(const void* img, int dtype, size_t idx)
+{
+    if (dtype == PBA_F32) return __ldg(reinterpret_cast<const float*>(img) + idx);
+    if (dtype == PBA_F16) {
+        unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(img) + idx);
+        return __half2float(__ushort_as_half(b));
+    }
+    unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(img) + idx);
+    return __uint_as_float(((unsigned)b) << 16);
+}
+
+// Bilinear sample at pixel coordinates (pixel centres on integers); valid
+// iff the 2x2 footprint lies in [1, W-2] x [1, H-2] (gradients defined).
+__device__ __forceinline__ bool bilinear(const DevProblem& pb, int f, float u, float v,
+                                         float& val, float& a, float& b, int& x, int& y)
+{
+    float fu = floorf(u), fv = floorf(v);
+    if (!(fu >= 1.0f && fu + 1.0f <= (float)(pb.W - 2) && fv >= 1.0f &&
+          fv + 1.0f <= (float)(pb.H - 2)))
+        return false;
+    x = (int)fu;
+    y = (int)fv;
+    a = u - fu;
+    b = v - fv;
+    const size_t base = ((size_t)f * pb.H + y) * pb.pitch + x;
+    float i00 = load_px(pb.img, pb.dtype, base);
+    float i10 = load_px(pb.img, pb.dtype, base + 1);
+    float i01 = load_px(pb.img, pb.dtype, base + pb.pitch);
+    float i11 = load_px(pb.img, pb.dtype, base + pb.pitch + 1);
+    float top = fmaf(a, i10 - i00, i00);
+    float bot = fmaf(a, i11 - i01, i01);
+    val = fmaf(b, bot - top, top);
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// warp reductions (butterfly: every lane ends with the same total)
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void warp_sum(float (&v)[K])
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+}
+
+__device__ __forceinline__ float warp_sum1(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum1d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_max1(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Neumaier compensated accumulation (Neumaier 1974)
+__device__ __forceinline__ void neumaier_add(float& s, float& c, float x)
+{
+    float t = s + x;
+    if (fabsf(s) >= fabsf(x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+}
+
+__device__ __forceinline__ float huber_w(float r, float k)
+{
+    float a = fabsf(r);
+    return a <= k ? 1.0f : k / a;
+}
+
+__device__ __forceinline__ float huber_rho(float r, float k)
+{
+    float a = fabsf(r);
+    return a <= k ? 0.5f * r * r : k * a - 0.5f * k * k;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 rotations: SO(3)/SE(3) exponential from Rodrigues' formula with the
+// Taylor series of its coefficients below theta = 1e-3.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline void so3_exp_d(const double* w, double* R)
+{
+    double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double th = sqrt(th2);
+    double A, B;
+    if (th < 1e-3) {
+        A = 1.0 - th2 * (1.0 / 6.0) + th2 * th2 * (1.0 / 120.0);
+        B = 0.5 - th2 * (1.0 / 24.0) + th2 * th2 * (1.0 / 720.0);
+    } else {
+        A = sin(th) / th;
+        B = (1.0 - cos(th)) / th2;
+    }
+    // R = I + A K + B K^2, K = [w]x, K^2 = w w^T - th2 I
+    R[0] = 1.0 + B * (w[0] * w[0] - th2);
+    R[1] = -A * w[2] + B * w[0] * w[1];
+    R[2] = A * w[1] + B * w[0] * w[2];
+    R[3] = A * w[2] + B * w[1] * w[0];
+    R[4] = 1.0 + B * (w[1] * w[1] - th2);
+    R[5] = -A * w[0] + B * w[1] * w[2];
+    R[6] = -A * w[1] + B * w[2] * w[0];
+    R[7] = A * w[0] + B * w[2] * w[1];
+    R[8] = 1.0 + B * (w[2] * w[2] - th2);
+}
+
+// V = I + B K + C K^2 (left Jacobian of SO(3)), C = (th - sin th)/th^3
+__host__ __device__ inline void so3_left_jacobian_d(const double* w, double* V)
+{
+    double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double th = sqrt(th2);
+    double B, C;
+    if (th < 1e-3) {
+        B = 0.5 - th2 * (1.0 / 24.0) + th2 * th2 * (1.0 / 720.0);
+        C = 1.0 / 6.0 - th2 * (1.0 / 120.0) + th2 * th2 * (1.0 / 5040.0);
+    } else {
+        B = (1.0 - cos(th)) / th2;
+        C = (th - sin(th)) / (th2 * th);
+    }
+    V[0] = 1.0 + C * (w[0] * w[0] - th2);
+    V[1] = -B * w[2] + C * w[0] * w[1];
+    V[2] = B * w[1] + C * w[0] * w[2];
+    V[3] = B * w[2] + C * w[1] * w[0];
+    V[4] = 1.0 + C * (w[1] * w[1] - th2);
+    V[5] = -B * w[0] + C * w[1] * w[2];
+    V[6] = -B * w[1] + C * w[2] * w[0];
+    V[7] = B * w[0] + C * w[2] * w[1];
+    V[8] = 1.0 + C * (w[2] * w[2] - th2);
+}
+
+__host__ __device__ inline void mat3_mul_d(const double* A, const double* B, double* C)
+{
+    double T[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            T[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+    for (int i = 0; i < 9; ++i) C[i] = T[i];
+}
+
+// FP32 pass constants of one frame from its FP64 pose: R (9), t (3) and the
+// pattern offsets of the P pattern pixels rotated into the frame,
+// delta_j = (o_jx / f_x) R[:,0] + (o_jy / f_y) R[:,1], so the 3-D point of
+// pattern pixel j is q_j = R x~_c + d t + delta_j.
+__host__ __device__ inline void frame_consts(const double* pose, const int* pat, int P, double fx,
+                                             double fy, float* out)
+{
+    for (int i = 0; i < 12; ++i) out[i] = (float)pose[i];
+    for (int j = 0; j < P; ++j) {
+        double ox = pat[2 * j] / fx, oy = pat[2 * j + 1] / fy;
+        for (int r = 0; r < 3; ++r) out[12 + 3 * j + r] = (float)(ox * pose[3 * r] + oy * pose[3 * r + 1]);
+    }
+}
+
+}  // namespace pba

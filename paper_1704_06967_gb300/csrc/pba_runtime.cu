@@ -1,0 +1,817 @@
+// Host runtime and C ABI of the photometric bundle adjustment library: the
+// context, input validation, point reordering into tiles, the (tile, frame)
+// entry lists, the workspace layout, uploads, and the IC / FC iteration
+// drivers that enqueue the kernels on the caller's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pba_kernels.cuh"
+
+using namespace pba;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+uint32_t spread16(uint32_t x)
+{
+    x &= 0xffffu;
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+// Timing slots (pba_last_timing): precompute, residual pass, reduce,
+// Schur/assemble, factor/solve/update, final evaluation.
+enum { TS_PRE = 0, TS_PASS, TS_REDUCE, TS_SCHUR, TS_SOLVE, TS_EVAL, TS_N };
+
+}  // namespace
+
+struct pba_ctx {
+    pba_config cfg{};
+    std::vector<int32_t> pattern;
+    cudaStream_t stream = nullptr;
+    std::string err = "no error";
+
+    // frames
+    bool have_frames = false;
+    int F = 0, W = 0, H = 0, pitch = 0;
+    pba_dtype dtype = PBA_F32;
+    pba_memory mem = PBA_MEM_DEVICE;
+    const void* images = nullptr;
+    std::vector<double> poses_init;  // F*12
+    double K[4] = {0, 0, 0, 0};
+
+    // points
+    bool have_points = false;
+    int N = 0;
+    std::vector<int32_t> uv;
+    std::vector<double> d_init;
+    std::vector<uint8_t> vis;  // N*F
+
+    // derived host structures
+    int T = 0, Npad = 0, E = 0, NC = 0;
+    int64_t V = 0;
+    std::vector<int> perm;  // sorted slot -> caller index (-1 for pads)
+    std::vector<Entry> entries;
+    std::vector<int> tile_entry, frame_entry, frame_entries, ent_of;
+    std::vector<int2> frame_pairs;
+
+    // workspace
+    bool ws_ready = false, ic_ready = false;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    struct {
+        void* img;
+        float *gx, *gy;
+        int* pat;
+        Entry* entries;
+        int *tile_entry, *frame_entry, *frame_entries, *ent_of;
+        int* uvs;
+        float2* xn;
+        float* I0p;
+        unsigned char* valid_pt;
+        double *d64, *d0_64, *dd_last;
+        float *gn_ic, *Hnn_ic, *gn_fc, *Hnn_fc;
+        float4* J4;
+        float *Hfd_ic, *Hfd_fc;
+        float* ent_part;
+        TileStats* tstats;
+        float *fc, *fc_prev, *dtheta32, *dthsq;
+        double *poses64, *poses0_64, *dtheta64;
+        double *red_ic, *red_y;
+        double *Soff, *S_ic, *L_ic, *Sinv, *S_fc, *L_fc;
+        int* active;
+        int2* frame_pairs;
+        int* err;
+        double* stats;
+    } d{};
+    int stats_slots = 0;
+    int last_fc = 0;  // which system the last update came from
+
+    // instrumentation
+    bool timing = false;
+    int64_t launches = 0;
+    double tms[TS_N] = {0, 0, 0, 0, 0, 0};
+    int64_t tcount[TS_N] = {0, 0, 0, 0, 0, 0};
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> tev;
+    std::vector<cudaEvent_t> evpool;
+};
+
+namespace {
+
+pba_status fail(pba_ctx* c, pba_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, PBA_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define LAUNCH(slot, call)            \
+    do {                              \
+        int ev_ = tbegin(ctx, slot);  \
+        CK(call);                     \
+        ++ctx->launches;              \
+        tend(ctx, ev_);               \
+    } while (0)
+
+cudaEvent_t take_event(pba_ctx* ctx)
+{
+    if (!ctx->evpool.empty()) {
+        cudaEvent_t e = ctx->evpool.back();
+        ctx->evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+int tbegin(pba_ctx* ctx, int slot)
+{
+    if (!ctx->timing) return -1;
+    cudaEvent_t a = take_event(ctx), b = take_event(ctx);
+    cudaEventRecord(a, ctx->stream);
+    ctx->tev.push_back({slot, {a, b}});
+    return (int)ctx->tev.size() - 1;
+}
+
+void tend(pba_ctx* ctx, int idx)
+{
+    if (idx < 0) return;
+    cudaEventRecord(ctx->tev[idx].second.second, ctx->stream);
+}
+
+void tcollect(pba_ctx* ctx)
+{
+    for (auto& ev : ctx->tev) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ev.second.first, ev.second.second) == cudaSuccess) {
+            ctx->tms[ev.first] += ms;
+            ctx->tcount[ev.first] += 1;
+        }
+        ctx->evpool.push_back(ev.second.first);
+        ctx->evpool.push_back(ev.second.second);
+    }
+    ctx->tev.clear();
+}
+
+size_t elem_size(pba_dtype t) { return t == PBA_F32 ? 4 : 2; }
+
+// Lays out (and optionally assigns) the workspace; returns its size.
+size_t layout(pba_ctx* c, char* base)
+{
+    size_t off = 0;
+    auto take = [&](auto*& ptr, size_t bytes) {
+        using P = std::remove_reference_t<decltype(ptr)>;
+        ptr = base ? reinterpret_cast<P>(base + off) : nullptr;
+        off += align_up(std::max<size_t>(bytes, 1));
+    };
+    const size_t F = c->F, HW = (size_t)c->H * c->W, Np = c->Npad, n6 = 6 * (c->F - 1);
+    if (c->mem == PBA_MEM_HOST) {
+        void*& img = c->d.img;
+        char* p = nullptr;
+        take(p, F * c->H * c->pitch * elem_size(c->dtype));
+        if (base) img = p;
+    }
+    take(c->d.gx, F * HW * 4);
+    take(c->d.gy, F * HW * 4);
+    take(c->d.pat, c->pattern.size() * sizeof(int));
+    take(c->d.entries, (size_t)c->E * sizeof(Entry));
+    take(c->d.tile_entry, (size_t)(c->T + 1) * 4);
+    take(c->d.frame_entry, (F + 1) * 4);
+    take(c->d.frame_entries, (size_t)c->E * 4);
+    take(c->d.ent_of, (size_t)c->T * F * 4);
+    take(c->d.uvs, Np * 8);
+    take(c->d.xn, Np * 8);
+    take(c->d.I0p, (size_t)c->T * (c->pattern.size() / 2) * kTile * 4);
+    take(c->d.valid_pt, Np);
+    take(c->d.d64, Np * 8);
+    take(c->d.d0_64, Np * 8);
+    take(c->d.dd_last, Np * 8);
+    take(c->d.gn_ic, Np * 4);
+    take(c->d.Hnn_ic, Np * 4);
+    take(c->d.gn_fc, Np * 4);
+    take(c->d.Hnn_fc, Np * 4);
+    take(c->d.J4, (size_t)c->V * c->NC * 16);
+    take(c->d.Hfd_ic, (size_t)c->V * 6 * 4);
+    take(c->d.Hfd_fc, (size_t)c->V * 6 * 4);
+    take(c->d.ent_part, (size_t)c->E * kEntryPartial * 4);
+    take(c->d.tstats, (size_t)c->T * sizeof(TileStats));
+    take(c->d.fc, F * kFrameConst * 4);
+    take(c->d.fc_prev, F * 12 * 4);
+    take(c->d.dtheta32, F * 6 * 4);
+    take(c->d.dthsq, F * 4);
+    take(c->d.poses64, F * 12 * 8);
+    take(c->d.poses0_64, F * 12 * 8);
+    take(c->d.dtheta64, F * 6 * 8);
+    take(c->d.red_ic, F * 21 * 8);
+    take(c->d.red_y, F * 27 * 8);
+    take(c->d.Soff, n6 * n6 * 8);
+    take(c->d.S_ic, n6 * n6 * 8);
+    take(c->d.L_ic, n6 * n6 * 8);
+    take(c->d.Sinv, n6 * n6 * 8);
+    take(c->d.S_fc, n6 * n6 * 8);
+    take(c->d.L_fc, n6 * n6 * 8);
+    take(c->d.active, F * 4);
+    take(c->d.frame_pairs, c->frame_pairs.size() * sizeof(int2));
+    take(c->d.err, 64);
+    take(c->d.stats, (size_t)(c->stats_slots) * kStats * 8);
+    return off;
+}
+
+// Sorted point order, tiles, (tile, frame) entries and their lookups.
+void build_structure(pba_ctx* c)
+{
+    const int N = c->N, F = c->F;
+    std::vector<std::pair<uint64_t, int>> key(N);
+    for (int n = 0; n < N; ++n) {
+        uint32_t u = (uint32_t)c->uv[2 * n], v = (uint32_t)c->uv[2 * n + 1];
+        key[n] = {((uint64_t)(spread16(u) | (spread16(v) << 1)) << 32) | (uint32_t)n, n};
+    }
+    std::sort(key.begin(), key.end());
+    c->T = (N + kTile - 1) / kTile;
+    c->Npad = c->T * kTile;
+    c->perm.assign(c->Npad, -1);
+    for (int i = 0; i < N; ++i) c->perm[i] = key[i].second;
+    c->entries.clear();
+    c->tile_entry.assign(c->T + 1, 0);
+    c->ent_of.assign((size_t)c->T * F, -1);
+    int64_t pairs = 0;
+    for (int t = 0; t < c->T; ++t) {
+        c->tile_entry[t] = (int)c->entries.size();
+        for (int f = 1; f < F; ++f) {
+            unsigned mask = 0;
+            for (int l = 0; l < kTile; ++l) {
+                const int n = c->perm[t * kTile + l];
+                if (n >= 0 && c->vis[(size_t)n * F + f]) mask |= 1u << l;
+            }
+            if (!mask) continue;
+            c->ent_of[(size_t)t * F + f] = (int)c->entries.size();
+            c->entries.push_back(Entry{f, mask, (int)pairs, t});
+            pairs += __builtin_popcount(mask);
+        }
+    }
+    c->tile_entry[c->T] = (int)c->entries.size();
+    c->E = (int)c->entries.size();
+    c->V = pairs;
+    c->frame_entry.assign(F + 1, 0);
+    for (const Entry& e : c->entries) c->frame_entry[e.f + 1]++;
+    for (int f = 0; f < F; ++f) c->frame_entry[f + 1] += c->frame_entry[f];
+    c->frame_entries.assign(c->E, 0);
+    std::vector<int> fill(c->frame_entry.begin(), c->frame_entry.end() - 1);
+    for (int e = 0; e < c->E; ++e) c->frame_entries[fill[c->entries[e].f]++] = e;
+    c->frame_pairs.clear();
+    for (int f = 1; f < F; ++f)
+        for (int g = f; g < F; ++g) c->frame_pairs.push_back(make_int2(f, g));
+    c->NC = (7 * (int)(c->pattern.size() / 2) + 3) / 4;
+}
+
+pba_status upload_params(pba_ctx* ctx, const double* poses, const double* depth)
+{
+    const int F = ctx->F;
+    std::vector<float> fcs((size_t)F * kFrameConst, 0.0f), prev((size_t)F * 12, 0.0f);
+    const int P = (int)ctx->pattern.size() / 2;
+    for (int f = 0; f < F; ++f) {
+        frame_consts(poses + 12 * f, ctx->pattern.data(), P, ctx->K[0], ctx->K[1],
+                     fcs.data() + (size_t)f * kFrameConst);
+        for (int i = 0; i < 12; ++i) prev[12 * f + i] = (float)poses[12 * f + i];
+    }
+    CK(cudaMemcpyAsync(ctx->d.poses64, poses, sizeof(double) * 12 * F, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.fc, fcs.data(), sizeof(float) * fcs.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.fc_prev, prev.data(), sizeof(float) * prev.size(), cudaMemcpyHostToDevice, ctx->stream));
+    if (depth) {
+        std::vector<double> ds(ctx->Npad, 1.0);
+        for (int i = 0; i < ctx->Npad; ++i)
+            if (ctx->perm[i] >= 0) ds[i] = depth[ctx->perm[i]];
+        CK(cudaMemcpyAsync(ctx->d.d64, ds.data(), sizeof(double) * ds.size(), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    // all host staging above is pageable: the copies have consumed it on return
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PBA_OK;
+}
+
+pba_status check_device_error(pba_ctx* ctx)
+{
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, ctx->d.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    tcollect(ctx);
+    if (herr) {
+        CK(cudaMemsetAsync(ctx->d.err, 0, sizeof(int), ctx->stream));
+        if (herr & kErrNotPD)
+            return fail(ctx, PBA_ERR_NOT_PD, "reduced camera system is not positive definite");
+        return fail(ctx, PBA_ERR_NONFINITE, "non-finite update");
+    }
+    return PBA_OK;
+}
+
+LaunchCtx make_launch(pba_ctx* c)
+{
+    LaunchCtx L{};
+    DevProblem& pb = L.pb;
+    pb.F = c->F;
+    pb.N = c->N;
+    pb.Npad = c->Npad;
+    pb.T = c->T;
+    pb.E = c->E;
+    pb.P = (int)c->pattern.size() / 2;
+    pb.W = c->W;
+    pb.H = c->H;
+    pb.pitch = c->pitch;
+    pb.dtype = c->dtype;
+    pb.fx = (float)c->K[0];
+    pb.fy = (float)c->K[1];
+    pb.cx = (float)c->K[2];
+    pb.cy = (float)c->K[3];
+    pb.huber_k = (float)c->cfg.huber_k;
+    pb.img = c->mem == PBA_MEM_HOST ? c->d.img : c->images;
+    pb.gx = c->d.gx;
+    pb.gy = c->d.gy;
+    pb.pat = c->d.pat;
+    pb.entries = c->d.entries;
+    pb.tile_entry = c->d.tile_entry;
+    pb.frame_entry = c->d.frame_entry;
+    pb.frame_entries = c->d.frame_entries;
+    pb.ent_of = c->d.ent_of;
+    pb.uvs = c->d.uvs;
+    pb.xn = c->d.xn;
+    pb.I0p = c->d.I0p;
+    pb.valid_pt = c->d.valid_pt;
+    L.fs = FrameState{c->d.fc, c->d.fc_prev, c->d.dtheta32};
+    L.ds_ic = DepthState{c->d.d64, c->d.d0_64, c->d.gn_ic, c->d.Hnn_ic, c->d.Hfd_ic, c->d.dd_last, c->d.err};
+    L.ds_fc = DepthState{c->d.d64, c->d.d0_64, c->d.gn_fc, c->d.Hnn_fc, c->d.Hfd_fc, c->d.dd_last, c->d.err};
+    L.ic = IcStore{c->d.J4, c->d.Hfd_ic, c->d.Hnn_ic};
+    L.Hfd_fc = c->d.Hfd_fc;
+    L.ent_part = c->d.ent_part;
+    L.tstats = c->d.tstats;
+    L.dthsq = c->d.dthsq;
+    L.stats = c->d.stats;
+    L.stream = c->stream;
+    return L;
+}
+
+SolveArgs make_solve(pba_ctx* c)
+{
+    SolveArgs a{};
+    a.F = c->F;
+    a.n6 = 6 * (c->F - 1);
+    a.pat = c->d.pat;
+    a.P = (int)c->pattern.size() / 2;
+    a.fx = c->K[0];
+    a.fy = c->K[1];
+    a.poses64 = c->d.poses64;
+    a.poses0 = c->d.poses0_64;
+    a.dtheta64 = c->d.dtheta64;
+    a.dtheta32 = c->d.dtheta32;
+    a.fc = c->d.fc;
+    a.fc_prev = c->d.fc_prev;
+    a.dthsq = c->d.dthsq;
+    a.err = c->d.err;
+    return a;
+}
+
+pba_status copy_stats(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
+{
+    pba_status s = check_device_error(ctx);
+    if (s != PBA_OK) return s;
+    if (!stats) return PBA_OK;
+    std::vector<double> h((size_t)(n_iters + 1) * kStats);
+    CK(cudaMemcpy(h.data(), ctx->d.stats, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+    for (int k = 0; k <= n_iters; ++k) {
+        const double* r = h.data() + (size_t)k * kStats;
+        stats[k] = pba_iter_stats{r[0], r[1], r[2], k < n_iters ? r[3] : 0.0,
+                                  k < n_iters ? r[4] : 0.0, k < n_iters ? r[5] : 0.0};
+    }
+    return PBA_OK;
+}
+
+}  // namespace
+
+namespace pba {
+
+// Setup: central-difference gradient images (FC) and the template
+// intensities of every (point, pattern pixel).
+__global__ void gradient_images_kernel(DevProblem pb, float* gx, float* gy)
+{
+    const size_t total = (size_t)pb.F * pb.H * pb.W;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % pb.W);
+        const size_t fy = i / pb.W;
+        const int y = (int)(fy % pb.H);
+        const size_t row = fy * pb.pitch;
+        float a = 0.0f, b = 0.0f;
+        if (x >= 1 && x <= pb.W - 2)
+            a = 0.5f * (load_px(pb.img, pb.dtype, row + x + 1) - load_px(pb.img, pb.dtype, row + x - 1));
+        if (y >= 1 && y <= pb.H - 2)
+            b = 0.5f * (load_px(pb.img, pb.dtype, row + pb.pitch + x) -
+                        load_px(pb.img, pb.dtype, row - pb.pitch + x));
+        gx[i] = a;
+        gy[i] = b;
+    }
+}
+
+__global__ void template_gather_kernel(DevProblem pb, float* I0p)
+{
+    const int total = pb.T * pb.P * kTile;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int lane = i % kTile, j = (i / kTile) % pb.P, t = i / (kTile * pb.P);
+        const int n = t * kTile + lane;
+        const int px = pb.uvs[2 * n] + pb.pat[2 * j], py = pb.uvs[2 * n + 1] + pb.pat[2 * j + 1];
+        I0p[i] = load_px(pb.img, pb.dtype, (size_t)py * pb.pitch + px);
+    }
+}
+
+cudaError_t launch_setup(const DevProblem& pb, float* gx, float* gy, float* I0p, cudaStream_t st)
+{
+    gradient_images_kernel<<<1024, 256, 0, st>>>(pb, gx, gy);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    template_gather_kernel<<<256, 256, 0, st>>>(pb, I0p);
+    return cudaGetLastError();
+}
+
+}  // namespace pba
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+pba_status pba_create(const pba_config* cfg, pba_ctx** out)
+{
+    if (!out) return PBA_ERR_ARG;
+    *out = nullptr;
+    if (!cfg || !(cfg->huber_k > 0.0) || cfg->pattern_size < 1 ||
+        cfg->pattern_size > PBA_MAX_PATTERN || !cfg->pattern || cfg->n_bundles > 1 ||
+        cfg->gauge_anchor_w < 0.0 || cfg->max_stats_iters < 0)
+        return PBA_ERR_ARG;
+    for (int j = 0; j < 2 * cfg->pattern_size; ++j)
+        if (cfg->pattern[j] < -32 || cfg->pattern[j] > 32) return PBA_ERR_ARG;
+    pba_ctx* c = new (std::nothrow) pba_ctx();
+    if (!c) return PBA_ERR_NOMEM;
+    c->cfg = *cfg;
+    c->pattern.assign(cfg->pattern, cfg->pattern + 2 * cfg->pattern_size);
+    c->cfg.pattern = nullptr;
+    if (c->cfg.gauge_anchor_w == 0.0) c->cfg.gauge_anchor_w = 1.0;
+    if (c->cfg.conv_px == 0.0) c->cfg.conv_px = 5e-3;
+    if (c->cfg.max_stats_iters == 0) c->cfg.max_stats_iters = 256;
+    c->stream = (cudaStream_t)cfg->cuda_stream;
+    c->stats_slots = c->cfg.max_stats_iters + 1;
+    *out = c;
+    return PBA_OK;
+}
+
+void pba_destroy(pba_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    tcollect(ctx);
+    for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
+    delete ctx;
+}
+
+const char* pba_last_error(const pba_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+pba_status pba_set_frames(pba_ctx* ctx, int bundle, int n_frames, int w, int h, int pitch_elems,
+                          pba_dtype dtype, pba_memory mem, const void* images,
+                          const double* poses, const double* intrinsics)
+{
+    if (!ctx) return PBA_ERR_ARG;
+    if (bundle != 0) return fail(ctx, PBA_ERR_ARG, "bundle %d out of range (one bundle per context)", bundle);
+    if (n_frames < 2 || w < 4 || h < 4 || pitch_elems < w || !images || !poses || !intrinsics)
+        return fail(ctx, PBA_ERR_ARG, "invalid frame arguments");
+    if (dtype != PBA_F32 && dtype != PBA_F16 && dtype != PBA_BF16)
+        return fail(ctx, PBA_ERR_ARG, "invalid dtype");
+    if (mem != PBA_MEM_DEVICE && mem != PBA_MEM_HOST) return fail(ctx, PBA_ERR_ARG, "invalid memory kind");
+    if (6 * (n_frames - 1) > 6 * 1024) return fail(ctx, PBA_ERR_ARG, "too many frames");
+    if (mem == PBA_MEM_DEVICE && ((uintptr_t)images % elem_size(dtype)))
+        return fail(ctx, PBA_ERR_ARG, "misaligned image pointer");
+    for (int i = 0; i < 4; ++i)
+        if (!std::isfinite(intrinsics[i])) return fail(ctx, PBA_ERR_ARG, "non-finite intrinsics");
+    if (!(intrinsics[0] > 0 && intrinsics[1] > 0)) return fail(ctx, PBA_ERR_ARG, "focal lengths must be positive");
+    for (int i = 0; i < 12 * n_frames; ++i)
+        if (!std::isfinite(poses[i])) return fail(ctx, PBA_ERR_ARG, "non-finite pose");
+    static const double I12[12] = {1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0};
+    for (int i = 0; i < 12; ++i)
+        if (std::fabs(poses[i] - I12[i]) > 1e-9) return fail(ctx, PBA_ERR_ARG, "frame 0 pose must be the identity");
+    ctx->F = n_frames;
+    ctx->W = w;
+    ctx->H = h;
+    ctx->pitch = pitch_elems;
+    ctx->dtype = dtype;
+    ctx->mem = mem;
+    ctx->images = images;
+    ctx->poses_init.assign(poses, poses + 12 * n_frames);
+    std::memcpy(ctx->K, intrinsics, sizeof ctx->K);
+    ctx->have_frames = true;
+    ctx->ws_ready = ctx->ic_ready = false;
+    if (ctx->have_points && ctx->vis.size() != (size_t)ctx->N * n_frames) ctx->have_points = false;
+    return PBA_OK;
+}
+
+pba_status pba_set_points(pba_ctx* ctx, int bundle, int n_points, const int32_t* uv,
+                          const double* inv_depth, const uint8_t* vis)
+{
+    if (!ctx) return PBA_ERR_ARG;
+    if (bundle != 0) return fail(ctx, PBA_ERR_ARG, "bundle %d out of range (one bundle per context)", bundle);
+    if (!ctx->have_frames) return fail(ctx, PBA_ERR_STATE, "pba_set_frames must come first");
+    if (n_points < 1 || !uv || !inv_depth) return fail(ctx, PBA_ERR_ARG, "invalid point arguments");
+    int rad = 0;
+    for (int32_t o : ctx->pattern) rad = std::max(rad, std::abs(o));
+    rad += 1;  // central differences of the template
+    for (int n = 0; n < n_points; ++n) {
+        const int u = uv[2 * n], v = uv[2 * n + 1];
+        if (u - rad < 0 || u + rad > ctx->W - 1 || v - rad < 0 || v + rad > ctx->H - 1)
+            return fail(ctx, PBA_ERR_ARG, "point %d: pattern leaves the reference image", n);
+        if (!(inv_depth[n] > 0.0) || !std::isfinite(inv_depth[n]))
+            return fail(ctx, PBA_ERR_ARG, "point %d: inverse depth must be positive", n);
+    }
+    ctx->N = n_points;
+    ctx->uv.assign(uv, uv + 2 * n_points);
+    ctx->d_init.assign(inv_depth, inv_depth + n_points);
+    if (vis)
+        ctx->vis.assign(vis, vis + (size_t)n_points * ctx->F);
+    else
+        ctx->vis.assign((size_t)n_points * ctx->F, 1);
+    for (int n = 0; n < n_points; ++n) ctx->vis[(size_t)n * ctx->F] = 0;
+    ctx->have_points = true;
+    ctx->ws_ready = ctx->ic_ready = false;
+    build_structure(ctx);
+    return PBA_OK;
+}
+
+pba_status pba_workspace_size(pba_ctx* ctx, size_t* bytes)
+{
+    if (!ctx || !bytes) return PBA_ERR_ARG;
+    if (!ctx->have_frames || !ctx->have_points)
+        return fail(ctx, PBA_ERR_STATE, "frames and points must be set first");
+    *bytes = layout(ctx, nullptr);
+    return PBA_OK;
+}
+
+pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
+{
+    if (!ctx) return PBA_ERR_ARG;
+    if (!ctx->have_frames || !ctx->have_points)
+        return fail(ctx, PBA_ERR_STATE, "frames and points must be set first");
+    const size_t need = layout(ctx, nullptr);
+    if (!dev_ptr || bytes < need)
+        return fail(ctx, PBA_ERR_NOMEM, "workspace of %zu bytes needed, %zu given", need, bytes);
+    if ((uintptr_t)dev_ptr % kAlign) return fail(ctx, PBA_ERR_ARG, "workspace must be 256-byte aligned");
+    ctx->ws = (char*)dev_ptr;
+    ctx->ws_bytes = bytes;
+    layout(ctx, ctx->ws);
+    ctx->ic_ready = false;
+    CK(cudaMemsetAsync(ctx->ws, 0, need, ctx->stream));
+    if (ctx->mem == PBA_MEM_HOST)
+        CK(cudaMemcpyAsync(ctx->d.img, ctx->images,
+                           (size_t)ctx->F * ctx->H * ctx->pitch * elem_size(ctx->dtype),
+                           cudaMemcpyHostToDevice, ctx->stream));
+    const int Np = ctx->Npad, P = (int)ctx->pattern.size() / 2;
+    std::vector<int> uvs(2 * Np);
+    std::vector<float2> xn(Np);
+    std::vector<unsigned char> valid(Np, 0);
+    int last = ctx->perm[0];
+    for (int i = 0; i < Np; ++i) {
+        const int n = ctx->perm[i] >= 0 ? ctx->perm[i] : last;
+        if (ctx->perm[i] >= 0) last = ctx->perm[i];
+        uvs[2 * i] = ctx->uv[2 * n];
+        uvs[2 * i + 1] = ctx->uv[2 * n + 1];
+        xn[i] = make_float2((float)((uvs[2 * i] - ctx->K[2]) / ctx->K[0]),
+                            (float)((uvs[2 * i + 1] - ctx->K[3]) / ctx->K[1]));
+        valid[i] = ctx->perm[i] >= 0;
+    }
+    std::vector<int> pat(ctx->pattern.begin(), ctx->pattern.end());
+    CK(cudaMemcpyAsync(ctx->d.pat, pat.data(), sizeof(int) * pat.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.entries, ctx->entries.data(), sizeof(Entry) * ctx->entries.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.tile_entry, ctx->tile_entry.data(), sizeof(int) * ctx->tile_entry.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.frame_entry, ctx->frame_entry.data(), sizeof(int) * ctx->frame_entry.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.frame_entries, ctx->frame_entries.data(), sizeof(int) * ctx->frame_entries.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.ent_of, ctx->ent_of.data(), sizeof(int) * ctx->ent_of.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.uvs, uvs.data(), sizeof(int) * uvs.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.xn, xn.data(), sizeof(float2) * xn.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.valid_pt, valid.data(), valid.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.frame_pairs, ctx->frame_pairs.data(), sizeof(int2) * ctx->frame_pairs.size(), cudaMemcpyHostToDevice, ctx->stream));
+    pba_status s = upload_params(ctx, ctx->poses_init.data(), ctx->d_init.data());
+    if (s != PBA_OK) return s;
+    CK(cudaMemcpyAsync(ctx->d.poses0_64, ctx->poses_init.data(), sizeof(double) * 12 * ctx->F, cudaMemcpyHostToDevice, ctx->stream));
+    CK(set_pass_smem_limits(ctx->F));
+    LaunchCtx L = make_launch(ctx);
+    LAUNCH(TS_PRE, launch_setup(L.pb, ctx->d.gx, ctx->d.gy, ctx->d.I0p, ctx->stream));
+    (void)P;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->ws_ready = true;
+    return PBA_OK;
+}
+
+pba_status pba_precompute_ic(pba_ctx* ctx)
+{
+    if (!ctx) return PBA_ERR_ARG;
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    const int F = ctx->F, n6 = 6 * (F - 1);
+    LaunchCtx L = make_launch(ctx);
+    // the current parameters become p_0
+    CK(cudaMemcpyAsync(ctx->d.poses0_64, ctx->d.poses64, sizeof(double) * 12 * F, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.d0_64, ctx->d.d64, sizeof(double) * ctx->Npad, cudaMemcpyDeviceToDevice, ctx->stream));
+    LAUNCH(TS_PRE, launch_ic_precompute(L));
+    LAUNCH(TS_PRE, launch_frame_reduce(L, 0, 21, ctx->d.red_ic, -1, -1, true));
+    LAUNCH(TS_PRE, launch_schur_offdiag(L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, ctx->d.frame_pairs,
+                                        (int)ctx->frame_pairs.size(), ctx->d.Soff, ctx->stream));
+    LAUNCH(TS_PRE, launch_assemble_S(F, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64,
+                                     ctx->cfg.gauge_anchor_w, ctx->d.S_ic, ctx->d.active, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.L_ic, ctx->d.S_ic, sizeof(double) * n6 * n6, cudaMemcpyDeviceToDevice, ctx->stream));
+    LAUNCH(TS_PRE, launch_cholesky(ctx->d.L_ic, n6, ctx->d.err, ctx->stream));
+    LAUNCH(TS_PRE, launch_chol_inverse(ctx->d.L_ic, ctx->d.Sinv, n6, ctx->stream));
+    pba_status s = check_device_error(ctx);
+    if (s != PBA_OK) return s;
+    ctx->ic_ready = true;
+    return PBA_OK;
+}
+
+pba_status pba_iterate(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
+{
+    if (!ctx) return PBA_ERR_ARG;
+    if (!ctx->ic_ready) return fail(ctx, PBA_ERR_STATE, "pba_precompute_ic must come first");
+    if (n_iters < 0 || n_iters > ctx->cfg.max_stats_iters)
+        return fail(ctx, PBA_ERR_ARG, "n_iters must be in [0, %d]", ctx->cfg.max_stats_iters);
+    LaunchCtx L = make_launch(ctx);
+    SolveArgs sa = make_solve(ctx);
+    for (int k = 0; k < n_iters; ++k) {
+        LAUNCH(TS_PASS, launch_ic_pass(L, true, k > 0, k > 0));
+        LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 6, ctx->d.red_y, k, k - 1, true));
+        LAUNCH(TS_SOLVE, launch_ic_solve_update(sa, ctx->d.Sinv, ctx->d.red_y, 6, 0, ctx->stream));
+    }
+    LAUNCH(TS_EVAL, launch_ic_pass(L, false, n_iters > 0, n_iters > 0));
+    LAUNCH(TS_EVAL, launch_frame_reduce(L, 0, 0, nullptr, n_iters, n_iters - 1, false));
+    ctx->last_fc = 0;
+    return copy_stats(ctx, n_iters, stats);
+}
+
+pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
+{
+    if (!ctx) return PBA_ERR_ARG;
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    if (n_iters < 0 || n_iters > ctx->cfg.max_stats_iters)
+        return fail(ctx, PBA_ERR_ARG, "n_iters must be in [0, %d]", ctx->cfg.max_stats_iters);
+    const int F = ctx->F, n6 = 6 * (F - 1);
+    LaunchCtx L = make_launch(ctx);
+    SolveArgs sa = make_solve(ctx);
+    for (int k = 0; k < n_iters; ++k) {
+        LAUNCH(TS_PASS, launch_fc_pass(L, true, k > 0, k > 0));
+        LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 27, ctx->d.red_y, k, k - 1, true));
+        LAUNCH(TS_SCHUR, launch_schur_offdiag(L.pb, ctx->d.Hfd_fc, ctx->d.Hnn_fc, ctx->d.frame_pairs,
+                                              (int)ctx->frame_pairs.size(), ctx->d.Soff, ctx->stream));
+        LAUNCH(TS_SCHUR, launch_assemble_S(F, ctx->d.red_y, 27, ctx->d.Soff, ctx->d.poses64,
+                                           ctx->cfg.gauge_anchor_w, ctx->d.S_fc, ctx->d.active, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d.L_fc, ctx->d.S_fc, sizeof(double) * n6 * n6, cudaMemcpyDeviceToDevice, ctx->stream));
+        LAUNCH(TS_SOLVE, launch_cholesky(ctx->d.L_fc, n6, ctx->d.err, ctx->stream));
+        LAUNCH(TS_SOLVE, launch_fc_solve_update(sa, ctx->d.L_fc, ctx->d.red_y, 27, 21, ctx->stream));
+    }
+    LAUNCH(TS_EVAL, launch_fc_pass(L, false, n_iters > 0, n_iters > 0));
+    LAUNCH(TS_EVAL, launch_frame_reduce(L, 0, 0, nullptr, n_iters, n_iters - 1, false));
+    ctx->last_fc = 1;
+    return copy_stats(ctx, n_iters, stats);
+}
+
+pba_status pba_get_params(pba_ctx* ctx, int bundle, double* poses, double* inv_depth)
+{
+    if (!ctx || bundle != 0) return PBA_ERR_ARG;
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (poses) CK(cudaMemcpy(poses, ctx->d.poses64, sizeof(double) * 12 * ctx->F, cudaMemcpyDeviceToHost));
+    if (inv_depth) {
+        std::vector<double> ds(ctx->Npad);
+        CK(cudaMemcpy(ds.data(), ctx->d.d64, sizeof(double) * ds.size(), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < ctx->Npad; ++i)
+            if (ctx->perm[i] >= 0) inv_depth[ctx->perm[i]] = ds[i];
+    }
+    return PBA_OK;
+}
+
+pba_status pba_set_params(pba_ctx* ctx, int bundle, const double* poses, const double* inv_depth)
+{
+    if (!ctx || bundle != 0 || !poses || !inv_depth) return PBA_ERR_ARG;
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    for (int i = 0; i < 12 * ctx->F; ++i)
+        if (!std::isfinite(poses[i])) return fail(ctx, PBA_ERR_ARG, "non-finite pose");
+    for (int n = 0; n < ctx->N; ++n)
+        if (!(inv_depth[n] > 0.0) || !std::isfinite(inv_depth[n]))
+            return fail(ctx, PBA_ERR_ARG, "point %d: inverse depth must be positive", n);
+    return upload_params(ctx, poses, inv_depth);
+}
+
+pba_status pba_get_last_update(pba_ctx* ctx, int bundle, double* dtheta, double* dd)
+{
+    if (!ctx || bundle != 0) return PBA_ERR_ARG;
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (dtheta) CK(cudaMemcpy(dtheta, ctx->d.dtheta64, sizeof(double) * 6 * ctx->F, cudaMemcpyDeviceToHost));
+    if (dd) {
+        std::vector<double> h(ctx->Npad);
+        CK(cudaMemcpy(h.data(), ctx->d.dd_last, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < ctx->Npad; ++i)
+            if (ctx->perm[i] >= 0) dd[ctx->perm[i]] = h[i];
+    }
+    return PBA_OK;
+}
+
+pba_status pba_get_system(pba_ctx* ctx, int bundle, int fc, double* Hff, double* Hfd, double* Hdd,
+                          double* S)
+{
+    if (!ctx || bundle != 0) return PBA_ERR_ARG;
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    if (!fc && !ctx->ic_ready) return fail(ctx, PBA_ERR_STATE, "no IC system yet");
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int F = ctx->F, n6 = 6 * (F - 1);
+    if (Hff) {
+        const int stride = fc ? 27 : 21;
+        std::vector<double> r((size_t)F * stride);
+        CK(cudaMemcpy(r.data(), fc ? ctx->d.red_y : ctx->d.red_ic, sizeof(double) * r.size(), cudaMemcpyDeviceToHost));
+        std::memset(Hff, 0, sizeof(double) * 36 * F);
+        for (int f = 1; f < F; ++f) {
+            int q = 0;
+            for (int a = 0; a < 6; ++a)
+                for (int b = a; b < 6; ++b, ++q)
+                    Hff[36 * f + 6 * a + b] = Hff[36 * f + 6 * b + a] = r[(size_t)f * stride + q];
+        }
+    }
+    if (Hfd) {
+        std::vector<float> h((size_t)ctx->V * 6);
+        CK(cudaMemcpy(h.data(), fc ? ctx->d.Hfd_fc : ctx->d.Hfd_ic, sizeof(float) * h.size(), cudaMemcpyDeviceToHost));
+        std::memset(Hfd, 0, sizeof(double) * 6 * (size_t)ctx->N * F);
+        for (const Entry& e : ctx->entries) {
+            const int nvis = __builtin_popcount(e.mask);
+            for (int l = 0; l < kTile; ++l) {
+                if (!((e.mask >> l) & 1u)) continue;
+                const int rank = __builtin_popcount(e.mask & ((1u << l) - 1u));
+                const int n = ctx->perm[e.tile * kTile + l];
+                for (int k = 0; k < 6; ++k)
+                    Hfd[((size_t)n * F + e.f) * 6 + k] = h[(size_t)e.pair_off * 6 + (size_t)k * nvis + rank];
+            }
+        }
+    }
+    if (Hdd) {
+        std::vector<float> h(ctx->Npad);
+        CK(cudaMemcpy(h.data(), fc ? ctx->d.Hnn_fc : ctx->d.Hnn_ic, sizeof(float) * h.size(), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < ctx->Npad; ++i)
+            if (ctx->perm[i] >= 0) Hdd[ctx->perm[i]] = h[i];
+    }
+    if (S) CK(cudaMemcpy(S, fc ? ctx->d.S_fc : ctx->d.S_ic, sizeof(double) * n6 * n6, cudaMemcpyDeviceToHost));
+    return PBA_OK;
+}
+
+pba_status pba_num_residuals(pba_ctx* ctx, int bundle, int64_t* n)
+{
+    if (!ctx || bundle != 0 || !n) return PBA_ERR_ARG;
+    if (!ctx->have_points) return fail(ctx, PBA_ERR_STATE, "points not set");
+    *n = ctx->V * (int64_t)(ctx->pattern.size() / 2);
+    return PBA_OK;
+}
+
+pba_status pba_enable_timing(pba_ctx* ctx, int on)
+{
+    if (!ctx) return PBA_ERR_ARG;
+    ctx->timing = on != 0;
+    for (int i = 0; i < TS_N; ++i) {
+        ctx->tms[i] = 0.0;
+        ctx->tcount[i] = 0;
+    }
+    ctx->launches = 0;
+    return PBA_OK;
+}
+
+pba_status pba_last_timing(pba_ctx* ctx, double* ms)
+{
+    if (!ctx || !ms) return PBA_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    tcollect(ctx);
+    for (int i = 0; i < TS_N; ++i) ms[i] = ctx->tms[i];
+    ms[TS_N] = (double)ctx->launches;
+    for (int i = 0; i < TS_N; ++i) ms[TS_N + 1 + i] = (double)ctx->tcount[i];
+    return PBA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,255 @@
+"""GPU path (libpba.so through its C ABI) against the FP64 CPU oracle.
+
+Every case uses the same seeded synthetic inputs on both sides. The bar:
+  * per-iteration update, from an identical input state (teacher forced):
+    |Dp_gpu - Dp_oracle| / max(|Dp_oracle|, 1e-3 |Dp_oracle at p0|) <= 1e-4;
+  * 20-iteration trajectories on converging scenes: poses within 1e-3 deg and
+    1e-5 scene units, inverse depths within 1e-5 relative;
+  * Hessian blocks and the anchored Schur complement within 1e-4 of their
+    largest entry; valid-residual counts exact; energy/RMS within 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_06967_gb300 import build
+    build.build()
+    return torch
+
+
+def _bundle(sc, **kw):
+    from paper_1704_06967_gb300 import Bundle
+    return Bundle.from_scene(sc, **kw)
+
+
+def _step_err(dth, dd, o_dth, o_dd, ref0):
+    got = np.concatenate([dth[1:].ravel(), dd])
+    ref = np.concatenate([o_dth[1:].ravel(), o_dd])
+    return np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-3 * ref0)
+
+
+def _pose_err(Pa, Pb):
+    rot, tr = 0.0, 0.0
+    for f in range(1, Pa.shape[0]):
+        Ra, Rb = Pa[f, :9].reshape(3, 3), Pb[f, :9].reshape(3, 3)
+        c = np.clip((np.trace(Ra @ Rb.T) - 1) / 2, -1, 1)
+        rot = max(rot, math.degrees(math.acos(c)))
+        tr = max(tr, np.abs(Pa[f, 9:] - Pb[f, 9:]).max())
+    return rot, tr
+
+
+# ----------------------------------------------------------------------------
+# IC precompute: H blocks and the reduced camera system
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["tiny", "small"])
+def test_ic_precompute_blocks_match_oracle(torch_cuda, name):
+    sc = synth.make_scene(name)
+    pb = oracle.Problem.from_scene(sc)
+    pre = oracle.ic_precompute(pb, sc.poses0, sc.depths0)
+    b = _bundle(sc)
+    b.precompute_ic()
+    sysg = b.system(fc=False)
+    for key, ref in (("Hff", pre.Hff), ("Hfd", pre.Hfd), ("Hdd", pre.Hdd)):
+        got = sysg[key]
+        assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max(), key
+    g_theta, g_d, _ = oracle.ic_gradient(pb, pre, sc.poses0, sc.depths0)
+    _, _, S = oracle.schur_solve(pb.F, pb.N, pre.Hff, pre.Hfd, pre.Hdd, g_theta, g_d,
+                                 sc.poses0[:, 9:], want_S=True)
+    assert np.abs(sysg["S"] - S).max() <= 1e-4 * np.abs(S).max()
+    assert np.array_equal(sysg["S"], sysg["S"].T)
+
+
+# ----------------------------------------------------------------------------
+# teacher-forced single steps
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["tiny", "small", "ring5"])
+def test_ic_step_matches_oracle_from_identical_states(torch_cuda, name):
+    sc = synth.make_scene(name)
+    pb = oracle.Problem.from_scene(sc)
+    pre = oracle.ic_precompute(pb, sc.poses0, sc.depths0)
+    b = _bundle(sc)
+    b.precompute_ic()
+    poses, depths = sc.poses0.copy(), sc.depths0.copy()
+    ref0 = None
+    for k in range(4):
+        b.set_params(poses, depths)
+        st = b.iterate(1)
+        dth, dd = b.last_update()
+        o_dth, o_dd, P1, D1, o_st = oracle.ic_step(pb, pre, sc.poses0, sc.depths0, poses, depths)
+        if ref0 is None:
+            ref0 = np.linalg.norm(np.concatenate([o_dth[1:].ravel(), o_dd]))
+        err = _step_err(dth, dd, o_dth, o_dd, ref0)
+        assert err <= STEP_TOL, (k, err)
+        assert st[0, 2] == o_st[oracle.ST_COUNT]
+        assert abs(st[0, 0] - o_st[oracle.ST_ENERGY]) <= 1e-5 * o_st[oracle.ST_ENERGY]
+        assert abs(st[0, 1] - o_st[oracle.ST_RMS]) <= 1e-5 * o_st[oracle.ST_RMS]
+        poses, depths = P1, D1
+
+
+@pytest.mark.parametrize("name", ["tiny", "small", "ring5"])
+def test_fc_step_matches_oracle_from_identical_states(torch_cuda, name):
+    sc = synth.make_scene(name)
+    pb = oracle.Problem.from_scene(sc)
+    b = _bundle(sc)
+    poses, depths = sc.poses0.copy(), sc.depths0.copy()
+    ref0 = None
+    for k in range(4):
+        b.set_params(poses, depths)
+        st = b.solve_fc(1)
+        dth, dd = b.last_update()
+        o_dth, o_dd, P1, D1, o_st = oracle.fc_step(pb, poses, depths)
+        if ref0 is None:
+            ref0 = np.linalg.norm(np.concatenate([o_dth[1:].ravel(), o_dd]))
+        err = _step_err(dth, dd, o_dth, o_dd, ref0)
+        assert err <= STEP_TOL, (k, err)
+        assert st[0, 2] == o_st[oracle.ST_COUNT]
+        poses, depths = P1, D1
+
+
+def test_fc_system_matches_oracle(torch_cuda):
+    sc = synth.make_scene("small")
+    pb = oracle.Problem.from_scene(sc)
+    b = _bundle(sc)
+    b.solve_fc(1)
+    g = b.system(fc=True)
+    Hff, Hfd, Hdd, g_theta, g_d, _ = oracle.fc_linearize(pb, sc.poses0, sc.depths0)
+    for key, ref in (("Hff", Hff), ("Hfd", Hfd), ("Hdd", Hdd)):
+        assert np.abs(g[key] - ref).max() <= 1e-4 * np.abs(ref).max(), key
+
+
+# ----------------------------------------------------------------------------
+# whole trajectories where both methods converge
+# ----------------------------------------------------------------------------
+def test_ic_trajectory_matches_oracle(torch_cuda):
+    sc = synth.make_scene("cards", rot_deg=0.5, trans=0.005, sigma_d=0.01)
+    pb = oracle.Problem.from_scene(sc)
+    P, D, hist = oracle.ic_run(pb, sc.poses0, sc.depths0, 20)
+    b = _bundle(sc)
+    b.precompute_ic()
+    st = b.iterate(20)
+    Pg, Dg = b.params()
+    rot, tr = _pose_err(Pg, P)
+    assert rot <= 1e-3 and tr <= 1e-5, (rot, tr)
+    assert np.abs(Dg / D - 1).max() <= 1e-5
+    assert np.abs(st[:, 1] - hist[:, 1]).max() <= 1e-4 * hist[0, 1]
+
+
+def test_fc_trajectory_matches_oracle(torch_cuda):
+    sc = synth.make_scene("cards")
+    pb = oracle.Problem.from_scene(sc)
+    P, D, hist = oracle.fc_run(pb, sc.poses0, sc.depths0, 20)
+    b = _bundle(sc)
+    st = b.solve_fc(20)
+    Pg, Dg = b.params()
+    rot, tr = _pose_err(Pg, P)
+    assert rot <= 1e-3 and tr <= 1e-5, (rot, tr)
+    assert np.abs(Dg / D - 1).max() <= 1e-5
+    assert np.abs(st[:, 1] - hist[:, 1]).max() <= 1e-4 * hist[0, 1]
+
+
+# ----------------------------------------------------------------------------
+# full-size helix (the benchmark workload): one teacher-forced step each
+# ----------------------------------------------------------------------------
+def test_helix30_full_size_steps(torch_cuda):
+    sc = synth.make_scene("helix30")
+    pb = oracle.Problem.from_scene(sc)
+    b = _bundle(sc)
+    assert b.n_residuals() == sc.n_residuals()
+    b.precompute_ic()
+    st = b.iterate(1)
+    dth, dd = b.last_update()
+    pre = oracle.ic_precompute(pb, sc.poses0, sc.depths0)
+    o_dth, o_dd, _, _, o_st = oracle.ic_step(pb, pre, sc.poses0, sc.depths0, sc.poses0, sc.depths0)
+    ref0 = np.linalg.norm(np.concatenate([o_dth[1:].ravel(), o_dd]))
+    assert _step_err(dth, dd, o_dth, o_dd, ref0) <= STEP_TOL
+    assert st[0, 2] == o_st[oracle.ST_COUNT]
+    b.set_params(sc.poses0, sc.depths0)
+    b.solve_fc(1)
+    dth, dd = b.last_update()
+    o_dth, o_dd, _, _, _ = oracle.fc_step(pb, sc.poses0, sc.depths0)
+    ref0 = np.linalg.norm(np.concatenate([o_dth[1:].ravel(), o_dd]))
+    assert _step_err(dth, dd, o_dth, o_dd, ref0) <= STEP_TOL
+    # 20 more iterations run without device errors, counts stay sane
+    b.set_params(sc.poses0, sc.depths0)
+    st = b.iterate(20)
+    assert np.isfinite(st).all() and (st[:, 2] > 0).all()
+
+
+# ----------------------------------------------------------------------------
+# storage types, host images, edge cases, determinism
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_half_precision_images(torch_cuda, dtype):
+    sc = synth.make_scene("small", dtype=dtype)
+    pb = oracle.Problem.from_scene(sc)
+    pre = oracle.ic_precompute(pb, sc.poses0, sc.depths0)
+    b = _bundle(sc)
+    b.precompute_ic()
+    b.iterate(1)
+    dth, dd = b.last_update()
+    o_dth, o_dd, _, _, _ = oracle.ic_step(pb, pre, sc.poses0, sc.depths0, sc.poses0, sc.depths0)
+    ref0 = np.linalg.norm(np.concatenate([o_dth[1:].ravel(), o_dd]))
+    assert _step_err(dth, dd, o_dth, o_dd, ref0) <= STEP_TOL
+
+
+def test_host_images_equal_device_images(torch_cuda):
+    sc = synth.make_scene("small")
+    a = _bundle(sc)
+    h = _bundle(sc, device_images=False)
+    for b in (a, h):
+        b.precompute_ic()
+        b.iterate(3)
+    Pa, Da = a.params()
+    Ph, Dh = h.params()
+    assert np.array_equal(Pa, Ph) and np.array_equal(Da, Dh)
+
+
+def test_runs_are_bitwise_deterministic(torch_cuda):
+    sc = synth.make_scene("ring5")
+    out = []
+    for _ in range(2):
+        b = _bundle(sc)
+        b.precompute_ic()
+        st = b.iterate(5)
+        P, D = b.params()
+        st2 = b.solve_fc(2)
+        P2, D2 = b.params()
+        out.append((st, P, D, st2, P2, D2))
+    for x, y in zip(out[0], out[1]):
+        assert np.array_equal(x, y)
+
+
+def test_ragged_tile_single_pixel_pattern_and_empty_rows(torch_cuda):
+    """N = 33 (one full tile and a tail of one), a frame that sees no point,
+    a point that no frame sees, and a one-pixel pattern."""
+    sc = synth.make_scene("small", n_points=33)
+    sc.vis[:, 2] = 0                 # frame 2 inactive
+    sc.vis[5, :] = 0                 # point 5 unobserved
+    for pattern in (synth.PATTERN8, np.zeros((1, 2), np.int32)):
+        sc.pattern = pattern
+        pb = oracle.Problem.from_scene(sc)
+        pre = oracle.ic_precompute(pb, sc.poses0, sc.depths0)
+        b = _bundle(sc)
+        b.precompute_ic()
+        st = b.iterate(1)
+        dth, dd = b.last_update()
+        o_dth, o_dd, P1, D1, o_st = oracle.ic_step(pb, pre, sc.poses0, sc.depths0, sc.poses0,
+                                                    sc.depths0)
+        ref0 = np.linalg.norm(np.concatenate([o_dth[1:].ravel(), o_dd]))
+        assert _step_err(dth, dd, o_dth, o_dd, ref0) <= STEP_TOL
+        assert np.all(dth[2] == 0.0) and dd[5] == 0.0
+        assert st[0, 2] == o_st[oracle.ST_COUNT]
