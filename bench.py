@@ -1,0 +1,419 @@
+#!/usr/bin/env python3
+"""Benchmark: IC-PBA iterations/s and residuals/s against FC on one GB300.
+
+Workload: the 30-frame, 2-turn helix bundle around a textured sphere
+(640x480 FP32 images, f = 525, 20,000 points with an 8-pixel pattern,
+reduced camera system 174 x 174), perturbed by 2 deg / 0.02 / 5 %.
+A step is one complete IC solve of the bundle from p_0 with the inputs
+resident in HBM: precompute (J, H, Schur complement, FP64 Cholesky and
+inverse) + 20 IC iterations. `value` = IC iterations per second over the
+timed steps (precompute amortised over the 20 iterations). FC solves of the
+same bundle (20 iterations each, Hessian and Cholesky rebuilt every
+iteration) are timed the same way beside it. L2 is flushed (512 MB write)
+between timed steps, outside the per-step CUDA events.
+
+--gpus N under torchrun runs N independent replicas (one bundle per rank,
+seeded by rank; no collective on the data path) and reports the aggregate.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "IC-PBA iterations/s & residuals/s vs FC on same GB300 at equal final RMS error"
+UNIT = "iterations/s"
+SCENE = "helix30"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--iters", type=int, default=20, help="IC / FC iterations per solve")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload_config(sc, iters):
+    return {"workload": f"{SCENE}: 30-frame 2-turn helix around a value-noise sphere, "
+                        f"{sc.W}x{sc.H} FP32, f={sc.fx:g}, {sc.N} points x 8-pixel pattern, "
+                        f"2 deg/0.02/5% perturbation, {iters} iterations per solve",
+            "frames": sc.F, "points": sc.N, "pattern": sc.P,
+            "residuals_per_iter": sc.n_residuals(), "reduced_system": 6 * (sc.F - 1),
+            "image": f"{sc.W}x{sc.H} {sc.dtype}", "iterations_per_step": iters,
+            "l2": "flushed (512 MB write) between timed steps"}
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.dev = device_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.dev:
+                cmd += ["-i", self.dev]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def device_uuid(torch):
+    try:
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, on a bounded sample
+# ----------------------------------------------------------------------------
+def oracle_sample(sc, iters, n_steps=2):
+    import oracle
+    pb = oracle.Problem.from_scene(sc)
+    t0 = time.perf_counter()
+    pre = oracle.ic_precompute(pb, sc.poses0, sc.depths0)
+    t_pre = time.perf_counter() - t0
+    poses, depths = sc.poses0, sc.depths0
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        _, _, poses, depths, _ = oracle.ic_step(pb, pre, sc.poses0, sc.depths0, poses, depths)
+    t_it = (time.perf_counter() - t0) / n_steps
+    value = iters / (t_pre + iters * t_it)
+    return value, t_pre, t_it
+
+
+# ----------------------------------------------------------------------------
+# reference arm
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    import synth
+    sc = synth.make_scene(SCENE)
+    pb = oracle.Problem.from_scene(sc)
+    t0 = time.perf_counter()
+    pre = oracle.ic_precompute(pb, sc.poses0, sc.depths0)
+    t_pre = time.perf_counter() - t0
+    poses, depths = sc.poses0, sc.depths0
+    for _ in range(args.warmup):
+        _, _, poses, depths, _ = oracle.ic_step(pb, pre, sc.poses0, sc.depths0, poses, depths)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, _, poses, depths, _ = oracle.ic_step(pb, pre, sc.poses0, sc.depths0, poses, depths)
+        times.append(time.perf_counter() - t0)
+    t_it = float(np.mean(times))
+    value = args.iters / (t_pre + args.iters * t_it)
+    sample = (f"one FP64 oracle IC iteration per step on the full {SCENE} bundle, precompute "
+              f"({t_pre:.2f} s) timed once and amortised over {args.iters} iterations")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t_it, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(sc, args.iters),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "residuals_per_s": value * sc.n_residuals()}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1704_06967_gb300 import Bundle
+    from paper_1704_06967_gb300 import build as pkg_build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        log(f"warning: --gpus {args.gpus} but WORLD_SIZE {world}")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        pkg_build.build()
+    if dist is not None:
+        dist.barrier()
+
+    iters = args.iters
+    sc = synth.make_scene(SCENE, seed_offset=rank)
+    b = Bundle.from_scene(sc)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def l2_flush(k):
+        flush.fill_(k & 0xFF)
+
+    def ic_solve(stats=False):
+        b.set_params(sc.poses0, sc.depths0)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        b.precompute_ic()
+        e1.record(stream)
+        st = b.iterate(iters, stats=stats)
+        e2.record(stream)
+        e2.synchronize()
+        return e0.elapsed_time(e1), e0.elapsed_time(e2), st
+
+    def fc_solve(stats=False):
+        b.set_params(sc.poses0, sc.depths0)
+        e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        e0.record(stream)
+        st = b.solve_fc(iters, stats=stats)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), st
+
+    # warm-up
+    for i in range(args.warmup):
+        l2_flush(i)
+        ic_solve()
+        l2_flush(i + 1)
+        fc_solve()
+    torch.cuda.synchronize()
+
+    # timed IC steps (kernel events around the residual pass only)
+    clocks = ClockSampler(device_uuid(torch))
+    clocks.start()
+    b.enable_timing(1 << 1)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    pre_ms, ic_ms = [], []
+    for i in range(args.steps):
+        l2_flush(i)
+        p, t, _ = ic_solve()
+        pre_ms.append(p)
+        ic_ms.append(t)
+    torch.cuda.synchronize()
+    kms, launches, kcounts = b.timing()
+    ic_launches = launches
+    b.enable_timing(0)
+    # FC steps, same protocol
+    b.enable_timing(0)
+    fc_ms = []
+    for i in range(args.steps):
+        l2_flush(i + 7)
+        t, _ = fc_solve()
+        fc_ms.append(t)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+
+    total_ic = sum(ic_ms)
+    if dist is not None:
+        tt = torch.tensor([total_ic, sum(fc_ms)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ic, total_fc = float(tt[0]), float(tt[1])
+    else:
+        total_fc = sum(fc_ms)
+    R = sc.n_residuals()
+    value = world * iters * args.steps / (total_ic / 1e3)
+    fc_value = world * iters * args.steps / (total_fc / 1e3)
+
+    # statistics trajectories for the equal-RMS comparison (untimed)
+    _, _, st_ic = ic_solve(stats=True)
+    _, st_fc = fc_solve(stats=True)
+    pre_avg = statistics.mean(pre_ms)
+    it_ic = (statistics.mean(ic_ms) - pre_avg) / iters
+    it_fc = statistics.mean(fc_ms) / iters
+    target = max(st_ic[-1, 1], st_fc[-1, 1])
+    k_ic = int(np.argmax(st_ic[:, 1] <= target * (1 + 1e-12)))
+    k_fc = int(np.argmax(st_fc[:, 1] <= target * (1 + 1e-12)))
+    t_ic = pre_avg + k_ic * it_ic
+    t_fc = k_fc * it_fc
+
+    # per-kernel breakdown of one IC and one FC solve (diagnostic, untimed)
+    b.enable_timing(-1)
+    l2_flush(3)
+    ic_solve()
+    ic_break, _, _ = b.timing()
+    b.enable_timing(-1)
+    l2_flush(4)
+    fc_solve()
+    fc_break, _, _ = b.timing()
+    b.enable_timing(0)
+
+    # roofline of the IC residual pass (algorithmic bytes per launch)
+    V = R // sc.P
+    img_bytes = sc.F * sc.H * sc.W * (4 if sc.dtype == "f32" else 2)
+    alg_bytes = R * 28 + V * 24 + sc.N * sc.P * 4 + sc.N * 16 + img_bytes
+    pass_ms = kms["pass"] / max(1, kcounts["pass"])
+    hbm_peak, peak_src = measured_peaks()
+    achieved = alg_bytes / (pass_ms * 1e-3) / 1e9
+    roofline = {"kernel": "ic_pass_kernel", "bound": "hbm", "achieved": achieved,
+                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+                "traffic": None, "algorithmic_bytes_per_launch": alg_bytes,
+                "avg_launch_ms": pass_ms, "launches": int(kcounts["pass"])}
+    traffic_file = os.path.join(ROOT, "profiles", "ic_pass_traffic.json")
+    if os.path.exists(traffic_file):
+        try:
+            tr = json.load(open(traffic_file))
+            if tr.get("kernel_sha") == kernel_sha() and tr.get("residuals") == R:
+                roofline["traffic"] = tr["dram_bytes_per_launch"]
+        except Exception:
+            pass
+
+    # end to end: host buffers through the C ABI (pinned host images)
+    pinned = torch.empty(sc.images_store.shape, dtype=torch.float32, pin_memory=True)
+    pinned.numpy()[...] = sc.images_store
+    host_imgs = pinned.numpy()
+    e2e_t, h2d_b, d2h_b = [], 0, 0
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eb = Bundle(host_imgs, sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis,
+                    pattern=sc.pattern, huber_k=sc.huber_k)
+        eb.precompute_ic()
+        eb.iterate(iters, stats=False)
+        P, D = eb.params()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_t.append(t1 - t0)
+            h2d_b, d2h_b = eb.transfer_bytes()
+        eb.close()
+    e2e_total = sum(e2e_t)
+    if dist is not None:
+        tt = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_total = float(tt[0])
+    e2e_value = world * iters * args.steps / e2e_total
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cv, ct_pre, ct_it = oracle_sample(sc, iters)
+        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 oracle on the full {SCENE} bundle: IC precompute ({ct_pre:.2f} s) "
+                         f"+ 2 IC iterations ({ct_it:.2f} s each), extrapolated to a "
+                         f"{iters}-iteration solve; single thread"}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": total_ic / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": workload_config(sc, iters),
+               "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_b,
+                       "d2h_bytes_per_step": d2h_b},
+               "gpu_launches": int(ic_launches), "roofline": roofline,
+               "cpu_baseline": cpu, "clocks": clk,
+               "residuals_per_s": value * R,
+               "ic": {"precompute_ms": pre_avg, "iteration_ms": it_ic,
+                      "final_rms": float(st_ic[-1, 1])},
+               "fc": {"iterations_per_s": fc_value, "residuals_per_s": fc_value * R,
+                      "ms_per_solve": total_fc / args.steps, "iteration_ms": it_fc,
+                      "final_rms": float(st_fc[-1, 1])},
+               "ic_over_fc_iterations_per_s": value / fc_value,
+               "equal_rms": {"target_rms": float(target), "ic_iterations": k_ic,
+                             "fc_iterations": k_fc, "ic_ms": t_ic, "fc_ms": t_fc,
+                             "fc_over_ic_time": (t_fc / t_ic) if t_ic > 0 else None},
+               "kernel_ms_per_solve": {"ic": ic_break, "fc": fc_break}}
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    b.close()
+    return 0
+
+
+def kernel_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("pba_pass.cu", "pba_internal.cuh", "pba_kernels.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1704_06967_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -171,18 +171,23 @@ pba_status pba_get_system(pba_ctx* ctx, int bundle, int fc, double* Hff, double*
 /* Residual count of the bundle (visible (point, frame) pairs times P). */
 pba_status pba_num_residuals(pba_ctx* ctx, int bundle, int64_t* n);
 
-/* Kernel timing. pba_enable_timing(ctx, 1) starts recording a CUDA event pair
- * on the context's stream around every kernel launch (and resets the
- * counters); 0 stops recording. pba_last_timing synchronises the stream and
- * fills out[2 * PBA_TIMING_SLOTS + 1]: out[s] = accumulated device ms of slot
- * s, out[PBA_TIMING_SLOTS] = kernel launches since the reset (counted whether
- * or not timing is on), out[PBA_TIMING_SLOTS + 1 + s] = timed launches of
- * slot s. Slots: 0 setup / IC precompute, 1 residual pass, 2 per-frame
- * reduction, 3 Schur complement + assembly (FC), 4 factorisation / solve /
- * pose update, 5 final evaluation pass. */
+/* Kernel timing. pba_enable_timing(ctx, mask) records a CUDA event pair on
+ * the context's stream around every kernel launch of the slots whose bit is
+ * set in mask (-1: all slots, 0: none) and resets the counters.
+ * pba_last_timing synchronises the stream and fills out[2 * PBA_TIMING_SLOTS
+ * + 1]: out[s] = accumulated device ms of slot s, out[PBA_TIMING_SLOTS] =
+ * kernel launches since the reset (counted whether or not timing is on),
+ * out[PBA_TIMING_SLOTS + 1 + s] = timed launches of slot s. Slots: 0 setup /
+ * IC precompute, 1 residual pass, 2 per-frame reduction, 3 Schur complement +
+ * assembly (FC), 4 factorisation / solve / pose update, 5 final evaluation. */
 #define PBA_TIMING_SLOTS 6
-pba_status pba_enable_timing(pba_ctx* ctx, int on);
+pba_status pba_enable_timing(pba_ctx* ctx, int mask);
 pba_status pba_last_timing(pba_ctx* ctx, double* out);
+
+/* Bytes this context copied host->device and device->host since it was
+ * created (uploads of images, points, structure and parameters; downloads of
+ * statistics, parameters, updates and systems). Host, nullable each. */
+pba_status pba_transfer_bytes(pba_ctx* ctx, int64_t* h2d, int64_t* d2h);
 
 #ifdef __cplusplus
 }

@@ -41,6 +41,7 @@ struct LaunchCtx {
     TileStats* tstats;
     float* dthsq;     // F
     double* stats;    // slots * kStats
+    const double* poses0;  // F*12 FP64 poses at p_0
     cudaStream_t stream;
 };
 
@@ -66,6 +67,8 @@ struct SolveArgs {
     float* fc_prev;         // F*12
     float* dthsq;           // F
     int* err;
+    const int* active;      // [0] anchor frame, [f] frame has residuals
+    const double* tanchor;  // F*12 poses whose t define the gauge direction
 };
 
 cudaError_t launch_schur_offdiag(const DevProblem& pb, const float* Hfd, const float* Hnn,

@@ -10,8 +10,10 @@ namespace pba {
 // ---------------------------------------------------------------------------
 // S_off[f][g] = sum_n H_fd(n,f) H_fd(n,g)^T / H_dd(n) for one frame pair per
 // CTA (f <= g, both target frames). Warps walk the tiles; a lane adds its
-// point when it is visible in both frames. Neumaier-compensated FP32 sums per
-// lane, then a fixed-order reduction to FP64: deterministic.
+// point when it is visible in both frames. The products and sums are FP64:
+// S = blockdiag(H_ff) - S_off cancels along the near-null directions of the
+// reduced system, where FP32 products would lose cond(S) * 2^-24. Fixed-order
+// reduction: deterministic.
 // ---------------------------------------------------------------------------
 constexpr int kSchurWarps = 4;
 
@@ -23,9 +25,9 @@ schur_offdiag_kernel(DevProblem pb, const float* Hfd, const float* Hnn, const in
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int2 fg = pairs[blockIdx.x];
     const int f = fg.x, g = fg.y;
-    float s[36], c[36];
+    double s[36];
 #pragma unroll
-    for (int k = 0; k < 36; ++k) s[k] = c[k] = 0.0f;
+    for (int k = 0; k < 36; ++k) s[k] = 0.0;
     for (int t = warp; t < pb.T; t += kSchurWarps) {
         const int ea = pb.ent_of[(size_t)t * pb.F + f];
         const int eb = pb.ent_of[(size_t)t * pb.F + g];
@@ -35,30 +37,32 @@ schur_offdiag_kernel(DevProblem pb, const float* Hfd, const float* Hnn, const in
         const int n = t * kTile + lane;
         const float h = Hnn[n];
         if (!(h > 0.0f)) continue;
-        const float ih = 1.0f / h;
+        const double ih = 1.0 / (double)h;
         const int na = __popc(A.mask), ra = __popc(A.mask & ((1u << lane) - 1u));
         const int nb = __popc(B.mask), rb = __popc(B.mask & ((1u << lane) - 1u));
         const float* pa = Hfd + (size_t)A.pair_off * 6 + ra;
         const float* pbp = Hfd + (size_t)B.pair_off * 6 + rb;
-        float ha[6], hb[6];
+        double ha[6], hb[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            ha[k] = pa[k * na] * ih;
-            hb[k] = pbp[k * nb];
+            ha[k] = (double)pa[k * na];
+            hb[k] = (double)pbp[k * nb];
         }
+        // (h_a h_b) / H_dd: the product commutes, so diagonal blocks come out
+        // exactly symmetric
 #pragma unroll
         for (int a = 0; a < 6; ++a)
 #pragma unroll
-            for (int b = 0; b < 6; ++b) neumaier_add(s[6 * a + b], c[6 * a + b], ha[a] * hb[b]);
+            for (int b = 0; b < 6; ++b) s[6 * a + b] = fma(ha[a] * hb[b], ih, s[6 * a + b]);
     }
-    // fixed-order reduction: lanes (butterfly, FP64), then warps
+    // fixed-order reduction: lanes (butterfly), then warps
 #pragma unroll
     for (int k = 0; k < 36; ++k) {
-        double v = warp_sum1d((double)s[k] + (double)c[k]);
+        double v = warp_sum1d(s[k]);
         if (lane == 0) red[warp][k] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 36) {
+    if (threadIdx.x < 36 && (f != g || threadIdx.x / 6 <= threadIdx.x % 6)) {
         const int k = threadIdx.x, a = k / 6, b = k % 6;
         double v = 0.0;
         for (int w = 0; w < kSchurWarps; ++w) v += red[w][k];
@@ -84,6 +88,7 @@ cudaError_t launch_schur_offdiag(const DevProblem& pb, const float* Hfd, const f
 // the prior gauge_w * mu * that that^T goes on the translation block of the
 // first active frame (that = unit translation of that frame in anchor_t).
 // H_ff comes as 21 upper-triangle values per frame at Hff[f*stride].
+// active[f] (f >= 1) receives the frame flags, active[0] the anchor frame.
 // ---------------------------------------------------------------------------
 __global__ void assemble_S_kernel(int F, const double* Hff, int stride, const double* Soff,
                                   const double* anchor_t, double gauge_w, double* S, int* active)
@@ -134,6 +139,7 @@ __global__ void assemble_S_kernel(int F, const double* Hff, int stride, const do
         }
         s_mu = cnt ? gauge_w * mu / cnt : 0.0;
         s_anchor = anchor;
+        active[0] = anchor;  // first active frame, -1 if none
     }
     __syncthreads();
     if (s_anchor > 0 && threadIdx.x < 9) {
@@ -142,7 +148,7 @@ __global__ void assemble_S_kernel(int F, const double* Hff, int stride, const do
         if (nt > 0.0) {
             const int a = threadIdx.x / 3, b = threadIdx.x % 3;
             const int base = 6 * (s_anchor - 1);
-            S[(size_t)(base + a) * n6 + base + b] += s_mu * (ta[a] / nt) * (ta[b] / nt);
+            S[(size_t)(base + a) * n6 + base + b] += s_mu * ((ta[a] / nt) * (ta[b] / nt));
         }
     }
 }
@@ -292,16 +298,32 @@ __device__ void fc_pose_update(const SolveArgs& a, int f, const double* dth)
     write_frame(a, f, Rn, tn, dth);
 }
 
+// Scale gauge (the one free direction of the system, Delta t_f = -t_f,
+// Delta d_n = d_n): the prior mu that that^T selects the solution with
+// that . Delta t_anchor = 0, but in floating point the prior pins that
+// component only to cond(S) * eps. Adding alpha times the null vector leaves
+// H Delta p unchanged, so the constraint is imposed exactly:
+//   alpha = (t_a . Delta t_a) / |t_a|^2,  Delta t_f -= alpha t_f (active f),
+// and the depth back-substitution carries the matching alpha d_n.
+__device__ __forceinline__ double gauge_alpha(const double* ta, const double* dta)
+{
+    const double n2 = ta[0] * ta[0] + ta[1] * ta[1] + ta[2] * ta[2];
+    return n2 > 0.0 ? (ta[0] * dta[0] + ta[1] * dta[1] + ta[2] * dta[2]) / n2 : 0.0;
+}
+
 // IC step 3 + 4: Dtheta = -S^-1 y (one CTA per target frame, one warp per
-// row, FP64 dot products), then the frame's pose update.
+// row, FP64 dot products; warps 6-8 also form the anchor frame's Delta t for
+// the gauge constraint), then the frame's pose update.
 __global__ void ic_solve_update_kernel(SolveArgs a, const double* Sinv, const double* y,
                                        int y_stride, int y_off)
 {
-    __shared__ double dth[6];
+    __shared__ double dth[9];
     const int f = blockIdx.x + 1, lane = threadIdx.x & 31, row = threadIdx.x >> 5;
     const int n6 = a.n6;
-    if (row < 6) {
-        const double* Sr = Sinv + (size_t)(6 * (f - 1) + row) * n6;
+    const int anchor = a.active[0];
+    const int rr = row < 6 ? 6 * (f - 1) + row : (anchor > 0 ? 6 * (anchor - 1) + row - 6 : -1);
+    if (rr >= 0) {
+        const double* Sr = Sinv + (size_t)rr * n6;
         double s = 0.0;
         for (int c = lane; c < n6; c += 32) s = fma(Sr[c], y[(size_t)(c / 6 + 1) * y_stride + y_off + c % 6], s);
         s = warp_sum1d(s);
@@ -315,6 +337,12 @@ __global__ void ic_solve_update_kernel(SolveArgs a, const double* Sinv, const do
             d[k] = dth[k];
             ok = ok && isfinite(d[k]);
         }
+        if (anchor > 0 && a.active[f]) {
+            const double* ta = a.tanchor + 12 * anchor + 9;
+            const double alpha = gauge_alpha(ta, dth + 6);
+            const double* tf = a.tanchor + 12 * f + 9;
+            for (int k = 0; k < 3; ++k) d[k] -= alpha * tf[k];
+        }
         if (!ok) {
             atomicOr(a.err, kErrNonFinite);
             for (int k = 0; k < 6; ++k) d[k] = 0.0;
@@ -326,12 +354,12 @@ __global__ void ic_solve_update_kernel(SolveArgs a, const double* Sinv, const do
 cudaError_t launch_ic_solve_update(const SolveArgs& a, const double* Sinv, const double* y,
                                    int y_stride, int y_off, cudaStream_t st)
 {
-    ic_solve_update_kernel<<<a.F - 1, 6 * 32, 0, st>>>(a, Sinv, y, y_stride, y_off);
+    ic_solve_update_kernel<<<a.F - 1, 9 * 32, 0, st>>>(a, Sinv, y, y_stride, y_off);
     return cudaGetLastError();
 }
 
-// FC: solve L L^T Dtheta = -y (one CTA, column-oriented substitutions), then
-// every frame's boxplus update.
+// FC: solve L L^T Dtheta = -y (one CTA, column-oriented substitutions), the
+// exact gauge constraint, then every frame's boxplus update.
 __global__ void __launch_bounds__(1024) fc_solve_update_kernel(SolveArgs a, const double* L,
                                                                const double* y, int y_stride,
                                                                int y_off)
@@ -354,6 +382,12 @@ __global__ void __launch_bounds__(1024) fc_solve_update_kernel(SolveArgs a, cons
         for (int i = tid; i < k; i += blockDim.x) x[i] = fma(-L[(size_t)k * n + i], xk, x[i]);
         __syncthreads();
     }
+    __shared__ double s_alpha;
+    if (tid == 0) {
+        const int anchor = a.active[0];
+        s_alpha = anchor > 0 ? gauge_alpha(a.tanchor + 12 * anchor + 9, x + 6 * (anchor - 1)) : 0.0;
+    }
+    __syncthreads();
     for (int f = 1 + tid; f < a.F; f += blockDim.x) {
         double d[6];
         bool ok = true;
@@ -361,6 +395,8 @@ __global__ void __launch_bounds__(1024) fc_solve_update_kernel(SolveArgs a, cons
             d[k] = x[6 * (f - 1) + k];
             ok = ok && isfinite(d[k]);
         }
+        if (a.active[f])
+            for (int k = 0; k < 3; ++k) d[k] -= s_alpha * a.tanchor[12 * f + 9 + k];
         if (!ok) {
             atomicOr(a.err, kErrNonFinite);
             for (int k = 0; k < 6; ++k) d[k] = 0.0;

@@ -20,7 +20,8 @@ __device__ __forceinline__ int lane_rank(unsigned mask, int lane)
 // Depth back-substitution of the previous step (Sec. 3.5 step 3 for the
 // point block): Dd_n = -(g_n + sum_f H_fd^T Dtheta_f) / H_dd, then the IC
 // rule d <- d (d0 - Dd)/d0 (Sec. 3.6) or the FC rule d <- d + Dd. Returns the
-// updated FP64 depth of the lane's point; all warps of the CTA call it.
+// updated depth of the lane's point (rounded to FP32, as the pass uses it);
+// all warps of the CTA call it.
 __device__ double depth_backsub(const DevProblem& pb, const DepthState& ds, const float* s_dth,
                                 float* s_red, int t, int e0, int e1, bool ic_rule, float& ddsq)
 {
@@ -60,7 +61,8 @@ __device__ double depth_backsub(const DevProblem& pb, const DepthState& ds, cons
         s_red[kPassWarps * 32 + lane] = (float)d;
     }
     __syncthreads();
-    return d;
+    // every warp continues with the updated depth (FP32 is what the pass uses)
+    return (double)s_red[kPassWarps * 32 + lane];
 }
 
 // Block-wide statistics of a tile: sums of energy, r^2, count, dd^2 and the
@@ -145,9 +147,10 @@ __device__ void load_frame_smem(const PassSmem& sm, const FrameState& fs, int F,
 }
 
 // ---------------------------------------------------------------------------
-// IC precompute (Sec. 3.4-3.5) at the current parameters p_0.
-// Per residual: template gradient (central differences at the integer
-// template pixel), the proxy-warp Jacobian row in pixel units
+// IC precompute (Sec. 3.4-3.5) at the current parameters p_0, evaluated in
+// FP64 once and stored in FP32. Per residual: template gradient (central
+// differences at the integer template pixel), the proxy-warp Jacobian row in
+// pixel units
 //   c = (1/zbar0) (g_u f_x, g_v f_y, -(g_u f_x x + g_v f_y y)),
 //   m = zbar0 R0 c - e_z (t0 . R0 c)            (m = M^T c),
 //   J = [d0 m, (R0 x~) x m, m . t0],
@@ -156,18 +159,20 @@ __device__ void load_frame_smem(const PassSmem& sm, const FrameState& fs, int F,
 // ---------------------------------------------------------------------------
 template <int PMAX>
 __global__ void __launch_bounds__(kTile * kPassWarps)
-ic_precompute_kernel(DevProblem pb, FrameState fs, DepthState ds, IcStore ic, float* ent_part,
-                     TileStats* tstats)
+ic_precompute_kernel(DevProblem pb, const double* poses0, DepthState ds, IcStore ic,
+                     float* ent_part, TileStats* tstats)
 {
     extern __shared__ float smraw[];
-    PassSmem sm(smraw, pb.F);
-    load_frame_smem(sm, fs, pb.F, false, false);
+    double* s_pose = reinterpret_cast<double*>(smraw);   // F * 12 FP64 poses at p_0
+    float* s_red = smraw + 2 * 12 * pb.F;
+    for (int i = threadIdx.x; i < 12 * pb.F; i += blockDim.x) s_pose[i] = poses0[i];
+    __syncthreads();
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = t * kTile + lane;
     const int e0 = pb.tile_entry[t], e1 = pb.tile_entry[t + 1];
     const int P = pb.P, NC = (7 * P + 3) / 4;
-    const float d0 = (float)ds.d64[n];
-    const float2 xc = pb.xn[n];
+    const double d0 = ds.d64[n];
+    const double fx = pb.fx, fy = pb.fy, cx = pb.cx, cy = pb.cy;
     const int ux = pb.uvs[2 * n], uy = pb.uvs[2 * n + 1];
     float I0[PMAX], gu[PMAX], gv[PMAX];
 #pragma unroll
@@ -184,32 +189,30 @@ ic_precompute_kernel(DevProblem pb, FrameState fs, DepthState ds, IcStore ic, fl
     float hnn = 0.0f, energy = 0.0f, sumsq = 0.0f, cnt = 0.0f;
     for (int e = e0 + warp; e < e1; e += kPassWarps) {
         const Entry en = pb.entries[e];
-        const float* c = sm.fc + en.f * kFrameConst;
+        const double* R = s_pose + 12 * en.f;
+        const double* t0 = R + 9;
         float hff[21];
 #pragma unroll
         for (int k = 0; k < 21; ++k) hff[k] = 0.0f;
         if ((en.mask >> lane) & 1u) {
             const int nvis = __popc(en.mask), rank = lane_rank(en.mask, lane);
             float Jr[7 * PMAX + 4];
-            float hfd[6] = {0, 0, 0, 0, 0, 0};
-            const float ax = fmaf(c[0], xc.x, fmaf(c[1], xc.y, c[2]));
-            const float ay = fmaf(c[3], xc.x, fmaf(c[4], xc.y, c[5]));
-            const float az = fmaf(c[6], xc.x, fmaf(c[7], xc.y, c[8]));
-            const float t0x = c[9], t0y = c[10], t0z = c[11];
+            double hfd[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
             for (int j = 0; j < PMAX; ++j) {
                 if (j >= P) break;
                 float* J = Jr + 7 * j;
-                const float a0 = ax + c[12 + 3 * j], a1 = ay + c[13 + 3 * j], a2 = az + c[14 + 3 * j];
-                const float qx = fmaf(d0, t0x, a0), qy = fmaf(d0, t0y, a1), qz = fmaf(d0, t0z, a2);
-                float val, wa, wb;
+                const double x = (ux + pb.pat[2 * j] - cx) / fx;
+                const double y = (uy + pb.pat[2 * j + 1] - cy) / fy;
+                const double a0 = R[0] * x + R[1] * y + R[2];
+                const double a1 = R[3] * x + R[4] * y + R[5];
+                const double a2 = R[6] * x + R[7] * y + R[8];
+                const double qx = a0 + d0 * t0[0], qy = a1 + d0 * t0[1], qz = a2 + d0 * t0[2];
+                bool valid = qz > 0.0;
+                float val = 0.f, wa, wb;
                 int bx, by;
-                bool valid = qz > 0.0f;
-                float u = 0.f, v = 0.f;
                 if (valid) {
-                    const float iz = 1.0f / qz;
-                    u = fmaf(pb.fx * qx, iz, pb.cx);
-                    v = fmaf(pb.fy * qy, iz, pb.cy);
+                    const float u = (float)(fx * qx / qz + cx), v = (float)(fy * qy / qz + cy);
                     valid = bilinear(pb, en.f, u, v, val, wa, wb, bx, by);
                 }
                 if (!valid) {
@@ -218,38 +221,42 @@ ic_precompute_kernel(DevProblem pb, FrameState fs, DepthState ds, IcStore ic, fl
                     continue;
                 }
                 const float r0 = I0[j] - val;
-                const float w0 = huber_w(r0, pb.huber_k);
+                const double w0 = (double)huber_w(r0, pb.huber_k);
                 energy += huber_rho(r0, pb.huber_k);
                 sumsq += r0 * r0;
                 cnt += 1.0f;
-                // template pixel in normalised coordinates
-                const float x = xc.x + pb.pat[2 * j] / pb.fx, y = xc.y + pb.pat[2 * j + 1] / pb.fy;
-                const float zb = qz / d0;
-                const float izb = 1.0f / zb;
-                const float gx = gu[j] * pb.fx, gy = gv[j] * pb.fy;
-                const float c0 = gx * izb, c1 = gy * izb, c2 = -(gx * x + gy * y) * izb;
-                // c' = R0 c
-                const float cp0 = fmaf(c[0], c0, fmaf(c[1], c1, c[2] * c2));
-                const float cp1 = fmaf(c[3], c0, fmaf(c[4], c1, c[5] * c2));
-                const float cp2 = fmaf(c[6], c0, fmaf(c[7], c1, c[8] * c2));
-                const float tc = fmaf(t0x, cp0, fmaf(t0y, cp1, t0z * cp2));
-                const float m0 = zb * cp0, m1 = zb * cp1, m2 = fmaf(zb, cp2, -tc);
-                J[0] = d0 * m0;
-                J[1] = d0 * m1;
-                J[2] = d0 * m2;
-                J[3] = a1 * m2 - a2 * m1;
-                J[4] = a2 * m0 - a0 * m2;
-                J[5] = a0 * m1 - a1 * m0;
-                J[6] = fmaf(m0, t0x, fmaf(m1, t0y, m2 * t0z));
+                const double zb = qz / d0;
+                const double gx = (double)gu[j] * fx, gy = (double)gv[j] * fy;
+                const double c0 = gx / zb, c1 = gy / zb, c2 = -(gx * x + gy * y) / zb;
+                const double cp0 = R[0] * c0 + R[1] * c1 + R[2] * c2;
+                const double cp1 = R[3] * c0 + R[4] * c1 + R[5] * c2;
+                const double cp2 = R[6] * c0 + R[7] * c1 + R[8] * c2;
+                const double tc = t0[0] * cp0 + t0[1] * cp1 + t0[2] * cp2;
+                const double m0 = zb * cp0, m1 = zb * cp1, m2 = zb * cp2 - tc;
+                double Jd[7];
+                Jd[0] = d0 * m0;
+                Jd[1] = d0 * m1;
+                Jd[2] = d0 * m2;
+                Jd[3] = a1 * m2 - a2 * m1;
+                Jd[4] = a2 * m0 - a0 * m2;
+                Jd[5] = a0 * m1 - a1 * m0;
+                Jd[6] = m0 * t0[0] + m1 * t0[1] + m2 * t0[2];
+                // H from the stored (FP32-rounded) row, so H = J^T W0 J holds
+                // exactly for the J the iterations use
+#pragma unroll
+                for (int k = 0; k < 7; ++k) J[k] = (float)Jd[k];
                 int q = 0;
 #pragma unroll
                 for (int a = 0; a < 6; ++a) {
-                    const float wa_ = w0 * J[a];
+                    const double wja = w0 * (double)J[a];
 #pragma unroll
-                    for (int b = a; b < 6; ++b) hff[q++] += wa_ * J[b];
-                    hfd[a] = fmaf(wa_, J[6], hfd[a]);
+                    for (int b = a; b < 6; ++b) {
+                        hff[q] += (float)(wja * (double)J[b]);
+                        ++q;
+                    }
+                    hfd[a] += wja * (double)J[6];
                 }
-                hnn = fmaf(w0 * J[6], J[6], hnn);
+                hnn += (float)(w0 * (double)J[6] * (double)J[6]);
             }
 #pragma unroll
             for (int k = 0; k < 7 * PMAX + 4; ++k)
@@ -262,7 +269,7 @@ ic_precompute_kernel(DevProblem pb, FrameState fs, DepthState ds, IcStore ic, fl
                         make_float4(Jr[4 * ch], Jr[4 * ch + 1], Jr[4 * ch + 2], Jr[4 * ch + 3]);
             float* hd = ic.Hfd + (size_t)en.pair_off * 6 + rank;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) hd[k * nvis] = hfd[k];
+            for (int k = 0; k < 6; ++k) hd[k * nvis] = (float)hfd[k];
         }
         warp_sum<21>(hff);
         if (lane == 0) {
@@ -271,14 +278,14 @@ ic_precompute_kernel(DevProblem pb, FrameState fs, DepthState ds, IcStore ic, fl
             for (int k = 0; k < 21; ++k) out[k] = hff[k];
         }
     }
-    sm.red[warp * 32 + lane] = hnn;
+    s_red[warp * 32 + lane] = hnn;
     __syncthreads();
     if (warp == 0) {
         float tot = 0.0f;
-        for (int w = 0; w < kPassWarps; ++w) tot += sm.red[w * 32 + lane];
+        for (int w = 0; w < kPassWarps; ++w) tot += s_red[w * 32 + lane];
         ic.Hnn[n] = pb.valid_pt[n] ? tot : 0.0f;
     }
-    tile_stats_write(tstats, t, energy, sumsq, cnt, 0.0f, 0.0f, sm.red);
+    tile_stats_write(tstats, t, energy, sumsq, cnt, 0.0f, 0.0f, s_red);
 }
 
 // ---------------------------------------------------------------------------
@@ -634,7 +641,7 @@ static cudaError_t launch_ic_precompute_p(const LaunchCtx& L)
 {
     size_t sm = pass_smem_bytes(L.pb.F);
     ic_precompute_kernel<PMAX><<<L.pb.T, kTile * kPassWarps, sm, L.stream>>>(
-        L.pb, L.fs, L.ds_ic, L.ic, L.ent_part, L.tstats);
+        L.pb, L.poses0, L.ds_ic, L.ic, L.ent_part, L.tstats);
     return cudaGetLastError();
 }
 

@@ -91,7 +91,7 @@ struct pba_ctx {
         double *poses64, *poses0_64, *dtheta64;
         double *red_ic, *red_y;
         double *Soff, *S_ic, *L_ic, *Sinv, *S_fc, *L_fc;
-        int* active;
+        int *active_ic, *active_fc;
         int2* frame_pairs;
         int* err;
         double* stats;
@@ -100,7 +100,8 @@ struct pba_ctx {
     int last_fc = 0;  // which system the last update came from
 
     // instrumentation
-    bool timing = false;
+    int timing = 0;  // slot mask
+    int64_t h2d = 0, d2h = 0;
     int64_t launches = 0;
     double tms[TS_N] = {0, 0, 0, 0, 0, 0};
     int64_t tcount[TS_N] = {0, 0, 0, 0, 0, 0};
@@ -150,7 +151,7 @@ cudaEvent_t take_event(pba_ctx* ctx)
 
 int tbegin(pba_ctx* ctx, int slot)
 {
-    if (!ctx->timing) return -1;
+    if (!((ctx->timing >> slot) & 1)) return -1;
     cudaEvent_t a = take_event(ctx), b = take_event(ctx);
     cudaEventRecord(a, ctx->stream);
     ctx->tev.push_back({slot, {a, b}});
@@ -178,6 +179,19 @@ void tcollect(pba_ctx* ctx)
 }
 
 size_t elem_size(pba_dtype t) { return t == PBA_F32 ? 4 : 2; }
+
+cudaError_t h2d(pba_ctx* ctx, void* dst, const void* src, size_t bytes)
+{
+    ctx->h2d += (int64_t)bytes;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
+}
+
+cudaError_t d2h(pba_ctx* ctx, void* dst, const void* src, size_t bytes)
+{
+    ctx->d2h += (int64_t)bytes;
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    return e == cudaSuccess ? cudaStreamSynchronize(ctx->stream) : e;
+}
 
 // Lays out (and optionally assigns) the workspace; returns its size.
 size_t layout(pba_ctx* c, char* base)
@@ -234,7 +248,8 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.Sinv, n6 * n6 * 8);
     take(c->d.S_fc, n6 * n6 * 8);
     take(c->d.L_fc, n6 * n6 * 8);
-    take(c->d.active, F * 4);
+    take(c->d.active_ic, F * 4);
+    take(c->d.active_fc, F * 4);
     take(c->d.frame_pairs, c->frame_pairs.size() * sizeof(int2));
     take(c->d.err, 64);
     take(c->d.stats, (size_t)(c->stats_slots) * kStats * 8);
@@ -298,14 +313,14 @@ pba_status upload_params(pba_ctx* ctx, const double* poses, const double* depth)
                      fcs.data() + (size_t)f * kFrameConst);
         for (int i = 0; i < 12; ++i) prev[12 * f + i] = (float)poses[12 * f + i];
     }
-    CK(cudaMemcpyAsync(ctx->d.poses64, poses, sizeof(double) * 12 * F, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.fc, fcs.data(), sizeof(float) * fcs.size(), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.fc_prev, prev.data(), sizeof(float) * prev.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(h2d(ctx, ctx->d.poses64, poses, sizeof(double) * 12 * F));
+    CK(h2d(ctx, ctx->d.fc, fcs.data(), sizeof(float) * fcs.size()));
+    CK(h2d(ctx, ctx->d.fc_prev, prev.data(), sizeof(float) * prev.size()));
     if (depth) {
         std::vector<double> ds(ctx->Npad, 1.0);
         for (int i = 0; i < ctx->Npad; ++i)
             if (ctx->perm[i] >= 0) ds[i] = depth[ctx->perm[i]];
-        CK(cudaMemcpyAsync(ctx->d.d64, ds.data(), sizeof(double) * ds.size(), cudaMemcpyHostToDevice, ctx->stream));
+        CK(h2d(ctx, ctx->d.d64, ds.data(), sizeof(double) * ds.size()));
     }
     // all host staging above is pageable: the copies have consumed it on return
     CK(cudaStreamSynchronize(ctx->stream));
@@ -315,8 +330,7 @@ pba_status upload_params(pba_ctx* ctx, const double* poses, const double* depth)
 pba_status check_device_error(pba_ctx* ctx)
 {
     int herr = 0;
-    CK(cudaMemcpyAsync(&herr, ctx->d.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(d2h(ctx, &herr, ctx->d.err, sizeof(int)));
     tcollect(ctx);
     if (herr) {
         CK(cudaMemsetAsync(ctx->d.err, 0, sizeof(int), ctx->stream));
@@ -368,6 +382,7 @@ LaunchCtx make_launch(pba_ctx* c)
     L.tstats = c->d.tstats;
     L.dthsq = c->d.dthsq;
     L.stats = c->d.stats;
+    L.poses0 = c->d.poses0_64;
     L.stream = c->stream;
     return L;
 }
@@ -398,7 +413,7 @@ pba_status copy_stats(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     if (s != PBA_OK) return s;
     if (!stats) return PBA_OK;
     std::vector<double> h((size_t)(n_iters + 1) * kStats);
-    CK(cudaMemcpy(h.data(), ctx->d.stats, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+    CK(d2h(ctx, h.data(), ctx->d.stats, sizeof(double) * h.size()));
     for (int k = 0; k <= n_iters; ++k) {
         const double* r = h.data() + (size_t)k * kStats;
         stats[k] = pba_iter_stats{r[0], r[1], r[2], k < n_iters ? r[3] : 0.0,
@@ -587,9 +602,8 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     ctx->ic_ready = false;
     CK(cudaMemsetAsync(ctx->ws, 0, need, ctx->stream));
     if (ctx->mem == PBA_MEM_HOST)
-        CK(cudaMemcpyAsync(ctx->d.img, ctx->images,
-                           (size_t)ctx->F * ctx->H * ctx->pitch * elem_size(ctx->dtype),
-                           cudaMemcpyHostToDevice, ctx->stream));
+        CK(h2d(ctx, ctx->d.img, ctx->images,
+               (size_t)ctx->F * ctx->H * ctx->pitch * elem_size(ctx->dtype)));
     const int Np = ctx->Npad, P = (int)ctx->pattern.size() / 2;
     std::vector<int> uvs(2 * Np);
     std::vector<float2> xn(Np);
@@ -605,19 +619,19 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
         valid[i] = ctx->perm[i] >= 0;
     }
     std::vector<int> pat(ctx->pattern.begin(), ctx->pattern.end());
-    CK(cudaMemcpyAsync(ctx->d.pat, pat.data(), sizeof(int) * pat.size(), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.entries, ctx->entries.data(), sizeof(Entry) * ctx->entries.size(), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.tile_entry, ctx->tile_entry.data(), sizeof(int) * ctx->tile_entry.size(), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.frame_entry, ctx->frame_entry.data(), sizeof(int) * ctx->frame_entry.size(), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.frame_entries, ctx->frame_entries.data(), sizeof(int) * ctx->frame_entries.size(), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.ent_of, ctx->ent_of.data(), sizeof(int) * ctx->ent_of.size(), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.uvs, uvs.data(), sizeof(int) * uvs.size(), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.xn, xn.data(), sizeof(float2) * xn.size(), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.valid_pt, valid.data(), valid.size(), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.frame_pairs, ctx->frame_pairs.data(), sizeof(int2) * ctx->frame_pairs.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(h2d(ctx, ctx->d.pat, pat.data(), sizeof(int) * pat.size()));
+    CK(h2d(ctx, ctx->d.entries, ctx->entries.data(), sizeof(Entry) * ctx->entries.size()));
+    CK(h2d(ctx, ctx->d.tile_entry, ctx->tile_entry.data(), sizeof(int) * ctx->tile_entry.size()));
+    CK(h2d(ctx, ctx->d.frame_entry, ctx->frame_entry.data(), sizeof(int) * ctx->frame_entry.size()));
+    CK(h2d(ctx, ctx->d.frame_entries, ctx->frame_entries.data(), sizeof(int) * ctx->frame_entries.size()));
+    CK(h2d(ctx, ctx->d.ent_of, ctx->ent_of.data(), sizeof(int) * ctx->ent_of.size()));
+    CK(h2d(ctx, ctx->d.uvs, uvs.data(), sizeof(int) * uvs.size()));
+    CK(h2d(ctx, ctx->d.xn, xn.data(), sizeof(float2) * xn.size()));
+    CK(h2d(ctx, ctx->d.valid_pt, valid.data(), valid.size()));
+    CK(h2d(ctx, ctx->d.frame_pairs, ctx->frame_pairs.data(), sizeof(int2) * ctx->frame_pairs.size()));
     pba_status s = upload_params(ctx, ctx->poses_init.data(), ctx->d_init.data());
     if (s != PBA_OK) return s;
-    CK(cudaMemcpyAsync(ctx->d.poses0_64, ctx->poses_init.data(), sizeof(double) * 12 * ctx->F, cudaMemcpyHostToDevice, ctx->stream));
+    CK(h2d(ctx, ctx->d.poses0_64, ctx->poses_init.data(), sizeof(double) * 12 * ctx->F));
     CK(set_pass_smem_limits(ctx->F));
     LaunchCtx L = make_launch(ctx);
     LAUNCH(TS_PRE, launch_setup(L.pb, ctx->d.gx, ctx->d.gy, ctx->d.I0p, ctx->stream));
@@ -641,7 +655,7 @@ pba_status pba_precompute_ic(pba_ctx* ctx)
     LAUNCH(TS_PRE, launch_schur_offdiag(L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, ctx->d.frame_pairs,
                                         (int)ctx->frame_pairs.size(), ctx->d.Soff, ctx->stream));
     LAUNCH(TS_PRE, launch_assemble_S(F, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64,
-                                     ctx->cfg.gauge_anchor_w, ctx->d.S_ic, ctx->d.active, ctx->stream));
+                                     ctx->cfg.gauge_anchor_w, ctx->d.S_ic, ctx->d.active_ic, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d.L_ic, ctx->d.S_ic, sizeof(double) * n6 * n6, cudaMemcpyDeviceToDevice, ctx->stream));
     LAUNCH(TS_PRE, launch_cholesky(ctx->d.L_ic, n6, ctx->d.err, ctx->stream));
     LAUNCH(TS_PRE, launch_chol_inverse(ctx->d.L_ic, ctx->d.Sinv, n6, ctx->stream));
@@ -659,6 +673,8 @@ pba_status pba_iterate(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
         return fail(ctx, PBA_ERR_ARG, "n_iters must be in [0, %d]", ctx->cfg.max_stats_iters);
     LaunchCtx L = make_launch(ctx);
     SolveArgs sa = make_solve(ctx);
+    sa.active = ctx->d.active_ic;
+    sa.tanchor = ctx->d.poses0_64;
     for (int k = 0; k < n_iters; ++k) {
         LAUNCH(TS_PASS, launch_ic_pass(L, true, k > 0, k > 0));
         LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 6, ctx->d.red_y, k, k - 1, true));
@@ -679,13 +695,15 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     const int F = ctx->F, n6 = 6 * (F - 1);
     LaunchCtx L = make_launch(ctx);
     SolveArgs sa = make_solve(ctx);
+    sa.active = ctx->d.active_fc;
+    sa.tanchor = ctx->d.poses64;
     for (int k = 0; k < n_iters; ++k) {
         LAUNCH(TS_PASS, launch_fc_pass(L, true, k > 0, k > 0));
         LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 27, ctx->d.red_y, k, k - 1, true));
         LAUNCH(TS_SCHUR, launch_schur_offdiag(L.pb, ctx->d.Hfd_fc, ctx->d.Hnn_fc, ctx->d.frame_pairs,
                                               (int)ctx->frame_pairs.size(), ctx->d.Soff, ctx->stream));
         LAUNCH(TS_SCHUR, launch_assemble_S(F, ctx->d.red_y, 27, ctx->d.Soff, ctx->d.poses64,
-                                           ctx->cfg.gauge_anchor_w, ctx->d.S_fc, ctx->d.active, ctx->stream));
+                                           ctx->cfg.gauge_anchor_w, ctx->d.S_fc, ctx->d.active_fc, ctx->stream));
         CK(cudaMemcpyAsync(ctx->d.L_fc, ctx->d.S_fc, sizeof(double) * n6 * n6, cudaMemcpyDeviceToDevice, ctx->stream));
         LAUNCH(TS_SOLVE, launch_cholesky(ctx->d.L_fc, n6, ctx->d.err, ctx->stream));
         LAUNCH(TS_SOLVE, launch_fc_solve_update(sa, ctx->d.L_fc, ctx->d.red_y, 27, 21, ctx->stream));
@@ -701,10 +719,10 @@ pba_status pba_get_params(pba_ctx* ctx, int bundle, double* poses, double* inv_d
     if (!ctx || bundle != 0) return PBA_ERR_ARG;
     if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
     CK(cudaStreamSynchronize(ctx->stream));
-    if (poses) CK(cudaMemcpy(poses, ctx->d.poses64, sizeof(double) * 12 * ctx->F, cudaMemcpyDeviceToHost));
+    if (poses) CK(d2h(ctx, poses, ctx->d.poses64, sizeof(double) * 12 * ctx->F));
     if (inv_depth) {
         std::vector<double> ds(ctx->Npad);
-        CK(cudaMemcpy(ds.data(), ctx->d.d64, sizeof(double) * ds.size(), cudaMemcpyDeviceToHost));
+        CK(d2h(ctx, ds.data(), ctx->d.d64, sizeof(double) * ds.size()));
         for (int i = 0; i < ctx->Npad; ++i)
             if (ctx->perm[i] >= 0) inv_depth[ctx->perm[i]] = ds[i];
     }
@@ -728,10 +746,10 @@ pba_status pba_get_last_update(pba_ctx* ctx, int bundle, double* dtheta, double*
     if (!ctx || bundle != 0) return PBA_ERR_ARG;
     if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
     CK(cudaStreamSynchronize(ctx->stream));
-    if (dtheta) CK(cudaMemcpy(dtheta, ctx->d.dtheta64, sizeof(double) * 6 * ctx->F, cudaMemcpyDeviceToHost));
+    if (dtheta) CK(d2h(ctx, dtheta, ctx->d.dtheta64, sizeof(double) * 6 * ctx->F));
     if (dd) {
         std::vector<double> h(ctx->Npad);
-        CK(cudaMemcpy(h.data(), ctx->d.dd_last, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+        CK(d2h(ctx, h.data(), ctx->d.dd_last, sizeof(double) * h.size()));
         for (int i = 0; i < ctx->Npad; ++i)
             if (ctx->perm[i] >= 0) dd[ctx->perm[i]] = h[i];
     }
@@ -749,7 +767,7 @@ pba_status pba_get_system(pba_ctx* ctx, int bundle, int fc, double* Hff, double*
     if (Hff) {
         const int stride = fc ? 27 : 21;
         std::vector<double> r((size_t)F * stride);
-        CK(cudaMemcpy(r.data(), fc ? ctx->d.red_y : ctx->d.red_ic, sizeof(double) * r.size(), cudaMemcpyDeviceToHost));
+        CK(d2h(ctx, r.data(), fc ? ctx->d.red_y : ctx->d.red_ic, sizeof(double) * r.size()));
         std::memset(Hff, 0, sizeof(double) * 36 * F);
         for (int f = 1; f < F; ++f) {
             int q = 0;
@@ -760,7 +778,7 @@ pba_status pba_get_system(pba_ctx* ctx, int bundle, int fc, double* Hff, double*
     }
     if (Hfd) {
         std::vector<float> h((size_t)ctx->V * 6);
-        CK(cudaMemcpy(h.data(), fc ? ctx->d.Hfd_fc : ctx->d.Hfd_ic, sizeof(float) * h.size(), cudaMemcpyDeviceToHost));
+        CK(d2h(ctx, h.data(), fc ? ctx->d.Hfd_fc : ctx->d.Hfd_ic, sizeof(float) * h.size()));
         std::memset(Hfd, 0, sizeof(double) * 6 * (size_t)ctx->N * F);
         for (const Entry& e : ctx->entries) {
             const int nvis = __builtin_popcount(e.mask);
@@ -775,11 +793,11 @@ pba_status pba_get_system(pba_ctx* ctx, int bundle, int fc, double* Hff, double*
     }
     if (Hdd) {
         std::vector<float> h(ctx->Npad);
-        CK(cudaMemcpy(h.data(), fc ? ctx->d.Hnn_fc : ctx->d.Hnn_ic, sizeof(float) * h.size(), cudaMemcpyDeviceToHost));
+        CK(d2h(ctx, h.data(), fc ? ctx->d.Hnn_fc : ctx->d.Hnn_ic, sizeof(float) * h.size()));
         for (int i = 0; i < ctx->Npad; ++i)
             if (ctx->perm[i] >= 0) Hdd[ctx->perm[i]] = h[i];
     }
-    if (S) CK(cudaMemcpy(S, fc ? ctx->d.S_fc : ctx->d.S_ic, sizeof(double) * n6 * n6, cudaMemcpyDeviceToHost));
+    if (S) CK(d2h(ctx, S, fc ? ctx->d.S_fc : ctx->d.S_ic, sizeof(double) * n6 * n6));
     return PBA_OK;
 }
 
@@ -791,15 +809,23 @@ pba_status pba_num_residuals(pba_ctx* ctx, int bundle, int64_t* n)
     return PBA_OK;
 }
 
-pba_status pba_enable_timing(pba_ctx* ctx, int on)
+pba_status pba_enable_timing(pba_ctx* ctx, int mask)
 {
     if (!ctx) return PBA_ERR_ARG;
-    ctx->timing = on != 0;
+    ctx->timing = mask & ((1 << TS_N) - 1);
     for (int i = 0; i < TS_N; ++i) {
         ctx->tms[i] = 0.0;
         ctx->tcount[i] = 0;
     }
     ctx->launches = 0;
+    return PBA_OK;
+}
+
+pba_status pba_transfer_bytes(pba_ctx* ctx, int64_t* h2d_out, int64_t* d2h_out)
+{
+    if (!ctx) return PBA_ERR_ARG;
+    if (h2d_out) *h2d_out = ctx->h2d;
+    if (d2h_out) *d2h_out = ctx->d2h;
     return PBA_OK;
 }
 

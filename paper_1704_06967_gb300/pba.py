@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pba_num_residuals": ([vp, i, ctypes.POINTER(i64)], i),
         "pba_enable_timing": ([vp, i], i),
         "pba_last_timing": ([vp, vp], i),
+        "pba_transfer_bytes": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], i),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -238,8 +239,14 @@ class Bundle:
         self._check(self.lib.pba_num_residuals(self.h, 0, ctypes.byref(n)))
         return int(n.value)
 
-    def enable_timing(self, on=True):
-        self._check(self.lib.pba_enable_timing(self.h, int(bool(on))))
+    def enable_timing(self, mask=-1):
+        """mask: bit s times slot s (TIMING_NAMES order); -1 all, 0 none."""
+        self._check(self.lib.pba_enable_timing(self.h, int(mask)))
+
+    def transfer_bytes(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.pba_transfer_bytes(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
 
     def timing(self):
         out = np.zeros(2 * TIMING_SLOTS + 1)
