@@ -60,7 +60,8 @@ typedef enum {
     PBA_ERR_NOMEM = 4,      /* workspace too small / host allocation failed */
     PBA_ERR_NOT_PD = 5,     /* reduced camera system not positive definite */
     PBA_ERR_NONFINITE = 6,  /* non-finite update or statistic */
-    PBA_ERR_TIMEOUT = 7     /* a bounded device wait gave up */
+    PBA_ERR_TIMEOUT = 7,    /* a bounded device wait gave up */
+    PBA_ERR_TOO_LARGE = 8   /* problem exceeds a fixed capacity (no-allocation entry point) */
 } pba_status;
 
 typedef enum { PBA_F32 = 0, PBA_F16 = 1, PBA_BF16 = 2 } pba_dtype;
@@ -188,6 +189,38 @@ pba_status pba_last_timing(pba_ctx* ctx, double* out);
  * created (uploads of images, points, structure and parameters; downloads of
  * statistics, parameters, updates and systems). Host, nullable each. */
 pba_status pba_transfer_bytes(pba_ctx* ctx, int64_t* h2d, int64_t* d2h);
+
+/* Reduced camera system without any allocation, for callers that cannot
+ * allocate device memory (code running inside a fixed pre-reserved memory
+ * arena, runtimes that forbid cudaMalloc after start-up, frameworks that
+ * hand an operation only its input and output tensors). The paper has no
+ * counterpart: it is a deployment form of the Schur-complement step.
+ *
+ * Builds the anchored reduced camera system from dense Hessian blocks:
+ *   S = blockdiag(Hff) - sum_n Hfd(n,.) Hfd(n,.)^T / Hdd(n)   (points with
+ *   Hdd(n) <= 0 skipped), frames whose Hff has zero trace replaced by an
+ *   identity block, and the scale-gauge prior gauge_anchor_w * mu * t t^T on
+ *   the translation block of the first active frame (t = unit translation of
+ *   that frame in poses, mu = mean diagonal of the active frames) -- the same
+ *   system pba_get_system returns.
+ * All pointers are device pointers, caller owned: Hff F*36 (row-major 6x6
+ * per frame, frame 0 ignored), Hfd N*F*6 (zero where a point is not
+ * observed), Hdd N, poses F*12 ([R|t] rows, only t is read), S output
+ * (6(F-1))^2 row-major. gauge_anchor_w 0 means 1. Work is enqueued on
+ * cuda_stream (NULL = legacy default stream) and not synchronised.
+ * Scratch lives in one static device array sized for n_frames <=
+ * PBA_NOALLOC_MAX_FRAMES (about 1.2 MB, held by every GPU that loads the
+ * library until exit); larger problems return PBA_ERR_TOO_LARGE without
+ * touching the GPU. The function calls no cudaMalloc/cudaFree. Its first
+ * call on a device looks up the array's device address (make that first
+ * call before any stream capture). Every call on a device shares the array:
+ * calls that overlap on the GPU (concurrent streams) race and must be
+ * serialised by the caller. Returns PBA_ERR_ARG for invalid arguments and
+ * PBA_ERR_CUDA when a launch fails. */
+#define PBA_NOALLOC_MAX_FRAMES 65
+pba_status pba_reduced_system_noalloc(int n_frames, int n_points, const double* Hff,
+                                      const double* Hfd, const double* Hdd, const double* poses,
+                                      double gauge_anchor_w, double* S, void* cuda_stream);
 
 #ifdef __cplusplus
 }
