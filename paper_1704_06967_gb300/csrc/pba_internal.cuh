@@ -57,8 +57,8 @@ struct DevProblem {
     const int* pat;             // P*2 offsets (device copy)
     const Entry* entries;       // E, tile-major
     const int* tile_entry;      // T+1 offsets into entries
-    const int* frame_entry;     // F+1 offsets into frame_entries
-    const int* frame_entries;   // E entry ids grouped by frame, tile order
+    const int* frame_entry;     // F+1 offsets of each frame's partial-sum rows
+    const int* entry_slot;      // E partial-sum row of each entry (frame-major order)
     const int* ent_of;          // T*F entry id of (tile, frame) or -1
     const int* uvs;             // Npad*2 sorted pixels (pad: copy of a real point)
     const float2* xn;           // Npad normalised centre coordinates
@@ -67,39 +67,45 @@ struct DevProblem {
 };
 
 // ---------------------------------------------------------------------------
-// image access
+// image access (offsets are 32-bit: the host checks F * H * pitch < 2^31)
 // ---------------------------------------------------------------------------
+template <int DT>
+__device__ __forceinline__ float load_px_t(const void* img, unsigned idx)
+{
+    if (DT == PBA_F32) return __ldg(reinterpret_cast<const float*>(img) + idx);
+    const unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(img) + idx);
+    if (DT == PBA_F16) return __half2float(__ushort_as_half(b));
+    return __uint_as_float(((unsigned)b) << 16);
+}
+
 __device__ __forceinline__ float load_px(const void* img, int dtype, size_t idx)
 {
-    if (dtype == PBA_F32) return __ldg(reinterpret_cast<const float*>(img) + idx);
-    if (dtype == PBA_F16) {
-        unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(img) + idx);
-        return __half2float(__ushort_as_half(b));
-    }
-    unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(img) + idx);
-    return __uint_as_float(((unsigned)b) << 16);
+    if (dtype == PBA_F32) return load_px_t<PBA_F32>(img, (unsigned)idx);
+    if (dtype == PBA_F16) return load_px_t<PBA_F16>(img, (unsigned)idx);
+    return load_px_t<PBA_BF16>(img, (unsigned)idx);
 }
 
 // Bilinear sample at pixel coordinates (pixel centres on integers); valid
 // iff the 2x2 footprint lies in [1, W-2] x [1, H-2] (gradients defined).
-__device__ __forceinline__ bool bilinear(const DevProblem& pb, int f, float u, float v,
-                                         float& val, float& a, float& b, int& x, int& y)
+template <int DT>
+__device__ __forceinline__ bool bilinear_t(const DevProblem& pb, int f, float u, float v,
+                                           float& val, float& a, float& b, int& x, int& y)
 {
-    float fu = floorf(u), fv = floorf(v);
-    if (!(fu >= 1.0f && fu + 1.0f <= (float)(pb.W - 2) && fv >= 1.0f &&
-          fv + 1.0f <= (float)(pb.H - 2)))
+    const float fu = floorf(u), fv = floorf(v);
+    // float range test first (also rejects NaN and values beyond int range)
+    if (!(fu >= 1.0f && fu <= (float)(pb.W - 3) && fv >= 1.0f && fv <= (float)(pb.H - 3)))
         return false;
     x = (int)fu;
     y = (int)fv;
     a = u - fu;
     b = v - fv;
-    const size_t base = ((size_t)f * pb.H + y) * pb.pitch + x;
-    float i00 = load_px(pb.img, pb.dtype, base);
-    float i10 = load_px(pb.img, pb.dtype, base + 1);
-    float i01 = load_px(pb.img, pb.dtype, base + pb.pitch);
-    float i11 = load_px(pb.img, pb.dtype, base + pb.pitch + 1);
-    float top = fmaf(a, i10 - i00, i00);
-    float bot = fmaf(a, i11 - i01, i01);
+    const unsigned base = ((unsigned)f * (unsigned)pb.H + (unsigned)y) * (unsigned)pb.pitch + (unsigned)x;
+    const float i00 = load_px_t<DT>(pb.img, base);
+    const float i10 = load_px_t<DT>(pb.img, base + 1);
+    const float i01 = load_px_t<DT>(pb.img, base + pb.pitch);
+    const float i11 = load_px_t<DT>(pb.img, base + pb.pitch + 1);
+    const float top = fmaf(a, i10 - i00, i00);
+    const float bot = fmaf(a, i11 - i01, i01);
     val = fmaf(b, bot - top, top);
     return true;
 }

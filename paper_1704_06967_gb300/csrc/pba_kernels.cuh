@@ -8,9 +8,10 @@ namespace pba {
 
 // Per-frame state used by the pass kernels.
 struct FrameState {
-    float* fc;        // F * kFrameConst FP32 constants of the current poses
-    float* fc_prev;   // F * 12 FP32 R|t of the previous poses
-    float* dtheta32;  // F * 6 last update (FP32)
+    float* fc;               // F * kFrameConst FP32 constants of the current poses
+    float* fc_prev;          // F * 12 FP32 R|t of the previous poses
+    float* dtheta32;         // F * 6 last update (FP32)
+    const double* dtheta64;  // F * 6 last update (FP64)
 };
 
 // Per-point state of one method (IC or FC) for the depth back-substitution.
@@ -58,7 +59,7 @@ struct SolveArgs {
     int F, n6;
     const int* pat;
     int P;
-    double fx, fy;
+    double fx, fy, inv_fx, inv_fy;
     double* poses64;        // F*12 current
     const double* poses0;   // F*12 p_0
     double* dtheta64;       // F*6
@@ -71,18 +72,37 @@ struct SolveArgs {
     const double* tanchor;  // F*12 poses whose t define the gauge direction
 };
 
-cudaError_t launch_schur_offdiag(const DevProblem& pb, const float* Hfd, const float* Hnn,
-                                 const int2* frame_pairs, int n_pairs, double* Soff,
-                                 cudaStream_t st);
+// Schur complement (pba_schur.cu)
+// Co-visibility lists of the sparse Schur complement (device pointers):
+// pair_fg[2p..2p+1] = frame pair (f <= g); the pair's chunks are
+// [pair_chunk[p], pair_chunk[p+1]); chunk c covers items [chunk_start[c],
+// chunk_start[c+1]) of pair chunk_pair[c]; an item is (entry of f, entry of
+// g) of one tile that sees both frames.
+struct SchurLists {
+    const int* pair_fg;
+    const int* pair_chunk;
+    const int* chunk_pair;
+    const int* chunk_start;
+    const int2* items;
+    int n_pairs, n_chunks;
+};
+constexpr int kSchurChunk = 16;
+cudaError_t launch_schur_sparse(const DevProblem& pb, const float* Hfd, const float* Hnn,
+                                const SchurLists& sl, float2* part, double* Soff,
+                                cudaStream_t st, int* launches);
 cudaError_t launch_assemble_S(int F, const double* Hff, int hff_stride, const double* Soff,
                               const double* anchor_t, double gauge_w, double* S, int* active,
                               cudaStream_t st);
-cudaError_t launch_cholesky(double* A, int n, int* err, cudaStream_t st);
-cudaError_t launch_chol_inverse(const double* L, double* Sinv, int n, cudaStream_t st);
+// FP64 Cholesky (pba_chol.cu): A (consumed) -> L (lower, with L^T in the
+// upper triangle) and inv_diag = 1/L_ii
+cudaError_t launch_cholesky(double* A, double* L, double* inv_diag, int n, int* err,
+                            cudaStream_t st, int* launches);
+cudaError_t launch_chol_inverse(const double* L, const double* inv_diag, double* Sinv, int n,
+                                cudaStream_t st);
 cudaError_t launch_ic_solve_update(const SolveArgs& a, const double* Sinv, const double* y,
                                    int y_stride, int y_off, cudaStream_t st);
-cudaError_t launch_fc_solve_update(const SolveArgs& a, const double* L, const double* y,
-                                   int y_stride, int y_off, cudaStream_t st);
+cudaError_t launch_fc_solve_update(const SolveArgs& a, const double* L, const double* inv_diag,
+                                   const double* y, int y_stride, int y_off, cudaStream_t st);
 
 // setup kernels (pba_runtime.cu)
 cudaError_t launch_setup(const DevProblem& pb, float* gx, float* gy, float* I0p, cudaStream_t st);

@@ -22,32 +22,36 @@ __device__ __forceinline__ int lane_rank(unsigned mask, int lane)
 // rule d <- d (d0 - Dd)/d0 (Sec. 3.6) or the FC rule d <- d + Dd. Returns the
 // updated depth of the lane's point (rounded to FP32, as the pass uses it);
 // all warps of the CTA call it.
-__device__ double depth_backsub(const DevProblem& pb, const DepthState& ds, const float* s_dth,
-                                float* s_red, int t, int e0, int e1, bool ic_rule, float& ddsq)
+__device__ double depth_backsub(const DevProblem& pb, const DepthState& ds, const Entry* s_ents,
+                                const double* s_dth, float* s_red, int t, int e0, int e1,
+                                bool ic_rule, float& ddsq)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = t * kTile + lane;
-    float s = 0.0f;
-    for (int e = e0 + warp; e < e1; e += kPassWarps) {
-        const Entry en = pb.entries[e];
+    // g_n + sum_f H_fd^T Dtheta_f nearly cancels for well-determined points:
+    // the dot products use the FP64 update and FP64 sums
+    double s = 0.0;
+    for (int le = warp; le < e1 - e0; le += kPassWarps) {
+        const Entry en = s_ents[le];
         if ((en.mask >> lane) & 1u) {
             const int nvis = __popc(en.mask), rank = lane_rank(en.mask, lane);
             const float* h = ds.Hfd + (size_t)en.pair_off * 6 + rank;
-            const float* dt = s_dth + 6 * en.f;
+            const double* dt = s_dth + 6 * le;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) s = fmaf(h[k * nvis], dt[k], s);
+            for (int k = 0; k < 6; ++k) s = fma((double)h[k * nvis], dt[k], s);
         }
     }
-    s_red[warp * 32 + lane] = s;
+    double* s_red64 = reinterpret_cast<double*>(s_red);
+    s_red64[warp * 32 + lane] = s;
     __syncthreads();
     double d = ds.d64[n];
     if (warp == 0) {
-        float tot = 0.0f;
-        for (int w = 0; w < kPassWarps; ++w) tot += s_red[w * 32 + lane];
+        double tot = 0.0;
+        for (int w = 0; w < kPassWarps; ++w) tot += s_red64[w * 32 + lane];
         const float hnn = ds.Hnn[n];
         double dd = 0.0;
         if (pb.valid_pt[n] && hnn > 0.0f) {
-            dd = -((double)ds.gn[n] + (double)tot) / (double)hnn;
+            dd = -((double)ds.gn[n] + tot) / (double)hnn;
             double dn = ic_rule ? d * (ds.d0_64[n] - dd) / ds.d0_64[n] : d + dd;
             if (isfinite(dn)) {
                 d = dn;
@@ -58,11 +62,12 @@ __device__ double depth_backsub(const DevProblem& pb, const DepthState& ds, cons
         }
         ds.dd_last[n] = dd;
         ddsq = (float)(dd * dd);
-        s_red[kPassWarps * 32 + lane] = (float)d;
     }
+    __syncthreads();  // all warps have read s_red64 before it is reused
+    if (warp == 0) s_red[2 * kPassWarps * 32 + lane] = (float)d;
     __syncthreads();
     // every warp continues with the updated depth (FP32 is what the pass uses)
-    return (double)s_red[kPassWarps * 32 + lane];
+    return (double)s_red[2 * kPassWarps * 32 + lane];
 }
 
 // Block-wide statistics of a tile: sums of energy, r^2, count, dd^2 and the
@@ -113,66 +118,81 @@ __device__ __forceinline__ float centre_disp(const DevProblem& pb, const float* 
     return sqrtf(du * du + dv * dv);
 }
 
-// Shared-memory carve-up of the pass kernels (floats).
+// Shared-memory carve-up of the pass kernels, per local entry le = e - e0 of
+// the tile (at most F - 1): the entry record, the FP32 constants of its frame
+// (R, t, rotated pattern offsets), the previous R|t, the FP64 update, and a
+// 32-float accumulator; then scratch.
 struct PassSmem {
-    float* fc;    // F * kFrameConst current constants
-    float* prev;  // F * 12 previous R|t
-    float* dth;   // F * 6 last update
-    float* ent;   // F * 32 per local entry accumulators
-    float* red;   // kPassWarps * 32 + 32 scratch
+    double* dth;  // ne * 6
+    Entry* ents;  // ne
+    float* fc;    // ne * kFrameConst
+    float* prev;  // ne * 12
+    float* ent;   // ne * kEntryPartial
+    float* red;   // 3 * kPassWarps * 32 + 64 scratch
     __device__ PassSmem(float* s, int F)
     {
-        fc = s;
+        dth = reinterpret_cast<double*>(s);
+        ents = reinterpret_cast<Entry*>(s + 12 * F);
+        fc = s + 16 * F;
         prev = fc + F * kFrameConst;
-        dth = prev + F * 12;
-        ent = dth + F * 6;
+        ent = prev + F * 12;
         red = ent + F * kEntryPartial;
     }
 };
 
 size_t pass_smem_bytes(int F)
 {
-    return sizeof(float) * ((size_t)F * (kFrameConst + 12 + 6 + kEntryPartial) + 3 * kPassWarps * 32 + 64);
+    return sizeof(float) * ((size_t)F * (16 + kFrameConst + 12 + kEntryPartial) + 3 * kPassWarps * 32 + 64);
 }
 
-__device__ void load_frame_smem(const PassSmem& sm, const FrameState& fs, int F, bool prev,
-                                bool dth)
+// Stages the tile's entries and their frames' constants (the first 12 + 3P
+// floats of each) in shared memory.
+__device__ void load_tile_smem(const PassSmem& sm, const DevProblem& pb, const FrameState& fs,
+                               int e0, int ne, bool prev, bool dth)
 {
-    for (int i = threadIdx.x; i < F * kFrameConst; i += blockDim.x) sm.fc[i] = fs.fc[i];
+    for (int i = threadIdx.x; i < ne; i += blockDim.x) sm.ents[i] = pb.entries[e0 + i];
+    __syncthreads();
+    const int nc = 12 + 3 * pb.P;
+    for (int i = threadIdx.x; i < ne * nc; i += blockDim.x) {
+        const int le = i / nc, k = i % nc;
+        sm.fc[le * kFrameConst + k] = fs.fc[sm.ents[le].f * kFrameConst + k];
+    }
     if (prev)
-        for (int i = threadIdx.x; i < F * 12; i += blockDim.x) sm.prev[i] = fs.fc_prev[i];
+        for (int i = threadIdx.x; i < ne * 12; i += blockDim.x)
+            sm.prev[i] = fs.fc_prev[sm.ents[i / 12].f * 12 + i % 12];
     if (dth)
-        for (int i = threadIdx.x; i < F * 6; i += blockDim.x) sm.dth[i] = fs.dtheta32[i];
+        for (int i = threadIdx.x; i < ne * 6; i += blockDim.x)
+            sm.dth[i] = fs.dtheta64[sm.ents[i / 6].f * 6 + i % 6];
     __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
-// IC precompute (Sec. 3.4-3.5) at the current parameters p_0, evaluated in
-// FP64 once and stored in FP32. Per residual: template gradient (central
-// differences at the integer template pixel), the proxy-warp Jacobian row in
-// pixel units
+// IC precompute (Sec. 3.4-3.5) at the current parameters p_0. Per residual:
+// template gradient (central differences at the integer template pixel), the
+// proxy-warp Jacobian row in pixel units
 //   c = (1/zbar0) (g_u f_x, g_v f_y, -(g_u f_x x + g_v f_y y)),
 //   m = zbar0 R0 c - e_z (t0 . R0 c)            (m = M^T c),
 //   J = [d0 m, (R0 x~) x m, m . t0],
 // the residual and Huber weight at p_0 (J = 0 when invalid there), and the
-// H blocks: H_fd per pair, H_dd per point, H_ff (21 unique) per entry.
+// H blocks from the stored rows: H_fd per pair, H_dd per point, H_ff (21
+// unique) per entry. FP32 throughout (GB300's FP64 issue rate would make
+// this pass FP64-bound); J is stored in FP32 either way and H is formed from
+// the stored rows, so H = J^T W_0 J holds for the J the iterations use.
 // ---------------------------------------------------------------------------
-template <int PMAX>
-__global__ void __launch_bounds__(kTile * kPassWarps)
-ic_precompute_kernel(DevProblem pb, const double* poses0, DepthState ds, IcStore ic,
-                     float* ent_part, TileStats* tstats)
+template <int PMAX, int DT>
+__global__ void __launch_bounds__(kTile * kPassWarps, 4)
+ic_precompute_kernel(DevProblem pb, FrameState fs, DepthState ds, IcStore ic, float* ent_part,
+                     TileStats* tstats)
 {
     extern __shared__ float smraw[];
-    double* s_pose = reinterpret_cast<double*>(smraw);   // F * 12 FP64 poses at p_0
-    float* s_red = smraw + 2 * 12 * pb.F;
-    for (int i = threadIdx.x; i < 12 * pb.F; i += blockDim.x) s_pose[i] = poses0[i];
-    __syncthreads();
+    PassSmem sm(smraw, pb.F);
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = t * kTile + lane;
     const int e0 = pb.tile_entry[t], e1 = pb.tile_entry[t + 1];
+    load_tile_smem(sm, pb, fs, e0, e1 - e0, false, false);
     const int P = pb.P, NC = (7 * P + 3) / 4;
-    const double d0 = ds.d64[n];
-    const double fx = pb.fx, fy = pb.fy, cx = pb.cx, cy = pb.cy;
+    const float d0 = (float)ds.d64[n];
+    const float2 xc = pb.xn[n];
     const int ux = pb.uvs[2 * n], uy = pb.uvs[2 * n + 1];
     float I0[PMAX], gu[PMAX], gv[PMAX];
 #pragma unroll
@@ -181,82 +201,78 @@ ic_precompute_kernel(DevProblem pb, const double* poses0, DepthState ds, IcStore
             I0[j] = pb.I0p[((size_t)t * P + j) * kTile + lane];
             const int px = ux + pb.pat[2 * j], py = uy + pb.pat[2 * j + 1];
             const size_t b = (size_t)py * pb.pitch + px;
-            gu[j] = 0.5f * (load_px(pb.img, pb.dtype, b + 1) - load_px(pb.img, pb.dtype, b - 1));
-            gv[j] = 0.5f * (load_px(pb.img, pb.dtype, b + pb.pitch) -
-                            load_px(pb.img, pb.dtype, b - pb.pitch));
+            gu[j] = 0.5f * (load_px_t<DT>(pb.img, (unsigned)(b + 1)) - load_px_t<DT>(pb.img, (unsigned)(b - 1)));
+            gv[j] = 0.5f * (load_px_t<DT>(pb.img, (unsigned)(b + pb.pitch)) -
+                            load_px_t<DT>(pb.img, (unsigned)(b - pb.pitch)));
         }
     }
     float hnn = 0.0f, energy = 0.0f, sumsq = 0.0f, cnt = 0.0f;
-    for (int e = e0 + warp; e < e1; e += kPassWarps) {
-        const Entry en = pb.entries[e];
-        const double* R = s_pose + 12 * en.f;
-        const double* t0 = R + 9;
+    for (int le = warp; le < e1 - e0; le += kPassWarps) {
+        const Entry en = sm.ents[le];
+        const float* c = sm.fc + le * kFrameConst;
         float hff[21];
 #pragma unroll
         for (int k = 0; k < 21; ++k) hff[k] = 0.0f;
         if ((en.mask >> lane) & 1u) {
             const int nvis = __popc(en.mask), rank = lane_rank(en.mask, lane);
             float Jr[7 * PMAX + 4];
-            double hfd[6] = {0, 0, 0, 0, 0, 0};
+            float hfd[6] = {0, 0, 0, 0, 0, 0};
+            const float ax = fmaf(c[0], xc.x, fmaf(c[1], xc.y, c[2]));
+            const float ay = fmaf(c[3], xc.x, fmaf(c[4], xc.y, c[5]));
+            const float az = fmaf(c[6], xc.x, fmaf(c[7], xc.y, c[8]));
+            const float t0x = c[9], t0y = c[10], t0z = c[11];
 #pragma unroll
             for (int j = 0; j < PMAX; ++j) {
                 if (j >= P) break;
-                float* J = Jr + 7 * j;
-                const double x = (ux + pb.pat[2 * j] - cx) / fx;
-                const double y = (uy + pb.pat[2 * j + 1] - cy) / fy;
-                const double a0 = R[0] * x + R[1] * y + R[2];
-                const double a1 = R[3] * x + R[4] * y + R[5];
-                const double a2 = R[6] * x + R[7] * y + R[8];
-                const double qx = a0 + d0 * t0[0], qy = a1 + d0 * t0[1], qz = a2 + d0 * t0[2];
-                bool valid = qz > 0.0;
+                const float a0 = ax + c[12 + 3 * j], a1 = ay + c[13 + 3 * j], a2 = az + c[14 + 3 * j];
+                const float qx = fmaf(d0, t0x, a0), qy = fmaf(d0, t0y, a1), qz = fmaf(d0, t0z, a2);
                 float val = 0.f, wa, wb;
                 int bx, by;
+                bool valid = qz > 0.0f;
                 if (valid) {
-                    const float u = (float)(fx * qx / qz + cx), v = (float)(fy * qy / qz + cy);
-                    valid = bilinear(pb, en.f, u, v, val, wa, wb, bx, by);
+                    const float iz = 1.0f / qz;
+                    valid = bilinear_t<DT>(pb, en.f, fmaf(pb.fx * qx, iz, pb.cx),
+                                     fmaf(pb.fy * qy, iz, pb.cy), val, wa, wb, bx, by);
                 }
-                if (!valid) {
+                float J[7] = {0, 0, 0, 0, 0, 0, 0};
+                if (valid) {
+                    const float r0 = I0[j] - val;
+                    const float w0 = huber_w(r0, pb.huber_k);
+                    energy += huber_rho(r0, pb.huber_k);
+                    sumsq = fmaf(r0, r0, sumsq);
+                    cnt += 1.0f;
+                    const float x = xc.x + pb.pat[2 * j] / pb.fx, y = xc.y + pb.pat[2 * j + 1] / pb.fy;
+                    const float zb = qz / d0;
+                    const float izb = 1.0f / zb;
+                    const float gx = gu[j] * pb.fx, gy = gv[j] * pb.fy;
+                    const float c0 = gx * izb, c1 = gy * izb, c2 = -fmaf(gx, x, gy * y) * izb;
+                    const float cp0 = fmaf(c[0], c0, fmaf(c[1], c1, c[2] * c2));
+                    const float cp1 = fmaf(c[3], c0, fmaf(c[4], c1, c[5] * c2));
+                    const float cp2 = fmaf(c[6], c0, fmaf(c[7], c1, c[8] * c2));
+                    const float tc = fmaf(t0x, cp0, fmaf(t0y, cp1, t0z * cp2));
+                    const float m0 = zb * cp0, m1 = zb * cp1, m2 = fmaf(zb, cp2, -tc);
+                    J[0] = d0 * m0;
+                    J[1] = d0 * m1;
+                    J[2] = d0 * m2;
+                    J[3] = fmaf(a1, m2, -a2 * m1);
+                    J[4] = fmaf(a2, m0, -a0 * m2);
+                    J[5] = fmaf(a0, m1, -a1 * m0);
+                    J[6] = fmaf(m0, t0x, fmaf(m1, t0y, m2 * t0z));
+                    int q = 0;
 #pragma unroll
-                    for (int k = 0; k < 7; ++k) J[k] = 0.0f;
-                    continue;
-                }
-                const float r0 = I0[j] - val;
-                const double w0 = (double)huber_w(r0, pb.huber_k);
-                energy += huber_rho(r0, pb.huber_k);
-                sumsq += r0 * r0;
-                cnt += 1.0f;
-                const double zb = qz / d0;
-                const double gx = (double)gu[j] * fx, gy = (double)gv[j] * fy;
-                const double c0 = gx / zb, c1 = gy / zb, c2 = -(gx * x + gy * y) / zb;
-                const double cp0 = R[0] * c0 + R[1] * c1 + R[2] * c2;
-                const double cp1 = R[3] * c0 + R[4] * c1 + R[5] * c2;
-                const double cp2 = R[6] * c0 + R[7] * c1 + R[8] * c2;
-                const double tc = t0[0] * cp0 + t0[1] * cp1 + t0[2] * cp2;
-                const double m0 = zb * cp0, m1 = zb * cp1, m2 = zb * cp2 - tc;
-                double Jd[7];
-                Jd[0] = d0 * m0;
-                Jd[1] = d0 * m1;
-                Jd[2] = d0 * m2;
-                Jd[3] = a1 * m2 - a2 * m1;
-                Jd[4] = a2 * m0 - a0 * m2;
-                Jd[5] = a0 * m1 - a1 * m0;
-                Jd[6] = m0 * t0[0] + m1 * t0[1] + m2 * t0[2];
-                // H from the stored (FP32-rounded) row, so H = J^T W0 J holds
-                // exactly for the J the iterations use
+                    for (int a = 0; a < 6; ++a) {
+                        const float wja = w0 * J[a];
 #pragma unroll
-                for (int k = 0; k < 7; ++k) J[k] = (float)Jd[k];
-                int q = 0;
-#pragma unroll
-                for (int a = 0; a < 6; ++a) {
-                    const double wja = w0 * (double)J[a];
-#pragma unroll
-                    for (int b = a; b < 6; ++b) {
-                        hff[q] += (float)(wja * (double)J[b]);
-                        ++q;
+                        for (int b = a; b < 6; ++b) {
+                            hff[q] = fmaf(wja, J[b], hff[q]);
+                            ++q;
+                        }
+                        hfd[a] = fmaf(wja, J[6], hfd[a]);
                     }
-                    hfd[a] += wja * (double)J[6];
+                    hnn = fmaf(w0 * J[6], J[6], hnn);
                 }
-                hnn += (float)(w0 * (double)J[6] * (double)J[6]);
+#pragma unroll
+                for (int k = 0; k < 7; ++k) Jr[7 * j + k] = J[k];
             }
 #pragma unroll
             for (int k = 0; k < 7 * PMAX + 4; ++k)
@@ -269,23 +285,23 @@ ic_precompute_kernel(DevProblem pb, const double* poses0, DepthState ds, IcStore
                         make_float4(Jr[4 * ch], Jr[4 * ch + 1], Jr[4 * ch + 2], Jr[4 * ch + 3]);
             float* hd = ic.Hfd + (size_t)en.pair_off * 6 + rank;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) hd[k * nvis] = (float)hfd[k];
+            for (int k = 0; k < 6; ++k) hd[k * nvis] = hfd[k];
         }
         warp_sum<21>(hff);
         if (lane == 0) {
-            float* out = ent_part + (size_t)e * kEntryPartial;
+            float* out = ent_part + (size_t)pb.entry_slot[e0 + le] * kEntryPartial;
 #pragma unroll
             for (int k = 0; k < 21; ++k) out[k] = hff[k];
         }
     }
-    s_red[warp * 32 + lane] = hnn;
+    sm.red[warp * 32 + lane] = hnn;
     __syncthreads();
     if (warp == 0) {
         float tot = 0.0f;
-        for (int w = 0; w < kPassWarps; ++w) tot += s_red[w * 32 + lane];
+        for (int w = 0; w < kPassWarps; ++w) tot += sm.red[w * 32 + lane];
         ic.Hnn[n] = pb.valid_pt[n] ? tot : 0.0f;
     }
-    tile_stats_write(tstats, t, energy, sumsq, cnt, 0.0f, 0.0f, s_red);
+    tile_stats_write(tstats, t, energy, sumsq, cnt, 0.0f, 0.0f, sm.red);
 }
 
 // ---------------------------------------------------------------------------
@@ -295,22 +311,22 @@ ic_precompute_kernel(DevProblem pb, const double* poses0, DepthState ds, IcStore
 // right-hand side y_f = g_f - sum_n H_fd g_n / H_dd per entry.
 // kAccum = false evaluates statistics only (after the last step).
 // ---------------------------------------------------------------------------
-template <int PMAX, bool kAccum>
-__global__ void __launch_bounds__(kTile * kPassWarps)
+template <int PMAX, bool kAccum, int DT>
+__global__ void __launch_bounds__(kTile * kPassWarps, 5)
 ic_pass_kernel(DevProblem pb, FrameState fs, DepthState ds, IcStore ic, float* ent_part,
                TileStats* tstats, int apply, int have_prev)
 {
     extern __shared__ float smraw[];
     PassSmem sm(smraw, pb.F);
-    load_frame_smem(sm, fs, pb.F, have_prev, apply);
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = t * kTile + lane;
     const int e0 = pb.tile_entry[t], e1 = pb.tile_entry[t + 1];
+    load_tile_smem(sm, pb, fs, e0, e1 - e0, have_prev, apply);
     const int P = pb.P, NC = (7 * P + 3) / 4;
     float ddsq = 0.0f;
     const float dprev = (float)ds.d64[n];
     float d = dprev;
-    if (apply) d = (float)depth_backsub(pb, ds, sm.dth, sm.red, t, e0, e1, true, ddsq);
+    if (apply) d = (float)depth_backsub(pb, ds, sm.ents, sm.dth, sm.red, t, e0, e1, true, ddsq);
     const float2 xc = pb.xn[n];
     float I0[PMAX];
 #pragma unroll
@@ -318,9 +334,9 @@ ic_pass_kernel(DevProblem pb, FrameState fs, DepthState ds, IcStore ic, float* e
         if (j < P) I0[j] = pb.I0p[((size_t)t * P + j) * kTile + lane];
     float gpart = 0.0f, energy = 0.0f, sumsq = 0.0f, cnt = 0.0f, maxdisp = 0.0f;
     const float k = pb.huber_k;
-    for (int e = e0 + warp; e < e1; e += kPassWarps) {
-        const Entry en = pb.entries[e];
-        const float* c = sm.fc + en.f * kFrameConst;
+    for (int le = warp; le < e1 - e0; le += kPassWarps) {
+        const Entry en = sm.ents[le];
+        const float* c = sm.fc + le * kFrameConst;
         float acc[6] = {0, 0, 0, 0, 0, 0};
         if ((en.mask >> lane) & 1u) {
             const int nvis = __popc(en.mask), rank = lane_rank(en.mask, lane);
@@ -350,25 +366,26 @@ ic_pass_kernel(DevProblem pb, FrameState fs, DepthState ds, IcStore ic, float* e
                 const float u = fmaf(pb.fx * qx, iz, pb.cx), v = fmaf(pb.fy * qy, iz, pb.cy);
                 float val, wa, wb;
                 int bx, by;
-                if (!bilinear(pb, en.f, u, v, val, wa, wb, bx, by)) continue;
+                if (!bilinear_t<DT>(pb, en.f, u, v, val, wa, wb, bx, by)) continue;
                 const float r = I0[j] - val;
                 energy += huber_rho(r, k);
                 sumsq = fmaf(r, r, sumsq);
                 cnt += 1.0f;
                 if (kAccum) {
-                    const float wr = huber_w(r, k) * r;
+                    // w r with w = min(1, k/|r|): r, or k sign(r) (exact, no division)
+                    const float wr = fabsf(r) <= k ? r : copysignf(k, r);
 #pragma unroll
                     for (int a = 0; a < 6; ++a) acc[a] = fmaf(Jr[7 * j + a], wr, acc[a]);
                     gpart = fmaf(Jr[7 * j + 6], wr, gpart);
                 }
             }
             if (have_prev)
-                maxdisp = fmaxf(maxdisp, centre_disp(pb, c, sm.prev + 12 * en.f, xc, d, dprev));
+                maxdisp = fmaxf(maxdisp, centre_disp(pb, c, sm.prev + 12 * le, xc, d, dprev));
         }
         if (kAccum) {
             warp_sum<6>(acc);
             if (lane == 0) {
-                float* o = sm.ent + (e - e0) * kEntryPartial;
+                float* o = sm.ent + le * kEntryPartial;
 #pragma unroll
                 for (int a = 0; a < 6; ++a) o[a] = acc[a];
             }
@@ -387,8 +404,8 @@ ic_pass_kernel(DevProblem pb, FrameState fs, DepthState ds, IcStore ic, float* e
         }
         __syncthreads();
         const float sn = sm.red[kPassWarps * 32 + lane];
-        for (int e = e0 + warp; e < e1; e += kPassWarps) {
-            const Entry en = pb.entries[e];
+        for (int le = warp; le < e1 - e0; le += kPassWarps) {
+            const Entry en = sm.ents[le];
             float acc[6] = {0, 0, 0, 0, 0, 0};
             if ((en.mask >> lane) & 1u) {
                 const int nvis = __popc(en.mask), rank = lane_rank(en.mask, lane);
@@ -398,8 +415,8 @@ ic_pass_kernel(DevProblem pb, FrameState fs, DepthState ds, IcStore ic, float* e
             }
             warp_sum<6>(acc);
             if (lane == 0) {
-                const float* o = sm.ent + (e - e0) * kEntryPartial;
-                float* out = ent_part + (size_t)e * kEntryPartial;
+                const float* o = sm.ent + le * kEntryPartial;
+                float* out = ent_part + (size_t)pb.entry_slot[e0 + le] * kEntryPartial;
 #pragma unroll
                 for (int a = 0; a < 6; ++a) out[a] = o[a] - acc[a];
             }
@@ -417,22 +434,22 @@ ic_pass_kernel(DevProblem pb, FrameState fs, DepthState ds, IcStore ic, float* e
 // accumulating H_ff (21) and g_f per entry, H_fd per pair, H_dd and g_d per
 // point with the current Huber weights; epilogue = Schur right-hand side.
 // ---------------------------------------------------------------------------
-template <int PMAX, bool kAccum>
+template <int PMAX, bool kAccum, int DT>
 __global__ void __launch_bounds__(kTile * kPassWarps)
 fc_pass_kernel(DevProblem pb, FrameState fs, DepthState ds, float* Hfd_out, float* ent_part,
                TileStats* tstats, int apply, int have_prev)
 {
     extern __shared__ float smraw[];
     PassSmem sm(smraw, pb.F);
-    load_frame_smem(sm, fs, pb.F, have_prev, apply);
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = t * kTile + lane;
     const int e0 = pb.tile_entry[t], e1 = pb.tile_entry[t + 1];
+    load_tile_smem(sm, pb, fs, e0, e1 - e0, have_prev, apply);
     const int P = pb.P;
     float ddsq = 0.0f;
     const float dprev = (float)ds.d64[n];
     float d = dprev;
-    if (apply) d = (float)depth_backsub(pb, ds, sm.dth, sm.red, t, e0, e1, false, ddsq);
+    if (apply) d = (float)depth_backsub(pb, ds, sm.ents, sm.dth, sm.red, t, e0, e1, false, ddsq);
     __syncthreads();  // the prologue read H_fd / g / H_dd that this pass rewrites
     const float2 xc = pb.xn[n];
     float I0[PMAX];
@@ -441,9 +458,9 @@ fc_pass_kernel(DevProblem pb, FrameState fs, DepthState ds, float* Hfd_out, floa
         if (j < P) I0[j] = pb.I0p[((size_t)t * P + j) * kTile + lane];
     float gpart = 0.0f, hnn = 0.0f, energy = 0.0f, sumsq = 0.0f, cnt = 0.0f, maxdisp = 0.0f;
     const float k = pb.huber_k;
-    for (int e = e0 + warp; e < e1; e += kPassWarps) {
-        const Entry en = pb.entries[e];
-        const float* c = sm.fc + en.f * kFrameConst;
+    for (int le = warp; le < e1 - e0; le += kPassWarps) {
+        const Entry en = sm.ents[le];
+        const float* c = sm.fc + le * kFrameConst;
         float acc[27];
 #pragma unroll
         for (int a = 0; a < 27; ++a) acc[a] = 0.0f;
@@ -462,7 +479,7 @@ fc_pass_kernel(DevProblem pb, FrameState fs, DepthState ds, float* Hfd_out, floa
                 const float u = fmaf(pb.fx * qx, iz, pb.cx), v = fmaf(pb.fy * qy, iz, pb.cy);
                 float val, wa, wb;
                 int bx, by;
-                if (!bilinear(pb, en.f, u, v, val, wa, wb, bx, by)) continue;
+                if (!bilinear_t<DT>(pb, en.f, u, v, val, wa, wb, bx, by)) continue;
                 const float r = I0[j] - val;
                 energy += huber_rho(r, k);
                 sumsq = fmaf(r, r, sumsq);
@@ -511,12 +528,12 @@ fc_pass_kernel(DevProblem pb, FrameState fs, DepthState ds, float* Hfd_out, floa
                 for (int a = 0; a < 6; ++a) hd[a * nvis] = hfd[a];
             }
             if (have_prev)
-                maxdisp = fmaxf(maxdisp, centre_disp(pb, c, sm.prev + 12 * en.f, xc, d, dprev));
+                maxdisp = fmaxf(maxdisp, centre_disp(pb, c, sm.prev + 12 * le, xc, d, dprev));
         }
         if (kAccum) {
             warp_sum<27>(acc);
             if (lane == 0) {
-                float* o = sm.ent + (e - e0) * kEntryPartial;
+                float* o = sm.ent + le * kEntryPartial;
 #pragma unroll
                 for (int a = 0; a < 27; ++a) o[a] = acc[a];
             }
@@ -539,8 +556,8 @@ fc_pass_kernel(DevProblem pb, FrameState fs, DepthState ds, float* Hfd_out, floa
         }
         __syncthreads();
         const float sn = sm.red[2 * kPassWarps * 32 + lane];
-        for (int e = e0 + warp; e < e1; e += kPassWarps) {
-            const Entry en = pb.entries[e];
+        for (int le = warp; le < e1 - e0; le += kPassWarps) {
+            const Entry en = sm.ents[le];
             float acc[6] = {0, 0, 0, 0, 0, 0};
             if ((en.mask >> lane) & 1u) {
                 const int nvis = __popc(en.mask), rank = lane_rank(en.mask, lane);
@@ -550,8 +567,8 @@ fc_pass_kernel(DevProblem pb, FrameState fs, DepthState ds, float* Hfd_out, floa
             }
             warp_sum<6>(acc);
             if (lane == 0) {
-                const float* o = sm.ent + (e - e0) * kEntryPartial;
-                float* out = ent_part + (size_t)e * kEntryPartial;
+                const float* o = sm.ent + le * kEntryPartial;
+                float* out = ent_part + (size_t)pb.entry_slot[e0 + le] * kEntryPartial;
 #pragma unroll
                 for (int a = 0; a < 21; ++a) out[a] = o[a];
 #pragma unroll
@@ -563,129 +580,177 @@ fc_pass_kernel(DevProblem pb, FrameState fs, DepthState ds, float* Hfd_out, floa
 }
 
 // ---------------------------------------------------------------------------
-// Fixed-order per-frame reduction of entry partials (Neumaier-compensated
-// FP32 per thread, fixed tree across threads, FP64 result), plus one extra
-// block that folds the tile statistics into the statistics slots.
+// Fixed-order per-frame reduction of entry partials, plus one extra block that
+// folds the tile statistics into the statistics slots. Sums are kept as
+// unevaluated FP32 pairs (s, c): Neumaier accumulation per lane, then a
+// butterfly whose additions are error-free two-sums (Knuth), converted to
+// FP64 once at the end. GB300 issues FP64 slowly; this keeps the reductions
+// on the FP32 pipes while carrying about 48 bits.
 // out[f * ncomp + k] = sum over the entries of frame f of part[e][off + k].
 // ---------------------------------------------------------------------------
 constexpr int kReduceThreads = 128;
+
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float s2, float c2)
+{
+    const float t = s + s2;
+    const float bb = t - s;
+    const float e = (s - (t - bb)) + (s2 - bb);
+    s = t;
+    c = c + c2 + e;
+}
+
+__device__ __forceinline__ void warp_sum_pair(float& s, float& c)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        two_sum_add(s, c, s2, c2);
+    }
+}
 
 __global__ void __launch_bounds__(kReduceThreads)
 frame_reduce_kernel(DevProblem pb, const float* ent_part, int off, int ncomp, double* out,
                     const TileStats* tstats, const float* dthsq, double* stats, int slot_cur,
                     int slot_prev, int nframes_blocks)
 {
-    __shared__ double red[kReduceThreads];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nw = kReduceThreads / 32;
     if ((int)blockIdx.x < nframes_blocks) {
         const int f = blockIdx.x + 1;
         const int s0 = pb.frame_entry[f], s1 = pb.frame_entry[f + 1];
-        for (int k = 0; k < ncomp; ++k) {
-            float s = 0.0f, cmp = 0.0f;
-            for (int i = s0 + tid; i < s1; i += kReduceThreads)
-                neumaier_add(s, cmp, ent_part[(size_t)pb.frame_entries[i] * kEntryPartial + off + k]);
-            red[tid] = (double)s + (double)cmp;
-            __syncthreads();
-            for (int h = kReduceThreads / 2; h > 0; h >>= 1) {
-                if (tid < h) red[tid] += red[tid + h];
-                __syncthreads();
-            }
-            if (tid == 0) out[(size_t)f * ncomp + k] = red[0];
-            __syncthreads();
+        for (int k = warp; k < ncomp; k += nw) {
+            float s = 0.0f, c = 0.0f;
+#pragma unroll 8
+            for (int i = s0 + lane; i < s1; i += 32)
+                neumaier_add(s, c, ent_part[(size_t)i * kEntryPartial + off + k]);
+            warp_sum_pair(s, c);
+            if (lane == 0) out[(size_t)f * ncomp + k] = (double)s + (double)c;
         }
         return;
     }
-    // statistics block
-    double acc[5] = {0, 0, 0, 0, 0};
+    // statistics block: every thread folds a strided share of the tiles
+    // (energy, r^2, count, dd^2 as unevaluated pairs; max displacement), then
+    // warps and the block combine them in a fixed order
+    __shared__ double res[5];
+    __shared__ float sh_s[4][nw], sh_c[4][nw], sh_m[nw];
+    float s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0}, m = 0.0f;
+#pragma unroll 4
     for (int i = tid; i < pb.T; i += kReduceThreads) {
-        const TileStats s = tstats[i];
-        acc[0] += s.energy;
-        acc[1] += s.sumsq;
-        acc[2] += s.count;
-        acc[3] = fmax(acc[3], (double)s.maxdisp);
-        acc[4] += s.ddsq;
+        const TileStats ts = tstats[i];
+        neumaier_add(s[0], c[0], ts.energy);
+        neumaier_add(s[1], c[1], ts.sumsq);
+        neumaier_add(s[2], c[2], ts.count);
+        neumaier_add(s[3], c[3], ts.ddsq);
+        m = fmaxf(m, ts.maxdisp);
     }
-    for (int k = 0; k < 5; ++k) {
-        red[tid] = acc[k];
-        __syncthreads();
-        for (int h = kReduceThreads / 2; h > 0; h >>= 1) {
-            if (tid < h) red[tid] = (k == 3) ? fmax(red[tid], red[tid + h]) : red[tid] + red[tid + h];
-            __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) warp_sum_pair(s[q], c[q]);
+    m = warp_max1(m);
+    if (lane == 0) {
+        for (int q = 0; q < 4; ++q) {
+            sh_s[q][warp] = s[q];
+            sh_c[q][warp] = c[q];
         }
-        acc[k] = red[0];
-        __syncthreads();
+        sh_m[warp] = m;
     }
+    __syncthreads();
+    if (tid < 4) {
+        float vs = sh_s[tid][0], vc = sh_c[tid][0];
+        for (int w = 1; w < nw; ++w) two_sum_add(vs, vc, sh_s[tid][w], sh_c[tid][w]);
+        res[tid == 3 ? 4 : tid] = (double)vs + (double)vc;
+    }
+    if (tid == 4) {
+        float mm = 0.0f;
+        for (int w = 0; w < nw; ++w) mm = fmaxf(mm, sh_m[w]);
+        res[3] = mm;
+    }
+    __syncthreads();
     if (tid == 0) {
         if (slot_cur >= 0) {
-            double* s = stats + (size_t)slot_cur * kStats;
-            s[0] = acc[0];
-            s[1] = acc[2] > 0 ? sqrt(acc[1] / acc[2]) : 0.0;
-            s[2] = acc[2];
+            double* st = stats + (size_t)slot_cur * kStats;
+            st[0] = res[0];
+            st[1] = res[2] > 0 ? sqrt(res[1] / res[2]) : 0.0;
+            st[2] = res[2];
         }
         if (slot_prev >= 0) {
-            double* s = stats + (size_t)slot_prev * kStats;
-            s[3] = acc[3];
-            s[5] = sqrt(acc[4]);
-            double q = 0.0;
-            for (int f = 0; f < pb.F; ++f) q += dthsq[f];
-            s[4] = sqrt(q);
+            double* st = stats + (size_t)slot_prev * kStats;
+            st[3] = res[3];
+            st[5] = sqrt(res[4]);
+            float q = 0.0f, qc = 0.0f;
+            for (int f = 0; f < pb.F; ++f) neumaier_add(q, qc, dthsq[f]);
+            st[4] = sqrt((double)q + (double)qc);
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// launchers
+// launchers (dispatch on the pattern capacity and the image storage type)
 // ---------------------------------------------------------------------------
-template <int PMAX>
-static cudaError_t launch_ic_precompute_p(const LaunchCtx& L)
+#define PBA_DISPATCH_DT(dtype, CALL) \
+    ((dtype) == PBA_F32 ? CALL(PBA_F32) : (dtype) == PBA_F16 ? CALL(PBA_F16) : CALL(PBA_BF16))
+
+template <int PMAX, int DT>
+static cudaError_t ic_precompute_p(const LaunchCtx& L)
 {
-    size_t sm = pass_smem_bytes(L.pb.F);
-    ic_precompute_kernel<PMAX><<<L.pb.T, kTile * kPassWarps, sm, L.stream>>>(
-        L.pb, L.poses0, L.ds_ic, L.ic, L.ent_part, L.tstats);
+    ic_precompute_kernel<PMAX, DT><<<L.pb.T, kTile * kPassWarps, pass_smem_bytes(L.pb.F), L.stream>>>(
+        L.pb, L.fs, L.ds_ic, L.ic, L.ent_part, L.tstats);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ic_precompute(const LaunchCtx& L)
 {
-    return L.pb.P <= 8 ? launch_ic_precompute_p<8>(L) : launch_ic_precompute_p<16>(L);
+#define PBA_C8(DT) ic_precompute_p<8, DT>(L)
+#define PBA_C16(DT) ic_precompute_p<16, DT>(L)
+    return L.pb.P <= 8 ? PBA_DISPATCH_DT(L.pb.dtype, PBA_C8) : PBA_DISPATCH_DT(L.pb.dtype, PBA_C16);
+#undef PBA_C8
+#undef PBA_C16
 }
 
-template <int PMAX>
-static cudaError_t launch_ic_pass_p(const LaunchCtx& L, bool accum, int apply, int have_prev)
+template <int PMAX, bool A, int DT>
+static cudaError_t ic_pass_p(const LaunchCtx& L, int apply, int have_prev)
 {
-    size_t sm = pass_smem_bytes(L.pb.F);
-    if (accum)
-        ic_pass_kernel<PMAX, true><<<L.pb.T, kTile * kPassWarps, sm, L.stream>>>(
-            L.pb, L.fs, L.ds_ic, L.ic, L.ent_part, L.tstats, apply, have_prev);
-    else
-        ic_pass_kernel<PMAX, false><<<L.pb.T, kTile * kPassWarps, sm, L.stream>>>(
-            L.pb, L.fs, L.ds_ic, L.ic, L.ent_part, L.tstats, apply, have_prev);
+    ic_pass_kernel<PMAX, A, DT><<<L.pb.T, kTile * kPassWarps, pass_smem_bytes(L.pb.F), L.stream>>>(
+        L.pb, L.fs, L.ds_ic, L.ic, L.ent_part, L.tstats, apply, have_prev);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ic_pass(const LaunchCtx& L, bool accum, int apply, int have_prev)
 {
-    return L.pb.P <= 8 ? launch_ic_pass_p<8>(L, accum, apply, have_prev)
-                       : launch_ic_pass_p<16>(L, accum, apply, have_prev);
+#define PBA_C(PM, A) \
+    [&]() { \
+        switch (L.pb.dtype) { \
+        case PBA_F32: return ic_pass_p<PM, A, PBA_F32>(L, apply, have_prev); \
+        case PBA_F16: return ic_pass_p<PM, A, PBA_F16>(L, apply, have_prev); \
+        default: return ic_pass_p<PM, A, PBA_BF16>(L, apply, have_prev); \
+        } \
+    }()
+    if (L.pb.P <= 8) return accum ? PBA_C(8, true) : PBA_C(8, false);
+    return accum ? PBA_C(16, true) : PBA_C(16, false);
+#undef PBA_C
 }
 
-template <int PMAX>
-static cudaError_t launch_fc_pass_p(const LaunchCtx& L, bool accum, int apply, int have_prev)
+template <int PMAX, bool A, int DT>
+static cudaError_t fc_pass_p(const LaunchCtx& L, int apply, int have_prev)
 {
-    size_t sm = pass_smem_bytes(L.pb.F);
-    if (accum)
-        fc_pass_kernel<PMAX, true><<<L.pb.T, kTile * kPassWarps, sm, L.stream>>>(
-            L.pb, L.fs, L.ds_fc, L.Hfd_fc, L.ent_part, L.tstats, apply, have_prev);
-    else
-        fc_pass_kernel<PMAX, false><<<L.pb.T, kTile * kPassWarps, sm, L.stream>>>(
-            L.pb, L.fs, L.ds_fc, L.Hfd_fc, L.ent_part, L.tstats, apply, have_prev);
+    fc_pass_kernel<PMAX, A, DT><<<L.pb.T, kTile * kPassWarps, pass_smem_bytes(L.pb.F), L.stream>>>(
+        L.pb, L.fs, L.ds_fc, L.Hfd_fc, L.ent_part, L.tstats, apply, have_prev);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fc_pass(const LaunchCtx& L, bool accum, int apply, int have_prev)
 {
-    return L.pb.P <= 8 ? launch_fc_pass_p<8>(L, accum, apply, have_prev)
-                       : launch_fc_pass_p<16>(L, accum, apply, have_prev);
+#define PBA_C(PM, A) \
+    [&]() { \
+        switch (L.pb.dtype) { \
+        case PBA_F32: return fc_pass_p<PM, A, PBA_F32>(L, apply, have_prev); \
+        case PBA_F16: return fc_pass_p<PM, A, PBA_F16>(L, apply, have_prev); \
+        default: return fc_pass_p<PM, A, PBA_BF16>(L, apply, have_prev); \
+        } \
+    }()
+    if (L.pb.P <= 8) return accum ? PBA_C(8, true) : PBA_C(8, false);
+    return accum ? PBA_C(16, true) : PBA_C(16, false);
+#undef PBA_C
 }
 
 cudaError_t launch_frame_reduce(const LaunchCtx& L, int off, int ncomp, double* out, int slot_cur,
@@ -697,26 +762,33 @@ cudaError_t launch_frame_reduce(const LaunchCtx& L, int off, int ncomp, double* 
     return cudaGetLastError();
 }
 
-cudaError_t set_pass_smem_limits(int F)
+template <int PM, int DT>
+static cudaError_t smem_limits_pd(int sm)
 {
-    size_t sm = pass_smem_bytes(F);
-    if (sm <= 48 * 1024) return cudaSuccess;
     cudaError_t e;
-#define PBA_SMEM(kern)                                                                     \
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+#define PBA_SMEM(...)                                                                                     \
+    e = cudaFuncSetAttribute(__VA_ARGS__, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); \
     if (e != cudaSuccess) return e;
-    PBA_SMEM(ic_precompute_kernel<8>)
-    PBA_SMEM(ic_precompute_kernel<16>)
-    PBA_SMEM((ic_pass_kernel<8, true>))
-    PBA_SMEM((ic_pass_kernel<8, false>))
-    PBA_SMEM((ic_pass_kernel<16, true>))
-    PBA_SMEM((ic_pass_kernel<16, false>))
-    PBA_SMEM((fc_pass_kernel<8, true>))
-    PBA_SMEM((fc_pass_kernel<8, false>))
-    PBA_SMEM((fc_pass_kernel<16, true>))
-    PBA_SMEM((fc_pass_kernel<16, false>))
+    PBA_SMEM(ic_precompute_kernel<PM, DT>)
+    PBA_SMEM(ic_pass_kernel<PM, true, DT>)
+    PBA_SMEM(ic_pass_kernel<PM, false, DT>)
+    PBA_SMEM(fc_pass_kernel<PM, true, DT>)
+    PBA_SMEM(fc_pass_kernel<PM, false, DT>)
 #undef PBA_SMEM
     return cudaSuccess;
+}
+
+cudaError_t set_pass_smem_limits(int F)
+{
+    const size_t sm = pass_smem_bytes(F);
+    if (sm <= 48 * 1024) return cudaSuccess;
+    cudaError_t e;
+    if ((e = smem_limits_pd<8, PBA_F32>((int)sm)) != cudaSuccess) return e;
+    if ((e = smem_limits_pd<8, PBA_F16>((int)sm)) != cudaSuccess) return e;
+    if ((e = smem_limits_pd<8, PBA_BF16>((int)sm)) != cudaSuccess) return e;
+    if ((e = smem_limits_pd<16, PBA_F32>((int)sm)) != cudaSuccess) return e;
+    if ((e = smem_limits_pd<16, PBA_F16>((int)sm)) != cudaSuccess) return e;
+    return smem_limits_pd<16, PBA_BF16>((int)sm);
 }
 
 }  // namespace pba

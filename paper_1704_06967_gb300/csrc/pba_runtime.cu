@@ -64,8 +64,9 @@ struct pba_ctx {
     int64_t V = 0;
     std::vector<int> perm;  // sorted slot -> caller index (-1 for pads)
     std::vector<Entry> entries;
-    std::vector<int> tile_entry, frame_entry, frame_entries, ent_of;
-    std::vector<int2> frame_pairs;
+    std::vector<int> tile_entry, frame_entry, entry_slot, ent_of;
+    std::vector<int> pair_fg, pair_chunk, chunk_pair, chunk_start;  // sparse Schur lists
+    std::vector<int2> pair_items;
 
     // workspace
     bool ws_ready = false, ic_ready = false;
@@ -76,7 +77,7 @@ struct pba_ctx {
         float *gx, *gy;
         int* pat;
         Entry* entries;
-        int *tile_entry, *frame_entry, *frame_entries, *ent_of;
+        int *tile_entry, *frame_entry, *entry_slot, *ent_of;
         int* uvs;
         float2* xn;
         float* I0p;
@@ -90,9 +91,12 @@ struct pba_ctx {
         float *fc, *fc_prev, *dtheta32, *dthsq;
         double *poses64, *poses0_64, *dtheta64;
         double *red_ic, *red_y;
-        double *Soff, *S_ic, *L_ic, *Sinv, *S_fc, *L_fc;
+        double *Soff, *S_ic, *L_ic, *Sinv, *S_fc, *L_fc, *chol_work;
+        double *invd_ic, *invd_fc;
+        int *pair_fg, *pair_chunk, *chunk_pair, *chunk_start;
+        int2* pair_items;
+        float2* schur_part;
         int *active_ic, *active_fc;
-        int2* frame_pairs;
         int* err;
         double* stats;
     } d{};
@@ -134,6 +138,16 @@ pba_status fail(pba_ctx* c, pba_status s, const char* fmt, ...)
         int ev_ = tbegin(ctx, slot);  \
         CK(call);                     \
         ++ctx->launches;              \
+        tend(ctx, ev_);               \
+    } while (0)
+
+// for launchers that enqueue several kernels and count them in `nl`
+#define LAUNCHN(slot, call)           \
+    do {                              \
+        int ev_ = tbegin(ctx, slot);  \
+        int nl = 0;                   \
+        CK(call);                     \
+        ctx->launches += nl;          \
         tend(ctx, ev_);               \
     } while (0)
 
@@ -215,7 +229,7 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.entries, (size_t)c->E * sizeof(Entry));
     take(c->d.tile_entry, (size_t)(c->T + 1) * 4);
     take(c->d.frame_entry, (F + 1) * 4);
-    take(c->d.frame_entries, (size_t)c->E * 4);
+    take(c->d.entry_slot, (size_t)c->E * 4);
     take(c->d.ent_of, (size_t)c->T * F * 4);
     take(c->d.uvs, Np * 8);
     take(c->d.xn, Np * 8);
@@ -248,9 +262,17 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.Sinv, n6 * n6 * 8);
     take(c->d.S_fc, n6 * n6 * 8);
     take(c->d.L_fc, n6 * n6 * 8);
+    take(c->d.chol_work, n6 * n6 * 8);
+    take(c->d.invd_ic, n6 * 8);
+    take(c->d.invd_fc, n6 * 8);
+    take(c->d.pair_fg, c->pair_fg.size() * sizeof(int));
+    take(c->d.pair_chunk, c->pair_chunk.size() * sizeof(int));
+    take(c->d.chunk_pair, c->chunk_pair.size() * sizeof(int));
+    take(c->d.chunk_start, c->chunk_start.size() * sizeof(int));
+    take(c->d.pair_items, c->pair_items.size() * sizeof(int2));
+    take(c->d.schur_part, c->chunk_pair.size() * 36 * sizeof(float2));
     take(c->d.active_ic, F * 4);
     take(c->d.active_fc, F * 4);
-    take(c->d.frame_pairs, c->frame_pairs.size() * sizeof(int2));
     take(c->d.err, 64);
     take(c->d.stats, (size_t)(c->stats_slots) * kStats * 8);
     return off;
@@ -294,13 +316,42 @@ void build_structure(pba_ctx* c)
     c->frame_entry.assign(F + 1, 0);
     for (const Entry& e : c->entries) c->frame_entry[e.f + 1]++;
     for (int f = 0; f < F; ++f) c->frame_entry[f + 1] += c->frame_entry[f];
-    c->frame_entries.assign(c->E, 0);
+    // partial sums of entry e go to row entry_slot[e]: frame-major, tile
+    // order within a frame (the reduction's fixed order, contiguous per frame)
+    c->entry_slot.assign(c->E, 0);
     std::vector<int> fill(c->frame_entry.begin(), c->frame_entry.end() - 1);
-    for (int e = 0; e < c->E; ++e) c->frame_entries[fill[c->entries[e].f]++] = e;
-    c->frame_pairs.clear();
-    for (int f = 1; f < F; ++f)
-        for (int g = f; g < F; ++g) c->frame_pairs.push_back(make_int2(f, g));
+    for (int e = 0; e < c->E; ++e) c->entry_slot[e] = fill[c->entries[e].f]++;
     c->NC = (7 * (int)(c->pattern.size() / 2) + 3) / 4;
+    // frame pairs with the (entry, entry) items of the tiles that see both
+    // (tile order: the sparse Schur kernel's fixed summation order), cut into
+    // chunks of at most kSchurChunk items
+    c->pair_fg.clear();
+    c->pair_chunk.assign(1, 0);
+    c->chunk_pair.clear();
+    c->chunk_start.assign(1, 0);
+    c->pair_items.clear();
+    for (int f = 1; f < F; ++f)
+        for (int g = f; g < F; ++g) {
+            const int p = (int)c->pair_fg.size() / 2;
+            size_t n_in_chunk = 0;
+            for (int t = 0; t < c->T; ++t) {
+                const int a = c->ent_of[(size_t)t * F + f], b = c->ent_of[(size_t)t * F + g];
+                if (!(a >= 0 && b >= 0 && (c->entries[a].mask & c->entries[b].mask))) continue;
+                c->pair_items.push_back(make_int2(a, b));
+                if (++n_in_chunk == (size_t)kSchurChunk) {
+                    c->chunk_pair.push_back(p);
+                    c->chunk_start.push_back((int)c->pair_items.size());
+                    n_in_chunk = 0;
+                }
+            }
+            if (n_in_chunk > 0) {
+                c->chunk_pair.push_back(p);
+                c->chunk_start.push_back((int)c->pair_items.size());
+            }
+            c->pair_fg.push_back(f);
+            c->pair_fg.push_back(g);
+            c->pair_chunk.push_back((int)c->chunk_pair.size());
+        }
 }
 
 pba_status upload_params(pba_ctx* ctx, const double* poses, const double* depth)
@@ -367,13 +418,13 @@ LaunchCtx make_launch(pba_ctx* c)
     pb.entries = c->d.entries;
     pb.tile_entry = c->d.tile_entry;
     pb.frame_entry = c->d.frame_entry;
-    pb.frame_entries = c->d.frame_entries;
+    pb.entry_slot = c->d.entry_slot;
     pb.ent_of = c->d.ent_of;
     pb.uvs = c->d.uvs;
     pb.xn = c->d.xn;
     pb.I0p = c->d.I0p;
     pb.valid_pt = c->d.valid_pt;
-    L.fs = FrameState{c->d.fc, c->d.fc_prev, c->d.dtheta32};
+    L.fs = FrameState{c->d.fc, c->d.fc_prev, c->d.dtheta32, c->d.dtheta64};
     L.ds_ic = DepthState{c->d.d64, c->d.d0_64, c->d.gn_ic, c->d.Hnn_ic, c->d.Hfd_ic, c->d.dd_last, c->d.err};
     L.ds_fc = DepthState{c->d.d64, c->d.d0_64, c->d.gn_fc, c->d.Hnn_fc, c->d.Hfd_fc, c->d.dd_last, c->d.err};
     L.ic = IcStore{c->d.J4, c->d.Hfd_ic, c->d.Hnn_ic};
@@ -387,6 +438,12 @@ LaunchCtx make_launch(pba_ctx* c)
     return L;
 }
 
+SchurLists schur_lists(pba_ctx* c)
+{
+    return SchurLists{c->d.pair_fg, c->d.pair_chunk, c->d.chunk_pair, c->d.chunk_start,
+                      c->d.pair_items, (int)c->pair_fg.size() / 2, (int)c->chunk_pair.size()};
+}
+
 SolveArgs make_solve(pba_ctx* c)
 {
     SolveArgs a{};
@@ -396,6 +453,8 @@ SolveArgs make_solve(pba_ctx* c)
     a.P = (int)c->pattern.size() / 2;
     a.fx = c->K[0];
     a.fy = c->K[1];
+    a.inv_fx = 1.0 / c->K[0];
+    a.inv_fy = 1.0 / c->K[1];
     a.poses64 = c->d.poses64;
     a.poses0 = c->d.poses0_64;
     a.dtheta64 = c->d.dtheta64;
@@ -522,6 +581,8 @@ pba_status pba_set_frames(pba_ctx* ctx, int bundle, int n_frames, int w, int h, 
         return fail(ctx, PBA_ERR_ARG, "invalid dtype");
     if (mem != PBA_MEM_DEVICE && mem != PBA_MEM_HOST) return fail(ctx, PBA_ERR_ARG, "invalid memory kind");
     if (6 * (n_frames - 1) > 6 * 1024) return fail(ctx, PBA_ERR_ARG, "too many frames");
+    if ((double)n_frames * h * pitch_elems >= 2147483648.0)
+        return fail(ctx, PBA_ERR_ARG, "image stack too large (F * h * pitch must stay below 2^31)");
     if (mem == PBA_MEM_DEVICE && ((uintptr_t)images % elem_size(dtype)))
         return fail(ctx, PBA_ERR_ARG, "misaligned image pointer");
     for (int i = 0; i < 4; ++i)
@@ -623,12 +684,16 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     CK(h2d(ctx, ctx->d.entries, ctx->entries.data(), sizeof(Entry) * ctx->entries.size()));
     CK(h2d(ctx, ctx->d.tile_entry, ctx->tile_entry.data(), sizeof(int) * ctx->tile_entry.size()));
     CK(h2d(ctx, ctx->d.frame_entry, ctx->frame_entry.data(), sizeof(int) * ctx->frame_entry.size()));
-    CK(h2d(ctx, ctx->d.frame_entries, ctx->frame_entries.data(), sizeof(int) * ctx->frame_entries.size()));
+    CK(h2d(ctx, ctx->d.entry_slot, ctx->entry_slot.data(), sizeof(int) * ctx->entry_slot.size()));
     CK(h2d(ctx, ctx->d.ent_of, ctx->ent_of.data(), sizeof(int) * ctx->ent_of.size()));
     CK(h2d(ctx, ctx->d.uvs, uvs.data(), sizeof(int) * uvs.size()));
     CK(h2d(ctx, ctx->d.xn, xn.data(), sizeof(float2) * xn.size()));
     CK(h2d(ctx, ctx->d.valid_pt, valid.data(), valid.size()));
-    CK(h2d(ctx, ctx->d.frame_pairs, ctx->frame_pairs.data(), sizeof(int2) * ctx->frame_pairs.size()));
+    CK(h2d(ctx, ctx->d.pair_fg, ctx->pair_fg.data(), sizeof(int) * ctx->pair_fg.size()));
+    CK(h2d(ctx, ctx->d.pair_chunk, ctx->pair_chunk.data(), sizeof(int) * ctx->pair_chunk.size()));
+    CK(h2d(ctx, ctx->d.chunk_pair, ctx->chunk_pair.data(), sizeof(int) * ctx->chunk_pair.size()));
+    CK(h2d(ctx, ctx->d.chunk_start, ctx->chunk_start.data(), sizeof(int) * ctx->chunk_start.size()));
+    CK(h2d(ctx, ctx->d.pair_items, ctx->pair_items.data(), sizeof(int2) * ctx->pair_items.size()));
     pba_status s = upload_params(ctx, ctx->poses_init.data(), ctx->d_init.data());
     if (s != PBA_OK) return s;
     CK(h2d(ctx, ctx->d.poses0_64, ctx->poses_init.data(), sizeof(double) * 12 * ctx->F));
@@ -652,13 +717,14 @@ pba_status pba_precompute_ic(pba_ctx* ctx)
     CK(cudaMemcpyAsync(ctx->d.d0_64, ctx->d.d64, sizeof(double) * ctx->Npad, cudaMemcpyDeviceToDevice, ctx->stream));
     LAUNCH(TS_PRE, launch_ic_precompute(L));
     LAUNCH(TS_PRE, launch_frame_reduce(L, 0, 21, ctx->d.red_ic, -1, -1, true));
-    LAUNCH(TS_PRE, launch_schur_offdiag(L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, ctx->d.frame_pairs,
-                                        (int)ctx->frame_pairs.size(), ctx->d.Soff, ctx->stream));
+    LAUNCHN(TS_PRE, launch_schur_sparse(L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, schur_lists(ctx),
+                                        ctx->d.schur_part, ctx->d.Soff, ctx->stream, &nl));
     LAUNCH(TS_PRE, launch_assemble_S(F, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64,
                                      ctx->cfg.gauge_anchor_w, ctx->d.S_ic, ctx->d.active_ic, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.L_ic, ctx->d.S_ic, sizeof(double) * n6 * n6, cudaMemcpyDeviceToDevice, ctx->stream));
-    LAUNCH(TS_PRE, launch_cholesky(ctx->d.L_ic, n6, ctx->d.err, ctx->stream));
-    LAUNCH(TS_PRE, launch_chol_inverse(ctx->d.L_ic, ctx->d.Sinv, n6, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.chol_work, ctx->d.S_ic, sizeof(double) * n6 * n6, cudaMemcpyDeviceToDevice, ctx->stream));
+    LAUNCHN(TS_PRE, launch_cholesky(ctx->d.chol_work, ctx->d.L_ic, ctx->d.invd_ic, n6, ctx->d.err,
+                                    ctx->stream, &nl));
+    LAUNCH(TS_PRE, launch_chol_inverse(ctx->d.L_ic, ctx->d.invd_ic, ctx->d.Sinv, n6, ctx->stream));
     pba_status s = check_device_error(ctx);
     if (s != PBA_OK) return s;
     ctx->ic_ready = true;
@@ -700,13 +766,14 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     for (int k = 0; k < n_iters; ++k) {
         LAUNCH(TS_PASS, launch_fc_pass(L, true, k > 0, k > 0));
         LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 27, ctx->d.red_y, k, k - 1, true));
-        LAUNCH(TS_SCHUR, launch_schur_offdiag(L.pb, ctx->d.Hfd_fc, ctx->d.Hnn_fc, ctx->d.frame_pairs,
-                                              (int)ctx->frame_pairs.size(), ctx->d.Soff, ctx->stream));
+        LAUNCHN(TS_SCHUR, launch_schur_sparse(L.pb, ctx->d.Hfd_fc, ctx->d.Hnn_fc, schur_lists(ctx),
+                                              ctx->d.schur_part, ctx->d.Soff, ctx->stream, &nl));
         LAUNCH(TS_SCHUR, launch_assemble_S(F, ctx->d.red_y, 27, ctx->d.Soff, ctx->d.poses64,
                                            ctx->cfg.gauge_anchor_w, ctx->d.S_fc, ctx->d.active_fc, ctx->stream));
-        CK(cudaMemcpyAsync(ctx->d.L_fc, ctx->d.S_fc, sizeof(double) * n6 * n6, cudaMemcpyDeviceToDevice, ctx->stream));
-        LAUNCH(TS_SOLVE, launch_cholesky(ctx->d.L_fc, n6, ctx->d.err, ctx->stream));
-        LAUNCH(TS_SOLVE, launch_fc_solve_update(sa, ctx->d.L_fc, ctx->d.red_y, 27, 21, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d.chol_work, ctx->d.S_fc, sizeof(double) * n6 * n6, cudaMemcpyDeviceToDevice, ctx->stream));
+        LAUNCHN(TS_SOLVE, launch_cholesky(ctx->d.chol_work, ctx->d.L_fc, ctx->d.invd_fc, n6, ctx->d.err,
+                                          ctx->stream, &nl));
+        LAUNCH(TS_SOLVE, launch_fc_solve_update(sa, ctx->d.L_fc, ctx->d.invd_fc, ctx->d.red_y, 27, 21, ctx->stream));
     }
     LAUNCH(TS_EVAL, launch_fc_pass(L, false, n_iters > 0, n_iters > 0));
     LAUNCH(TS_EVAL, launch_frame_reduce(L, 0, 0, nullptr, n_iters, n_iters - 1, false));
