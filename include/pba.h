@@ -76,7 +76,14 @@ typedef struct {
     double conv_px;          /* convergence threshold of Sec. 4.1 in pixels; 0 -> 5e-3 */
     int n_bundles;           /* independent bundles in this context; must be 1 */
     void* cuda_stream;       /* cudaStream_t for all work; NULL = legacy default stream */
-    int use_graphs;          /* non-zero: replay iteration loops from captured CUDA graphs */
+    int use_graphs;          /* non-zero (and cuda_stream non-NULL): pba_precompute_ic,
+                                pba_iterate and pba_solve_fc submit their kernels by
+                                replaying a CUDA graph captured on the first call with
+                                the same iteration count and timing mask (one
+                                cudaGraphLaunch per call instead of one launch per
+                                kernel); the graphs hold workspace pointers and are
+                                dropped by pba_set_workspace. Ignored with a NULL
+                                stream (the legacy stream cannot be captured). */
     int max_stats_iters;     /* capacity of the per-iteration statistics; 0 -> 256 */
 } pba_config;
 
@@ -179,9 +186,11 @@ pba_status pba_num_residuals(pba_ctx* ctx, int bundle, int64_t* n);
  * + 1]: out[s] = accumulated device ms of slot s, out[PBA_TIMING_SLOTS] =
  * kernel launches since the reset (counted whether or not timing is on),
  * out[PBA_TIMING_SLOTS + 1 + s] = timed launches of slot s. Slots: 0 setup /
- * IC precompute, 1 residual pass, 2 per-frame reduction, 3 Schur complement +
- * assembly (FC), 4 factorisation / solve / pose update, 5 final evaluation. */
-#define PBA_TIMING_SLOTS 6
+ * IC precompute, 1 residual pass (the kernel that samples the images), 2
+ * per-frame reduction, 3 Schur complement + assembly (FC), 4 factorisation /
+ * solve / pose update, 5 final evaluation, 6 per-point kernels of the
+ * iteration (depth back-substitution, point sums and Schur right-hand side). */
+#define PBA_TIMING_SLOTS 7
 pba_status pba_enable_timing(pba_ctx* ctx, int mask);
 pba_status pba_last_timing(pba_ctx* ctx, double* out);
 

@@ -1,160 +1,260 @@
-// FP64 Cholesky factorisation of the reduced camera system and the
-// substitutions that use it (Sec. 3.5 step 3: Delta p = -H^-1 g through the
-// Schur complement S).
+// LDL^T factorisation of the reduced camera system (Sec. 3.5 step 3:
+// Delta p = -H^-1 g through the Schur complement S) in double-float
+// arithmetic, and the IC inverse S^-1 = L^-T D^-1 L^-1.
 //
-// GB300 runs FP64 at a small fraction of its FP32 rate, so a factorisation on
-// one SM is slow; the blocked right-looking algorithm spreads the trailing
-// updates over all SMs. The working copy A is consumed; the factor goes to a
-// separate matrix L. Per block column k (NB x NB blocks):
-//   panel:  every CTA factors the diagonal block A_kk in shared memory (a
-//           redundant 16x16 or 32x32 Cholesky), then CTA i > k solves
-//           L_ik = A_ik L_kk^-T; results go to the lower triangle of L and,
-//           transposed, to its upper triangle (so the backward substitution
-//           reads rows);
-//   update: one CTA per trailing tile (i, j), k < j <= i:
-//           A_ij -= L_ik L_jk^T.
-// Each launch reads one matrix and writes the other, so no CTA reads what
-// another CTA of the same launch writes; the launches on the stream order the
-// steps and no CTA waits on another. A non-positive pivot sets kErrNotPD and
-// is replaced by 1.
+// GB300 issues FP64 at 1/64 of the FP32 rate and its dependent FP64 latency
+// is ~14x the FP32 one; a factorisation of a 174 x 174 system is a chain of
+// 174 dependent pivots, so its FP64 form is latency-bound at tens of
+// microseconds and throughput-bound on any single SM. Here the matrix is held
+// as double-float pairs (about 48 bits; the system's condition number,
+// ~3e7 on the helix bundle, leaves ~1e-7 relative error in the solution,
+// well inside the 1e-4 step tolerance) and factored by one thread-block
+// cluster: blocked right-looking LDL^T with 32 x 32 blocks, where per block
+// column k
+//   every CTA factors the diagonal block A_kk in shared memory (redundantly,
+//     so no CTA waits for it) and, in the same steps, eliminates its share
+//     of the rows below (W_ik L_kk^T = A_ik, W = L D): one barrier per pivot,
+//     the reciprocal of the next pivot formed by the thread that updated it;
+//     it stores L_ik = W_ik D_k^-1;
+//   cluster barrier; the trailing tiles (i, j), k < j <= i, are dealt
+//     round-robin to the CTAs: A_ij -= (L_ik D_k) L_jk^T;
+//   cluster barrier.
+// The cluster barriers order the global-memory writes of one step before the
+// reads of the next (release / acquire at cluster scope); no CTA spins.
+// A non-positive pivot sets kErrNotPD and is replaced by 1.
+//
+// Augmented right-hand side: with aug = 1 the input has one extra row n
+// holding b^T; it is eliminated like any other row, so on exit row n of L
+// holds (D^-1 L^-1 b)^T and only the backward substitution remains.
+#include <cooperative_groups.h>
+
 #include "pba_chol.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pba {
 
-template <int NB>
-__global__ void __launch_bounds__(NB * NB)
-chol_panel_kernel(const double* A, double* L, double* inv_diag, int n, int k, int* err)
+namespace {
+
+constexpr int kNB = 32;
+constexpr int kCholThreads = 1024;  // one thread per element of a 32 x 32 block
+// cluster size: 16 CTAs (non-portable, allowed on sm_103a) when the device
+// can co-schedule them, else the portable 8; chosen once by ldl_setup()
+int g_chol_cluster = 8;
+
+struct CholSmem {
+    dfloat D[kNB][kNB + 1];   // diagonal block: W below the diagonal, pivots d_j on it
+    dfloat r[kNB];            // 1 / d_j
+    dfloat T0[kNB][kNB + 1];  // rows being eliminated / rows i of a trailing tile (L D)
+    dfloat T1[kNB][kNB + 1];  // rows j of a trailing tile (L)
+};
+
+// reciprocal of a pivot; a non-positive one (of a real row) is flagged and
+// replaced by 1
+__device__ __forceinline__ dfloat pivot_recip(dfloat& d, bool real, int* err)
 {
-    __shared__ double D[NB][NB + 1];
-    __shared__ double P[NB][NB + 1];
-    __shared__ double rd[NB];
-    const int tid = threadIdx.x, r = tid / NB, c = tid % NB;
-    const int k0 = k * NB, nk = min(NB, n - k0);
-    const int ib = k + blockIdx.x, i0 = ib * NB, ni = min(NB, n - i0);
-    // the lower triangle of A_kk is current (updates touch only c <= r there)
-    D[r][c] = (r < nk && c < nk) ? A[(size_t)(k0 + max(r, c)) * n + k0 + min(r, c)]
-                                 : (r == c ? 1.0 : 0.0);
-    if (blockIdx.x > 0) P[r][c] = (r < ni && c < nk) ? A[(size_t)(i0 + r) * n + k0 + c] : 0.0;
-    __syncthreads();
-    // unblocked right-looking factorisation of the diagonal block; one
-    // division per column (FP64 division is slow), the rest multiplies
-    for (int j = 0; j < NB; ++j) {
-        if (tid == 0) {
-            double v = D[j][j];
-            if (!(v > 0.0)) {
-                if (j < nk) atomicOr(err, kErrNotPD);
-                v = 1.0;
-            }
-            // 1/sqrt(v) by Newton-Raphson from an FP32 seed: y <- y (3 - v y^2) / 2
-            // (two steps take the ~23-bit seed past double precision); far
-            // fewer dependent FP64 operations than a square root and a division
-            double y = (double)rsqrtf((float)v);
-            y = y * fma(-0.5 * v, y * y, 1.5);
-            y = y * fma(-0.5 * v, y * y, 1.5);
-            D[j][j] = v * y;
-            rd[j] = y;
-        }
-        __syncthreads();
-        if (c == j && r > j) D[r][j] *= rd[j];
-        __syncthreads();
-        if (r > j && c > j && c <= r) D[r][c] = fma(-D[r][j], D[c][j], D[r][c]);
-        __syncthreads();
+    if (!(d.x > 0.0f)) {
+        if (real) atomicOr(err, kErrNotPD);
+        d = df_make(1.0f, 0.0f);
     }
-    if (blockIdx.x == 0) {
-        if (r < nk && c <= r) {
-            L[(size_t)(k0 + r) * n + k0 + c] = D[r][c];
-            L[(size_t)(k0 + c) * n + k0 + r] = D[r][c];
-        }
-        if (tid < nk) inv_diag[k0 + tid] = rd[tid];
-        return;
-    }
-    // X L_kk^T = P, right-looking over the columns: every (row, column)
-    // element in parallel
-    for (int j = 0; j < NB; ++j) {
-        if (c == j) P[r][j] *= rd[j];
-        __syncthreads();
-        if (c > j) P[r][c] = fma(-P[r][j], D[c][j], P[r][c]);
-        __syncthreads();
-    }
-    if (r < ni && c < nk) {
-        L[(size_t)(i0 + r) * n + k0 + c] = P[r][c];
-        L[(size_t)(k0 + c) * n + i0 + r] = P[r][c];
-    }
+    return df_recip(d);
 }
 
-template <int NB>
-__global__ void __launch_bounds__(NB * NB)
-chol_update_kernel(double* A, const double* L, int n, int k, int nblk)
+// One thread per element of a 32 x 32 block (1024 threads: warp = row,
+// lane = column), so each elimination step costs every thread at most one
+// double-float update and whole warps skip rows that are already done.
+__global__ void __launch_bounds__(kCholThreads)
+ldl_cluster_kernel(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv, int n, int aug,
+                   int* err)
 {
-    __shared__ double Li[NB][NB + 1];
-    __shared__ double Lj[NB][NB + 1];
-    // tile (i, j), k < j <= i < nblk, from the block index
-    int t = blockIdx.x, j = k + 1, cnt = nblk - j;
-    while (t >= cnt) {
-        t -= cnt;
-        ++j;
-        cnt = nblk - j;
-    }
-    const int i = j + t;
-    const int tid = threadIdx.x, r = tid / NB, c = tid % NB;
-    const int k0 = k * NB, nk = min(NB, n - k0);
-    const int i0 = i * NB, ni = min(NB, n - i0);
-    const int j0 = j * NB, nj = min(NB, n - j0);
-    Li[r][c] = (r < ni && c < nk) ? L[(size_t)(i0 + r) * n + k0 + c] : 0.0;
-    Lj[r][c] = (r < nj && c < nk) ? L[(size_t)(j0 + r) * n + k0 + c] : 0.0;
-    __syncthreads();
-    if (r < ni && c < nj && (i > j || c <= r)) {
-        double s = A[(size_t)(i0 + r) * n + j0 + c];
-#pragma unroll
-        for (int q = 0; q < NB; ++q) s = fma(-Li[r][q], Lj[c][q], s);
-        A[(size_t)(i0 + r) * n + j0 + c] = s;
-    }
-}
-
-template <int NB>
-static cudaError_t chol_blocked(double* A, double* L, double* inv_diag, int n, int* err,
-                               cudaStream_t st, int* launches)
-{
-    const int nblk = (n + NB - 1) / NB;
+    __shared__ CholSmem sm;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), C = (int)cl.num_blocks();
+    const int tid = threadIdx.x, wi = tid >> 5, lm = tid & 31;
+    const int nrow = n + aug;  // rows of A / L (the last one is b^T when aug)
+    const int nblk = (n + kNB - 1) / kNB;
+    const int nblk_r = (nrow + kNB - 1) / kNB;
     for (int k = 0; k < nblk; ++k) {
-        chol_panel_kernel<NB><<<nblk - k, NB * NB, 0, st>>>(A, L, inv_diag, n, k, err);
-        ++*launches;
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        const int rem = nblk - k - 1;
-        if (rem > 0) {
-            chol_update_kernel<NB><<<rem * (rem + 1) / 2, NB * NB, 0, st>>>(A, L, n, k, nblk);
-            ++*launches;
-            e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
+        const int k0 = k * kNB, nk = min(kNB, n - k0);
+        // rows below the block are split over the CTAs; this CTA eliminates
+        // its share (32 rows at a time) together with the diagonal block
+        const int below = nrow - k0 - nk;
+        const int per = (below + C - 1) / C;
+        const int a0 = k0 + nk + rank * per, a1 = min(nrow, a0 + per);
+        for (int r0 = a0; r0 < max(a1, a0 + 1); r0 += kNB) {
+            const int nr = max(0, min(kNB, a1 - r0));
+            const bool first = r0 == a0;
+            // ---- load: diagonal block (lower triangle current, identity
+            // outside nk) on the first chunk, and this chunk of rows below
+            if (first) {
+                dfloat v = df_make(wi == lm ? 1.0f : 0.0f, 0.0f);
+                if (wi < nk && lm <= wi) v = A[(size_t)(k0 + wi) * n + k0 + lm];
+                sm.D[wi][lm] = v;
+            }
+            sm.T0[wi][lm] = (wi < nr && lm < nk) ? A[(size_t)(r0 + wi) * n + k0 + lm] : df_make(0.0f, 0.0f);
+            __syncthreads();
+            if (first && tid == 0) sm.r[0] = pivot_recip(sm.D[0][0], nk > 0, err);
+            __syncthreads();
+            // ---- right-looking elimination, one barrier per pivot: the
+            // diagonal block (first chunk only; later chunks reuse its
+            // factor) and the rows below, A_im -= (A_ij / d_j) A_mj
+            for (int j = 0; j < kNB - 1; ++j) {
+                if (first && wi > j) {
+                    if (lm > j && lm <= wi) {
+                        const dfloat lij = df_mul(sm.D[wi][j], sm.r[j]);
+                        sm.D[wi][lm] = df_fnms(lij, sm.D[lm][j], sm.D[wi][lm]);
+                        // the owner of (j+1, j+1) has just updated it: next reciprocal
+                        if (wi == j + 1 && lm == j + 1)
+                            sm.r[j + 1] = pivot_recip(sm.D[j + 1][j + 1], j + 1 < nk, err);
+                    }
+                }
+                if (wi < nr && lm > j && lm < nk) {
+                    const dfloat wj = df_mul(sm.T0[wi][j], sm.r[j]);
+                    sm.T0[wi][lm] = df_fnms(wj, sm.D[lm][j], sm.T0[wi][lm]);
+                }
+                __syncthreads();
+            }
+            if (first && rank == 0) {
+                if (wi < nk && lm < nk && lm <= wi) {
+                    const dfloat l = lm < wi ? df_mul(sm.D[wi][lm], sm.r[lm]) : df_make(1.0f, 0.0f);
+                    L[(size_t)(k0 + wi) * n + k0 + lm] = l;
+                    L[(size_t)(k0 + lm) * n + k0 + wi] = l;
+                }
+                if (tid < nk) {
+                    dpiv[k0 + tid] = sm.D[tid][tid];
+                    rpiv[k0 + tid] = sm.r[tid];
+                }
+            }
+            // L_ik = W_ik D_k^-1 of this chunk
+            if (wi < nr && lm < nk) {
+                const dfloat l = df_mul(sm.T0[wi][lm], sm.r[lm]);
+                L[(size_t)(r0 + wi) * n + k0 + lm] = l;
+                if (r0 + wi < n) L[(size_t)(k0 + lm) * n + r0 + wi] = l;
+            }
+            __syncthreads();
         }
+        cl.sync();
+        // ---- trailing tiles (bi, bj), k < bj <= bi, round-robin over the CTAs
+        const int nt = nblk - k - 1;     // trailing block columns
+        const int ntr = nblk_r - k - 1;  // trailing block rows (one more with b^T in a new block)
+        const int tiles = nt * (nt + 1) / 2 + (ntr > nt ? nt : 0);
+        for (int tt = rank; tt < tiles; tt += C) {
+            int bi, bj;
+            if (tt < nt * (nt + 1) / 2) {
+                int t = tt;
+                bi = k + 1;
+                while (t > bi - k - 1) {
+                    t -= bi - k;
+                    ++bi;
+                }
+                bj = k + 1 + t;
+            } else {  // the block row that holds only b^T
+                bi = nblk;
+                bj = k + 1 + (tt - nt * (nt + 1) / 2);
+            }
+            const int i0 = bi * kNB, j0 = bj * kNB;
+            const int ni = min(kNB, nrow - i0), nj = min(kNB, n - j0);
+            {
+                dfloat a = df_make(0.0f, 0.0f), b = df_make(0.0f, 0.0f);
+                if (lm < nk) {
+                    if (wi < ni) a = df_mul(L[(size_t)(i0 + wi) * n + k0 + lm], sm.D[lm][lm]);
+                    if (wi < nj) b = L[(size_t)(j0 + wi) * n + k0 + lm];
+                }
+                sm.T0[wi][lm] = a;
+                sm.T1[wi][lm] = b;
+            }
+            __syncthreads();
+            if (wi < ni && lm < nj && (bi > bj || lm <= wi)) {
+                DfAcc acc;
+#pragma unroll 8
+                for (int j = 0; j < nk; ++j) acc.add_prod(sm.T0[wi][j], sm.T1[lm][j]);
+                dfloat* p = A + (size_t)(i0 + wi) * n + j0 + lm;
+                *p = df_sub(*p, acc.value());
+            }
+            __syncthreads();
+        }
+        cl.sync();
     }
+    // ---- inverses of the diagonal blocks (unit lower), block b by CTA
+    // b mod C: X = I, then X_i -= L_ij X_j for i > j, one barrier per column
+    for (int b = rank; b < nblk; b += C) {
+        const int b0 = b * kNB, nb = min(kNB, n - b0);
+        sm.D[wi][lm] = (wi < nb && lm < wi) ? L[(size_t)(b0 + wi) * n + b0 + lm] : df_make(0.0f, 0.0f);
+        sm.T0[wi][lm] = df_make(wi == lm ? 1.0f : 0.0f, 0.0f);
+        __syncthreads();
+        for (int j = 0; j < kNB - 1; ++j) {
+            if (wi > j && lm <= j) sm.T0[wi][lm] = df_fnms(sm.D[wi][j], sm.T0[j][lm], sm.T0[wi][lm]);
+            __syncthreads();
+        }
+        dfloat* out = Linv + (size_t)b * kLinvStride;
+        out[wi * kNB + lm] = sm.T0[wi][lm];
+        out[kNB * kNB + lm * kNB + wi] = sm.T0[wi][lm];
+        __syncthreads();
+    }
+}
+
+// S^-1 = L^-T D^-1 L^-1, one column (= row) per CTA, written as FP64; the
+// forward substitution of e_c starts at c's block.
+__global__ void __launch_bounds__(256)
+ldl_inverse_kernel(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, double* Sinv, int n)
+{
+    extern __shared__ dfloat xs[];
+    __shared__ dfloat t[kLdlBlock];
+    const int c = blockIdx.x;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = df_make(i == c ? 1.0f : 0.0f, 0.0f);
+    __syncthreads();
+    ldl_forward_smem(L, Linv, n, xs, t, c / kLdlBlock);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = df_mul(xs[i], rpiv[i]);
+    __syncthreads();
+    ldl_backward_smem(L, Linv, n, xs, t);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Sinv[(size_t)c * n + i] = df_to_double(xs[i]);
+}
+
+}  // namespace
+
+cudaError_t launch_ldl(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv, int n, int aug,
+                       int* err, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g_chol_cluster);
+    cfg.blockDim = dim3(kCholThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = g_chol_cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ldl_cluster_kernel, A, L, Linv, dpiv, rpiv, n, aug, err);
+}
+
+cudaError_t ldl_setup()
+{
+    cudaError_t e = cudaFuncSetAttribute(ldl_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(kCholThreads);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&nclusters, ldl_cluster_kernel, &cfg);
+    g_chol_cluster = (e == cudaSuccess && nclusters > 0) ? 16 : 8;
+    cudaGetLastError();  // a refused query leaves the portable size
     return cudaSuccess;
 }
 
-cudaError_t launch_cholesky(double* A, double* L, double* inv_diag, int n, int* err,
-                            cudaStream_t st, int* launches)
+cudaError_t launch_ldl_inverse(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, double* Sinv,
+                               int n, cudaStream_t st)
 {
-    return n <= 256 ? chol_blocked<16>(A, L, inv_diag, n, err, st, launches)
-                    : chol_blocked<32>(A, L, inv_diag, n, err, st, launches);
-}
-
-// S^-1 = L^-T L^-1, one column (= row, S^-1 is symmetric) per CTA.
-__global__ void __launch_bounds__(256)
-chol_inverse_kernel(const double* L, const double* inv_diag, double* Sinv, int n)
-{
-    extern __shared__ double x[];
-    const int c = blockIdx.x;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = (i == c) ? 1.0 : 0.0;
-    __syncthreads();
-    chol_solve_smem(L, inv_diag, n, x);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) Sinv[(size_t)c * n + i] = x[i];
-}
-
-cudaError_t launch_chol_inverse(const double* L, const double* inv_diag, double* Sinv, int n,
-                                cudaStream_t st)
-{
-    chol_inverse_kernel<<<n, 256, sizeof(double) * n, st>>>(L, inv_diag, Sinv, n);
+    ldl_inverse_kernel<<<n, 256, sizeof(dfloat) * n, st>>>(L, Linv, rpiv, Sinv, n);
     return cudaGetLastError();
 }
 

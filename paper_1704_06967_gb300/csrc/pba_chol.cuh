@@ -1,63 +1,82 @@
-// Substitutions with the FP64 Cholesky factor of the reduced camera system
-// (Sec. 3.5 step 3). L holds the factor in its lower triangle and L^T in its
-// upper triangle; inv_diag holds 1 / L_ii (FP64 division is slow on GB300, so
-// the substitutions only multiply).
+// Substitutions with the LDL^T factor of the reduced camera system (Sec. 3.5
+// step 3), in double-float arithmetic. L (unit lower, row-major n x n of
+// dfloat) holds the factor in its lower triangle and L^T in its upper
+// triangle, so both substitutions read rows; Linv holds the inverses of its
+// 32 x 32 diagonal blocks (block b at Linv + b * 2048: the inverse, then its
+// transpose), so a block's triangular solve is a matrix-vector product
+// instead of 32 dependent steps.
 #pragma once
 
+#include "pba_df.cuh"
 #include "pba_kernels.cuh"
 
 namespace pba {
 
-// L L^T x = b with x in shared memory (in: b, out: x), one CTA. Blocks of 32
-// rows: the off-diagonal part is a warp-per-row GEMV along rows of the lower
-// (forward) or upper = L^T (backward) triangle; the 32x32 diagonal triangle
-// is solved by one warp with shuffles.
-__device__ inline void chol_solve_smem(const double* L, const double* inv_diag, int n, double* x)
+constexpr int kLdlBlock = 32;
+constexpr int kLinvStride = 2 * kLdlBlock * kLdlBlock;  // dfloats per diagonal block in Linv
+
+// y[r] = sum_{c in [c0, c1)} M[r * ldm + c] x[c] for the rows r < nr of a
+// block (warp w takes rows w, w + nw, ...; lanes take columns; four rows at
+// a time, their sums interleaved), written as out[r] = base[r] - y[r]
+// (sub = true) or out[r] = y[r].
+__device__ __forceinline__ void block_gemv(const dfloat* M, int ldm, int nr, int c0, int c1,
+                                           const dfloat* x, dfloat* out, bool sub)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int b0 = 0; b0 < n; b0 += 32) {
-        const int nb = min(32, n - b0);
-        for (int r = warp; r < nb; r += nw) {
-            const double* Lr = L + (size_t)(b0 + r) * n;
-            double s = 0.0;
-            for (int j = lane; j < b0; j += 32) s = fma(Lr[j], x[j], s);
-            s = warp_sum1d(s);
-            if (lane == 0) x[b0 + r] -= s;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            double xi = lane < nb ? x[b0 + lane] : 0.0;
-            const double ri = lane < nb ? inv_diag[b0 + lane] : 0.0;
-            for (int c = 0; c < nb; ++c) {
-                if (lane == c) xi *= ri;
-                const double xc = __shfl_sync(0xffffffffu, xi, c);
-                if (lane > c && lane < nb) xi = fma(-L[(size_t)(b0 + lane) * n + b0 + c], xc, xi);
+    for (int r = warp; r < nr; r += 4 * nw) {
+        DfAcc acc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int rr = r + u * nw;
+            if (rr < nr) {
+                const dfloat* Mr = M + (size_t)rr * ldm;
+                for (int c = c0 + lane; c < c1; c += 32) acc[u].add_prod(Mr[c], x[c]);
             }
-            if (lane < nb) x[b0 + lane] = xi;
         }
+        dfloat s[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] = df_warp_sum(acc[u].value());
+        if (lane < 4) {
+            const int rr = r + lane * nw;
+            dfloat v = s[0];
+#pragma unroll
+            for (int u = 1; u < 4; ++u) v = lane == u ? s[u] : v;
+            if (rr < nr) out[rr] = sub ? df_sub(out[rr], v) : v;
+        }
+    }
+}
+
+// x <- L^-1 x (forward substitution, unit diagonal), x in shared memory,
+// one CTA; blocks before block b_first are known to be zero on entry.
+// t: 32 dfloats of shared scratch.
+__device__ inline void ldl_forward_smem(const dfloat* L, const dfloat* Linv, int n, dfloat* x,
+                                        dfloat* t, int b_first)
+{
+    for (int b0 = b_first * kLdlBlock; b0 < n; b0 += kLdlBlock) {
+        const int nb = min(kLdlBlock, n - b0);
+        const dfloat* Li = Linv + (size_t)(b0 / kLdlBlock) * kLinvStride;
+        if (b0 > b_first * kLdlBlock)
+            block_gemv(L + (size_t)b0 * n, n, nb, b_first * kLdlBlock, b0, x, x + b0, true);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) t[i] = x[b0 + i];
+        __syncthreads();
+        block_gemv(Li, kLdlBlock, nb, 0, nb, t, x + b0, false);
         __syncthreads();
     }
-    for (int b0 = ((n - 1) / 32) * 32; b0 >= 0; b0 -= 32) {
-        const int nb = min(32, n - b0);
-        for (int r = warp; r < nb; r += nw) {
-            const double* Ur = L + (size_t)(b0 + r) * n;  // row of L^T (upper triangle)
-            double s = 0.0;
-            for (int j = b0 + nb + lane; j < n; j += 32) s = fma(Ur[j], x[j], s);
-            s = warp_sum1d(s);
-            if (lane == 0) x[b0 + r] -= s;
-        }
+}
+
+// x <- L^-T x (backward substitution), same layout.
+__device__ inline void ldl_backward_smem(const dfloat* L, const dfloat* Linv, int n, dfloat* x,
+                                         dfloat* t)
+{
+    for (int b0 = ((n - 1) / kLdlBlock) * kLdlBlock; b0 >= 0; b0 -= kLdlBlock) {
+        const int nb = min(kLdlBlock, n - b0);
+        const dfloat* LiT = Linv + (size_t)(b0 / kLdlBlock) * kLinvStride + kLdlBlock * kLdlBlock;
+        if (b0 + nb < n) block_gemv(L + (size_t)b0 * n, n, nb, b0 + nb, n, x, x + b0, true);
         __syncthreads();
-        if (warp == 0) {
-            double xi = lane < nb ? x[b0 + lane] : 0.0;
-            const double ri = lane < nb ? inv_diag[b0 + lane] : 0.0;
-            for (int c = nb - 1; c >= 0; --c) {
-                if (lane == c) xi *= ri;
-                const double xc = __shfl_sync(0xffffffffu, xi, c);
-                // L^T(lane, c) = L(c, lane), read from the lower triangle
-                if (lane < c) xi = fma(-L[(size_t)(b0 + c) * n + b0 + lane], xc, xi);
-            }
-            if (lane < nb) x[b0 + lane] = xi;
-        }
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) t[i] = x[b0 + i];
+        __syncthreads();
+        block_gemv(LiT, kLdlBlock, nb, 0, nb, t, x + b0, false);
         __syncthreads();
     }
 }

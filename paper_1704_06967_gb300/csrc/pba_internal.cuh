@@ -28,7 +28,7 @@ namespace pba {
 constexpr int kTile = 32;             // points per tile (= lanes of a warp)
 constexpr int kPassWarps = 4;         // warps per CTA of the pass kernels
 constexpr int kFrameConst = 64;       // floats of FP32 constants per frame
-constexpr int kEntryPartial = 32;     // floats of partial sums per entry
+constexpr int kEntryPartial = 40;     // floats of partial sums per entry (FC: 21 H_ff, 6 g_f, 6 corrections)
 constexpr int kStats = 8;             // doubles per statistics slot
 
 // device error word values (bit flags)

@@ -1,0 +1,646 @@
+// IC iteration kernels (Sec. 3.5 steps 1-3 with the J, W_0 and H fixed by
+// the precompute at p_0). An iteration is three launches, none of which
+// waits on another part of the grid:
+//   depth_update_kernel  one CTA per tile: back-substitution of the previous
+//                        step's depth update (Sec. 3.5 step 3, point block)
+//                        and the depth rule (IC: Sec. 3.6; FC: d <- d + Dd);
+//   ic_residual_kernel   one warp per (tile, frame) entry: warp, bilinear
+//                        sample, residual, Huber weight, and the entry's
+//                        share of g_f = sum J_theta^T w r and of g_d;
+//   ic_point_kernel      one CTA per tile: g_d per point (entries added in
+//                        tile order), the Schur right-hand-side correction
+//                        sum_n H_fd g_d / H_dd per entry, and the tile
+//                        statistics.
+// A tile has about ten entries, so a CTA per tile (earlier design) left its
+// warps waiting at barriers between the phases; a warp per entry gives the
+// scheduler ~6k independent warps whose image taps are all in flight at once.
+// Every sum has a fixed order: results are deterministic run to run.
+#include "pba_kernels.cuh"
+
+namespace pba {
+
+namespace {
+
+constexpr int kResWarps = 8;    // warps (entries) per CTA of the residual kernels
+constexpr int kTileWarps = 4;   // warps per CTA of the per-tile kernels
+
+__device__ __forceinline__ int rank_of(unsigned mask, int lane)
+{
+    return __popc(mask & ((1u << lane) - 1u));
+}
+
+// (s, c) += h (t.x + t.y): h t.x split exactly by TwoProduct (Ogita, Rump
+// and Oishi 2005), the sum carried by Knuth's two-sum; t = (hi, lo) is an
+// FP64 value as an unevaluated pair of floats.
+__device__ __forceinline__ void dot_pair_add(float& s, float& c, float h, float2 t)
+{
+    const float p = h * t.x;
+    const float e = fmaf(h, t.x, -p);
+    const float tail = fmaf(h, t.y, e);
+    const float u = s + p;
+    const float bb = u - s;
+    const float err = (s - (u - bb)) + (p - bb);
+    s = u;
+    c += err + tail;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Depth back-substitution: Dd_n = -(g_n + sum_f H_fd^T Dtheta_f) / H_dd.
+// g_n + sum H_fd^T Dtheta nearly cancels for well-determined points, so the
+// dot products are carried as unevaluated FP32 pairs (about 48 bits) and the
+// quotient and the depth rule are FP64 (IC: 1/H_dd and 1/d_0 come from the
+// precompute, so no FP64 division is left). One CTA per tile; warp w takes
+// the tile's entries w, w + 4, ... (their records loaded one per lane, so no
+// load waits on another), then warp 0 adds the four partial sums in order.
+// Writes the FP32 depth the residual kernels use (dcur), the one before this
+// update (dprev) and the tile's sum of Dd^2. apply = 0 only refreshes
+// dcur/dprev from the FP64 depths.
+// ---------------------------------------------------------------------------
+template <bool kIcRule>
+__global__ void __launch_bounds__(kTileWarps * 32)
+depth_update_kernel(DevProblem pb, DepthState ds, const float2* __restrict__ dth2,
+                    const double* __restrict__ inv_hnn, const double* __restrict__ inv_d0,
+                    float* __restrict__ dcur, float* __restrict__ dprev, float* __restrict__ ddsq_t,
+                    int apply)
+{
+    __shared__ float2 red[kTileWarps][32];
+    const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = t * kTile + lane;
+    // warp 0's per-point operands, fetched before the entry loop so their
+    // latency overlaps it
+    double d = 0.0, d0 = 0.0, ih = 0.0, id0 = 0.0;
+    float gn = 0.0f, hnn = 0.0f;
+    bool valid = false;
+    if (warp == 0) {
+        d = ds.d64[n];
+        if (apply) {
+            gn = ds.gn[n];
+            hnn = ds.Hnn[n];
+            valid = pb.valid_pt[n];
+            if (kIcRule) {
+                d0 = ds.d0_64[n];
+                ih = inv_hnn[n];
+                id0 = inv_d0[n];
+            }
+        }
+    }
+    if (apply) {
+        const int e0 = pb.tile_entry[t], ne = pb.tile_entry[t + 1] - e0;
+        float s = 0.0f, c = 0.0f;
+        for (int b = 0; b < ne; b += 32) {
+            Entry mine = {0, 0u, 0, 0};
+            if (b + lane < ne) mine = pb.entries[e0 + b + lane];
+            const int cnt = min(32, ne - b);
+#pragma unroll 2
+            for (int i = warp; i < cnt; i += kTileWarps) {
+                const int f = __shfl_sync(0xffffffffu, mine.f, i);
+                const unsigned mask = __shfl_sync(0xffffffffu, mine.mask, i);
+                const int po = __shfl_sync(0xffffffffu, mine.pair_off, i);
+                const bool vis = (mask >> lane) & 1u;
+                const int nvis = __popc(mask);
+                const float* h = ds.Hfd + (size_t)po * 6 + (vis ? rank_of(mask, lane) : 0);
+                const float2* th = dth2 + 6 * f;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) dot_pair_add(s, c, vis ? h[k * nvis] : 0.0f, th[k]);
+            }
+        }
+        red[warp][lane] = make_float2(s, c);
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    const float dold = (float)d;
+    float ddsq = 0.0f;
+    if (apply) {
+        float s = red[0][lane].x, c = red[0][lane].y;
+        for (int w = 1; w < kTileWarps; ++w) {
+            const float2 v = red[w][lane];
+            const float u = s + v.x, bb = u - s;
+            c += v.y + ((s - (u - bb)) + (v.x - bb));
+            s = u;
+        }
+        double dd = 0.0;
+        if (valid && hnn > 0.0f) {
+            const double num = (double)gn + ((double)s + (double)c);
+            dd = kIcRule ? -num * ih : -num / (double)hnn;
+            const double dn = kIcRule ? d * ((d0 - dd) * id0) : d + dd;
+            if (isfinite(dn)) {
+                d = dn;
+                ds.d64[n] = d;
+            } else {
+                atomicOr(ds.err, kErrNonFinite);
+            }
+        }
+        ds.dd_last[n] = dd;
+        ddsq = (float)(dd * dd);
+    }
+    dcur[n] = (float)d;
+    dprev[n] = dold;
+    ddsq = warp_sum1(ddsq);
+    if (lane == 0) ddsq_t[t] = ddsq;
+}
+
+// ---------------------------------------------------------------------------
+// IC residuals of one entry (Sec. 3.5 steps 1-2). Lane l is point 32 t + l of
+// the entry's tile; lanes whose point the frame does not see stay idle.
+// Phase 1 projects the P pattern pixels (q = R x~_c + d t + delta_j) and
+// forms their bilinear footprints; a footprint outside [1, W-2] x [1, H-2]
+// (or behind the camera) marks the residual invalid and is clamped into the
+// image, so phase 2 can issue every tap of every pattern pixel at once with
+// no branch in between. Phase 3 forms r = I_0 - I(W(x)), the Huber terms and
+// w r (r, or k sign r: exact, no division); phase 4 streams the stored rows
+// J and adds J_theta w r into the frame sum and J_d w r into the point's.
+// ---------------------------------------------------------------------------
+template <int PMAX, bool kAccum, int DT>
+__global__ void __launch_bounds__(kResWarps * 32, PMAX <= 8 ? 4 : 2)
+ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float* __restrict__ fprev,
+                   const float* __restrict__ dcur, const float* __restrict__ dprev,
+                   const float4* __restrict__ J4, float* __restrict__ ent_part,
+                   float* __restrict__ gpart, float4* __restrict__ estats, int have_prev)
+{
+    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.x * kResWarps + (threadIdx.x >> 5);
+    if (e >= pb.E) return;
+    const Entry en = pb.entries[e];
+    const int P = pb.P;
+    const float k = pb.huber_k;
+    float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // g_f (6), energy, r^2, count
+    float gp = 0.0f, disp = 0.0f;
+    if ((en.mask >> lane) & 1u) {
+        const int n = en.tile * kTile + lane;
+        const float* c = fconst + (size_t)en.f * kFrameConst;
+        const float d = dcur[n];
+        const float2 xc = pb.xn[n];
+        float I0[PMAX];
+#pragma unroll
+        for (int j = 0; j < PMAX; ++j)
+            if (j < P) I0[j] = pb.I0p[((size_t)en.tile * P + j) * kTile + lane];
+        const float qcx = fmaf(c[0], xc.x, fmaf(c[1], xc.y, fmaf(d, c[9], c[2])));
+        const float qcy = fmaf(c[3], xc.x, fmaf(c[4], xc.y, fmaf(d, c[10], c[5])));
+        const float qcz = fmaf(c[6], xc.x, fmaf(c[7], xc.y, fmaf(d, c[11], c[8])));
+        const float umax = (float)(pb.W - 3), vmax = (float)(pb.H - 3);
+        const unsigned row0 = (unsigned)en.f * (unsigned)pb.H, pitch = (unsigned)pb.pitch;
+        unsigned base[PMAX], ok = 0;
+        float wa[PMAX], wb[PMAX];
+#pragma unroll
+        for (int j = 0; j < PMAX; ++j) {
+            if (j < P) {
+                const float qx = qcx + c[12 + 3 * j], qy = qcy + c[13 + 3 * j], qz = qcz + c[14 + 3 * j];
+                const float iz = 1.0f / qz;
+                const float u = fmaf(pb.fx * qx, iz, pb.cx), v = fmaf(pb.fy * qy, iz, pb.cy);
+                const float fu = floorf(u), fv = floorf(v);
+                // (a NaN coordinate fails the test and clamps to 1)
+                if (qz > 0.0f && fu >= 1.0f && fu <= umax && fv >= 1.0f && fv <= vmax) ok |= 1u << j;
+                const float xu = fminf(fmaxf(fu, 1.0f), umax), yv = fminf(fmaxf(fv, 1.0f), vmax);
+                wa[j] = u - fu;
+                wb[j] = v - fv;
+                base[j] = (row0 + (unsigned)(int)yv) * pitch + (unsigned)(int)xu;
+            }
+        }
+        float val[PMAX];
+#pragma unroll
+        for (int j = 0; j < PMAX; ++j) {
+            if (j < P) {
+                const unsigned b = base[j];
+                const float i00 = load_px_t<DT>(pb.img, b), i10 = load_px_t<DT>(pb.img, b + 1);
+                const float i01 = load_px_t<DT>(pb.img, b + pitch), i11 = load_px_t<DT>(pb.img, b + pitch + 1);
+                const float top = fmaf(wa[j], i10 - i00, i00);
+                const float bot = fmaf(wa[j], i11 - i01, i01);
+                val[j] = fmaf(wb[j], bot - top, top);
+            }
+        }
+        float wr[PMAX];
+#pragma unroll
+        for (int j = 0; j < PMAX; ++j) {
+            wr[j] = 0.0f;
+            if (j < P && ((ok >> j) & 1u)) {
+                const float r = I0[j] - val[j];
+                acc[6] += huber_rho(r, k);
+                acc[7] = fmaf(r, r, acc[7]);
+                acc[8] += 1.0f;
+                wr[j] = fabsf(r) <= k ? r : copysignf(k, r);
+            }
+        }
+        if (kAccum) {
+            const int NC = (7 * P + 3) / 4, nvis = __popc(en.mask);
+            const float4* src = J4 + (size_t)en.pair_off * NC + rank_of(en.mask, lane);
+            // rows of four pattern pixels (seven float4 chunks) at a time,
+            // loaded after the taps are consumed (register pressure)
+#pragma unroll
+            for (int g = 0; g < PMAX / 4; ++g) {
+                if (4 * g < P) {
+                    asm volatile("" ::: "memory");
+                    float Jr[28];
+#pragma unroll
+                    for (int q = 0; q < 7; ++q) {
+                        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        if (7 * g + q < NC) v = __ldg(src + (size_t)(7 * g + q) * nvis);
+                        Jr[4 * q] = v.x;
+                        Jr[4 * q + 1] = v.y;
+                        Jr[4 * q + 2] = v.z;
+                        Jr[4 * q + 3] = v.w;
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int j = 4 * g + jj;
+                        if (j < P) {
+#pragma unroll
+                            for (int a = 0; a < 6; ++a) acc[a] = fmaf(Jr[7 * jj + a], wr[j], acc[a]);
+                            gp = fmaf(Jr[7 * jj + 6], wr[j], gp);
+                        }
+                    }
+                }
+            }
+        }
+        if (have_prev) {
+            // pattern-centre displacement since the previous parameters
+            // (convergence rule of Sec. 4.1)
+            const float* cp = fprev + 12 * en.f;
+            const float dp = dprev[n];
+            const float px = fmaf(cp[0], xc.x, fmaf(cp[1], xc.y, fmaf(dp, cp[9], cp[2])));
+            const float py = fmaf(cp[3], xc.x, fmaf(cp[4], xc.y, fmaf(dp, cp[10], cp[5])));
+            const float pz = fmaf(cp[6], xc.x, fmaf(cp[7], xc.y, fmaf(dp, cp[11], cp[8])));
+            const float du = pb.fx * (qcx / qcz - px / pz), dv = pb.fy * (qcy / qcz - py / pz);
+            disp = sqrtf(du * du + dv * dv);
+        }
+    }
+    if (kAccum) {
+        gpart[(size_t)e * kTile + lane] = gp;
+        warp_sum<9>(acc);
+    } else {
+        float st[3] = {acc[6], acc[7], acc[8]};
+        warp_sum<3>(st);
+        acc[6] = st[0];
+        acc[7] = st[1];
+        acc[8] = st[2];
+    }
+    disp = warp_max1(disp);
+    if (lane == 0) {
+        if (kAccum) {
+            float* o = ent_part + (size_t)pb.entry_slot[e] * kEntryPartial;
+#pragma unroll
+            for (int a = 0; a < 6; ++a) o[a] = acc[a];
+        }
+        estats[e] = make_float4(acc[6], acc[7], acc[8], disp);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FC linearisation of one entry: per residual the target-image gradient
+// (bilinear of the central-difference gradient images, same footprint as the
+// intensity) and the row
+//   c3 = -(1/q_z) (g_u f_x, g_v f_y, -(g_u f_x q_x + g_v f_y q_y)/q_z),
+//   J = [d c3, q x c3, c3 . t]      ([upsilon, omega, d] of T <- exp(xi) T),
+// with the current Huber weight w: the entry's H_ff (21 upper entries) and
+// g_f = J_theta^T w r, H_fd of each pair, and per lane J_d^T w r and
+// J_d^T w J_d. Pattern pixels go in groups of kFcGroup, each group's twelve
+// taps per pixel issued together (register pressure bounds the group).
+// ---------------------------------------------------------------------------
+constexpr int kFcGroup = 2;
+
+template <int PMAX, bool kAccum, int DT>
+__global__ void __launch_bounds__(kResWarps * 32, 2)
+fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float* __restrict__ fprev,
+                   const float* __restrict__ dcur, const float* __restrict__ dprev,
+                   float* __restrict__ Hfd_out, float* __restrict__ ent_part,
+                   float* __restrict__ gpart, float4* __restrict__ estats, int have_prev)
+{
+    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.x * kResWarps + (threadIdx.x >> 5);
+    if (e >= pb.E) return;
+    const Entry en = pb.entries[e];
+    const int P = pb.P;
+    const float k = pb.huber_k;
+    float acc[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) acc[q] = 0.0f;
+    float hfd[6] = {0, 0, 0, 0, 0, 0};
+    float st[3] = {0, 0, 0};
+    float gp = 0.0f, hnn = 0.0f, disp = 0.0f;
+    if ((en.mask >> lane) & 1u) {
+        const int n = en.tile * kTile + lane;
+        const float* c = fconst + (size_t)en.f * kFrameConst;
+        const float d = dcur[n];
+        const float2 xc = pb.xn[n];
+        const float qcx = fmaf(c[0], xc.x, fmaf(c[1], xc.y, fmaf(d, c[9], c[2])));
+        const float qcy = fmaf(c[3], xc.x, fmaf(c[4], xc.y, fmaf(d, c[10], c[5])));
+        const float qcz = fmaf(c[6], xc.x, fmaf(c[7], xc.y, fmaf(d, c[11], c[8])));
+        const float t0 = c[9], t1 = c[10], t2 = c[11];
+        const float umax = (float)(pb.W - 3), vmax = (float)(pb.H - 3);
+        const unsigned row0 = (unsigned)en.f * (unsigned)pb.H, pitch = (unsigned)pb.pitch;
+        const unsigned W = (unsigned)pb.W;
+#pragma unroll
+        for (int g = 0; g < PMAX; g += kFcGroup) {
+            if (g < P) {
+                asm volatile("" ::: "memory");
+                unsigned ib[kFcGroup], gb[kFcGroup], ok = 0;
+                float wa[kFcGroup], wb[kFcGroup], qx[kFcGroup], qy[kFcGroup], qz[kFcGroup],
+                    iz[kFcGroup], I0[kFcGroup];
+#pragma unroll
+                for (int jj = 0; jj < kFcGroup; ++jj) {
+                    const int j = g + jj;
+                    if (j < P) {
+                        I0[jj] = pb.I0p[((size_t)en.tile * P + j) * kTile + lane];
+                        qx[jj] = qcx + c[12 + 3 * j];
+                        qy[jj] = qcy + c[13 + 3 * j];
+                        qz[jj] = qcz + c[14 + 3 * j];
+                        iz[jj] = 1.0f / qz[jj];
+                        const float u = fmaf(pb.fx * qx[jj], iz[jj], pb.cx);
+                        const float v = fmaf(pb.fy * qy[jj], iz[jj], pb.cy);
+                        const float fu = floorf(u), fv = floorf(v);
+                        if (qz[jj] > 0.0f && fu >= 1.0f && fu <= umax && fv >= 1.0f && fv <= vmax)
+                            ok |= 1u << jj;
+                        const unsigned x = (unsigned)(int)fminf(fmaxf(fu, 1.0f), umax);
+                        const unsigned y = (unsigned)(int)fminf(fmaxf(fv, 1.0f), vmax);
+                        wa[jj] = u - fu;
+                        wb[jj] = v - fv;
+                        ib[jj] = (row0 + y) * pitch + x;
+                        gb[jj] = (row0 + y) * W + x;
+                    }
+                }
+                float val[kFcGroup], gxv[kFcGroup], gyv[kFcGroup];
+#pragma unroll
+                for (int jj = 0; jj < kFcGroup; ++jj) {
+                    if (g + jj < P) {
+                        const unsigned b = ib[jj];
+                        const float i00 = load_px_t<DT>(pb.img, b), i10 = load_px_t<DT>(pb.img, b + 1);
+                        const float i01 = load_px_t<DT>(pb.img, b + pitch);
+                        const float i11 = load_px_t<DT>(pb.img, b + pitch + 1);
+                        const float top = fmaf(wa[jj], i10 - i00, i00);
+                        const float bot = fmaf(wa[jj], i11 - i01, i01);
+                        val[jj] = fmaf(wb[jj], bot - top, top);
+                        if (kAccum) {
+                            const float* GX = pb.gx + gb[jj];
+                            const float* GY = pb.gy + gb[jj];
+                            const float gxt = fmaf(wa[jj], __ldg(GX + 1) - __ldg(GX), __ldg(GX));
+                            const float gxb = fmaf(wa[jj], __ldg(GX + W + 1) - __ldg(GX + W), __ldg(GX + W));
+                            const float gyt = fmaf(wa[jj], __ldg(GY + 1) - __ldg(GY), __ldg(GY));
+                            const float gyb = fmaf(wa[jj], __ldg(GY + W + 1) - __ldg(GY + W), __ldg(GY + W));
+                            gxv[jj] = fmaf(wb[jj], gxb - gxt, gxt) * pb.fx;
+                            gyv[jj] = fmaf(wb[jj], gyb - gyt, gyt) * pb.fy;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int jj = 0; jj < kFcGroup; ++jj) {
+                    if (g + jj < P && ((ok >> jj) & 1u)) {
+                        const float r = I0[jj] - val[jj];
+                        st[0] += huber_rho(r, k);
+                        st[1] = fmaf(r, r, st[1]);
+                        st[2] += 1.0f;
+                        if (kAccum) {
+                            const float c0 = -gxv[jj] * iz[jj], c1 = -gyv[jj] * iz[jj];
+                            const float c2 = (gxv[jj] * qx[jj] + gyv[jj] * qy[jj]) * iz[jj] * iz[jj];
+                            float J[7];
+                            J[0] = d * c0;
+                            J[1] = d * c1;
+                            J[2] = d * c2;
+                            J[3] = qy[jj] * c2 - qz[jj] * c1;
+                            J[4] = qz[jj] * c0 - qx[jj] * c2;
+                            J[5] = qx[jj] * c1 - qy[jj] * c0;
+                            J[6] = fmaf(c0, t0, fmaf(c1, t1, c2 * t2));
+                            const float w = huber_w(r, k);
+                            const float wr = w * r;
+                            int q = 0;
+#pragma unroll
+                            for (int a = 0; a < 6; ++a) {
+                                const float wja = w * J[a];
+#pragma unroll
+                                for (int b = a; b < 6; ++b) {
+                                    acc[q] = fmaf(wja, J[b], acc[q]);
+                                    ++q;
+                                }
+                                acc[21 + a] = fmaf(J[a], wr, acc[21 + a]);
+                                hfd[a] = fmaf(wja, J[6], hfd[a]);
+                            }
+                            hnn = fmaf(w * J[6], J[6], hnn);
+                            gp = fmaf(J[6], wr, gp);
+                        }
+                    }
+                }
+            }
+        }
+        if (kAccum) {
+            const int nvis = __popc(en.mask);
+            float* hd = Hfd_out + (size_t)en.pair_off * 6 + rank_of(en.mask, lane);
+#pragma unroll
+            for (int a = 0; a < 6; ++a) hd[a * nvis] = hfd[a];
+        }
+        if (have_prev) {
+            const float* cp = fprev + 12 * en.f;
+            const float dp = dprev[n];
+            const float px = fmaf(cp[0], xc.x, fmaf(cp[1], xc.y, fmaf(dp, cp[9], cp[2])));
+            const float py = fmaf(cp[3], xc.x, fmaf(cp[4], xc.y, fmaf(dp, cp[10], cp[5])));
+            const float pz = fmaf(cp[6], xc.x, fmaf(cp[7], xc.y, fmaf(dp, cp[11], cp[8])));
+            const float du = pb.fx * (qcx / qcz - px / pz), dv = pb.fy * (qcy / qcz - py / pz);
+            disp = sqrtf(du * du + dv * dv);
+        }
+    }
+    if (kAccum) {
+        gpart[(size_t)e * 2 * kTile + lane] = gp;
+        gpart[(size_t)e * 2 * kTile + kTile + lane] = hnn;
+        warp_sum<27>(acc);
+    }
+    warp_sum<3>(st);
+    disp = warp_max1(disp);
+    if (lane == 0) {
+        if (kAccum) {
+            float* o = ent_part + (size_t)pb.entry_slot[e] * kEntryPartial;
+#pragma unroll
+            for (int q = 0; q < 27; ++q) o[q] = acc[q];
+        }
+        estats[e] = make_float4(st[0], st[1], st[2], disp);
+    }
+}
+
+// Statistics of tile t from its entries' (energy, r^2, count, max
+// displacement) and the tile's sum of Dd^2; lanes take entries, then a
+// butterfly (fixed order).
+__device__ __forceinline__ void tile_stats_from_entries(const DevProblem& pb, const float4* estats,
+                                                        const float* ddsq_t, TileStats* out, int t,
+                                                        int e0, int e1, int lane)
+{
+    float s[3] = {0, 0, 0}, m = 0.0f;
+    for (int e = e0 + lane; e < e1; e += 32) {
+        const float4 v = estats[e];
+        s[0] += v.x;
+        s[1] += v.y;
+        s[2] += v.z;
+        m = fmaxf(m, v.w);
+    }
+    warp_sum<3>(s);
+    m = warp_max1(m);
+    if (lane == 0) out[t] = TileStats{s[0], s[1], s[2], m, ddsq_t[t], 0, 0, 0};
+}
+
+// ---------------------------------------------------------------------------
+// Per tile: g_n = sum over the tile's entries of J_d^T w r (fixed entry
+// order; FC also sums H_dd = J_d^T w J_d the same way), then the Schur
+// right-hand-side correction c_e = sum_n H_fd(n, f) g_n / H_dd(n) of every
+// entry e, written beside the entry's g_f partial at coff (the frame
+// reduction forms y_f = sum_e (g_f,e - c_e), Sec. 3.5 step 3). Every warp
+// forms g_n itself (a few independent loads) and takes entries round-robin,
+// their records loaded one per lane, so no warp waits on another.
+// kFc: per-lane partials are E x 64 (g then H_dd) and H_dd is written out.
+// ---------------------------------------------------------------------------
+template <bool kAccum, bool kFc>
+__global__ void __launch_bounds__(kTileWarps * 32)
+point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __restrict__ Hfd,
+             float* __restrict__ Hnn, float* __restrict__ gn, float* __restrict__ ent_part, int coff,
+             const float4* __restrict__ estats, const float* __restrict__ ddsq_t,
+             TileStats* __restrict__ tstats)
+{
+    const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int e0 = pb.tile_entry[t], e1 = pb.tile_entry[t + 1], ne = e1 - e0;
+    if (kAccum) {
+        const int n = t * kTile + lane;
+        const int stride = kFc ? 2 * kTile : kTile;
+        float hnn = kFc ? 0.0f : Hnn[n];
+        const bool valid = pb.valid_pt[n];
+        float g = 0.0f;
+        for (int e = e0; e < e1; e += 8) {
+            float v[8], h[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const bool in = e + u < e1;
+                v[u] = in ? gpart[(size_t)(e + u) * stride + lane] : 0.0f;
+                h[u] = (kFc && in) ? gpart[(size_t)(e + u) * stride + kTile + lane] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                g += v[u];
+                if (kFc) hnn += h[u];
+            }
+        }
+        const bool ok = valid && hnn > 0.0f;
+        const float sn = ok ? g / hnn : 0.0f;
+        if (warp == 0) {
+            gn[n] = ok ? g : 0.0f;
+            if (kFc) Hnn[n] = ok ? hnn : 0.0f;
+        }
+        for (int b = 0; b < ne; b += 32) {
+            Entry mine = {0, 0u, 0, 0};
+            int slot = 0;
+            if (b + lane < ne) {
+                mine = pb.entries[e0 + b + lane];
+                slot = pb.entry_slot[e0 + b + lane];
+            }
+            const int cnt = min(32, ne - b);
+            for (int i = warp; i < cnt; i += kTileWarps) {
+                const unsigned mask = __shfl_sync(0xffffffffu, mine.mask, i);
+                const int po = __shfl_sync(0xffffffffu, mine.pair_off, i);
+                const int sl = __shfl_sync(0xffffffffu, slot, i);
+                const bool vis = (mask >> lane) & 1u;
+                const int nvis = __popc(mask);
+                const float* h = Hfd + (size_t)po * 6 + (vis ? rank_of(mask, lane) : 0);
+                float corr[6];
+#pragma unroll
+                for (int a = 0; a < 6; ++a) corr[a] = vis ? h[a * nvis] * sn : 0.0f;
+                warp_sum<6>(corr);
+                if (lane < 6) {
+                    float v = corr[0];
+#pragma unroll
+                    for (int a = 1; a < 6; ++a) v = lane == a ? corr[a] : v;
+                    ent_part[(size_t)sl * kEntryPartial + coff + lane] = v;
+                }
+            }
+        }
+    }
+    if (warp == kTileWarps - 1) tile_stats_from_entries(pb, estats, ddsq_t, tstats, t, e0, e1, lane);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_depth_update(const LaunchCtx& L, bool ic_rule, int apply)
+{
+    const DepthState& ds = ic_rule ? L.ds_ic : L.ds_fc;
+    if (ic_rule)
+        depth_update_kernel<true><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
+            L.pb, ds, L.fs.dth2, L.ic.inv_hnn, L.ic.inv_d0, L.it.dcur, L.it.dprev, L.it.ddsq_t, apply);
+    else
+        depth_update_kernel<false><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
+            L.pb, ds, L.fs.dth2, nullptr, nullptr, L.it.dcur, L.it.dprev, L.it.ddsq_t, apply);
+    return cudaGetLastError();
+}
+
+template <int PMAX, bool A, int DT>
+static cudaError_t ic_residual_p(const LaunchCtx& L, int have_prev)
+{
+    const int blocks = (L.pb.E + kResWarps - 1) / kResWarps;
+    ic_residual_kernel<PMAX, A, DT><<<blocks, kResWarps * 32, 0, L.stream>>>(
+        L.pb, L.fs.fc, L.fs.fc_prev, L.it.dcur, L.it.dprev, L.ic.J4, L.ent_part, L.it.gpart,
+        L.it.estats, have_prev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ic_residual(const LaunchCtx& L, bool accum, int have_prev)
+{
+    if (L.pb.E == 0) return cudaSuccess;
+#define PBA_C(PM, A)                                                           \
+    [&]() {                                                                    \
+        switch (L.pb.dtype) {                                                  \
+        case PBA_F32: return ic_residual_p<PM, A, PBA_F32>(L, have_prev);      \
+        case PBA_F16: return ic_residual_p<PM, A, PBA_F16>(L, have_prev);      \
+        default: return ic_residual_p<PM, A, PBA_BF16>(L, have_prev);          \
+        }                                                                      \
+    }()
+    if (L.pb.P <= 8) return accum ? PBA_C(8, true) : PBA_C(8, false);
+    return accum ? PBA_C(16, true) : PBA_C(16, false);
+#undef PBA_C
+}
+
+cudaError_t launch_ic_point(const LaunchCtx& L, bool accum)
+{
+    if (accum)
+        point_kernel<true, false><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
+            L.pb, L.it.gpart, L.ic.Hfd, L.ic.Hnn, L.ds_ic.gn, L.ent_part, 6, L.it.estats, L.it.ddsq_t,
+            L.tstats);
+    else
+        point_kernel<false, false><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
+            L.pb, L.it.gpart, L.ic.Hfd, L.ic.Hnn, L.ds_ic.gn, L.ent_part, 6, L.it.estats, L.it.ddsq_t,
+            L.tstats);
+    return cudaGetLastError();
+}
+
+template <int PMAX, bool A, int DT>
+static cudaError_t fc_residual_p(const LaunchCtx& L, int have_prev)
+{
+    const int blocks = (L.pb.E + kResWarps - 1) / kResWarps;
+    fc_residual_kernel<PMAX, A, DT><<<blocks, kResWarps * 32, 0, L.stream>>>(
+        L.pb, L.fs.fc, L.fs.fc_prev, L.it.dcur, L.it.dprev, L.Hfd_fc, L.ent_part, L.it.gpart,
+        L.it.estats, have_prev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fc_residual(const LaunchCtx& L, bool accum, int have_prev)
+{
+    if (L.pb.E == 0) return cudaSuccess;
+#define PBA_C(PM, A)                                                           \
+    [&]() {                                                                    \
+        switch (L.pb.dtype) {                                                  \
+        case PBA_F32: return fc_residual_p<PM, A, PBA_F32>(L, have_prev);      \
+        case PBA_F16: return fc_residual_p<PM, A, PBA_F16>(L, have_prev);      \
+        default: return fc_residual_p<PM, A, PBA_BF16>(L, have_prev);          \
+        }                                                                      \
+    }()
+    if (L.pb.P <= 8) return accum ? PBA_C(8, true) : PBA_C(8, false);
+    return accum ? PBA_C(16, true) : PBA_C(16, false);
+#undef PBA_C
+}
+
+cudaError_t launch_fc_point(const LaunchCtx& L, bool accum)
+{
+    if (accum)
+        point_kernel<true, true><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
+            L.pb, L.it.gpart, L.Hfd_fc, L.ds_fc.Hnn, L.ds_fc.gn, L.ent_part, 27, L.it.estats,
+            L.it.ddsq_t, L.tstats);
+    else
+        point_kernel<false, true><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
+            L.pb, L.it.gpart, L.Hfd_fc, L.ds_fc.Hnn, L.ds_fc.gn, L.ent_part, 27, L.it.estats,
+            L.it.ddsq_t, L.tstats);
+    return cudaGetLastError();
+}
+
+}  // namespace pba

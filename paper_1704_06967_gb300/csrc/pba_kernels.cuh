@@ -2,6 +2,7 @@
 // library's translation units.
 #pragma once
 
+#include "pba_df.cuh"
 #include "pba_internal.cuh"
 
 namespace pba {
@@ -10,8 +11,18 @@ namespace pba {
 struct FrameState {
     float* fc;               // F * kFrameConst FP32 constants of the current poses
     float* fc_prev;          // F * 12 FP32 R|t of the previous poses
-    float* dtheta32;         // F * 6 last update (FP32)
+    float2* dth2;            // F * 6 last update as FP32 pairs (hi, lo = v - hi)
     const double* dtheta64;  // F * 6 last update (FP64)
+};
+
+// Buffers of the per-entry iteration kernels (pba_iter.cu).
+struct IterBufs {
+    float* dcur;     // Npad FP32 depths the residual kernels use
+    float* dprev;    // Npad FP32 depths before the last update
+    float* gpart;    // E * 32 per-(entry, lane) J_d^T w r (FC: E * 64: that, then J_d^T w J_d)
+    float4* estats;  // E (energy, r^2, count, max displacement)
+    float* ddsq_t;   // T sum of Dd^2 of the last depth update
+    float2* G0p;     // T * P * 32 template gradients (g_u, g_v) at the pattern pixels
 };
 
 // Per-point state of one method (IC or FC) for the depth back-substitution.
@@ -27,9 +38,11 @@ struct DepthState {
 
 // IC precompute products.
 struct IcStore {
-    float4* J4;  // pairs * NC float4 chunks
-    float* Hfd;  // pairs * 6
-    float* Hnn;  // Npad
+    float4* J4;       // pairs * NC float4 chunks
+    float* Hfd;       // pairs * 6
+    float* Hnn;       // Npad
+    double* inv_hnn;  // Npad 1 / H_dd (0 where H_dd = 0)
+    double* inv_d0;   // Npad 1 / d_0
 };
 
 struct LaunchCtx {
@@ -40,19 +53,23 @@ struct LaunchCtx {
     float* Hfd_fc;
     float* ent_part;
     TileStats* tstats;
+    IterBufs it;
     float* dthsq;     // F
     double* stats;    // slots * kStats
     const double* poses0;  // F*12 FP64 poses at p_0
     cudaStream_t stream;
 };
 
-size_t pass_smem_bytes(int F);
-cudaError_t set_pass_smem_limits(int F);
 cudaError_t launch_ic_precompute(const LaunchCtx& L);
-cudaError_t launch_ic_pass(const LaunchCtx& L, bool accum, int apply, int have_prev);
-cudaError_t launch_fc_pass(const LaunchCtx& L, bool accum, int apply, int have_prev);
+cudaError_t launch_depth_update(const LaunchCtx& L, bool ic_rule, int apply);
+cudaError_t launch_ic_residual(const LaunchCtx& L, bool accum, int have_prev);
+cudaError_t launch_ic_point(const LaunchCtx& L, bool accum);
+// out[f * ncomp + k] = sum over frame f's entries of part[off + k]
+// (minus part[sub + k - sub_from] for k >= sub_from when sub >= 0)
 cudaError_t launch_frame_reduce(const LaunchCtx& L, int off, int ncomp, double* out, int slot_cur,
-                                int slot_prev, bool frames);
+                                int slot_prev, bool frames, int sub = -1, int sub_from = 0);
+cudaError_t launch_fc_residual(const LaunchCtx& L, bool accum, int have_prev);
+cudaError_t launch_fc_point(const LaunchCtx& L, bool accum);
 
 // linear algebra (pba_linalg.cu)
 struct SolveArgs {
@@ -63,7 +80,7 @@ struct SolveArgs {
     double* poses64;        // F*12 current
     const double* poses0;   // F*12 p_0
     double* dtheta64;       // F*6
-    float* dtheta32;        // F*6
+    float2* dth2;           // F*6 (hi, lo) pairs
     float* fc;              // F*kFrameConst
     float* fc_prev;         // F*12
     float* dthsq;           // F
@@ -90,21 +107,29 @@ constexpr int kSchurChunk = 16;
 cudaError_t launch_schur_sparse(const DevProblem& pb, const float* Hfd, const float* Hnn,
                                 const SchurLists& sl, float2* part, double* Soff,
                                 cudaStream_t st, int* launches);
+// S (FP64) and, when S2 is given, its double-float copy (the factorisation's
+// working matrix; with rhs, one extra row b = -y taken from
+// rhs[f * rhs_stride + rhs_off + a])
 cudaError_t launch_assemble_S(int F, const double* Hff, int hff_stride, const double* Soff,
                               const double* anchor_t, double gauge_w, double* S, int* active,
-                              cudaStream_t st);
-// FP64 Cholesky (pba_chol.cu): A (consumed) -> L (lower, with L^T in the
-// upper triangle) and inv_diag = 1/L_ii
-cudaError_t launch_cholesky(double* A, double* L, double* inv_diag, int n, int* err,
-                            cudaStream_t st, int* launches);
-cudaError_t launch_chol_inverse(const double* L, const double* inv_diag, double* Sinv, int n,
-                                cudaStream_t st);
+                              cudaStream_t st, dfloat* S2 = nullptr, const double* rhs = nullptr,
+                              int rhs_stride = 0, int rhs_off = 0);
+// double-float LDL^T (pba_chol.cu): A ((n + aug) x n, consumed) -> L (unit
+// lower with L^T in the upper triangle; with aug, row n = D^-1 L^-1 b),
+// Linv (inverses of the 32 x 32 diagonal blocks and their transposes),
+// dpiv = d_j, rpiv = 1 / d_j
+cudaError_t launch_ldl(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv, int n, int aug,
+                       int* err, cudaStream_t st);
+cudaError_t ldl_setup();  // once per process and device, before any capture
+cudaError_t launch_ldl_inverse(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, double* Sinv,
+                               int n, cudaStream_t st);
 cudaError_t launch_ic_solve_update(const SolveArgs& a, const double* Sinv, const double* y,
                                    int y_stride, int y_off, cudaStream_t st);
-cudaError_t launch_fc_solve_update(const SolveArgs& a, const double* L, const double* inv_diag,
-                                   const double* y, int y_stride, int y_off, cudaStream_t st);
+cudaError_t launch_fc_solve_update(const SolveArgs& a, const dfloat* L, const dfloat* Linv,
+                                   cudaStream_t st);
 
 // setup kernels (pba_runtime.cu)
-cudaError_t launch_setup(const DevProblem& pb, float* gx, float* gy, float* I0p, cudaStream_t st);
+cudaError_t launch_setup(const DevProblem& pb, float* gx, float* gy, float* I0p, float2* G0p,
+                         cudaStream_t st);
 
 }  // namespace pba

@@ -33,7 +33,8 @@ constexpr int kAssembleThreads = 256;
 
 __global__ void __launch_bounds__(kAssembleThreads)
 assemble_S_kernel(int F, const double* Hff, int stride, const double* Soff,
-                  const double* anchor_t, double gauge_w, double* S, int* active)
+                  const double* anchor_t, double gauge_w, double* S, int* active, dfloat* S2,
+                  const double* rhs, int rhs_stride, int rhs_off)
 {
     __shared__ int s_act[1024];
     __shared__ double s_red[kAssembleThreads / 32];
@@ -97,18 +98,29 @@ assemble_S_kernel(int F, const double* Hff, int stride, const double* Soff,
             }
         }
         S[idx] = v;
+        if (S2) S2[idx] = df_from_double(v);
     }
+    // augmented row n6 of the double-float copy: b = -y (0 for frames without
+    // residuals), eliminated with the matrix by the factorisation
+    if (S2 && rhs)
+        for (int j = blockIdx.x * blockDim.x + tid; j < n6; j += gridDim.x * blockDim.x) {
+            const int f = j / 6 + 1;
+            S2[total + j] = s_act[f] ? df_from_double(-rhs[(size_t)f * rhs_stride + rhs_off + j % 6])
+                                     : df_make(0.0f, 0.0f);
+        }
 }
 
 cudaError_t launch_assemble_S(int F, const double* Hff, int hff_stride, const double* Soff,
                               const double* anchor_t, double gauge_w, double* S, int* active,
-                              cudaStream_t st)
+                              cudaStream_t st, dfloat* S2, const double* rhs, int rhs_stride,
+                              int rhs_off)
 {
     const int n6 = 6 * (F - 1);
     if (F > 1024) return cudaErrorInvalidValue;
     const int blocks = std::max(1, std::min(148, (n6 * n6 + 4 * kAssembleThreads - 1) / (4 * kAssembleThreads)));
     assemble_S_kernel<<<blocks, kAssembleThreads, 0, st>>>(F, Hff, hff_stride, Soff, anchor_t,
-                                                            gauge_w, S, active);
+                                                            gauge_w, S, active, S2, rhs, rhs_stride,
+                                                            rhs_off);
     return cudaGetLastError();
 }
 
@@ -129,12 +141,12 @@ __device__ __forceinline__ void mat3_mul_lanes(const double* A, const double* B,
 
 // Writes the new pose of frame f (lanes of one warp; Rn, tn in shared
 // memory), its FP32 pass constants, the previous R|t and the update.
-__device__ void write_frame_lanes(const SolveArgs& a, int f, const double* Rn, const double* tn,
-                                  const double* dth, int lane)
+__device__ void write_frame_lanes(const SolveArgs& a, int f, const double* pose_old, const double* Rn,
+                                  const double* tn, const double* dth, int lane)
 {
     double* pose = a.poses64 + 12 * f;
     float* prev = a.fc_prev + 12 * f;
-    if (lane < 12) prev[lane] = (float)pose[lane];
+    if (lane < 12) prev[lane] = (float)pose_old[lane];
     __syncwarp();
     if (lane < 9) pose[lane] = Rn[lane];
     if (lane < 3) pose[9 + lane] = tn[lane];
@@ -146,29 +158,58 @@ __device__ void write_frame_lanes(const SolveArgs& a, int f, const double* Rn, c
         const double ox = a.pat[2 * j] * a.inv_fx, oy = a.pat[2 * j + 1] * a.inv_fy;
         out[12 + q] = (float)(ox * Rn[3 * r] + oy * Rn[3 * r + 1]);
     }
+    float q = 0.0f;
     if (lane < 6) {
-        a.dtheta64[6 * f + lane] = dth[lane];
-        a.dtheta32[6 * f + lane] = (float)dth[lane];
+        const double v = dth[lane];
+        const float hi = (float)v;
+        a.dtheta64[6 * f + lane] = v;
+        a.dth2[6 * f + lane] = make_float2(hi, (float)(v - (double)hi));
+        q = hi * hi;  // |Dtheta_f|^2 is a convergence statistic: FP32 is enough
     }
-    if (lane == 0) {
-        double q = 0.0;
-        for (int k = 0; k < 6; ++k) q += dth[k] * dth[k];
-        a.dthsq[f] = (float)q;
-    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) a.dthsq[f] = q;
 }
 
 // Rodrigues coefficients of omega: A = sin/th, B = (1-cos)/th^2,
-// C = (th-sin)/th^3 (Taylor series below th = 1e-3), one sincos per warp.
+// C = (th-sin)/th^3. Updates are small rotations, so below th = 0.5 the
+// coefficients come from their Taylor series in x = th^2 (Horner, eight
+// terms: the first omitted one is below 1e-19 there); FP64 sincos and three
+// FP64 divisions on one lane cost several microseconds on GB300.
 __device__ void rodrigues_coeffs(const double* w, double* ABC, int lane)
 {
     if (lane == 0) {
         const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-        const double th = sqrt(th2);
-        if (th < 1e-3) {
-            ABC[0] = 1.0 - th2 * (1.0 / 6.0) + th2 * th2 * (1.0 / 120.0);
-            ABC[1] = 0.5 - th2 * (1.0 / 24.0) + th2 * th2 * (1.0 / 720.0);
-            ABC[2] = 1.0 / 6.0 - th2 * (1.0 / 120.0) + th2 * th2 * (1.0 / 5040.0);
+        if (th2 < 0.25) {
+            // 1/(2k+1)!, 1/(2k+2)!, 1/(2k+3)! for k = 7 .. 0, in powers of -x
+            const double y = -th2;
+            double A = 1.0 / 1307674368000.0, B = 1.0 / 20922789888000.0, C = 1.0 / 355687428096000.0;
+            A = fma(A, y, 1.0 / 6227020800.0);
+            B = fma(B, y, 1.0 / 87178291200.0);
+            C = fma(C, y, 1.0 / 1307674368000.0);
+            A = fma(A, y, 1.0 / 39916800.0);
+            B = fma(B, y, 1.0 / 479001600.0);
+            C = fma(C, y, 1.0 / 6227020800.0);
+            A = fma(A, y, 1.0 / 362880.0);
+            B = fma(B, y, 1.0 / 3628800.0);
+            C = fma(C, y, 1.0 / 39916800.0);
+            A = fma(A, y, 1.0 / 5040.0);
+            B = fma(B, y, 1.0 / 40320.0);
+            C = fma(C, y, 1.0 / 362880.0);
+            A = fma(A, y, 1.0 / 120.0);
+            B = fma(B, y, 1.0 / 720.0);
+            C = fma(C, y, 1.0 / 5040.0);
+            A = fma(A, y, 1.0 / 6.0);
+            B = fma(B, y, 1.0 / 24.0);
+            C = fma(C, y, 1.0 / 120.0);
+            A = fma(A, y, 1.0);
+            B = fma(B, y, 0.5);
+            C = fma(C, y, 1.0 / 6.0);
+            ABC[0] = A;
+            ABC[1] = B;
+            ABC[2] = C;
         } else {
+            const double th = sqrt(th2);
             double sn, cs;
             sincos(th, &sn, &cs);
             ABC[0] = sn / th;
@@ -193,13 +234,13 @@ __device__ __forceinline__ double rodrigues_entry(const double* w, double p, dou
 }
 
 // Sec. 3.6: R <- R R0^T exp(omega)^T R0, t <- t - R R0^T Dt (old R on the
-// right-hand sides). sh: 48 doubles of warp-private shared memory.
-__device__ void ic_pose_update_warp(const SolveArgs& a, int f, const double* dth, double* sh, int lane)
+// right-hand sides). pose, p0: the frame's current and p_0 poses (12 each,
+// shared memory); sh: 48 doubles of warp-private shared memory.
+__device__ void ic_pose_update_warp(const SolveArgs& a, int f, const double* pose, const double* p0,
+                                    const double* dth, double* sh, int lane)
 {
     double *R = sh, *R0t = sh + 9, *A = sh + 18, *E = sh + 27, *B = sh + 36, *t = sh + 45;
     double ABC[3];
-    const double* pose = a.poses64 + 12 * f;
-    const double* p0 = a.poses0 + 12 * f;
     if (lane < 9) {
         R[lane] = pose[lane];
         R0t[lane] = p0[3 * (lane % 3) + lane / 3];
@@ -223,14 +264,16 @@ __device__ void ic_pose_update_warp(const SolveArgs& a, int f, const double* dth
     if (lane < 3)
         t[lane] = pose[9 + lane] - fma(A[3 * lane], dth[0], fma(A[3 * lane + 1], dth[1], A[3 * lane + 2] * dth[2]));
     __syncwarp();
-    write_frame_lanes(a, f, Rn, t, dth, lane);
+    write_frame_lanes(a, f, pose, Rn, t, dth, lane);
 }
 
 // Boxplus: T <- exp([upsilon, omega]) T.
 __device__ void fc_pose_update_warp(const SolveArgs& a, int f, const double* dth, double* sh, int lane)
 {
     double *E = sh, *V = sh + 9, *Rn = sh + 18, *R = sh + 27, *t = sh + 36, *ABC = sh + 39;
-    const double* pose = a.poses64 + 12 * f;
+    double* pose = sh + 42;  // 12 (sh holds 54 doubles)
+    if (lane < 12) pose[lane] = a.poses64[12 * f + lane];
+    __syncwarp();
     if (lane < 9) R[lane] = pose[lane];
     rodrigues_coeffs(dth + 3, ABC, lane);
     if (lane < 9) E[lane] = rodrigues_entry(dth + 3, ABC[0], ABC[1], lane);
@@ -241,7 +284,7 @@ __device__ void fc_pose_update_warp(const SolveArgs& a, int f, const double* dth
         t[lane] = fma(E[3 * lane], pose[9], fma(E[3 * lane + 1], pose[10], E[3 * lane + 2] * pose[11])) +
                   fma(V[3 * lane], dth[0], fma(V[3 * lane + 1], dth[1], V[3 * lane + 2] * dth[2]));
     __syncwarp();
-    write_frame_lanes(a, f, Rn, t, dth, lane);
+    write_frame_lanes(a, f, pose, Rn, t, dth, lane);
 }
 
 // Scale gauge (the one free direction of the system, Delta t_f = -t_f,
@@ -259,31 +302,47 @@ __device__ __forceinline__ double gauge_alpha(const double* ta, const double* dt
 
 // IC step 3 + 4: Dtheta = -S^-1 y (one CTA per target frame, one warp per
 // row, FP64 dot products; warps 6-8 also form the anchor frame's Delta t for
-// the gauge constraint), then the frame's pose update by warp 0.
-__global__ void ic_solve_update_kernel(SolveArgs a, const double* Sinv, const double* y,
-                                       int y_stride, int y_off)
+// the gauge constraint), then the frame's pose update by warp 0. Everything
+// the update reads besides Dtheta is fetched at the start, beside the rows.
+__global__ void __launch_bounds__(9 * 32) ic_solve_update_kernel(SolveArgs a, const double* Sinv,
+                                                                 const double* y, int y_stride,
+                                                                 int y_off)
 {
     __shared__ double dth[9];
     __shared__ double d[6];
     __shared__ double sh[48];
-    const int f = blockIdx.x + 1, lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    __shared__ double s_pose[12], s_p0[12], s_ta[3], s_tf[3];
+    __shared__ int s_act;
+    const int f = blockIdx.x + 1, tid = threadIdx.x, lane = tid & 31, row = tid >> 5;
     const int n6 = a.n6;
     const int anchor = a.active[0];
+    if (row == 8) {
+        if (lane < 12) s_pose[lane] = a.poses64[12 * f + lane];
+        else if (lane < 24) s_p0[lane - 12] = a.poses0[12 * f + lane - 12];
+        else if (lane < 27) s_tf[lane - 24] = a.tanchor[12 * f + 9 + lane - 24];
+        else if (lane < 30) s_ta[lane - 27] = anchor > 0 ? a.tanchor[12 * anchor + 9 + lane - 27] : 0.0;
+        else if (lane == 30) s_act = a.active[f];
+    }
     const int rr = row < 6 ? 6 * (f - 1) + row : (anchor > 0 ? 6 * (anchor - 1) + row - 6 : -1);
     if (rr >= 0) {
         const double* Sr = Sinv + (size_t)rr * n6;
-        double s = 0.0;
-        for (int c = lane; c < n6; c += 32) s = fma(Sr[c], y[(size_t)(c / 6 + 1) * y_stride + y_off + c % 6], s);
-        s = warp_sum1d(s);
+        double s0 = 0.0, s1 = 0.0;  // two chains halve the dependent FP64 latency
+        int c = lane;
+        for (; c + 32 < n6; c += 64) {
+            s0 = fma(Sr[c], y[(size_t)(c / 6 + 1) * y_stride + y_off + c % 6], s0);
+            s1 = fma(Sr[c + 32], y[(size_t)((c + 32) / 6 + 1) * y_stride + y_off + (c + 32) % 6], s1);
+        }
+        if (c < n6) s0 = fma(Sr[c], y[(size_t)(c / 6 + 1) * y_stride + y_off + c % 6], s0);
+        const double s = warp_sum1d(s0 + s1);
         if (lane == 0) dth[row] = -s;
     }
     __syncthreads();
     if (row != 0) return;
     if (lane < 6) {
         double v = dth[lane];
-        if (lane < 3 && anchor > 0 && a.active[f]) {
-            const double alpha = gauge_alpha(a.tanchor + 12 * anchor + 9, dth + 6);
-            v = fma(-alpha, a.tanchor[12 * f + 9 + lane], v);
+        if (lane < 3 && anchor > 0 && s_act) {
+            const double alpha = gauge_alpha(s_ta, dth + 6);
+            v = fma(-alpha, s_tf[lane], v);
         }
         d[lane] = v;
     }
@@ -294,7 +353,7 @@ __global__ void ic_solve_update_kernel(SolveArgs a, const double* Sinv, const do
         if (lane < 6) d[lane] = 0.0;
         __syncwarp();
     }
-    ic_pose_update_warp(a, f, d, sh, lane);
+    ic_pose_update_warp(a, f, s_pose, s_p0, d, sh, lane);
 }
 
 cudaError_t launch_ic_solve_update(const SolveArgs& a, const double* Sinv, const double* y,
@@ -304,21 +363,27 @@ cudaError_t launch_ic_solve_update(const SolveArgs& a, const double* Sinv, const
     return cudaGetLastError();
 }
 
-// FC: solve L L^T Dtheta = -y (one CTA, blocked substitutions), the exact
-// gauge constraint, then every frame's boxplus update (one warp per frame).
-__global__ void __launch_bounds__(256) fc_solve_update_kernel(SolveArgs a, const double* L,
-                                                              const double* inv_diag,
-                                                              const double* y, int y_stride,
-                                                              int y_off)
+// FC: the factorisation has eliminated b = -y with the matrix, so row n of L
+// holds D^-1 L^-1 b; the backward substitution L^T Dtheta = that row gives
+// Dtheta = -S^-1 y (double-float, one CTA). Then the exact gauge constraint
+// and every frame's boxplus update (one warp per frame, FP64).
+constexpr int kFcSolveWarps = 32;  // one warp per frame's update (F <= 33 in one round)
+
+__global__ void __launch_bounds__(kFcSolveWarps * 32) fc_solve_update_kernel(SolveArgs a, const dfloat* L,
+                                                                           const dfloat* Linv)
 {
-    extern __shared__ double x[];
+    extern __shared__ dfloat xs[];
+    __shared__ dfloat tb[kLdlBlock];
+    double* x = reinterpret_cast<double*>(xs + a.n6);
     __shared__ double s_alpha;
-    __shared__ double sh[8][48];
-    __shared__ double dsh[8][6];
+    __shared__ double sh[kFcSolveWarps][54];
+    __shared__ double dsh[kFcSolveWarps][6];
     const int n = a.n6, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < n; i += blockDim.x) x[i] = -y[(size_t)(i / 6 + 1) * y_stride + y_off + i % 6];
+    for (int i = tid; i < n; i += blockDim.x) xs[i] = L[(size_t)n * n + i];
     __syncthreads();
-    chol_solve_smem(L, inv_diag, n, x);
+    ldl_backward_smem(L, Linv, n, xs, tb);
+    for (int i = tid; i < n; i += blockDim.x) x[i] = df_to_double(xs[i]);
+    __syncthreads();
     if (tid == 0) {
         const int anchor = a.active[0];
         s_alpha = anchor > 0 ? gauge_alpha(a.tanchor + 12 * anchor + 9, x + 6 * (anchor - 1)) : 0.0;
@@ -343,10 +408,10 @@ __global__ void __launch_bounds__(256) fc_solve_update_kernel(SolveArgs a, const
     }
 }
 
-cudaError_t launch_fc_solve_update(const SolveArgs& a, const double* L, const double* inv_diag,
-                                   const double* y, int y_stride, int y_off, cudaStream_t st)
+cudaError_t launch_fc_solve_update(const SolveArgs& a, const dfloat* L, const dfloat* Linv,
+                                   cudaStream_t st)
 {
-    fc_solve_update_kernel<<<1, 256, sizeof(double) * a.n6, st>>>(a, L, inv_diag, y, y_stride, y_off);
+    fc_solve_update_kernel<<<1, kFcSolveWarps * 32, (sizeof(dfloat) + sizeof(double)) * a.n6, st>>>(a, L, Linv);
     return cudaGetLastError();
 }
 

@@ -7,10 +7,13 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
+#include "pba_chol.cuh"
 #include "pba_kernels.cuh"
 
 using namespace pba;
@@ -32,8 +35,23 @@ uint32_t spread16(uint32_t x)
 }
 
 // Timing slots (pba_last_timing): precompute, residual pass, reduce,
-// Schur/assemble, factor/solve/update, final evaluation.
-enum { TS_PRE = 0, TS_PASS, TS_REDUCE, TS_SCHUR, TS_SOLVE, TS_EVAL, TS_N };
+// Schur/assemble, factor/solve/update, final evaluation, per-point kernels.
+enum { TS_PRE = 0, TS_PASS, TS_REDUCE, TS_SCHUR, TS_SOLVE, TS_EVAL, TS_POINT, TS_N };
+static_assert(TS_N == PBA_TIMING_SLOTS, "timing slots");
+
+using TimedPair = std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>;
+
+// A captured launch sequence: replaying it submits every kernel of a call
+// with one cudaGraphLaunch (the host no longer paces the small kernels).
+struct GraphRec {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<TimedPair> tev;  // event pairs recorded by the graph's nodes
+    int64_t launches = 0;        // kernels per replay
+};
+
+// graph key: (kind, iterations, timing mask)
+enum { G_ITERATE = 0, G_FC = 1, G_PRECOMPUTE = 2 };
+using GraphKey = std::tuple<int, int, int>;
 
 }  // namespace
 
@@ -82,17 +100,21 @@ struct pba_ctx {
         float2* xn;
         float* I0p;
         unsigned char* valid_pt;
-        double *d64, *d0_64, *dd_last;
+        double *d64, *d0_64, *dd_last, *inv_hnn, *inv_d0;
         float *gn_ic, *Hnn_ic, *gn_fc, *Hnn_fc;
         float4* J4;
         float *Hfd_ic, *Hfd_fc;
         float* ent_part;
         TileStats* tstats;
-        float *fc, *fc_prev, *dtheta32, *dthsq;
+        float *fc, *fc_prev, *dthsq;
+        float2* dth2;
+        float *dcur, *dprev, *gpart, *ddsq_t;
+        float2* G0p;
+        float4* estats;
         double *poses64, *poses0_64, *dtheta64;
         double *red_ic, *red_y;
-        double *Soff, *S_ic, *L_ic, *Sinv, *S_fc, *L_fc, *chol_work;
-        double *invd_ic, *invd_fc;
+        double *Soff, *S_ic, *Sinv, *S_fc;
+        dfloat *A2, *L2, *Linv, *dpiv, *rpiv;  // double-float factorisation (IC and FC in turn)
         int *pair_fg, *pair_chunk, *chunk_pair, *chunk_start;
         int2* pair_items;
         float2* schur_part;
@@ -107,10 +129,15 @@ struct pba_ctx {
     int timing = 0;  // slot mask
     int64_t h2d = 0, d2h = 0;
     int64_t launches = 0;
-    double tms[TS_N] = {0, 0, 0, 0, 0, 0};
-    int64_t tcount[TS_N] = {0, 0, 0, 0, 0, 0};
-    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> tev;
+    double tms[TS_N] = {};
+    int64_t tcount[TS_N] = {};
+    std::vector<TimedPair> tev;        // pooled events recorded by direct launches
+    std::vector<TimedPair> tev_graph;  // events of replayed graphs (owned by the graphs)
     std::vector<cudaEvent_t> evpool;
+
+    // captured launch sequences (cfg.use_graphs with a non-null stream)
+    bool capturing = false;
+    std::map<GraphKey, GraphRec> graphs;
 };
 
 namespace {
@@ -167,7 +194,9 @@ int tbegin(pba_ctx* ctx, int slot)
 {
     if (!((ctx->timing >> slot) & 1)) return -1;
     cudaEvent_t a = take_event(ctx), b = take_event(ctx);
-    cudaEventRecord(a, ctx->stream);
+    // inside a capture the pair becomes event-record nodes of the graph
+    if (ctx->capturing) cudaEventRecordWithFlags(a, ctx->stream, cudaEventRecordExternal);
+    else cudaEventRecord(a, ctx->stream);
     ctx->tev.push_back({slot, {a, b}});
     return (int)ctx->tev.size() - 1;
 }
@@ -175,7 +204,8 @@ int tbegin(pba_ctx* ctx, int slot)
 void tend(pba_ctx* ctx, int idx)
 {
     if (idx < 0) return;
-    cudaEventRecord(ctx->tev[idx].second.second, ctx->stream);
+    if (ctx->capturing) cudaEventRecordWithFlags(ctx->tev[idx].second.second, ctx->stream, cudaEventRecordExternal);
+    else cudaEventRecord(ctx->tev[idx].second.second, ctx->stream);
 }
 
 void tcollect(pba_ctx* ctx)
@@ -190,6 +220,29 @@ void tcollect(pba_ctx* ctx)
         ctx->evpool.push_back(ev.second.second);
     }
     ctx->tev.clear();
+    for (auto& ev : ctx->tev_graph) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ev.second.first, ev.second.second) == cudaSuccess) {
+            ctx->tms[ev.first] += ms;
+            ctx->tcount[ev.first] += 1;
+        }
+    }
+    ctx->tev_graph.clear();
+}
+
+void destroy_graphs(pba_ctx* ctx)
+{
+    if (ctx->graphs.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    tcollect(ctx);
+    for (auto& kv : ctx->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        for (auto& ev : kv.second.tev) {
+            ctx->evpool.push_back(ev.second.first);
+            ctx->evpool.push_back(ev.second.second);
+        }
+    }
+    ctx->graphs.clear();
 }
 
 size_t elem_size(pba_dtype t) { return t == PBA_F32 ? 4 : 2; }
@@ -238,6 +291,8 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.d64, Np * 8);
     take(c->d.d0_64, Np * 8);
     take(c->d.dd_last, Np * 8);
+    take(c->d.inv_hnn, Np * 8);
+    take(c->d.inv_d0, Np * 8);
     take(c->d.gn_ic, Np * 4);
     take(c->d.Hnn_ic, Np * 4);
     take(c->d.gn_fc, Np * 4);
@@ -249,7 +304,13 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.tstats, (size_t)c->T * sizeof(TileStats));
     take(c->d.fc, F * kFrameConst * 4);
     take(c->d.fc_prev, F * 12 * 4);
-    take(c->d.dtheta32, F * 6 * 4);
+    take(c->d.dth2, F * 6 * sizeof(float2));
+    take(c->d.dcur, Np * 4);
+    take(c->d.dprev, Np * 4);
+    take(c->d.gpart, (size_t)c->E * kTile * 2 * 4);  // FC: g and H_dd per (entry, lane)
+    take(c->d.estats, (size_t)c->E * sizeof(float4));
+    take(c->d.ddsq_t, (size_t)c->T * 4);
+    take(c->d.G0p, (size_t)c->T * (c->pattern.size() / 2) * kTile * sizeof(float2));
     take(c->d.dthsq, F * 4);
     take(c->d.poses64, F * 12 * 8);
     take(c->d.poses0_64, F * 12 * 8);
@@ -258,13 +319,13 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.red_y, F * 27 * 8);
     take(c->d.Soff, n6 * n6 * 8);
     take(c->d.S_ic, n6 * n6 * 8);
-    take(c->d.L_ic, n6 * n6 * 8);
     take(c->d.Sinv, n6 * n6 * 8);
     take(c->d.S_fc, n6 * n6 * 8);
-    take(c->d.L_fc, n6 * n6 * 8);
-    take(c->d.chol_work, n6 * n6 * 8);
-    take(c->d.invd_ic, n6 * 8);
-    take(c->d.invd_fc, n6 * 8);
+    take(c->d.A2, (n6 + 1) * n6 * sizeof(dfloat));
+    take(c->d.L2, (n6 + 1) * n6 * sizeof(dfloat));
+    take(c->d.Linv, (n6 + 31) / 32 * kLinvStride * sizeof(dfloat));
+    take(c->d.dpiv, n6 * sizeof(dfloat));
+    take(c->d.rpiv, n6 * sizeof(dfloat));
     take(c->d.pair_fg, c->pair_fg.size() * sizeof(int));
     take(c->d.pair_chunk, c->pair_chunk.size() * sizeof(int));
     take(c->d.chunk_pair, c->chunk_pair.size() * sizeof(int));
@@ -424,10 +485,11 @@ LaunchCtx make_launch(pba_ctx* c)
     pb.xn = c->d.xn;
     pb.I0p = c->d.I0p;
     pb.valid_pt = c->d.valid_pt;
-    L.fs = FrameState{c->d.fc, c->d.fc_prev, c->d.dtheta32, c->d.dtheta64};
+    L.fs = FrameState{c->d.fc, c->d.fc_prev, c->d.dth2, c->d.dtheta64};
+    L.it = IterBufs{c->d.dcur, c->d.dprev, c->d.gpart, c->d.estats, c->d.ddsq_t, c->d.G0p};
     L.ds_ic = DepthState{c->d.d64, c->d.d0_64, c->d.gn_ic, c->d.Hnn_ic, c->d.Hfd_ic, c->d.dd_last, c->d.err};
     L.ds_fc = DepthState{c->d.d64, c->d.d0_64, c->d.gn_fc, c->d.Hnn_fc, c->d.Hfd_fc, c->d.dd_last, c->d.err};
-    L.ic = IcStore{c->d.J4, c->d.Hfd_ic, c->d.Hnn_ic};
+    L.ic = IcStore{c->d.J4, c->d.Hfd_ic, c->d.Hnn_ic, c->d.inv_hnn, c->d.inv_d0};
     L.Hfd_fc = c->d.Hfd_fc;
     L.ent_part = c->d.ent_part;
     L.tstats = c->d.tstats;
@@ -458,7 +520,7 @@ SolveArgs make_solve(pba_ctx* c)
     a.poses64 = c->d.poses64;
     a.poses0 = c->d.poses0_64;
     a.dtheta64 = c->d.dtheta64;
-    a.dtheta32 = c->d.dtheta32;
+    a.dth2 = c->d.dth2;
     a.fc = c->d.fc;
     a.fc_prev = c->d.fc_prev;
     a.dthsq = c->d.dthsq;
@@ -475,9 +537,56 @@ pba_status copy_stats(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     CK(d2h(ctx, h.data(), ctx->d.stats, sizeof(double) * h.size()));
     for (int k = 0; k <= n_iters; ++k) {
         const double* r = h.data() + (size_t)k * kStats;
-        stats[k] = pba_iter_stats{r[0], r[1], r[2], k < n_iters ? r[3] : 0.0,
-                                  k < n_iters ? r[4] : 0.0, k < n_iters ? r[5] : 0.0};
+        // slots hold raw sums: energy, sum r^2, count, max displacement,
+        // sum |Dtheta|^2, sum Dd^2
+        stats[k] = pba_iter_stats{r[0], r[2] > 0 ? std::sqrt(r[1] / r[2]) : 0.0, r[2],
+                                  k < n_iters ? r[3] : 0.0, k < n_iters ? std::sqrt(r[4]) : 0.0,
+                                  k < n_iters ? std::sqrt(r[5]) : 0.0};
     }
+    return PBA_OK;
+}
+
+// Runs `body` (which enqueues kernels on ctx->stream) directly, or, with
+// cfg.use_graphs and a non-null stream, replays it from a graph captured on
+// the first call with this key. The kernels read all state from the
+// workspace, so a replay computes exactly what the direct launches would.
+template <class Fn>
+pba_status run_enqueued(pba_ctx* ctx, GraphKey key, Fn&& body)
+{
+    if (!ctx->cfg.use_graphs || !ctx->stream) return body();
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        GraphRec rec;
+        std::vector<TimedPair> saved;
+        saved.swap(ctx->tev);
+        const int64_t l0 = ctx->launches;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        ctx->capturing = true;
+        pba_status s = body();
+        ctx->capturing = false;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+        rec.tev.swap(ctx->tev);
+        ctx->tev.swap(saved);
+        rec.launches = ctx->launches - l0;
+        ctx->launches = l0;
+        cudaError_t ei = cudaSuccess;
+        if (s == PBA_OK && e == cudaSuccess) ei = cudaGraphInstantiate(&rec.exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (s != PBA_OK || e != cudaSuccess || ei != cudaSuccess) {
+            for (auto& ev : rec.tev) {
+                ctx->evpool.push_back(ev.second.first);
+                ctx->evpool.push_back(ev.second.second);
+            }
+            if (s != PBA_OK) return s;
+            return fail(ctx, PBA_ERR_CUDA, "graph capture failed: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : ei));
+        }
+        it = ctx->graphs.emplace(key, std::move(rec)).first;
+    }
+    CK(cudaGraphLaunch(it->second.exec, ctx->stream));
+    ctx->launches += it->second.launches;
+    ctx->tev_graph.insert(ctx->tev_graph.end(), it->second.tev.begin(), it->second.tev.end());
     return PBA_OK;
 }
 
@@ -507,7 +616,10 @@ __global__ void gradient_images_kernel(DevProblem pb, float* gx, float* gy)
     }
 }
 
-__global__ void template_gather_kernel(DevProblem pb, float* I0p)
+// Template intensities and gradients (central differences of the reference
+// image, read from the gradient images) at every pattern pixel, laid out
+// [tile][j][lane].
+__global__ void template_gather_kernel(DevProblem pb, float* I0p, float2* G0p)
 {
     const int total = pb.T * pb.P * kTile;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -515,15 +627,18 @@ __global__ void template_gather_kernel(DevProblem pb, float* I0p)
         const int n = t * kTile + lane;
         const int px = pb.uvs[2 * n] + pb.pat[2 * j], py = pb.uvs[2 * n + 1] + pb.pat[2 * j + 1];
         I0p[i] = load_px(pb.img, pb.dtype, (size_t)py * pb.pitch + px);
+        const size_t g = (size_t)py * pb.W + px;
+        G0p[i] = make_float2(pb.gx[g], pb.gy[g]);
     }
 }
 
-cudaError_t launch_setup(const DevProblem& pb, float* gx, float* gy, float* I0p, cudaStream_t st)
+cudaError_t launch_setup(const DevProblem& pb, float* gx, float* gy, float* I0p, float2* G0p,
+                         cudaStream_t st)
 {
     gradient_images_kernel<<<1024, 256, 0, st>>>(pb, gx, gy);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    template_gather_kernel<<<256, 256, 0, st>>>(pb, I0p);
+    template_gather_kernel<<<256, 256, 0, st>>>(pb, I0p, G0p);
     return cudaGetLastError();
 }
 
@@ -562,6 +677,7 @@ void pba_destroy(pba_ctx* ctx)
 {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    destroy_graphs(ctx);
     tcollect(ctx);
     for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
     delete ctx;
@@ -657,6 +773,7 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     if (!dev_ptr || bytes < need)
         return fail(ctx, PBA_ERR_NOMEM, "workspace of %zu bytes needed, %zu given", need, bytes);
     if ((uintptr_t)dev_ptr % kAlign) return fail(ctx, PBA_ERR_ARG, "workspace must be 256-byte aligned");
+    destroy_graphs(ctx);  // captured kernels hold the old workspace's pointers
     ctx->ws = (char*)dev_ptr;
     ctx->ws_bytes = bytes;
     layout(ctx, ctx->ws);
@@ -697,9 +814,9 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     pba_status s = upload_params(ctx, ctx->poses_init.data(), ctx->d_init.data());
     if (s != PBA_OK) return s;
     CK(h2d(ctx, ctx->d.poses0_64, ctx->poses_init.data(), sizeof(double) * 12 * ctx->F));
-    CK(set_pass_smem_limits(ctx->F));
     LaunchCtx L = make_launch(ctx);
-    LAUNCH(TS_PRE, launch_setup(L.pb, ctx->d.gx, ctx->d.gy, ctx->d.I0p, ctx->stream));
+    CK(ldl_setup());
+    LAUNCH(TS_PRE, launch_setup(L.pb, ctx->d.gx, ctx->d.gy, ctx->d.I0p, ctx->d.G0p, ctx->stream));
     (void)P;
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->ws_ready = true;
@@ -712,20 +829,27 @@ pba_status pba_precompute_ic(pba_ctx* ctx)
     if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
     const int F = ctx->F, n6 = 6 * (F - 1);
     LaunchCtx L = make_launch(ctx);
-    // the current parameters become p_0
-    CK(cudaMemcpyAsync(ctx->d.poses0_64, ctx->d.poses64, sizeof(double) * 12 * F, cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.d0_64, ctx->d.d64, sizeof(double) * ctx->Npad, cudaMemcpyDeviceToDevice, ctx->stream));
-    LAUNCH(TS_PRE, launch_ic_precompute(L));
-    LAUNCH(TS_PRE, launch_frame_reduce(L, 0, 21, ctx->d.red_ic, -1, -1, true));
-    LAUNCHN(TS_PRE, launch_schur_sparse(L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, schur_lists(ctx),
-                                        ctx->d.schur_part, ctx->d.Soff, ctx->stream, &nl));
-    LAUNCH(TS_PRE, launch_assemble_S(F, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64,
-                                     ctx->cfg.gauge_anchor_w, ctx->d.S_ic, ctx->d.active_ic, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.chol_work, ctx->d.S_ic, sizeof(double) * n6 * n6, cudaMemcpyDeviceToDevice, ctx->stream));
-    LAUNCHN(TS_PRE, launch_cholesky(ctx->d.chol_work, ctx->d.L_ic, ctx->d.invd_ic, n6, ctx->d.err,
-                                    ctx->stream, &nl));
-    LAUNCH(TS_PRE, launch_chol_inverse(ctx->d.L_ic, ctx->d.invd_ic, ctx->d.Sinv, n6, ctx->stream));
-    pba_status s = check_device_error(ctx);
+    pba_status s = run_enqueued(ctx, GraphKey{G_PRECOMPUTE, 0, ctx->timing}, [&]() -> pba_status {
+        // the current parameters become p_0
+        CK(cudaMemcpyAsync(ctx->d.poses0_64, ctx->d.poses64, sizeof(double) * 12 * F,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d.d0_64, ctx->d.d64, sizeof(double) * ctx->Npad,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+        LAUNCH(TS_PRE, launch_depth_update(L, true, 0));  // FP32 depths of p_0
+        LAUNCH(TS_PRE, launch_ic_precompute(L));
+        LAUNCH(TS_PRE, launch_frame_reduce(L, 0, 21, ctx->d.red_ic, -1, -1, true));
+        LAUNCHN(TS_PRE, launch_schur_sparse(L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, schur_lists(ctx),
+                                            ctx->d.schur_part, ctx->d.Soff, ctx->stream, &nl));
+        LAUNCH(TS_PRE, launch_assemble_S(F, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64,
+                                         ctx->cfg.gauge_anchor_w, ctx->d.S_ic, ctx->d.active_ic,
+                                         ctx->stream, ctx->d.A2));
+        LAUNCH(TS_PRE, launch_ldl(ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv, n6, 0, ctx->d.err,
+                                  ctx->stream));
+        LAUNCH(TS_PRE, launch_ldl_inverse(ctx->d.L2, ctx->d.Linv, ctx->d.rpiv, ctx->d.Sinv, n6, ctx->stream));
+        return PBA_OK;
+    });
+    if (s != PBA_OK) return s;
+    s = check_device_error(ctx);
     if (s != PBA_OK) return s;
     ctx->ic_ready = true;
     return PBA_OK;
@@ -741,13 +865,21 @@ pba_status pba_iterate(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     SolveArgs sa = make_solve(ctx);
     sa.active = ctx->d.active_ic;
     sa.tanchor = ctx->d.poses0_64;
-    for (int k = 0; k < n_iters; ++k) {
-        LAUNCH(TS_PASS, launch_ic_pass(L, true, k > 0, k > 0));
-        LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 6, ctx->d.red_y, k, k - 1, true));
-        LAUNCH(TS_SOLVE, launch_ic_solve_update(sa, ctx->d.Sinv, ctx->d.red_y, 6, 0, ctx->stream));
-    }
-    LAUNCH(TS_EVAL, launch_ic_pass(L, false, n_iters > 0, n_iters > 0));
-    LAUNCH(TS_EVAL, launch_frame_reduce(L, 0, 0, nullptr, n_iters, n_iters - 1, false));
+    pba_status s = run_enqueued(ctx, GraphKey{G_ITERATE, n_iters, ctx->timing}, [&]() -> pba_status {
+        for (int k = 0; k < n_iters; ++k) {
+            LAUNCH(TS_POINT, launch_depth_update(L, true, k > 0));
+            LAUNCH(TS_PASS, launch_ic_residual(L, true, k > 0));
+            LAUNCH(TS_POINT, launch_ic_point(L, true));
+            LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 6, ctx->d.red_y, k, k - 1, true, 6));
+            LAUNCH(TS_SOLVE, launch_ic_solve_update(sa, ctx->d.Sinv, ctx->d.red_y, 6, 0, ctx->stream));
+        }
+        LAUNCH(TS_EVAL, launch_depth_update(L, true, n_iters > 0));
+        LAUNCH(TS_EVAL, launch_ic_residual(L, false, n_iters > 0));
+        LAUNCH(TS_EVAL, launch_ic_point(L, false));
+        LAUNCH(TS_EVAL, launch_frame_reduce(L, 0, 0, nullptr, n_iters, n_iters - 1, false));
+        return PBA_OK;
+    });
+    if (s != PBA_OK) return s;
     ctx->last_fc = 0;
     return copy_stats(ctx, n_iters, stats);
 }
@@ -763,20 +895,28 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     SolveArgs sa = make_solve(ctx);
     sa.active = ctx->d.active_fc;
     sa.tanchor = ctx->d.poses64;
-    for (int k = 0; k < n_iters; ++k) {
-        LAUNCH(TS_PASS, launch_fc_pass(L, true, k > 0, k > 0));
-        LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 27, ctx->d.red_y, k, k - 1, true));
-        LAUNCHN(TS_SCHUR, launch_schur_sparse(L.pb, ctx->d.Hfd_fc, ctx->d.Hnn_fc, schur_lists(ctx),
-                                              ctx->d.schur_part, ctx->d.Soff, ctx->stream, &nl));
-        LAUNCH(TS_SCHUR, launch_assemble_S(F, ctx->d.red_y, 27, ctx->d.Soff, ctx->d.poses64,
-                                           ctx->cfg.gauge_anchor_w, ctx->d.S_fc, ctx->d.active_fc, ctx->stream));
-        CK(cudaMemcpyAsync(ctx->d.chol_work, ctx->d.S_fc, sizeof(double) * n6 * n6, cudaMemcpyDeviceToDevice, ctx->stream));
-        LAUNCHN(TS_SOLVE, launch_cholesky(ctx->d.chol_work, ctx->d.L_fc, ctx->d.invd_fc, n6, ctx->d.err,
-                                          ctx->stream, &nl));
-        LAUNCH(TS_SOLVE, launch_fc_solve_update(sa, ctx->d.L_fc, ctx->d.invd_fc, ctx->d.red_y, 27, 21, ctx->stream));
-    }
-    LAUNCH(TS_EVAL, launch_fc_pass(L, false, n_iters > 0, n_iters > 0));
-    LAUNCH(TS_EVAL, launch_frame_reduce(L, 0, 0, nullptr, n_iters, n_iters - 1, false));
+    pba_status s = run_enqueued(ctx, GraphKey{G_FC, n_iters, ctx->timing}, [&]() -> pba_status {
+        for (int k = 0; k < n_iters; ++k) {
+            LAUNCH(TS_POINT, launch_depth_update(L, false, k > 0));
+            LAUNCH(TS_PASS, launch_fc_residual(L, true, k > 0));
+            LAUNCH(TS_POINT, launch_fc_point(L, true));
+            LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 27, ctx->d.red_y, k, k - 1, true, 27, 21));
+            LAUNCHN(TS_SCHUR, launch_schur_sparse(L.pb, ctx->d.Hfd_fc, ctx->d.Hnn_fc, schur_lists(ctx),
+                                                  ctx->d.schur_part, ctx->d.Soff, ctx->stream, &nl));
+            LAUNCH(TS_SCHUR, launch_assemble_S(F, ctx->d.red_y, 27, ctx->d.Soff, ctx->d.poses64,
+                                               ctx->cfg.gauge_anchor_w, ctx->d.S_fc, ctx->d.active_fc,
+                                               ctx->stream, ctx->d.A2, ctx->d.red_y, 27, 21));
+            LAUNCH(TS_SOLVE, launch_ldl(ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv, n6, 1,
+                                        ctx->d.err, ctx->stream));
+            LAUNCH(TS_SOLVE, launch_fc_solve_update(sa, ctx->d.L2, ctx->d.Linv, ctx->stream));
+        }
+        LAUNCH(TS_EVAL, launch_depth_update(L, false, n_iters > 0));
+        LAUNCH(TS_EVAL, launch_fc_residual(L, false, n_iters > 0));
+        LAUNCH(TS_EVAL, launch_fc_point(L, false));
+        LAUNCH(TS_EVAL, launch_frame_reduce(L, 0, 0, nullptr, n_iters, n_iters - 1, false));
+        return PBA_OK;
+    });
+    if (s != PBA_OK) return s;
     ctx->last_fc = 1;
     return copy_stats(ctx, n_iters, stats);
 }

@@ -19,8 +19,8 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "pba.h")
 
 PBA_F32, PBA_F16, PBA_BF16 = 0, 1, 2
 PBA_MEM_DEVICE, PBA_MEM_HOST = 0, 1
-TIMING_SLOTS = 6
-TIMING_NAMES = ["precompute", "pass", "reduce", "schur", "solve", "eval"]
+TIMING_SLOTS = 7
+TIMING_NAMES = ["precompute", "pass", "reduce", "schur", "solve", "eval", "point"]
 STATUS = {0: "PBA_OK", 1: "PBA_ERR_ARG", 2: "PBA_ERR_STATE", 3: "PBA_ERR_CUDA",
           4: "PBA_ERR_NOMEM", 5: "PBA_ERR_NOT_PD", 6: "PBA_ERR_NONFINITE",
           7: "PBA_ERR_TIMEOUT"}
@@ -104,7 +104,7 @@ class Bundle:
     """
 
     def __init__(self, images, poses0, intrinsics, uv, inv_depth, vis=None, *, pattern,
-                 huber_k, stream=None, gauge_anchor_w=1.0, max_stats_iters=256):
+                 huber_k, stream=None, gauge_anchor_w=1.0, max_stats_iters=256, use_graphs=False):
         import torch
         self.torch = torch
         lib = load()
@@ -116,7 +116,8 @@ class Bundle:
         self._pat = pat
         cfg = Config(float(huber_k), pat.shape[0],
                      pat.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), float(gauge_anchor_w),
-                     0.0, 1, ctypes.c_void_p(stream.cuda_stream), 0, int(max_stats_iters))
+                     0.0, 1, ctypes.c_void_p(stream.cuda_stream), int(bool(use_graphs)),
+                     int(max_stats_iters))
         h = ctypes.c_void_p()
         self._check(lib.pba_create(ctypes.byref(cfg), ctypes.byref(h)), None)
         self.h = h

@@ -248,6 +248,34 @@ def test_runs_are_bitwise_deterministic(torch_cuda):
         assert np.array_equal(x, y)
 
 
+def test_graph_replay_equals_direct_launches(torch_cuda):
+    """cfg.use_graphs: the captured launch sequence, replayed (twice, so the
+    second call runs from the cached graph), gives bit-identical results to
+    direct launches; timing through the graph's event nodes still counts
+    every kernel of the timed slot."""
+    torch = torch_cuda
+    sc = synth.make_scene("ring5")
+    stream = torch.cuda.Stream()
+    out = []
+    for graphs in (False, True):
+        with torch.cuda.stream(stream):
+            b = _bundle(sc, stream=stream, use_graphs=graphs)
+            b.enable_timing(1 << 1)
+            b.precompute_ic()
+            st = b.iterate(4)
+            st_b = b.iterate(4)
+            P, D = b.params()
+            ms, launches, counts = b.timing()
+            st2 = b.solve_fc(2)
+            st2_b = b.solve_fc(2)
+            P2, D2 = b.params()
+            b.close()
+        assert counts["pass"] == 8 and ms["pass"] > 0.0
+        out.append((st, st_b, P, D, st2, st2_b, P2, D2))
+    for x, y in zip(out[0], out[1]):
+        assert np.array_equal(x, y)
+
+
 def test_ragged_tile_single_pixel_pattern_and_empty_rows(torch_cuda):
     """N = 33 (one full tile and a tail of one), a frame that sees no point,
     a point that no frame sees, and a one-pixel pattern."""
