@@ -45,6 +45,7 @@ int g_chol_cluster = 8;
 struct CholSmem {
     dfloat D[kNB][kNB + 1];   // diagonal block: W below the diagonal, pivots d_j on it
     dfloat r[kNB];            // 1 / d_j
+    unsigned short tri[kNB * (kNB - 1) / 2];  // packed index -> (i', m') of the trailing triangle
     dfloat T0[kNB][kNB + 1];  // rows being eliminated / rows i of a trailing tile (L D)
     dfloat T1[kNB][kNB + 1];  // rows j of a trailing tile (L)
 };
@@ -61,19 +62,32 @@ __device__ __forceinline__ dfloat pivot_recip(dfloat& d, bool real, int* err)
 }
 
 // One thread per element of a 32 x 32 block (1024 threads: warp = row,
-// lane = column), so each elimination step costs every thread at most one
-// double-float update and whole warps skip rows that are already done.
+// lane = column) for loads, stores and the trailing tiles. In elimination
+// step j the diagonal block's active elements (j < m <= i) are packed onto
+// the first (31-j)(32-j)/2 threads through a table, and the rows below use
+// the top warps, so no issue slot goes to an element that is already done.
 __global__ void __launch_bounds__(kCholThreads)
-ldl_cluster_kernel(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv, int n, int aug,
-                   int* err)
+ldl_cluster_kernel(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv, const int* cmap,
+                   int F, int aug, int* err)
 {
     __shared__ CholSmem sm;
+    const int n = 6 * cmap[F];  // active frames only (the same value in every CTA)
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank(), C = (int)cl.num_blocks();
     const int tid = threadIdx.x, wi = tid >> 5, lm = tid & 31;
     const int nrow = n + aug;  // rows of A / L (the last one is b^T when aug)
     const int nblk = (n + kNB - 1) / kNB;
     const int nblk_r = (nrow + kNB - 1) / kNB;
+    // triangle enumeration, column-major from the bottom-right corner:
+    // e = m'(m'+1)/2 + i', 0 <= i' <= m', element (31 - i', 31 - m'); the
+    // first s(s+1)/2 entries are the triangle left after step 31 - s
+    if (tid < kNB * (kNB - 1) / 2) {
+        int mp = (int)((sqrtf(8.0f * tid + 1.0f) - 1.0f) * 0.5f);
+        while (mp * (mp + 1) / 2 > tid) --mp;
+        while ((mp + 1) * (mp + 2) / 2 <= tid) ++mp;
+        const int ip = tid - mp * (mp + 1) / 2;
+        sm.tri[tid] = (unsigned short)(ip | (mp << 8));
+    }
     for (int k = 0; k < nblk; ++k) {
         const int k0 = k * kNB, nk = min(kNB, n - k0);
         // rows below the block are split over the CTAs; this CTA eliminates
@@ -99,18 +113,21 @@ ldl_cluster_kernel(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpi
             // diagonal block (first chunk only; later chunks reuse its
             // factor) and the rows below, A_im -= (A_ij / d_j) A_mj
             for (int j = 0; j < kNB - 1; ++j) {
-                if (first && wi > j) {
-                    if (lm > j && lm <= wi) {
-                        const dfloat lij = df_mul(sm.D[wi][j], sm.r[j]);
-                        sm.D[wi][lm] = df_fnms(lij, sm.D[lm][j], sm.D[wi][lm]);
-                        // the owner of (j+1, j+1) has just updated it: next reciprocal
-                        if (wi == j + 1 && lm == j + 1)
-                            sm.r[j + 1] = pivot_recip(sm.D[j + 1][j + 1], j + 1 < nk, err);
-                    }
+                const int s = kNB - 1 - j;  // trailing triangle size
+                if (first && tid < s * (s + 1) / 2) {
+                    const unsigned short te = sm.tri[tid];
+                    const int i = kNB - 1 - (te & 0xff), m = kNB - 1 - (te >> 8);
+                    const dfloat lij = df_mul(sm.D[i][j], sm.r[j]);
+                    dfloat v = df_fnms(lij, sm.D[m][j], sm.D[i][m]);
+                    // the owner of (j+1, j+1) has just formed it: next reciprocal
+                    // straight from the register
+                    if (i == j + 1 && m == j + 1) sm.r[j + 1] = pivot_recip(v, j + 1 < nk, err);
+                    sm.D[i][m] = v;
                 }
-                if (wi < nr && lm > j && lm < nk) {
-                    const dfloat wj = df_mul(sm.T0[wi][j], sm.r[j]);
-                    sm.T0[wi][lm] = df_fnms(wj, sm.D[lm][j], sm.T0[wi][lm]);
+                const int ra = kNB - 1 - wi;  // rows below on the top warps
+                if (ra < nr && lm > j && lm < nk) {
+                    const dfloat wj = df_mul(sm.T0[ra][j], sm.r[j]);
+                    sm.T0[ra][lm] = df_fnms(wj, sm.D[lm][j], sm.T0[ra][lm]);
                 }
                 __syncthreads();
             }
@@ -193,27 +210,53 @@ ldl_cluster_kernel(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpi
     }
 }
 
-// S^-1 = L^-T D^-1 L^-1, one column (= row) per CTA, written as FP64; the
-// forward substitution of e_c starts at c's block.
+// S^-1 = L^-T D^-1 L^-1 in the full 6(F-1) layout, one row per CTA,
+// written as FP64. Rows of active frames: the compact column's forward
+// substitution (starting at its block), scaling and backward substitution,
+// scattered to the full column order (zero for frames left out); rows of
+// frames left out: identity (their block of S is the identity).
 __global__ void __launch_bounds__(256)
-ldl_inverse_kernel(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, double* Sinv, int n)
+ldl_inverse_kernel(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, const int* cmap, int F,
+                   double* Sinv)
 {
     extern __shared__ dfloat xs[];
     __shared__ dfloat t[kLdlBlock];
-    const int c = blockIdx.x;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = df_make(i == c ? 1.0f : 0.0f, 0.0f);
+    __shared__ int s_full[1024], s_out[1024], s_nout;
+    const int n6 = 6 * (F - 1), nc = 6 * cmap[F], c = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int no = 0;
+        for (int f = 1; f < F; ++f) {
+            const int k = cmap[f];
+            if (k >= 0) s_full[k] = f;
+            else s_out[no++] = f;
+        }
+        s_nout = no;
+    }
     __syncthreads();
-    ldl_forward_smem(L, Linv, n, xs, t, c / kLdlBlock);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = df_mul(xs[i], rpiv[i]);
+    if (c >= nc) {
+        const int q = c - nc;  // q-th row of the frames left out
+        if (q / 6 >= s_nout) return;
+        const int row = 6 * (s_out[q / 6] - 1) + q % 6;
+        for (int j = threadIdx.x; j < n6; j += blockDim.x) Sinv[(size_t)row * n6 + j] = j == row ? 1.0 : 0.0;
+        return;
+    }
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) xs[i] = df_make(i == c ? 1.0f : 0.0f, 0.0f);
     __syncthreads();
-    ldl_backward_smem(L, Linv, n, xs, t);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) Sinv[(size_t)c * n + i] = df_to_double(xs[i]);
+    ldl_forward_smem(L, Linv, nc, xs, t, c / kLdlBlock);
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) xs[i] = df_mul(xs[i], rpiv[i]);
+    __syncthreads();
+    ldl_backward_smem(L, Linv, nc, xs, t);
+    const int row = 6 * (s_full[c / 6] - 1) + c % 6;
+    for (int j = threadIdx.x; j < n6; j += blockDim.x) {
+        const int k = cmap[j / 6 + 1];
+        Sinv[(size_t)row * n6 + j] = k >= 0 ? df_to_double(xs[6 * k + j % 6]) : 0.0;
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_ldl(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv, int n, int aug,
-                       int* err, cudaStream_t st)
+cudaError_t launch_ldl(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv, const int* cmap,
+                       int F, int aug, int* err, cudaStream_t st)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(g_chol_cluster);
@@ -227,7 +270,7 @@ cudaError_t launch_ldl(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat*
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, ldl_cluster_kernel, A, L, Linv, dpiv, rpiv, n, aug, err);
+    return cudaLaunchKernelEx(&cfg, ldl_cluster_kernel, A, L, Linv, dpiv, rpiv, cmap, F, aug, err);
 }
 
 cudaError_t ldl_setup()
@@ -251,10 +294,12 @@ cudaError_t ldl_setup()
     return cudaSuccess;
 }
 
-cudaError_t launch_ldl_inverse(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, double* Sinv,
-                               int n, cudaStream_t st)
+cudaError_t launch_ldl_inverse(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, const int* cmap,
+                               int F, double* Sinv, cudaStream_t st)
 {
-    ldl_inverse_kernel<<<n, 256, sizeof(dfloat) * n, st>>>(L, Linv, rpiv, Sinv, n);
+    if (F > 1024) return cudaErrorInvalidValue;
+    const int n6 = 6 * (F - 1);
+    ldl_inverse_kernel<<<n6, 256, sizeof(dfloat) * n6, st>>>(L, Linv, rpiv, cmap, F, Sinv);
     return cudaGetLastError();
 }
 

@@ -84,7 +84,10 @@ __device__ __forceinline__ dfloat df_fnms(dfloat a, dfloat b, dfloat c)
 // y1 = y + y (1 - a y); the seed's relative error (~2^-23) is squared
 __device__ __forceinline__ dfloat df_recip(dfloat a)
 {
-    const float y = 1.0f / a.x;
+    // hardware reciprocal approximation as the seed (the Newton step below
+    // squares its ~2^-22 relative error)
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a.x));
     // 1 - a y with a = hi + lo: fma gives 1 - hi y exactly rounded once
     const float r = fmaf(-a.x, y, 1.0f) - a.y * y;
     return df_norm(y, y * r);

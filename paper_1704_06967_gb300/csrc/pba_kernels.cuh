@@ -86,6 +86,7 @@ struct SolveArgs {
     float* dthsq;           // F
     int* err;
     const int* active;      // [0] anchor frame, [f] frame has residuals
+    const int* cmap;        // [f] compact index of an active frame or -1, [F] their number
     const double* tanchor;  // F*12 poses whose t define the gauge direction
 };
 
@@ -103,26 +104,29 @@ struct SchurLists {
     const int2* items;
     int n_pairs, n_chunks;
 };
-constexpr int kSchurChunk = 16;
+constexpr int kSchurChunk = 32;
 cudaError_t launch_schur_sparse(const DevProblem& pb, const float* Hfd, const float* Hnn,
                                 const SchurLists& sl, float2* part, double* Soff,
                                 cudaStream_t st, int* launches);
-// S (FP64) and, when S2 is given, its double-float copy (the factorisation's
-// working matrix; with rhs, one extra row b = -y taken from
-// rhs[f * rhs_stride + rhs_off + a])
+// S (FP64) and, when S2 is given, its double-float copy over the active
+// frames only (compact order, cmap[f] = compact index or -1, cmap[F] = their
+// number; the factorisation's working matrix; with rhs, one extra row b = -y
+// taken from rhs[f * rhs_stride + rhs_off + a])
 cudaError_t launch_assemble_S(int F, const double* Hff, int hff_stride, const double* Soff,
                               const double* anchor_t, double gauge_w, double* S, int* active,
-                              cudaStream_t st, dfloat* S2 = nullptr, const double* rhs = nullptr,
-                              int rhs_stride = 0, int rhs_off = 0);
+                              cudaStream_t st, dfloat* S2 = nullptr, int* cmap = nullptr,
+                              const double* rhs = nullptr, int rhs_stride = 0, int rhs_off = 0);
 // double-float LDL^T (pba_chol.cu): A ((n + aug) x n, consumed) -> L (unit
 // lower with L^T in the upper triangle; with aug, row n = D^-1 L^-1 b),
 // Linv (inverses of the 32 x 32 diagonal blocks and their transposes),
 // dpiv = d_j, rpiv = 1 / d_j
-cudaError_t launch_ldl(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv, int n, int aug,
-                       int* err, cudaStream_t st);
+// the order n = 6 * cmap[F] is read on the device (the active frames)
+cudaError_t launch_ldl(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv, const int* cmap,
+                       int F, int aug, int* err, cudaStream_t st);
 cudaError_t ldl_setup();  // once per process and device, before any capture
-cudaError_t launch_ldl_inverse(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, double* Sinv,
-                               int n, cudaStream_t st);
+// full 6(F-1) x 6(F-1) S^-1 (identity rows for frames left out)
+cudaError_t launch_ldl_inverse(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, const int* cmap,
+                               int F, double* Sinv, cudaStream_t st);
 cudaError_t launch_ic_solve_update(const SolveArgs& a, const double* Sinv, const double* y,
                                    int y_stride, int y_off, cudaStream_t st);
 cudaError_t launch_fc_solve_update(const SolveArgs& a, const dfloat* L, const dfloat* Linv,

@@ -15,7 +15,9 @@ namespace pba {
 // the prior gauge_w * mu * that that^T goes on the translation block of the
 // first active frame (that = unit translation of that frame in anchor_t).
 // H_ff comes as 21 upper-triangle values per frame at Hff[f*stride].
-// active[f] (f >= 1) receives the frame flags, active[0] the anchor frame.
+// active[f] (f >= 1) receives the frame flags, active[0] the anchor frame;
+// cmap[f] the compact index of an active frame (-1 otherwise) and cmap[F]
+// their number.
 // Every CTA recomputes the flags, mu and the anchor (a few hundred FP64
 // operations) and fills its share of S.
 // ---------------------------------------------------------------------------
@@ -34,9 +36,11 @@ constexpr int kAssembleThreads = 256;
 __global__ void __launch_bounds__(kAssembleThreads)
 assemble_S_kernel(int F, const double* Hff, int stride, const double* Soff,
                   const double* anchor_t, double gauge_w, double* S, int* active, dfloat* S2,
-                  const double* rhs, int rhs_stride, int rhs_off)
+                  int* cmap, const double* rhs, int rhs_stride, int rhs_off)
 {
     __shared__ int s_act[1024];
+    __shared__ int s_cidx[1024];  // compact index of an active frame
+    __shared__ int s_nact;
     __shared__ double s_red[kAssembleThreads / 32];
     __shared__ int s_anchor;
     __shared__ double s_mu;
@@ -61,15 +65,22 @@ assemble_S_kernel(int F, const double* Hff, int stride, const double* Soff,
         for (int w = 0; w < kAssembleThreads / 32; ++w) mu += s_red[w];
         int cnt = 0, anchor = -1;
         for (int f = 1; f < F; ++f) {
+            s_cidx[f] = s_act[f] ? cnt / 6 : -1;
             if (!s_act[f]) continue;
             if (anchor < 0) anchor = f;
             cnt += 6;
         }
         s_mu = cnt ? gauge_w * mu / cnt : 0.0;
         s_anchor = anchor;
+        s_nact = cnt / 6;
         if (blockIdx.x == 0) {
             active[0] = anchor;
             for (int f = 1; f < F; ++f) active[f] = s_act[f];
+            if (cmap) {
+                for (int f = 1; f < F; ++f) cmap[f] = s_cidx[f];
+                cmap[0] = -1;
+                cmap[F] = s_nact;
+            }
         }
     }
     __syncthreads();
@@ -82,6 +93,7 @@ assemble_S_kernel(int F, const double* Hff, int stride, const double* Soff,
             for (int a = 0; a < 3; ++a) th[a] = ta[a] / nt;
     }
     const size_t total = (size_t)n6 * n6;
+    const int nc = 6 * s_nact;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + tid; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(idx / n6), j = (int)(idx % n6);
@@ -98,29 +110,36 @@ assemble_S_kernel(int F, const double* Hff, int stride, const double* Soff,
             }
         }
         S[idx] = v;
-        if (S2) S2[idx] = df_from_double(v);
+        // the double-float working copy holds the active frames only
+        // (compact order, row stride nc): frames without residuals have
+        // identity blocks and a zero update, so they are left out of the
+        // factorisation
+        if (S2 && s_act[fi] && s_act[fj])
+            S2[(size_t)(6 * s_cidx[fi] + i % 6) * nc + 6 * s_cidx[fj] + j % 6] = df_from_double(v);
     }
-    // augmented row n6 of the double-float copy: b = -y (0 for frames without
-    // residuals), eliminated with the matrix by the factorisation
+    // augmented row nc of the double-float copy: b = -y, eliminated with the
+    // matrix by the factorisation
     if (S2 && rhs)
         for (int j = blockIdx.x * blockDim.x + tid; j < n6; j += gridDim.x * blockDim.x) {
             const int f = j / 6 + 1;
-            S2[total + j] = s_act[f] ? df_from_double(-rhs[(size_t)f * rhs_stride + rhs_off + j % 6])
-                                     : df_make(0.0f, 0.0f);
+            if (s_act[f])
+                S2[(size_t)nc * nc + 6 * s_cidx[f] + j % 6] =
+                    df_from_double(-rhs[(size_t)f * rhs_stride + rhs_off + j % 6]);
         }
 }
 
 cudaError_t launch_assemble_S(int F, const double* Hff, int hff_stride, const double* Soff,
                               const double* anchor_t, double gauge_w, double* S, int* active,
-                              cudaStream_t st, dfloat* S2, const double* rhs, int rhs_stride,
-                              int rhs_off)
+                              cudaStream_t st, dfloat* S2, int* cmap, const double* rhs,
+                              int rhs_stride, int rhs_off)
 {
+    if (S2 && !cmap) return cudaErrorInvalidValue;
     const int n6 = 6 * (F - 1);
     if (F > 1024) return cudaErrorInvalidValue;
     const int blocks = std::max(1, std::min(148, (n6 * n6 + 4 * kAssembleThreads - 1) / (4 * kAssembleThreads)));
     assemble_S_kernel<<<blocks, kAssembleThreads, 0, st>>>(F, Hff, hff_stride, Soff, anchor_t,
-                                                            gauge_w, S, active, S2, rhs, rhs_stride,
-                                                            rhs_off);
+                                                            gauge_w, S, active, S2, cmap, rhs,
+                                                            rhs_stride, rhs_off);
     return cudaGetLastError();
 }
 
@@ -378,11 +397,15 @@ __global__ void __launch_bounds__(kFcSolveWarps * 32) fc_solve_update_kernel(Sol
     __shared__ double s_alpha;
     __shared__ double sh[kFcSolveWarps][54];
     __shared__ double dsh[kFcSolveWarps][6];
-    const int n = a.n6, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < n; i += blockDim.x) xs[i] = L[(size_t)n * n + i];
+    const int n = a.n6, nc = 6 * a.cmap[a.F], tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < nc; i += blockDim.x) xs[i] = L[(size_t)nc * nc + i];
     __syncthreads();
-    ldl_backward_smem(L, Linv, n, xs, tb);
-    for (int i = tid; i < n; i += blockDim.x) x[i] = df_to_double(xs[i]);
+    ldl_backward_smem(L, Linv, nc, xs, tb);
+    // back to the full frame order (frames left out get no update)
+    for (int i = tid; i < n; i += blockDim.x) {
+        const int k = a.cmap[i / 6 + 1];
+        x[i] = k >= 0 ? df_to_double(xs[6 * k + i % 6]) : 0.0;
+    }
     __syncthreads();
     if (tid == 0) {
         const int anchor = a.active[0];

@@ -118,7 +118,7 @@ struct pba_ctx {
         int *pair_fg, *pair_chunk, *chunk_pair, *chunk_start;
         int2* pair_items;
         float2* schur_part;
-        int *active_ic, *active_fc;
+        int *active_ic, *active_fc, *cmap;
         int* err;
         double* stats;
     } d{};
@@ -334,6 +334,7 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.schur_part, c->chunk_pair.size() * 36 * sizeof(float2));
     take(c->d.active_ic, F * 4);
     take(c->d.active_fc, F * 4);
+    take(c->d.cmap, (F + 1) * 4);
     take(c->d.err, 64);
     take(c->d.stats, (size_t)(c->stats_slots) * kStats * 8);
     return off;
@@ -521,6 +522,7 @@ SolveArgs make_solve(pba_ctx* c)
     a.poses0 = c->d.poses0_64;
     a.dtheta64 = c->d.dtheta64;
     a.dth2 = c->d.dth2;
+    a.cmap = c->d.cmap;
     a.fc = c->d.fc;
     a.fc_prev = c->d.fc_prev;
     a.dthsq = c->d.dthsq;
@@ -696,7 +698,7 @@ pba_status pba_set_frames(pba_ctx* ctx, int bundle, int n_frames, int w, int h, 
     if (dtype != PBA_F32 && dtype != PBA_F16 && dtype != PBA_BF16)
         return fail(ctx, PBA_ERR_ARG, "invalid dtype");
     if (mem != PBA_MEM_DEVICE && mem != PBA_MEM_HOST) return fail(ctx, PBA_ERR_ARG, "invalid memory kind");
-    if (6 * (n_frames - 1) > 6 * 1024) return fail(ctx, PBA_ERR_ARG, "too many frames");
+    if (n_frames > 1024) return fail(ctx, PBA_ERR_ARG, "at most 1024 frames");
     if ((double)n_frames * h * pitch_elems >= 2147483648.0)
         return fail(ctx, PBA_ERR_ARG, "image stack too large (F * h * pitch must stay below 2^31)");
     if (mem == PBA_MEM_DEVICE && ((uintptr_t)images % elem_size(dtype)))
@@ -827,7 +829,7 @@ pba_status pba_precompute_ic(pba_ctx* ctx)
 {
     if (!ctx) return PBA_ERR_ARG;
     if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
-    const int F = ctx->F, n6 = 6 * (F - 1);
+    const int F = ctx->F;
     LaunchCtx L = make_launch(ctx);
     pba_status s = run_enqueued(ctx, GraphKey{G_PRECOMPUTE, 0, ctx->timing}, [&]() -> pba_status {
         // the current parameters become p_0
@@ -842,10 +844,11 @@ pba_status pba_precompute_ic(pba_ctx* ctx)
                                             ctx->d.schur_part, ctx->d.Soff, ctx->stream, &nl));
         LAUNCH(TS_PRE, launch_assemble_S(F, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64,
                                          ctx->cfg.gauge_anchor_w, ctx->d.S_ic, ctx->d.active_ic,
-                                         ctx->stream, ctx->d.A2));
-        LAUNCH(TS_PRE, launch_ldl(ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv, n6, 0, ctx->d.err,
-                                  ctx->stream));
-        LAUNCH(TS_PRE, launch_ldl_inverse(ctx->d.L2, ctx->d.Linv, ctx->d.rpiv, ctx->d.Sinv, n6, ctx->stream));
+                                         ctx->stream, ctx->d.A2, ctx->d.cmap));
+        LAUNCH(TS_PRE, launch_ldl(ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv, ctx->d.cmap,
+                                  F, 0, ctx->d.err, ctx->stream));
+        LAUNCH(TS_PRE, launch_ldl_inverse(ctx->d.L2, ctx->d.Linv, ctx->d.rpiv, ctx->d.cmap, F, ctx->d.Sinv,
+                                          ctx->stream));
         return PBA_OK;
     });
     if (s != PBA_OK) return s;
@@ -890,7 +893,7 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
     if (n_iters < 0 || n_iters > ctx->cfg.max_stats_iters)
         return fail(ctx, PBA_ERR_ARG, "n_iters must be in [0, %d]", ctx->cfg.max_stats_iters);
-    const int F = ctx->F, n6 = 6 * (F - 1);
+    const int F = ctx->F;
     LaunchCtx L = make_launch(ctx);
     SolveArgs sa = make_solve(ctx);
     sa.active = ctx->d.active_fc;
@@ -905,9 +908,9 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
                                                   ctx->d.schur_part, ctx->d.Soff, ctx->stream, &nl));
             LAUNCH(TS_SCHUR, launch_assemble_S(F, ctx->d.red_y, 27, ctx->d.Soff, ctx->d.poses64,
                                                ctx->cfg.gauge_anchor_w, ctx->d.S_fc, ctx->d.active_fc,
-                                               ctx->stream, ctx->d.A2, ctx->d.red_y, 27, 21));
-            LAUNCH(TS_SOLVE, launch_ldl(ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv, n6, 1,
-                                        ctx->d.err, ctx->stream));
+                                               ctx->stream, ctx->d.A2, ctx->d.cmap, ctx->d.red_y, 27, 21));
+            LAUNCH(TS_SOLVE, launch_ldl(ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv,
+                                        ctx->d.cmap, F, 1, ctx->d.err, ctx->stream));
             LAUNCH(TS_SOLVE, launch_fc_solve_update(sa, ctx->d.L2, ctx->d.Linv, ctx->stream));
         }
         LAUNCH(TS_EVAL, launch_depth_update(L, false, n_iters > 0));

@@ -51,14 +51,69 @@ __device__ __forceinline__ void pair_add(float& s, float& c, float s2, float c2)
 
 constexpr int kSchurWarps = 4;
 
+// Lane-sums of the 36 unevaluated pairs of a warp, in a fixed order. The
+// first 32 go through a reduce-scatter (at each of the five levels a lane
+// keeps half of its values and adds its partner's copy of them: 31 pair
+// exchanges instead of 32 x 5); the last 4 through butterflies. Lane l ends
+// with value l of the first 32 (returned in *v0, its index in *k0) and, on
+// every lane, values 32..35 in s[32..35], c[32..35].
+__device__ __forceinline__ void warp_reduce_36(float (&s)[36], float (&c)[36], int lane, float2* v0,
+                                               int* k0)
+{
+#pragma unroll
+    for (int lvl = 0; lvl < 5; ++lvl) {
+        const int o = 16 >> lvl, half = 16 >> lvl;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            // keep k (lower) or k + half (upper); send the other
+            const float ss = up ? s[k] : s[k + half], sc = up ? c[k] : c[k + half];
+            const float ks = up ? s[k + half] : s[k], kc = up ? c[k + half] : c[k];
+            const float rs = __shfl_xor_sync(0xffffffffu, ss, o);
+            const float rc = __shfl_xor_sync(0xffffffffu, sc, o);
+            float a = ks, b = kc;
+            // the lower lane adds (its value, partner's) and the upper lane
+            // (partner's, its value) in the same order
+            if (up) {
+                a = rs;
+                b = rc;
+                pair_add(a, b, ks, kc);
+            } else {
+                pair_add(a, b, rs, rc);
+            }
+            s[k] = a;
+            c[k] = b;
+        }
+    }
+    // level with stride o kept the upper half iff lane bit o is set, so
+    // after the five levels lane l holds value index l
+    *v0 = make_float2(s[0], c[0]);
+    *k0 = lane;
+#pragma unroll
+    for (int k = 32; k < 36; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float a2 = __shfl_xor_sync(0xffffffffu, s[k], o);
+            const float b2 = __shfl_xor_sync(0xffffffffu, c[k], o);
+            if (lane & o) {
+                float a = a2, b = b2;
+                pair_add(a, b, s[k], c[k]);
+                s[k] = a;
+                c[k] = b;
+            } else {
+                pair_add(s[k], c[k], a2, b2);
+            }
+        }
+    }
+}
+
 // chunk c covers items [chunk_start[c], chunk_start[c+1]) of one frame pair;
 // it writes 36 unevaluated pairs (s, c) to part[c].
 __global__ void __launch_bounds__(32 * kSchurWarps)
 schur_chunk_kernel(DevProblem pb, const float* Hfd, const float* Hnn, const int* chunk_start,
                    const int2* items, float2* part)
 {
-    __shared__ float red_s[kSchurWarps][36];
-    __shared__ float red_c[kSchurWarps][36];
+    __shared__ float2 red[kSchurWarps][36];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ch = blockIdx.x;
     const int i0 = chunk_start[ch], i1 = chunk_start[ch + 1];
@@ -89,26 +144,25 @@ schur_chunk_kernel(DevProblem pb, const float* Hfd, const float* Hnn, const int*
 #pragma unroll
             for (int b = 0; b < 6; ++b) acc_product(s[6 * a + b], c[6 * a + b], ha[a], hb[b], ih);
     }
-    // fixed-order reduction of the pairs: lanes (butterfly), then warps
+    float2 v0;
+    int k0;
+    warp_reduce_36(s, c, lane, &v0, &k0);
+    red[warp][k0] = v0;
+    if (lane < 4) {
+        float a = s[32], b = c[32];
 #pragma unroll
-    for (int k = 0; k < 36; ++k) {
-        float a = s[k], b = c[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float a2 = __shfl_xor_sync(0xffffffffu, a, o);
-            const float b2 = __shfl_xor_sync(0xffffffffu, b, o);
-            pair_add(a, b, a2, b2);
-        }
-        if (lane == 0) {
-            red_s[warp][k] = a;
-            red_c[warp][k] = b;
-        }
+        for (int k = 33; k < 36; ++k)
+            if (lane == k - 32) {
+                a = s[k];
+                b = c[k];
+            }
+        red[warp][32 + lane] = make_float2(a, b);
     }
     __syncthreads();
     if (threadIdx.x < 36) {
         const int k = threadIdx.x;
-        float vs = red_s[0][k], vc = red_c[0][k];
-        for (int w = 1; w < kSchurWarps; ++w) pair_add(vs, vc, red_s[w][k], red_c[w][k]);
+        float vs = red[0][k].x, vc = red[0][k].y;
+        for (int w = 1; w < kSchurWarps; ++w) pair_add(vs, vc, red[w][k].x, red[w][k].y);
         part[(size_t)ch * 36 + k] = make_float2(vs, vc);
     }
 }
