@@ -339,7 +339,7 @@ def run_ours(args):
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
                 "traffic": None, "algorithmic_bytes_per_launch": alg_bytes,
                 "avg_launch_ms": pass_ms, "launches": int(kcounts["pass"])}
-    traffic_file = os.path.join(ROOT, "profiles", "ic_residual_traffic.json")
+    traffic_file = os.path.join(ROOT, "profiles", "ic_residual_helix30_traffic.txt")
     if os.path.exists(traffic_file):
         try:
             tr = json.load(open(traffic_file))
@@ -414,10 +414,15 @@ def run_ours(args):
 
 
 def kernel_sha():
+    """Hash of the residual kernel's own source text and the device helpers it
+    uses: the stored DRAM traffic applies only while these are unchanged."""
     import hashlib
-    h = hashlib.sha256()
-    for name in ("pba_iter.cu", "pba_internal.cuh", "pba_kernels.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1704_06967_gb300", "csrc", name), "rb").read())
+    csrc = os.path.join(ROOT, "paper_1704_06967_gb300", "csrc")
+    src = open(os.path.join(csrc, "pba_iter.cu")).read()
+    start = src.index("ic_residual_kernel(DevProblem pb")
+    end = src.index("\n}\n", start)
+    h = hashlib.sha256(src[start:end].encode())
+    h.update(open(os.path.join(csrc, "pba_internal.cuh"), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -210,47 +210,25 @@ ldl_cluster_kernel(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpi
     }
 }
 
-// S^-1 = L^-T D^-1 L^-1 in the full 6(F-1) layout, one row per CTA,
-// written as FP64. Rows of active frames: the compact column's forward
-// substitution (starting at its block), scaling and backward substitution,
-// scattered to the full column order (zero for frames left out); rows of
-// frames left out: identity (their block of S is the identity).
+// S^-1 = L^-T D^-1 L^-1 over the active frames (compact nc x nc order,
+// double-float), one column (= row) per CTA: the column's forward
+// substitution (starting at its block), scaling and backward substitution.
+// CTAs beyond nc (the grid is sized for all frames) return at once.
 __global__ void __launch_bounds__(256)
 ldl_inverse_kernel(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, const int* cmap, int F,
-                   double* Sinv)
+                   dfloat* Sinv)
 {
     extern __shared__ dfloat xs[];
     __shared__ dfloat t[kLdlBlock];
-    __shared__ int s_full[1024], s_out[1024], s_nout;
-    const int n6 = 6 * (F - 1), nc = 6 * cmap[F], c = blockIdx.x;
-    if (threadIdx.x == 0) {
-        int no = 0;
-        for (int f = 1; f < F; ++f) {
-            const int k = cmap[f];
-            if (k >= 0) s_full[k] = f;
-            else s_out[no++] = f;
-        }
-        s_nout = no;
-    }
-    __syncthreads();
-    if (c >= nc) {
-        const int q = c - nc;  // q-th row of the frames left out
-        if (q / 6 >= s_nout) return;
-        const int row = 6 * (s_out[q / 6] - 1) + q % 6;
-        for (int j = threadIdx.x; j < n6; j += blockDim.x) Sinv[(size_t)row * n6 + j] = j == row ? 1.0 : 0.0;
-        return;
-    }
+    const int nc = 6 * cmap[F], c = blockIdx.x;
+    if (c >= nc) return;
     for (int i = threadIdx.x; i < nc; i += blockDim.x) xs[i] = df_make(i == c ? 1.0f : 0.0f, 0.0f);
     __syncthreads();
     ldl_forward_smem(L, Linv, nc, xs, t, c / kLdlBlock);
     for (int i = threadIdx.x; i < nc; i += blockDim.x) xs[i] = df_mul(xs[i], rpiv[i]);
     __syncthreads();
     ldl_backward_smem(L, Linv, nc, xs, t);
-    const int row = 6 * (s_full[c / 6] - 1) + c % 6;
-    for (int j = threadIdx.x; j < n6; j += blockDim.x) {
-        const int k = cmap[j / 6 + 1];
-        Sinv[(size_t)row * n6 + j] = k >= 0 ? df_to_double(xs[6 * k + j % 6]) : 0.0;
-    }
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) Sinv[(size_t)c * nc + j] = xs[j];
 }
 
 }  // namespace
@@ -295,7 +273,7 @@ cudaError_t ldl_setup()
 }
 
 cudaError_t launch_ldl_inverse(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, const int* cmap,
-                               int F, double* Sinv, cudaStream_t st)
+                               int F, dfloat* Sinv, cudaStream_t st)
 {
     if (F > 1024) return cudaErrorInvalidValue;
     const int n6 = 6 * (F - 1);

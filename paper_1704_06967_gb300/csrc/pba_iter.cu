@@ -1,6 +1,5 @@
 // IC iteration kernels (Sec. 3.5 steps 1-3 with the J, W_0 and H fixed by
-// the precompute at p_0). An iteration is three launches, none of which
-// waits on another part of the grid:
+// the precompute at p_0), none of which waits on another part of the grid:
 //   depth_update_kernel  one CTA per tile: back-substitution of the previous
 //                        step's depth update (Sec. 3.5 step 3, point block)
 //                        and the depth rule (IC: Sec. 3.6; FC: d <- d + Dd);
@@ -9,13 +8,18 @@
 //                        share of g_f = sum J_theta^T w r and of g_d;
 //   ic_point_kernel      one CTA per tile: g_d per point (entries added in
 //                        tile order), the Schur right-hand-side correction
-//                        sum_n H_fd g_d / H_dd per entry, and the tile
-//                        statistics.
+//                        sum_n H_fd g_d / H_dd per entry, the tile
+//                        statistics;
+// then the frame reduction of y (pba_pass.cu) and ic_solve_kernel (CTA per
+// frame: Dtheta = -S^-1 y). The pose updates of a step run in the next
+// depth_update_kernel, one frame per CTA.
 // A tile has about ten entries, so a CTA per tile (earlier design) left its
 // warps waiting at barriers between the phases; a warp per entry gives the
 // scheduler ~6k independent warps whose image taps are all in flight at once.
 // Every sum has a fixed order: results are deterministic run to run.
 #include "pba_kernels.cuh"
+#include "pba_pose.cuh"
+#include "pba_reduce.cuh"
 
 namespace pba {
 
@@ -63,10 +67,22 @@ __global__ void __launch_bounds__(kTileWarps * 32)
 depth_update_kernel(DevProblem pb, DepthState ds, const float2* __restrict__ dth2,
                     const double* __restrict__ inv_hnn, const double* __restrict__ inv_d0,
                     float* __restrict__ dcur, float* __restrict__ dprev, float* __restrict__ ddsq_t,
-                    int apply)
+                    int apply, SolveArgs a)
 {
     __shared__ float2 red[kTileWarps][32];
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (t >= pb.T) {
+        // CTA T + f - 1: pose update of frame f with the update the solve
+        // wrote (FP64; one frame per CTA, spread over the SMs)
+        __shared__ double sh[54], d[6];
+        const int f = t - pb.T + 1;
+        if (warp != 0) return;
+        if (lane < 6) d[lane] = a.dtheta64[6 * f + lane];
+        __syncwarp();
+        if (kIcRule) ic_pose_update_warp(a, f, a.poses64 + 12 * f, a.poses0 + 12 * f, d, sh, lane);
+        else fc_pose_update_warp(a, f, d, sh, lane);
+        return;
+    }
     const int n = t * kTile + lane;
     // warp 0's per-point operands, fetched before the entry loop so their
     // latency overlaps it
@@ -140,6 +156,27 @@ depth_update_kernel(DevProblem pb, DepthState ds, const float2* __restrict__ dth
     ddsq = warp_sum1(ddsq);
     if (lane == 0) ddsq_t[t] = ddsq;
 }
+
+// Statistics of tile t from its entries' (energy, r^2, count, max
+// displacement) and the tile's sum of Dd^2; lanes take entries, then a
+// butterfly (fixed order).
+__device__ __forceinline__ void tile_stats_from_entries(const DevProblem& pb, const float4* estats,
+                                                        const float* ddsq_t, TileStats* out, int t,
+                                                        int e0, int e1, int lane)
+{
+    float s[3] = {0, 0, 0}, m = 0.0f;
+    for (int e = e0 + lane; e < e1; e += 32) {
+        const float4 v = __ldcg(estats + e);
+        s[0] += v.x;
+        s[1] += v.y;
+        s[2] += v.z;
+        m = fmaxf(m, v.w);
+    }
+    warp_sum<3>(s);
+    m = warp_max1(m);
+    if (lane == 0) out[t] = TileStats{s[0], s[1], s[2], m, ddsq_t[t], 0, 0, 0};
+}
+
 
 // ---------------------------------------------------------------------------
 // IC residuals of one entry (Sec. 3.5 steps 1-2). Lane l is point 32 t + l of
@@ -454,26 +491,6 @@ fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
     }
 }
 
-// Statistics of tile t from its entries' (energy, r^2, count, max
-// displacement) and the tile's sum of Dd^2; lanes take entries, then a
-// butterfly (fixed order).
-__device__ __forceinline__ void tile_stats_from_entries(const DevProblem& pb, const float4* estats,
-                                                        const float* ddsq_t, TileStats* out, int t,
-                                                        int e0, int e1, int lane)
-{
-    float s[3] = {0, 0, 0}, m = 0.0f;
-    for (int e = e0 + lane; e < e1; e += 32) {
-        const float4 v = estats[e];
-        s[0] += v.x;
-        s[1] += v.y;
-        s[2] += v.z;
-        m = fmaxf(m, v.w);
-    }
-    warp_sum<3>(s);
-    m = warp_max1(m);
-    if (lane == 0) out[t] = TileStats{s[0], s[1], s[2], m, ddsq_t[t], 0, 0, 0};
-}
-
 // ---------------------------------------------------------------------------
 // Per tile: g_n = sum over the tile's entries of J_d^T w r (fixed entry
 // order; FC also sums H_dd = J_d^T w J_d the same way), then the Schur
@@ -553,15 +570,176 @@ point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __rest
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_depth_update(const LaunchCtx& L, bool ic_rule, int apply)
+// IC solve (Sec. 3.5 step 4): Dtheta = -S^-1 y, one CTA per target frame:
+// nine warps take the frame's six rows and the anchor frame's three
+// translation rows of the compact S^-1 (double-float GEMV against y), then
+// the exact gauge constraint and the frame's update are written (the pose
+// update itself follows in the next launch, one frame per CTA). Frames
+// without residuals get a zero update.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(9 * 32)
+ic_solve_kernel(SolveArgs a, const dfloat* __restrict__ Sinv, const double* __restrict__ y)
+{
+    extern __shared__ dfloat ys[];  // nc, compact order; then F ints
+    __shared__ double dth[9], d[6];
+    const int F = a.F, f = blockIdx.x + 1, lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    const int kf = a.cmap[f], nc = 6 * a.cmap[F], anchor = a.active[0];
+    int* frame_of = reinterpret_cast<int*>(ys + 6 * (F - 1));
+    if (kf < 0) {
+        if (row == 0) {
+            if (lane < 6) d[lane] = 0.0;
+            __syncwarp();
+            write_update_lanes(a, f, d, lane);
+        }
+        return;
+    }
+    for (int g = 1 + threadIdx.x; g < F; g += blockDim.x) {
+        const int k = a.cmap[g];
+        if (k >= 0) frame_of[k] = g;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < nc; c += blockDim.x)
+        ys[c] = df_from_double(y[(size_t)frame_of[c / 6] * 6 + c % 6]);
+    __syncthreads();
+    const int r = row < 6 ? 6 * kf + row : (anchor > 0 ? 6 * a.cmap[anchor] + row - 6 : -1);
+    if (r >= 0) {
+        DfAcc acc;
+        const dfloat* Sr = Sinv + (size_t)r * nc;
+        for (int c = lane; c < nc; c += 32) acc.add_prod(Sr[c], ys[c]);
+        float ss = acc.s, cc = acc.c;
+        warp_sum_pair(ss, cc);
+        if (lane == 0) dth[row] = -((double)ss + (double)cc);
+    }
+    __syncthreads();
+    if (row != 0) return;
+    if (lane < 6) {
+        double v = dth[lane];
+        if (lane < 3 && anchor > 0) v = fma(-gauge_alpha(a.tanchor + 12 * anchor + 9, dth + 6), a.tanchor[12 * f + 9 + lane], v);
+        d[lane] = v;
+    }
+    __syncwarp();
+    const bool ok = __all_sync(0xffffffffu, lane >= 6 || isfinite(d[lane]));
+    if (!ok) {
+        if (lane == 0) atomicOr(a.err, kErrNonFinite);
+        if (lane < 6) d[lane] = 0.0;
+        __syncwarp();
+    }
+    write_update_lanes(a, f, d, lane);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+// IC step (Sec. 3.5 steps 3-4, Sec. 3.6) in one launch of F CTAs: CTA f-1
+// sums frame f's right-hand side y_f = sum_e (g_f,e - c_e) over its entries
+// in a fixed order, CTA F-1 folds the statistics; the CTA that finishes last
+// (a ticket drawn after a memory fence; nothing waits) forms
+// Dtheta = -S^-1 y over the active frames as a double-float GEMV (S^-1 in
+// compact order; a warp takes four rows at once so their loads share one
+// round trip), imposes the exact gauge constraint and writes the update;
+// the pose updates run in the next launch (depth_update_kernel), one frame
+// per CTA.
+// ---------------------------------------------------------------------------
+constexpr int kStepThreads = 1024;
+constexpr int kStepWarps = kStepThreads / 32;
+
+__global__ void __launch_bounds__(kStepThreads)
+ic_step_kernel(DevProblem pb, const float* __restrict__ ent_part, const TileStats* __restrict__ tstats,
+               const float* __restrict__ dthsq, double* __restrict__ stats, int slot_cur, int slot_prev,
+               SolveArgs a, const dfloat* __restrict__ Sinv, dfloat* y2, unsigned* ticket)
+{
+    extern __shared__ double tail_smem[];
+    __shared__ unsigned s_ticket;
+    __shared__ double s_alpha;
+    __shared__ double dsh[kStepWarps][6];
+    const int F = pb.F, n6 = 6 * (F - 1), tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if ((int)blockIdx.x < F - 1) {
+        const int f = blockIdx.x + 1;
+        float vs, vc;
+        frame_rows_sum<6, 6, 0, kStepThreads>(pb, ent_part, f, vs, vc);
+        if (tid < 6) y2[6 * (f - 1) + tid] = df_norm(vs, vc);
+    } else {
+        stats_block<kStepThreads>(pb, tstats, dthsq, stats, slot_cur, slot_prev);
+    }
+    // the last CTA to finish takes the solve
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_ticket = atomicAdd(ticket, 1u);
+    __syncthreads();
+    if (s_ticket != gridDim.x - 1) return;
+    __threadfence();
+    const int nc = 6 * a.cmap[F];
+    double* dth = tail_smem;                                     // n6, full order
+    double* dthc = tail_smem + n6;                               // nc, compact order
+    dfloat* ys = reinterpret_cast<dfloat*>(tail_smem + 2 * n6);  // nc, compact order
+    for (int i = tid; i < n6; i += kStepThreads) {
+        const int k = a.cmap[i / 6 + 1];
+        if (k >= 0) ys[6 * k + i % 6] = __ldcg(y2 + i);
+    }
+    __syncthreads();
+    for (int r0 = warp; r0 < nc; r0 += 4 * kStepWarps) {
+        DfAcc acc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = r0 + u * kStepWarps;
+            if (r < nc) {
+                const dfloat* Sr = Sinv + (size_t)r * nc;
+                for (int c = lane; c < nc; c += 32) acc[u].add_prod(Sr[c], ys[c]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float ss = acc[u].s, cc = acc[u].c;
+            warp_sum_pair(ss, cc);
+            const int r = r0 + u * kStepWarps;
+            if (lane == 0 && r < nc) dthc[r] = -((double)ss + (double)cc);
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < n6; i += kStepThreads) {
+        const int k = a.cmap[i / 6 + 1];
+        dth[i] = k >= 0 ? dthc[6 * k + i % 6] : 0.0;
+    }
+    __syncthreads();
+    const int anchor = a.active[0];
+    if (tid == 0) {
+        s_alpha = anchor > 0 ? gauge_alpha(a.tanchor + 12 * anchor + 9, dth + 6 * (anchor - 1)) : 0.0;
+        *ticket = 0u;  // ready for the next launch
+    }
+    __syncthreads();
+    for (int f = 1 + warp; f < F; f += kStepWarps) {
+        double* d = dsh[warp];
+        if (lane < 6) {
+            double v = dth[6 * (f - 1) + lane];
+            if (lane < 3 && anchor > 0 && a.active[f]) v = fma(-s_alpha, a.tanchor[12 * f + 9 + lane], v);
+            d[lane] = v;
+        }
+        __syncwarp();
+        const bool ok = __all_sync(0xffffffffu, lane >= 6 || isfinite(d[lane]));
+        if (!ok) {
+            if (lane == 0) atomicOr(a.err, kErrNonFinite);
+            if (lane < 6) d[lane] = 0.0;
+            __syncwarp();
+        }
+        write_update_lanes(a, f, d, lane);
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_depth_update(const LaunchCtx& L, const SolveArgs& a, bool ic_rule, int apply)
 {
     const DepthState& ds = ic_rule ? L.ds_ic : L.ds_fc;
+    const int grid = L.pb.T + (apply ? L.pb.F - 1 : 0);  // + one CTA per frame's pose update
     if (ic_rule)
-        depth_update_kernel<true><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
-            L.pb, ds, L.fs.dth2, L.ic.inv_hnn, L.ic.inv_d0, L.it.dcur, L.it.dprev, L.it.ddsq_t, apply);
+        depth_update_kernel<true><<<grid, kTileWarps * 32, 0, L.stream>>>(
+            L.pb, ds, L.fs.dth2, L.ic.inv_hnn, L.ic.inv_d0, L.it.dcur, L.it.dprev, L.it.ddsq_t,
+            apply, a);
     else
-        depth_update_kernel<false><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
-            L.pb, ds, L.fs.dth2, nullptr, nullptr, L.it.dcur, L.it.dprev, L.it.ddsq_t, apply);
+        depth_update_kernel<false><<<grid, kTileWarps * 32, 0, L.stream>>>(
+            L.pb, ds, L.fs.dth2, nullptr, nullptr, L.it.dcur, L.it.dprev, L.it.ddsq_t, apply, a);
     return cudaGetLastError();
 }
 
@@ -591,19 +769,6 @@ cudaError_t launch_ic_residual(const LaunchCtx& L, bool accum, int have_prev)
 #undef PBA_C
 }
 
-cudaError_t launch_ic_point(const LaunchCtx& L, bool accum)
-{
-    if (accum)
-        point_kernel<true, false><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
-            L.pb, L.it.gpart, L.ic.Hfd, L.ic.Hnn, L.ds_ic.gn, L.ent_part, 6, L.it.estats, L.it.ddsq_t,
-            L.tstats);
-    else
-        point_kernel<false, false><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
-            L.pb, L.it.gpart, L.ic.Hfd, L.ic.Hnn, L.ds_ic.gn, L.ent_part, 6, L.it.estats, L.it.ddsq_t,
-            L.tstats);
-    return cudaGetLastError();
-}
-
 template <int PMAX, bool A, int DT>
 static cudaError_t fc_residual_p(const LaunchCtx& L, int have_prev)
 {
@@ -630,6 +795,19 @@ cudaError_t launch_fc_residual(const LaunchCtx& L, bool accum, int have_prev)
 #undef PBA_C
 }
 
+cudaError_t launch_ic_point(const LaunchCtx& L, bool accum)
+{
+    if (accum)
+        point_kernel<true, false><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
+            L.pb, L.it.gpart, L.ic.Hfd, L.ic.Hnn, L.ds_ic.gn, L.ent_part, 6, L.it.estats, L.it.ddsq_t,
+            L.tstats);
+    else
+        point_kernel<false, false><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
+            L.pb, L.it.gpart, L.ic.Hfd, L.ic.Hnn, L.ds_ic.gn, L.ent_part, 6, L.it.estats, L.it.ddsq_t,
+            L.tstats);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fc_point(const LaunchCtx& L, bool accum)
 {
     if (accum)
@@ -640,6 +818,13 @@ cudaError_t launch_fc_point(const LaunchCtx& L, bool accum)
         point_kernel<false, true><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
             L.pb, L.it.gpart, L.Hfd_fc, L.ds_fc.Hnn, L.ds_fc.gn, L.ent_part, 27, L.it.estats,
             L.it.ddsq_t, L.tstats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ic_solve(const SolveArgs& a, const dfloat* Sinv, const double* y, cudaStream_t st)
+{
+    const int F = a.F;
+    ic_solve_kernel<<<F - 1, 9 * 32, sizeof(dfloat) * 6 * (F - 1) + sizeof(int) * F, st>>>(a, Sinv, y);
     return cudaGetLastError();
 }
 

@@ -61,15 +61,12 @@ struct LaunchCtx {
 };
 
 cudaError_t launch_ic_precompute(const LaunchCtx& L);
-cudaError_t launch_depth_update(const LaunchCtx& L, bool ic_rule, int apply);
 cudaError_t launch_ic_residual(const LaunchCtx& L, bool accum, int have_prev);
-cudaError_t launch_ic_point(const LaunchCtx& L, bool accum);
 // out[f * ncomp + k] = sum over frame f's entries of part[off + k]
 // (minus part[sub + k - sub_from] for k >= sub_from when sub >= 0)
 cudaError_t launch_frame_reduce(const LaunchCtx& L, int off, int ncomp, double* out, int slot_cur,
                                 int slot_prev, bool frames, int sub = -1, int sub_from = 0);
 cudaError_t launch_fc_residual(const LaunchCtx& L, bool accum, int have_prev);
-cudaError_t launch_fc_point(const LaunchCtx& L, bool accum);
 
 // linear algebra (pba_linalg.cu)
 struct SolveArgs {
@@ -89,6 +86,15 @@ struct SolveArgs {
     const int* cmap;        // [f] compact index of an active frame or -1, [F] their number
     const double* tanchor;  // F*12 poses whose t define the gauge direction
 };
+
+// depth back-substitution (when apply) of the last update and, in extra
+// CTAs, every frame's pose update with it (a.active / tanchor unused)
+cudaError_t launch_depth_update(const LaunchCtx& L, const SolveArgs& a, bool ic_rule, int apply);
+cudaError_t launch_ic_point(const LaunchCtx& L, bool accum);
+cudaError_t launch_fc_point(const LaunchCtx& L, bool accum);
+// Dtheta = -S^-1 y (compact S^-1, y per frame as written by the frame
+// reduction), the gauge constraint and every frame's update
+cudaError_t launch_ic_solve(const SolveArgs& a, const dfloat* Sinv, const double* y, cudaStream_t st);
 
 // Schur complement (pba_schur.cu)
 // Co-visibility lists of the sparse Schur complement (device pointers):
@@ -124,11 +130,9 @@ cudaError_t launch_assemble_S(int F, const double* Hff, int hff_stride, const do
 cudaError_t launch_ldl(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv, const int* cmap,
                        int F, int aug, int* err, cudaStream_t st);
 cudaError_t ldl_setup();  // once per process and device, before any capture
-// full 6(F-1) x 6(F-1) S^-1 (identity rows for frames left out)
+// S^-1 over the active frames (compact nc x nc, nc = 6 cmap[F])
 cudaError_t launch_ldl_inverse(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, const int* cmap,
-                               int F, double* Sinv, cudaStream_t st);
-cudaError_t launch_ic_solve_update(const SolveArgs& a, const double* Sinv, const double* y,
-                                   int y_stride, int y_off, cudaStream_t st);
+                               int F, dfloat* Sinv, cudaStream_t st);
 cudaError_t launch_fc_solve_update(const SolveArgs& a, const dfloat* L, const dfloat* Linv,
                                    cudaStream_t st);
 

@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "pba_chol.cuh"
+#include "pba_pose.cuh"
 
 namespace pba {
 
@@ -136,256 +137,20 @@ cudaError_t launch_assemble_S(int F, const double* Hff, int hff_stride, const do
     if (S2 && !cmap) return cudaErrorInvalidValue;
     const int n6 = 6 * (F - 1);
     if (F > 1024) return cudaErrorInvalidValue;
-    const int blocks = std::max(1, std::min(148, (n6 * n6 + 4 * kAssembleThreads - 1) / (4 * kAssembleThreads)));
+    // one element per thread on up to 148 SMs (the FP64 -> double-float
+    // conversions go to the slow FP64 pipe)
+    const int blocks = std::max(1, std::min(148, (n6 * n6 + kAssembleThreads - 1) / kAssembleThreads));
     assemble_S_kernel<<<blocks, kAssembleThreads, 0, st>>>(F, Hff, hff_stride, Soff, anchor_t,
                                                             gauge_w, S, active, S2, cmap, rhs,
                                                             rhs_stride, rhs_off);
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// pose updates (FP64). GB300 issues an FP64 warp instruction at a small
-// fraction of the FP32 rate whatever the number of active lanes, so the 3x3
-// products are spread over lanes of one warp instead of one thread.
-// ---------------------------------------------------------------------------
-// C = A B for 3x3 matrices in shared memory; lanes 0..8 each one entry.
-__device__ __forceinline__ void mat3_mul_lanes(const double* A, const double* B, double* C, int lane)
-{
-    if (lane < 9) {
-        const int i = lane / 3, j = lane % 3;
-        C[lane] = fma(A[3 * i], B[j], fma(A[3 * i + 1], B[3 + j], A[3 * i + 2] * B[6 + j]));
-    }
-    __syncwarp();
-}
-
-// Writes the new pose of frame f (lanes of one warp; Rn, tn in shared
-// memory), its FP32 pass constants, the previous R|t and the update.
-__device__ void write_frame_lanes(const SolveArgs& a, int f, const double* pose_old, const double* Rn,
-                                  const double* tn, const double* dth, int lane)
-{
-    double* pose = a.poses64 + 12 * f;
-    float* prev = a.fc_prev + 12 * f;
-    if (lane < 12) prev[lane] = (float)pose_old[lane];
-    __syncwarp();
-    if (lane < 9) pose[lane] = Rn[lane];
-    if (lane < 3) pose[9 + lane] = tn[lane];
-    __syncwarp();
-    float* out = a.fc + (size_t)f * kFrameConst;
-    if (lane < 12) out[lane] = (float)(lane < 9 ? Rn[lane] : tn[lane - 9]);
-    for (int q = lane; q < 3 * a.P; q += 32) {
-        const int j = q / 3, r = q % 3;
-        const double ox = a.pat[2 * j] * a.inv_fx, oy = a.pat[2 * j + 1] * a.inv_fy;
-        out[12 + q] = (float)(ox * Rn[3 * r] + oy * Rn[3 * r + 1]);
-    }
-    float q = 0.0f;
-    if (lane < 6) {
-        const double v = dth[lane];
-        const float hi = (float)v;
-        a.dtheta64[6 * f + lane] = v;
-        a.dth2[6 * f + lane] = make_float2(hi, (float)(v - (double)hi));
-        q = hi * hi;  // |Dtheta_f|^2 is a convergence statistic: FP32 is enough
-    }
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-    if (lane == 0) a.dthsq[f] = q;
-}
-
-// Rodrigues coefficients of omega: A = sin/th, B = (1-cos)/th^2,
-// C = (th-sin)/th^3. Updates are small rotations, so below th = 0.5 the
-// coefficients come from their Taylor series in x = th^2 (Horner, eight
-// terms: the first omitted one is below 1e-19 there); FP64 sincos and three
-// FP64 divisions on one lane cost several microseconds on GB300.
-__device__ void rodrigues_coeffs(const double* w, double* ABC, int lane)
-{
-    if (lane == 0) {
-        const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-        if (th2 < 0.25) {
-            // 1/(2k+1)!, 1/(2k+2)!, 1/(2k+3)! for k = 7 .. 0, in powers of -x
-            const double y = -th2;
-            double A = 1.0 / 1307674368000.0, B = 1.0 / 20922789888000.0, C = 1.0 / 355687428096000.0;
-            A = fma(A, y, 1.0 / 6227020800.0);
-            B = fma(B, y, 1.0 / 87178291200.0);
-            C = fma(C, y, 1.0 / 1307674368000.0);
-            A = fma(A, y, 1.0 / 39916800.0);
-            B = fma(B, y, 1.0 / 479001600.0);
-            C = fma(C, y, 1.0 / 6227020800.0);
-            A = fma(A, y, 1.0 / 362880.0);
-            B = fma(B, y, 1.0 / 3628800.0);
-            C = fma(C, y, 1.0 / 39916800.0);
-            A = fma(A, y, 1.0 / 5040.0);
-            B = fma(B, y, 1.0 / 40320.0);
-            C = fma(C, y, 1.0 / 362880.0);
-            A = fma(A, y, 1.0 / 120.0);
-            B = fma(B, y, 1.0 / 720.0);
-            C = fma(C, y, 1.0 / 5040.0);
-            A = fma(A, y, 1.0 / 6.0);
-            B = fma(B, y, 1.0 / 24.0);
-            C = fma(C, y, 1.0 / 120.0);
-            A = fma(A, y, 1.0);
-            B = fma(B, y, 0.5);
-            C = fma(C, y, 1.0 / 6.0);
-            ABC[0] = A;
-            ABC[1] = B;
-            ABC[2] = C;
-        } else {
-            const double th = sqrt(th2);
-            double sn, cs;
-            sincos(th, &sn, &cs);
-            ABC[0] = sn / th;
-            ABC[1] = (1.0 - cs) / th2;
-            ABC[2] = (th - sn) / (th2 * th);
-        }
-    }
-    __syncwarp();
-}
-
-// Entry e (0..8) of I + p [w]x + q [w]x^2 with [w]x^2 = w w^T - |w|^2 I.
-__device__ __forceinline__ double rodrigues_entry(const double* w, double p, double q, int e)
-{
-    const int i = e / 3, j = e % 3;
-    const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-    double K = 0.0;  // [w]x (i, j)
-    if (i != j) {
-        const int k = 3 - i - j;
-        K = ((j - i + 3) % 3 == 1) ? -w[k] : w[k];
-    }
-    return (i == j ? 1.0 : 0.0) + p * K + q * (w[i] * w[j] - (i == j ? th2 : 0.0));
-}
-
-// Sec. 3.6: R <- R R0^T exp(omega)^T R0, t <- t - R R0^T Dt (old R on the
-// right-hand sides). pose, p0: the frame's current and p_0 poses (12 each,
-// shared memory); sh: 48 doubles of warp-private shared memory.
-__device__ void ic_pose_update_warp(const SolveArgs& a, int f, const double* pose, const double* p0,
-                                    const double* dth, double* sh, int lane)
-{
-    double *R = sh, *R0t = sh + 9, *A = sh + 18, *E = sh + 27, *B = sh + 36, *t = sh + 45;
-    double ABC[3];
-    if (lane < 9) {
-        R[lane] = pose[lane];
-        R0t[lane] = p0[3 * (lane % 3) + lane / 3];
-    }
-    double* coef = B;  // scratch until B is formed
-    rodrigues_coeffs(dth + 3, coef, lane);
-    for (int k = 0; k < 3; ++k) ABC[k] = coef[k];
-    __syncwarp();
-    if (lane < 9) {
-        const double mw[3] = {-dth[3], -dth[4], -dth[5]};
-        E[lane] = rodrigues_entry(mw, ABC[0], ABC[1], lane);  // exp(omega)^T = exp(-omega)
-    }
-    __syncwarp();
-    mat3_mul_lanes(R, R0t, A, lane);   // A = R R0^T
-    mat3_mul_lanes(A, E, B, lane);     // B = A exp(-omega)
-    double* Rn = E;                    // E no longer needed
-    if (lane < 9) {
-        const int i = lane / 3, j = lane % 3;
-        Rn[lane] = fma(B[3 * i], p0[j], fma(B[3 * i + 1], p0[3 + j], B[3 * i + 2] * p0[6 + j]));
-    }
-    if (lane < 3)
-        t[lane] = pose[9 + lane] - fma(A[3 * lane], dth[0], fma(A[3 * lane + 1], dth[1], A[3 * lane + 2] * dth[2]));
-    __syncwarp();
-    write_frame_lanes(a, f, pose, Rn, t, dth, lane);
-}
-
-// Boxplus: T <- exp([upsilon, omega]) T.
-__device__ void fc_pose_update_warp(const SolveArgs& a, int f, const double* dth, double* sh, int lane)
-{
-    double *E = sh, *V = sh + 9, *Rn = sh + 18, *R = sh + 27, *t = sh + 36, *ABC = sh + 39;
-    double* pose = sh + 42;  // 12 (sh holds 54 doubles)
-    if (lane < 12) pose[lane] = a.poses64[12 * f + lane];
-    __syncwarp();
-    if (lane < 9) R[lane] = pose[lane];
-    rodrigues_coeffs(dth + 3, ABC, lane);
-    if (lane < 9) E[lane] = rodrigues_entry(dth + 3, ABC[0], ABC[1], lane);
-    else if (lane < 18) V[lane - 9] = rodrigues_entry(dth + 3, ABC[1], ABC[2], lane - 9);
-    __syncwarp();
-    mat3_mul_lanes(E, R, Rn, lane);
-    if (lane < 3)
-        t[lane] = fma(E[3 * lane], pose[9], fma(E[3 * lane + 1], pose[10], E[3 * lane + 2] * pose[11])) +
-                  fma(V[3 * lane], dth[0], fma(V[3 * lane + 1], dth[1], V[3 * lane + 2] * dth[2]));
-    __syncwarp();
-    write_frame_lanes(a, f, pose, Rn, t, dth, lane);
-}
-
-// Scale gauge (the one free direction of the system, Delta t_f = -t_f,
-// Delta d_n = d_n): the prior mu that that^T selects the solution with
-// that . Delta t_anchor = 0, but in floating point the prior pins that
-// component only to cond(S) * eps. Adding alpha times the null vector leaves
-// H Delta p unchanged, so the constraint is imposed exactly:
-//   alpha = (t_a . Delta t_a) / |t_a|^2,  Delta t_f -= alpha t_f (active f),
-// and the depth back-substitution carries the matching alpha d_n.
-__device__ __forceinline__ double gauge_alpha(const double* ta, const double* dta)
-{
-    const double n2 = ta[0] * ta[0] + ta[1] * ta[1] + ta[2] * ta[2];
-    return n2 > 0.0 ? (ta[0] * dta[0] + ta[1] * dta[1] + ta[2] * dta[2]) / n2 : 0.0;
-}
-
-// IC step 3 + 4: Dtheta = -S^-1 y (one CTA per target frame, one warp per
-// row, FP64 dot products; warps 6-8 also form the anchor frame's Delta t for
-// the gauge constraint), then the frame's pose update by warp 0. Everything
-// the update reads besides Dtheta is fetched at the start, beside the rows.
-__global__ void __launch_bounds__(9 * 32) ic_solve_update_kernel(SolveArgs a, const double* Sinv,
-                                                                 const double* y, int y_stride,
-                                                                 int y_off)
-{
-    __shared__ double dth[9];
-    __shared__ double d[6];
-    __shared__ double sh[48];
-    __shared__ double s_pose[12], s_p0[12], s_ta[3], s_tf[3];
-    __shared__ int s_act;
-    const int f = blockIdx.x + 1, tid = threadIdx.x, lane = tid & 31, row = tid >> 5;
-    const int n6 = a.n6;
-    const int anchor = a.active[0];
-    if (row == 8) {
-        if (lane < 12) s_pose[lane] = a.poses64[12 * f + lane];
-        else if (lane < 24) s_p0[lane - 12] = a.poses0[12 * f + lane - 12];
-        else if (lane < 27) s_tf[lane - 24] = a.tanchor[12 * f + 9 + lane - 24];
-        else if (lane < 30) s_ta[lane - 27] = anchor > 0 ? a.tanchor[12 * anchor + 9 + lane - 27] : 0.0;
-        else if (lane == 30) s_act = a.active[f];
-    }
-    const int rr = row < 6 ? 6 * (f - 1) + row : (anchor > 0 ? 6 * (anchor - 1) + row - 6 : -1);
-    if (rr >= 0) {
-        const double* Sr = Sinv + (size_t)rr * n6;
-        double s0 = 0.0, s1 = 0.0;  // two chains halve the dependent FP64 latency
-        int c = lane;
-        for (; c + 32 < n6; c += 64) {
-            s0 = fma(Sr[c], y[(size_t)(c / 6 + 1) * y_stride + y_off + c % 6], s0);
-            s1 = fma(Sr[c + 32], y[(size_t)((c + 32) / 6 + 1) * y_stride + y_off + (c + 32) % 6], s1);
-        }
-        if (c < n6) s0 = fma(Sr[c], y[(size_t)(c / 6 + 1) * y_stride + y_off + c % 6], s0);
-        const double s = warp_sum1d(s0 + s1);
-        if (lane == 0) dth[row] = -s;
-    }
-    __syncthreads();
-    if (row != 0) return;
-    if (lane < 6) {
-        double v = dth[lane];
-        if (lane < 3 && anchor > 0 && s_act) {
-            const double alpha = gauge_alpha(s_ta, dth + 6);
-            v = fma(-alpha, s_tf[lane], v);
-        }
-        d[lane] = v;
-    }
-    __syncwarp();
-    const bool ok = __all_sync(0xffffffffu, lane >= 6 || isfinite(d[lane]));
-    if (!ok) {
-        if (lane == 0) atomicOr(a.err, kErrNonFinite);
-        if (lane < 6) d[lane] = 0.0;
-        __syncwarp();
-    }
-    ic_pose_update_warp(a, f, s_pose, s_p0, d, sh, lane);
-}
-
-cudaError_t launch_ic_solve_update(const SolveArgs& a, const double* Sinv, const double* y,
-                                   int y_stride, int y_off, cudaStream_t st)
-{
-    ic_solve_update_kernel<<<a.F - 1, 9 * 32, 0, st>>>(a, Sinv, y, y_stride, y_off);
-    return cudaGetLastError();
-}
-
 // FC: the factorisation has eliminated b = -y with the matrix, so row n of L
 // holds D^-1 L^-1 b; the backward substitution L^T Dtheta = that row gives
-// Dtheta = -S^-1 y (double-float, one CTA). Then the exact gauge constraint
-// and every frame's boxplus update (one warp per frame, FP64).
+// Dtheta = -S^-1 y (double-float, one CTA). Then the exact gauge constraint;
+// the update is written per frame and the boxplus pose updates run in the
+// next launch, one frame per CTA.
 constexpr int kFcSolveWarps = 32;  // one warp per frame's update (F <= 33 in one round)
 
 __global__ void __launch_bounds__(kFcSolveWarps * 32) fc_solve_update_kernel(SolveArgs a, const dfloat* L,
@@ -426,7 +191,7 @@ __global__ void __launch_bounds__(kFcSolveWarps * 32) fc_solve_update_kernel(Sol
             if (lane < 6) d[lane] = 0.0;
             __syncwarp();
         }
-        fc_pose_update_warp(a, f, d, sh[warp], lane);
+        write_update_lanes(a, f, d, lane);
         __syncwarp();
     }
 }

@@ -113,12 +113,13 @@ struct pba_ctx {
         float4* estats;
         double *poses64, *poses0_64, *dtheta64;
         double *red_ic, *red_y;
-        double *Soff, *S_ic, *Sinv, *S_fc;
+        double *Soff, *S_ic, *S_fc;
+        dfloat* Sinv2;  // IC S^-1 over the active frames (double-float, compact)
         dfloat *A2, *L2, *Linv, *dpiv, *rpiv;  // double-float factorisation (IC and FC in turn)
         int *pair_fg, *pair_chunk, *chunk_pair, *chunk_start;
         int2* pair_items;
         float2* schur_part;
-        int *active_ic, *active_fc, *cmap;
+        int *active_ic, *active_fc, *cmap_ic, *cmap_fc;
         int* err;
         double* stats;
     } d{};
@@ -319,7 +320,7 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.red_y, F * 27 * 8);
     take(c->d.Soff, n6 * n6 * 8);
     take(c->d.S_ic, n6 * n6 * 8);
-    take(c->d.Sinv, n6 * n6 * 8);
+    take(c->d.Sinv2, n6 * n6 * sizeof(dfloat));
     take(c->d.S_fc, n6 * n6 * 8);
     take(c->d.A2, (n6 + 1) * n6 * sizeof(dfloat));
     take(c->d.L2, (n6 + 1) * n6 * sizeof(dfloat));
@@ -334,7 +335,8 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.schur_part, c->chunk_pair.size() * 36 * sizeof(float2));
     take(c->d.active_ic, F * 4);
     take(c->d.active_fc, F * 4);
-    take(c->d.cmap, (F + 1) * 4);
+    take(c->d.cmap_ic, (F + 1) * 4);
+    take(c->d.cmap_fc, (F + 1) * 4);
     take(c->d.err, 64);
     take(c->d.stats, (size_t)(c->stats_slots) * kStats * 8);
     return off;
@@ -522,7 +524,6 @@ SolveArgs make_solve(pba_ctx* c)
     a.poses0 = c->d.poses0_64;
     a.dtheta64 = c->d.dtheta64;
     a.dth2 = c->d.dth2;
-    a.cmap = c->d.cmap;
     a.fc = c->d.fc;
     a.fc_prev = c->d.fc_prev;
     a.dthsq = c->d.dthsq;
@@ -837,17 +838,17 @@ pba_status pba_precompute_ic(pba_ctx* ctx)
                            cudaMemcpyDeviceToDevice, ctx->stream));
         CK(cudaMemcpyAsync(ctx->d.d0_64, ctx->d.d64, sizeof(double) * ctx->Npad,
                            cudaMemcpyDeviceToDevice, ctx->stream));
-        LAUNCH(TS_PRE, launch_depth_update(L, true, 0));  // FP32 depths of p_0
+        LAUNCH(TS_PRE, launch_depth_update(L, make_solve(ctx), true, 0));  // FP32 depths of p_0
         LAUNCH(TS_PRE, launch_ic_precompute(L));
         LAUNCH(TS_PRE, launch_frame_reduce(L, 0, 21, ctx->d.red_ic, -1, -1, true));
         LAUNCHN(TS_PRE, launch_schur_sparse(L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, schur_lists(ctx),
                                             ctx->d.schur_part, ctx->d.Soff, ctx->stream, &nl));
         LAUNCH(TS_PRE, launch_assemble_S(F, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64,
                                          ctx->cfg.gauge_anchor_w, ctx->d.S_ic, ctx->d.active_ic,
-                                         ctx->stream, ctx->d.A2, ctx->d.cmap));
-        LAUNCH(TS_PRE, launch_ldl(ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv, ctx->d.cmap,
+                                         ctx->stream, ctx->d.A2, ctx->d.cmap_ic));
+        LAUNCH(TS_PRE, launch_ldl(ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv, ctx->d.cmap_ic,
                                   F, 0, ctx->d.err, ctx->stream));
-        LAUNCH(TS_PRE, launch_ldl_inverse(ctx->d.L2, ctx->d.Linv, ctx->d.rpiv, ctx->d.cmap, F, ctx->d.Sinv,
+        LAUNCH(TS_PRE, launch_ldl_inverse(ctx->d.L2, ctx->d.Linv, ctx->d.rpiv, ctx->d.cmap_ic, F, ctx->d.Sinv2,
                                           ctx->stream));
         return PBA_OK;
     });
@@ -868,15 +869,16 @@ pba_status pba_iterate(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     SolveArgs sa = make_solve(ctx);
     sa.active = ctx->d.active_ic;
     sa.tanchor = ctx->d.poses0_64;
+    sa.cmap = ctx->d.cmap_ic;
     pba_status s = run_enqueued(ctx, GraphKey{G_ITERATE, n_iters, ctx->timing}, [&]() -> pba_status {
         for (int k = 0; k < n_iters; ++k) {
-            LAUNCH(TS_POINT, launch_depth_update(L, true, k > 0));
+            LAUNCH(TS_POINT, launch_depth_update(L, sa, true, k > 0));
             LAUNCH(TS_PASS, launch_ic_residual(L, true, k > 0));
             LAUNCH(TS_POINT, launch_ic_point(L, true));
             LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 6, ctx->d.red_y, k, k - 1, true, 6));
-            LAUNCH(TS_SOLVE, launch_ic_solve_update(sa, ctx->d.Sinv, ctx->d.red_y, 6, 0, ctx->stream));
+            LAUNCH(TS_SOLVE, launch_ic_solve(sa, ctx->d.Sinv2, ctx->d.red_y, ctx->stream));
         }
-        LAUNCH(TS_EVAL, launch_depth_update(L, true, n_iters > 0));
+        LAUNCH(TS_EVAL, launch_depth_update(L, sa, true, n_iters > 0));
         LAUNCH(TS_EVAL, launch_ic_residual(L, false, n_iters > 0));
         LAUNCH(TS_EVAL, launch_ic_point(L, false));
         LAUNCH(TS_EVAL, launch_frame_reduce(L, 0, 0, nullptr, n_iters, n_iters - 1, false));
@@ -898,9 +900,10 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     SolveArgs sa = make_solve(ctx);
     sa.active = ctx->d.active_fc;
     sa.tanchor = ctx->d.poses64;
+    sa.cmap = ctx->d.cmap_fc;
     pba_status s = run_enqueued(ctx, GraphKey{G_FC, n_iters, ctx->timing}, [&]() -> pba_status {
         for (int k = 0; k < n_iters; ++k) {
-            LAUNCH(TS_POINT, launch_depth_update(L, false, k > 0));
+            LAUNCH(TS_POINT, launch_depth_update(L, sa, false, k > 0));
             LAUNCH(TS_PASS, launch_fc_residual(L, true, k > 0));
             LAUNCH(TS_POINT, launch_fc_point(L, true));
             LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 27, ctx->d.red_y, k, k - 1, true, 27, 21));
@@ -908,12 +911,12 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
                                                   ctx->d.schur_part, ctx->d.Soff, ctx->stream, &nl));
             LAUNCH(TS_SCHUR, launch_assemble_S(F, ctx->d.red_y, 27, ctx->d.Soff, ctx->d.poses64,
                                                ctx->cfg.gauge_anchor_w, ctx->d.S_fc, ctx->d.active_fc,
-                                               ctx->stream, ctx->d.A2, ctx->d.cmap, ctx->d.red_y, 27, 21));
+                                               ctx->stream, ctx->d.A2, ctx->d.cmap_fc, ctx->d.red_y, 27, 21));
             LAUNCH(TS_SOLVE, launch_ldl(ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv,
-                                        ctx->d.cmap, F, 1, ctx->d.err, ctx->stream));
+                                        ctx->d.cmap_fc, F, 1, ctx->d.err, ctx->stream));
             LAUNCH(TS_SOLVE, launch_fc_solve_update(sa, ctx->d.L2, ctx->d.Linv, ctx->stream));
         }
-        LAUNCH(TS_EVAL, launch_depth_update(L, false, n_iters > 0));
+        LAUNCH(TS_EVAL, launch_depth_update(L, sa, false, n_iters > 0));
         LAUNCH(TS_EVAL, launch_fc_residual(L, false, n_iters > 0));
         LAUNCH(TS_EVAL, launch_fc_point(L, false));
         LAUNCH(TS_EVAL, launch_frame_reduce(L, 0, 0, nullptr, n_iters, n_iters - 1, false));

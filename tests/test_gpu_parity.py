@@ -276,6 +276,27 @@ def test_graph_replay_equals_direct_launches(torch_cuda):
         assert np.array_equal(x, y)
 
 
+def test_fc_between_ic_calls_leaves_ic_state_alone(torch_cuda):
+    """pba_solve_fc between two pba_iterate calls (same p_0 precompute) must
+    not change what the second IC call computes: the IC system, its inverse
+    and its active-frame map are kept apart from the FC ones."""
+    sc = synth.make_scene("ring5")
+    out = []
+    for with_fc in (False, True):
+        b = _bundle(sc)
+        b.precompute_ic()
+        b.iterate(3)
+        P, D = b.params()
+        if with_fc:
+            b.solve_fc(2)
+        b.set_params(P, D)
+        st = b.iterate(2)
+        out.append((st, *b.params()))
+        b.close()
+    for x, y in zip(out[0], out[1]):
+        assert np.array_equal(x, y)
+
+
 def test_ragged_tile_single_pixel_pattern_and_empty_rows(torch_cuda):
     """N = 33 (one full tile and a tail of one), a frame that sees no point,
     a point that no frame sees, and a one-pixel pattern."""
