@@ -49,14 +49,24 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--iters", type=int, default=20, help="IC / FC iterations per solve")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", choices=sorted(WORKLOAD_TEXT), default=SCENE,
+                   help="helix30 (the benchmark workload) or orbit101 (the 100-frame BF16 "
+                        "precision workload)")
     p.add_argument("--no-graphs", action="store_true",
                    help="submit every kernel with its own launch instead of replaying CUDA graphs")
     return p.parse_args()
 
 
+WORKLOAD_TEXT = {
+    "helix30": "30-frame 2-turn helix around a value-noise sphere",
+    "orbit101": "reference + 100 frames on a 30-degree orbit around a value-noise sphere on a "
+                "textured ground plane",
+}
+
+
 def workload_config(sc, iters):
-    return {"workload": f"{SCENE}: 30-frame 2-turn helix around a value-noise sphere, "
-                        f"{sc.W}x{sc.H} FP32, f={sc.fx:g}, {sc.N} points x 8-pixel pattern, "
+    return {"workload": f"{SCENE}: {WORKLOAD_TEXT[SCENE]}, {sc.W}x{sc.H} {sc.dtype.upper()}, "
+                        f"f={sc.fx:g}, {sc.N} points x 8-pixel pattern, "
                         f"2 deg/0.02/5% perturbation, {iters} iterations per solve",
             "frames": sc.F, "points": sc.N, "pattern": sc.P,
             "residuals_per_iter": sc.n_residuals(), "reduced_system": 6 * (sc.F - 1),
@@ -349,8 +359,7 @@ def run_ours(args):
             pass
 
     # end to end: host buffers through the C ABI (pinned host images)
-    pinned = torch.empty(sc.images_store.shape, dtype=torch.float32, pin_memory=True)
-    pinned.numpy()[...] = sc.images_store
+    pinned = torch.from_numpy(sc.images_store).pin_memory()
     host_imgs = pinned.numpy()
     e2e_t, h2d_b, d2h_b = [], 0, 0
     for i in range(args.warmup + args.steps):
@@ -427,7 +436,9 @@ def kernel_sha():
 
 
 def main():
+    global SCENE
     args = parse()
+    SCENE = args.workload
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

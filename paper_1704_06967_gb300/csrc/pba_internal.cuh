@@ -67,6 +67,17 @@ struct DevProblem {
 };
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch. A kernel launched with the programmatic
+// stream-serialisation attribute may be scheduled while the previous kernel
+// on the stream is still finishing: it calls pdl_wait() before it reads
+// anything an earlier kernel wrote (the wait returns once the previous grid
+// has completed and its memory is visible, and at once for an ordinary
+// launch). pdl_trigger() lets the next such kernel be scheduled early.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // image access (offsets are 32-bit: the host checks F * H * pitch < 2^31)
 // ---------------------------------------------------------------------------
 template <int DT>

@@ -71,6 +71,8 @@ depth_update_kernel(DevProblem pb, DepthState ds, const float2* __restrict__ dth
 {
     __shared__ float2 red[kTileWarps][32];
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    pdl_trigger();
+    pdl_wait();
     if (t >= pb.T) {
         // CTA T + f - 1: pose update of frame f with the update the solve
         // wrote (FP64; one frame per CTA, spread over the SMs)
@@ -198,6 +200,8 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
 {
     const int lane = threadIdx.x & 31;
     const int e = blockIdx.x * kResWarps + (threadIdx.x >> 5);
+    pdl_trigger();
+    pdl_wait();
     if (e >= pb.E) return;
     const Entry en = pb.entries[e];
     const int P = pb.P;
@@ -345,6 +349,8 @@ fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
 {
     const int lane = threadIdx.x & 31;
     const int e = blockIdx.x * kResWarps + (threadIdx.x >> 5);
+    pdl_trigger();
+    pdl_wait();
     if (e >= pb.E) return;
     const Entry en = pb.entries[e];
     const int P = pb.P;
@@ -509,6 +515,8 @@ point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __rest
              TileStats* __restrict__ tstats)
 {
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    pdl_trigger();
+    pdl_wait();
     const int e0 = pb.tile_entry[t], e1 = pb.tile_entry[t + 1], ne = e1 - e0;
     if (kAccum) {
         const int n = t * kTile + lane;
@@ -583,6 +591,8 @@ ic_solve_kernel(SolveArgs a, const dfloat* __restrict__ Sinv, const double* __re
     extern __shared__ dfloat ys[];  // nc, compact order; then F ints
     __shared__ double dth[9], d[6];
     const int F = a.F, f = blockIdx.x + 1, lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    pdl_trigger();
+    pdl_wait();
     const int kf = a.cmap[f], nc = 6 * a.cmap[F], anchor = a.active[0];
     int* frame_of = reinterpret_cast<int*>(ys + 6 * (F - 1));
     if (kf < 0) {
@@ -734,12 +744,12 @@ cudaError_t launch_depth_update(const LaunchCtx& L, const SolveArgs& a, bool ic_
     const DepthState& ds = ic_rule ? L.ds_ic : L.ds_fc;
     const int grid = L.pb.T + (apply ? L.pb.F - 1 : 0);  // + one CTA per frame's pose update
     if (ic_rule)
-        depth_update_kernel<true><<<grid, kTileWarps * 32, 0, L.stream>>>(
-            L.pb, ds, L.fs.dth2, L.ic.inv_hnn, L.ic.inv_d0, L.it.dcur, L.it.dprev, L.it.ddsq_t,
-            apply, a);
+        return launch_pdl(depth_update_kernel<true>, grid, kTileWarps * 32, 0, L.stream, L.pb, ds, L.fs.dth2,
+                          L.ic.inv_hnn, L.ic.inv_d0, L.it.dcur, L.it.dprev, L.it.ddsq_t, apply, a);
     else
-        depth_update_kernel<false><<<grid, kTileWarps * 32, 0, L.stream>>>(
-            L.pb, ds, L.fs.dth2, nullptr, nullptr, L.it.dcur, L.it.dprev, L.it.ddsq_t, apply, a);
+        return launch_pdl(depth_update_kernel<false>, grid, kTileWarps * 32, 0, L.stream, L.pb, ds, L.fs.dth2,
+                          (const double*)nullptr, (const double*)nullptr, L.it.dcur, L.it.dprev, L.it.ddsq_t,
+                          apply, a);
     return cudaGetLastError();
 }
 
@@ -747,10 +757,9 @@ template <int PMAX, bool A, int DT>
 static cudaError_t ic_residual_p(const LaunchCtx& L, int have_prev)
 {
     const int blocks = (L.pb.E + kResWarps - 1) / kResWarps;
-    ic_residual_kernel<PMAX, A, DT><<<blocks, kResWarps * 32, 0, L.stream>>>(
-        L.pb, L.fs.fc, L.fs.fc_prev, L.it.dcur, L.it.dprev, L.ic.J4, L.ent_part, L.it.gpart,
-        L.it.estats, have_prev);
-    return cudaGetLastError();
+    return launch_pdl(ic_residual_kernel<PMAX, A, DT>, blocks, kResWarps * 32, 0, L.stream, L.pb, L.fs.fc,
+                      L.fs.fc_prev, L.it.dcur, L.it.dprev, L.ic.J4, L.ent_part, L.it.gpart, L.it.estats,
+                      have_prev);
 }
 
 cudaError_t launch_ic_residual(const LaunchCtx& L, bool accum, int have_prev)
@@ -773,10 +782,9 @@ template <int PMAX, bool A, int DT>
 static cudaError_t fc_residual_p(const LaunchCtx& L, int have_prev)
 {
     const int blocks = (L.pb.E + kResWarps - 1) / kResWarps;
-    fc_residual_kernel<PMAX, A, DT><<<blocks, kResWarps * 32, 0, L.stream>>>(
-        L.pb, L.fs.fc, L.fs.fc_prev, L.it.dcur, L.it.dprev, L.Hfd_fc, L.ent_part, L.it.gpart,
-        L.it.estats, have_prev);
-    return cudaGetLastError();
+    return launch_pdl(fc_residual_kernel<PMAX, A, DT>, blocks, kResWarps * 32, 0, L.stream, L.pb, L.fs.fc,
+                      L.fs.fc_prev, L.it.dcur, L.it.dprev, L.Hfd_fc, L.ent_part, L.it.gpart, L.it.estats,
+                      have_prev);
 }
 
 cudaError_t launch_fc_residual(const LaunchCtx& L, bool accum, int have_prev)
@@ -797,35 +805,23 @@ cudaError_t launch_fc_residual(const LaunchCtx& L, bool accum, int have_prev)
 
 cudaError_t launch_ic_point(const LaunchCtx& L, bool accum)
 {
-    if (accum)
-        point_kernel<true, false><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
-            L.pb, L.it.gpart, L.ic.Hfd, L.ic.Hnn, L.ds_ic.gn, L.ent_part, 6, L.it.estats, L.it.ddsq_t,
-            L.tstats);
-    else
-        point_kernel<false, false><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
-            L.pb, L.it.gpart, L.ic.Hfd, L.ic.Hnn, L.ds_ic.gn, L.ent_part, 6, L.it.estats, L.it.ddsq_t,
-            L.tstats);
-    return cudaGetLastError();
+    auto k = accum ? point_kernel<true, false> : point_kernel<false, false>;
+    return launch_pdl(k, L.pb.T, kTileWarps * 32, 0, L.stream, L.pb, L.it.gpart, L.ic.Hfd, L.ic.Hnn,
+                      L.ds_ic.gn, L.ent_part, 6, L.it.estats, L.it.ddsq_t, L.tstats);
 }
 
 cudaError_t launch_fc_point(const LaunchCtx& L, bool accum)
 {
-    if (accum)
-        point_kernel<true, true><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
-            L.pb, L.it.gpart, L.Hfd_fc, L.ds_fc.Hnn, L.ds_fc.gn, L.ent_part, 27, L.it.estats,
-            L.it.ddsq_t, L.tstats);
-    else
-        point_kernel<false, true><<<L.pb.T, kTileWarps * 32, 0, L.stream>>>(
-            L.pb, L.it.gpart, L.Hfd_fc, L.ds_fc.Hnn, L.ds_fc.gn, L.ent_part, 27, L.it.estats,
-            L.it.ddsq_t, L.tstats);
-    return cudaGetLastError();
+    auto k = accum ? point_kernel<true, true> : point_kernel<false, true>;
+    return launch_pdl(k, L.pb.T, kTileWarps * 32, 0, L.stream, L.pb, L.it.gpart, L.Hfd_fc, L.ds_fc.Hnn,
+                      L.ds_fc.gn, L.ent_part, 27, L.it.estats, L.it.ddsq_t, L.tstats);
 }
 
 cudaError_t launch_ic_solve(const SolveArgs& a, const dfloat* Sinv, const double* y, cudaStream_t st)
 {
     const int F = a.F;
-    ic_solve_kernel<<<F - 1, 9 * 32, sizeof(dfloat) * 6 * (F - 1) + sizeof(int) * F, st>>>(a, Sinv, y);
-    return cudaGetLastError();
+    return launch_pdl(ic_solve_kernel, F - 1, 9 * 32, sizeof(dfloat) * 6 * (F - 1) + sizeof(int) * F, st, a,
+                      Sinv, y);
 }
 
 }  // namespace pba

@@ -2,10 +2,31 @@
 // library's translation units.
 #pragma once
 
+#include <utility>
+
 #include "pba_df.cuh"
 #include "pba_internal.cuh"
 
 namespace pba {
+
+// Launch with programmatic stream serialisation (the kernel must call
+// pdl_wait() before reading what the previous kernel on the stream wrote).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Per-frame state used by the pass kernels.
 struct FrameState {

@@ -215,6 +215,8 @@ frame_reduce_kernel(DevProblem pb, const float* __restrict__ ent_part, double* _
                     const TileStats* __restrict__ tstats, const float* __restrict__ dthsq,
                     double* __restrict__ stats, int slot_cur, int slot_prev, int nframes_blocks)
 {
+    pdl_trigger();
+    pdl_wait();
     if ((int)blockIdx.x < nframes_blocks) {
         const int f = blockIdx.x + 1;
         float vs, vc;
@@ -262,16 +264,14 @@ cudaError_t launch_frame_reduce(const LaunchCtx& L, int off, int ncomp, double* 
     const int nfb = frames ? L.pb.F - 1 : 0;
     const dim3 grid(nfb + 1), block(kReduceThreads);
     if (off != 0) return cudaErrorInvalidValue;
-#define PBA_R(NC, SB, SF)                                                                        \
-    frame_reduce_kernel<NC, SB, SF><<<grid, block, 0, L.stream>>>(L.pb, L.ent_part, out, L.tstats, \
-                                                                   L.dthsq, L.stats, slot_cur,     \
-                                                                   slot_prev, nfb)
-    if (!frames || (ncomp == 6 && sub == 6 && sub_from == 0)) PBA_R(6, 6, 0);
-    else if (ncomp == 21 && sub < 0) PBA_R(21, -1, 0);
-    else if (ncomp == 27 && sub == 27 && sub_from == 21) PBA_R(27, 27, 21);
-    else return cudaErrorInvalidValue;
+#define PBA_R(NC, SB, SF)                                                                           \
+    launch_pdl(frame_reduce_kernel<NC, SB, SF>, grid, block, 0, L.stream, L.pb, L.ent_part, out, L.tstats, \
+               L.dthsq, L.stats, slot_cur, slot_prev, nfb)
+    if (!frames || (ncomp == 6 && sub == 6 && sub_from == 0)) return PBA_R(6, 6, 0);
+    if (ncomp == 21 && sub < 0) return PBA_R(21, -1, 0);
+    if (ncomp == 27 && sub == 27 && sub_from == 21) return PBA_R(27, 27, 21);
+    return cudaErrorInvalidValue;
 #undef PBA_R
-    return cudaGetLastError();
 }
 
 }  // namespace pba
