@@ -142,7 +142,8 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes);
  * per residual the proxy-template Jacobian row J = grad I_0 dphi/dDelta p
  * (Sec. 3.4), initial residual and Huber weight W_0; H = J^T W_0 J in frame,
  * frame-point and point blocks; the Schur complement S of the point block
- * with the scale-gauge prior, its FP64 Cholesky factor and inverse. */
+ * with the scale-gauge prior, its LDL^T factor (double-float arithmetic,
+ * ~48 bits, over the frames that have residuals) and inverse. */
 pba_status pba_precompute_ic(pba_ctx* ctx);
 
 /* Runs n_iters IC iterations (Sec. 3.5 steps 1-4 with the Sec. 3.6 update):
@@ -154,8 +155,8 @@ pba_status pba_precompute_ic(pba_ctx* ctx);
 pba_status pba_iterate(pba_ctx* ctx, int n_iters, pba_iter_stats* stats);
 
 /* Runs n_iters FC iterations: Jacobians from the target-image gradients, the
- * Hessian blocks, the Schur complement and its FP64 Cholesky factor rebuilt
- * every iteration, then T <- exp([upsilon, omega]) T, d <- d + Dd (Sec. 3,
+ * Hessian blocks, the Schur complement and its LDL^T factor (double-float)
+ * rebuilt every iteration, then T <- exp([upsilon, omega]) T, d <- d + Dd (Sec. 3,
  * the boxplus operator). stats as for pba_iterate. Needs no precompute. */
 pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats);
 
