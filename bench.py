@@ -54,6 +54,8 @@ def parse():
                         "precision workload)")
     p.add_argument("--no-graphs", action="store_true",
                    help="submit every kernel with its own launch instead of replaying CUDA graphs")
+    p.add_argument("--bundles", type=int, default=256,
+                   help="batch workload: number of bundles (default 256)")
     return p.parse_args()
 
 
@@ -61,6 +63,9 @@ WORKLOAD_TEXT = {
     "helix30": "30-frame 2-turn helix around a value-noise sphere",
     "orbit101": "reference + 100 frames on a 30-degree orbit around a value-noise sphere on a "
                 "textured ground plane",
+    "batch256": "independent bundles of uneven size solved together: frames uniform 4-64 on a "
+                "helix (24 deg per frame), points log-uniform 500-50,000, sphere radius uniform "
+                "0.5-2, texture seed = bundle index, 640x480 FP16, f=525",
 }
 
 
@@ -165,10 +170,51 @@ def oracle_sample(sc, iters, n_steps=2):
 # ----------------------------------------------------------------------------
 # reference arm
 # ----------------------------------------------------------------------------
+def run_reference_batch(args):
+    """The oracle on a sample of the batch: per step, one bundle (in batch
+    order) gets its IC precompute and one IC iteration, extrapolated to a
+    --iters iteration solve; the sample's bundle-iterations over its total
+    solve time is the rate of a CPU solving the bundles one after another."""
+    import numpy as np
+    import oracle
+    import synth
+    draws = synth.draw_batch(args.bundles)
+    n = args.warmup + args.steps
+    times = []
+    scenes = synth.make_batch(min(n, args.bundles), keep_f32=True, workers=1)
+    for i, sc in enumerate(scenes):
+        pb = oracle.Problem.from_scene(sc)
+        t0 = time.perf_counter()
+        pre = oracle.ic_precompute(pb, sc.poses0, sc.depths0)
+        t1 = time.perf_counter()
+        oracle.ic_step(pb, pre, sc.poses0, sc.depths0, sc.poses0, sc.depths0)
+        t2 = time.perf_counter()
+        if i >= args.warmup:
+            times.append((t1 - t0) + args.iters * (t2 - t1))
+    value = args.iters * len(times) / float(np.sum(times))
+    sample = (f"{len(times)} bundles of the batch (in batch order, after {args.warmup} warm-up bundles): "
+              f"FP64 oracle IC precompute + one IC iteration each, extrapolated to {args.iters} "
+              f"iterations; single thread")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "bundle-iterations/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"batch{args.bundles}: {args.bundles} {WORKLOAD_TEXT['batch256']}",
+                      "bundles": args.bundles, "frames_total": sum(d.n_frames for d in draws)},
+           "cpu_baseline": {"value": value, "unit": "bundle-iterations/s", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "bundle-iterations/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if SCENE == "batch256":
+        return run_reference_batch(args)
     import numpy as np
     import oracle
     import synth
@@ -423,16 +469,212 @@ def run_ours(args):
 
 
 def kernel_sha():
-    """Hash of the residual kernel's own source text and the device helpers it
-    uses: the stored DRAM traffic applies only while these are unchanged."""
+    """Hash of the residual kernel's own source text and of the device
+    helpers it calls: the stored DRAM traffic applies only while these are
+    unchanged."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1704_06967_gb300", "csrc")
+
+    def body(text, head):
+        start = text.index(head)
+        return text[start:text.index("\n}\n", start)]
+
     src = open(os.path.join(csrc, "pba_iter.cu")).read()
-    start = src.index("ic_residual_kernel(DevProblem pb")
-    end = src.index("\n}\n", start)
-    h = hashlib.sha256(src[start:end].encode())
-    h.update(open(os.path.join(csrc, "pba_internal.cuh"), "rb").read())
+    h = hashlib.sha256(body(src, "ic_residual_kernel(DevProblem pb").encode())
+    inc = open(os.path.join(csrc, "pba_internal.cuh")).read()
+    for head in ("__device__ __forceinline__ float load_px_t(", "__device__ __forceinline__ void warp_sum(",
+                 "__device__ __forceinline__ float warp_max1(", "__device__ __forceinline__ float huber_rho("):
+        h.update(body(inc, head).encode())
     return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------------------
+# batch workload: many independent bundles in one context vs a per-bundle loop
+# ----------------------------------------------------------------------------
+def run_batch(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1704_06967_gb300 import Batch, Bundle
+    from paper_1704_06967_gb300 import build as pkg_build
+    from paper_1704_06967_gb300.pba import _scene_images
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        pkg_build.build()
+    if dist is not None:
+        dist.barrier()
+    iters = args.iters
+    t0 = time.perf_counter()
+    # replicas draw disjoint batches (seed per rank)
+    scenes = synth.make_batch(args.bundles, seed=synth.BATCH_SEED + 1000 * rank)
+    log(f"generated {len(scenes)} bundles in {time.perf_counter() - t0:.1f} s")
+    B = len(scenes)
+    R = sum(sc.n_residuals() for sc in scenes)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    imgs = [_scene_images(sc) for sc in scenes]
+    s0 = scenes[0]
+    items = [(imgs[i], sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis) for i, sc in enumerate(scenes)]
+    batch = Batch(items, pattern=s0.pattern, huber_k=s0.huber_k, stream=stream, use_graphs=True)
+    singles = [Bundle(imgs[i], sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis, pattern=sc.pattern,
+                      huber_k=sc.huber_k, stream=stream, use_graphs=True) for i, sc in enumerate(scenes)]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def reset():
+        for i, sc in enumerate(scenes):
+            batch.set_params(sc.poses0, sc.depths0, bundle=i)
+            singles[i].set_params(sc.poses0, sc.depths0)
+
+    def timed(fn, k):
+        flush.fill_(k & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    def batch_ic():
+        batch.precompute_ic()
+        batch.iterate(iters, stats=False)
+
+    def loop_ic():
+        for b in singles:
+            b.precompute_ic()
+            b.iterate(iters, stats=False)
+
+    def batch_fc():
+        batch.solve_fc(iters, stats=False)
+
+    for i in range(args.warmup):
+        reset()
+        batch.enable_timing(1 << 1)
+        timed(batch_ic, i)
+        batch.enable_timing(0)
+        timed(loop_ic, i + 1)
+        timed(batch_fc, i + 2)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(device_uuid(torch))
+    clocks.start()
+    batch.enable_timing(1 << 1)
+    if dist is not None:
+        dist.barrier()
+    ic_ms, loop_ms, fc_ms = [], [], []
+    for i in range(args.steps):
+        reset()
+        ic_ms.append(timed(batch_ic, i))
+    kms, launches, kcounts = batch.timing()
+    batch.enable_timing(0)
+    for i in range(args.steps):
+        reset()
+        loop_ms.append(timed(loop_ic, i + 3))
+        fc_ms.append(timed(batch_fc, i + 5))
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    tot = torch.tensor([sum(ic_ms), sum(loop_ms), sum(fc_ms)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    total_ic, total_loop, total_fc = (float(x) for x in tot)
+    units = world * B * iters * args.steps
+    value = units / (total_ic / 1e3)
+    loop_value = units / (total_loop / 1e3)
+    fc_value = units / (total_fc / 1e3)
+
+    # the batch and the loop must agree exactly (each bundle's sums keep their order)
+    reset()
+    batch_ic()
+    loop_ic()
+    torch.cuda.synchronize()
+    mismatch = 0
+    for i in range(0, B, max(1, B // 16)):
+        P1, D1 = batch.params(i)
+        P2, D2 = singles[i].params()
+        mismatch += int(not (np.array_equal(P1, P2) and np.array_equal(D1, D2)))
+    # final RMS of the batch's IC and FC solves (sums over the bundles)
+    reset()
+    batch.precompute_ic()
+    st_ic = batch.iterate(iters)
+    reset()
+    st_fc = batch.solve_fc(iters)
+
+    # roofline of the residual kernel over all bundles
+    V = R // s0.P
+    img_bytes = sum(sc.F for sc in scenes) * s0.H * s0.W * 2
+    N = sum(sc.N for sc in scenes)
+    alg_bytes = R * 28 + V * 4 + N * s0.P * 4 + N * 12 + img_bytes
+    pass_ms = kms["pass"] / max(1, kcounts["pass"])
+    hbm_peak, peak_src = measured_peaks()
+    achieved = alg_bytes / (pass_ms * 1e-3) / 1e9
+    roofline = {"kernel": "ic_residual_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+                "traffic": None, "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": pass_ms,
+                "launches": int(kcounts["pass"])}
+
+    # end to end through the C ABI with host images (pinned), one context
+    e2e_t, h2d_b, d2h_b = [], 0, 0
+    host = [torch.from_numpy(sc.images_store).pin_memory().numpy() for sc in scenes]
+    for i in range(1 + min(args.steps, 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eb = Batch([(host[j], sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis)
+                    for j, sc in enumerate(scenes)], pattern=s0.pattern, huber_k=s0.huber_k)
+        eb.precompute_ic()
+        eb.iterate(iters, stats=False)
+        for j in range(B):
+            eb.params(j)
+        torch.cuda.synchronize()
+        if i >= 1:
+            e2e_t.append(time.perf_counter() - t0)
+            h2d_b, d2h_b = eb.transfer_bytes()
+        eb.close()
+    e2e_value = world * B * iters * len(e2e_t) / sum(e2e_t)
+
+    Fs = [sc.F for sc in scenes]
+    Ns = [sc.N for sc in scenes]
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "bundle-iterations/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ic / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": f"batch{B}: {B} {WORKLOAD_TEXT['batch256']}, 8-pixel pattern, "
+                                      f"2 deg/0.02/5% perturbation; a step is one IC solve of every "
+                                      f"bundle (precompute + {iters} iterations) in one context",
+                          "bundles": B, "frames_total": sum(Fs), "frames_min_max": [min(Fs), max(Fs)],
+                          "points_total": N, "points_min_max": [min(Ns), max(Ns)],
+                          "residuals_per_iter": R, "iterations_per_step": iters,
+                          "submission": "one CUDA graph replay per library call",
+                          "l2": "flushed (512 MB write) between timed steps"},
+               "e2e": {"value": e2e_value, "unit": "bundle-iterations/s", "h2d_bytes_per_step": h2d_b,
+                       "d2h_bytes_per_step": d2h_b},
+               "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": None, "clocks": clk,
+               "residuals_per_s": value * R / B,
+               "per_bundle_loop": {"value": loop_value, "unit": "bundle-iterations/s",
+                                   "ms_per_step": total_loop / args.steps,
+                                   "batch_over_loop": value / loop_value},
+               "fc_batch": {"value": fc_value, "unit": "bundle-iterations/s",
+                            "ms_per_step": total_fc / args.steps, "final_rms": float(st_fc[-1, 1])},
+               "ic_final_rms": float(st_ic[-1, 1]), "ic_over_fc_iterations_per_s": value / fc_value,
+               "batch_equals_loop": {"bundles_checked": len(range(0, B, max(1, B // 16))),
+                                     "mismatches": mismatch}}
+        print(json.dumps(out), flush=True)
+    for b in singles:
+        b.close()
+    batch.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0 if mismatch == 0 else 1
 
 
 def main():
@@ -441,6 +683,8 @@ def main():
     SCENE = args.workload
     if args.impl == "reference":
         return run_reference(args)
+    if SCENE == "batch256":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -49,6 +49,7 @@ extern "C" {
 #endif
 
 #define PBA_MAX_PATTERN 16
+#define PBA_MAX_BUNDLES 65535
 
 typedef struct pba_ctx pba_ctx;
 
@@ -74,7 +75,14 @@ typedef struct {
     const int32_t* pattern;  /* host, P*2 pixel offsets (dx, dy), copied at create */
     double gauge_anchor_w;   /* scale-gauge prior weight relative to mean diag(S); 0 -> 1 */
     double conv_px;          /* convergence threshold of Sec. 4.1 in pixels; 0 -> 5e-3 */
-    int n_bundles;           /* independent bundles in this context; must be 1 */
+    int n_bundles;           /* independent bundles solved together, 1..PBA_MAX_BUNDLES
+                                (0 -> 1). Their frames, points and residuals are
+                                concatenated, so every kernel of an iteration runs over
+                                all bundles in one launch; each bundle keeps its own
+                                reference frame, gauge and reduced camera system
+                                (factored by its own thread-block cluster). The bundles
+                                share the camera: image size, pitch, element type, memory
+                                kind and intrinsics. Statistics are summed over them. */
     void* cuda_stream;       /* cudaStream_t for all work; NULL = legacy default stream */
     int use_graphs;          /* non-zero (and cuda_stream non-NULL): pba_precompute_ic,
                                 pba_iterate and pba_solve_fc submit their kernels by
@@ -85,6 +93,13 @@ typedef struct {
                                 dropped by pba_set_workspace. Ignored with a NULL
                                 stream (the legacy stream cannot be captured). */
     int max_stats_iters;     /* capacity of the per-iteration statistics; 0 -> 256 */
+    int autotune;            /* non-zero: the first pba_precompute_ic times the candidate
+                                launch shapes on this problem and keeps the fastest: warps
+                                per CTA of the IC residual pass (4, 8, 16: the number of
+                                (tile, frame) entries a CTA takes) and CTAs per bundle of
+                                the cluster that factors the reduced camera system (4, 8,
+                                16). Results do not depend on the choice (every sum keeps
+                                its order); see pba_get_tuning. */
 } pba_config;
 
 /* Statistics of one iteration (Sec. 4.1): Huber energy, RMS and count of the
@@ -115,8 +130,10 @@ const char* pba_last_error(const pba_ctx* ctx);
  *   pba_set_workspace) according to mem.
  * poses: host, F*12 doubles (p_0), frame 0 = identity. Copied.
  * intrinsics: host, {f_x, f_y, c_x, c_y}. Copied.
- * Requires bundle == 0, F >= 2, w, h >= 4. Invalidates the precompute and the
- * workspace layout. */
+ * Requires 0 <= bundle < n_bundles, 2 <= F <= 1024, w, h >= 4, and (all
+ * bundles together) fewer than 2^32 image elements; the camera (w, h,
+ * pitch_elems, dtype, mem, intrinsics) must equal that of the other bundles
+ * already set. Invalidates the precompute and the workspace layout. */
 pba_status pba_set_frames(pba_ctx* ctx, int bundle, int n_frames, int w, int h, int pitch_elems,
                           pba_dtype dtype, pba_memory mem, const void* images,
                           const double* poses, const double* intrinsics);
@@ -194,6 +211,19 @@ pba_status pba_num_residuals(pba_ctx* ctx, int bundle, int64_t* n);
 #define PBA_TIMING_SLOTS 7
 pba_status pba_enable_timing(pba_ctx* ctx, int mask);
 pba_status pba_last_timing(pba_ctx* ctx, double* out);
+
+/* Per-bundle device errors seen by the last call that synchronised (bit 0:
+ * reduced camera system not positive definite, bit 1: non-finite update).
+ * When a call returns PBA_ERR_NOT_PD or PBA_ERR_NONFINITE, the bundles whose
+ * flags are 0 were solved normally (bundles never share a sum). flags: host,
+ * n_bundles ints. */
+pba_status pba_bundle_errors(pba_ctx* ctx, int* flags);
+
+/* Launch shapes in use (after autotuning, or the defaults 8 and the largest
+ * cluster the device co-schedules): res_warps = warps per CTA of the IC
+ * residual pass, ldl_cluster = CTAs per bundle of the factorisation. Host,
+ * nullable each. */
+pba_status pba_get_tuning(pba_ctx* ctx, int* res_warps, int* ldl_cluster);
 
 /* Bytes this context copied host->device and device->host since it was
  * created (uploads of images, points, structure and parameters; downloads of

@@ -5,6 +5,6 @@ Singh (ICCV 2017, arXiv 1704.06967).
 The compute path is libpba.so (hand-written CUDA for sm_103a, C ABI in
 include/pba.h); `pba` is its thin ctypes binding.
 """
-from .pba import Bundle, PbaError, declared_symbols, load
+from .pba import Batch, Bundle, PbaError, declared_symbols, load
 
-__all__ = ["Bundle", "PbaError", "declared_symbols", "load"]
+__all__ = ["Batch", "Bundle", "PbaError", "declared_symbols", "load"]

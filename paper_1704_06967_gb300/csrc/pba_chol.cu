@@ -52,10 +52,10 @@ struct CholSmem {
 
 // reciprocal of a pivot; a non-positive one (of a real row) is flagged and
 // replaced by 1
-__device__ __forceinline__ dfloat pivot_recip(dfloat& d, bool real, int* err)
+__device__ __forceinline__ dfloat pivot_recip(dfloat& d, bool real, int* err, int bundle)
 {
     if (!(d.x > 0.0f)) {
-        if (real) atomicOr(err, kErrNotPD);
+        if (real) flag_error(err, bundle, kErrNotPD);
         d = df_make(1.0f, 0.0f);
     }
     return df_recip(d);
@@ -66,14 +66,22 @@ __device__ __forceinline__ dfloat pivot_recip(dfloat& d, bool real, int* err)
 // step j the diagonal block's active elements (j < m <= i) are packed onto
 // the first (31-j)(32-j)/2 threads through a table, and the rows below use
 // the top warps, so no issue slot goes to an element that is already done.
+// Cluster c of the grid factors bundle c's system.
 __global__ void __launch_bounds__(kCholThreads)
-ldl_cluster_kernel(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv, const int* cmap,
-                   int F, int aug, int* err)
+ldl_cluster_kernel(BundleSet bs, dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv,
+                   const int* cmap, int aug, int* err)
 {
     __shared__ CholSmem sm;
-    const int n = 6 * cmap[F];  // active frames only (the same value in every CTA)
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank(), C = (int)cl.num_blocks();
+    const int bundle = (int)blockIdx.x / C;
+    const BundleDesc bd = bundle_at(bs, bundle);
+    A += bd.ao;
+    L += bd.ao;
+    Linv += bd.lo;
+    dpiv += bd.po;
+    rpiv += bd.po;
+    const int n = 6 * cmap[bd.co + bd.F];  // active frames only (the same value in every CTA)
     const int tid = threadIdx.x, wi = tid >> 5, lm = tid & 31;
     const int nrow = n + aug;  // rows of A / L (the last one is b^T when aug)
     const int nblk = (n + kNB - 1) / kNB;
@@ -107,7 +115,7 @@ ldl_cluster_kernel(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpi
             }
             sm.T0[wi][lm] = (wi < nr && lm < nk) ? A[(size_t)(r0 + wi) * n + k0 + lm] : df_make(0.0f, 0.0f);
             __syncthreads();
-            if (first && tid == 0) sm.r[0] = pivot_recip(sm.D[0][0], nk > 0, err);
+            if (first && tid == 0) sm.r[0] = pivot_recip(sm.D[0][0], nk > 0, err, bundle);
             __syncthreads();
             // ---- right-looking elimination, one barrier per pivot: the
             // diagonal block (first chunk only; later chunks reuse its
@@ -121,7 +129,7 @@ ldl_cluster_kernel(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpi
                     dfloat v = df_fnms(lij, sm.D[m][j], sm.D[i][m]);
                     // the owner of (j+1, j+1) has just formed it: next reciprocal
                     // straight from the register
-                    if (i == j + 1 && m == j + 1) sm.r[j + 1] = pivot_recip(v, j + 1 < nk, err);
+                    if (i == j + 1 && m == j + 1) sm.r[j + 1] = pivot_recip(v, j + 1 < nk, err, bundle);
                     sm.D[i][m] = v;
                 }
                 const int ra = kNB - 1 - wi;  // rows below on the top warps
@@ -213,15 +221,21 @@ ldl_cluster_kernel(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpi
 // S^-1 = L^-T D^-1 L^-1 over the active frames (compact nc x nc order,
 // double-float), one column (= row) per CTA: the column's forward
 // substitution (starting at its block), scaling and backward substitution.
-// CTAs beyond nc (the grid is sized for all frames) return at once.
+// blockIdx.y is the bundle; CTAs beyond its nc (the grid is sized for all
+// frames of the largest bundle) return at once.
 __global__ void __launch_bounds__(256)
-ldl_inverse_kernel(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, const int* cmap, int F,
+ldl_inverse_kernel(BundleSet bs, const dfloat* L, const dfloat* Linv, const dfloat* rpiv, const int* cmap,
                    dfloat* Sinv)
 {
     extern __shared__ dfloat xs[];
     __shared__ dfloat t[kLdlBlock];
-    const int nc = 6 * cmap[F], c = blockIdx.x;
+    const BundleDesc bd = bundle_at(bs, blockIdx.y);
+    const int nc = 6 * cmap[bd.co + bd.F], c = blockIdx.x;
     if (c >= nc) return;
+    L += bd.ao;
+    Linv += bd.lo;
+    rpiv += bd.po;
+    Sinv += bd.so;
     for (int i = threadIdx.x; i < nc; i += blockDim.x) xs[i] = df_make(i == c ? 1.0f : 0.0f, 0.0f);
     __syncthreads();
     ldl_forward_smem(L, Linv, nc, xs, t, c / kLdlBlock);
@@ -233,23 +247,27 @@ ldl_inverse_kernel(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, cons
 
 }  // namespace
 
-cudaError_t launch_ldl(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv, const int* cmap,
-                       int F, int aug, int* err, cudaStream_t st)
+cudaError_t launch_ldl(const BundleSet& bs, dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv,
+                       const int* cmap, int aug, int* err, cudaStream_t st, int cluster)
 {
+    const int C = cluster > 0 ? cluster : g_chol_cluster;
+    if (C > g_chol_cluster || (C & (C - 1)) || bs.B < 1) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(g_chol_cluster);
+    cfg.gridDim = dim3(C * bs.B);
     cfg.blockDim = dim3(kCholThreads);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = g_chol_cluster;
+    attr[0].val.clusterDim.x = C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, ldl_cluster_kernel, A, L, Linv, dpiv, rpiv, cmap, F, aug, err);
+    return cudaLaunchKernelEx(&cfg, ldl_cluster_kernel, bs, A, L, Linv, dpiv, rpiv, cmap, aug, err);
 }
+
+int ldl_max_cluster() { return g_chol_cluster; }
 
 cudaError_t ldl_setup()
 {
@@ -272,12 +290,12 @@ cudaError_t ldl_setup()
     return cudaSuccess;
 }
 
-cudaError_t launch_ldl_inverse(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, const int* cmap,
-                               int F, dfloat* Sinv, cudaStream_t st)
+cudaError_t launch_ldl_inverse(const BundleSet& bs, const dfloat* L, const dfloat* Linv, const dfloat* rpiv,
+                               const int* cmap, dfloat* Sinv, cudaStream_t st)
 {
-    if (F > 1024) return cudaErrorInvalidValue;
-    const int n6 = 6 * (F - 1);
-    ldl_inverse_kernel<<<n6, 256, sizeof(dfloat) * n6, st>>>(L, Linv, rpiv, cmap, F, Sinv);
+    const int n6 = bs.n6max;
+    if (n6 > 6 * 1023 || n6 < 1 || bs.B < 1 || bs.B > 65535) return cudaErrorInvalidValue;
+    ldl_inverse_kernel<<<dim3(n6, bs.B), 256, sizeof(dfloat) * n6, st>>>(bs, L, Linv, rpiv, cmap, Sinv);
     return cudaGetLastError();
 }
 

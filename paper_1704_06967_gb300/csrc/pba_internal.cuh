@@ -31,15 +31,36 @@ constexpr int kFrameConst = 64;       // floats of FP32 constants per frame
 constexpr int kEntryPartial = 40;     // floats of partial sums per entry (FC: 21 H_ff, 6 g_f, 6 corrections)
 constexpr int kStats = 8;             // doubles per statistics slot
 
-// device error word values (bit flags)
+// device error word values (bit flags); the error words are err[0] for the
+// whole context and err[1 + b] for bundle b
 constexpr int kErrNotPD = 1;
 constexpr int kErrNonFinite = 2;
+constexpr int kErrTimeout = 4;
+
+__device__ __forceinline__ void flag_error(int* err, int bundle, int bits)
+{
+    atomicOr(err, bits);
+    atomicOr(err + 1 + bundle, bits);
+}
 
 struct Entry {
     int f;          // target frame (1..F-1)
     unsigned mask;  // visible lanes
     int pair_off;   // first pair of the entry
     int tile;
+};
+
+// One bundle of a context (a context solves one or several independent
+// bundles; their frames, tiles and entries are concatenated, so the
+// per-entry, per-tile and per-frame kernels run over all bundles in one
+// launch). Its frames are the global frames fo .. fo + F - 1, fo being its
+// reference frame; its reduced camera system (order n6 = 6 (F - 1)) sits at
+// element offset so of the S, S_off and S^-1 arrays, its factorisation
+// matrices ((n6 + 1) x n6) at ao, the inverses of its diagonal blocks at lo,
+// its pivots at po and the compact frame map of its frames (F + 1 ints) at co.
+struct BundleDesc {
+    int fo, F, co, po;
+    long long so, ao, lo;
 };
 
 // Per-tile statistics partials (FP32 sums of one tile).
@@ -49,7 +70,7 @@ struct TileStats {
 
 // Everything the kernels need, passed by value.
 struct DevProblem {
-    int F, N, Npad, T, E, P, W, H, pitch, dtype;
+    int F, N, Npad, T, E, P, W, H, pitch, dtype;  // F, N, T, E: totals over the bundles
     float fx, fy, cx, cy, huber_k;
     const void* img;            // F frames, H rows of `pitch` elements
     const float* gx;            // FC gradient images (F*H*W), nullable for IC
@@ -59,7 +80,9 @@ struct DevProblem {
     const int* tile_entry;      // T+1 offsets into entries
     const int* frame_entry;     // F+1 offsets of each frame's partial-sum rows
     const int* entry_slot;      // E partial-sum row of each entry (frame-major order)
-    const int* ent_of;          // T*F entry id of (tile, frame) or -1
+    const int* frame_bundle;    // F bundle of each global frame
+    const BundleDesc* bund;     // bundles
+    const int* tile_f0;         // T reference frame of each tile's bundle
     const int* uvs;             // Npad*2 sorted pixels (pad: copy of a real point)
     const float2* xn;           // Npad normalised centre coordinates
     const float* I0p;           // T*P*32 template intensities [tile][j][lane]
@@ -78,7 +101,8 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
-// image access (offsets are 32-bit: the host checks F * H * pitch < 2^31)
+// image access (offsets are unsigned 32-bit: the host checks that the whole
+// stack, F * H * pitch elements over all bundles, stays below 2^32)
 // ---------------------------------------------------------------------------
 template <int DT>
 __device__ __forceinline__ float load_px_t(const void* img, unsigned idx)

@@ -81,6 +81,12 @@ depth_update_kernel(DevProblem pb, DepthState ds, const float2* __restrict__ dth
         if (warp != 0) return;
         if (lane < 6) d[lane] = a.dtheta64[6 * f + lane];
         __syncwarp();
+        // a zero update (a bundle's reference frame, a frame without
+        // residuals) leaves the pose exactly as it is
+        if (__all_sync(0xffffffffu, lane >= 6 || d[lane] == 0.0)) {
+            if (lane < 12) a.fc_prev[12 * f + lane] = (float)a.poses64[12 * f + lane];
+            return;
+        }
         if (kIcRule) ic_pose_update_warp(a, f, a.poses64 + 12 * f, a.poses0 + 12 * f, d, sh, lane);
         else fc_pose_update_warp(a, f, d, sh, lane);
         return;
@@ -147,7 +153,7 @@ depth_update_kernel(DevProblem pb, DepthState ds, const float2* __restrict__ dth
                 d = dn;
                 ds.d64[n] = d;
             } else {
-                atomicOr(ds.err, kErrNonFinite);
+                flag_error(ds.err, pb.frame_bundle[pb.tile_f0[t]], kErrNonFinite);
             }
         }
         ds.dd_last[n] = dd;
@@ -191,15 +197,15 @@ __device__ __forceinline__ void tile_stats_from_entries(const DevProblem& pb, co
 // w r (r, or k sign r: exact, no division); phase 4 streams the stored rows
 // J and adds J_theta w r into the frame sum and J_d w r into the point's.
 // ---------------------------------------------------------------------------
-template <int PMAX, bool kAccum, int DT>
-__global__ void __launch_bounds__(kResWarps * 32, PMAX <= 8 ? 4 : 2)
+template <int PMAX, bool kAccum, int DT, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, (PMAX <= 8 ? 32 : 16) / WARPS)
 ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float* __restrict__ fprev,
                    const float* __restrict__ dcur, const float* __restrict__ dprev,
                    const float4* __restrict__ J4, float* __restrict__ ent_part,
                    float* __restrict__ gpart, float4* __restrict__ estats, int have_prev)
 {
     const int lane = threadIdx.x & 31;
-    const int e = blockIdx.x * kResWarps + (threadIdx.x >> 5);
+    const int e = blockIdx.x * WARPS + (threadIdx.x >> 5);
     pdl_trigger();
     pdl_wait();
     if (e >= pb.E) return;
@@ -590,28 +596,37 @@ ic_solve_kernel(SolveArgs a, const dfloat* __restrict__ Sinv, const double* __re
 {
     extern __shared__ dfloat ys[];  // nc, compact order; then F ints
     __shared__ double dth[9], d[6];
-    const int F = a.F, f = blockIdx.x + 1, lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    const int fg = blockIdx.x + 1, lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    // the bundle of global frame fg (static data: read before the wait)
+    const BundleDesc bd = a.bund[a.frame_bundle[fg]];
+    const int F = bd.F, f = fg - bd.fo;
+    const int* cmap = a.cmap + bd.co;
+    const double* tanchor = a.tanchor + (size_t)12 * bd.fo;
+    Sinv += bd.so;
+    y += (size_t)6 * bd.fo;
     pdl_trigger();
     pdl_wait();
-    const int kf = a.cmap[f], nc = 6 * a.cmap[F], anchor = a.active[0];
+    // the reference frame of a bundle (f = 0) and frames without residuals
+    // get a zero update
+    const int kf = f > 0 ? cmap[f] : -1, nc = 6 * cmap[F], anchor = a.active[bd.fo];
     int* frame_of = reinterpret_cast<int*>(ys + 6 * (F - 1));
     if (kf < 0) {
         if (row == 0) {
             if (lane < 6) d[lane] = 0.0;
             __syncwarp();
-            write_update_lanes(a, f, d, lane);
+            write_update_lanes(a, fg, d, lane);
         }
         return;
     }
     for (int g = 1 + threadIdx.x; g < F; g += blockDim.x) {
-        const int k = a.cmap[g];
+        const int k = cmap[g];
         if (k >= 0) frame_of[k] = g;
     }
     __syncthreads();
     for (int c = threadIdx.x; c < nc; c += blockDim.x)
         ys[c] = df_from_double(y[(size_t)frame_of[c / 6] * 6 + c % 6]);
     __syncthreads();
-    const int r = row < 6 ? 6 * kf + row : (anchor > 0 ? 6 * a.cmap[anchor] + row - 6 : -1);
+    const int r = row < 6 ? 6 * kf + row : (anchor > 0 ? 6 * cmap[anchor] + row - 6 : -1);
     if (r >= 0) {
         DfAcc acc;
         const dfloat* Sr = Sinv + (size_t)r * nc;
@@ -624,116 +639,17 @@ ic_solve_kernel(SolveArgs a, const dfloat* __restrict__ Sinv, const double* __re
     if (row != 0) return;
     if (lane < 6) {
         double v = dth[lane];
-        if (lane < 3 && anchor > 0) v = fma(-gauge_alpha(a.tanchor + 12 * anchor + 9, dth + 6), a.tanchor[12 * f + 9 + lane], v);
+        if (lane < 3 && anchor > 0) v = fma(-gauge_alpha(tanchor + 12 * anchor + 9, dth + 6), tanchor[12 * f + 9 + lane], v);
         d[lane] = v;
     }
     __syncwarp();
     const bool ok = __all_sync(0xffffffffu, lane >= 6 || isfinite(d[lane]));
     if (!ok) {
-        if (lane == 0) atomicOr(a.err, kErrNonFinite);
+        if (lane == 0) flag_error(a.err, a.frame_bundle[fg], kErrNonFinite);
         if (lane < 6) d[lane] = 0.0;
         __syncwarp();
     }
-    write_update_lanes(a, f, d, lane);
-}
-
-// ---------------------------------------------------------------------------
-// launchers
-// ---------------------------------------------------------------------------
-// IC step (Sec. 3.5 steps 3-4, Sec. 3.6) in one launch of F CTAs: CTA f-1
-// sums frame f's right-hand side y_f = sum_e (g_f,e - c_e) over its entries
-// in a fixed order, CTA F-1 folds the statistics; the CTA that finishes last
-// (a ticket drawn after a memory fence; nothing waits) forms
-// Dtheta = -S^-1 y over the active frames as a double-float GEMV (S^-1 in
-// compact order; a warp takes four rows at once so their loads share one
-// round trip), imposes the exact gauge constraint and writes the update;
-// the pose updates run in the next launch (depth_update_kernel), one frame
-// per CTA.
-// ---------------------------------------------------------------------------
-constexpr int kStepThreads = 1024;
-constexpr int kStepWarps = kStepThreads / 32;
-
-__global__ void __launch_bounds__(kStepThreads)
-ic_step_kernel(DevProblem pb, const float* __restrict__ ent_part, const TileStats* __restrict__ tstats,
-               const float* __restrict__ dthsq, double* __restrict__ stats, int slot_cur, int slot_prev,
-               SolveArgs a, const dfloat* __restrict__ Sinv, dfloat* y2, unsigned* ticket)
-{
-    extern __shared__ double tail_smem[];
-    __shared__ unsigned s_ticket;
-    __shared__ double s_alpha;
-    __shared__ double dsh[kStepWarps][6];
-    const int F = pb.F, n6 = 6 * (F - 1), tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if ((int)blockIdx.x < F - 1) {
-        const int f = blockIdx.x + 1;
-        float vs, vc;
-        frame_rows_sum<6, 6, 0, kStepThreads>(pb, ent_part, f, vs, vc);
-        if (tid < 6) y2[6 * (f - 1) + tid] = df_norm(vs, vc);
-    } else {
-        stats_block<kStepThreads>(pb, tstats, dthsq, stats, slot_cur, slot_prev);
-    }
-    // the last CTA to finish takes the solve
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_ticket = atomicAdd(ticket, 1u);
-    __syncthreads();
-    if (s_ticket != gridDim.x - 1) return;
-    __threadfence();
-    const int nc = 6 * a.cmap[F];
-    double* dth = tail_smem;                                     // n6, full order
-    double* dthc = tail_smem + n6;                               // nc, compact order
-    dfloat* ys = reinterpret_cast<dfloat*>(tail_smem + 2 * n6);  // nc, compact order
-    for (int i = tid; i < n6; i += kStepThreads) {
-        const int k = a.cmap[i / 6 + 1];
-        if (k >= 0) ys[6 * k + i % 6] = __ldcg(y2 + i);
-    }
-    __syncthreads();
-    for (int r0 = warp; r0 < nc; r0 += 4 * kStepWarps) {
-        DfAcc acc[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int r = r0 + u * kStepWarps;
-            if (r < nc) {
-                const dfloat* Sr = Sinv + (size_t)r * nc;
-                for (int c = lane; c < nc; c += 32) acc[u].add_prod(Sr[c], ys[c]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            float ss = acc[u].s, cc = acc[u].c;
-            warp_sum_pair(ss, cc);
-            const int r = r0 + u * kStepWarps;
-            if (lane == 0 && r < nc) dthc[r] = -((double)ss + (double)cc);
-        }
-    }
-    __syncthreads();
-    for (int i = tid; i < n6; i += kStepThreads) {
-        const int k = a.cmap[i / 6 + 1];
-        dth[i] = k >= 0 ? dthc[6 * k + i % 6] : 0.0;
-    }
-    __syncthreads();
-    const int anchor = a.active[0];
-    if (tid == 0) {
-        s_alpha = anchor > 0 ? gauge_alpha(a.tanchor + 12 * anchor + 9, dth + 6 * (anchor - 1)) : 0.0;
-        *ticket = 0u;  // ready for the next launch
-    }
-    __syncthreads();
-    for (int f = 1 + warp; f < F; f += kStepWarps) {
-        double* d = dsh[warp];
-        if (lane < 6) {
-            double v = dth[6 * (f - 1) + lane];
-            if (lane < 3 && anchor > 0 && a.active[f]) v = fma(-s_alpha, a.tanchor[12 * f + 9 + lane], v);
-            d[lane] = v;
-        }
-        __syncwarp();
-        const bool ok = __all_sync(0xffffffffu, lane >= 6 || isfinite(d[lane]));
-        if (!ok) {
-            if (lane == 0) atomicOr(a.err, kErrNonFinite);
-            if (lane < 6) d[lane] = 0.0;
-            __syncwarp();
-        }
-        write_update_lanes(a, f, d, lane);
-        __syncwarp();
-    }
+    write_update_lanes(a, fg, d, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -753,13 +669,23 @@ cudaError_t launch_depth_update(const LaunchCtx& L, const SolveArgs& a, bool ic_
     return cudaGetLastError();
 }
 
+template <int PMAX, bool A, int DT, int WARPS>
+static cudaError_t ic_residual_w(const LaunchCtx& L, int have_prev)
+{
+    const int blocks = (L.pb.E + WARPS - 1) / WARPS;
+    return launch_pdl(ic_residual_kernel<PMAX, A, DT, WARPS>, blocks, WARPS * 32, 0, L.stream, L.pb, L.fs.fc,
+                      L.fs.fc_prev, L.it.dcur, L.it.dprev, L.ic.J4, L.ent_part, L.it.gpart, L.it.estats,
+                      have_prev);
+}
+
+// warps (entries) per CTA: the autotuner's choice for the accumulating pass
+// (4, 8 or 16); the evaluation pass keeps 8
 template <int PMAX, bool A, int DT>
 static cudaError_t ic_residual_p(const LaunchCtx& L, int have_prev)
 {
-    const int blocks = (L.pb.E + kResWarps - 1) / kResWarps;
-    return launch_pdl(ic_residual_kernel<PMAX, A, DT>, blocks, kResWarps * 32, 0, L.stream, L.pb, L.fs.fc,
-                      L.fs.fc_prev, L.it.dcur, L.it.dprev, L.ic.J4, L.ent_part, L.it.gpart, L.it.estats,
-                      have_prev);
+    if (A && L.res_warps == 4) return ic_residual_w<PMAX, A, DT, 4>(L, have_prev);
+    if (A && L.res_warps == 16) return ic_residual_w<PMAX, A, DT, 16>(L, have_prev);
+    return ic_residual_w<PMAX, A, DT, kResWarps>(L, have_prev);
 }
 
 cudaError_t launch_ic_residual(const LaunchCtx& L, bool accum, int have_prev)
@@ -819,9 +745,17 @@ cudaError_t launch_fc_point(const LaunchCtx& L, bool accum)
 
 cudaError_t launch_ic_solve(const SolveArgs& a, const dfloat* Sinv, const double* y, cudaStream_t st)
 {
-    const int F = a.F;
-    return launch_pdl(ic_solve_kernel, F - 1, 9 * 32, sizeof(dfloat) * 6 * (F - 1) + sizeof(int) * F, st, a,
+    return launch_pdl(ic_solve_kernel, a.F - 1, 9 * 32, sizeof(dfloat) * a.n6 + sizeof(int) * a.Fmax, st, a,
                       Sinv, y);
+}
+
+cudaError_t iter_setup()
+{
+    // dynamic shared memory above the default 48 KB for the largest systems
+    // (1024 frames: 6138 rows)
+    cudaError_t e = cudaFuncSetAttribute(ic_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(dfloat) * 6 * 1023 + sizeof(int) * 1024));
+    return e;
 }
 
 }  // namespace pba

@@ -79,6 +79,7 @@ struct LaunchCtx {
     double* stats;    // slots * kStats
     const double* poses0;  // F*12 FP64 poses at p_0
     cudaStream_t stream;
+    int res_warps;         // warps per CTA of the accumulating IC residual pass (4, 8, 16)
 };
 
 cudaError_t launch_ic_precompute(const LaunchCtx& L);
@@ -89,9 +90,26 @@ cudaError_t launch_frame_reduce(const LaunchCtx& L, int off, int ncomp, double* 
                                 int slot_prev, bool frames, int sub = -1, int sub_from = 0);
 cudaError_t launch_fc_residual(const LaunchCtx& L, bool accum, int have_prev);
 
+// The bundles of a launch over reduced camera systems: B bundles described
+// by the device array bund, or (bund null) the one bundle `one`.
+struct BundleSet {
+    int B;
+    const BundleDesc* bund;
+    BundleDesc one;
+    int n6max;  // largest 6 (F - 1) of the bundles
+};
+
+__device__ __forceinline__ BundleDesc bundle_at(const BundleSet& s, int b)
+{
+    return s.bund ? s.bund[b] : s.one;
+}
+
 // linear algebra (pba_linalg.cu)
 struct SolveArgs {
-    int F, n6;
+    int F, n6;              // total frames; largest 6 (F_b - 1) of the bundles
+    int B, Fmax;            // bundles; largest frame count of a bundle
+    const BundleDesc* bund;        // B bundles (device)
+    const int* frame_bundle;       // F bundle of each global frame
     const int* pat;
     int P;
     double fx, fy, inv_fx, inv_fy;
@@ -103,8 +121,9 @@ struct SolveArgs {
     float* fc_prev;         // F*12
     float* dthsq;           // F
     int* err;
-    const int* active;      // [0] anchor frame, [f] frame has residuals
-    const int* cmap;        // [f] compact index of an active frame or -1, [F] their number
+    const int* active;      // per bundle at fo: [0] anchor frame, [f] frame has residuals
+    const int* cmap;        // per bundle at co: [f] compact index of an active frame or -1,
+                            // [F_b] their number
     const double* tanchor;  // F*12 poses whose t define the gauge direction
 };
 
@@ -113,8 +132,8 @@ struct SolveArgs {
 cudaError_t launch_depth_update(const LaunchCtx& L, const SolveArgs& a, bool ic_rule, int apply);
 cudaError_t launch_ic_point(const LaunchCtx& L, bool accum);
 cudaError_t launch_fc_point(const LaunchCtx& L, bool accum);
-// Dtheta = -S^-1 y (compact S^-1, y per frame as written by the frame
-// reduction), the gauge constraint and every frame's update
+// Dtheta = -S^-1 y (per bundle the compact S^-1 at so, y per global frame as
+// written by the frame reduction), the gauge constraint and every frame's update
 cudaError_t launch_ic_solve(const SolveArgs& a, const dfloat* Sinv, const double* y, cudaStream_t st);
 
 // Schur complement (pba_schur.cu)
@@ -135,30 +154,38 @@ constexpr int kSchurChunk = 32;
 cudaError_t launch_schur_sparse(const DevProblem& pb, const float* Hfd, const float* Hnn,
                                 const SchurLists& sl, float2* part, double* Soff,
                                 cudaStream_t st, int* launches);
-// S (FP64) and, when S2 is given, its double-float copy over the active
-// frames only (compact order, cmap[f] = compact index or -1, cmap[F] = their
-// number; the factorisation's working matrix; with rhs, one extra row b = -y
-// taken from rhs[f * rhs_stride + rhs_off + a])
-cudaError_t launch_assemble_S(int F, const double* Hff, int hff_stride, const double* Soff,
+// Per bundle (arrays at the bundle's offsets; Hff, anchor_t, rhs and active
+// indexed by global frame): S (FP64) and, when S2 is given, its double-float
+// copy over the active frames only (compact order, cmap[f] = compact index
+// or -1, cmap[F_b] = their number; the factorisation's working matrix; with
+// rhs, one extra row b = -y taken from rhs[f * rhs_stride + rhs_off + a])
+cudaError_t launch_assemble_S(const BundleSet& bs, const double* Hff, int hff_stride, const double* Soff,
                               const double* anchor_t, double gauge_w, double* S, int* active,
                               cudaStream_t st, dfloat* S2 = nullptr, int* cmap = nullptr,
                               const double* rhs = nullptr, int rhs_stride = 0, int rhs_off = 0);
-// double-float LDL^T (pba_chol.cu): A ((n + aug) x n, consumed) -> L (unit
-// lower with L^T in the upper triangle; with aug, row n = D^-1 L^-1 b),
-// Linv (inverses of the 32 x 32 diagonal blocks and their transposes),
-// dpiv = d_j, rpiv = 1 / d_j
-// the order n = 6 * cmap[F] is read on the device (the active frames)
-cudaError_t launch_ldl(dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv, const int* cmap,
-                       int F, int aug, int* err, cudaStream_t st);
-cudaError_t ldl_setup();  // once per process and device, before any capture
-// S^-1 over the active frames (compact nc x nc, nc = 6 cmap[F])
-cudaError_t launch_ldl_inverse(const dfloat* L, const dfloat* Linv, const dfloat* rpiv, const int* cmap,
-                               int F, dfloat* Sinv, cudaStream_t st);
+// double-float LDL^T (pba_chol.cu), one thread-block cluster per bundle:
+// A ((n + aug) x n, consumed) -> L (unit lower with L^T in the upper
+// triangle; with aug, row n = D^-1 L^-1 b), Linv (inverses of the 32 x 32
+// diagonal blocks and their transposes), dpiv = d_j, rpiv = 1 / d_j.
+// The order n = 6 * cmap[F_b] is read on the device (the active frames).
+// cluster: CTAs per bundle (0: the default chosen by ldl_setup)
+cudaError_t launch_ldl(const BundleSet& bs, dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpiv, dfloat* rpiv,
+                       const int* cmap, int aug, int* err, cudaStream_t st, int cluster = 0);
+// once per process and device, before any capture: cluster size of the
+// factorisation, shared-memory limits of the solves
+cudaError_t ldl_setup();
+cudaError_t iter_setup();
+cudaError_t linalg_setup();
+int ldl_max_cluster();    // the largest cluster size ldl_setup found usable (8 or 16)
+// S^-1 over the active frames (compact nc x nc, nc = 6 cmap[F_b]) per bundle
+cudaError_t launch_ldl_inverse(const BundleSet& bs, const dfloat* L, const dfloat* Linv, const dfloat* rpiv,
+                               const int* cmap, dfloat* Sinv, cudaStream_t st);
+// one CTA per bundle
 cudaError_t launch_fc_solve_update(const SolveArgs& a, const dfloat* L, const dfloat* Linv,
                                    cudaStream_t st);
 
-// setup kernels (pba_runtime.cu)
-cudaError_t launch_setup(const DevProblem& pb, float* gx, float* gy, float* I0p, float2* G0p,
-                         cudaStream_t st);
+// setup kernels (pba_runtime.cu); tile_f0[t] = reference frame of tile t
+cudaError_t launch_setup(const DevProblem& pb, const int* tile_f0, float* gx, float* gy, float* I0p,
+                         float2* G0p, cudaStream_t st);
 
 }  // namespace pba

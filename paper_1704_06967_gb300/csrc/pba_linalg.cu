@@ -34,8 +34,9 @@ __device__ __forceinline__ int upper_index(int a, int b)
 
 constexpr int kAssembleThreads = 256;
 
+// Bundle blockIdx.y of bs, gridDim.x CTAs per bundle.
 __global__ void __launch_bounds__(kAssembleThreads)
-assemble_S_kernel(int F, const double* Hff, int stride, const double* Soff,
+assemble_S_kernel(BundleSet bs, const double* Hff, int stride, const double* Soff,
                   const double* anchor_t, double gauge_w, double* S, int* active, dfloat* S2,
                   int* cmap, const double* rhs, int rhs_stride, int rhs_off)
 {
@@ -45,6 +46,16 @@ assemble_S_kernel(int F, const double* Hff, int stride, const double* Soff,
     __shared__ double s_red[kAssembleThreads / 32];
     __shared__ int s_anchor;
     __shared__ double s_mu;
+    const BundleDesc bd = bundle_at(bs, blockIdx.y);
+    const int F = bd.F;
+    Hff += (size_t)bd.fo * stride;
+    anchor_t += (size_t)12 * bd.fo;
+    active += bd.fo;
+    Soff += bd.so;
+    S += bd.so;
+    if (S2) S2 += bd.ao;
+    if (cmap) cmap += bd.co;
+    if (rhs) rhs += (size_t)bd.fo * rhs_stride;
     const int n6 = 6 * (F - 1), tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int f = 1 + tid; f < F; f += blockDim.x) {
         const double* h = Hff + (size_t)f * stride;
@@ -129,77 +140,95 @@ assemble_S_kernel(int F, const double* Hff, int stride, const double* Soff,
         }
 }
 
-cudaError_t launch_assemble_S(int F, const double* Hff, int hff_stride, const double* Soff,
+cudaError_t launch_assemble_S(const BundleSet& bs, const double* Hff, int hff_stride, const double* Soff,
                               const double* anchor_t, double gauge_w, double* S, int* active,
                               cudaStream_t st, dfloat* S2, int* cmap, const double* rhs,
                               int rhs_stride, int rhs_off)
 {
     if (S2 && !cmap) return cudaErrorInvalidValue;
-    const int n6 = 6 * (F - 1);
-    if (F > 1024) return cudaErrorInvalidValue;
+    const int n6 = bs.n6max;
+    if (n6 > 6 * 1023 || bs.B < 1 || bs.B > 65535) return cudaErrorInvalidValue;
     // one element per thread on up to 148 SMs (the FP64 -> double-float
-    // conversions go to the slow FP64 pipe)
-    const int blocks = std::max(1, std::min(148, (n6 * n6 + kAssembleThreads - 1) / kAssembleThreads));
-    assemble_S_kernel<<<blocks, kAssembleThreads, 0, st>>>(F, Hff, hff_stride, Soff, anchor_t,
-                                                            gauge_w, S, active, S2, cmap, rhs,
-                                                            rhs_stride, rhs_off);
+    // conversions go to the slow FP64 pipe), spread over the bundles
+    const int per_bundle = std::max(1, 1184 / bs.B);
+    const int blocks =
+        std::max(1, std::min(std::min(148, per_bundle), (n6 * n6 + kAssembleThreads - 1) / kAssembleThreads));
+    assemble_S_kernel<<<dim3(blocks, bs.B), kAssembleThreads, 0, st>>>(bs, Hff, hff_stride, Soff, anchor_t,
+                                                                       gauge_w, S, active, S2, cmap, rhs,
+                                                                       rhs_stride, rhs_off);
     return cudaGetLastError();
 }
 
 // FC: the factorisation has eliminated b = -y with the matrix, so row n of L
 // holds D^-1 L^-1 b; the backward substitution L^T Dtheta = that row gives
-// Dtheta = -S^-1 y (double-float, one CTA). Then the exact gauge constraint;
-// the update is written per frame and the boxplus pose updates run in the
-// next launch, one frame per CTA.
-constexpr int kFcSolveWarps = 32;  // one warp per frame's update (F <= 33 in one round)
+// Dtheta = -S^-1 y (double-float, one CTA per bundle). Then the exact gauge
+// constraint; the update is written per frame (the reference frame's is
+// zero) and the boxplus pose updates run in the next launch, one frame per
+// CTA.
+constexpr int kFcSolveWarps = 32;  // one warp per frame's update
 
 __global__ void __launch_bounds__(kFcSolveWarps * 32) fc_solve_update_kernel(SolveArgs a, const dfloat* L,
                                                                            const dfloat* Linv)
 {
     extern __shared__ dfloat xs[];
     __shared__ dfloat tb[kLdlBlock];
-    double* x = reinterpret_cast<double*>(xs + a.n6);
     __shared__ double s_alpha;
-    __shared__ double sh[kFcSolveWarps][54];
     __shared__ double dsh[kFcSolveWarps][6];
-    const int n = a.n6, nc = 6 * a.cmap[a.F], tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const BundleDesc bd = a.bund[blockIdx.x];
+    const int F = bd.F, fo = bd.fo;
+    const int* cmap = a.cmap + bd.co;
+    const int* active = a.active + fo;
+    const double* tanchor = a.tanchor + (size_t)12 * fo;
+    L += bd.ao;
+    Linv += bd.lo;
+    double* x = reinterpret_cast<double*>(xs + a.n6);
+    const int n = 6 * (F - 1), nc = 6 * cmap[F], tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < nc; i += blockDim.x) xs[i] = L[(size_t)nc * nc + i];
     __syncthreads();
     ldl_backward_smem(L, Linv, nc, xs, tb);
     // back to the full frame order (frames left out get no update)
     for (int i = tid; i < n; i += blockDim.x) {
-        const int k = a.cmap[i / 6 + 1];
+        const int k = cmap[i / 6 + 1];
         x[i] = k >= 0 ? df_to_double(xs[6 * k + i % 6]) : 0.0;
     }
     __syncthreads();
     if (tid == 0) {
-        const int anchor = a.active[0];
-        s_alpha = anchor > 0 ? gauge_alpha(a.tanchor + 12 * anchor + 9, x + 6 * (anchor - 1)) : 0.0;
+        const int anchor = active[0];
+        s_alpha = anchor > 0 ? gauge_alpha(tanchor + 12 * anchor + 9, x + 6 * (anchor - 1)) : 0.0;
     }
     __syncthreads();
-    for (int f = 1 + warp; f < a.F; f += blockDim.x >> 5) {
+    for (int f = warp; f < F; f += blockDim.x >> 5) {
         double* d = dsh[warp];
         if (lane < 6) {
-            double v = x[6 * (f - 1) + lane];
-            if (lane < 3 && a.active[f]) v = fma(-s_alpha, a.tanchor[12 * f + 9 + lane], v);
+            double v = f > 0 ? x[6 * (f - 1) + lane] : 0.0;
+            if (lane < 3 && f > 0 && active[f]) v = fma(-s_alpha, tanchor[12 * f + 9 + lane], v);
             d[lane] = v;
         }
         __syncwarp();
         const bool ok = __all_sync(0xffffffffu, lane >= 6 || isfinite(d[lane]));
         if (!ok) {
-            if (lane == 0) atomicOr(a.err, kErrNonFinite);
+            if (lane == 0) flag_error(a.err, blockIdx.x, kErrNonFinite);
             if (lane < 6) d[lane] = 0.0;
             __syncwarp();
         }
-        write_update_lanes(a, f, d, lane);
+        write_update_lanes(a, fo + f, d, lane);
         __syncwarp();
     }
+}
+
+cudaError_t linalg_setup()
+{
+    // dynamic shared memory above the default 48 KB for the largest systems
+    // (1024 frames: 6138 rows)
+    return cudaFuncSetAttribute(fc_solve_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((sizeof(dfloat) + sizeof(double)) * 6 * 1023));
 }
 
 cudaError_t launch_fc_solve_update(const SolveArgs& a, const dfloat* L, const dfloat* Linv,
                                    cudaStream_t st)
 {
-    fc_solve_update_kernel<<<1, kFcSolveWarps * 32, (sizeof(dfloat) + sizeof(double)) * a.n6, st>>>(a, L, Linv);
+    fc_solve_update_kernel<<<a.B, kFcSolveWarps * 32, (sizeof(dfloat) + sizeof(double)) * a.n6, st>>>(a, L,
+                                                                                                     Linv);
     return cudaGetLastError();
 }
 

@@ -144,7 +144,11 @@ extern "C" pba_status pba_reduced_system_noalloc(int n_frames, int n_points, con
     schur_offdiag_dense_kernel<<<n_pairs, 32 * kWarps, 0, st>>>(F, n_points, Hff, Hfd, Hdd, soff,
                                                                 hff21);
     if (cudaGetLastError() != cudaSuccess) return PBA_ERR_CUDA;
-    if (launch_assemble_S(F, hff21, 21, soff, poses, gauge_anchor_w == 0.0 ? 1.0 : gauge_anchor_w,
+    BundleSet one{};
+    one.B = 1;
+    one.one.F = F;
+    one.n6max = 6 * (F - 1);
+    if (launch_assemble_S(one, hff21, 21, soff, poses, gauge_anchor_w == 0.0 ? 1.0 : gauge_anchor_w,
                           S, active, st) != cudaSuccess)
         return PBA_ERR_CUDA;
     return PBA_OK;

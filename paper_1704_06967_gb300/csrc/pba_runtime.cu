@@ -15,6 +15,7 @@
 
 #include "pba_chol.cuh"
 #include "pba_kernels.cuh"
+#include "pba_mlp.cuh"
 
 using namespace pba;
 
@@ -55,34 +56,49 @@ using GraphKey = std::tuple<int, int, int>;
 
 }  // namespace
 
+// Inputs of one bundle as the caller gave them, and its place in the
+// concatenated problem.
+struct BundleIn {
+    bool have_frames = false, have_points = false;
+    int F = 0;
+    const void* images = nullptr;
+    std::vector<double> poses_init;  // F*12
+    int N = 0;
+    std::vector<int32_t> uv;
+    std::vector<double> d_init;
+    std::vector<uint8_t> vis;  // N*F
+    // set by build_structure
+    int fo = 0, to = 0, T = 0, e0 = 0, e1 = 0;
+    int64_t V = 0;
+    std::vector<int> perm;  // slot (within the bundle's tiles) -> caller index, -1 for pads
+};
+
 struct pba_ctx {
     pba_config cfg{};
     std::vector<int32_t> pattern;
     cudaStream_t stream = nullptr;
     std::string err = "no error";
 
-    // frames
-    bool have_frames = false;
-    int F = 0, W = 0, H = 0, pitch = 0;
+    // bundles (cfg.n_bundles); they share the camera: image size, pitch,
+    // element type, memory kind and intrinsics
+    int B = 1;
+    std::vector<BundleIn> bun;
+    int W = 0, H = 0, pitch = 0;
     pba_dtype dtype = PBA_F32;
     pba_memory mem = PBA_MEM_DEVICE;
-    const void* images = nullptr;
-    std::vector<double> poses_init;  // F*12
     double K[4] = {0, 0, 0, 0};
 
-    // points
-    bool have_points = false;
-    int N = 0;
-    std::vector<int32_t> uv;
-    std::vector<double> d_init;
-    std::vector<uint8_t> vis;  // N*F
-
-    // derived host structures
-    int T = 0, Npad = 0, E = 0, NC = 0;
+    // derived host structures over all bundles (frames, tiles, entries and
+    // frame pairs concatenated bundle after bundle)
+    bool built = false;
+    int F = 0, N = 0;  // total frames and points
+    int T = 0, Npad = 0, E = 0, NC = 0, Fmax = 0, n6max = 0;
     int64_t V = 0;
-    std::vector<int> perm;  // sorted slot -> caller index (-1 for pads)
     std::vector<Entry> entries;
-    std::vector<int> tile_entry, frame_entry, entry_slot, ent_of;
+    std::vector<int> tile_entry, frame_entry, entry_slot, frame_bundle, tile_f0;
+    std::vector<BundleDesc> bdesc;
+    int64_t n_so = 0, n_ao = 0, n_lo = 0;  // sizes of the per-bundle system arrays
+    int n_po = 0, n_cmap = 0;
     std::vector<int> pair_fg, pair_chunk, chunk_pair, chunk_start;  // sparse Schur lists
     std::vector<int2> pair_items;
 
@@ -95,7 +111,8 @@ struct pba_ctx {
         float *gx, *gy;
         int* pat;
         Entry* entries;
-        int *tile_entry, *frame_entry, *entry_slot, *ent_of;
+        int *tile_entry, *frame_entry, *entry_slot, *frame_bundle, *tile_f0, *slot_caller;
+        BundleDesc* bund;
         int* uvs;
         float2* xn;
         float* I0p;
@@ -125,6 +142,10 @@ struct pba_ctx {
     } d{};
     int stats_slots = 0;
     int last_fc = 0;  // which system the last update came from
+    int ldl_cluster = 0;  // CTAs per bundle of the factorisation (0: default)
+    std::vector<int> bundle_err;  // per-bundle error bits of the last check
+    int res_warps = 8;    // warps per CTA of the IC residual pass
+    bool tuned = false;
 
     // instrumentation
     int timing = 0;  // slot mask
@@ -261,6 +282,11 @@ cudaError_t d2h(pba_ctx* ctx, void* dst, const void* src, size_t bytes)
     return e == cudaSuccess ? cudaStreamSynchronize(ctx->stream) : e;
 }
 
+// The context keeps its own copy of the image stack (in the workspace) when
+// the images come from the host, or when several bundles' stacks must be
+// made one contiguous array.
+bool own_images(const pba_ctx* c) { return c->mem == PBA_MEM_HOST || c->B > 1; }
+
 // Lays out (and optionally assigns) the workspace; returns its size.
 size_t layout(pba_ctx* c, char* base)
 {
@@ -270,8 +296,8 @@ size_t layout(pba_ctx* c, char* base)
         ptr = base ? reinterpret_cast<P>(base + off) : nullptr;
         off += align_up(std::max<size_t>(bytes, 1));
     };
-    const size_t F = c->F, HW = (size_t)c->H * c->W, Np = c->Npad, n6 = 6 * (c->F - 1);
-    if (c->mem == PBA_MEM_HOST) {
+    const size_t F = c->F, HW = (size_t)c->H * c->W, Np = c->Npad;
+    if (own_images(c)) {
         void*& img = c->d.img;
         char* p = nullptr;
         take(p, F * c->H * c->pitch * elem_size(c->dtype));
@@ -284,7 +310,10 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.tile_entry, (size_t)(c->T + 1) * 4);
     take(c->d.frame_entry, (F + 1) * 4);
     take(c->d.entry_slot, (size_t)c->E * 4);
-    take(c->d.ent_of, (size_t)c->T * F * 4);
+    take(c->d.frame_bundle, F * 4);
+    take(c->d.tile_f0, (size_t)c->T * 4);
+    take(c->d.bund, (size_t)c->B * sizeof(BundleDesc));
+    take(c->d.slot_caller, Np * 4);
     take(c->d.uvs, Np * 8);
     take(c->d.xn, Np * 8);
     take(c->d.I0p, (size_t)c->T * (c->pattern.size() / 2) * kTile * 4);
@@ -318,15 +347,15 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.dtheta64, F * 6 * 8);
     take(c->d.red_ic, F * 21 * 8);
     take(c->d.red_y, F * 27 * 8);
-    take(c->d.Soff, n6 * n6 * 8);
-    take(c->d.S_ic, n6 * n6 * 8);
-    take(c->d.Sinv2, n6 * n6 * sizeof(dfloat));
-    take(c->d.S_fc, n6 * n6 * 8);
-    take(c->d.A2, (n6 + 1) * n6 * sizeof(dfloat));
-    take(c->d.L2, (n6 + 1) * n6 * sizeof(dfloat));
-    take(c->d.Linv, (n6 + 31) / 32 * kLinvStride * sizeof(dfloat));
-    take(c->d.dpiv, n6 * sizeof(dfloat));
-    take(c->d.rpiv, n6 * sizeof(dfloat));
+    take(c->d.Soff, (size_t)c->n_so * 8);
+    take(c->d.S_ic, (size_t)c->n_so * 8);
+    take(c->d.Sinv2, (size_t)c->n_so * sizeof(dfloat));
+    take(c->d.S_fc, (size_t)c->n_so * 8);
+    take(c->d.A2, (size_t)c->n_ao * sizeof(dfloat));
+    take(c->d.L2, (size_t)c->n_ao * sizeof(dfloat));
+    take(c->d.Linv, (size_t)c->n_lo * sizeof(dfloat));
+    take(c->d.dpiv, (size_t)c->n_po * sizeof(dfloat));
+    take(c->d.rpiv, (size_t)c->n_po * sizeof(dfloat));
     take(c->d.pair_fg, c->pair_fg.size() * sizeof(int));
     take(c->d.pair_chunk, c->pair_chunk.size() * sizeof(int));
     take(c->d.chunk_pair, c->chunk_pair.size() * sizeof(int));
@@ -335,48 +364,128 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.schur_part, c->chunk_pair.size() * 36 * sizeof(float2));
     take(c->d.active_ic, F * 4);
     take(c->d.active_fc, F * 4);
-    take(c->d.cmap_ic, (F + 1) * 4);
-    take(c->d.cmap_fc, (F + 1) * 4);
-    take(c->d.err, 64);
+    take(c->d.cmap_ic, (size_t)c->n_cmap * 4);
+    take(c->d.cmap_fc, (size_t)c->n_cmap * 4);
+    take(c->d.err, (size_t)(1 + c->B) * 4);
     take(c->d.stats, (size_t)(c->stats_slots) * kStats * 8);
     return off;
 }
 
-// Sorted point order, tiles, (tile, frame) entries and their lookups.
+bool all_set(const pba_ctx* c)
+{
+    for (const BundleIn& b : c->bun)
+        if (!b.have_frames || !b.have_points) return false;
+    return true;
+}
+
+// Sorted point order, tiles, (tile, frame) entries, frame pairs and the
+// per-bundle system offsets, bundle after bundle (frames, tiles and entries
+// of bundle b follow those of bundle b - 1).
 void build_structure(pba_ctx* c)
 {
-    const int N = c->N, F = c->F;
-    std::vector<std::pair<uint64_t, int>> key(N);
-    for (int n = 0; n < N; ++n) {
-        uint32_t u = (uint32_t)c->uv[2 * n], v = (uint32_t)c->uv[2 * n + 1];
-        key[n] = {((uint64_t)(spread16(u) | (spread16(v) << 1)) << 32) | (uint32_t)n, n};
-    }
-    std::sort(key.begin(), key.end());
-    c->T = (N + kTile - 1) / kTile;
-    c->Npad = c->T * kTile;
-    c->perm.assign(c->Npad, -1);
-    for (int i = 0; i < N; ++i) c->perm[i] = key[i].second;
+    c->F = c->N = c->T = 0;
+    c->V = 0;
+    c->Fmax = c->n6max = 0;
     c->entries.clear();
-    c->tile_entry.assign(c->T + 1, 0);
-    c->ent_of.assign((size_t)c->T * F, -1);
+    c->tile_entry.clear();
+    c->frame_bundle.clear();
+    c->tile_f0.clear();
+    c->bdesc.clear();
+    c->n_so = c->n_ao = c->n_lo = 0;
+    c->n_po = c->n_cmap = 0;
+    c->pair_fg.clear();
+    c->pair_chunk.assign(1, 0);
+    c->chunk_pair.clear();
+    c->chunk_start.assign(1, 0);
+    c->pair_items.clear();
+    c->NC = (7 * (int)(c->pattern.size() / 2) + 3) / 4;
     int64_t pairs = 0;
-    for (int t = 0; t < c->T; ++t) {
-        c->tile_entry[t] = (int)c->entries.size();
-        for (int f = 1; f < F; ++f) {
-            unsigned mask = 0;
-            for (int l = 0; l < kTile; ++l) {
-                const int n = c->perm[t * kTile + l];
-                if (n >= 0 && c->vis[(size_t)n * F + f]) mask |= 1u << l;
-            }
-            if (!mask) continue;
-            c->ent_of[(size_t)t * F + f] = (int)c->entries.size();
-            c->entries.push_back(Entry{f, mask, (int)pairs, t});
-            pairs += __builtin_popcount(mask);
+    for (int bi = 0; bi < c->B; ++bi) {
+        BundleIn& b = c->bun[bi];
+        const int N = b.N, F = b.F;
+        b.fo = c->F;
+        b.to = c->T;
+        b.e0 = (int)c->entries.size();
+        std::vector<std::pair<uint64_t, int>> key(N);
+        for (int n = 0; n < N; ++n) {
+            uint32_t u = (uint32_t)b.uv[2 * n], v = (uint32_t)b.uv[2 * n + 1];
+            key[n] = {((uint64_t)(spread16(u) | (spread16(v) << 1)) << 32) | (uint32_t)n, n};
         }
+        std::sort(key.begin(), key.end());
+        b.T = (N + kTile - 1) / kTile;
+        b.perm.assign((size_t)b.T * kTile, -1);
+        for (int i = 0; i < N; ++i) b.perm[i] = key[i].second;
+        std::vector<int> ent_of((size_t)b.T * F, -1);  // local (tile, frame) -> entry
+        const int64_t pairs0 = pairs;
+        for (int t = 0; t < b.T; ++t) {
+            c->tile_entry.push_back((int)c->entries.size());
+            c->tile_f0.push_back(b.fo);
+            for (int f = 1; f < F; ++f) {
+                unsigned mask = 0;
+                for (int l = 0; l < kTile; ++l) {
+                    const int n = b.perm[t * kTile + l];
+                    if (n >= 0 && b.vis[(size_t)n * F + f]) mask |= 1u << l;
+                }
+                if (!mask) continue;
+                ent_of[(size_t)t * F + f] = (int)c->entries.size();
+                c->entries.push_back(Entry{b.fo + f, mask, (int)pairs, b.to + t});
+                pairs += __builtin_popcount(mask);
+            }
+        }
+        b.e1 = (int)c->entries.size();
+        b.V = pairs - pairs0;
+        // frame pairs f <= g of the bundle with the (entry, entry) items of
+        // the tiles that see both (tile order: the sparse Schur kernel's
+        // fixed summation order), cut into chunks of at most kSchurChunk items
+        for (int f = 1; f < F; ++f)
+            for (int g = f; g < F; ++g) {
+                const int p = (int)c->pair_fg.size() / 2;
+                size_t n_in_chunk = 0;
+                for (int t = 0; t < b.T; ++t) {
+                    const int ea = ent_of[(size_t)t * F + f], eb = ent_of[(size_t)t * F + g];
+                    if (!(ea >= 0 && eb >= 0 && (c->entries[ea].mask & c->entries[eb].mask))) continue;
+                    c->pair_items.push_back(make_int2(ea, eb));
+                    if (++n_in_chunk == (size_t)kSchurChunk) {
+                        c->chunk_pair.push_back(p);
+                        c->chunk_start.push_back((int)c->pair_items.size());
+                        n_in_chunk = 0;
+                    }
+                }
+                if (n_in_chunk > 0) {
+                    c->chunk_pair.push_back(p);
+                    c->chunk_start.push_back((int)c->pair_items.size());
+                }
+                c->pair_fg.push_back(b.fo + f);
+                c->pair_fg.push_back(b.fo + g);
+                c->pair_chunk.push_back((int)c->chunk_pair.size());
+            }
+        const int64_t n6 = 6 * (F - 1);
+        BundleDesc bd{};
+        bd.fo = b.fo;
+        bd.F = F;
+        bd.co = c->n_cmap;
+        bd.po = c->n_po;
+        bd.so = c->n_so;
+        bd.ao = c->n_ao;
+        bd.lo = c->n_lo;
+        c->bdesc.push_back(bd);
+        c->n_so += n6 * n6;
+        c->n_ao += (n6 + 1) * n6;
+        c->n_lo += (n6 + kLdlBlock - 1) / kLdlBlock * kLinvStride;
+        c->n_po += (int)n6;
+        c->n_cmap += F + 1;
+        for (int f = 0; f < F; ++f) c->frame_bundle.push_back(bi);
+        c->F += F;
+        c->N += N;
+        c->T += b.T;
+        c->Fmax = std::max(c->Fmax, F);
+        c->n6max = std::max(c->n6max, (int)n6);
     }
-    c->tile_entry[c->T] = (int)c->entries.size();
+    c->tile_entry.push_back((int)c->entries.size());
+    c->Npad = c->T * kTile;
     c->E = (int)c->entries.size();
     c->V = pairs;
+    const int F = c->F;
     c->frame_entry.assign(F + 1, 0);
     for (const Entry& e : c->entries) c->frame_entry[e.f + 1]++;
     for (int f = 0; f < F; ++f) c->frame_entry[f + 1] += c->frame_entry[f];
@@ -385,42 +494,30 @@ void build_structure(pba_ctx* c)
     c->entry_slot.assign(c->E, 0);
     std::vector<int> fill(c->frame_entry.begin(), c->frame_entry.end() - 1);
     for (int e = 0; e < c->E; ++e) c->entry_slot[e] = fill[c->entries[e].f]++;
-    c->NC = (7 * (int)(c->pattern.size() / 2) + 3) / 4;
-    // frame pairs with the (entry, entry) items of the tiles that see both
-    // (tile order: the sparse Schur kernel's fixed summation order), cut into
-    // chunks of at most kSchurChunk items
-    c->pair_fg.clear();
-    c->pair_chunk.assign(1, 0);
-    c->chunk_pair.clear();
-    c->chunk_start.assign(1, 0);
-    c->pair_items.clear();
-    for (int f = 1; f < F; ++f)
-        for (int g = f; g < F; ++g) {
-            const int p = (int)c->pair_fg.size() / 2;
-            size_t n_in_chunk = 0;
-            for (int t = 0; t < c->T; ++t) {
-                const int a = c->ent_of[(size_t)t * F + f], b = c->ent_of[(size_t)t * F + g];
-                if (!(a >= 0 && b >= 0 && (c->entries[a].mask & c->entries[b].mask))) continue;
-                c->pair_items.push_back(make_int2(a, b));
-                if (++n_in_chunk == (size_t)kSchurChunk) {
-                    c->chunk_pair.push_back(p);
-                    c->chunk_start.push_back((int)c->pair_items.size());
-                    n_in_chunk = 0;
-                }
-            }
-            if (n_in_chunk > 0) {
-                c->chunk_pair.push_back(p);
-                c->chunk_start.push_back((int)c->pair_items.size());
-            }
-            c->pair_fg.push_back(f);
-            c->pair_fg.push_back(g);
-            c->pair_chunk.push_back((int)c->chunk_pair.size());
-        }
+    c->built = true;
 }
 
-pba_status upload_params(pba_ctx* ctx, const double* poses, const double* depth)
+// Builds the concatenated structure once every bundle has frames and points.
+pba_status ensure_structure(pba_ctx* ctx)
 {
-    const int F = ctx->F;
+    if (!all_set(ctx)) return fail(ctx, PBA_ERR_STATE, "frames and points of every bundle must be set first");
+    if (ctx->built) return PBA_OK;
+    int64_t frames = 0;
+    for (const BundleIn& b : ctx->bun) frames += b.F;
+    if ((double)frames * ctx->H * ctx->pitch >= 4294967296.0)
+        return fail(ctx, PBA_ERR_ARG, "image stack too large (frames * h * pitch over all bundles must stay below 2^32)");
+    build_structure(ctx);
+    if (ctx->V >= 2147483647LL)
+        return fail(ctx, PBA_ERR_ARG, "too many (point, frame) observations (limit 2^31 - 1)");
+    return PBA_OK;
+}
+
+// Uploads the parameters of bundle b (poses F_b*12, depths in the caller's
+// point order, nullable) with their FP32 pass constants.
+pba_status upload_params(pba_ctx* ctx, int bi, const double* poses, const double* depth)
+{
+    const BundleIn& b = ctx->bun[bi];
+    const int F = b.F, fo = b.fo;
     std::vector<float> fcs((size_t)F * kFrameConst, 0.0f), prev((size_t)F * 12, 0.0f);
     const int P = (int)ctx->pattern.size() / 2;
     for (int f = 0; f < F; ++f) {
@@ -428,32 +525,44 @@ pba_status upload_params(pba_ctx* ctx, const double* poses, const double* depth)
                      fcs.data() + (size_t)f * kFrameConst);
         for (int i = 0; i < 12; ++i) prev[12 * f + i] = (float)poses[12 * f + i];
     }
-    CK(h2d(ctx, ctx->d.poses64, poses, sizeof(double) * 12 * F));
-    CK(h2d(ctx, ctx->d.fc, fcs.data(), sizeof(float) * fcs.size()));
-    CK(h2d(ctx, ctx->d.fc_prev, prev.data(), sizeof(float) * prev.size()));
+    CK(h2d(ctx, ctx->d.poses64 + (size_t)12 * fo, poses, sizeof(double) * 12 * F));
+    CK(h2d(ctx, ctx->d.fc + (size_t)kFrameConst * fo, fcs.data(), sizeof(float) * fcs.size()));
+    CK(h2d(ctx, ctx->d.fc_prev + (size_t)12 * fo, prev.data(), sizeof(float) * prev.size()));
     if (depth) {
-        std::vector<double> ds(ctx->Npad, 1.0);
-        for (int i = 0; i < ctx->Npad; ++i)
-            if (ctx->perm[i] >= 0) ds[i] = depth[ctx->perm[i]];
-        CK(h2d(ctx, ctx->d.d64, ds.data(), sizeof(double) * ds.size()));
+        std::vector<double> ds(b.perm.size(), 1.0);
+        for (size_t i = 0; i < ds.size(); ++i)
+            if (b.perm[i] >= 0) ds[i] = depth[b.perm[i]];
+        CK(h2d(ctx, ctx->d.d64 + (size_t)kTile * b.to, ds.data(), sizeof(double) * ds.size()));
     }
     // all host staging above is pageable: the copies have consumed it on return
     CK(cudaStreamSynchronize(ctx->stream));
     return PBA_OK;
 }
 
+// Reads the device error words: the context's and, when it is set, every
+// bundle's (kept for pba_bundle_errors), then clears them.
 pba_status check_device_error(pba_ctx* ctx)
 {
     int herr = 0;
     CK(d2h(ctx, &herr, ctx->d.err, sizeof(int)));
     tcollect(ctx);
-    if (herr) {
-        CK(cudaMemsetAsync(ctx->d.err, 0, sizeof(int), ctx->stream));
-        if (herr & kErrNotPD)
-            return fail(ctx, PBA_ERR_NOT_PD, "reduced camera system is not positive definite");
-        return fail(ctx, PBA_ERR_NONFINITE, "non-finite update");
-    }
-    return PBA_OK;
+    ctx->bundle_err.assign(ctx->B, 0);
+    if (!herr) return PBA_OK;
+    CK(d2h(ctx, ctx->bundle_err.data(), ctx->d.err + 1, sizeof(int) * ctx->B));
+    CK(cudaMemsetAsync(ctx->d.err, 0, sizeof(int) * (1 + ctx->B), ctx->stream));
+    std::string which;
+    int nbad = 0;
+    for (int b = 0; b < ctx->B; ++b)
+        if (ctx->bundle_err[b]) {
+            if (nbad < 8) which += (nbad ? ", " : "") + std::to_string(b);
+            ++nbad;
+        }
+    if (nbad > 8) which += ", ...";
+    const std::string where = ctx->B > 1 ? " (bundle" + std::string(nbad > 1 ? "s " : " ") + which + ")" : "";
+    if (herr & kErrNotPD)
+        return fail(ctx, PBA_ERR_NOT_PD, "reduced camera system is not positive definite%s", where.c_str());
+    if (herr & kErrTimeout) return fail(ctx, PBA_ERR_TIMEOUT, "a tensor-core wait gave up");
+    return fail(ctx, PBA_ERR_NONFINITE, "non-finite update%s", where.c_str());
 }
 
 LaunchCtx make_launch(pba_ctx* c)
@@ -475,7 +584,7 @@ LaunchCtx make_launch(pba_ctx* c)
     pb.cx = (float)c->K[2];
     pb.cy = (float)c->K[3];
     pb.huber_k = (float)c->cfg.huber_k;
-    pb.img = c->mem == PBA_MEM_HOST ? c->d.img : c->images;
+    pb.img = own_images(c) ? c->d.img : c->bun[0].images;
     pb.gx = c->d.gx;
     pb.gy = c->d.gy;
     pb.pat = c->d.pat;
@@ -483,7 +592,9 @@ LaunchCtx make_launch(pba_ctx* c)
     pb.tile_entry = c->d.tile_entry;
     pb.frame_entry = c->d.frame_entry;
     pb.entry_slot = c->d.entry_slot;
-    pb.ent_of = c->d.ent_of;
+    pb.frame_bundle = c->d.frame_bundle;
+    pb.bund = c->d.bund;
+    pb.tile_f0 = c->d.tile_f0;
     pb.uvs = c->d.uvs;
     pb.xn = c->d.xn;
     pb.I0p = c->d.I0p;
@@ -500,6 +611,7 @@ LaunchCtx make_launch(pba_ctx* c)
     L.stats = c->d.stats;
     L.poses0 = c->d.poses0_64;
     L.stream = c->stream;
+    L.res_warps = c->res_warps;
     return L;
 }
 
@@ -513,7 +625,11 @@ SolveArgs make_solve(pba_ctx* c)
 {
     SolveArgs a{};
     a.F = c->F;
-    a.n6 = 6 * (c->F - 1);
+    a.n6 = c->n6max;
+    a.B = c->B;
+    a.Fmax = c->Fmax;
+    a.bund = c->d.bund;
+    a.frame_bundle = c->d.frame_bundle;
     a.pat = c->d.pat;
     a.P = (int)c->pattern.size() / 2;
     a.fx = c->K[0];
@@ -529,6 +645,15 @@ SolveArgs make_solve(pba_ctx* c)
     a.dthsq = c->d.dthsq;
     a.err = c->d.err;
     return a;
+}
+
+BundleSet bundle_set(pba_ctx* c)
+{
+    BundleSet bs{};
+    bs.B = c->B;
+    bs.bund = c->d.bund;
+    bs.n6max = c->n6max;
+    return bs;
 }
 
 pba_status copy_stats(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
@@ -621,27 +746,28 @@ __global__ void gradient_images_kernel(DevProblem pb, float* gx, float* gy)
 
 // Template intensities and gradients (central differences of the reference
 // image, read from the gradient images) at every pattern pixel, laid out
-// [tile][j][lane].
-__global__ void template_gather_kernel(DevProblem pb, float* I0p, float2* G0p)
+// [tile][j][lane]; tile t's reference image is frame tile_f0[t].
+__global__ void template_gather_kernel(DevProblem pb, const int* tile_f0, float* I0p, float2* G0p)
 {
     const int total = pb.T * pb.P * kTile;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const int lane = i % kTile, j = (i / kTile) % pb.P, t = i / (kTile * pb.P);
         const int n = t * kTile + lane;
+        const size_t row0 = (size_t)tile_f0[t] * pb.H;
         const int px = pb.uvs[2 * n] + pb.pat[2 * j], py = pb.uvs[2 * n + 1] + pb.pat[2 * j + 1];
-        I0p[i] = load_px(pb.img, pb.dtype, (size_t)py * pb.pitch + px);
-        const size_t g = (size_t)py * pb.W + px;
+        I0p[i] = load_px(pb.img, pb.dtype, (row0 + py) * pb.pitch + px);
+        const size_t g = (row0 + py) * pb.W + px;
         G0p[i] = make_float2(pb.gx[g], pb.gy[g]);
     }
 }
 
-cudaError_t launch_setup(const DevProblem& pb, float* gx, float* gy, float* I0p, float2* G0p,
-                         cudaStream_t st)
+cudaError_t launch_setup(const DevProblem& pb, const int* tile_f0, float* gx, float* gy, float* I0p,
+                         float2* G0p, cudaStream_t st)
 {
     gradient_images_kernel<<<1024, 256, 0, st>>>(pb, gx, gy);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    template_gather_kernel<<<256, 256, 0, st>>>(pb, I0p, G0p);
+    template_gather_kernel<<<256, 256, 0, st>>>(pb, tile_f0, I0p, G0p);
     return cudaGetLastError();
 }
 
@@ -657,7 +783,8 @@ pba_status pba_create(const pba_config* cfg, pba_ctx** out)
     if (!out) return PBA_ERR_ARG;
     *out = nullptr;
     if (!cfg || !(cfg->huber_k > 0.0) || cfg->pattern_size < 1 ||
-        cfg->pattern_size > PBA_MAX_PATTERN || !cfg->pattern || cfg->n_bundles > 1 ||
+        cfg->pattern_size > PBA_MAX_PATTERN || !cfg->pattern || cfg->n_bundles < 0 ||
+        cfg->n_bundles > PBA_MAX_BUNDLES ||
         cfg->gauge_anchor_w < 0.0 || cfg->max_stats_iters < 0)
         return PBA_ERR_ARG;
     for (int j = 0; j < 2 * cfg->pattern_size; ++j)
@@ -672,6 +799,9 @@ pba_status pba_create(const pba_config* cfg, pba_ctx** out)
     if (c->cfg.max_stats_iters == 0) c->cfg.max_stats_iters = 256;
     c->stream = (cudaStream_t)cfg->cuda_stream;
     c->stats_slots = c->cfg.max_stats_iters + 1;
+    c->B = std::max(1, cfg->n_bundles);
+    c->cfg.n_bundles = c->B;
+    c->bun.resize(c->B);
     *out = c;
     return PBA_OK;
 }
@@ -693,15 +823,16 @@ pba_status pba_set_frames(pba_ctx* ctx, int bundle, int n_frames, int w, int h, 
                           const double* poses, const double* intrinsics)
 {
     if (!ctx) return PBA_ERR_ARG;
-    if (bundle != 0) return fail(ctx, PBA_ERR_ARG, "bundle %d out of range (one bundle per context)", bundle);
+    if (bundle < 0 || bundle >= ctx->B)
+        return fail(ctx, PBA_ERR_ARG, "bundle %d out of range (%d bundles)", bundle, ctx->B);
     if (n_frames < 2 || w < 4 || h < 4 || pitch_elems < w || !images || !poses || !intrinsics)
         return fail(ctx, PBA_ERR_ARG, "invalid frame arguments");
     if (dtype != PBA_F32 && dtype != PBA_F16 && dtype != PBA_BF16)
         return fail(ctx, PBA_ERR_ARG, "invalid dtype");
     if (mem != PBA_MEM_DEVICE && mem != PBA_MEM_HOST) return fail(ctx, PBA_ERR_ARG, "invalid memory kind");
-    if (n_frames > 1024) return fail(ctx, PBA_ERR_ARG, "at most 1024 frames");
-    if ((double)n_frames * h * pitch_elems >= 2147483648.0)
-        return fail(ctx, PBA_ERR_ARG, "image stack too large (F * h * pitch must stay below 2^31)");
+    if (n_frames > 1024) return fail(ctx, PBA_ERR_ARG, "at most 1024 frames per bundle");
+    if ((double)n_frames * h * pitch_elems >= 4294967296.0)
+        return fail(ctx, PBA_ERR_ARG, "image stack too large (F * h * pitch must stay below 2^32)");
     if (mem == PBA_MEM_DEVICE && ((uintptr_t)images % elem_size(dtype)))
         return fail(ctx, PBA_ERR_ARG, "misaligned image pointer");
     for (int i = 0; i < 4; ++i)
@@ -712,18 +843,30 @@ pba_status pba_set_frames(pba_ctx* ctx, int bundle, int n_frames, int w, int h, 
     static const double I12[12] = {1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0};
     for (int i = 0; i < 12; ++i)
         if (std::fabs(poses[i] - I12[i]) > 1e-9) return fail(ctx, PBA_ERR_ARG, "frame 0 pose must be the identity");
-    ctx->F = n_frames;
+    // the bundles of a context share one camera
+    for (int o = 0; o < ctx->B; ++o) {
+        if (o == bundle || !ctx->bun[o].have_frames) continue;
+        if (w != ctx->W || h != ctx->H || pitch_elems != ctx->pitch || dtype != ctx->dtype || mem != ctx->mem ||
+            std::memcmp(intrinsics, ctx->K, sizeof ctx->K) != 0)
+            return fail(ctx, PBA_ERR_ARG,
+                        "bundle %d: the bundles of a context share image size, pitch, type, memory kind "
+                        "and intrinsics", bundle);
+    }
+    BundleIn& b = ctx->bun[bundle];
+    if (b.have_points && (w != ctx->W || h != ctx->H)) b.have_points = false;  // revalidate the points
+    b.F = n_frames;
+    b.images = images;
+    b.poses_init.assign(poses, poses + 12 * n_frames);
+    b.have_frames = true;
+    if (b.have_points && b.vis.size() != (size_t)b.N * n_frames) b.have_points = false;
     ctx->W = w;
     ctx->H = h;
     ctx->pitch = pitch_elems;
     ctx->dtype = dtype;
     ctx->mem = mem;
-    ctx->images = images;
-    ctx->poses_init.assign(poses, poses + 12 * n_frames);
     std::memcpy(ctx->K, intrinsics, sizeof ctx->K);
-    ctx->have_frames = true;
+    ctx->built = false;
     ctx->ws_ready = ctx->ic_ready = false;
-    if (ctx->have_points && ctx->vis.size() != (size_t)ctx->N * n_frames) ctx->have_points = false;
     return PBA_OK;
 }
 
@@ -731,8 +874,10 @@ pba_status pba_set_points(pba_ctx* ctx, int bundle, int n_points, const int32_t*
                           const double* inv_depth, const uint8_t* vis)
 {
     if (!ctx) return PBA_ERR_ARG;
-    if (bundle != 0) return fail(ctx, PBA_ERR_ARG, "bundle %d out of range (one bundle per context)", bundle);
-    if (!ctx->have_frames) return fail(ctx, PBA_ERR_STATE, "pba_set_frames must come first");
+    if (bundle < 0 || bundle >= ctx->B)
+        return fail(ctx, PBA_ERR_ARG, "bundle %d out of range (%d bundles)", bundle, ctx->B);
+    BundleIn& b = ctx->bun[bundle];
+    if (!b.have_frames) return fail(ctx, PBA_ERR_STATE, "pba_set_frames must come first");
     if (n_points < 1 || !uv || !inv_depth) return fail(ctx, PBA_ERR_ARG, "invalid point arguments");
     int rad = 0;
     for (int32_t o : ctx->pattern) rad = std::max(rad, std::abs(o));
@@ -744,25 +889,25 @@ pba_status pba_set_points(pba_ctx* ctx, int bundle, int n_points, const int32_t*
         if (!(inv_depth[n] > 0.0) || !std::isfinite(inv_depth[n]))
             return fail(ctx, PBA_ERR_ARG, "point %d: inverse depth must be positive", n);
     }
-    ctx->N = n_points;
-    ctx->uv.assign(uv, uv + 2 * n_points);
-    ctx->d_init.assign(inv_depth, inv_depth + n_points);
+    b.N = n_points;
+    b.uv.assign(uv, uv + 2 * n_points);
+    b.d_init.assign(inv_depth, inv_depth + n_points);
     if (vis)
-        ctx->vis.assign(vis, vis + (size_t)n_points * ctx->F);
+        b.vis.assign(vis, vis + (size_t)n_points * b.F);
     else
-        ctx->vis.assign((size_t)n_points * ctx->F, 1);
-    for (int n = 0; n < n_points; ++n) ctx->vis[(size_t)n * ctx->F] = 0;
-    ctx->have_points = true;
+        b.vis.assign((size_t)n_points * b.F, 1);
+    for (int n = 0; n < n_points; ++n) b.vis[(size_t)n * b.F] = 0;
+    b.have_points = true;
+    ctx->built = false;
     ctx->ws_ready = ctx->ic_ready = false;
-    build_structure(ctx);
     return PBA_OK;
 }
 
 pba_status pba_workspace_size(pba_ctx* ctx, size_t* bytes)
 {
     if (!ctx || !bytes) return PBA_ERR_ARG;
-    if (!ctx->have_frames || !ctx->have_points)
-        return fail(ctx, PBA_ERR_STATE, "frames and points must be set first");
+    pba_status s = ensure_structure(ctx);
+    if (s != PBA_OK) return s;
     *bytes = layout(ctx, nullptr);
     return PBA_OK;
 }
@@ -770,8 +915,8 @@ pba_status pba_workspace_size(pba_ctx* ctx, size_t* bytes)
 pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
 {
     if (!ctx) return PBA_ERR_ARG;
-    if (!ctx->have_frames || !ctx->have_points)
-        return fail(ctx, PBA_ERR_STATE, "frames and points must be set first");
+    pba_status st = ensure_structure(ctx);
+    if (st != PBA_OK) return st;
     const size_t need = layout(ctx, nullptr);
     if (!dev_ptr || bytes < need)
         return fail(ctx, PBA_ERR_NOMEM, "workspace of %zu bytes needed, %zu given", need, bytes);
@@ -782,22 +927,32 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     layout(ctx, ctx->ws);
     ctx->ic_ready = false;
     CK(cudaMemsetAsync(ctx->ws, 0, need, ctx->stream));
-    if (ctx->mem == PBA_MEM_HOST)
-        CK(h2d(ctx, ctx->d.img, ctx->images,
-               (size_t)ctx->F * ctx->H * ctx->pitch * elem_size(ctx->dtype)));
-    const int Np = ctx->Npad, P = (int)ctx->pattern.size() / 2;
+    if (own_images(ctx)) {
+        const size_t fbytes = (size_t)ctx->H * ctx->pitch * elem_size(ctx->dtype);
+        for (const BundleIn& b : ctx->bun) {
+            char* dst = static_cast<char*>(ctx->d.img) + fbytes * b.fo;
+            if (ctx->mem == PBA_MEM_HOST) CK(h2d(ctx, dst, b.images, fbytes * b.F));
+            else CK(cudaMemcpyAsync(dst, b.images, fbytes * b.F, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+    }
+    const int Np = ctx->Npad;
     std::vector<int> uvs(2 * Np);
     std::vector<float2> xn(Np);
     std::vector<unsigned char> valid(Np, 0);
-    int last = ctx->perm[0];
-    for (int i = 0; i < Np; ++i) {
-        const int n = ctx->perm[i] >= 0 ? ctx->perm[i] : last;
-        if (ctx->perm[i] >= 0) last = ctx->perm[i];
-        uvs[2 * i] = ctx->uv[2 * n];
-        uvs[2 * i + 1] = ctx->uv[2 * n + 1];
-        xn[i] = make_float2((float)((uvs[2 * i] - ctx->K[2]) / ctx->K[0]),
-                            (float)((uvs[2 * i + 1] - ctx->K[3]) / ctx->K[1]));
-        valid[i] = ctx->perm[i] >= 0;
+    std::vector<int> slot_caller(Np, -1);
+    for (const BundleIn& b : ctx->bun) {
+        int last = b.perm[0];
+        for (size_t k = 0; k < b.perm.size(); ++k) {
+            const size_t i = (size_t)kTile * b.to + k;
+            const int n = b.perm[k] >= 0 ? b.perm[k] : last;
+            if (b.perm[k] >= 0) last = b.perm[k];
+            uvs[2 * i] = b.uv[2 * n];
+            uvs[2 * i + 1] = b.uv[2 * n + 1];
+            xn[i] = make_float2((float)((uvs[2 * i] - ctx->K[2]) / ctx->K[0]),
+                                (float)((uvs[2 * i + 1] - ctx->K[3]) / ctx->K[1]));
+            valid[i] = b.perm[k] >= 0;
+            slot_caller[i] = b.perm[k];
+        }
     }
     std::vector<int> pat(ctx->pattern.begin(), ctx->pattern.end());
     CK(h2d(ctx, ctx->d.pat, pat.data(), sizeof(int) * pat.size()));
@@ -805,24 +960,120 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     CK(h2d(ctx, ctx->d.tile_entry, ctx->tile_entry.data(), sizeof(int) * ctx->tile_entry.size()));
     CK(h2d(ctx, ctx->d.frame_entry, ctx->frame_entry.data(), sizeof(int) * ctx->frame_entry.size()));
     CK(h2d(ctx, ctx->d.entry_slot, ctx->entry_slot.data(), sizeof(int) * ctx->entry_slot.size()));
-    CK(h2d(ctx, ctx->d.ent_of, ctx->ent_of.data(), sizeof(int) * ctx->ent_of.size()));
+    CK(h2d(ctx, ctx->d.frame_bundle, ctx->frame_bundle.data(), sizeof(int) * ctx->frame_bundle.size()));
+    CK(h2d(ctx, ctx->d.tile_f0, ctx->tile_f0.data(), sizeof(int) * ctx->tile_f0.size()));
+    CK(h2d(ctx, ctx->d.bund, ctx->bdesc.data(), sizeof(BundleDesc) * ctx->bdesc.size()));
     CK(h2d(ctx, ctx->d.uvs, uvs.data(), sizeof(int) * uvs.size()));
     CK(h2d(ctx, ctx->d.xn, xn.data(), sizeof(float2) * xn.size()));
     CK(h2d(ctx, ctx->d.valid_pt, valid.data(), valid.size()));
+    CK(h2d(ctx, ctx->d.slot_caller, slot_caller.data(), sizeof(int) * slot_caller.size()));
     CK(h2d(ctx, ctx->d.pair_fg, ctx->pair_fg.data(), sizeof(int) * ctx->pair_fg.size()));
     CK(h2d(ctx, ctx->d.pair_chunk, ctx->pair_chunk.data(), sizeof(int) * ctx->pair_chunk.size()));
     CK(h2d(ctx, ctx->d.chunk_pair, ctx->chunk_pair.data(), sizeof(int) * ctx->chunk_pair.size()));
     CK(h2d(ctx, ctx->d.chunk_start, ctx->chunk_start.data(), sizeof(int) * ctx->chunk_start.size()));
     CK(h2d(ctx, ctx->d.pair_items, ctx->pair_items.data(), sizeof(int2) * ctx->pair_items.size()));
-    pba_status s = upload_params(ctx, ctx->poses_init.data(), ctx->d_init.data());
-    if (s != PBA_OK) return s;
-    CK(h2d(ctx, ctx->d.poses0_64, ctx->poses_init.data(), sizeof(double) * 12 * ctx->F));
+    for (int bi = 0; bi < ctx->B; ++bi) {
+        const BundleIn& b = ctx->bun[bi];
+        pba_status s = upload_params(ctx, bi, b.poses_init.data(), b.d_init.data());
+        if (s != PBA_OK) return s;
+        CK(h2d(ctx, ctx->d.poses0_64 + (size_t)12 * b.fo, b.poses_init.data(), sizeof(double) * 12 * b.F));
+    }
     LaunchCtx L = make_launch(ctx);
     CK(ldl_setup());
-    LAUNCH(TS_PRE, launch_setup(L.pb, ctx->d.gx, ctx->d.gy, ctx->d.I0p, ctx->d.G0p, ctx->stream));
-    (void)P;
+    CK(iter_setup());
+    CK(linalg_setup());
+    LAUNCH(TS_PRE, launch_setup(L.pb, ctx->d.tile_f0, ctx->d.gx, ctx->d.gy, ctx->d.I0p, ctx->d.G0p, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->ws_ready = true;
+    return PBA_OK;
+}
+
+// The IC precompute's launches (Sec. 3.5): p_0 from the current parameters,
+// J, W_0 and the H blocks per entry, the frame sums, the Schur complement, S
+// with the gauge prior, its LDL^T factor and S^-1.
+pba_status precompute_body(pba_ctx* ctx)
+{
+    const int F = ctx->F;
+    LaunchCtx L = make_launch(ctx);
+    const BundleSet bs = bundle_set(ctx);
+    // the current parameters become p_0
+    CK(cudaMemcpyAsync(ctx->d.poses0_64, ctx->d.poses64, sizeof(double) * 12 * F, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.d0_64, ctx->d.d64, sizeof(double) * ctx->Npad, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    LAUNCH(TS_PRE, launch_depth_update(L, make_solve(ctx), true, 0));  // FP32 depths of p_0
+    LAUNCH(TS_PRE, launch_ic_precompute(L));
+    LAUNCH(TS_PRE, launch_frame_reduce(L, 0, 21, ctx->d.red_ic, -1, -1, true));
+    LAUNCHN(TS_PRE, launch_schur_sparse(L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, schur_lists(ctx), ctx->d.schur_part,
+                                        ctx->d.Soff, ctx->stream, &nl));
+    LAUNCH(TS_PRE, launch_assemble_S(bs, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64, ctx->cfg.gauge_anchor_w,
+                                     ctx->d.S_ic, ctx->d.active_ic, ctx->stream, ctx->d.A2, ctx->d.cmap_ic));
+    LAUNCH(TS_PRE, launch_ldl(bs, ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv, ctx->d.cmap_ic, 0,
+                              ctx->d.err, ctx->stream, ctx->ldl_cluster));
+    LAUNCH(TS_PRE, launch_ldl_inverse(bs, ctx->d.L2, ctx->d.Linv, ctx->d.rpiv, ctx->d.cmap_ic, ctx->d.Sinv2,
+                                      ctx->stream));
+    return PBA_OK;
+}
+
+// Autotuner: with the precompute's state in place, times each candidate
+// launch shape on this problem (events on the context's stream, after one
+// warm-up launch) and keeps the fastest. The candidates compute identical
+// results, so the choice only moves time. Leaves the IC system as the
+// precompute left it.
+pba_status autotune(pba_ctx* ctx)
+{
+    cudaEvent_t a = take_event(ctx), b = take_event(ctx);
+    auto elapsed = [&](auto&& launch, int reps, float* ms) -> pba_status {
+        CK(launch());
+        CK(cudaEventRecord(a, ctx->stream));
+        for (int r = 0; r < reps; ++r) CK(launch());
+        CK(cudaEventRecord(b, ctx->stream));
+        CK(cudaEventSynchronize(b));
+        CK(cudaEventElapsedTime(ms, a, b));
+        return PBA_OK;
+    };
+    pba_status s = PBA_OK;
+    // warps per CTA of the accumulating IC residual pass
+    float best = 0.0f;
+    int best_w = ctx->res_warps;
+    for (int w : {4, 8, 16}) {
+        LaunchCtx L = make_launch(ctx);
+        L.res_warps = w;
+        float ms = 0.0f;
+        s = elapsed([&]() { return launch_ic_residual(L, true, 0); }, 5, &ms);
+        if (s != PBA_OK) break;
+        if (w == 4 || ms < best) {
+            best = ms;
+            best_w = w;
+        }
+    }
+    // CTAs per bundle of the factorisation (each trial re-forms A from S)
+    const BundleSet bs = bundle_set(ctx);
+    int best_c = ctx->ldl_cluster;
+    best = 0.0f;
+    for (int C = 4; s == PBA_OK && C <= ldl_max_cluster(); C *= 2) {
+        float ms = 0.0f;
+        auto once = [&]() -> cudaError_t {
+            cudaError_t e = launch_assemble_S(bs, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64,
+                                              ctx->cfg.gauge_anchor_w, ctx->d.S_ic, ctx->d.active_ic, ctx->stream,
+                                              ctx->d.A2, ctx->d.cmap_ic);
+            if (e != cudaSuccess) return e;
+            return launch_ldl(bs, ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv, ctx->d.cmap_ic, 0,
+                              ctx->d.err, ctx->stream, C);
+        };
+        s = elapsed(once, 3, &ms);
+        if (s == PBA_OK && (C == 4 || ms < best)) {
+            best = ms;
+            best_c = C;
+        }
+    }
+    ctx->evpool.push_back(a);
+    ctx->evpool.push_back(b);
+    if (s != PBA_OK) return s;
+    ctx->res_warps = best_w;
+    ctx->ldl_cluster = best_c;
+    ctx->tuned = true;
+    destroy_graphs(ctx);  // captured with the previous shapes
     return PBA_OK;
 }
 
@@ -830,28 +1081,16 @@ pba_status pba_precompute_ic(pba_ctx* ctx)
 {
     if (!ctx) return PBA_ERR_ARG;
     if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
-    const int F = ctx->F;
-    LaunchCtx L = make_launch(ctx);
-    pba_status s = run_enqueued(ctx, GraphKey{G_PRECOMPUTE, 0, ctx->timing}, [&]() -> pba_status {
-        // the current parameters become p_0
-        CK(cudaMemcpyAsync(ctx->d.poses0_64, ctx->d.poses64, sizeof(double) * 12 * F,
-                           cudaMemcpyDeviceToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(ctx->d.d0_64, ctx->d.d64, sizeof(double) * ctx->Npad,
-                           cudaMemcpyDeviceToDevice, ctx->stream));
-        LAUNCH(TS_PRE, launch_depth_update(L, make_solve(ctx), true, 0));  // FP32 depths of p_0
-        LAUNCH(TS_PRE, launch_ic_precompute(L));
-        LAUNCH(TS_PRE, launch_frame_reduce(L, 0, 21, ctx->d.red_ic, -1, -1, true));
-        LAUNCHN(TS_PRE, launch_schur_sparse(L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, schur_lists(ctx),
-                                            ctx->d.schur_part, ctx->d.Soff, ctx->stream, &nl));
-        LAUNCH(TS_PRE, launch_assemble_S(F, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64,
-                                         ctx->cfg.gauge_anchor_w, ctx->d.S_ic, ctx->d.active_ic,
-                                         ctx->stream, ctx->d.A2, ctx->d.cmap_ic));
-        LAUNCH(TS_PRE, launch_ldl(ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv, ctx->d.cmap_ic,
-                                  F, 0, ctx->d.err, ctx->stream));
-        LAUNCH(TS_PRE, launch_ldl_inverse(ctx->d.L2, ctx->d.Linv, ctx->d.rpiv, ctx->d.cmap_ic, F, ctx->d.Sinv2,
-                                          ctx->stream));
-        return PBA_OK;
-    });
+    if (ctx->cfg.autotune && !ctx->tuned) {
+        const int timing = ctx->timing;
+        ctx->timing = 0;
+        pba_status s = precompute_body(ctx);
+        if (s == PBA_OK) s = autotune(ctx);
+        ctx->timing = timing;
+        if (s != PBA_OK) return s;
+    }
+    pba_status s = run_enqueued(ctx, GraphKey{G_PRECOMPUTE, 0, ctx->timing},
+                                [&]() -> pba_status { return precompute_body(ctx); });
     if (s != PBA_OK) return s;
     s = check_device_error(ctx);
     if (s != PBA_OK) return s;
@@ -895,8 +1134,8 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
     if (n_iters < 0 || n_iters > ctx->cfg.max_stats_iters)
         return fail(ctx, PBA_ERR_ARG, "n_iters must be in [0, %d]", ctx->cfg.max_stats_iters);
-    const int F = ctx->F;
     LaunchCtx L = make_launch(ctx);
+    const BundleSet bs = bundle_set(ctx);
     SolveArgs sa = make_solve(ctx);
     sa.active = ctx->d.active_fc;
     sa.tanchor = ctx->d.poses64;
@@ -909,11 +1148,11 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
             LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 27, ctx->d.red_y, k, k - 1, true, 27, 21));
             LAUNCHN(TS_SCHUR, launch_schur_sparse(L.pb, ctx->d.Hfd_fc, ctx->d.Hnn_fc, schur_lists(ctx),
                                                   ctx->d.schur_part, ctx->d.Soff, ctx->stream, &nl));
-            LAUNCH(TS_SCHUR, launch_assemble_S(F, ctx->d.red_y, 27, ctx->d.Soff, ctx->d.poses64,
+            LAUNCH(TS_SCHUR, launch_assemble_S(bs, ctx->d.red_y, 27, ctx->d.Soff, ctx->d.poses64,
                                                ctx->cfg.gauge_anchor_w, ctx->d.S_fc, ctx->d.active_fc,
                                                ctx->stream, ctx->d.A2, ctx->d.cmap_fc, ctx->d.red_y, 27, 21));
-            LAUNCH(TS_SOLVE, launch_ldl(ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv,
-                                        ctx->d.cmap_fc, F, 1, ctx->d.err, ctx->stream));
+            LAUNCH(TS_SOLVE, launch_ldl(bs, ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv,
+                                        ctx->d.cmap_fc, 1, ctx->d.err, ctx->stream, ctx->ldl_cluster));
             LAUNCH(TS_SOLVE, launch_fc_solve_update(sa, ctx->d.L2, ctx->d.Linv, ctx->stream));
         }
         LAUNCH(TS_EVAL, launch_depth_update(L, sa, false, n_iters > 0));
@@ -927,98 +1166,123 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     return copy_stats(ctx, n_iters, stats);
 }
 
+// Device values of bundle b's point slots mapped back to the caller's point order.
+static pba_status gather_points(pba_ctx* ctx, const BundleIn& b, const void* dev, bool fp32, double* out)
+{
+    const size_t n = b.perm.size(), off = (size_t)kTile * b.to;
+    if (fp32) {
+        std::vector<float> h(n);
+        CK(d2h(ctx, h.data(), static_cast<const float*>(dev) + off, sizeof(float) * n));
+        for (size_t i = 0; i < n; ++i)
+            if (b.perm[i] >= 0) out[b.perm[i]] = h[i];
+    } else {
+        std::vector<double> h(n);
+        CK(d2h(ctx, h.data(), static_cast<const double*>(dev) + off, sizeof(double) * n));
+        for (size_t i = 0; i < n; ++i)
+            if (b.perm[i] >= 0) out[b.perm[i]] = h[i];
+    }
+    return PBA_OK;
+}
+
+#define CHECK_BUNDLE()                                                                         \
+    do {                                                                                       \
+        if (!ctx) return PBA_ERR_ARG;                                                          \
+        if (bundle < 0 || bundle >= ctx->B)                                                    \
+            return fail(ctx, PBA_ERR_ARG, "bundle %d out of range (%d bundles)", bundle, ctx->B); \
+    } while (0)
+
 pba_status pba_get_params(pba_ctx* ctx, int bundle, double* poses, double* inv_depth)
 {
-    if (!ctx || bundle != 0) return PBA_ERR_ARG;
+    CHECK_BUNDLE();
     if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    const BundleIn& b = ctx->bun[bundle];
     CK(cudaStreamSynchronize(ctx->stream));
-    if (poses) CK(d2h(ctx, poses, ctx->d.poses64, sizeof(double) * 12 * ctx->F));
-    if (inv_depth) {
-        std::vector<double> ds(ctx->Npad);
-        CK(d2h(ctx, ds.data(), ctx->d.d64, sizeof(double) * ds.size()));
-        for (int i = 0; i < ctx->Npad; ++i)
-            if (ctx->perm[i] >= 0) inv_depth[ctx->perm[i]] = ds[i];
-    }
+    if (poses) CK(d2h(ctx, poses, ctx->d.poses64 + (size_t)12 * b.fo, sizeof(double) * 12 * b.F));
+    if (inv_depth) return gather_points(ctx, b, ctx->d.d64, false, inv_depth);
     return PBA_OK;
 }
 
 pba_status pba_set_params(pba_ctx* ctx, int bundle, const double* poses, const double* inv_depth)
 {
-    if (!ctx || bundle != 0 || !poses || !inv_depth) return PBA_ERR_ARG;
+    CHECK_BUNDLE();
+    if (!poses || !inv_depth) return fail(ctx, PBA_ERR_ARG, "null parameters");
     if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
-    for (int i = 0; i < 12 * ctx->F; ++i)
+    const BundleIn& b = ctx->bun[bundle];
+    for (int i = 0; i < 12 * b.F; ++i)
         if (!std::isfinite(poses[i])) return fail(ctx, PBA_ERR_ARG, "non-finite pose");
-    for (int n = 0; n < ctx->N; ++n)
+    for (int n = 0; n < b.N; ++n)
         if (!(inv_depth[n] > 0.0) || !std::isfinite(inv_depth[n]))
             return fail(ctx, PBA_ERR_ARG, "point %d: inverse depth must be positive", n);
-    return upload_params(ctx, poses, inv_depth);
+    return upload_params(ctx, bundle, poses, inv_depth);
 }
 
 pba_status pba_get_last_update(pba_ctx* ctx, int bundle, double* dtheta, double* dd)
 {
-    if (!ctx || bundle != 0) return PBA_ERR_ARG;
+    CHECK_BUNDLE();
     if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    const BundleIn& b = ctx->bun[bundle];
     CK(cudaStreamSynchronize(ctx->stream));
-    if (dtheta) CK(d2h(ctx, dtheta, ctx->d.dtheta64, sizeof(double) * 6 * ctx->F));
-    if (dd) {
-        std::vector<double> h(ctx->Npad);
-        CK(d2h(ctx, h.data(), ctx->d.dd_last, sizeof(double) * h.size()));
-        for (int i = 0; i < ctx->Npad; ++i)
-            if (ctx->perm[i] >= 0) dd[ctx->perm[i]] = h[i];
-    }
+    if (dtheta) CK(d2h(ctx, dtheta, ctx->d.dtheta64 + (size_t)6 * b.fo, sizeof(double) * 6 * b.F));
+    if (dd) return gather_points(ctx, b, ctx->d.dd_last, false, dd);
     return PBA_OK;
 }
 
 pba_status pba_get_system(pba_ctx* ctx, int bundle, int fc, double* Hff, double* Hfd, double* Hdd,
                           double* S)
 {
-    if (!ctx || bundle != 0) return PBA_ERR_ARG;
+    CHECK_BUNDLE();
     if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
     if (!fc && !ctx->ic_ready) return fail(ctx, PBA_ERR_STATE, "no IC system yet");
     CK(cudaStreamSynchronize(ctx->stream));
-    const int F = ctx->F, n6 = 6 * (F - 1);
+    const BundleIn& b = ctx->bun[bundle];
+    const int F = b.F, n6 = 6 * (F - 1);
     if (Hff) {
         const int stride = fc ? 27 : 21;
         std::vector<double> r((size_t)F * stride);
-        CK(d2h(ctx, r.data(), fc ? ctx->d.red_y : ctx->d.red_ic, sizeof(double) * r.size()));
+        CK(d2h(ctx, r.data(), (fc ? ctx->d.red_y : ctx->d.red_ic) + (size_t)b.fo * stride,
+               sizeof(double) * r.size()));
         std::memset(Hff, 0, sizeof(double) * 36 * F);
         for (int f = 1; f < F; ++f) {
             int q = 0;
             for (int a = 0; a < 6; ++a)
-                for (int b = a; b < 6; ++b, ++q)
-                    Hff[36 * f + 6 * a + b] = Hff[36 * f + 6 * b + a] = r[(size_t)f * stride + q];
+                for (int c = a; c < 6; ++c, ++q)
+                    Hff[36 * f + 6 * a + c] = Hff[36 * f + 6 * c + a] = r[(size_t)f * stride + q];
         }
     }
     if (Hfd) {
-        std::vector<float> h((size_t)ctx->V * 6);
-        CK(d2h(ctx, h.data(), fc ? ctx->d.Hfd_fc : ctx->d.Hfd_ic, sizeof(float) * h.size()));
-        std::memset(Hfd, 0, sizeof(double) * 6 * (size_t)ctx->N * F);
-        for (const Entry& e : ctx->entries) {
+        const int64_t p0 = b.e1 > b.e0 ? ctx->entries[b.e0].pair_off : 0;
+        std::vector<float> h((size_t)b.V * 6);
+        CK(d2h(ctx, h.data(), (fc ? ctx->d.Hfd_fc : ctx->d.Hfd_ic) + (size_t)p0 * 6, sizeof(float) * h.size()));
+        std::memset(Hfd, 0, sizeof(double) * 6 * (size_t)b.N * F);
+        for (int ei = b.e0; ei < b.e1; ++ei) {
+            const Entry& e = ctx->entries[ei];
             const int nvis = __builtin_popcount(e.mask);
             for (int l = 0; l < kTile; ++l) {
                 if (!((e.mask >> l) & 1u)) continue;
                 const int rank = __builtin_popcount(e.mask & ((1u << l) - 1u));
-                const int n = ctx->perm[e.tile * kTile + l];
+                const int n = b.perm[(e.tile - b.to) * kTile + l];
                 for (int k = 0; k < 6; ++k)
-                    Hfd[((size_t)n * F + e.f) * 6 + k] = h[(size_t)e.pair_off * 6 + (size_t)k * nvis + rank];
+                    Hfd[((size_t)n * F + (e.f - b.fo)) * 6 + k] =
+                        h[(size_t)(e.pair_off - p0) * 6 + (size_t)k * nvis + rank];
             }
         }
     }
     if (Hdd) {
-        std::vector<float> h(ctx->Npad);
-        CK(d2h(ctx, h.data(), fc ? ctx->d.Hnn_fc : ctx->d.Hnn_ic, sizeof(float) * h.size()));
-        for (int i = 0; i < ctx->Npad; ++i)
-            if (ctx->perm[i] >= 0) Hdd[ctx->perm[i]] = h[i];
+        pba_status s = gather_points(ctx, b, fc ? ctx->d.Hnn_fc : ctx->d.Hnn_ic, true, Hdd);
+        if (s != PBA_OK) return s;
     }
-    if (S) CK(d2h(ctx, S, fc ? ctx->d.S_fc : ctx->d.S_ic, sizeof(double) * n6 * n6));
+    if (S)
+        CK(d2h(ctx, S, (fc ? ctx->d.S_fc : ctx->d.S_ic) + ctx->bdesc[bundle].so, sizeof(double) * n6 * n6));
     return PBA_OK;
 }
 
 pba_status pba_num_residuals(pba_ctx* ctx, int bundle, int64_t* n)
 {
-    if (!ctx || bundle != 0 || !n) return PBA_ERR_ARG;
-    if (!ctx->have_points) return fail(ctx, PBA_ERR_STATE, "points not set");
-    *n = ctx->V * (int64_t)(ctx->pattern.size() / 2);
+    CHECK_BUNDLE();
+    if (!n) return fail(ctx, PBA_ERR_ARG, "null output");
+    pba_status s = ensure_structure(ctx);
+    if (s != PBA_OK) return s;
+    *n = ctx->bun[bundle].V * (int64_t)(ctx->pattern.size() / 2);
     return PBA_OK;
 }
 
@@ -1031,6 +1295,48 @@ pba_status pba_enable_timing(pba_ctx* ctx, int mask)
         ctx->tcount[i] = 0;
     }
     ctx->launches = 0;
+    return PBA_OK;
+}
+
+pba_status pba_depth_features(pba_ctx* ctx, int bundle, float* features)
+{
+    CHECK_BUNDLE();
+    if (!features) return fail(ctx, PBA_ERR_ARG, "null features");
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    const BundleIn& b = ctx->bun[bundle];
+    LaunchCtx L = make_launch(ctx);
+    CK(launch_mlp_features(L.pb, ctx->d.fc, ctx->d.slot_caller, b.to, b.T, features, ctx->stream));
+    return PBA_OK;
+}
+
+pba_status pba_propose_depths(pba_ctx* ctx, int bundle, const void* packed, float* scratch)
+{
+    CHECK_BUNDLE();
+    if (!packed || !scratch || ((uintptr_t)packed & 15) || ((uintptr_t)scratch & 15))
+        return fail(ctx, PBA_ERR_ARG, "null or misaligned network / scratch");
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    const BundleIn& b = ctx->bun[bundle];
+    LaunchCtx L = make_launch(ctx);
+    float* y = scratch + (size_t)b.N * kMlpIn;
+    CK(launch_mlp_features(L.pb, ctx->d.fc, ctx->d.slot_caller, b.to, b.T, scratch, ctx->stream));
+    CK(launch_mlp_infer(static_cast<const uint8_t*>(packed), b.N, scratch, y, ctx->d.err, ctx->stream));
+    CK(launch_mlp_propose(ctx->d.slot_caller, kTile * b.to, kTile * b.T, y, ctx->d.d64, ctx->stream));
+    ctx->ic_ready = false;  // p_0 changes: the precompute must run again
+    return check_device_error(ctx);
+}
+
+pba_status pba_bundle_errors(pba_ctx* ctx, int* flags)
+{
+    if (!ctx || !flags) return PBA_ERR_ARG;
+    for (int b = 0; b < ctx->B; ++b) flags[b] = b < (int)ctx->bundle_err.size() ? ctx->bundle_err[b] : 0;
+    return PBA_OK;
+}
+
+pba_status pba_get_tuning(pba_ctx* ctx, int* res_warps, int* ldl_cluster)
+{
+    if (!ctx) return PBA_ERR_ARG;
+    if (res_warps) *res_warps = ctx->res_warps;
+    if (ldl_cluster) *ldl_cluster = ctx->ldl_cluster > 0 ? ctx->ldl_cluster : ldl_max_cluster();
     return PBA_OK;
 }
 

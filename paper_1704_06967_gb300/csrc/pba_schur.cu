@@ -167,9 +167,11 @@ schur_chunk_kernel(DevProblem pb, const float* Hfd, const float* Hnn, const int*
     }
 }
 
-// S_off blocks from the chunk sums, chunks of a pair added in order.
-__global__ void schur_pair_reduce_kernel(const int* pair_fg, const int* pair_chunk,
-                                         const float2* part, int n_pairs, double* Soff, int n6)
+// S_off blocks from the chunk sums, chunks of a pair added in order; a
+// pair's frames belong to one bundle, whose block of S_off it fills.
+__global__ void schur_pair_reduce_kernel(const int* pair_fg, const int* pair_chunk, const int* frame_bundle,
+                                         const BundleDesc* bund, const float2* part, int n_pairs,
+                                         double* Soff)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n_pairs * 36) return;
@@ -182,9 +184,11 @@ __global__ void schur_pair_reduce_kernel(const int* pair_fg, const int* pair_chu
         pair_add(vs, vc, v.x, v.y);
     }
     const double v = (double)vs + (double)vc;
-    const int i = 6 * (f - 1) + a, j = 6 * (g - 1) + b;
-    Soff[(size_t)i * n6 + j] = v;
-    Soff[(size_t)j * n6 + i] = v;
+    const BundleDesc bd = bund[frame_bundle[f]];
+    const size_t n6 = 6 * (bd.F - 1);
+    const int i = 6 * (f - bd.fo - 1) + a, j = 6 * (g - bd.fo - 1) + b;
+    Soff[bd.so + i * n6 + j] = v;
+    Soff[bd.so + j * n6 + i] = v;
 }
 
 cudaError_t launch_schur_sparse(const DevProblem& pb, const float* Hfd, const float* Hnn,
@@ -200,7 +204,7 @@ cudaError_t launch_schur_sparse(const DevProblem& pb, const float* Hfd, const fl
         if (e != cudaSuccess) return e;
     }
     schur_pair_reduce_kernel<<<(sl.n_pairs * 36 + 255) / 256, 256, 0, st>>>(
-        sl.pair_fg, sl.pair_chunk, part, sl.n_pairs, Soff, 6 * (pb.F - 1));
+        sl.pair_fg, sl.pair_chunk, pb.frame_bundle, pb.bund, part, sl.n_pairs, Soff);
     ++*launches;
     return cudaGetLastError();
 }

@@ -15,7 +15,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpba.so")
-HEADER = os.path.join(os.path.dirname(HERE), "include", "pba.h")
+HEADERS = [os.path.join(os.path.dirname(HERE), "include", h) for h in ("pba.h", "pba_mlp.h")]
 
 PBA_F32, PBA_F16, PBA_BF16 = 0, 1, 2
 PBA_MEM_DEVICE, PBA_MEM_HOST = 0, 1
@@ -39,7 +39,7 @@ class Config(ctypes.Structure):
                 ("pattern", ctypes.POINTER(ctypes.c_int32)), ("gauge_anchor_w", ctypes.c_double),
                 ("conv_px", ctypes.c_double), ("n_bundles", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("use_graphs", ctypes.c_int),
-                ("max_stats_iters", ctypes.c_int)]
+                ("max_stats_iters", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class IterStats(ctypes.Structure):
@@ -48,8 +48,8 @@ class IterStats(ctypes.Structure):
 
 
 def declared_symbols():
-    """Function names declared in include/pba.h."""
-    text = open(HEADER).read()
+    """Function names declared in include/pba.h and include/pba_mlp.h."""
+    text = "".join(open(h).read() for h in HEADERS)
     return sorted(set(re.findall(r"\b(pba_[a-z_0-9]+)\s*\(", text)))
 
 
@@ -81,6 +81,15 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pba_enable_timing": ([vp, i], i),
         "pba_last_timing": ([vp, vp], i),
         "pba_transfer_bytes": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], i),
+        "pba_get_tuning": ([vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
+        "pba_bundle_errors": ([vp, vp], i),
+        "pba_depth_features": ([vp, i, vp], i),
+        "pba_mlp_pack": ([vp, vp, vp], i),
+        "pba_mlp_infer": ([vp, i, vp, vp, vp, vp], i),
+        "pba_mlp_scratch_floats": ([i], ctypes.c_size_t),
+        "pba_mlp_grad": ([vp, i, vp, vp, vp, vp, vp, vp], i),
+        "pba_mlp_train_step": ([vp, vp, vp, i, ctypes.c_float, i, vp, vp, vp, vp, vp], i),
+        "pba_propose_depths": ([vp, i, vp, vp], i),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -94,17 +103,34 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-class Bundle:
-    """One bundle: reference + target images, p_0, points, visibility.
+def _scene_images(scene, device_images=True):
+    """A synth.Scene's image stack as a CUDA tensor (or the host array)."""
+    import torch
+    if not device_images:
+        return scene.images_store
+    store = scene.images_store
+    if scene.dtype == "bf16":
+        t = torch.from_numpy(store.view(np.int16)).cuda().view(torch.bfloat16)
+    else:
+        t = torch.from_numpy(store).cuda()
+    return t.contiguous()
 
-    images: torch tensor [F, H, W] on the GPU (float32, float16 or bfloat16;
-    borrowed) or a host numpy array of the same layout (copied into the
-    workspace by the library: mem="host"). The workspace is one torch uint8
-    tensor on the current CUDA device.
+
+class Batch:
+    """Independent bundles solved together in one context: every kernel of
+    an iteration runs over all of them in one launch, each bundle keeping its
+    own reference frame, gauge and reduced camera system.
+
+    items: sequence of (images, poses0, intrinsics, uv, inv_depth, vis) per
+    bundle. images: torch tensor [F, H, W] on the GPU (float32, float16 or
+    bfloat16; borrowed) or a host numpy array of the same layout (copied into
+    the workspace by the library). The bundles share the camera (image size,
+    type, intrinsics). The workspace is one torch uint8 tensor on the current
+    CUDA device.
     """
 
-    def __init__(self, images, poses0, intrinsics, uv, inv_depth, vis=None, *, pattern,
-                 huber_k, stream=None, gauge_anchor_w=1.0, max_stats_iters=256, use_graphs=False):
+    def __init__(self, items, *, pattern, huber_k, stream=None, gauge_anchor_w=1.0, max_stats_iters=256,
+                 use_graphs=False, autotune=False):
         import torch
         self.torch = torch
         lib = load()
@@ -114,41 +140,49 @@ class Bundle:
         self.stream = stream
         pat = np.ascontiguousarray(pattern, dtype=np.int32)
         self._pat = pat
+        items = list(items)
+        self.B = len(items)
         cfg = Config(float(huber_k), pat.shape[0],
                      pat.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), float(gauge_anchor_w),
-                     0.0, 1, ctypes.c_void_p(stream.cuda_stream), int(bool(use_graphs)),
-                     int(max_stats_iters))
+                     0.0, self.B, ctypes.c_void_p(stream.cuda_stream), int(bool(use_graphs)),
+                     int(max_stats_iters), int(bool(autotune)))
         h = ctypes.c_void_p()
+        self.h = None
         self._check(lib.pba_create(ctypes.byref(cfg), ctypes.byref(h)), None)
         self.h = h
         self.P = pat.shape[0]
         self._keep = []
-        if isinstance(images, torch.Tensor):
-            assert images.is_cuda and images.dim() == 3 and images.is_contiguous()
-            dt = {torch.float32: PBA_F32, torch.float16: PBA_F16, torch.bfloat16: PBA_BF16}[images.dtype]
-            mem, ptr = PBA_MEM_DEVICE, ctypes.c_void_p(images.data_ptr())
-            self._keep.append(images)
-        else:
-            arr = np.ascontiguousarray(images)
-            dt = {np.dtype(np.float32): PBA_F32, np.dtype(np.float16): PBA_F16,
-                  np.dtype(np.uint16): PBA_BF16}[arr.dtype]
-            mem, ptr = PBA_MEM_HOST, _p(arr)
-            self._keep.append(arr)
-        F, H, W = images.shape
-        self.F, self.H, self.W = int(F), int(H), int(W)
-        poses0 = np.ascontiguousarray(poses0, dtype=np.float64)
-        K = np.ascontiguousarray(intrinsics, dtype=np.float64)
-        self._check(lib.pba_set_frames(h, 0, self.F, self.W, self.H, self.W, dt, mem, ptr,
-                                       _p(poses0), _p(K)))
-        uv = np.ascontiguousarray(uv, dtype=np.int32)
-        d0 = np.ascontiguousarray(inv_depth, dtype=np.float64)
-        self.N = uv.shape[0]
-        visp = None
-        if vis is not None:
-            vis = np.ascontiguousarray(vis, dtype=np.uint8)
-            assert vis.shape == (self.N, self.F)
-            visp = _p(vis)
-        self._check(lib.pba_set_points(h, 0, self.N, _p(uv), _p(d0), visp))
+        self.Fs, self.Ns = [], []
+        for b, (images, poses0, intrinsics, uv, inv_depth, vis) in enumerate(items):
+            if isinstance(images, torch.Tensor):
+                assert images.is_cuda and images.dim() == 3 and images.is_contiguous()
+                dt = {torch.float32: PBA_F32, torch.float16: PBA_F16,
+                      torch.bfloat16: PBA_BF16}[images.dtype]
+                mem, ptr = PBA_MEM_DEVICE, ctypes.c_void_p(images.data_ptr())
+                self._keep.append(images)
+            else:
+                arr = np.ascontiguousarray(images)
+                dt = {np.dtype(np.float32): PBA_F32, np.dtype(np.float16): PBA_F16,
+                      np.dtype(np.uint16): PBA_BF16}[arr.dtype]
+                mem, ptr = PBA_MEM_HOST, _p(arr)
+                self._keep.append(arr)
+            F, H, W = images.shape
+            self.H, self.W = int(H), int(W)
+            self.Fs.append(int(F))
+            poses0 = np.ascontiguousarray(poses0, dtype=np.float64)
+            K = np.ascontiguousarray(intrinsics, dtype=np.float64)
+            self._check(lib.pba_set_frames(h, b, int(F), self.W, self.H, self.W, dt, mem, ptr,
+                                           _p(poses0), _p(K)))
+            uv = np.ascontiguousarray(uv, dtype=np.int32)
+            d0 = np.ascontiguousarray(inv_depth, dtype=np.float64)
+            self.Ns.append(uv.shape[0])
+            visp = None
+            if vis is not None:
+                vis = np.ascontiguousarray(vis, dtype=np.uint8)
+                assert vis.shape == (uv.shape[0], int(F))
+                visp = _p(vis)
+                self._keep.append(vis)
+            self._check(lib.pba_set_points(h, b, uv.shape[0], _p(uv), _p(d0), visp))
         nb = ctypes.c_size_t()
         self._check(lib.pba_workspace_size(h, ctypes.byref(nb)))
         self.workspace = torch.empty(int(nb.value) + 256, dtype=torch.uint8, device="cuda")
@@ -158,20 +192,12 @@ class Bundle:
         self.workspace_bytes = int(nb.value)
 
     @classmethod
-    def from_scene(cls, scene, device_images=True, **kw):
-        """Bundle from a synth.Scene (images uploaded with torch, or host)."""
-        import torch
-        if device_images:
-            store = scene.images_store
-            if scene.dtype == "bf16":
-                t = torch.from_numpy(store.view(np.int16)).cuda().view(torch.bfloat16)
-            else:
-                t = torch.from_numpy(store).cuda()
-            images = t.contiguous()
-        else:
-            images = scene.images_store
-        return cls(images, scene.poses0, scene.intrinsics, scene.uv, scene.depths0, scene.vis,
-                   pattern=scene.pattern, huber_k=scene.huber_k, **kw)
+    def from_scenes(cls, scenes, device_images=True, **kw):
+        """Batch from synth.Scene objects that share the camera and pattern."""
+        s0 = scenes[0]
+        items = [(_scene_images(sc, device_images), sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis)
+                 for sc in scenes]
+        return cls(items, pattern=s0.pattern, huber_k=s0.huber_k, **kw)
 
     # ------------------------------------------------------------------
     def _check(self, st, h=True):
@@ -209,40 +235,72 @@ class Bundle:
     def solve_fc(self, n_iters, stats=True):
         return self._stats(self.lib.pba_solve_fc, n_iters, stats)
 
-    def params(self):
-        poses = np.zeros((self.F, 12))
-        d = np.zeros(self.N)
-        self._check(self.lib.pba_get_params(self.h, 0, _p(poses), _p(d)))
+    def params(self, bundle=0):
+        poses = np.zeros((self.Fs[bundle], 12))
+        d = np.zeros(self.Ns[bundle])
+        self._check(self.lib.pba_get_params(self.h, bundle, _p(poses), _p(d)))
         return poses, d
 
-    def set_params(self, poses, depths):
+    def set_params(self, poses, depths, bundle=0):
         poses = np.ascontiguousarray(poses, dtype=np.float64)
         depths = np.ascontiguousarray(depths, dtype=np.float64)
-        self._check(self.lib.pba_set_params(self.h, 0, _p(poses), _p(depths)))
+        self._check(self.lib.pba_set_params(self.h, bundle, _p(poses), _p(depths)))
 
-    def last_update(self):
-        dth = np.zeros((self.F, 6))
-        dd = np.zeros(self.N)
-        self._check(self.lib.pba_get_last_update(self.h, 0, _p(dth), _p(dd)))
+    def last_update(self, bundle=0):
+        dth = np.zeros((self.Fs[bundle], 6))
+        dd = np.zeros(self.Ns[bundle])
+        self._check(self.lib.pba_get_last_update(self.h, bundle, _p(dth), _p(dd)))
         return dth, dd
 
-    def system(self, fc=False):
-        n6 = 6 * (self.F - 1)
-        Hff = np.zeros((self.F, 6, 6))
-        Hfd = np.zeros((self.N, self.F, 6))
-        Hdd = np.zeros(self.N)
+    def system(self, fc=False, bundle=0):
+        F, N = self.Fs[bundle], self.Ns[bundle]
+        n6 = 6 * (F - 1)
+        Hff = np.zeros((F, 6, 6))
+        Hfd = np.zeros((N, F, 6))
+        Hdd = np.zeros(N)
         S = np.zeros((n6, n6))
-        self._check(self.lib.pba_get_system(self.h, 0, int(bool(fc)), _p(Hff), _p(Hfd), _p(Hdd), _p(S)))
+        self._check(self.lib.pba_get_system(self.h, bundle, int(bool(fc)), _p(Hff), _p(Hfd), _p(Hdd), _p(S)))
         return dict(Hff=Hff, Hfd=Hfd, Hdd=Hdd, S=S)
 
-    def n_residuals(self):
-        n = ctypes.c_int64()
-        self._check(self.lib.pba_num_residuals(self.h, 0, ctypes.byref(n)))
-        return int(n.value)
+    def n_residuals(self, bundle=None):
+        """Residual count of one bundle, or of all (bundle=None)."""
+        total = 0
+        for b in (range(self.B) if bundle is None else [bundle]):
+            n = ctypes.c_int64()
+            self._check(self.lib.pba_num_residuals(self.h, b, ctypes.byref(n)))
+            total += int(n.value)
+        return total
 
     def enable_timing(self, mask=-1):
         """mask: bit s times slot s (TIMING_NAMES order); -1 all, 0 none."""
         self._check(self.lib.pba_enable_timing(self.h, int(mask)))
+
+    def bundle_errors(self):
+        """Per-bundle error bits of the last synchronising call (1: system
+        not positive definite, 2: non-finite update)."""
+        out = np.zeros(self.B, dtype=np.int32)
+        self._check(self.lib.pba_bundle_errors(self.h, _p(out)))
+        return out
+
+    def depth_features(self, bundle=0):
+        """Learned-proposal features of the bundle's points at the current
+        poses: torch float32 [N, 96] on the GPU (caller's point order)."""
+        t = self.torch.empty((self.Ns[bundle], 96), dtype=self.torch.float32, device="cuda")
+        self._check(self.lib.pba_depth_features(self.h, bundle, ctypes.c_void_p(t.data_ptr())))
+        return t
+
+    def propose_depths(self, packed, bundle=0):
+        """Replaces the bundle's inverse depths by the network's proposals
+        (packed: the inference layout, a torch uint8 CUDA tensor)."""
+        scratch = self.torch.empty(self.Ns[bundle] * 97 + 4, dtype=self.torch.float32, device="cuda")
+        self._check(self.lib.pba_propose_depths(self.h, bundle, ctypes.c_void_p(packed.data_ptr()),
+                                                ctypes.c_void_p(scratch.data_ptr())))
+
+    def tuning(self):
+        """(warps per CTA of the IC residual pass, CTAs per bundle of the factorisation)."""
+        w, c = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.pba_get_tuning(self.h, ctypes.byref(w), ctypes.byref(c)))
+        return int(w.value), int(c.value)
 
     def transfer_bytes(self):
         a, b = ctypes.c_int64(), ctypes.c_int64()
@@ -255,3 +313,18 @@ class Bundle:
         ms = dict(zip(TIMING_NAMES, out[:TIMING_SLOTS]))
         counts = dict(zip(TIMING_NAMES, out[TIMING_SLOTS + 1:].astype(int)))
         return ms, int(out[TIMING_SLOTS]), counts
+
+
+class Bundle(Batch):
+    """One bundle: reference + target images, p_0, points, visibility (a
+    context of one bundle; see Batch for the arguments)."""
+
+    def __init__(self, images, poses0, intrinsics, uv, inv_depth, vis=None, **kw):
+        super().__init__([(images, poses0, intrinsics, uv, inv_depth, vis)], **kw)
+        self.F, self.N = self.Fs[0], self.Ns[0]
+
+    @classmethod
+    def from_scene(cls, scene, device_images=True, **kw):
+        """Bundle from a synth.Scene (images uploaded with torch, or host)."""
+        return cls(_scene_images(scene, device_images), scene.poses0, scene.intrinsics, scene.uv,
+                   scene.depths0, scene.vis, pattern=scene.pattern, huber_k=scene.huber_k, **kw)

@@ -156,6 +156,7 @@ class SceneConfig:
     margin_px: float = 6.0
     min_pts_per_frame: int = 16
     edge_px: int = 1                # candidate points keep this distance from object edges
+    allow_fewer_points: bool = False  # take all candidates when fewer than n_points exist
 
 
 CONFIGS = {
@@ -208,7 +209,7 @@ class Scene:
 
     @property
     def F(self):
-        return self.images_f32.shape[0]
+        return self.images_store.shape[0]
 
     @property
     def N(self):
@@ -271,7 +272,7 @@ def _camera_centres(cfg: SceneConfig) -> np.ndarray:
 
 
 def _select_points(I0: np.ndarray, hit: np.ndarray, pattern: np.ndarray, n: int,
-                   spacing: int, border: int, edge_px: int) -> np.ndarray:
+                   spacing: int, border: int, edge_px: int, allow_fewer: bool = False) -> np.ndarray:
     from scipy.ndimage import maximum_filter, minimum_filter
     H, W = I0.shape
     gx = np.zeros_like(I0, dtype=np.float64)
@@ -303,7 +304,7 @@ def _select_points(I0: np.ndarray, hit: np.ndarray, pattern: np.ndarray, n: int,
         pts.append((u, v))
         if len(pts) == n:
             break
-    if len(pts) < n:
+    if len(pts) < n and not allow_fewer:
         raise ValueError(f"only {len(pts)} candidate points for {n} requested")
     return np.array(pts, dtype=np.int32)
 
@@ -357,7 +358,8 @@ def make_scene(name_or_cfg, seed_offset: int = 0, noise_free: bool = False,
     pattern = PATTERN8.copy()
     prad = int(np.abs(pattern).max())
     border = prad + 2 + int(math.ceil(cfg.margin_px))
-    uv = _select_points(deq[0], hit0, pattern, cfg.n_points, cfg.spacing, border, cfg.edge_px)
+    uv = _select_points(deq[0], hit0, pattern, cfg.n_points, cfg.spacing, border, cfg.edge_px,
+                        cfg.allow_fewer_points)
     N = uv.shape[0]
 
     # ground-truth 3-D points (world) from the reference camera's rays

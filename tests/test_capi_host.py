@@ -38,9 +38,10 @@ def test_create_rejects_bad_configs(lib):
     assert lib.pba_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
     cfg, pat = _cfg(P=17)
     assert lib.pba_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
-    cfg, pat = _cfg()
-    cfg.n_bundles = 2
-    assert lib.pba_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
+    for nb in (-1, 65536):
+        cfg, pat = _cfg()
+        cfg.n_bundles = nb
+        assert lib.pba_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
     assert lib.pba_create(None, ctypes.byref(h)) == 1
 
 
@@ -118,3 +119,72 @@ def test_workspace_grows_with_the_problem(lib):
         sizes.append(nb.value)
         lib.pba_destroy(h)
     assert sizes[0] < sizes[1] < sizes[2]
+
+
+def _frames(F, W=64, H=48, K=(50.0, 50.0, 31.5, 23.5)):
+    img = np.zeros((F, H, W), np.float32)
+    poses = np.zeros((F, 12))
+    poses[:, [0, 4, 8]] = 1.0
+    return img, poses, np.array(K)
+
+
+def test_batched_bundles_share_the_camera_and_count_separately(lib):
+    cfg, pat = _cfg()
+    cfg.n_bundles = 3
+    h = ctypes.c_void_p()
+    assert lib.pba_create(ctypes.byref(cfg), ctypes.byref(h)) == 0
+    try:
+        W, H = 64, 48
+        keep = []
+        for b, F in enumerate((3, 5, 2)):
+            img, poses, K = _frames(F)
+            keep.append((img, poses, K))
+            assert lib.pba_set_frames(h, b, F, W, H, W, 0, 1, img.ctypes.data, poses.ctypes.data,
+                                      K.ctypes.data) == 0
+        assert lib.pba_set_frames(h, 3, *((2, W, H, W, 0, 1) + tuple(
+            a.ctypes.data for a in keep[2]))) == 1
+        # another camera for bundle 1 while the others are set: refused
+        img, poses, K = _frames(5, K=(60.0, 50.0, 31.5, 23.5))
+        assert lib.pba_set_frames(h, 1, 5, W, H, W, 0, 1, img.ctypes.data, poses.ctypes.data,
+                                  K.ctypes.data) == 1
+        assert b"share" in lib.pba_last_error(h)
+        img2, poses2, K2 = _frames(5, W=80)
+        assert lib.pba_set_frames(h, 1, 5, 80, H, 80, 0, 1, img2.ctypes.data, poses2.ctypes.data,
+                                  K2.ctypes.data) == 1
+        nb = ctypes.c_size_t()
+        rng = np.random.default_rng(1)
+        counts = (7, 40, 33)
+        for b, N in enumerate(counts):
+            # the workspace needs every bundle's points
+            assert lib.pba_workspace_size(h, ctypes.byref(nb)) == 2
+            uv = np.stack([rng.integers(5, W - 5, N), rng.integers(5, H - 5, N)], 1).astype(np.int32)
+            d = np.ones(N)
+            assert lib.pba_set_points(h, b, N, uv.ctypes.data, d.ctypes.data, None) == 0
+        assert lib.pba_workspace_size(h, ctypes.byref(nb)) == 0
+        for b, (N, F) in enumerate(zip(counts, (3, 5, 2))):
+            n = ctypes.c_int64()
+            assert lib.pba_num_residuals(h, b, ctypes.byref(n)) == 0
+            assert n.value == N * (F - 1) * 8
+        # the batch holds every bundle's data: more than any one bundle needs
+        # alone, and close to their sum (per-context pieces such as the
+        # statistics slots are held once)
+        total, largest = 0, 0
+        for b, (N, F) in enumerate(zip(counts, (3, 5, 2))):
+            cfg1, pat1 = _cfg()
+            h1 = ctypes.c_void_p()
+            assert lib.pba_create(ctypes.byref(cfg1), ctypes.byref(h1)) == 0
+            img, poses, K = keep[b]
+            assert lib.pba_set_frames(h1, 0, F, W, H, W, 0, 1, img.ctypes.data, poses.ctypes.data,
+                                      K.ctypes.data) == 0
+            rng1 = np.random.default_rng(b)
+            uv = np.stack([rng1.integers(5, W - 5, N), rng1.integers(5, H - 5, N)], 1).astype(np.int32)
+            d = np.ones(N)
+            assert lib.pba_set_points(h1, 0, N, uv.ctypes.data, d.ctypes.data, None) == 0
+            nb1 = ctypes.c_size_t()
+            assert lib.pba_workspace_size(h1, ctypes.byref(nb1)) == 0
+            total += nb1.value
+            largest = max(largest, nb1.value)
+            lib.pba_destroy(h1)
+        assert largest < nb.value <= total
+    finally:
+        lib.pba_destroy(h)
