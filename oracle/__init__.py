@@ -48,7 +48,7 @@ class _Problem(ctypes.Structure):
                 ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double),
                 ("cy", ctypes.c_double), ("huber_k", ctypes.c_double),
                 ("img", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("pat", ctypes.c_void_p),
-                ("vis", ctypes.c_void_p)]
+                ("vis", ctypes.c_void_p), ("damping", ctypes.c_double)]
 
 
 class _IcPre(ctypes.Structure):
@@ -78,7 +78,7 @@ def _L():
             "or_ic_residual": ([pp, vp, vp, i, i, i, vp, vp], i),
             "or_fc_residual": ([pp, vp, vp, i, i, i, vp, vp], i),
             "or_ic_precompute": ([pp, vp, vp, ctypes.POINTER(_IcPre)], None),
-            "or_schur_solve": ([i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp], i),
+            "or_schur_solve": ([i, i, vp, vp, vp, vp, vp, vp, d, vp, vp, vp], i),
             "or_max_reproj_disp": ([pp, vp, vp, vp, vp], d),
             "or_ic_gradient": ([pp, ctypes.POINTER(_IcPre), vp, vp, vp, vp, vp], None),
             "or_ic_update": ([i, i, vp, vp, vp, vp, vp, vp, vp, vp], None),
@@ -178,7 +178,7 @@ class Problem:
     """A bundle as the oracle sees it: FP64 copies of the (dequantised) images,
     integer point pixels, pattern, visibility, intrinsics and Huber k."""
 
-    def __init__(self, images, uv, pattern, vis, intrinsics, huber_k):
+    def __init__(self, images, uv, pattern, vis, intrinsics, huber_k, damping=0.0):
         self.img = _f64(images)
         self.F, self.H, self.W = self.img.shape
         self.uv = np.ascontiguousarray(uv, dtype=np.int32)
@@ -188,13 +188,15 @@ class Problem:
         fx, fy, cx, cy = [float(v) for v in intrinsics]
         self.fx, self.fy, self.cx, self.cy = fx, fy, cx, cy
         self.huber_k = float(huber_k)
+        self.damping = float(damping)
         self.c = _Problem(self.W, self.H, self.F, self.N, self.P, fx, fy, cx, cy,
-                          self.huber_k, _p(self.img), _p(self.uv), _p(self.pat), _p(self.vis))
+                          self.huber_k, _p(self.img), _p(self.uv), _p(self.pat), _p(self.vis),
+                          self.damping)
 
     @classmethod
-    def from_scene(cls, scene):
+    def from_scene(cls, scene, damping=0.0):
         return cls(scene.images_f32, scene.uv, scene.pattern, scene.vis, scene.intrinsics,
-                   scene.huber_k)
+                   scene.huber_k, damping)
 
     def ref(self):
         return ctypes.byref(self.c)
@@ -243,14 +245,14 @@ def ic_precompute(pb: Problem, poses0, depths0) -> IcPre:
     return pre
 
 
-def schur_solve(F, N, Hff, Hfd, Hdd, g_theta, g_d, t_anchor, want_S=False):
+def schur_solve(F, N, Hff, Hfd, Hdd, g_theta, g_d, t_anchor, want_S=False, damping=0.0):
     Hff, Hfd, Hdd = _f64(Hff), _f64(Hfd), _f64(Hdd)
     g_theta, g_d, t_anchor = _f64(g_theta), _f64(g_d), _f64(t_anchor)
     dtheta, dd = np.zeros(6 * F), np.zeros(N)
     n6 = 6 * (F - 1)
     S = np.zeros((n6, n6)) if want_S else None
     st = _L().or_schur_solve(F, N, _p(Hff), _p(Hfd), _p(Hdd), _p(g_theta), _p(g_d),
-                             _p(t_anchor), _p(dtheta), _p(dd), _p(S) if want_S else None)
+                             _p(t_anchor), float(damping), _p(dtheta), _p(dd), _p(S) if want_S else None)
     if st != 0:
         raise np.linalg.LinAlgError(f"reduced camera system not positive definite ({st})")
     return dtheta.reshape(F, 6), dd, S

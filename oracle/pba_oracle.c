@@ -54,6 +54,7 @@ typedef struct {
     const int* uv;              /* N*2 integer pixel centres in frame 0 */
     const int* pat;             /* P*2 pattern offsets (pixels) */
     const unsigned char* vis;   /* N*F visibility, vis[n*F+f] */
+    double damping;             /* Levenberg-Marquardt lambda (0: Gauss-Newton) */
 } or_problem;
 
 /* IC precompute (Sec. 3.5), indexed by residual id ((n*F + f)*P + j). */
@@ -483,13 +484,22 @@ static void cholesky_solve(const double* L, int n, double* b)
  * diagonal (one 6x6 per target frame) and Hdd diagonal (one scalar per point):
  *   S = Hpp - Hpd Hdd^-1 Hdp,  S dtheta = -(g_theta - Hpd Hdd^-1 g_d),
  *   dd = -Hdd^-1 (g_d + Hdp dtheta).
- * t_anchor: F*3 translations used for the scale-gauge prior.
- * S_out (nullable): the anchored (6(F-1))^2 matrix that was factorised. */
+ * t_anchor: F*3 translations used for the scale gauge.
+ * damping = 0 (Gauss-Newton, Sec. 3.5): the scale-gauge prior mu that^T on
+ *   the first active frame's translation block makes S definite.
+ * damping = lambda > 0 (Levenberg-Marquardt, an option beyond the paper):
+ *   every diagonal entry of Hpp and Hdd is multiplied by 1 + lambda, which
+ *   makes S definite without the prior; the gauge is then fixed by moving
+ *   dtheta along the scale null vector (Delta t_f -= alpha t_f on the active
+ *   frames, alpha = t_a . Delta t_a / |t_a|^2 of the anchor frame a) before
+ *   the depth back-substitution.
+ * S_out (nullable): the (6(F-1))^2 matrix that was factorised. */
 int or_schur_solve(int F, int N, const double* Hff, const double* Hfd, const double* Hdd,
-                   const double* g_theta, const double* g_d, const double* t_anchor,
+                   const double* g_theta, const double* g_d, const double* t_anchor, double damping,
                    double* dtheta, double* dd, double* S_out)
 {
     int Fp = F - 1, n6 = 6 * Fp;
+    const double ld = 1.0 + damping;
     double* S = (double*)calloc((size_t)n6 * n6, sizeof(double));
     double* b = (double*)calloc(n6, sizeof(double));
     int* active = (int*)calloc(F, sizeof(int));
@@ -499,20 +509,22 @@ int or_schur_solve(int F, int N, const double* Hff, const double* Hfd, const dou
         active[f] = tr > 0.0;
         for (int a = 0; a < 6; ++a) {
             for (int c = 0; c < 6; ++c)
-                S[(size_t)(6 * (f - 1) + a) * n6 + 6 * (f - 1) + c] = Hff[36 * f + 6 * a + c];
+                S[(size_t)(6 * (f - 1) + a) * n6 + 6 * (f - 1) + c] =
+                    Hff[36 * f + 6 * a + c] * (a == c ? ld : 1.0);
             b[6 * (f - 1) + a] = -g_theta[6 * f + a];
         }
     }
     for (int n = 0; n < N; ++n) {
         if (!(Hdd[n] > 0.0)) continue;
+        const double hd = Hdd[n] * ld;
         for (int f = 1; f < F; ++f) {
             const double* hf = Hfd + 6 * ((size_t)n * F + f);
-            for (int a = 0; a < 6; ++a) b[6 * (f - 1) + a] += hf[a] * g_d[n] / Hdd[n];
+            for (int a = 0; a < 6; ++a) b[6 * (f - 1) + a] += hf[a] * g_d[n] / hd;
             for (int g = 1; g < F; ++g) {
                 const double* hg = Hfd + 6 * ((size_t)n * F + g);
                 for (int a = 0; a < 6; ++a)
                     for (int c = 0; c < 6; ++c)
-                        S[(size_t)(6 * (f - 1) + a) * n6 + 6 * (g - 1) + c] -= hf[a] * hg[c] / Hdd[n];
+                        S[(size_t)(6 * (f - 1) + a) * n6 + 6 * (g - 1) + c] -= hf[a] * hg[c] / hd;
             }
         }
     }
@@ -536,7 +548,7 @@ int or_schur_solve(int F, int N, const double* Hff, const double* Hfd, const dou
             b[6 * (f - 1) + a] = 0.0;
         }
     }
-    if (anchor > 0) {
+    if (anchor > 0 && damping == 0.0) {
         const double* ta = t_anchor + 3 * anchor;
         double nt = sqrt(ta[0] * ta[0] + ta[1] * ta[1] + ta[2] * ta[2]);
         if (nt > 0.0) {
@@ -553,6 +565,15 @@ int or_schur_solve(int F, int N, const double* Hff, const double* Hfd, const dou
         memset(dtheta, 0, sizeof(double) * 6 * F);
         for (int f = 1; f < F; ++f)
             for (int a = 0; a < 6; ++a) dtheta[6 * f + a] = b[6 * (f - 1) + a];
+        if (damping > 0.0 && anchor > 0) {
+            const double* ta = t_anchor + 3 * anchor;
+            const double* da = dtheta + 6 * anchor;
+            const double n2 = ta[0] * ta[0] + ta[1] * ta[1] + ta[2] * ta[2];
+            const double alpha = n2 > 0.0 ? (ta[0] * da[0] + ta[1] * da[1] + ta[2] * da[2]) / n2 : 0.0;
+            for (int f = 1; f < F; ++f)
+                if (active[f])
+                    for (int a = 0; a < 3; ++a) dtheta[6 * f + a] -= alpha * t_anchor[3 * f + a];
+        }
         for (int n = 0; n < N; ++n) {
             if (!(Hdd[n] > 0.0)) { dd[n] = 0.0; continue; }
             double s = g_d[n];
@@ -560,7 +581,7 @@ int or_schur_solve(int F, int N, const double* Hff, const double* Hfd, const dou
                 const double* hf = Hfd + 6 * ((size_t)n * F + f);
                 for (int a = 0; a < 6; ++a) s += hf[a] * dtheta[6 * f + a];
             }
-            dd[n] = -s / Hdd[n];
+            dd[n] = -s / (Hdd[n] * ld);
         }
     }
     free(S);
@@ -671,8 +692,8 @@ int or_ic_step(const or_problem* pb, const or_ic_pre* pre, const double* poses0,
     or_ic_gradient(pb, pre, poses, depths, g_theta, g_d, stats);
     for (int f = 0; f < F; ++f)
         for (int i = 0; i < 3; ++i) t_anchor[3 * f + i] = poses0[12 * f + 9 + i];
-    int st = or_schur_solve(F, N, pre->Hff, pre->Hfd, pre->Hdd, g_theta, g_d, t_anchor, dtheta,
-                            dd, NULL);
+    int st = or_schur_solve(F, N, pre->Hff, pre->Hfd, pre->Hdd, g_theta, g_d, t_anchor, pb->damping,
+                            dtheta, dd, NULL);
     if (st == OR_OK) {
         or_ic_update(F, N, poses0, depths0, poses, depths, dtheta, dd, poses_out, depths_out);
         stats[ST_MAXDISP] = or_max_reproj_disp(pb, poses, depths, poses_out, depths_out);
@@ -758,7 +779,7 @@ int or_fc_step(const or_problem* pb, const double* poses, const double* depths, 
     or_fc_linearize(pb, poses, depths, Hff, Hfd, Hdd, g_theta, g_d, stats);
     for (int f = 0; f < F; ++f)
         for (int i = 0; i < 3; ++i) t_anchor[3 * f + i] = poses[12 * f + 9 + i];
-    int st = or_schur_solve(F, N, Hff, Hfd, Hdd, g_theta, g_d, t_anchor, dtheta, dd, NULL);
+    int st = or_schur_solve(F, N, Hff, Hfd, Hdd, g_theta, g_d, t_anchor, pb->damping, dtheta, dd, NULL);
     if (st == OR_OK) {
         or_fc_update(F, N, poses, depths, dtheta, dd, poses_out, depths_out);
         stats[ST_MAXDISP] = or_max_reproj_disp(pb, poses, depths, poses_out, depths_out);

@@ -388,6 +388,38 @@ def test_schur_solution_solves_the_full_normal_equations(tiny):
     assert abs(dtheta[1, :3] @ t1) < 1e-10 * np.abs(dtheta).max()
 
 
+@pytest.mark.parametrize("lam", [0.05, 0.7])
+def test_damped_schur_solution_matches_the_dense_damped_solve(tiny, lam):
+    """Levenberg-Marquardt (beyond the paper's Gauss-Newton): the Schur path
+    with every diagonal entry of H scaled by 1 + lambda gives the frame update
+    of the dense damped solve up to the scale null vector (Delta t_f ~ t_f),
+    fixes the gauge (t_a . Delta t_a = 0) and back-substitutes the depths from
+    the damped point equations."""
+    sc, pb, pre = tiny
+    F, N = pb.F, pb.N
+    g_theta, g_d, _ = oracle.ic_gradient(pb, pre, sc.poses0, sc.depths0)
+    dth, dd, _ = oracle.schur_solve(F, N, pre.Hff, pre.Hfd, pre.Hdd, g_theta, g_d, sc.poses0[:, 9:],
+                                    damping=lam)
+    J, w = _dense_ic(pb, pre)
+    H = J.T @ (w[:, None] * J)
+    H = H + lam * np.diag(np.diag(H))
+    g = np.concatenate([g_theta[1:].ravel(), g_d])
+    keep = np.concatenate([np.arange(6 * (F - 1)), 6 * (F - 1) + np.flatnonzero(pre.Hdd > 0)])
+    dp = np.zeros(6 * (F - 1) + N)
+    dp[keep] = np.linalg.solve(H[np.ix_(keep, keep)], -g[keep])
+    diff = (dth[1:] - dp[:6 * (F - 1)].reshape(F - 1, 6))
+    assert np.abs(diff[:, 3:]).max() < 1e-9 * np.abs(dth).max()
+    t = sc.poses0[1:, 9:]
+    alpha = -(diff[:, :3] * t).sum() / (t * t).sum()
+    assert np.abs(diff[:, :3] + alpha * t).max() < 1e-9 * np.abs(dth).max()
+    assert abs(alpha) > 1e-6 * np.abs(dth).max()  # the damped step does move along the gauge
+    t1 = sc.poses0[1, 9:]
+    assert abs(dth[1, :3] @ t1) < 1e-12 * np.abs(dth).max()
+    Hdp = np.array([pre.Hfd[n, 1:].ravel() for n in range(N)])
+    r = pre.Hdd * (1 + lam) * dd + Hdp @ dth[1:].ravel() + g_d
+    assert np.abs(r[pre.Hdd > 0]).max() < 1e-9 * np.abs(g_d).max()
+
+
 # ----------------------------------------------------------------------------
 # updates (Sec. 3.6)
 # ----------------------------------------------------------------------------
