@@ -56,6 +56,9 @@ def parse():
                    help="submit every kernel with its own launch instead of replaying CUDA graphs")
     p.add_argument("--bundles", type=int, default=256,
                    help="batch workload: number of bundles (default 256)")
+    p.add_argument("--train-bundles", type=int, default=48, help="learned workload: training bundles")
+    p.add_argument("--eval-bundles", type=int, default=16, help="learned workload: held-out bundles")
+    p.add_argument("--epochs", type=int, default=20, help="learned workload: training epochs")
     return p.parse_args()
 
 
@@ -63,6 +66,10 @@ WORKLOAD_TEXT = {
     "helix30": "30-frame 2-turn helix around a value-noise sphere",
     "orbit101": "reference + 100 frames on a 30-degree orbit around a value-noise sphere on a "
                 "textured ground plane",
+    "learned": "learned inverse-depth proposal: trained on the converged inverse depths of "
+               "generated 30-frame 640x480 FP16 helix bundles (sphere radius uniform 0.5-2, texture "
+               "seed = bundle index), evaluated on held-out bundles against the constant-depth "
+               "initialisation",
     "batch256": "independent bundles of uneven size solved together: frames uniform 4-64 on a "
                 "helix (24 deg per frame), points log-uniform 500-50,000, sphere radius uniform "
                 "0.5-2, texture seed = bundle index, 640x480 FP16, f=525",
@@ -215,6 +222,10 @@ def run_reference(args):
         return 0
     if SCENE == "batch256":
         return run_reference_batch(args)
+    if SCENE == "learned":
+        print(json.dumps({"impl": "reference", "unavailable": "the learned workload has no CPU arm: the "
+                          "FP64 oracle of the network (oracle/mlp.py) checks its kernels in tests"}), flush=True)
+        return 0
     import numpy as np
     import oracle
     import synth
@@ -496,7 +507,7 @@ def run_batch(args):
     import torch
 
     import synth
-    from paper_1704_06967_gb300 import Batch, Bundle
+    from paper_1704_06967_gb300 import Batch, Bundle, PbaError
     from paper_1704_06967_gb300 import build as pkg_build
     from paper_1704_06967_gb300.pba import _scene_images
 
@@ -543,17 +554,42 @@ def run_batch(args):
         e1.synchronize()
         return e0.elapsed_time(e1)
 
+    ic_failed = set()
+
+    def flagged(fn, ctx, failed, bundle=None):
+        # a weakly observed bundle can have an indefinite system (flagged by
+        # the library per bundle; the others are solved normally)
+        try:
+            return fn()
+        except PbaError as e:
+            if e.status not in (5, 6):
+                raise
+            errs = ctx.bundle_errors()
+            failed.update([bundle] if bundle is not None else [int(b) for b in np.flatnonzero(errs)])
+            return None
+
     def batch_ic():
-        batch.precompute_ic()
-        batch.iterate(iters, stats=False)
+        flagged(batch.precompute_ic, batch, ic_failed)
+        flagged(lambda: batch.iterate(iters, stats=False), batch, ic_failed)
 
     def loop_ic():
-        for b in singles:
-            b.precompute_ic()
-            b.iterate(iters, stats=False)
+        for i, b in enumerate(singles):
+            flagged(b.precompute_ic, b, ic_failed, i)
+            flagged(lambda: b.iterate(iters, stats=False), b, ic_failed, i)
 
-    def batch_fc():
-        batch.solve_fc(iters, stats=False)
+    fc_failed = set()
+
+    def batch_fc(stats=False):
+        # a weakly observed bundle can make FC's system indefinite (the FP64
+        # oracle agrees on such bundles); the library flags that bundle and
+        # the others are solved normally
+        try:
+            return batch.solve_fc(iters, stats=stats)
+        except PbaError as e:
+            if e.status not in (5, 6):
+                raise
+            fc_failed.update(int(b) for b in np.flatnonzero(batch.bundle_errors()))
+            return None
 
     for i in range(args.warmup):
         reset()
@@ -597,19 +633,24 @@ def run_batch(args):
     torch.cuda.synchronize()
     mismatch = 0
     for i in range(0, B, max(1, B // 16)):
+        if i in ic_failed:
+            continue
         P1, D1 = batch.params(i)
         P2, D2 = singles[i].params()
         mismatch += int(not (np.array_equal(P1, P2) and np.array_equal(D1, D2)))
     # final RMS of the batch's IC and FC solves (sums over the bundles)
     reset()
-    batch.precompute_ic()
-    st_ic = batch.iterate(iters)
+    flagged(batch.precompute_ic, batch, ic_failed)
+    st_ic = flagged(lambda: batch.iterate(iters), batch, ic_failed)
     reset()
-    st_fc = batch.solve_fc(iters)
+    st_fc = batch_fc(stats=True)
 
-    # roofline of the residual kernel over all bundles
+    # roofline of the residual kernel over all bundles. Image term: each
+    # image once, capped at the four taps of every residual (the batch's
+    # bundles hold 500-50,000 points, so most of an image is never sampled
+    # and "every pixel once" would exceed what the pass has to read)
     V = R // s0.P
-    img_bytes = sum(sc.F for sc in scenes) * s0.H * s0.W * 2
+    img_bytes = min(sum(sc.F for sc in scenes) * s0.H * s0.W, 4 * R) * 2
     N = sum(sc.N for sc in scenes)
     alg_bytes = R * 28 + V * 4 + N * s0.P * 4 + N * 12 + img_bytes
     pass_ms = kms["pass"] / max(1, kcounts["pass"])
@@ -619,7 +660,8 @@ def run_batch(args):
                 "unit": "GB/s", "frac": achieved / hbm_peak,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
                 "traffic": None, "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": pass_ms,
-                "launches": int(kcounts["pass"])}
+                "launches": int(kcounts["pass"]),
+                "image_bytes": "each image once, capped at 4 taps x 2 B per residual"}
 
     # end to end through the C ABI with host images (pinned), one context
     e2e_t, h2d_b, d2h_b = [], 0, 0
@@ -629,8 +671,8 @@ def run_batch(args):
         t0 = time.perf_counter()
         eb = Batch([(host[j], sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis)
                     for j, sc in enumerate(scenes)], pattern=s0.pattern, huber_k=s0.huber_k)
-        eb.precompute_ic()
-        eb.iterate(iters, stats=False)
+        flagged(eb.precompute_ic, eb, set())
+        flagged(lambda: eb.iterate(iters, stats=False), eb, set())
         for j in range(B):
             eb.params(j)
         torch.cuda.synchronize()
@@ -663,8 +705,12 @@ def run_batch(args):
                                    "ms_per_step": total_loop / args.steps,
                                    "batch_over_loop": value / loop_value},
                "fc_batch": {"value": fc_value, "unit": "bundle-iterations/s",
-                            "ms_per_step": total_fc / args.steps, "final_rms": float(st_fc[-1, 1])},
-               "ic_final_rms": float(st_ic[-1, 1]), "ic_over_fc_iterations_per_s": value / fc_value,
+                            "ms_per_step": total_fc / args.steps,
+                            "final_rms": float(st_fc[-1, 1]) if st_fc is not None else None,
+                            "bundles_not_positive_definite": sorted(fc_failed)},
+               "ic_final_rms": float(st_ic[-1, 1]) if st_ic is not None else None,
+               "ic_bundles_not_positive_definite": sorted(ic_failed),
+               "ic_over_fc_iterations_per_s": value / fc_value,
                "batch_equals_loop": {"bundles_checked": len(range(0, B, max(1, B // 16))),
                                      "mismatches": mismatch}}
         print(json.dumps(out), flush=True)
@@ -677,6 +723,125 @@ def run_batch(args):
     return 0 if mismatch == 0 else 1
 
 
+# ----------------------------------------------------------------------------
+# learned workload: depth proposal trained on the method's own solutions
+# ----------------------------------------------------------------------------
+def learned_scene(i):
+    import synth
+    rng = __import__("numpy").random.default_rng(synth.BATCH_SEED + 7 + i)
+    cfg = synth.SceneConfig(f"learned{i}", 640, 480, 525.0, 5000, "helix", n_frames=30, spacing=1,
+                            sphere_r=float(rng.uniform(0.5, 2.0)), dtype="f16", allow_fewer_points=True)
+    return synth.make_scene(cfg, seed_offset=5000 + i)
+
+
+def _learned_scene_star(i):
+    sc = learned_scene(i)
+    sc.images_f32 = None
+    return sc
+
+
+def run_learned(args):
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import numpy as np
+    import torch
+
+    from paper_1704_06967_gb300 import Bundle
+    from paper_1704_06967_gb300 import build as pkg_build
+    from paper_1704_06967_gb300.learned import DepthMLP, training_pairs
+    from paper_1704_06967_gb300.pba import _scene_images
+
+    pkg_build.build()
+    ntr, nev, iters = args.train_bundles, args.eval_bundles, args.iters
+    t0 = time.perf_counter()
+    with cf.ProcessPoolExecutor(max_workers=max(1, min(8, (os.cpu_count() or 2) // 2)),
+                                mp_context=mp.get_context("spawn")) as ex:
+        scenes = list(ex.map(_learned_scene_star, range(ntr + nev)))
+    log(f"generated {len(scenes)} bundles in {time.perf_counter() - t0:.1f} s")
+    train, held = scenes[:ntr], scenes[ntr:]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    Xs, Ts = [], []
+    for sc in train:
+        tp = training_pairs(sc, iters=iters, stream=stream)
+        if tp is None:
+            continue
+        X, d, use = tp
+        Xs.append(X[torch.tensor(use, device="cuda")])
+        Ts.append(torch.tensor(d[use], dtype=torch.float32, device="cuda"))
+    X, T = torch.cat(Xs).contiguous(), torch.cat(Ts).contiguous()
+    net = DepthMLP(seed=0, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hist = net.train(X, T, epochs=args.epochs, batch=1024, lr=2e-3)
+    e1.record(stream)
+    e1.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    n_samples = (X.shape[0] // 1024) * 1024 * args.epochs
+
+    # inference throughput of the tensor-core kernel on the held-out features
+    feats = []
+    for sc in held:
+        b = Bundle(_scene_images(sc), sc.poses0, sc.intrinsics, sc.uv, np.ones(sc.N), sc.vis,
+                   pattern=sc.pattern, huber_k=sc.huber_k, stream=stream)
+        feats.append(b.depth_features())
+        b.close()
+    Fe = torch.cat(feats).contiguous()
+    for _ in range(3):
+        net.infer(Fe)
+    reps = 10
+    e0.record(stream)
+    for _ in range(reps):
+        net.infer(Fe)
+    e1.record(stream)
+    e1.synchronize()
+    infer_ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * Fe.shape[0] * (96 * 128 + 2 * 128 * 128 + 128)
+
+    # held-out bundles: constant inverse depth 1 against the proposal
+    rows = []
+    for sc in held:
+        out = {}
+        for mode in ("constant", "proposal"):
+            b = Bundle(_scene_images(sc), sc.poses0, sc.intrinsics, sc.uv, np.ones(sc.N), sc.vis,
+                       pattern=sc.pattern, huber_k=sc.huber_k, stream=stream)
+            if mode == "proposal":
+                net.propose(b)
+            b.precompute_ic()
+            st = b.iterate(iters)
+            conv = np.flatnonzero(st[:-1, 3] < 0.01)
+            _, d = b.params()
+            err = np.median(np.abs(d / sc.depths_gt - 1.0))
+            out[mode] = (float(st[-1, 0]), float(st[-1, 1]), int(conv[0]) + 1 if conv.size else iters,
+                         float(err))
+            b.close()
+        rows.append(out)
+    ec = np.array([r["constant"][0] for r in rows])
+    ep = np.array([r["proposal"][0] for r in rows])
+    res = {"metric": "learned inverse-depth proposal vs constant-depth initialisation: final Huber energy "
+                     f"after {iters} IC iterations on held-out bundles (ratio constant / proposal)",
+           "value": float(np.mean(ec / ep)), "unit": "energy ratio", "higher_is_better": True,
+           "n_gpus": 1, "dtype": "bf16 inference (FP32 accumulation), f32 training", "data": "synthetic",
+           "config": {"workload": f"learned: {WORKLOAD_TEXT['learned']}; {ntr} training and {nev} held-out "
+                                  f"bundles of up to 5,000 points, targets from {iters} IC iterations, "
+                                  f"{args.epochs} epochs of Adam (batch 1024, lr 2e-3)",
+                      "training_samples": int(X.shape[0])},
+           "held_out": {"energy_constant": ec.tolist(), "energy_proposal": ep.tolist(),
+                        "rms_constant": [r["constant"][1] for r in rows],
+                        "rms_proposal": [r["proposal"][1] for r in rows],
+                        "iterations_to_convergence_constant": [r["constant"][2] for r in rows],
+                        "iterations_to_convergence_proposal": [r["proposal"][2] for r in rows],
+                        "median_depth_error_constant": [r["constant"][3] for r in rows],
+                        "median_depth_error_proposal": [r["proposal"][3] for r in rows],
+                        "convergence_rule": "max pattern-centre displacement of a step < 0.01 px"},
+           "training": {"loss_per_epoch": hist, "ms": train_ms, "samples_per_s": n_samples / (train_ms / 1e3)},
+           "inference": {"points": int(Fe.shape[0]), "ms": infer_ms, "points_per_s": Fe.shape[0] / (infer_ms / 1e3),
+                         "tflops": flops / (infer_ms * 1e-3) / 1e12, "kernel": "mlp_infer_tc_kernel (tcgen05)"}}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     global SCENE
     args = parse()
@@ -685,6 +850,8 @@ def main():
         return run_reference(args)
     if SCENE == "batch256":
         return run_batch(args)
+    if SCENE == "learned":
+        return run_learned(args)
     return run_ours(args)
 
 

@@ -100,6 +100,14 @@ typedef struct {
                                 the cluster that factors the reduced camera system (4, 8,
                                 16). Results do not depend on the choice (every sum keeps
                                 its order); see pba_get_tuning. */
+    double damping;          /* Levenberg-Marquardt lambda >= 0; 0 = Gauss-Newton as in the
+                                paper (Sec. 3.5). lambda > 0 scales every diagonal entry of
+                                the frame blocks H_ff and of H_dd by 1 + lambda in the
+                                solve (IC: in the system fixed at p_0; FC: every
+                                iteration), replaces the scale-gauge prior (the damped
+                                system is definite) and keeps the exact gauge constraint
+                                t_a . Delta t_a = 0. pba_get_system returns the undamped
+                                blocks and the S that was factorised. */
 } pba_config;
 
 /* Statistics of one iteration (Sec. 4.1): Huber energy, RMS and count of the
@@ -160,7 +168,10 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes);
  * (Sec. 3.4), initial residual and Huber weight W_0; H = J^T W_0 J in frame,
  * frame-point and point blocks; the Schur complement S of the point block
  * with the scale-gauge prior, its LDL^T factor (double-float arithmetic,
- * ~48 bits, over the frames that have residuals) and inverse. */
+ * ~48 bits, over the frames that have residuals) and inverse.
+ * PBA_ERR_NOT_PD: the system of a bundle (pba_bundle_errors says which) had
+ * a non-positive pivot, replaced by 1; the precompute still counts as done,
+ * so the other bundles of a batch can iterate. */
 pba_status pba_precompute_ic(pba_ctx* ctx);
 
 /* Runs n_iters IC iterations (Sec. 3.5 steps 1-4 with the Sec. 3.6 update):
@@ -170,6 +181,17 @@ pba_status pba_precompute_ic(pba_ctx* ctx);
  * the parameters p_k (the last one has no update). PBA_ERR_STATE before
  * pba_precompute_ic. */
 pba_status pba_iterate(pba_ctx* ctx, int n_iters, pba_iter_stats* stats);
+
+/* A whole IC solve in one call: the precompute at the current parameters,
+ * then n_iters IC iterations (as pba_iterate) with re-anchoring: after every
+ * reanchor_every iterations (0: never) the parameters reached become the new
+ * p_0 and J, W_0, H, S and S^-1 are formed there again (the precompute of
+ * Sec. 3.5 at the new linearisation point; an option beyond the paper, for
+ * bundles where the Hessian fixed at the first p_0 stops describing the
+ * problem). With reanchor_every = 0 the result equals pba_precompute_ic +
+ * pba_iterate bit for bit. stats as for pba_iterate. Replayed from one CUDA
+ * graph per (n_iters, reanchor_every, timing mask) under cfg.use_graphs. */
+pba_status pba_solve_ic(pba_ctx* ctx, int n_iters, int reanchor_every, pba_iter_stats* stats);
 
 /* Runs n_iters FC iterations: Jacobians from the target-image gradients, the
  * Hessian blocks, the Schur complement and its LDL^T factor (double-float)

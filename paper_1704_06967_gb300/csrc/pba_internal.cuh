@@ -72,6 +72,7 @@ struct TileStats {
 struct DevProblem {
     int F, N, Npad, T, E, P, W, H, pitch, dtype;  // F, N, T, E: totals over the bundles
     float fx, fy, cx, cy, huber_k;
+    float damp1;                // 1 + Levenberg-Marquardt lambda (scales every H_dd that is solved with)
     const void* img;            // F frames, H rows of `pitch` elements
     const float* gx;            // FC gradient images (F*H*W), nullable for IC
     const float* gy;
@@ -197,81 +198,6 @@ __device__ __forceinline__ float huber_rho(float r, float k)
 {
     float a = fabsf(r);
     return a <= k ? 0.5f * r * r : k * a - 0.5f * k * k;
-}
-
-// ---------------------------------------------------------------------------
-// FP64 rotations: SO(3)/SE(3) exponential from Rodrigues' formula with the
-// Taylor series of its coefficients below theta = 1e-3.
-// ---------------------------------------------------------------------------
-__host__ __device__ inline void so3_exp_d(const double* w, double* R)
-{
-    double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-    double th = sqrt(th2);
-    double A, B;
-    if (th < 1e-3) {
-        A = 1.0 - th2 * (1.0 / 6.0) + th2 * th2 * (1.0 / 120.0);
-        B = 0.5 - th2 * (1.0 / 24.0) + th2 * th2 * (1.0 / 720.0);
-    } else {
-        A = sin(th) / th;
-        B = (1.0 - cos(th)) / th2;
-    }
-    // R = I + A K + B K^2, K = [w]x, K^2 = w w^T - th2 I
-    R[0] = 1.0 + B * (w[0] * w[0] - th2);
-    R[1] = -A * w[2] + B * w[0] * w[1];
-    R[2] = A * w[1] + B * w[0] * w[2];
-    R[3] = A * w[2] + B * w[1] * w[0];
-    R[4] = 1.0 + B * (w[1] * w[1] - th2);
-    R[5] = -A * w[0] + B * w[1] * w[2];
-    R[6] = -A * w[1] + B * w[2] * w[0];
-    R[7] = A * w[0] + B * w[2] * w[1];
-    R[8] = 1.0 + B * (w[2] * w[2] - th2);
-}
-
-// V = I + B K + C K^2 (left Jacobian of SO(3)), C = (th - sin th)/th^3
-__host__ __device__ inline void so3_left_jacobian_d(const double* w, double* V)
-{
-    double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-    double th = sqrt(th2);
-    double B, C;
-    if (th < 1e-3) {
-        B = 0.5 - th2 * (1.0 / 24.0) + th2 * th2 * (1.0 / 720.0);
-        C = 1.0 / 6.0 - th2 * (1.0 / 120.0) + th2 * th2 * (1.0 / 5040.0);
-    } else {
-        B = (1.0 - cos(th)) / th2;
-        C = (th - sin(th)) / (th2 * th);
-    }
-    V[0] = 1.0 + C * (w[0] * w[0] - th2);
-    V[1] = -B * w[2] + C * w[0] * w[1];
-    V[2] = B * w[1] + C * w[0] * w[2];
-    V[3] = B * w[2] + C * w[1] * w[0];
-    V[4] = 1.0 + C * (w[1] * w[1] - th2);
-    V[5] = -B * w[0] + C * w[1] * w[2];
-    V[6] = -B * w[1] + C * w[2] * w[0];
-    V[7] = B * w[0] + C * w[2] * w[1];
-    V[8] = 1.0 + C * (w[2] * w[2] - th2);
-}
-
-__host__ __device__ inline void mat3_mul_d(const double* A, const double* B, double* C)
-{
-    double T[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            T[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
-    for (int i = 0; i < 9; ++i) C[i] = T[i];
-}
-
-// FP32 pass constants of one frame from its FP64 pose: R (9), t (3) and the
-// pattern offsets of the P pattern pixels rotated into the frame,
-// delta_j = (o_jx / f_x) R[:,0] + (o_jy / f_y) R[:,1], so the 3-D point of
-// pattern pixel j is q_j = R x~_c + d t + delta_j.
-__host__ __device__ inline void frame_consts(const double* pose, const int* pat, int P, double fx,
-                                             double fy, float* out)
-{
-    for (int i = 0; i < 12; ++i) out[i] = (float)pose[i];
-    for (int j = 0; j < P; ++j) {
-        double ox = pat[2 * j] / fx, oy = pat[2 * j + 1] / fy;
-        for (int r = 0; r < 3; ++r) out[12 + 3 * j + r] = (float)(ox * pose[3 * r] + oy * pose[3 * r + 1]);
-    }
 }
 
 }  // namespace pba

@@ -147,7 +147,7 @@ depth_update_kernel(DevProblem pb, DepthState ds, const float2* __restrict__ dth
         double dd = 0.0;
         if (valid && hnn > 0.0f) {
             const double num = (double)gn + ((double)s + (double)c);
-            dd = kIcRule ? -num * ih : -num / (double)hnn;
+            dd = kIcRule ? -num * ih : -num / ((double)hnn * (double)pb.damp1);
             const double dn = kIcRule ? d * ((d0 - dd) * id0) : d + dd;
             if (isfinite(dn)) {
                 d = dn;
@@ -545,7 +545,7 @@ point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __rest
             }
         }
         const bool ok = valid && hnn > 0.0f;
-        const float sn = ok ? g / hnn : 0.0f;
+        const float sn = ok ? g / (hnn * pb.damp1) : 0.0f;
         if (warp == 0) {
             gn[n] = ok ? g : 0.0f;
             if (kFc) Hnn[n] = ok ? hnn : 0.0f;
@@ -741,6 +741,28 @@ cudaError_t launch_fc_point(const LaunchCtx& L, bool accum)
     auto k = accum ? point_kernel<true, true> : point_kernel<false, true>;
     return launch_pdl(k, L.pb.T, kTileWarps * 32, 0, L.stream, L.pb, L.it.gpart, L.Hfd_fc, L.ds_fc.Hnn,
                       L.ds_fc.gn, L.ent_part, 27, L.it.estats, L.it.ddsq_t, L.tstats);
+}
+
+// FP32 pass constants and previous R|t of frames [f0, f0 + nf) from their
+// FP64 poses (set-up and pba_set_params), one warp per frame: the same
+// arithmetic as the pose updates, so a state restored from its FP64
+// parameters continues exactly as the uninterrupted run.
+__global__ void frame_consts_kernel(SolveArgs a, int f0, int nf)
+{
+    __shared__ double sh[4][12];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, f = f0 + blockIdx.x * 4 + w;
+    if (f >= f0 + nf) return;
+    double* p = sh[w];
+    if (lane < 12) p[lane] = a.poses64[12 * f + lane];
+    __syncwarp();
+    write_frame_lanes(a, f, p, p, p + 9, lane);
+}
+
+cudaError_t launch_frame_consts(const SolveArgs& a, int f0, int nf, cudaStream_t st)
+{
+    if (nf <= 0) return cudaSuccess;
+    frame_consts_kernel<<<(nf + 3) / 4, 128, 0, st>>>(a, f0, nf);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ic_solve(const SolveArgs& a, const dfloat* Sinv, const double* y, cudaStream_t st)

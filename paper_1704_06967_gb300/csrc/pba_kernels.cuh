@@ -130,6 +130,8 @@ struct SolveArgs {
 // depth back-substitution (when apply) of the last update and, in extra
 // CTAs, every frame's pose update with it (a.active / tanchor unused)
 cudaError_t launch_depth_update(const LaunchCtx& L, const SolveArgs& a, bool ic_rule, int apply);
+// FP32 constants and previous R|t of frames [f0, f0 + nf) from a.poses64
+cudaError_t launch_frame_consts(const SolveArgs& a, int f0, int nf, cudaStream_t st);
 cudaError_t launch_ic_point(const LaunchCtx& L, bool accum);
 cudaError_t launch_fc_point(const LaunchCtx& L, bool accum);
 // Dtheta = -S^-1 y (per bundle the compact S^-1 at so, y per global frame as
@@ -160,7 +162,7 @@ cudaError_t launch_schur_sparse(const DevProblem& pb, const float* Hfd, const fl
 // or -1, cmap[F_b] = their number; the factorisation's working matrix; with
 // rhs, one extra row b = -y taken from rhs[f * rhs_stride + rhs_off + a])
 cudaError_t launch_assemble_S(const BundleSet& bs, const double* Hff, int hff_stride, const double* Soff,
-                              const double* anchor_t, double gauge_w, double* S, int* active,
+                              const double* anchor_t, double gauge_w, double damping, double* S, int* active,
                               cudaStream_t st, dfloat* S2 = nullptr, int* cmap = nullptr,
                               const double* rhs = nullptr, int rhs_stride = 0, int rhs_off = 0);
 // double-float LDL^T (pba_chol.cu), one thread-block cluster per bundle:

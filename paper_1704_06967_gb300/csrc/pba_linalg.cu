@@ -15,6 +15,9 @@ namespace pba {
 // trace) get an identity block; mu = mean diagonal over the active frames;
 // the prior gauge_w * mu * that that^T goes on the translation block of the
 // first active frame (that = unit translation of that frame in anchor_t).
+// With Levenberg-Marquardt damping lambda > 0 the diagonal entries of H_ff
+// are scaled by 1 + lambda (S_off already holds the damped H_dd) and the
+// prior is left out: the damped system is definite without it.
 // H_ff comes as 21 upper-triangle values per frame at Hff[f*stride].
 // active[f] (f >= 1) receives the frame flags, active[0] the anchor frame;
 // cmap[f] the compact index of an active frame (-1 otherwise) and cmap[F]
@@ -37,7 +40,7 @@ constexpr int kAssembleThreads = 256;
 // Bundle blockIdx.y of bs, gridDim.x CTAs per bundle.
 __global__ void __launch_bounds__(kAssembleThreads)
 assemble_S_kernel(BundleSet bs, const double* Hff, int stride, const double* Soff,
-                  const double* anchor_t, double gauge_w, double* S, int* active, dfloat* S2,
+                  const double* anchor_t, double gauge_w, double damping, double* S, int* active, dfloat* S2,
                   int* cmap, const double* rhs, int rhs_stride, int rhs_off)
 {
     __shared__ int s_act[1024];
@@ -57,6 +60,7 @@ assemble_S_kernel(BundleSet bs, const double* Hff, int stride, const double* Sof
     if (cmap) cmap += bd.co;
     if (rhs) rhs += (size_t)bd.fo * rhs_stride;
     const int n6 = 6 * (F - 1), tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double ld = 1.0 + damping;  // Levenberg-Marquardt: diagonal entries x (1 + lambda)
     for (int f = 1 + tid; f < F; f += blockDim.x) {
         const double* h = Hff + (size_t)f * stride;
         double tr = 0.0;
@@ -67,7 +71,8 @@ assemble_S_kernel(BundleSet bs, const double* Hff, int stride, const double* Sof
     double part = 0.0;
     for (int i = tid; i < n6; i += blockDim.x) {
         const int f = i / 6 + 1;
-        if (s_act[f]) part += Hff[(size_t)f * stride + upper_index(i % 6, i % 6)] - Soff[(size_t)i * n6 + i];
+        if (s_act[f])
+            part += Hff[(size_t)f * stride + upper_index(i % 6, i % 6)] * ld - Soff[(size_t)i * n6 + i];
     }
     part = warp_sum1d(part);
     if (lane == 0) s_red[warp] = part;
@@ -116,9 +121,10 @@ assemble_S_kernel(BundleSet bs, const double* Hff, int stride, const double* Sof
         } else {
             v = -Soff[idx];
             if (fi == fj) {
-                v += Hff[(size_t)fi * stride + upper_index(i % 6, j % 6)];
+                v += Hff[(size_t)fi * stride + upper_index(i % 6, j % 6)] * (i == j ? ld : 1.0);
                 const int a = i % 6, b = j % 6;
-                if (fi == anchor && a < 3 && b < 3) v += s_mu * (th[a] * th[b]);
+                // the damped system is definite without the gauge prior
+                if (fi == anchor && a < 3 && b < 3 && damping == 0.0) v += s_mu * (th[a] * th[b]);
             }
         }
         S[idx] = v;
@@ -141,7 +147,7 @@ assemble_S_kernel(BundleSet bs, const double* Hff, int stride, const double* Sof
 }
 
 cudaError_t launch_assemble_S(const BundleSet& bs, const double* Hff, int hff_stride, const double* Soff,
-                              const double* anchor_t, double gauge_w, double* S, int* active,
+                              const double* anchor_t, double gauge_w, double damping, double* S, int* active,
                               cudaStream_t st, dfloat* S2, int* cmap, const double* rhs,
                               int rhs_stride, int rhs_off)
 {
@@ -154,8 +160,8 @@ cudaError_t launch_assemble_S(const BundleSet& bs, const double* Hff, int hff_st
     const int blocks =
         std::max(1, std::min(std::min(148, per_bundle), (n6 * n6 + kAssembleThreads - 1) / kAssembleThreads));
     assemble_S_kernel<<<dim3(blocks, bs.B), kAssembleThreads, 0, st>>>(bs, Hff, hff_stride, Soff, anchor_t,
-                                                                       gauge_w, S, active, S2, cmap, rhs,
-                                                                       rhs_stride, rhs_off);
+                                                                       gauge_w, damping, S, active, S2, cmap,
+                                                                       rhs, rhs_stride, rhs_off);
     return cudaGetLastError();
 }
 

@@ -148,7 +148,7 @@ extern "C" pba_status pba_reduced_system_noalloc(int n_frames, int n_points, con
     one.B = 1;
     one.one.F = F;
     one.n6max = 6 * (F - 1);
-    if (launch_assemble_S(one, hff21, 21, soff, poses, gauge_anchor_w == 0.0 ? 1.0 : gauge_anchor_w,
+    if (launch_assemble_S(one, hff21, 21, soff, poses, gauge_anchor_w == 0.0 ? 1.0 : gauge_anchor_w, 0.0,
                           S, active, st) != cudaSuccess)
         return PBA_ERR_CUDA;
     return PBA_OK;

@@ -198,7 +198,7 @@ ic_hdd_kernel(DevProblem pb, const float* __restrict__ hpart, const double* __re
     }
     const bool ok = valid && tot > 0.0f;
     ic.Hnn[n] = valid ? tot : 0.0f;
-    ic.inv_hnn[n] = ok ? 1.0 / (double)tot : 0.0;
+    ic.inv_hnn[n] = ok ? 1.0 / ((double)tot * (double)pb.damp1) : 0.0;
     ic.inv_d0[n] = 1.0 / d0;
 }
 

@@ -51,8 +51,8 @@ struct GraphRec {
 };
 
 // graph key: (kind, iterations, timing mask)
-enum { G_ITERATE = 0, G_FC = 1, G_PRECOMPUTE = 2 };
-using GraphKey = std::tuple<int, int, int>;
+enum { G_ITERATE = 0, G_FC = 1, G_PRECOMPUTE = 2, G_SOLVE = 3 };
+using GraphKey = std::tuple<int, int, int>;  // (kind, iterations [+ re-anchoring period << 16], timing)
 
 }  // namespace
 
@@ -512,22 +512,15 @@ pba_status ensure_structure(pba_ctx* ctx)
     return PBA_OK;
 }
 
+SolveArgs make_solve(pba_ctx* c);
+
 // Uploads the parameters of bundle b (poses F_b*12, depths in the caller's
-// point order, nullable) with their FP32 pass constants.
+// point order, nullable); the FP32 pass constants are formed on the device.
 pba_status upload_params(pba_ctx* ctx, int bi, const double* poses, const double* depth)
 {
     const BundleIn& b = ctx->bun[bi];
-    const int F = b.F, fo = b.fo;
-    std::vector<float> fcs((size_t)F * kFrameConst, 0.0f), prev((size_t)F * 12, 0.0f);
-    const int P = (int)ctx->pattern.size() / 2;
-    for (int f = 0; f < F; ++f) {
-        frame_consts(poses + 12 * f, ctx->pattern.data(), P, ctx->K[0], ctx->K[1],
-                     fcs.data() + (size_t)f * kFrameConst);
-        for (int i = 0; i < 12; ++i) prev[12 * f + i] = (float)poses[12 * f + i];
-    }
-    CK(h2d(ctx, ctx->d.poses64 + (size_t)12 * fo, poses, sizeof(double) * 12 * F));
-    CK(h2d(ctx, ctx->d.fc + (size_t)kFrameConst * fo, fcs.data(), sizeof(float) * fcs.size()));
-    CK(h2d(ctx, ctx->d.fc_prev + (size_t)12 * fo, prev.data(), sizeof(float) * prev.size()));
+    CK(h2d(ctx, ctx->d.poses64 + (size_t)12 * b.fo, poses, sizeof(double) * 12 * b.F));
+    CK(launch_frame_consts(make_solve(ctx), b.fo, b.F, ctx->stream));
     if (depth) {
         std::vector<double> ds(b.perm.size(), 1.0);
         for (size_t i = 0; i < ds.size(); ++i)
@@ -584,6 +577,7 @@ LaunchCtx make_launch(pba_ctx* c)
     pb.cx = (float)c->K[2];
     pb.cy = (float)c->K[3];
     pb.huber_k = (float)c->cfg.huber_k;
+    pb.damp1 = (float)(1.0 + c->cfg.damping);
     pb.img = own_images(c) ? c->d.img : c->bun[0].images;
     pb.gx = c->d.gx;
     pb.gy = c->d.gy;
@@ -785,7 +779,8 @@ pba_status pba_create(const pba_config* cfg, pba_ctx** out)
     if (!cfg || !(cfg->huber_k > 0.0) || cfg->pattern_size < 1 ||
         cfg->pattern_size > PBA_MAX_PATTERN || !cfg->pattern || cfg->n_bundles < 0 ||
         cfg->n_bundles > PBA_MAX_BUNDLES ||
-        cfg->gauge_anchor_w < 0.0 || cfg->max_stats_iters < 0)
+        cfg->gauge_anchor_w < 0.0 || cfg->max_stats_iters < 0 || !(cfg->damping >= 0.0) ||
+        !(cfg->damping < 1e6))
         return PBA_ERR_ARG;
     for (int j = 0; j < 2 * cfg->pattern_size; ++j)
         if (cfg->pattern[j] < -32 || cfg->pattern[j] > 32) return PBA_ERR_ARG;
@@ -988,6 +983,8 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     return PBA_OK;
 }
 
+pba_status precompute_core(pba_ctx* ctx, const LaunchCtx& L, const BundleSet& bs);
+
 // The IC precompute's launches (Sec. 3.5): p_0 from the current parameters,
 // J, W_0 and the H blocks per entry, the frame sums, the Schur complement, S
 // with the gauge prior, its LDL^T factor and S^-1.
@@ -1002,12 +999,19 @@ pba_status precompute_body(pba_ctx* ctx)
     CK(cudaMemcpyAsync(ctx->d.d0_64, ctx->d.d64, sizeof(double) * ctx->Npad, cudaMemcpyDeviceToDevice,
                        ctx->stream));
     LAUNCH(TS_PRE, launch_depth_update(L, make_solve(ctx), true, 0));  // FP32 depths of p_0
+    return precompute_core(ctx, L, bs);
+}
+
+// The precompute after the FP32 depths of the new p_0 are in place.
+pba_status precompute_core(pba_ctx* ctx, const LaunchCtx& L, const BundleSet& bs)
+{
     LAUNCH(TS_PRE, launch_ic_precompute(L));
     LAUNCH(TS_PRE, launch_frame_reduce(L, 0, 21, ctx->d.red_ic, -1, -1, true));
     LAUNCHN(TS_PRE, launch_schur_sparse(L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, schur_lists(ctx), ctx->d.schur_part,
                                         ctx->d.Soff, ctx->stream, &nl));
     LAUNCH(TS_PRE, launch_assemble_S(bs, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64, ctx->cfg.gauge_anchor_w,
-                                     ctx->d.S_ic, ctx->d.active_ic, ctx->stream, ctx->d.A2, ctx->d.cmap_ic));
+                                     ctx->cfg.damping, ctx->d.S_ic, ctx->d.active_ic, ctx->stream, ctx->d.A2,
+                                     ctx->d.cmap_ic));
     LAUNCH(TS_PRE, launch_ldl(bs, ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv, ctx->d.cmap_ic, 0,
                               ctx->d.err, ctx->stream, ctx->ldl_cluster));
     LAUNCH(TS_PRE, launch_ldl_inverse(bs, ctx->d.L2, ctx->d.Linv, ctx->d.rpiv, ctx->d.cmap_ic, ctx->d.Sinv2,
@@ -1055,8 +1059,8 @@ pba_status autotune(pba_ctx* ctx)
         float ms = 0.0f;
         auto once = [&]() -> cudaError_t {
             cudaError_t e = launch_assemble_S(bs, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64,
-                                              ctx->cfg.gauge_anchor_w, ctx->d.S_ic, ctx->d.active_ic, ctx->stream,
-                                              ctx->d.A2, ctx->d.cmap_ic);
+                                              ctx->cfg.gauge_anchor_w, ctx->cfg.damping, ctx->d.S_ic,
+                                              ctx->d.active_ic, ctx->stream, ctx->d.A2, ctx->d.cmap_ic);
             if (e != cudaSuccess) return e;
             return launch_ldl(bs, ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv, ctx->d.cmap_ic, 0,
                               ctx->d.err, ctx->stream, C);
@@ -1093,9 +1097,11 @@ pba_status pba_precompute_ic(pba_ctx* ctx)
                                 [&]() -> pba_status { return precompute_body(ctx); });
     if (s != PBA_OK) return s;
     s = check_device_error(ctx);
-    if (s != PBA_OK) return s;
-    ctx->ic_ready = true;
-    return PBA_OK;
+    // a system that is not positive definite is reported (per bundle); its
+    // non-positive pivots were replaced, so the other bundles of a batch can
+    // iterate (that one only at the caller's risk)
+    if (s == PBA_OK || s == PBA_ERR_NOT_PD) ctx->ic_ready = true;
+    return s;
 }
 
 pba_status pba_iterate(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
@@ -1128,6 +1134,56 @@ pba_status pba_iterate(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     return copy_stats(ctx, n_iters, stats);
 }
 
+pba_status pba_solve_ic(pba_ctx* ctx, int n_iters, int reanchor_every, pba_iter_stats* stats)
+{
+    if (!ctx) return PBA_ERR_ARG;
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    if (n_iters < 0 || n_iters > ctx->cfg.max_stats_iters || n_iters >= (1 << 16))
+        return fail(ctx, PBA_ERR_ARG, "n_iters must be in [0, %d]", ctx->cfg.max_stats_iters);
+    if (reanchor_every < 0 || reanchor_every >= (1 << 14))
+        return fail(ctx, PBA_ERR_ARG, "reanchor_every must be in [0, 16383]");
+    const int m = reanchor_every > 0 && reanchor_every < n_iters ? reanchor_every : 0;
+    LaunchCtx L = make_launch(ctx);
+    const BundleSet bs = bundle_set(ctx);
+    SolveArgs sa = make_solve(ctx);
+    sa.active = ctx->d.active_ic;
+    sa.tanchor = ctx->d.poses0_64;
+    sa.cmap = ctx->d.cmap_ic;
+    pba_status s = run_enqueued(ctx, GraphKey{G_SOLVE, n_iters | (m << 16), ctx->timing}, [&]() -> pba_status {
+        pba_status q = precompute_body(ctx);
+        if (q != PBA_OK) return q;
+        for (int k = 0; k < n_iters; ++k) {
+            const bool reanchor = m > 0 && k > 0 && k % m == 0;
+            // the step of iteration k - 1 is applied here; at a re-anchoring
+            // the parameters it produces become the new p_0 and J, H, S and
+            // S^-1 are formed there before the iteration's residual pass
+            LAUNCH(TS_POINT, launch_depth_update(L, sa, true, k > 0));
+            if (reanchor) {
+                CK(cudaMemcpyAsync(ctx->d.poses0_64, ctx->d.poses64, sizeof(double) * 12 * ctx->F,
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+                CK(cudaMemcpyAsync(ctx->d.d0_64, ctx->d.d64, sizeof(double) * ctx->Npad, cudaMemcpyDeviceToDevice,
+                                   ctx->stream));
+                q = precompute_core(ctx, L, bs);
+                if (q != PBA_OK) return q;
+            }
+            LAUNCH(TS_PASS, launch_ic_residual(L, true, k > 0));
+            LAUNCH(TS_POINT, launch_ic_point(L, true));
+            LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 6, ctx->d.red_y, k, k - 1, true, 6));
+            LAUNCH(TS_SOLVE, launch_ic_solve(sa, ctx->d.Sinv2, ctx->d.red_y, ctx->stream));
+        }
+        LAUNCH(TS_EVAL, launch_depth_update(L, sa, true, n_iters > 0));
+        LAUNCH(TS_EVAL, launch_ic_residual(L, false, n_iters > 0));
+        LAUNCH(TS_EVAL, launch_ic_point(L, false));
+        LAUNCH(TS_EVAL, launch_frame_reduce(L, 0, 0, nullptr, n_iters, n_iters - 1, false));
+        return PBA_OK;
+    });
+    if (s != PBA_OK) return s;
+    ctx->last_fc = 0;
+    s = copy_stats(ctx, n_iters, stats);
+    if (s == PBA_OK || s == PBA_ERR_NOT_PD) ctx->ic_ready = true;
+    return s;
+}
+
 pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
 {
     if (!ctx) return PBA_ERR_ARG;
@@ -1149,7 +1205,8 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
             LAUNCHN(TS_SCHUR, launch_schur_sparse(L.pb, ctx->d.Hfd_fc, ctx->d.Hnn_fc, schur_lists(ctx),
                                                   ctx->d.schur_part, ctx->d.Soff, ctx->stream, &nl));
             LAUNCH(TS_SCHUR, launch_assemble_S(bs, ctx->d.red_y, 27, ctx->d.Soff, ctx->d.poses64,
-                                               ctx->cfg.gauge_anchor_w, ctx->d.S_fc, ctx->d.active_fc,
+                                               ctx->cfg.gauge_anchor_w, ctx->cfg.damping, ctx->d.S_fc,
+                                               ctx->d.active_fc,
                                                ctx->stream, ctx->d.A2, ctx->d.cmap_fc, ctx->d.red_y, 27, 21));
             LAUNCH(TS_SOLVE, launch_ldl(bs, ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv,
                                         ctx->d.cmap_fc, 1, ctx->d.err, ctx->stream, ctx->ldl_cluster));

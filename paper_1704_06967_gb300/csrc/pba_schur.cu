@@ -127,7 +127,7 @@ schur_chunk_kernel(DevProblem pb, const float* Hfd, const float* Hnn, const int*
         const int n = A.tile * kTile + lane;
         const float h = Hnn[n];
         if (!(h > 0.0f)) continue;
-        const float ih = 1.0f / h;
+        const float ih = 1.0f / (h * pb.damp1);
         const int na = __popc(A.mask), ra = __popc(A.mask & ((1u << lane) - 1u));
         const int nb = __popc(B.mask), rb = __popc(B.mask & ((1u << lane) - 1u));
         const float* pa = Hfd + (size_t)A.pair_off * 6 + ra;

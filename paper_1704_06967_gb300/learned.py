@@ -125,13 +125,18 @@ class DepthMLP:
 
 def training_pairs(scene, iters: int = 20, stream=None, **kw):
     """(features at p_0, converged inverse depths, mask of usable points) of
-    one generated bundle: the bundle is solved with IC from its own
-    initialisation; points that no target frame observes are not usable."""
+    one generated bundle, or None when the method cannot solve it: the
+    bundle is solved with IC from its own initialisation; points that no
+    target frame observes are not usable."""
     from .pba import Bundle
     b = Bundle.from_scene(scene, stream=stream, **kw)
     X = b.depth_features()
-    b.precompute_ic()
-    b.iterate(iters, stats=False)
+    try:
+        b.precompute_ic()
+        b.iterate(iters, stats=False)
+    except PbaError:
+        b.close()
+        return None  # a bundle the method cannot solve gives no targets
     _, d = b.params()
     b.close()
     usable = (scene.vis[:, 1:].sum(1) > 0) & np.isfinite(d) & (d > 0)

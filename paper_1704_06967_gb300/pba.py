@@ -39,7 +39,7 @@ class Config(ctypes.Structure):
                 ("pattern", ctypes.POINTER(ctypes.c_int32)), ("gauge_anchor_w", ctypes.c_double),
                 ("conv_px", ctypes.c_double), ("n_bundles", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("use_graphs", ctypes.c_int),
-                ("max_stats_iters", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("max_stats_iters", ctypes.c_int), ("autotune", ctypes.c_int), ("damping", ctypes.c_double)]
 
 
 class IterStats(ctypes.Structure):
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pba_precompute_ic": ([vp], i),
         "pba_iterate": ([vp, i, vp], i),
         "pba_solve_fc": ([vp, i, vp], i),
+        "pba_solve_ic": ([vp, i, i, vp], i),
         "pba_get_params": ([vp, i, vp, vp], i),
         "pba_set_params": ([vp, i, vp, vp], i),
         "pba_get_last_update": ([vp, i, vp, vp], i),
@@ -130,7 +131,7 @@ class Batch:
     """
 
     def __init__(self, items, *, pattern, huber_k, stream=None, gauge_anchor_w=1.0, max_stats_iters=256,
-                 use_graphs=False, autotune=False):
+                 use_graphs=False, autotune=False, damping=0.0):
         import torch
         self.torch = torch
         lib = load()
@@ -145,7 +146,7 @@ class Batch:
         cfg = Config(float(huber_k), pat.shape[0],
                      pat.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), float(gauge_anchor_w),
                      0.0, self.B, ctypes.c_void_p(stream.cuda_stream), int(bool(use_graphs)),
-                     int(max_stats_iters), int(bool(autotune)))
+                     int(max_stats_iters), int(bool(autotune)), float(damping))
         h = ctypes.c_void_p()
         self.h = None
         self._check(lib.pba_create(ctypes.byref(cfg), ctypes.byref(h)), None)
@@ -231,6 +232,12 @@ class Batch:
         """IC iterations; returns stats [n+1, 6] (energy, rms, n_valid,
         max_disp_px, dtheta_norm, dd_norm) or None."""
         return self._stats(self.lib.pba_iterate, n_iters, stats)
+
+    def solve_ic(self, n_iters, reanchor_every=0, stats=True):
+        """Precompute + n_iters IC iterations, re-anchoring p_0 every
+        reanchor_every iterations (0: never), in one library call."""
+        fn = lambda h, n, p: self.lib.pba_solve_ic(h, n, int(reanchor_every), p)
+        return self._stats(fn, n_iters, stats)
 
     def solve_fc(self, n_iters, stats=True):
         return self._stats(self.lib.pba_solve_fc, n_iters, stats)
