@@ -14,14 +14,18 @@ Features of point n (pixel (u, v) in the reference frame 0), 96 values:
     (row-major in dy, then dx; coordinates clamped into the image),
     normalised by its own mean mu and population standard deviation sigma:
     (I - mu) / (sigma + EPS);
-  * 16 samples along the epipolar line in each of two target frames: the
-    first two frames g >= 1 (in frame order) that observe the point (one
-    frame: used twice; none: zeros). For k = 0 .. 15 the inverse depth
-    d_k = D_LO + k (D_HI - D_LO) / 15 places the point at
-    q = R_g x~ + d_k t_g, u_k = f_x q_x / q_z + c_x (likewise v_k), and the
-    sample is I_g(u_k, v_k) (bilinear, pixel centres on integers) normalised
-    as the patch; a projection behind the camera (q_z <= 0) or whose 2 x 2
-    footprint leaves the image gives 0.
+  * a 16-bin matching cost along the epipolar line in each of two target
+    frames: the first two frames g >= 1 (in frame order) that observe the
+    point (one frame: used twice; none: NO_DATA everywhere). The inverse
+    depths d_m = D_LO + (m + 1/2) (D_HI - D_LO) / 256, m = 0 .. 255, place
+    every pattern pixel x_j of the point (the method's P-pixel pattern) at
+    q = R_g x~_j + d_m t_g; the cost of d_m is the mean over j of
+    (I_g(pi(q)) normalised as the patch - the template's normalised value
+    at x_j)^2, NO_DATA when a projection is behind the camera or its 2 x 2
+    footprint leaves the image; bin k holds the least cost of d_m,
+    m = 16 k .. 16 k + 15. (Sixteen raw intensities at sixteen depths would
+    sample the line tens of pixels apart, far coarser than the texture: the
+    least cost per bin keeps the match wherever it falls in the bin.)
 Network: x (96) -> 128 -> 128 -> 128 -> 1, GELU (the exact form
 x Phi(x)) after each hidden layer; y = w4 . h3 + b4 is the inverse depth.
 Loss of a batch: mean of (y - target)^2 / 2. Adam (Kingma and Ba 2015).
@@ -34,10 +38,12 @@ import numpy as np
 
 PATCH = 8
 PATCH_LO = -3
-N_SAMPLES = 16
+N_SAMPLES = 16          # bins per frame
+N_SUB = 16              # inverse depths per bin
 N_FRAMES = 2
 D_LO, D_HI = 0.5, 2.0
 EPS = 1.0 / 255.0
+NO_DATA = 4.0
 N_IN = PATCH * PATCH + N_FRAMES * N_SAMPLES  # 96
 N_HID = 128
 
@@ -79,25 +85,18 @@ def init_params(seed: int = 0) -> dict:
 # ----------------------------------------------------------------------------
 # features
 # ----------------------------------------------------------------------------
-def _bilinear(img: np.ndarray, u: float, v: float):
-    H, W = img.shape
-    x0, y0 = math.floor(u), math.floor(v)
-    if x0 < 0 or y0 < 0 or x0 + 1 > W - 1 or y0 + 1 > H - 1:
-        return None
-    a, b = u - x0, v - y0
-    top = (1 - a) * img[y0, x0] + a * img[y0, x0 + 1]
-    bot = (1 - a) * img[y0 + 1, x0] + a * img[y0 + 1, x0 + 1]
-    return (1 - b) * top + b * bot
-
-
-def features(images: np.ndarray, K, poses: np.ndarray, uv: np.ndarray, vis: np.ndarray) -> np.ndarray:
+def features(images: np.ndarray, K, poses: np.ndarray, uv: np.ndarray, vis: np.ndarray,
+             pattern: np.ndarray) -> np.ndarray:
     """images [F, H, W] (the values the solver reads), K = (fx, fy, cx, cy),
-    poses [F, 12] row-major [R | t], uv [N, 2], vis [N, F] -> [N, 96]."""
+    poses [F, 12] row-major [R | t], uv [N, 2], vis [N, F], pattern [P, 2]
+    -> [N, 96]."""
     images = np.asarray(images, dtype=np.float64)
     F, H, W = images.shape
     fx, fy, cx, cy = (float(k) for k in K)
     N = uv.shape[0]
     out = np.zeros((N, N_IN))
+    nd = N_SAMPLES * N_SUB
+    dm = D_LO + (np.arange(nd) + 0.5) * (D_HI - D_LO) / nd
     for n in range(N):
         u, v = int(uv[n, 0]), int(uv[n, 1])
         patch = np.empty((PATCH, PATCH))
@@ -112,21 +111,41 @@ def features(images: np.ndarray, K, poses: np.ndarray, uv: np.ndarray, vis: np.n
         out[n, :PATCH * PATCH] = ((patch - mu) * scale).ravel()
         frames = [g for g in range(1, F) if vis[n, g]][:N_FRAMES]
         if not frames:
+            out[n, PATCH * PATCH:] = NO_DATA
             continue
         if len(frames) == 1:
             frames = frames * 2
-        xt = np.array([(u - cx) / fx, (v - cy) / fy, 1.0])
+        tmpl = np.array([(images[0, v + oy, u + ox] - mu) * scale for ox, oy in pattern])
+        # normalised coordinates of the pattern pixels, [P, 3]
+        xt = np.stack([(u + pattern[:, 0] - cx) / fx, (v + pattern[:, 1] - cy) / fy,
+                       np.ones(len(pattern))], axis=1)
         for s, g in enumerate(frames):
             R = poses[g, :9].reshape(3, 3)
             t = poses[g, 9:]
-            for k in range(N_SAMPLES):
-                d = D_LO + k * (D_HI - D_LO) / (N_SAMPLES - 1)
-                q = R @ xt + d * t
-                val = None
-                if q[2] > 0:
-                    val = _bilinear(images[g], fx * q[0] / q[2] + cx, fy * q[1] / q[2] + cy)
-                out[n, PATCH * PATCH + s * N_SAMPLES + k] = 0.0 if val is None else (val - mu) * scale
+            q = (xt @ R.T)[None, :, :] + dm[:, None, None] * t[None, None, :]  # [nd, P, 3]
+            front = q[..., 2] > 0
+            qz = np.where(front, q[..., 2], 1.0)
+            val, ok = _bilinear_all(images[g], fx * q[..., 0] / qz + cx, fy * q[..., 1] / qz + cy)
+            ok &= front
+            c = np.where(ok, ((val - mu) * scale - tmpl[None, :]) ** 2, 0.0).mean(axis=1)
+            cost = np.where(ok.all(axis=1), c, NO_DATA)
+            out[n, PATCH * PATCH + s * N_SAMPLES:PATCH * PATCH + (s + 1) * N_SAMPLES] = \
+                cost.reshape(N_SAMPLES, N_SUB).min(1)
     return out
+
+
+def _bilinear_all(img: np.ndarray, u: np.ndarray, v: np.ndarray):
+    """Bilinear samples at arrays of positions and whether each 2 x 2
+    footprint lies inside the image (out-of-image samples are 0)."""
+    H, W = img.shape
+    x0, y0 = np.floor(u), np.floor(v)
+    ok = (x0 >= 0) & (y0 >= 0) & (x0 + 1 <= W - 1) & (y0 + 1 <= H - 1)
+    xi = np.where(ok, x0, 0).astype(np.int64)
+    yi = np.where(ok, y0, 0).astype(np.int64)
+    a, b = u - x0, v - y0
+    top = (1 - a) * img[yi, xi] + a * img[yi, np.minimum(xi + 1, W - 1)]
+    bot = (1 - a) * img[np.minimum(yi + 1, H - 1), xi] + a * img[np.minimum(yi + 1, H - 1), np.minimum(xi + 1, W - 1)]
+    return np.where(ok, (1 - b) * top + b * bot, 0.0), ok
 
 
 # ----------------------------------------------------------------------------

@@ -103,13 +103,14 @@ def _ramp(F, H, W, a, b, c):
 
 
 def test_features_of_linear_ramps():
-    # bilinear interpolation is exact on I = a x + b y + c, the patch
-    # statistics have closed forms (offsets -3..4: mean 0.5, variance 5.25),
-    # and with R = I, t = (tx, 0, 0) the sample at inverse depth d lands at
-    # u + fx d tx on the reference row v
+    # bilinear interpolation is exact on I = a x + b y + c_f; the patch
+    # statistics have closed forms (offsets -3..4: mean 0.5, variance 5.25);
+    # with R = I and t = (tx, 0, 0) every pattern pixel moves by fx d tx
+    # along its row, so with a common slope the matching cost of inverse
+    # depth d is ((a fx tx d + c_g - c_0) / (sigma + eps))^2 for every pixel
     F, H, W = 4, 60, 160
-    a, b, c = [0.002, 0.001, 0.003, 0.0015], [0.001, 0.0, 0.002, 0.0005], [0.1, 0.2, 0.3, 0.4]
-    imgs = _ramp(F, H, W, a, b, c)
+    a, b, c = 0.002, 0.001, [0.1, 0.2, 0.3, 0.4]
+    imgs = _ramp(F, H, W, [a] * F, [b] * F, c)
     K = (100.0, 100.0, 79.5, 29.5)
     poses = np.zeros((F, 12))
     poses[:, [0, 4, 8]] = 1.0
@@ -118,29 +119,55 @@ def test_features_of_linear_ramps():
     vis = np.ones((2, F), np.uint8)
     vis[:, 0] = 0
     vis[0, 1] = 0  # point 0: frames 2 and 3; point 1: frames 1 and 2
-    X = mlp.features(imgs, K, poses, uv, vis)
-    sig = math.sqrt(5.25 * (a[0] ** 2 + b[0] ** 2))
+    pat = np.array([(-1, -1), (1, -1), (-1, 1), (1, 1), (-2, 0), (2, 0), (0, -2), (0, 2)], np.int32)
+    X = mlp.features(imgs, K, poses, uv, vis, pat)
+    sig = math.sqrt(5.25 * (a ** 2 + b ** 2))
+    s = 1.0 / (sig + mlp.EPS)
+    dm = 0.5 + (np.arange(256) + 0.5) * 1.5 / 256
     for n, frames in ((0, (2, 3)), (1, (1, 2))):
         u, v = uv[n]
-        mu = a[0] * (u + 0.5) + b[0] * (v + 0.5) + c[0]
-        s = 1.0 / (sig + mlp.EPS)
+        mu = a * (u + 0.5) + b * (v + 0.5) + c[0]
         for i in range(8):
             for j in range(8):
-                ref = (a[0] * (u - 3 + j) + b[0] * (v - 3 + i) + c[0] - mu) * s
+                ref = (a * (u - 3 + j) + b * (v - 3 + i) + c[0] - mu) * s
                 assert abs(X[n, 8 * i + j] - ref) < 1e-12
         for fi, g in enumerate(frames):
-            for k in range(16):
-                d = 0.5 + k * 0.1
-                uk = u + K[0] * d * poses[g, 9]
-                ref = (a[g] * uk + b[g] * v + c[g] - mu) * s if 0 <= uk <= W - 2 else 0.0
-                assert abs(X[n, 64 + 16 * fi + k] - ref) < 1e-12, (n, g, k)
+            cost = ((a * K[0] * poses[g, 9] * dm + c[g] - c[0]) * s) ** 2
+            ref = cost.reshape(16, 16).min(1)
+            assert np.abs(X[n, 64 + 16 * fi:64 + 16 * (fi + 1)] - ref).max() < 1e-9 * max(1.0, ref.max()), (n, g)
 
 
-def test_features_without_observations_are_patch_only():
+def test_matching_cost_is_zero_at_the_true_depth():
+    # a textured reference warped exactly by the pose and a constant inverse
+    # depth d*: the bin holding d* has (near) zero cost and is the least
+    rng = np.random.default_rng(8)
+    H, W = 80, 200
+    base = rng.uniform(0, 1, size=(H, W))
+    K = (100.0, 100.0, 99.5, 39.5)
+    dstar = 1.2
+    tx = 0.1
+    shift = K[0] * dstar * tx  # pixels; a pure x translation keeps rows
+    # frame 1 shows frame 0 moved by `shift` pixels: I_1(x + shift, y) = I_0(x, y)
+    x = np.arange(W)
+    img1 = np.stack([np.interp(x - shift, x, base[y]) for y in range(H)])
+    imgs = np.stack([base, img1, img1])
+    poses = np.zeros((3, 12))
+    poses[:, [0, 4, 8]] = 1.0
+    poses[1, 9] = poses[2, 9] = tx
+    pat = np.array([(-1, -1), (1, -1), (-1, 1), (1, 1), (-2, 0), (2, 0), (0, -2), (0, 2)], np.int32)
+    uv = np.array([[60, 40]], np.int32)
+    vis = np.array([[0, 1, 1]], np.uint8)
+    X = mlp.features(imgs, K, poses, uv, vis, pat)
+    k = int((dstar - 0.5) / (1.5 / 16))
+    bins = X[0, 64:80]
+    assert bins.argmin() == k and bins[k] < 1e-3
+
+
+def test_features_without_observations_have_no_matching_data():
     F, H, W = 3, 40, 40
     imgs = _ramp(F, H, W, [0.01] * F, [0.0] * F, [0.0] * F)
     poses = np.zeros((F, 12))
     poses[:, [0, 4, 8]] = 1.0
     X = mlp.features(imgs, (50.0, 50.0, 19.5, 19.5), poses, np.array([[20, 20]], np.int32),
-                     np.zeros((1, F), np.uint8))
-    assert not X[0, 64:].any() and X[0, :64].any()
+                     np.zeros((1, F), np.uint8), np.array([(-1, 0), (1, 0)], np.int32))
+    assert np.all(X[0, 64:] == mlp.NO_DATA) and X[0, :64].any()
