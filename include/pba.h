@@ -174,6 +174,24 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes);
  * so the other bundles of a batch can iterate. */
 pba_status pba_precompute_ic(pba_ctx* ctx);
 
+/* Sliding window over a bundle's frames (the dynamic Hessian the paper
+ * suggests for windows of keyframes, Sec. 4.2). in_window: host, F_b flags
+ * (frame 0 ignored: the reference is always in). Frames outside the window
+ * keep their images, poses and stored products, but none of their residuals
+ * enters any sum (IC, FC, statistics). After a change pba_iterate needs
+ * pba_update_ic (PBA_ERR_STATE otherwise); pba_solve_ic and pba_solve_fc
+ * work on the window as it is. All frames are in the window initially. */
+pba_status pba_set_window(pba_ctx* ctx, int bundle, const uint8_t* in_window);
+
+/* Brings the IC system up to date with the window without a full
+ * precompute: the Jacobian rows and H products of the entering frames are
+ * formed (anchored at their current poses; every point keeps its d_0),
+ * those of the frames already in are reused from the workspace, and H_dd,
+ * the frame blocks, S, its factor and S^-1 are formed again from the stored
+ * products. The result equals a full pba_precompute_ic whose p_0 holds the
+ * same anchors. Before any precompute it runs the full one. */
+pba_status pba_update_ic(pba_ctx* ctx);
+
 /* Runs n_iters IC iterations (Sec. 3.5 steps 1-4 with the Sec. 3.6 update):
  * Huber weights from the current residuals, g = J^T W r, Delta p = -H^-1 g by
  * the Schur complement, then R <- R R0^T exp(omega)^T R0, t <- t - R R0^T Dt,

@@ -14,14 +14,18 @@
  *             row-major in dy then dx (coordinates clamped into the image),
  *             as (I - mu) / (sigma + 1/255) with the patch's own mean mu and
  *             population standard deviation sigma;
- *   [64, 96)  16 samples along the epipolar line in each of two target
- *             frames: the first two frames (in frame order) that observe the
- *             point (one such frame: used twice; none: zeros). Sample k
- *             places the point at inverse depth d_k = 0.5 + 0.1 k with the
- *             frame's current pose, q = R x~ + d_k t, and reads the image
- *             bilinearly at (f_x q_x / q_z + c_x, f_y q_y / q_z + c_y),
- *             normalised as the patch; 0 when q_z <= 0 or the 2 x 2
- *             footprint leaves the image.
+ *   [64, 96)  16 matching costs along the epipolar line in each of two
+ *             target frames: the first two frames (in frame order) that
+ *             observe the point (one such frame: used twice; none: 4.0
+ *             everywhere). Inverse depths d_m = 0.5 + (m + 1/2) 1.5 / 256,
+ *             m = 0..255, place every pixel x_j of the point's P-pixel
+ *             pattern at q = R x~_j + d_m t with the frame's current pose;
+ *             the cost of d_m is the mean over j of (I(f_x q_x / q_z + c_x,
+ *             f_y q_y / q_z + c_y), bilinear, normalised as the patch, minus
+ *             the template's normalised value at x_j)^2, 4.0 when a
+ *             projection is behind the camera or its 2 x 2 footprint leaves
+ *             the image; value k of a frame is the least cost of
+ *             d_m, m = 16 k .. 16 k + 15.
  * Network: 96 -> 128 -> 128 -> 128 -> 1, GELU (x Phi(x)) after each hidden
  * layer, output = inverse depth. Parameters, PBA_MLP_NPARAMS FP32 values in
  * this order: W1 [128][96] (row = output unit), b1 [128], W2 [128][128],
@@ -85,8 +89,11 @@ pba_status pba_mlp_train_step(float* params, float* m, float* v, int step, float
 
 /* Proposes the inverse depths of `bundle` from its features at the current
  * poses and replaces the bundle's current inverse depths with them (clamped
- * into [0.05, 20]); call pba_precompute_ic afterwards. scratch: N_b * 97
- * floats. Synchronises the context's stream. */
+ * into [0.05, 20]); points without matching data (no observing target frame,
+ * or all 32 costs 4.0) keep their current inverse depth, the constant
+ * initialisation being the fallback. Call pba_precompute_ic (or
+ * pba_solve_ic) afterwards. scratch: N_b * 97 floats. Synchronises the
+ * context's stream. */
 pba_status pba_propose_depths(pba_ctx* ctx, int bundle, const void* packed, float* scratch);
 
 #ifdef __cplusplus

@@ -64,6 +64,8 @@ struct IcStore {
     float* Hnn;       // Npad
     double* inv_hnn;  // Npad 1 / H_dd (0 where H_dd = 0)
     double* inv_d0;   // Npad 1 / d_0
+    float* part;      // E rows of kEntryPartial: the entry's 21 H_ff sums (kept for window updates)
+    float* hpart;     // E * 32 per-(entry, lane) J_d^T W_0 J_d (kept for window updates)
 };
 
 struct LaunchCtx {
@@ -82,12 +84,15 @@ struct LaunchCtx {
     int res_warps;         // warps per CTA of the accumulating IC residual pass (4, 8, 16)
 };
 
-cudaError_t launch_ic_precompute(const LaunchCtx& L);
+// IC precompute of the entries of the frames with todo[f] != 0 (all when
+// todo is null), then H_dd and its reciprocals for every point
+cudaError_t launch_ic_precompute(const LaunchCtx& L, const unsigned char* todo = nullptr);
 cudaError_t launch_ic_residual(const LaunchCtx& L, bool accum, int have_prev);
 // out[f * ncomp + k] = sum over frame f's entries of part[off + k]
 // (minus part[sub + k - sub_from] for k >= sub_from when sub >= 0)
 cudaError_t launch_frame_reduce(const LaunchCtx& L, int off, int ncomp, double* out, int slot_cur,
-                                int slot_prev, bool frames, int sub = -1, int sub_from = 0);
+                                int slot_prev, bool frames, int sub = -1, int sub_from = 0,
+                                const float* src = nullptr);
 cudaError_t launch_fc_residual(const LaunchCtx& L, bool accum, int have_prev);
 
 // The bundles of a launch over reduced camera systems: B bundles described

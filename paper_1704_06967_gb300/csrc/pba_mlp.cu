@@ -4,8 +4,9 @@
 // epipolar lines in two target frames to an initial inverse depth. It is
 // trained on the inverse depths the bundle adjustment converges to.
 //
-//   mlp_features_kernel   thread per point: the 8 x 8 normalised template
-//                         patch and 2 x 16 epipolar samples (96 FP32 values)
+//   mlp_features_kernel   warp per point: the 8 x 8 normalised template
+//                         patch and 2 x 16 epipolar matching costs (96 FP32
+//                         values)
 //   mlp_infer_tc_kernel   inference on the 5th-generation tensor cores:
 //                         BF16 weights and activations in shared memory,
 //                         tcgen05.mma with the FP32 accumulator in tensor
@@ -42,81 +43,97 @@ __device__ __forceinline__ bool bilinear_any(const DevProblem& pb, int f, float 
     return true;
 }
 
-// Tiles [tile0, tile0 + ntiles), one warp per tile (lane = point).
+// One warp per point of tiles [tile0, tile0 + ntiles). Lanes share the 8 x 8
+// patch (two pixels each, mean and deviation by butterflies); lane
+// 16 s + k then takes bin k of frame s: the least mean squared difference
+// between the normalised pattern and the target frame over the bin's 16
+// inverse depths.
 __global__ void __launch_bounds__(128)
 mlp_features_kernel(DevProblem pb, const float* __restrict__ fconst, const int* __restrict__ slot_caller,
                     int tile0, int ntiles, float* __restrict__ out)
 {
     const int lane = threadIdx.x & 31;
-    const int tl = blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (tl >= ntiles) return;
-    const int t = tile0 + tl, n = t * kTile + lane;
+    const int slot = (blockIdx.x * 4 + (threadIdx.x >> 5));
+    if (slot >= ntiles * kTile) return;
+    const int t = tile0 + slot / kTile, pl = slot % kTile, n = t * kTile + pl;
     const int caller = slot_caller[n];
     if (caller < 0) return;
     float* o = out + (size_t)caller * kMlpIn;
     const int f0 = pb.tile_f0[t];
     const int u = pb.uvs[2 * n], v = pb.uvs[2 * n + 1];
-    float p[kMlpPatch * kMlpPatch];
-    float sum = 0.0f;
+    const size_t ref = (size_t)f0 * pb.H;
+    float p[2];
 #pragma unroll
-    for (int i = 0; i < kMlpPatch; ++i)
-#pragma unroll
-        for (int j = 0; j < kMlpPatch; ++j) {
-            const int y = min(max(v + kMlpPatchLo + i, 0), pb.H - 1);
-            const int x = min(max(u + kMlpPatchLo + j, 0), pb.W - 1);
-            const float val = load_px(pb.img, pb.dtype, ((size_t)f0 * pb.H + y) * pb.pitch + x);
-            p[kMlpPatch * i + j] = val;
-            sum += val;
-        }
-    const float mu = sum * (1.0f / (kMlpPatch * kMlpPatch));
-    float ss = 0.0f;
-#pragma unroll
-    for (int k = 0; k < kMlpPatch * kMlpPatch; ++k) ss += (p[k] - mu) * (p[k] - mu);
+    for (int h = 0; h < 2; ++h) {
+        const int k = lane + 32 * h, i = k / kMlpPatch, j = k % kMlpPatch;
+        const int y = min(max(v + kMlpPatchLo + i, 0), pb.H - 1);
+        const int x = min(max(u + kMlpPatchLo + j, 0), pb.W - 1);
+        p[h] = load_px(pb.img, pb.dtype, (ref + y) * pb.pitch + x);
+    }
+    const float mu = warp_sum1(p[0] + p[1]) * (1.0f / (kMlpPatch * kMlpPatch));
+    const float ss = warp_sum1((p[0] - mu) * (p[0] - mu) + (p[1] - mu) * (p[1] - mu));
     const float scale = 1.0f / (sqrtf(ss * (1.0f / (kMlpPatch * kMlpPatch))) + kMlpEps);
-#pragma unroll
-    for (int k = 0; k < kMlpPatch * kMlpPatch; ++k) o[k] = (p[k] - mu) * scale;
+    o[lane] = (p[0] - mu) * scale;
+    o[lane + 32] = (p[1] - mu) * scale;
     // the first two target frames (in frame order) that observe the point:
     // a tile's entries are stored in frame order
     int g[2] = {-1, -1}, found = 0;
     for (int e = pb.tile_entry[t]; e < pb.tile_entry[t + 1] && found < 2; ++e) {
         const Entry en = pb.entries[e];
-        if ((en.mask >> lane) & 1u) g[found++] = en.f;
+        if ((en.mask >> pl) & 1u) g[found++] = en.f;
+    }
+    if (found == 0) {
+        o[kMlpPatch * kMlpPatch + lane] = kMlpNoData;
+        return;
     }
     if (found == 1) g[1] = g[0];
-    const float2 xc = pb.xn[n];
-    for (int s = 0; s < kMlpFrames; ++s) {
-        float* os = o + kMlpPatch * kMlpPatch + s * kMlpSamples;
-        if (found == 0) {
-            for (int k = 0; k < kMlpSamples; ++k) os[k] = 0.0f;
-            continue;
-        }
-        const float* c = fconst + (size_t)g[s] * kFrameConst;
-        const float rx = fmaf(c[0], xc.x, fmaf(c[1], xc.y, c[2]));
-        const float ry = fmaf(c[3], xc.x, fmaf(c[4], xc.y, c[5]));
-        const float rz = fmaf(c[6], xc.x, fmaf(c[7], xc.y, c[8]));
-        for (int k = 0; k < kMlpSamples; ++k) {
-            const float d = kMlpDLo + k * ((kMlpDHi - kMlpDLo) / (kMlpSamples - 1));
-            const float qx = fmaf(d, c[9], rx), qy = fmaf(d, c[10], ry), qz = fmaf(d, c[11], rz);
-            float val = 0.0f, sample;
-            bool ok = false;
-            if (qz > 0.0f) ok = bilinear_any(pb, g[s], pb.fx * qx / qz + pb.cx, pb.fy * qy / qz + pb.cy, val);
-            sample = ok ? (val - mu) * scale : 0.0f;
-            os[k] = sample;
-        }
+    const int P = pb.P, s = lane >> 4, k = lane & 15;
+    float tm[PBA_MAX_PATTERN], xx[PBA_MAX_PATTERN], xy[PBA_MAX_PATTERN];
+    for (int j = 0; j < P; ++j) {
+        const int ox = pb.pat[2 * j], oy = pb.pat[2 * j + 1];
+        tm[j] = (load_px(pb.img, pb.dtype, (ref + v + oy) * pb.pitch + u + ox) - mu) * scale;
+        xx[j] = ((float)(u + ox) - pb.cx) / pb.fx;
+        xy[j] = ((float)(v + oy) - pb.cy) / pb.fy;
     }
+    const float* c = fconst + (size_t)g[s] * kFrameConst;
+    const float step = (kMlpDHi - kMlpDLo) / (kMlpSamples * kMlpSub);
+    float best = 3.0e38f;
+    for (int i = 0; i < kMlpSub; ++i) {
+        const float d = kMlpDLo + ((float)(kMlpSub * k + i) + 0.5f) * step;
+        float cost = 0.0f;
+        bool ok = true;
+        for (int j = 0; j < P && ok; ++j) {
+            const float qx = fmaf(c[0], xx[j], fmaf(c[1], xy[j], fmaf(d, c[9], c[2])));
+            const float qy = fmaf(c[3], xx[j], fmaf(c[4], xy[j], fmaf(d, c[10], c[5])));
+            const float qz = fmaf(c[6], xx[j], fmaf(c[7], xy[j], fmaf(d, c[11], c[8])));
+            float val = 0.0f;
+            ok = qz > 0.0f && bilinear_any(pb, g[s], pb.fx * qx / qz + pb.cx, pb.fy * qy / qz + pb.cy, val);
+            const float r = (val - mu) * scale - tm[j];
+            cost = fmaf(r, r, cost);
+        }
+        best = fminf(best, ok ? cost / (float)P : kMlpNoData);
+    }
+    o[kMlpPatch * kMlpPatch + lane] = best;
 }
 
 // Writes the proposals (clamped to a positive range) as the inverse depths
-// of the bundle's points; pads keep theirs.
+// of the bundle's points. Pads, and points without any matching data (no
+// target frame observes them, or every hypothesis leaves the image), keep
+// their inverse depth: the constant-depth initialisation is the fallback.
 __global__ void mlp_propose_kernel(const int* __restrict__ slot_caller, int slot0, int nslots,
-                                   const float* __restrict__ y, double* __restrict__ d64)
+                                   const float* __restrict__ X, const float* __restrict__ y,
+                                   double* __restrict__ d64)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nslots) return;
     const int caller = slot_caller[slot0 + i];
     if (caller < 0) return;
+    const float* m = X + (size_t)caller * kMlpIn + kMlpPatch * kMlpPatch;
+    bool any = false;
+    for (int k = 0; k < kMlpFrames * kMlpSamples; ++k) any |= m[k] != kMlpNoData;
+    if (!any) return;
     const float v = y[caller];
-    d64[slot0 + i] = isfinite(v) ? (double)fminf(fmaxf(v, kMlpDMin), kMlpDMax) : 1.0;
+    if (isfinite(v)) d64[slot0 + i] = (double)fminf(fmaxf(v, kMlpDMin), kMlpDMax);
 }
 
 // ---------------------------------------------------------------------------
@@ -543,15 +560,15 @@ cudaError_t launch_mlp_features(const DevProblem& pb, const float* fconst, const
                                 int ntiles, float* out, cudaStream_t st)
 {
     if (ntiles <= 0) return cudaSuccess;
-    mlp_features_kernel<<<(ntiles + 3) / 4, 128, 0, st>>>(pb, fconst, slot_caller, tile0, ntiles, out);
+    mlp_features_kernel<<<(ntiles * kTile + 3) / 4, 128, 0, st>>>(pb, fconst, slot_caller, tile0, ntiles, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_propose(const int* slot_caller, int slot0, int nslots, const float* y, double* d64,
-                               cudaStream_t st)
+cudaError_t launch_mlp_propose(const int* slot_caller, int slot0, int nslots, const float* X, const float* y,
+                               double* d64, cudaStream_t st)
 {
     if (nslots <= 0) return cudaSuccess;
-    mlp_propose_kernel<<<(nslots + 255) / 256, 256, 0, st>>>(slot_caller, slot0, nslots, y, d64);
+    mlp_propose_kernel<<<(nslots + 255) / 256, 256, 0, st>>>(slot_caller, slot0, nslots, X, y, d64);
     return cudaGetLastError();
 }
 

@@ -14,7 +14,9 @@ namespace pba {
 constexpr int kMlpPatch = 8;        // 8 x 8 template patch
 constexpr int kMlpPatchLo = -3;     // offsets -3 .. 4
 constexpr int kMlpFrames = 2;       // target frames sampled along the epipolar line
-constexpr int kMlpSamples = 16;     // samples per frame
+constexpr int kMlpSamples = 16;     // matching-cost bins per frame
+constexpr int kMlpSub = 16;         // inverse depths per bin
+constexpr float kMlpNoData = 4.0f;  // cost where the pattern leaves the image
 constexpr float kMlpDLo = 0.5f;     // inverse-depth range of the samples
 constexpr float kMlpDHi = 2.0f;
 constexpr float kMlpEps = 1.0f / 255.0f;
@@ -44,8 +46,8 @@ static_assert(PBA_MLP_PACKED_BYTES >= kMlpPackedWeightBytes + kMlpBiasFloats * 4
 
 cudaError_t launch_mlp_features(const DevProblem& pb, const float* fconst, const int* slot_caller, int tile0,
                                 int ntiles, float* out, cudaStream_t st);
-cudaError_t launch_mlp_propose(const int* slot_caller, int slot0, int nslots, const float* y, double* d64,
-                               cudaStream_t st);
+cudaError_t launch_mlp_propose(const int* slot_caller, int slot0, int nslots, const float* X, const float* y,
+                               double* d64, cudaStream_t st);
 cudaError_t launch_mlp_pack(const float* params, uint8_t* packed, cudaStream_t st);
 cudaError_t launch_mlp_infer(const uint8_t* packed, int n, const float* X, float* out, int* err, cudaStream_t st);
 size_t mlp_grad_scratch_floats(int n);

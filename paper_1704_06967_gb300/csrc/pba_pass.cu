@@ -43,14 +43,16 @@ __device__ __forceinline__ int rank_in(unsigned mask, int lane)
 // ---------------------------------------------------------------------------
 template <int PMAX, int DT>
 __global__ void __launch_bounds__(kPreWarps * 32, 2)
-ic_precompute_kernel(DevProblem pb, const float* __restrict__ fconst, const float* __restrict__ dcur,
-                     const float2* __restrict__ G0p, IcStore ic, float* __restrict__ ent_part,
-                     float* __restrict__ hpart)
+ic_precompute_kernel(DevProblem pb, const float* __restrict__ fconst, const double* __restrict__ d0_64,
+                     const float2* __restrict__ G0p, IcStore ic, const unsigned char* __restrict__ todo)
 {
     const int lane = threadIdx.x & 31;
     const int e = blockIdx.x * kPreWarps + (threadIdx.x >> 5);
     if (e >= pb.E) return;
     const Entry en = pb.entries[e];
+    if (todo && !todo[en.f]) return;  // window update: only the frames that entered
+    float* ent_part = ic.part;
+    float* hpart = ic.hpart;
     const int P = pb.P, NC = (7 * P + 3) / 4;
     const float k = pb.huber_k;
     float hff[21];
@@ -61,7 +63,7 @@ ic_precompute_kernel(DevProblem pb, const float* __restrict__ fconst, const floa
         const int n = en.tile * kTile + lane;
         const int nvis = __popc(en.mask), rank = rank_in(en.mask, lane);
         const float* c = fconst + (size_t)en.f * kFrameConst;
-        const float d0 = dcur[n];
+        const float d0 = (float)d0_64[n];
         const float2 xc = pb.xn[n];
         const float ax = fmaf(c[0], xc.x, fmaf(c[1], xc.y, c[2]));
         const float ay = fmaf(c[3], xc.x, fmaf(c[4], xc.y, c[5]));
@@ -176,8 +178,9 @@ ic_precompute_kernel(DevProblem pb, const float* __restrict__ fconst, const floa
     }
 }
 
-// H_dd per point (entries of its tile added in order) and the FP64
-// reciprocals 1/H_dd and 1/d_0 that the depth back-substitution multiplies by.
+// H_dd per point (entries of its tile added in order; entries of frames
+// outside the window have no visible lanes) and the FP64 reciprocals 1/H_dd
+// and 1/d_0 that the depth back-substitution multiplies by.
 __global__ void __launch_bounds__(kTileWarps * 32)
 ic_hdd_kernel(DevProblem pb, const float* __restrict__ hpart, const double* __restrict__ d64, IcStore ic)
 {
@@ -192,7 +195,9 @@ ic_hdd_kernel(DevProblem pb, const float* __restrict__ hpart, const double* __re
     for (int e = e0; e < e1; e += 8) {
         float v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = e + u < e1 ? hpart[(size_t)(e + u) * kTile + lane] : 0.0f;
+        for (int u = 0; u < 8; ++u)
+            v[u] = (e + u < e1 && ((pb.entries[e + u].mask >> lane) & 1u)) ? hpart[(size_t)(e + u) * kTile + lane]
+                                                                           : 0.0f;
 #pragma unroll
         for (int u = 0; u < 8; ++u) tot += v[u];
     }
@@ -234,38 +239,39 @@ frame_reduce_kernel(DevProblem pb, const float* __restrict__ ent_part, double* _
     ((dtype) == PBA_F32 ? CALL(PBA_F32) : (dtype) == PBA_F16 ? CALL(PBA_F16) : CALL(PBA_BF16))
 
 template <int PMAX, int DT>
-static cudaError_t ic_precompute_p(const LaunchCtx& L)
+static cudaError_t ic_precompute_p(const LaunchCtx& L, const unsigned char* todo)
 {
     const int blocks = (L.pb.E + kPreWarps - 1) / kPreWarps;
-    ic_precompute_kernel<PMAX, DT><<<blocks, kPreWarps * 32, 0, L.stream>>>(
-        L.pb, L.fs.fc, L.it.dcur, L.it.G0p, L.ic, L.ent_part, L.it.gpart);
+    ic_precompute_kernel<PMAX, DT><<<blocks, kPreWarps * 32, 0, L.stream>>>(L.pb, L.fs.fc, L.ds_ic.d0_64,
+                                                                            L.it.G0p, L.ic, todo);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ic_precompute(const LaunchCtx& L)
+cudaError_t launch_ic_precompute(const LaunchCtx& L, const unsigned char* todo)
 {
     cudaError_t e = cudaSuccess;
     if (L.pb.E > 0) {
-#define PBA_C8(DT) ic_precompute_p<8, DT>(L)
-#define PBA_C16(DT) ic_precompute_p<16, DT>(L)
+#define PBA_C8(DT) ic_precompute_p<8, DT>(L, todo)
+#define PBA_C16(DT) ic_precompute_p<16, DT>(L, todo)
         e = L.pb.P <= 8 ? PBA_DISPATCH_DT(L.pb.dtype, PBA_C8) : PBA_DISPATCH_DT(L.pb.dtype, PBA_C16);
 #undef PBA_C8
 #undef PBA_C16
         if (e != cudaSuccess) return e;
     }
     ic_hdd_kernel<<<(L.pb.T + kTileWarps - 1) / kTileWarps, kTileWarps * 32, 0, L.stream>>>(
-        L.pb, L.it.gpart, L.ds_ic.d64, L.ic);
+        L.pb, L.ic.hpart, L.ds_ic.d0_64, L.ic);
     return cudaGetLastError();
 }
 
 cudaError_t launch_frame_reduce(const LaunchCtx& L, int off, int ncomp, double* out, int slot_cur,
-                                int slot_prev, bool frames, int sub, int sub_from)
+                                int slot_prev, bool frames, int sub, int sub_from, const float* src)
 {
     const int nfb = frames ? L.pb.F - 1 : 0;
     const dim3 grid(nfb + 1), block(kReduceThreads);
     if (off != 0) return cudaErrorInvalidValue;
+    const float* rows = src ? src : L.ent_part;
 #define PBA_R(NC, SB, SF)                                                                           \
-    launch_pdl(frame_reduce_kernel<NC, SB, SF>, grid, block, 0, L.stream, L.pb, L.ent_part, out, L.tstats, \
+    launch_pdl(frame_reduce_kernel<NC, SB, SF>, grid, block, 0, L.stream, L.pb, rows, out, L.tstats, \
                L.dthsq, L.stats, slot_cur, slot_prev, nfb)
     if (!frames || (ncomp == 6 && sub == 6 && sub_from == 0)) return PBA_R(6, 6, 0);
     if (ncomp == 21 && sub < 0) return PBA_R(21, -1, 0);

@@ -112,6 +112,8 @@ struct pba_ctx {
         int* pat;
         Entry* entries;
         int *tile_entry, *frame_entry, *entry_slot, *frame_bundle, *tile_f0, *slot_caller;
+        float *ic_part, *ic_hpart;  // per-entry IC H_ff sums and J_d^T W_0 J_d (kept for window updates)
+        unsigned char* todo;        // F: frames whose entries a window update must precompute
         BundleDesc* bund;
         int* uvs;
         float2* xn;
@@ -144,6 +146,10 @@ struct pba_ctx {
     int last_fc = 0;  // which system the last update came from
     int ldl_cluster = 0;  // CTAs per bundle of the factorisation (0: default)
     std::vector<int> bundle_err;  // per-bundle error bits of the last check
+    // sliding window: frames outside it keep their data but their entries
+    // are uploaded with no visible lane, so no kernel sees their residuals
+    std::vector<unsigned char> frame_on, frame_todo;  // F
+    bool window_dirty = false;  // the window changed after the last (pre)computation
     int res_warps = 8;    // warps per CTA of the IC residual pass
     bool tuned = false;
 
@@ -188,6 +194,13 @@ pba_status fail(pba_ctx* c, pba_status s, const char* fmt, ...)
         CK(call);                     \
         ++ctx->launches;              \
         tend(ctx, ev_);               \
+    } while (0)
+
+#define CHECK_BUNDLE()                                                                         \
+    do {                                                                                       \
+        if (!ctx) return PBA_ERR_ARG;                                                          \
+        if (bundle < 0 || bundle >= ctx->B)                                                    \
+            return fail(ctx, PBA_ERR_ARG, "bundle %d out of range (%d bundles)", bundle, ctx->B); \
     } while (0)
 
 // for launchers that enqueue several kernels and count them in `nl`
@@ -331,6 +344,9 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.Hfd_ic, (size_t)c->V * 6 * 4);
     take(c->d.Hfd_fc, (size_t)c->V * 6 * 4);
     take(c->d.ent_part, (size_t)c->E * kEntryPartial * 4);
+    take(c->d.ic_part, (size_t)c->E * kEntryPartial * 4);
+    take(c->d.ic_hpart, (size_t)c->E * kTile * 4);
+    take(c->d.todo, F);
     take(c->d.tstats, (size_t)c->T * sizeof(TileStats));
     take(c->d.fc, F * kFrameConst * 4);
     take(c->d.fc_prev, F * 12 * 4);
@@ -597,7 +613,7 @@ LaunchCtx make_launch(pba_ctx* c)
     L.it = IterBufs{c->d.dcur, c->d.dprev, c->d.gpart, c->d.estats, c->d.ddsq_t, c->d.G0p};
     L.ds_ic = DepthState{c->d.d64, c->d.d0_64, c->d.gn_ic, c->d.Hnn_ic, c->d.Hfd_ic, c->d.dd_last, c->d.err};
     L.ds_fc = DepthState{c->d.d64, c->d.d0_64, c->d.gn_fc, c->d.Hnn_fc, c->d.Hfd_fc, c->d.dd_last, c->d.err};
-    L.ic = IcStore{c->d.J4, c->d.Hfd_ic, c->d.Hnn_ic, c->d.inv_hnn, c->d.inv_d0};
+    L.ic = IcStore{c->d.J4, c->d.Hfd_ic, c->d.Hnn_ic, c->d.inv_hnn, c->d.inv_d0, c->d.ic_part, c->d.ic_hpart};
     L.Hfd_fc = c->d.Hfd_fc;
     L.ent_part = c->d.ent_part;
     L.tstats = c->d.tstats;
@@ -952,6 +968,9 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     std::vector<int> pat(ctx->pattern.begin(), ctx->pattern.end());
     CK(h2d(ctx, ctx->d.pat, pat.data(), sizeof(int) * pat.size()));
     CK(h2d(ctx, ctx->d.entries, ctx->entries.data(), sizeof(Entry) * ctx->entries.size()));
+    ctx->frame_on.assign(ctx->F, 1);
+    ctx->frame_todo.assign(ctx->F, 0);
+    ctx->window_dirty = false;
     CK(h2d(ctx, ctx->d.tile_entry, ctx->tile_entry.data(), sizeof(int) * ctx->tile_entry.size()));
     CK(h2d(ctx, ctx->d.frame_entry, ctx->frame_entry.data(), sizeof(int) * ctx->frame_entry.size()));
     CK(h2d(ctx, ctx->d.entry_slot, ctx->entry_slot.data(), sizeof(int) * ctx->entry_slot.size()));
@@ -983,7 +1002,8 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     return PBA_OK;
 }
 
-pba_status precompute_core(pba_ctx* ctx, const LaunchCtx& L, const BundleSet& bs);
+pba_status precompute_core(pba_ctx* ctx, const LaunchCtx& L, const BundleSet& bs,
+                           const unsigned char* todo = nullptr);
 
 // The IC precompute's launches (Sec. 3.5): p_0 from the current parameters,
 // J, W_0 and the H blocks per entry, the frame sums, the Schur complement, S
@@ -1002,11 +1022,12 @@ pba_status precompute_body(pba_ctx* ctx)
     return precompute_core(ctx, L, bs);
 }
 
-// The precompute after the FP32 depths of the new p_0 are in place.
-pba_status precompute_core(pba_ctx* ctx, const LaunchCtx& L, const BundleSet& bs)
+// The precompute after the FP32 depths of the new p_0 are in place; with
+// todo, the entries of the frames flagged there only (a window update).
+pba_status precompute_core(pba_ctx* ctx, const LaunchCtx& L, const BundleSet& bs, const unsigned char* todo)
 {
-    LAUNCH(TS_PRE, launch_ic_precompute(L));
-    LAUNCH(TS_PRE, launch_frame_reduce(L, 0, 21, ctx->d.red_ic, -1, -1, true));
+    LAUNCH(TS_PRE, launch_ic_precompute(L, todo));
+    LAUNCH(TS_PRE, launch_frame_reduce(L, 0, 21, ctx->d.red_ic, -1, -1, true, -1, 0, ctx->d.ic_part));
     LAUNCHN(TS_PRE, launch_schur_sparse(L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, schur_lists(ctx), ctx->d.schur_part,
                                         ctx->d.Soff, ctx->stream, &nl));
     LAUNCH(TS_PRE, launch_assemble_S(bs, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64, ctx->cfg.gauge_anchor_w,
@@ -1100,7 +1121,68 @@ pba_status pba_precompute_ic(pba_ctx* ctx)
     // a system that is not positive definite is reported (per bundle); its
     // non-positive pivots were replaced, so the other bundles of a batch can
     // iterate (that one only at the caller's risk)
-    if (s == PBA_OK || s == PBA_ERR_NOT_PD) ctx->ic_ready = true;
+    if (s == PBA_OK || s == PBA_ERR_NOT_PD) {
+        ctx->ic_ready = true;
+        ctx->window_dirty = false;
+        std::fill(ctx->frame_todo.begin(), ctx->frame_todo.end(), 0);
+    }
+    return s;
+}
+
+// Sliding window (Sec. 4.2 suggests a dynamic Hessian for windows of
+// keyframes): frames leave and enter; the IC system is brought up to date
+// from the stored per-entry products, precomputing only the entering frames.
+pba_status pba_set_window(pba_ctx* ctx, int bundle, const uint8_t* in_window)
+{
+    CHECK_BUNDLE();
+    if (!in_window) return fail(ctx, PBA_ERR_ARG, "null window flags");
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    const BundleIn& b = ctx->bun[bundle];
+    bool changed = false;
+    for (int f = 1; f < b.F; ++f) {
+        const int g = b.fo + f;
+        const unsigned char on = in_window[f] != 0;
+        if (on == ctx->frame_on[g]) continue;
+        changed = true;
+        ctx->frame_on[g] = on;
+        ctx->frame_todo[g] = on;
+        if (!on) {  // the frame's stored H_ff sums leave the frame reduction
+            const int s0 = ctx->frame_entry[g], s1 = ctx->frame_entry[g + 1];
+            if (s1 > s0)
+                CK(cudaMemsetAsync(ctx->d.ic_part + (size_t)s0 * kEntryPartial, 0,
+                                   sizeof(float) * kEntryPartial * (s1 - s0), ctx->stream));
+        }
+    }
+    if (!changed) return PBA_OK;
+    std::vector<Entry> masked(ctx->entries);
+    for (Entry& e : masked)
+        if (!ctx->frame_on[e.f]) e.mask = 0u;
+    CK(h2d(ctx, ctx->d.entries, masked.data(), sizeof(Entry) * masked.size()));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->window_dirty = true;
+    return PBA_OK;
+}
+
+pba_status pba_update_ic(pba_ctx* ctx)
+{
+    if (!ctx) return PBA_ERR_ARG;
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    if (!ctx->ic_ready) return pba_precompute_ic(ctx);
+    LaunchCtx L = make_launch(ctx);
+    const BundleSet bs = bundle_set(ctx);
+    // an entering frame is anchored at its current pose; the points keep d_0
+    for (int f = 0; f < ctx->F; ++f)
+        if (ctx->frame_todo[f])
+            CK(cudaMemcpyAsync(ctx->d.poses0_64 + 12 * (size_t)f, ctx->d.poses64 + 12 * (size_t)f,
+                               sizeof(double) * 12, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(h2d(ctx, ctx->d.todo, ctx->frame_todo.data(), ctx->frame_todo.size()));
+    pba_status s = precompute_core(ctx, L, bs, ctx->d.todo);
+    if (s != PBA_OK) return s;
+    s = check_device_error(ctx);
+    if (s == PBA_OK || s == PBA_ERR_NOT_PD) {
+        ctx->window_dirty = false;
+        std::fill(ctx->frame_todo.begin(), ctx->frame_todo.end(), 0);
+    }
     return s;
 }
 
@@ -1108,6 +1190,7 @@ pba_status pba_iterate(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
 {
     if (!ctx) return PBA_ERR_ARG;
     if (!ctx->ic_ready) return fail(ctx, PBA_ERR_STATE, "pba_precompute_ic must come first");
+    if (ctx->window_dirty) return fail(ctx, PBA_ERR_STATE, "the window changed: pba_update_ic first");
     if (n_iters < 0 || n_iters > ctx->cfg.max_stats_iters)
         return fail(ctx, PBA_ERR_ARG, "n_iters must be in [0, %d]", ctx->cfg.max_stats_iters);
     LaunchCtx L = make_launch(ctx);
@@ -1180,7 +1263,11 @@ pba_status pba_solve_ic(pba_ctx* ctx, int n_iters, int reanchor_every, pba_iter_
     if (s != PBA_OK) return s;
     ctx->last_fc = 0;
     s = copy_stats(ctx, n_iters, stats);
-    if (s == PBA_OK || s == PBA_ERR_NOT_PD) ctx->ic_ready = true;
+    if (s == PBA_OK || s == PBA_ERR_NOT_PD) {
+        ctx->ic_ready = true;
+        ctx->window_dirty = false;
+        std::fill(ctx->frame_todo.begin(), ctx->frame_todo.end(), 0);
+    }
     return s;
 }
 
@@ -1240,13 +1327,6 @@ static pba_status gather_points(pba_ctx* ctx, const BundleIn& b, const void* dev
     }
     return PBA_OK;
 }
-
-#define CHECK_BUNDLE()                                                                         \
-    do {                                                                                       \
-        if (!ctx) return PBA_ERR_ARG;                                                          \
-        if (bundle < 0 || bundle >= ctx->B)                                                    \
-            return fail(ctx, PBA_ERR_ARG, "bundle %d out of range (%d bundles)", bundle, ctx->B); \
-    } while (0)
 
 pba_status pba_get_params(pba_ctx* ctx, int bundle, double* poses, double* inv_depth)
 {
@@ -1377,7 +1457,7 @@ pba_status pba_propose_depths(pba_ctx* ctx, int bundle, const void* packed, floa
     float* y = scratch + (size_t)b.N * kMlpIn;
     CK(launch_mlp_features(L.pb, ctx->d.fc, ctx->d.slot_caller, b.to, b.T, scratch, ctx->stream));
     CK(launch_mlp_infer(static_cast<const uint8_t*>(packed), b.N, scratch, y, ctx->d.err, ctx->stream));
-    CK(launch_mlp_propose(ctx->d.slot_caller, kTile * b.to, kTile * b.T, y, ctx->d.d64, ctx->stream));
+    CK(launch_mlp_propose(ctx->d.slot_caller, kTile * b.to, kTile * b.T, scratch, y, ctx->d.d64, ctx->stream));
     ctx->ic_ready = false;  // p_0 changes: the precompute must run again
     return check_device_error(ctx);
 }

@@ -123,17 +123,16 @@ class DepthMLP:
         ctx.propose_depths(self.pack(), bundle)
 
 
-def training_pairs(scene, iters: int = 20, stream=None, **kw):
+def training_pairs(scene, iters: int = 20, stream=None, damping: float = 0.01, reanchor_every: int = 3, **kw):
     """(features at p_0, converged inverse depths, mask of usable points) of
     one generated bundle, or None when the method cannot solve it: the
-    bundle is solved with IC from its own initialisation; points that no
-    target frame observes are not usable."""
+    bundle is solved with IC (damped, re-anchored) from its own
+    initialisation; points that no target frame observes are not usable."""
     from .pba import Bundle
-    b = Bundle.from_scene(scene, stream=stream, **kw)
+    b = Bundle.from_scene(scene, stream=stream, damping=damping, **kw)
     X = b.depth_features()
     try:
-        b.precompute_ic()
-        b.iterate(iters, stats=False)
+        b.solve_ic(iters, reanchor_every=reanchor_every, stats=False)
     except PbaError:
         b.close()
         return None  # a bundle the method cannot solve gives no targets

@@ -74,6 +74,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pba_iterate": ([vp, i, vp], i),
         "pba_solve_fc": ([vp, i, vp], i),
         "pba_solve_ic": ([vp, i, i, vp], i),
+        "pba_set_window": ([vp, i, vp], i),
+        "pba_update_ic": ([vp], i),
         "pba_get_params": ([vp, i, vp, vp], i),
         "pba_set_params": ([vp, i, vp, vp], i),
         "pba_get_last_update": ([vp, i, vp, vp], i),
@@ -232,6 +234,16 @@ class Batch:
         """IC iterations; returns stats [n+1, 6] (energy, rms, n_valid,
         max_disp_px, dtheta_norm, dd_norm) or None."""
         return self._stats(self.lib.pba_iterate, n_iters, stats)
+
+    def set_window(self, in_window, bundle=0):
+        """Frames of the bundle in the sliding window (F_b flags)."""
+        flags = np.ascontiguousarray(np.asarray(in_window, dtype=bool).astype(np.uint8))
+        assert flags.shape == (self.Fs[bundle],)
+        self._check(self.lib.pba_set_window(self.h, bundle, _p(flags)))
+
+    def update_ic(self):
+        """Incremental IC system update after a window change."""
+        self._check(self.lib.pba_update_ic(self.h))
 
     def solve_ic(self, n_iters, reanchor_every=0, stats=True):
         """Precompute + n_iters IC iterations, re-anchoring p_0 every

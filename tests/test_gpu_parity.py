@@ -436,3 +436,63 @@ def test_reanchoring_settles_a_weakly_observed_bundle(torch_cuda):
     re = b.solve_ic(20, reanchor_every=3)
     assert re[-1, 1] < 0.85 * plain[-1, 1], (re[-1, 1], plain[-1, 1])
     assert re[-1, 1] < re[0, 1]
+
+
+# ----------------------------------------------------------------------------
+# sliding window (pba_set_window / pba_update_ic)
+# ----------------------------------------------------------------------------
+def test_window_steps_match_oracle_without_the_frames_outside(torch_cuda):
+    sc = synth.make_scene("small")
+    vis = sc.vis.copy()
+    vis[:, 4] = 0  # the oracle's bundle without frame 4
+    pb = oracle.Problem(sc.images_f32, sc.uv, sc.pattern, vis, sc.intrinsics, sc.huber_k)
+    pre = oracle.ic_precompute(pb, sc.poses0, sc.depths0)
+    b = _bundle(sc)
+    b.set_window([1, 1, 1, 1, 0, 1])
+    b.precompute_ic()
+    b.iterate(1)
+    dth, dd = b.last_update()
+    o_dth, o_dd, _, _, _ = oracle.ic_step(pb, pre, sc.poses0, sc.depths0, sc.poses0, sc.depths0)
+    ref0 = np.linalg.norm(np.concatenate([o_dth[1:].ravel(), o_dd]))
+    assert _step_err(dth, dd, o_dth, o_dd, ref0) <= STEP_TOL
+    assert not dth[4].any()
+    b.set_params(sc.poses0, sc.depths0)
+    b.solve_fc(1)
+    dth, dd = b.last_update()
+    o_dth, o_dd, _, _, _ = oracle.fc_step(pb, sc.poses0, sc.depths0)
+    ref0 = np.linalg.norm(np.concatenate([o_dth[1:].ravel(), o_dd]))
+    assert _step_err(dth, dd, o_dth, o_dd, ref0) <= STEP_TOL
+
+
+def test_window_update_equals_a_full_precompute_with_the_same_anchors(torch_cuda):
+    """Frame 4 enters after three iterations, anchored at its current pose:
+    the incremental update reuses the other frames' products and gives the
+    system a full precompute forms from the same anchors, bit for bit."""
+    sc = synth.make_scene("small")
+    a = _bundle(sc)
+    a.set_window([1, 1, 1, 1, 0, 1])
+    a.precompute_ic()
+    a.iterate(3)
+    P, D = a.params()
+    P4 = P.copy()
+    w = np.array([0.004, -0.003, 0.002])
+    R = oracle.so3_exp(w) @ P[4, :9].reshape(3, 3)
+    P4[4, :9] = R.ravel()
+    P4[4, 9:] += np.array([0.003, 0.001, -0.002])
+    a.set_params(P4, D)
+    with pytest.raises(Exception):
+        a.iterate(1)  # the window changed: the system is stale
+    a.set_window([1, 1, 1, 1, 1, 1])
+    a.update_ic()
+    anchors = sc.poses0.copy()
+    anchors[4] = P4[4]
+    from paper_1704_06967_gb300 import Bundle
+    b = Bundle.from_scene(sc)
+    b.set_params(anchors, sc.depths0)
+    b.precompute_ic()
+    sa, sb = a.system(fc=False), b.system(fc=False)
+    for key in ("Hff", "Hdd", "S"):
+        assert np.array_equal(sa[key], sb[key]), key
+    a.iterate(2)
+    a.close()
+    b.close()
