@@ -270,6 +270,16 @@ pba_status pba_get_tuning(pba_ctx* ctx, int* res_warps, int* ldl_cluster);
  * statistics, parameters, updates and systems). Host, nullable each. */
 pba_status pba_transfer_bytes(pba_ctx* ctx, int64_t* h2d, int64_t* d2h);
 
+/* One level of an image pyramid (coarse-to-fine solving; an addition beyond
+ * the paper): dst[f][y][x] = mean of src[f][2y .. 2y+1][2x .. 2x+1], FP32,
+ * floor(w/2) x floor(h/2) per frame, rows of floor(w/2) elements. Pixel
+ * centres map as x_coarse = (x_fine + 0.5) / 2 - 0.5, so a camera's
+ * intrinsics become f / 2 and (c + 0.5) / 2 - 0.5. src: device, n_frames x h
+ * rows of pitch_elems elements of dtype; dst: device. Enqueued on
+ * cuda_stream (NULL = legacy default), not synchronised. */
+pba_status pba_downsample(const void* src, pba_dtype dtype, int n_frames, int w, int h, int pitch_elems,
+                          float* dst, void* cuda_stream);
+
 /* Reduced camera system without any allocation, for callers that cannot
  * allocate device memory (code running inside a fixed pre-reserved memory
  * arena, runtimes that forbid cudaMalloc after start-up, frameworks that

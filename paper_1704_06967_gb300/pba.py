@@ -75,6 +75,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pba_solve_fc": ([vp, i, vp], i),
         "pba_solve_ic": ([vp, i, i, vp], i),
         "pba_set_window": ([vp, i, vp], i),
+        "pba_downsample": ([vp, i, i, i, i, i, vp, vp], i),
         "pba_update_ic": ([vp], i),
         "pba_get_params": ([vp, i, vp, vp], i),
         "pba_set_params": ([vp, i, vp, vp], i),

@@ -480,9 +480,9 @@ def test_window_update_equals_a_full_precompute_with_the_same_anchors(torch_cuda
     P4[4, :9] = R.ravel()
     P4[4, 9:] += np.array([0.003, 0.001, -0.002])
     a.set_params(P4, D)
+    a.set_window([1, 1, 1, 1, 1, 1])
     with pytest.raises(Exception):
         a.iterate(1)  # the window changed: the system is stale
-    a.set_window([1, 1, 1, 1, 1, 1])
     a.update_ic()
     anchors = sc.poses0.copy()
     anchors[4] = P4[4]
