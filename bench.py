@@ -41,6 +41,24 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def max_over_ranks(values, dist=None, device="cuda"):
+    """The slowest rank's timings: every rank's list reduced element-wise by
+    MAX (the value all ranks report); the list itself without a process
+    group."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def aggregate_rate(units_per_rank, world, total_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: each rank does the same work)."""
+    return world * units_per_rank / (total_ms / 1e3)
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -359,16 +377,10 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
 
-    total_ic = sum(ic_ms)
-    if dist is not None:
-        tt = torch.tensor([total_ic, sum(fc_ms)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ic, total_fc = float(tt[0]), float(tt[1])
-    else:
-        total_fc = sum(fc_ms)
+    total_ic, total_fc = max_over_ranks([sum(ic_ms), sum(fc_ms)], dist)
     R = sc.n_residuals()
-    value = world * iters * args.steps / (total_ic / 1e3)
-    fc_value = world * iters * args.steps / (total_fc / 1e3)
+    value = aggregate_rate(iters * args.steps, world, total_ic)
+    fc_value = aggregate_rate(iters * args.steps, world, total_fc)
 
     # statistics trajectories for the equal-RMS comparison (untimed)
     _, _, st_ic = ic_solve(stats=True)
@@ -460,12 +472,8 @@ def run_ours(args):
             e2e_t.append(t1 - t0)
             h2d_b, d2h_b = eb.transfer_bytes()
         eb.close()
-    e2e_total = sum(e2e_t)
-    if dist is not None:
-        tt = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_total = float(tt[0])
-    e2e_value = world * iters * args.steps / e2e_total
+    (e2e_total,) = max_over_ranks([sum(e2e_t)], dist)
+    e2e_value = aggregate_rate(iters * args.steps, world, 1e3 * e2e_total)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -645,14 +653,10 @@ def run_batch(args):
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
-    tot = torch.tensor([sum(ic_ms), sum(loop_ms), sum(fc_ms)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    total_ic, total_loop, total_fc = (float(x) for x in tot)
-    units = world * B * iters * args.steps
-    value = units / (total_ic / 1e3)
-    loop_value = units / (total_loop / 1e3)
-    fc_value = units / (total_fc / 1e3)
+    total_ic, total_loop, total_fc = max_over_ranks([sum(ic_ms), sum(loop_ms), sum(fc_ms)], dist)
+    value = aggregate_rate(B * iters * args.steps, world, total_ic)
+    loop_value = aggregate_rate(B * iters * args.steps, world, total_loop)
+    fc_value = aggregate_rate(B * iters * args.steps, world, total_fc)
 
     # the batch and the loop must agree exactly (each bundle's sums keep their order)
     reset()
