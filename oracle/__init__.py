@@ -48,7 +48,7 @@ class _Problem(ctypes.Structure):
                 ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double),
                 ("cy", ctypes.c_double), ("huber_k", ctypes.c_double),
                 ("img", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("pat", ctypes.c_void_p),
-                ("vis", ctypes.c_void_p), ("damping", ctypes.c_double)]
+                ("vis", ctypes.c_void_p), ("damping", ctypes.c_double), ("photo", ctypes.c_void_p)]
 
 
 class _IcPre(ctypes.Structure):
@@ -87,6 +87,7 @@ def _L():
             "or_fc_update": ([i, i, vp, vp, vp, vp, vp, vp], None),
             "or_fc_step": ([pp, vp, vp, vp, vp, vp, vp, vp], i),
             "or_eval": ([pp, vp, vp, vp], None),
+            "or_photo_update": ([pp, vp, vp], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -178,7 +179,7 @@ class Problem:
     """A bundle as the oracle sees it: FP64 copies of the (dequantised) images,
     integer point pixels, pattern, visibility, intrinsics and Huber k."""
 
-    def __init__(self, images, uv, pattern, vis, intrinsics, huber_k, damping=0.0):
+    def __init__(self, images, uv, pattern, vis, intrinsics, huber_k, damping=0.0, photometric=False):
         self.img = _f64(images)
         self.F, self.H, self.W = self.img.shape
         self.uv = np.ascontiguousarray(uv, dtype=np.int32)
@@ -189,14 +190,17 @@ class Problem:
         self.fx, self.fy, self.cx, self.cy = fx, fy, cx, cy
         self.huber_k = float(huber_k)
         self.damping = float(damping)
+        # affine brightness pairs (alpha_f, beta_f): the model's state, updated
+        # in place by every step (None: model off)
+        self.photo = np.tile([1.0, 0.0], self.F) if photometric else None
         self.c = _Problem(self.W, self.H, self.F, self.N, self.P, fx, fy, cx, cy,
                           self.huber_k, _p(self.img), _p(self.uv), _p(self.pat), _p(self.vis),
-                          self.damping)
+                          self.damping, _p(self.photo) if photometric else None)
 
     @classmethod
-    def from_scene(cls, scene, damping=0.0):
+    def from_scene(cls, scene, damping=0.0, photometric=False):
         return cls(scene.images_f32, scene.uv, scene.pattern, scene.vis, scene.intrinsics,
-                   scene.huber_k, damping)
+                   scene.huber_k, damping, photometric)
 
     def ref(self):
         return ctypes.byref(self.c)
@@ -315,6 +319,14 @@ def fc_step(pb: Problem, poses, depths):
     if st != 0:
         raise np.linalg.LinAlgError("reduced camera system not positive definite")
     return dtheta.reshape(pb.F, 6), dd, po, do, stats
+
+
+def photo_update(pb: Problem, poses, depths):
+    """Fits every target frame's brightness pair to the residuals at
+    (poses, depths) in place (pb.photo); no-op with the model off."""
+    poses, depths = _f64(poses), _f64(depths)
+    _L().or_photo_update(pb.ref(), _p(poses), _p(depths))
+    return pb.photo
 
 
 def evaluate(pb: Problem, poses, depths):

@@ -55,6 +55,7 @@ typedef struct {
     const int* pat;             /* P*2 pattern offsets (pixels) */
     const unsigned char* vis;   /* N*F visibility, vis[n*F+f] */
     double damping;             /* Levenberg-Marquardt lambda (0: Gauss-Newton) */
+    double* photo;              /* F*2 affine brightness (alpha_f, beta_f) or NULL (model off) */
 } or_problem;
 
 /* IC precompute (Sec. 3.5), indexed by residual id ((n*F + f)*P + j). */
@@ -343,6 +344,8 @@ static int residual_at(const or_problem* pb, int n, int f, int j, const double* 
         *r = 0.0;
         return 0;
     }
+    /* affine brightness of frame f: the template sees alpha_f I_f + beta_f */
+    if (pb->photo) If = pb->photo[2 * f] * If + pb->photo[2 * f + 1];
     *r = pix(frame_img(pb, 0), pb->W, px, py) - If;
     return 1;
 }
@@ -391,10 +394,11 @@ int or_fc_residual(const or_problem* pb, const double* poses, const double* dept
         dq[i][6] = t[i];
     }
     double iz = 1.0 / q[2];
+    const double alpha = pb->photo ? pb->photo[2 * f] : 1.0;
     for (int k = 0; k < 7; ++k) {
         double dx = iz * (dq[0][k] - q[0] * iz * dq[2][k]);
         double dy = iz * (dq[1][k] - q[1] * iz * dq[2][k]);
-        Jrow[k] = -(gu * pb->fx * dx + gv * pb->fy * dy);
+        Jrow[k] = -alpha * (gu * pb->fx * dx + gv * pb->fy * dy);
     }
     return 1;
 }
@@ -679,6 +683,53 @@ void or_ic_update(int F, int N, const double* poses0, const double* depths0,
     for (int n = 0; n < N; ++n) depths_out[n] = depths[n] * (depths0[n] - dd[n]) / depths0[n];
 }
 
+/* Affine brightness (an option beyond the paper; its Sec. 2 notes that
+ * direct methods must model lighting): with the residuals of the parameters
+ * (poses, depths) and the current (alpha_f, beta_f), each target frame's
+ * pair is set so that the warped samples v take the template's weighted
+ * mean and spread over the frame's valid residuals (w the Huber weights of
+ * those residuals):
+ *   alpha = sqrt(var_w(I_0) / var_w(v)),  beta = mean_w(I_0) - alpha mean_w(v).
+ * (A least-squares fit of I_0 on v would shrink alpha wherever the
+ * geometry is still off, down to alpha ~ 0 that ignores the target image;
+ * matching the spreads does not depend on the alignment.) A frame with no
+ * residuals or without spread keeps its pair. No-op when the model is off. */
+void or_photo_update(const or_problem* pb, const double* poses, const double* depths)
+{
+    if (!pb->photo) return;
+    int F = pb->F, N = pb->N, P = pb->P;
+    for (int f = 1; f < F; ++f) {
+        const double* R = poses + 12 * f;
+        const double* t = R + 9;
+        double Sw = 0.0, Sv = 0.0, Svv = 0.0, S0 = 0.0, S00 = 0.0;
+        for (int n = 0; n < N; ++n) {
+            if (!pb->vis[(size_t)n * F + f]) continue;
+            for (int j = 0; j < P; ++j) {
+                double r, u[2], q[3];
+                if (!residual_at(pb, n, f, j, R, t, depths[n], &r, u, q)) continue;
+                const double w = or_huber_weight(r, pb->huber_k);
+                int px, py;
+                double x, y, v;
+                pattern_pixel(pb, n, j, &px, &py, &x, &y);
+                const double I0 = pix(frame_img(pb, 0), pb->W, px, py);
+                or_bilinear(frame_img(pb, f), pb->W, pb->H, u[0], u[1], &v);  /* the raw sample */
+                Sw += w;
+                Sv += w * v;
+                Svv += w * v * v;
+                S0 += w * I0;
+                S00 += w * I0 * I0;
+            }
+        }
+        if (!(Sw > 0.0)) continue;
+        const double mv = Sv / Sw, m0 = S0 / Sw;
+        const double vv = Svv / Sw - mv * mv, v0 = S00 / Sw - m0 * m0;
+        if (!(vv > 1e-12) || !(v0 > 1e-12)) continue;
+        const double alpha = sqrt(v0 / vv);
+        pb->photo[2 * f] = alpha;
+        pb->photo[2 * f + 1] = m0 - alpha * mv;
+    }
+}
+
 /* One IC iteration: steps 1-4. Returns 0 or OR_ERR_NOT_PD. */
 int or_ic_step(const or_problem* pb, const or_ic_pre* pre, const double* poses0,
                const double* depths0, const double* poses, const double* depths,
@@ -697,6 +748,8 @@ int or_ic_step(const or_problem* pb, const or_ic_pre* pre, const double* poses0,
     if (st == OR_OK) {
         or_ic_update(F, N, poses0, depths0, poses, depths, dtheta, dd, poses_out, depths_out);
         stats[ST_MAXDISP] = or_max_reproj_disp(pb, poses, depths, poses_out, depths_out);
+        /* the brightness pairs from this iteration's residuals (at p_k) */
+        or_photo_update(pb, poses, depths);
         double a = 0.0, b = 0.0;
         for (int i = 0; i < 6 * F; ++i) a += dtheta[i] * dtheta[i];
         for (int n = 0; n < N; ++n) b += dd[n] * dd[n];
@@ -783,6 +836,7 @@ int or_fc_step(const or_problem* pb, const double* poses, const double* depths, 
     if (st == OR_OK) {
         or_fc_update(F, N, poses, depths, dtheta, dd, poses_out, depths_out);
         stats[ST_MAXDISP] = or_max_reproj_disp(pb, poses, depths, poses_out, depths_out);
+        or_photo_update(pb, poses, depths);
         double a = 0.0, b = 0.0;
         for (int i = 0; i < 6 * F; ++i) a += dtheta[i] * dtheta[i];
         for (int n = 0; n < N; ++n) b += dd[n] * dd[n];
