@@ -108,6 +108,14 @@ typedef struct {
                                 system is definite) and keeps the exact gauge constraint
                                 t_a . Delta t_a = 0. pba_get_system returns the undamped
                                 blocks and the S that was factorised. */
+    int photometric;         /* non-zero: affine brightness per target frame (an option
+                                beyond the paper, whose Sec. 2 notes that direct methods
+                                must model lighting): residual r = I_0 - (alpha_f I_f +
+                                beta_f); after every IC/FC step each frame's pair is set
+                                from that step's residuals so that the warped samples
+                                take the template's Huber-weighted mean and spread
+                                (alpha = sqrt(var I_0 / var v), beta = mean I_0 - alpha
+                                mean v). Pairs start at (1, 0); see pba_get_brightness. */
 } pba_config;
 
 /* Statistics of one iteration (Sec. 4.1): Huber energy, RMS and count of the
@@ -258,6 +266,13 @@ pba_status pba_last_timing(pba_ctx* ctx, double* out);
  * flags are 0 were solved normally (bundles never share a sum). flags: host,
  * n_bundles ints. */
 pba_status pba_bundle_errors(pba_ctx* ctx, int* flags);
+
+/* Affine brightness pairs of a bundle's frames: ab host, F_b x 2 doubles
+ * (alpha_f, beta_f; frame 0 is (1, 0)), stored as FP32 on the device. They
+ * are used in every residual (an identity pair changes nothing) and fitted
+ * by the steps when cfg.photometric is set. */
+pba_status pba_get_brightness(pba_ctx* ctx, int bundle, double* ab);
+pba_status pba_set_brightness(pba_ctx* ctx, int bundle, const double* ab);
 
 /* Launch shapes in use (after autotuning, or the defaults 8 and the largest
  * cluster the device co-schedules): res_warps = warps per CTA of the IC

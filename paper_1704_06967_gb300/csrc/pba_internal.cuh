@@ -28,7 +28,10 @@ namespace pba {
 constexpr int kTile = 32;             // points per tile (= lanes of a warp)
 constexpr int kPassWarps = 4;         // warps per CTA of the pass kernels
 constexpr int kFrameConst = 64;       // floats of FP32 constants per frame
-constexpr int kEntryPartial = 40;     // floats of partial sums per entry (FC: 21 H_ff, 6 g_f, 6 corrections)
+constexpr int kEntryPartial = 44;     // floats of partial sums per entry (FC: 21 H_ff, 6 g_f, 6 corrections)
+constexpr int kPhotoColIc = 12;       // brightness fit sums of an entry (IC), 5 floats, 16-byte aligned
+constexpr int kPhotoColFc = 36;       // the same for FC
+constexpr int kFrameAlpha = 60;       // frame constants [60], [61]: affine brightness alpha, beta
 constexpr int kStats = 8;             // doubles per statistics slot
 
 // device error word values (bit flags); the error words are err[0] for the

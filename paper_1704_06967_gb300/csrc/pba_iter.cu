@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(WARPS * 32, (PMAX <= 8 ? 32 : 16) / WARPS)
 ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float* __restrict__ fprev,
                    const float* __restrict__ dcur, const float* __restrict__ dprev,
                    const float4* __restrict__ J4, float* __restrict__ ent_part,
-                   float* __restrict__ gpart, float4* __restrict__ estats, int have_prev)
+                   float* __restrict__ gpart, float4* __restrict__ estats, int have_prev, int photo)
 {
     const int lane = threadIdx.x & 31;
     const int e = blockIdx.x * WARPS + (threadIdx.x >> 5);
@@ -213,10 +213,12 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
     const int P = pb.P;
     const float k = pb.huber_k;
     float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // g_f (6), energy, r^2, count
+    float ph[5] = {0, 0, 0, 0, 0};               // brightness fit sums (w, w v, w v^2, w I_0, w I_0^2)
     float gp = 0.0f, disp = 0.0f;
     if ((en.mask >> lane) & 1u) {
         const int n = en.tile * kTile + lane;
         const float* c = fconst + (size_t)en.f * kFrameConst;
+        const float alpha = c[kFrameAlpha], beta = c[kFrameAlpha + 1];
         const float d = dcur[n];
         const float2 xc = pb.xn[n];
         float I0[PMAX];
@@ -262,11 +264,20 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
         for (int j = 0; j < PMAX; ++j) {
             wr[j] = 0.0f;
             if (j < P && ((ok >> j) & 1u)) {
-                const float r = I0[j] - val[j];
+                // affine brightness: the template sees alpha I_f + beta (1, 0: exact no-op)
+                const float r = I0[j] - fmaf(alpha, val[j], beta);
                 acc[6] += huber_rho(r, k);
                 acc[7] = fmaf(r, r, acc[7]);
                 acc[8] += 1.0f;
                 wr[j] = fabsf(r) <= k ? r : copysignf(k, r);
+                if (kAccum && photo) {
+                    const float w = huber_w(r, k);
+                    ph[0] += w;
+                    ph[1] = fmaf(w, val[j], ph[1]);
+                    ph[2] = fmaf(w * val[j], val[j], ph[2]);
+                    ph[3] = fmaf(w, I0[j], ph[3]);
+                    ph[4] = fmaf(w * I0[j], I0[j], ph[4]);
+                }
             }
         }
         if (kAccum) {
@@ -315,6 +326,7 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
     if (kAccum) {
         gpart[(size_t)e * kTile + lane] = gp;
         warp_sum<9>(acc);
+        if (photo) warp_sum<5>(ph);
     } else {
         float st[3] = {acc[6], acc[7], acc[8]};
         warp_sum<3>(st);
@@ -328,6 +340,9 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
             float* o = ent_part + (size_t)pb.entry_slot[e] * kEntryPartial;
 #pragma unroll
             for (int a = 0; a < 6; ++a) o[a] = acc[a];
+            if (photo)
+#pragma unroll
+                for (int a = 0; a < 5; ++a) o[kPhotoColIc + a] = ph[a];
         }
         estats[e] = make_float4(acc[6], acc[7], acc[8], disp);
     }
@@ -351,7 +366,7 @@ __global__ void __launch_bounds__(kResWarps * 32, 2)
 fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float* __restrict__ fprev,
                    const float* __restrict__ dcur, const float* __restrict__ dprev,
                    float* __restrict__ Hfd_out, float* __restrict__ ent_part,
-                   float* __restrict__ gpart, float4* __restrict__ estats, int have_prev)
+                   float* __restrict__ gpart, float4* __restrict__ estats, int have_prev, int photo)
 {
     const int lane = threadIdx.x & 31;
     const int e = blockIdx.x * kResWarps + (threadIdx.x >> 5);
@@ -366,10 +381,12 @@ fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
     for (int q = 0; q < 27; ++q) acc[q] = 0.0f;
     float hfd[6] = {0, 0, 0, 0, 0, 0};
     float st[3] = {0, 0, 0};
+    float ph[5] = {0, 0, 0, 0, 0};  // brightness fit sums (w, w v, w v^2, w I_0, w I_0^2)
     float gp = 0.0f, hnn = 0.0f, disp = 0.0f;
     if ((en.mask >> lane) & 1u) {
         const int n = en.tile * kTile + lane;
         const float* c = fconst + (size_t)en.f * kFrameConst;
+        const float alpha = c[kFrameAlpha], beta = c[kFrameAlpha + 1];
         const float d = dcur[n];
         const float2 xc = pb.xn[n];
         const float qcx = fmaf(c[0], xc.x, fmaf(c[1], xc.y, fmaf(d, c[9], c[2])));
@@ -426,18 +443,26 @@ fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
                             const float gxb = fmaf(wa[jj], __ldg(GX + W + 1) - __ldg(GX + W), __ldg(GX + W));
                             const float gyt = fmaf(wa[jj], __ldg(GY + 1) - __ldg(GY), __ldg(GY));
                             const float gyb = fmaf(wa[jj], __ldg(GY + W + 1) - __ldg(GY + W), __ldg(GY + W));
-                            gxv[jj] = fmaf(wb[jj], gxb - gxt, gxt) * pb.fx;
-                            gyv[jj] = fmaf(wb[jj], gyb - gyt, gyt) * pb.fy;
+                            gxv[jj] = fmaf(wb[jj], gxb - gxt, gxt) * (pb.fx * alpha);
+                            gyv[jj] = fmaf(wb[jj], gyb - gyt, gyt) * (pb.fy * alpha);
                         }
                     }
                 }
 #pragma unroll
                 for (int jj = 0; jj < kFcGroup; ++jj) {
                     if (g + jj < P && ((ok >> jj) & 1u)) {
-                        const float r = I0[jj] - val[jj];
+                        const float r = I0[jj] - fmaf(alpha, val[jj], beta);
                         st[0] += huber_rho(r, k);
                         st[1] = fmaf(r, r, st[1]);
                         st[2] += 1.0f;
+                        if (kAccum && photo) {
+                            const float w = huber_w(r, k);
+                            ph[0] += w;
+                            ph[1] = fmaf(w, val[jj], ph[1]);
+                            ph[2] = fmaf(w * val[jj], val[jj], ph[2]);
+                            ph[3] = fmaf(w, I0[jj], ph[3]);
+                            ph[4] = fmaf(w * I0[jj], I0[jj], ph[4]);
+                        }
                         if (kAccum) {
                             const float c0 = -gxv[jj] * iz[jj], c1 = -gyv[jj] * iz[jj];
                             const float c2 = (gxv[jj] * qx[jj] + gyv[jj] * qy[jj]) * iz[jj] * iz[jj];
@@ -490,6 +515,7 @@ fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
         gpart[(size_t)e * 2 * kTile + lane] = gp;
         gpart[(size_t)e * 2 * kTile + kTile + lane] = hnn;
         warp_sum<27>(acc);
+        if (photo) warp_sum<5>(ph);
     }
     warp_sum<3>(st);
     disp = warp_max1(disp);
@@ -498,6 +524,9 @@ fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
             float* o = ent_part + (size_t)pb.entry_slot[e] * kEntryPartial;
 #pragma unroll
             for (int q = 0; q < 27; ++q) o[q] = acc[q];
+            if (photo)
+#pragma unroll
+                for (int a = 0; a < 5; ++a) o[kPhotoColFc + a] = ph[a];
         }
         estats[e] = make_float4(st[0], st[1], st[2], disp);
     }
@@ -606,6 +635,10 @@ ic_solve_kernel(SolveArgs a, const dfloat* __restrict__ Sinv, const double* __re
     y += (size_t)6 * bd.fo;
     pdl_trigger();
     pdl_wait();
+    // the frame's brightness pair from this step's residuals (the next
+    // residual pass reads it)
+    if (a.photo_sums && f > 0 && threadIdx.x == 0)
+        photo_update_frame(a.photo_sums + (size_t)5 * fg, a.fc + (size_t)fg * kFrameConst);
     // the reference frame of a bundle (f = 0) and frames without residuals
     // get a zero update
     const int kf = f > 0 ? cmap[f] : -1, nc = 6 * cmap[F], anchor = a.active[bd.fo];
@@ -675,7 +708,7 @@ static cudaError_t ic_residual_w(const LaunchCtx& L, int have_prev)
     const int blocks = (L.pb.E + WARPS - 1) / WARPS;
     return launch_pdl(ic_residual_kernel<PMAX, A, DT, WARPS>, blocks, WARPS * 32, 0, L.stream, L.pb, L.fs.fc,
                       L.fs.fc_prev, L.it.dcur, L.it.dprev, L.ic.J4, L.ent_part, L.it.gpart, L.it.estats,
-                      have_prev);
+                      have_prev, L.photo);
 }
 
 // warps (entries) per CTA: the autotuner's choice for the accumulating pass
@@ -710,7 +743,7 @@ static cudaError_t fc_residual_p(const LaunchCtx& L, int have_prev)
     const int blocks = (L.pb.E + kResWarps - 1) / kResWarps;
     return launch_pdl(fc_residual_kernel<PMAX, A, DT>, blocks, kResWarps * 32, 0, L.stream, L.pb, L.fs.fc,
                       L.fs.fc_prev, L.it.dcur, L.it.dprev, L.Hfd_fc, L.ent_part, L.it.gpart, L.it.estats,
-                      have_prev);
+                      have_prev, L.photo);
 }
 
 cudaError_t launch_fc_residual(const LaunchCtx& L, bool accum, int have_prev)
@@ -747,7 +780,7 @@ cudaError_t launch_fc_point(const LaunchCtx& L, bool accum)
 // FP64 poses (set-up and pba_set_params), one warp per frame: the same
 // arithmetic as the pose updates, so a state restored from its FP64
 // parameters continues exactly as the uninterrupted run.
-__global__ void frame_consts_kernel(SolveArgs a, int f0, int nf)
+__global__ void frame_consts_kernel(SolveArgs a, int f0, int nf, int init_photo)
 {
     __shared__ double sh[4][12];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, f = f0 + blockIdx.x * 4 + w;
@@ -756,12 +789,13 @@ __global__ void frame_consts_kernel(SolveArgs a, int f0, int nf)
     if (lane < 12) p[lane] = a.poses64[12 * f + lane];
     __syncwarp();
     write_frame_lanes(a, f, p, p, p + 9, lane);
+    if (init_photo && lane < 2) a.fc[(size_t)f * kFrameConst + kFrameAlpha + lane] = lane == 0 ? 1.0f : 0.0f;
 }
 
-cudaError_t launch_frame_consts(const SolveArgs& a, int f0, int nf, cudaStream_t st)
+cudaError_t launch_frame_consts(const SolveArgs& a, int f0, int nf, cudaStream_t st, int init_photo)
 {
     if (nf <= 0) return cudaSuccess;
-    frame_consts_kernel<<<(nf + 3) / 4, 128, 0, st>>>(a, f0, nf);
+    frame_consts_kernel<<<(nf + 3) / 4, 128, 0, st>>>(a, f0, nf, init_photo);
     return cudaGetLastError();
 }
 

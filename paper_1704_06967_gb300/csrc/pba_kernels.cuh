@@ -82,6 +82,7 @@ struct LaunchCtx {
     const double* poses0;  // F*12 FP64 poses at p_0
     cudaStream_t stream;
     int res_warps;         // warps per CTA of the accumulating IC residual pass (4, 8, 16)
+    int photo;             // affine brightness fit on: the residual passes write its sums
 };
 
 // IC precompute of the entries of the frames with todo[f] != 0 (all when
@@ -130,13 +131,30 @@ struct SolveArgs {
     const int* cmap;        // per bundle at co: [f] compact index of an active frame or -1,
                             // [F_b] their number
     const double* tanchor;  // F*12 poses whose t define the gauge direction
+    const double* photo_sums;  // F*5 brightness fit sums of the step (null: model off)
 };
+
+// Affine brightness of frame f from its fit sums (w, w v, w v^2, w I_0,
+// w I_0^2): v takes the template's weighted mean and spread,
+// alpha = sqrt(var(I_0) / var(v)), beta = mean(I_0) - alpha mean(v); the
+// pair is kept without residuals or without spread (FP64).
+__device__ inline void photo_update_frame(const double* s, float* fc_f)
+{
+    if (!(s[0] > 0.0)) return;
+    const double mv = s[1] / s[0], m0 = s[3] / s[0];
+    const double vv = s[2] / s[0] - mv * mv, v0 = s[4] / s[0] - m0 * m0;
+    if (!(vv > 1e-12) || !(v0 > 1e-12)) return;
+    const double alpha = sqrt(v0 / vv);
+    fc_f[kFrameAlpha] = (float)alpha;
+    fc_f[kFrameAlpha + 1] = (float)(m0 - alpha * mv);
+}
 
 // depth back-substitution (when apply) of the last update and, in extra
 // CTAs, every frame's pose update with it (a.active / tanchor unused)
 cudaError_t launch_depth_update(const LaunchCtx& L, const SolveArgs& a, bool ic_rule, int apply);
-// FP32 constants and previous R|t of frames [f0, f0 + nf) from a.poses64
-cudaError_t launch_frame_consts(const SolveArgs& a, int f0, int nf, cudaStream_t st);
+// FP32 constants and previous R|t of frames [f0, f0 + nf) from a.poses64;
+// init_photo also resets their brightness pairs to (1, 0)
+cudaError_t launch_frame_consts(const SolveArgs& a, int f0, int nf, cudaStream_t st, int init_photo = 0);
 cudaError_t launch_ic_point(const LaunchCtx& L, bool accum);
 cudaError_t launch_fc_point(const LaunchCtx& L, bool accum);
 // Dtheta = -S^-1 y (per bundle the compact S^-1 at so, y per global frame as

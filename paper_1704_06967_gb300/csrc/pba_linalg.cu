@@ -189,6 +189,10 @@ __global__ void __launch_bounds__(kFcSolveWarps * 32) fc_solve_update_kernel(Sol
     Linv += bd.lo;
     double* x = reinterpret_cast<double*>(xs + a.n6);
     const int n = 6 * (F - 1), nc = 6 * cmap[F], tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // the brightness pairs from this step's residuals
+    if (a.photo_sums)
+        for (int f = 1 + tid; f < F; f += blockDim.x)
+            photo_update_frame(a.photo_sums + (size_t)5 * (fo + f), a.fc + (size_t)(fo + f) * kFrameConst);
     for (int i = tid; i < nc; i += blockDim.x) xs[i] = L[(size_t)nc * nc + i];
     __syncthreads();
     ldl_backward_smem(L, Linv, nc, xs, tb);

@@ -122,7 +122,7 @@ ic_precompute_kernel(DevProblem pb, const float* __restrict__ fconst, const doub
                     if (j < P && ((ok >> jj) & 1u)) {
                         const float a0 = ax + c[12 + 3 * j], a1 = ay + c[13 + 3 * j], a2 = az + c[14 + 3 * j];
                         const float qz = fmaf(d0, t0z, a2);
-                        const float r0 = I0[jj] - val[jj];
+                        const float r0 = I0[jj] - fmaf(c[kFrameAlpha], val[jj], c[kFrameAlpha + 1]);
                         const float w0 = huber_w(r0, k);
                         const float x = xc.x + pb.pat[2 * j] / pb.fx, y = xc.y + pb.pat[2 * j + 1] / pb.fy;
                         const float zb = qz / d0;
@@ -275,6 +275,7 @@ cudaError_t launch_frame_reduce(const LaunchCtx& L, int off, int ncomp, double* 
                L.dthsq, L.stats, slot_cur, slot_prev, nfb)
     if (!frames || (ncomp == 6 && sub == 6 && sub_from == 0)) return PBA_R(6, 6, 0);
     if (ncomp == 21 && sub < 0) return PBA_R(21, -1, 0);
+    if (ncomp == 5 && sub < 0) return PBA_R(5, -1, 0);
     if (ncomp == 27 && sub == 27 && sub_from == 21) return PBA_R(27, 27, 21);
     return cudaErrorInvalidValue;
 #undef PBA_R

@@ -131,7 +131,7 @@ struct pba_ctx {
         float2* G0p;
         float4* estats;
         double *poses64, *poses0_64, *dtheta64;
-        double *red_ic, *red_y;
+        double *red_ic, *red_y, *red_photo;
         double *Soff, *S_ic, *S_fc;
         dfloat* Sinv2;  // IC S^-1 over the active frames (double-float, compact)
         dfloat *A2, *L2, *Linv, *dpiv, *rpiv;  // double-float factorisation (IC and FC in turn)
@@ -363,6 +363,7 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.dtheta64, F * 6 * 8);
     take(c->d.red_ic, F * 21 * 8);
     take(c->d.red_y, F * 27 * 8);
+    take(c->d.red_photo, F * 5 * 8);
     take(c->d.Soff, (size_t)c->n_so * 8);
     take(c->d.S_ic, (size_t)c->n_so * 8);
     take(c->d.Sinv2, (size_t)c->n_so * sizeof(dfloat));
@@ -532,11 +533,11 @@ SolveArgs make_solve(pba_ctx* c);
 
 // Uploads the parameters of bundle b (poses F_b*12, depths in the caller's
 // point order, nullable); the FP32 pass constants are formed on the device.
-pba_status upload_params(pba_ctx* ctx, int bi, const double* poses, const double* depth)
+pba_status upload_params(pba_ctx* ctx, int bi, const double* poses, const double* depth, int init_photo = 0)
 {
     const BundleIn& b = ctx->bun[bi];
     CK(h2d(ctx, ctx->d.poses64 + (size_t)12 * b.fo, poses, sizeof(double) * 12 * b.F));
-    CK(launch_frame_consts(make_solve(ctx), b.fo, b.F, ctx->stream));
+    CK(launch_frame_consts(make_solve(ctx), b.fo, b.F, ctx->stream, init_photo));
     if (depth) {
         std::vector<double> ds(b.perm.size(), 1.0);
         for (size_t i = 0; i < ds.size(); ++i)
@@ -622,6 +623,7 @@ LaunchCtx make_launch(pba_ctx* c)
     L.poses0 = c->d.poses0_64;
     L.stream = c->stream;
     L.res_warps = c->res_warps;
+    L.photo = c->cfg.photometric != 0;
     return L;
 }
 
@@ -988,7 +990,7 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     CK(h2d(ctx, ctx->d.pair_items, ctx->pair_items.data(), sizeof(int2) * ctx->pair_items.size()));
     for (int bi = 0; bi < ctx->B; ++bi) {
         const BundleIn& b = ctx->bun[bi];
-        pba_status s = upload_params(ctx, bi, b.poses_init.data(), b.d_init.data());
+        pba_status s = upload_params(ctx, bi, b.poses_init.data(), b.d_init.data(), 1);
         if (s != PBA_OK) return s;
         CK(h2d(ctx, ctx->d.poses0_64 + (size_t)12 * b.fo, b.poses_init.data(), sizeof(double) * 12 * b.F));
     }
@@ -1198,12 +1200,16 @@ pba_status pba_iterate(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     sa.active = ctx->d.active_ic;
     sa.tanchor = ctx->d.poses0_64;
     sa.cmap = ctx->d.cmap_ic;
+    sa.photo_sums = ctx->cfg.photometric ? ctx->d.red_photo : nullptr;
     pba_status s = run_enqueued(ctx, GraphKey{G_ITERATE, n_iters, ctx->timing}, [&]() -> pba_status {
         for (int k = 0; k < n_iters; ++k) {
             LAUNCH(TS_POINT, launch_depth_update(L, sa, true, k > 0));
             LAUNCH(TS_PASS, launch_ic_residual(L, true, k > 0));
             LAUNCH(TS_POINT, launch_ic_point(L, true));
             LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 6, ctx->d.red_y, k, k - 1, true, 6));
+            if (ctx->cfg.photometric)
+                LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 5, ctx->d.red_photo, -1, -1, true, -1, 0,
+                                                      ctx->d.ent_part + kPhotoColIc));
             LAUNCH(TS_SOLVE, launch_ic_solve(sa, ctx->d.Sinv2, ctx->d.red_y, ctx->stream));
         }
         LAUNCH(TS_EVAL, launch_depth_update(L, sa, true, n_iters > 0));
@@ -1232,6 +1238,7 @@ pba_status pba_solve_ic(pba_ctx* ctx, int n_iters, int reanchor_every, pba_iter_
     sa.active = ctx->d.active_ic;
     sa.tanchor = ctx->d.poses0_64;
     sa.cmap = ctx->d.cmap_ic;
+    sa.photo_sums = ctx->cfg.photometric ? ctx->d.red_photo : nullptr;
     pba_status s = run_enqueued(ctx, GraphKey{G_SOLVE, n_iters | (m << 16), ctx->timing}, [&]() -> pba_status {
         pba_status q = precompute_body(ctx);
         if (q != PBA_OK) return q;
@@ -1252,6 +1259,9 @@ pba_status pba_solve_ic(pba_ctx* ctx, int n_iters, int reanchor_every, pba_iter_
             LAUNCH(TS_PASS, launch_ic_residual(L, true, k > 0));
             LAUNCH(TS_POINT, launch_ic_point(L, true));
             LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 6, ctx->d.red_y, k, k - 1, true, 6));
+            if (ctx->cfg.photometric)
+                LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 5, ctx->d.red_photo, -1, -1, true, -1, 0,
+                                                      ctx->d.ent_part + kPhotoColIc));
             LAUNCH(TS_SOLVE, launch_ic_solve(sa, ctx->d.Sinv2, ctx->d.red_y, ctx->stream));
         }
         LAUNCH(TS_EVAL, launch_depth_update(L, sa, true, n_iters > 0));
@@ -1283,12 +1293,16 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     sa.active = ctx->d.active_fc;
     sa.tanchor = ctx->d.poses64;
     sa.cmap = ctx->d.cmap_fc;
+    sa.photo_sums = ctx->cfg.photometric ? ctx->d.red_photo : nullptr;
     pba_status s = run_enqueued(ctx, GraphKey{G_FC, n_iters, ctx->timing}, [&]() -> pba_status {
         for (int k = 0; k < n_iters; ++k) {
             LAUNCH(TS_POINT, launch_depth_update(L, sa, false, k > 0));
             LAUNCH(TS_PASS, launch_fc_residual(L, true, k > 0));
             LAUNCH(TS_POINT, launch_fc_point(L, true));
             LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 27, ctx->d.red_y, k, k - 1, true, 27, 21));
+            if (ctx->cfg.photometric)
+                LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 5, ctx->d.red_photo, -1, -1, true, -1, 0,
+                                                      ctx->d.ent_part + kPhotoColFc));
             LAUNCHN(TS_SCHUR, launch_schur_sparse(L.pb, ctx->d.Hfd_fc, ctx->d.Hnn_fc, schur_lists(ctx),
                                                   ctx->d.schur_part, ctx->d.Soff, ctx->stream, &nl));
             LAUNCH(TS_SCHUR, launch_assemble_S(bs, ctx->d.red_y, 27, ctx->d.Soff, ctx->d.poses64,
@@ -1460,6 +1474,37 @@ pba_status pba_propose_depths(pba_ctx* ctx, int bundle, const void* packed, floa
     CK(launch_mlp_propose(ctx->d.slot_caller, kTile * b.to, kTile * b.T, scratch, y, ctx->d.d64, ctx->stream));
     ctx->ic_ready = false;  // p_0 changes: the precompute must run again
     return check_device_error(ctx);
+}
+
+pba_status pba_get_brightness(pba_ctx* ctx, int bundle, double* ab)
+{
+    CHECK_BUNDLE();
+    if (!ab) return fail(ctx, PBA_ERR_ARG, "null output");
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    const BundleIn& b = ctx->bun[bundle];
+    std::vector<float> h((size_t)b.F * kFrameConst);
+    CK(d2h(ctx, h.data(), ctx->d.fc + (size_t)kFrameConst * b.fo, sizeof(float) * h.size()));
+    for (int f = 0; f < b.F; ++f) {
+        ab[2 * f] = h[(size_t)f * kFrameConst + kFrameAlpha];
+        ab[2 * f + 1] = h[(size_t)f * kFrameConst + kFrameAlpha + 1];
+    }
+    return PBA_OK;
+}
+
+pba_status pba_set_brightness(pba_ctx* ctx, int bundle, const double* ab)
+{
+    CHECK_BUNDLE();
+    if (!ab) return fail(ctx, PBA_ERR_ARG, "null pairs");
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    const BundleIn& b = ctx->bun[bundle];
+    for (int i = 0; i < 2 * b.F; ++i)
+        if (!std::isfinite(ab[i])) return fail(ctx, PBA_ERR_ARG, "non-finite brightness");
+    for (int f = 0; f < b.F; ++f) {
+        const float v[2] = {(float)ab[2 * f], (float)ab[2 * f + 1]};
+        CK(h2d(ctx, ctx->d.fc + (size_t)kFrameConst * (b.fo + f) + kFrameAlpha, v, sizeof v));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PBA_OK;
 }
 
 pba_status pba_bundle_errors(pba_ctx* ctx, int* flags)

@@ -39,7 +39,8 @@ class Config(ctypes.Structure):
                 ("pattern", ctypes.POINTER(ctypes.c_int32)), ("gauge_anchor_w", ctypes.c_double),
                 ("conv_px", ctypes.c_double), ("n_bundles", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("use_graphs", ctypes.c_int),
-                ("max_stats_iters", ctypes.c_int), ("autotune", ctypes.c_int), ("damping", ctypes.c_double)]
+                ("max_stats_iters", ctypes.c_int), ("autotune", ctypes.c_int), ("damping", ctypes.c_double),
+                ("photometric", ctypes.c_int)]
 
 
 class IterStats(ctypes.Structure):
@@ -76,6 +77,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pba_solve_ic": ([vp, i, i, vp], i),
         "pba_set_window": ([vp, i, vp], i),
         "pba_downsample": ([vp, i, i, i, i, i, vp, vp], i),
+        "pba_get_brightness": ([vp, i, vp], i),
+        "pba_set_brightness": ([vp, i, vp], i),
         "pba_update_ic": ([vp], i),
         "pba_get_params": ([vp, i, vp, vp], i),
         "pba_set_params": ([vp, i, vp, vp], i),
@@ -134,7 +137,7 @@ class Batch:
     """
 
     def __init__(self, items, *, pattern, huber_k, stream=None, gauge_anchor_w=1.0, max_stats_iters=256,
-                 use_graphs=False, autotune=False, damping=0.0):
+                 use_graphs=False, autotune=False, damping=0.0, photometric=False):
         import torch
         self.torch = torch
         lib = load()
@@ -149,7 +152,7 @@ class Batch:
         cfg = Config(float(huber_k), pat.shape[0],
                      pat.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), float(gauge_anchor_w),
                      0.0, self.B, ctypes.c_void_p(stream.cuda_stream), int(bool(use_graphs)),
-                     int(max_stats_iters), int(bool(autotune)), float(damping))
+                     int(max_stats_iters), int(bool(autotune)), float(damping), int(bool(photometric)))
         h = ctypes.c_void_p()
         self.h = None
         self._check(lib.pba_create(ctypes.byref(cfg), ctypes.byref(h)), None)
@@ -235,6 +238,17 @@ class Batch:
         """IC iterations; returns stats [n+1, 6] (energy, rms, n_valid,
         max_disp_px, dtheta_norm, dd_norm) or None."""
         return self._stats(self.lib.pba_iterate, n_iters, stats)
+
+    def brightness(self, bundle=0):
+        """Affine brightness pairs [F_b, 2] (alpha_f, beta_f)."""
+        ab = np.zeros((self.Fs[bundle], 2))
+        self._check(self.lib.pba_get_brightness(self.h, bundle, _p(ab)))
+        return ab
+
+    def set_brightness(self, ab, bundle=0):
+        ab = np.ascontiguousarray(ab, dtype=np.float64)
+        assert ab.shape == (self.Fs[bundle], 2)
+        self._check(self.lib.pba_set_brightness(self.h, bundle, _p(ab)))
 
     def set_window(self, in_window, bundle=0):
         """Frames of the bundle in the sliding window (F_b flags)."""

@@ -73,6 +73,11 @@ def solve_coarse_to_fine(images, poses0, intrinsics, uv, inv_depth, vis, *, patt
         p, d = b.params()
         b.close()
         poses = p
-        depth[keep] = d
+        # a point the level drove to a non-positive inverse depth keeps the
+        # one it entered the level with
+        sub = depth[keep]
+        good = np.isfinite(d) & (d > 0)
+        sub[good] = d[good]
+        depth[keep] = sub
         stats.append(st)
     return poses, depth, stats

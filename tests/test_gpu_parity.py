@@ -496,3 +496,66 @@ def test_window_update_equals_a_full_precompute_with_the_same_anchors(torch_cuda
     a.iterate(2)
     a.close()
     b.close()
+
+
+# ----------------------------------------------------------------------------
+# affine brightness per frame (cfg.photometric)
+# ----------------------------------------------------------------------------
+_ALPHAS = np.r_[1.0, 0.75, 1.25, 0.8, 1.2, 0.9]
+_BETAS = np.r_[0.0, 0.06, -0.05, 0.04, -0.06, 0.03]
+
+
+def _relit_small():
+    sc = synth.make_scene("small")
+    imgs = sc.images_f32.astype(np.float64).copy()
+    for f in range(1, sc.F):
+        imgs[f] = (imgs[f] - _BETAS[f]) / _ALPHAS[f]
+    return sc, imgs.astype(np.float32)
+
+
+@pytest.mark.parametrize("method", ["ic", "fc"])
+def test_brightness_steps_match_oracle(torch_cuda, method):
+    torch = torch_cuda
+    from paper_1704_06967_gb300 import Bundle
+    sc, imgs = _relit_small()
+    pb = oracle.Problem(imgs, sc.uv, sc.pattern, sc.vis, sc.intrinsics, sc.huber_k, photometric=True)
+    b = Bundle(torch.tensor(imgs, device="cuda"), sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis,
+               pattern=sc.pattern, huber_k=sc.huber_k, photometric=True)
+    pre = None
+    if method == "ic":
+        b.precompute_ic()
+        pre = oracle.ic_precompute(pb, sc.poses0, sc.depths0)
+    P, D = sc.poses0.copy(), sc.depths0.copy()
+    for k in range(3):
+        ab = b.brightness()  # FP32 on the device: give the oracle the same pair
+        pb.photo[:] = ab.ravel()
+        b.set_params(P, D)
+        if method == "ic":
+            b.iterate(1)
+            o_dth, o_dd, P1, D1, _ = oracle.ic_step(pb, pre, sc.poses0, sc.depths0, P, D)
+        else:
+            b.solve_fc(1)
+            o_dth, o_dd, P1, D1, _ = oracle.fc_step(pb, P, D)
+        dth, dd = b.last_update()
+        ref0 = np.linalg.norm(np.concatenate([o_dth[1:].ravel(), o_dd]))
+        assert _step_err(dth, dd, o_dth, o_dd, ref0) <= STEP_TOL, (method, k)
+        got = b.brightness()
+        assert np.abs(got.ravel() - pb.photo).max() <= 1e-4 * np.abs(pb.photo).max(), (method, k)
+        P, D = P1, D1
+    b.close()
+
+
+def test_brightness_model_lowers_the_cost_under_relighting(torch_cuda):
+    torch = torch_cuda
+    from paper_1704_06967_gb300 import Bundle
+    sc, imgs = _relit_small()
+    rms = {}
+    for on in (False, True):
+        b = Bundle(torch.tensor(imgs, device="cuda"), sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis,
+                   pattern=sc.pattern, huber_k=sc.huber_k, photometric=on)
+        rms[on] = b.solve_fc(10)[-1, 1]
+        if on:
+            ab = b.brightness()
+            assert np.abs(ab[1:, 0] - _ALPHAS[1:]).max() < 0.05
+        b.close()
+    assert rms[True] < 0.5 * rms[False], rms
