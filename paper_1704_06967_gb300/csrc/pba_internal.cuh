@@ -100,6 +100,11 @@ struct DevProblem {
 // anything an earlier kernel wrote (the wait returns once the previous grid
 // has completed and its memory is visible, and at once for an ordinary
 // launch). pdl_trigger() lets the next such kernel be scheduled early.
+// Every kernel triggers at its start, so a kernel's code before its wait may
+// run beside any earlier kernel of the chain back to the last ordinary
+// launch or copy on the stream: there it reads only data that no kernel of
+// the chain writes (the set-up's topology; in IC the J, H and S^-1 that the
+// precompute, which ends with an ordinary launch, fixed).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }

@@ -72,8 +72,8 @@ depth_update_kernel(DevProblem pb, DepthState ds, const float2* __restrict__ dth
     __shared__ float2 red[kTileWarps][32];
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     pdl_trigger();
-    pdl_wait();
     if (t >= pb.T) {
+        pdl_wait();
         // CTA T + f - 1: pose update of frame f with the update the solve
         // wrote (FP64; one frame per CTA, spread over the SMs)
         __shared__ double sh[54], d[6];
@@ -92,43 +92,78 @@ depth_update_kernel(DevProblem pb, DepthState ds, const float2* __restrict__ dth
         return;
     }
     const int n = t * kTile + lane;
-    // warp 0's per-point operands, fetched before the entry loop so their
-    // latency overlaps it
+    const int e0 = pb.tile_entry[t], ne = pb.tile_entry[t + 1] - e0, cnt0 = min(32, ne);
+    // Before the wait: the tile's entry records and, for IC, what the
+    // precompute fixed (H_fd rows of each warp's first kDepthPre entries,
+    // H_dd, 1/H_dd, d_0, 1/d_0); no kernel of the iteration writes them.
+    constexpr int kDepthPre = 4;
     double d = 0.0, d0 = 0.0, ih = 0.0, id0 = 0.0;
     float gn = 0.0f, hnn = 0.0f;
     bool valid = false;
-    if (warp == 0) {
-        d = ds.d64[n];
-        if (apply) {
-            gn = ds.gn[n];
-            hnn = ds.Hnn[n];
+    Entry mine = {0, 0u, 0, 0};
+    float hpre[kDepthPre][6];
+    if (apply) {
+        if (lane < ne) mine = pb.entries[e0 + lane];
+        if (warp == 0) {
             valid = pb.valid_pt[n];
             if (kIcRule) {
+                hnn = ds.Hnn[n];
                 d0 = ds.d0_64[n];
                 ih = inv_hnn[n];
                 id0 = inv_d0[n];
             }
         }
+        if (kIcRule) {
+#pragma unroll
+            for (int r = 0; r < kDepthPre; ++r) {
+                const int i = warp + kTileWarps * r;
+                const unsigned mask = __shfl_sync(0xffffffffu, mine.mask, i);
+                const int po = __shfl_sync(0xffffffffu, mine.pair_off, i);
+                const bool vis = i < cnt0 && ((mask >> lane) & 1u);
+                const int nvis = __popc(mask);
+                const float* h = ds.Hfd + (size_t)po * 6 + (vis ? rank_of(mask, lane) : 0);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) hpre[r][k] = vis ? h[k * nvis] : 0.0f;
+            }
+        }
+    }
+    pdl_wait();
+    if (warp == 0) {
+        d = ds.d64[n];
+        if (apply) {
+            gn = ds.gn[n];
+            if (!kIcRule) hnn = ds.Hnn[n];
+        }
     }
     if (apply) {
-        const int e0 = pb.tile_entry[t], ne = pb.tile_entry[t + 1] - e0;
         float s = 0.0f, c = 0.0f;
-        for (int b = 0; b < ne; b += 32) {
-            Entry mine = {0, 0u, 0, 0};
+        // entry i of the current batch (hv: its prefetched H_fd values, or
+        // null to load them)
+        auto add_entry = [&](int i, const float* hv) {
+            const int f = __shfl_sync(0xffffffffu, mine.f, i);
+            const unsigned mask = __shfl_sync(0xffffffffu, mine.mask, i);
+            const int po = __shfl_sync(0xffffffffu, mine.pair_off, i);
+            const bool vis = (mask >> lane) & 1u;
+            const int nvis = __popc(mask);
+            const float* h = ds.Hfd + (size_t)po * 6 + (vis ? rank_of(mask, lane) : 0);
+            const float2* th = dth2 + 6 * f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) dot_pair_add(s, c, vis ? (hv ? hv[k] : h[k * nvis]) : 0.0f, th[k]);
+        };
+        int i = warp;
+        if (kIcRule) {
+#pragma unroll
+            for (int r = 0; r < kDepthPre; ++r, i += kTileWarps)
+                if (i < cnt0) add_entry(i, hpre[r]);
+        }
+#pragma unroll 2
+        for (; i < cnt0; i += kTileWarps) add_entry(i, nullptr);
+        for (int b = 32; b < ne; b += 32) {
+            mine = Entry{0, 0u, 0, 0};
             if (b + lane < ne) mine = pb.entries[e0 + b + lane];
             const int cnt = min(32, ne - b);
 #pragma unroll 2
-            for (int i = warp; i < cnt; i += kTileWarps) {
-                const int f = __shfl_sync(0xffffffffu, mine.f, i);
-                const unsigned mask = __shfl_sync(0xffffffffu, mine.mask, i);
-                const int po = __shfl_sync(0xffffffffu, mine.pair_off, i);
-                const bool vis = (mask >> lane) & 1u;
-                const int nvis = __popc(mask);
-                const float* h = ds.Hfd + (size_t)po * 6 + (vis ? rank_of(mask, lane) : 0);
-                const float2* th = dth2 + 6 * f;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) dot_pair_add(s, c, vis ? h[k * nvis] : 0.0f, th[k]);
-            }
+            for (int j = warp; j < cnt; j += kTileWarps) add_entry(j, nullptr);
         }
         red[warp][lane] = make_float2(s, c);
     }
@@ -541,7 +576,13 @@ fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
 // forms g_n itself (a few independent loads) and takes entries round-robin,
 // their records loaded one per lane, so no warp waits on another.
 // kFc: per-lane partials are E x 64 (g then H_dd) and H_dd is written out.
+// Before the wait each warp loads the tile's entry records and (IC) the H_fd
+// rows of its first kPointPre entries and H_dd: the precompute wrote them and
+// no kernel of the iteration does (FC forms H_fd and H_dd in the residual
+// pass just before, so FC reads them after the wait).
 // ---------------------------------------------------------------------------
+constexpr int kPointPre = 4;
+
 template <bool kAccum, bool kFc>
 __global__ void __launch_bounds__(kTileWarps * 32)
 point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __restrict__ Hfd,
@@ -551,13 +592,38 @@ point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __rest
 {
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     pdl_trigger();
-    pdl_wait();
     const int e0 = pb.tile_entry[t], e1 = pb.tile_entry[t + 1], ne = e1 - e0;
+    const int n = t * kTile + lane;
+    const int cnt0 = min(32, ne);
+    Entry mine = {0, 0u, 0, 0};
+    int slot = 0;
+    bool valid = false;
+    float hnn = 0.0f;
+    float hpre[kPointPre][6];
     if (kAccum) {
-        const int n = t * kTile + lane;
+        if (lane < ne) {
+            mine = pb.entries[e0 + lane];
+            slot = pb.entry_slot[e0 + lane];
+        }
+        valid = pb.valid_pt[n];
+        if (!kFc) {
+            hnn = Hnn[n];
+#pragma unroll
+            for (int r = 0; r < kPointPre; ++r) {
+                const int i = warp + kTileWarps * r;
+                const unsigned mask = __shfl_sync(0xffffffffu, mine.mask, i);
+                const int po = __shfl_sync(0xffffffffu, mine.pair_off, i);
+                const bool vis = i < cnt0 && ((mask >> lane) & 1u);
+                const int nvis = __popc(mask);
+                const float* h = Hfd + (size_t)po * 6 + (vis ? rank_of(mask, lane) : 0);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) hpre[r][q] = vis ? h[q * nvis] : 0.0f;
+            }
+        }
+    }
+    pdl_wait();
+    if (kAccum) {
         const int stride = kFc ? 2 * kTile : kTile;
-        float hnn = kFc ? 0.0f : Hnn[n];
-        const bool valid = pb.valid_pt[n];
         float g = 0.0f;
         for (int e = e0; e < e1; e += 8) {
             float v[8], h[8];
@@ -579,39 +645,49 @@ point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __rest
             gn[n] = ok ? g : 0.0f;
             if (kFc) Hnn[n] = ok ? hnn : 0.0f;
         }
-        for (int b = 0; b < ne; b += 32) {
-            Entry mine = {0, 0u, 0, 0};
-            int slot = 0;
+        // the correction of entry i of the current batch (hv: its prefetched
+        // H_fd values, or null to load them)
+        auto correct = [&](int i, const float* hv) {
+            const unsigned mask = __shfl_sync(0xffffffffu, mine.mask, i);
+            const int po = __shfl_sync(0xffffffffu, mine.pair_off, i);
+            const int sl = __shfl_sync(0xffffffffu, slot, i);
+            const bool vis = (mask >> lane) & 1u;
+            const int nvis = __popc(mask);
+            const float* h = Hfd + (size_t)po * 6 + (vis ? rank_of(mask, lane) : 0);
+            float corr[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) corr[q] = vis ? (hv ? hv[q] : h[q * nvis]) * sn : 0.0f;
+            warp_sum<6>(corr);
+            if (lane < 6) {
+                float v = corr[0];
+#pragma unroll
+                for (int q = 1; q < 6; ++q) v = lane == q ? corr[q] : v;
+                ent_part[(size_t)sl * kEntryPartial + coff + lane] = v;
+            }
+        };
+        int i = warp;
+        if (!kFc) {
+#pragma unroll
+            for (int r = 0; r < kPointPre; ++r, i += kTileWarps)
+                if (i < cnt0) correct(i, hpre[r]);
+        }
+#pragma unroll 2
+        for (; i < cnt0; i += kTileWarps) correct(i, nullptr);
+        for (int b = 32; b < ne; b += 32) {
+            mine = Entry{0, 0u, 0, 0};
+            slot = 0;
             if (b + lane < ne) {
                 mine = pb.entries[e0 + b + lane];
                 slot = pb.entry_slot[e0 + b + lane];
             }
             const int cnt = min(32, ne - b);
-            for (int i = warp; i < cnt; i += kTileWarps) {
-                const unsigned mask = __shfl_sync(0xffffffffu, mine.mask, i);
-                const int po = __shfl_sync(0xffffffffu, mine.pair_off, i);
-                const int sl = __shfl_sync(0xffffffffu, slot, i);
-                const bool vis = (mask >> lane) & 1u;
-                const int nvis = __popc(mask);
-                const float* h = Hfd + (size_t)po * 6 + (vis ? rank_of(mask, lane) : 0);
-                float corr[6];
-#pragma unroll
-                for (int a = 0; a < 6; ++a) corr[a] = vis ? h[a * nvis] * sn : 0.0f;
-                warp_sum<6>(corr);
-                if (lane < 6) {
-                    float v = corr[0];
-#pragma unroll
-                    for (int a = 1; a < 6; ++a) v = lane == a ? corr[a] : v;
-                    ent_part[(size_t)sl * kEntryPartial + coff + lane] = v;
-                }
-            }
+#pragma unroll 2
+            for (int j = warp; j < cnt; j += kTileWarps) correct(j, nullptr);
         }
     }
     if (warp == kTileWarps - 1) tile_stats_from_entries(pb, estats, ddsq_t, tstats, t, e0, e1, lane);
 }
 
-// ---------------------------------------------------------------------------
-// launchers
 // ---------------------------------------------------------------------------
 // IC solve (Sec. 3.5 step 4): Dtheta = -S^-1 y, one CTA per target frame:
 // nine warps take the frame's six rows and the anchor frame's three
@@ -626,23 +702,41 @@ ic_solve_kernel(SolveArgs a, const dfloat* __restrict__ Sinv, const double* __re
     extern __shared__ dfloat ys[];  // nc, compact order; then F ints
     __shared__ double dth[9], d[6];
     const int fg = blockIdx.x + 1, lane = threadIdx.x & 31, row = threadIdx.x >> 5;
-    // the bundle of global frame fg (static data: read before the wait)
+    pdl_trigger();
+    // Before the wait: the reduced system's layout and the row of S^-1 this
+    // warp multiplies (the first kSinvPre elements per lane, in registers).
+    // The precompute, which ends with an ordinary launch, wrote them; no
+    // kernel of the iteration writes them.
     const BundleDesc bd = a.bund[a.frame_bundle[fg]];
     const int F = bd.F, f = fg - bd.fo;
     const int* cmap = a.cmap + bd.co;
     const double* tanchor = a.tanchor + (size_t)12 * bd.fo;
     Sinv += bd.so;
     y += (size_t)6 * bd.fo;
-    pdl_trigger();
+    // the reference frame of a bundle (f = 0) and frames without residuals
+    // get a zero update
+    const int kf = f > 0 ? cmap[f] : -1, nc = 6 * cmap[F], anchor = a.active[bd.fo];
+    int* frame_of = reinterpret_cast<int*>(ys + 6 * (F - 1));
+    const int r = row < 6 ? 6 * kf + row : (anchor > 0 ? 6 * cmap[anchor] + row - 6 : -1);
+    const dfloat* Sr = Sinv + (size_t)(r >= 0 ? r : 0) * nc;
+    constexpr int kSinvPre = 8;
+    dfloat pre[kSinvPre];
+#pragma unroll
+    for (int q = 0; q < kSinvPre; ++q) {
+        const int c = lane + 32 * q;
+        pre[q] = (kf >= 0 && r >= 0 && c < nc) ? Sr[c] : df_make(0.0f, 0.0f);
+    }
+    if (kf >= 0) {
+        for (int g = 1 + threadIdx.x; g < F; g += blockDim.x) {
+            const int k = cmap[g];
+            if (k >= 0) frame_of[k] = g;
+        }
+    }
     pdl_wait();
     // the frame's brightness pair from this step's residuals (the next
     // residual pass reads it)
     if (a.photo_sums && f > 0 && threadIdx.x == 0)
         photo_update_frame(a.photo_sums + (size_t)5 * fg, a.fc + (size_t)fg * kFrameConst);
-    // the reference frame of a bundle (f = 0) and frames without residuals
-    // get a zero update
-    const int kf = f > 0 ? cmap[f] : -1, nc = 6 * cmap[F], anchor = a.active[bd.fo];
-    int* frame_of = reinterpret_cast<int*>(ys + 6 * (F - 1));
     if (kf < 0) {
         if (row == 0) {
             if (lane < 6) d[lane] = 0.0;
@@ -651,19 +745,18 @@ ic_solve_kernel(SolveArgs a, const dfloat* __restrict__ Sinv, const double* __re
         }
         return;
     }
-    for (int g = 1 + threadIdx.x; g < F; g += blockDim.x) {
-        const int k = cmap[g];
-        if (k >= 0) frame_of[k] = g;
-    }
     __syncthreads();
     for (int c = threadIdx.x; c < nc; c += blockDim.x)
         ys[c] = df_from_double(y[(size_t)frame_of[c / 6] * 6 + c % 6]);
     __syncthreads();
-    const int r = row < 6 ? 6 * kf + row : (anchor > 0 ? 6 * cmap[anchor] + row - 6 : -1);
     if (r >= 0) {
         DfAcc acc;
-        const dfloat* Sr = Sinv + (size_t)r * nc;
-        for (int c = lane; c < nc; c += 32) acc.add_prod(Sr[c], ys[c]);
+#pragma unroll
+        for (int q = 0; q < kSinvPre; ++q) {
+            const int c = lane + 32 * q;
+            if (c < nc) acc.add_prod(pre[q], ys[c]);
+        }
+        for (int c = lane + 32 * kSinvPre; c < nc; c += 32) acc.add_prod(Sr[c], ys[c]);
         float ss = acc.s, cc = acc.c;
         warp_sum_pair(ss, cc);
         if (lane == 0) dth[row] = -((double)ss + (double)cc);

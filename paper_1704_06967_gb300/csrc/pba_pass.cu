@@ -221,14 +221,17 @@ frame_reduce_kernel(DevProblem pb, const float* __restrict__ ent_part, double* _
                     double* __restrict__ stats, int slot_cur, int slot_prev, int nframes_blocks)
 {
     pdl_trigger();
-    pdl_wait();
     if ((int)blockIdx.x < nframes_blocks) {
         const int f = blockIdx.x + 1;
+        // the frame's slot range is fixed at set-up: read before the wait
+        const int s0 = pb.frame_entry[f], s1 = pb.frame_entry[f + 1];
+        pdl_wait();
         float vs, vc;
-        frame_rows_sum<NCOMP, SUB, SUB_FROM, kReduceThreads>(pb, ent_part, f, vs, vc);
+        frame_rows_sum<NCOMP, SUB, SUB_FROM, kReduceThreads>(ent_part, s0, s1, vs, vc);
         if (threadIdx.x < NCOMP) out[(size_t)f * NCOMP + threadIdx.x] = (double)vs + (double)vc;
         return;
     }
+    pdl_wait();
     stats_block<kReduceThreads>(pb, tstats, dthsq, stats, slot_cur, slot_prev);
 }
 

@@ -37,15 +37,15 @@ __device__ __forceinline__ void warp_sum_pair(float& s, float& c)
     }
 }
 
-// Sum over the entry rows of frame f (slots frame_entry[f] .. [f+1]) of
+// Sum over the entry rows [s0, s1) of a frame (its slots frame_entry[f] ..
+// frame_entry[f + 1]) of
 // row[k] (minus row[SUB + k - SUB_FROM] for k >= SUB_FROM when SUB >= 0),
 // k < NCOMP. Thread t takes rows t, t + THREADS, ... and loads each row's
 // partials as float4 chunks, so a frame of up to THREADS entries is read in
 // one latency round. Thread k < NCOMP receives component k as (vs, vc).
 // All threads of the CTA must call it.
 template <int NCOMP, int SUB, int SUB_FROM, int THREADS>
-__device__ inline void frame_rows_sum(const DevProblem& pb, const float* __restrict__ ent_part, int f,
-                                      float& vs, float& vc)
+__device__ inline void frame_rows_sum(const float* __restrict__ ent_part, int s0, int s1, float& vs, float& vc)
 {
     constexpr int kWarps = THREADS / 32;
     constexpr int kLast = SUB < 0 ? NCOMP - 1
@@ -55,7 +55,6 @@ __device__ inline void frame_rows_sum(const DevProblem& pb, const float* __restr
     static_assert(4 * kChunks <= kEntryPartial, "row chunks");
     __shared__ float red_s[kWarps][NCOMP], red_c[kWarps][NCOMP];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int s0 = pb.frame_entry[f], s1 = pb.frame_entry[f + 1];
     float s[NCOMP], c[NCOMP];
 #pragma unroll
     for (int k = 0; k < NCOMP; ++k) s[k] = c[k] = 0.0f;
