@@ -176,9 +176,11 @@ struct SchurLists {
     int n_pairs, n_chunks;
 };
 constexpr int kSchurChunk = 32;
+// tile_todo (nullable): form only the chunks with an item of a flagged tile
+// and keep the other chunks' sums in part
 cudaError_t launch_schur_sparse(const DevProblem& pb, const float* Hfd, const float* Hnn,
                                 const SchurLists& sl, float2* part, double* Soff,
-                                cudaStream_t st, int* launches);
+                                cudaStream_t st, int* launches, const unsigned char* tile_todo = nullptr);
 // Per bundle (arrays at the bundle's offsets; Hff, anchor_t, rhs and active
 // indexed by global frame): S (FP64) and, when S2 is given, its double-float
 // copy over the active frames only (compact order, cmap[f] = compact index

@@ -114,6 +114,7 @@ struct pba_ctx {
         int *tile_entry, *frame_entry, *entry_slot, *frame_bundle, *tile_f0, *slot_caller;
         float *ic_part, *ic_hpart;  // per-entry IC H_ff sums and J_d^T W_0 J_d (kept for window updates)
         unsigned char* todo;        // F: frames whose entries a window update must precompute
+        unsigned char* tile_todo;   // T: tiles that see a frame that entered or left the window
         BundleDesc* bund;
         int* uvs;
         float2* xn;
@@ -137,7 +138,8 @@ struct pba_ctx {
         dfloat *A2, *L2, *Linv, *dpiv, *rpiv;  // double-float factorisation (IC and FC in turn)
         int *pair_fg, *pair_chunk, *chunk_pair, *chunk_start;
         int2* pair_items;
-        float2* schur_part;
+        float2* schur_part;     // FC: chunk sums of the Schur complement (every iteration)
+        float2* ic_schur_part;  // IC: chunk sums at p_0, kept for window updates
         int *active_ic, *active_fc, *cmap_ic, *cmap_fc;
         int* err;
         double* stats;
@@ -149,6 +151,9 @@ struct pba_ctx {
     // sliding window: frames outside it keep their data but their entries
     // are uploaded with no visible lane, so no kernel sees their residuals
     std::vector<unsigned char> frame_on, frame_todo;  // F
+    // F: frames that entered or left since the last IC (pre)computation; the
+    // Schur terms of every point they see change
+    std::vector<unsigned char> frame_changed;
     bool window_dirty = false;  // the window changed after the last (pre)computation
     int res_warps = 8;    // warps per CTA of the IC residual pass
     bool tuned = false;
@@ -347,6 +352,7 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.ic_part, (size_t)c->E * kEntryPartial * 4);
     take(c->d.ic_hpart, (size_t)c->E * kTile * 4);
     take(c->d.todo, F);
+    take(c->d.tile_todo, (size_t)c->T);
     take(c->d.tstats, (size_t)c->T * sizeof(TileStats));
     take(c->d.fc, F * kFrameConst * 4);
     take(c->d.fc_prev, F * 12 * 4);
@@ -379,6 +385,7 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.chunk_start, c->chunk_start.size() * sizeof(int));
     take(c->d.pair_items, c->pair_items.size() * sizeof(int2));
     take(c->d.schur_part, c->chunk_pair.size() * 36 * sizeof(float2));
+    take(c->d.ic_schur_part, c->chunk_pair.size() * 36 * sizeof(float2));
     take(c->d.active_ic, F * 4);
     take(c->d.active_fc, F * 4);
     take(c->d.cmap_ic, (size_t)c->n_cmap * 4);
@@ -972,6 +979,7 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     CK(h2d(ctx, ctx->d.entries, ctx->entries.data(), sizeof(Entry) * ctx->entries.size()));
     ctx->frame_on.assign(ctx->F, 1);
     ctx->frame_todo.assign(ctx->F, 0);
+    ctx->frame_changed.assign(ctx->F, 0);
     ctx->window_dirty = false;
     CK(h2d(ctx, ctx->d.tile_entry, ctx->tile_entry.data(), sizeof(int) * ctx->tile_entry.size()));
     CK(h2d(ctx, ctx->d.frame_entry, ctx->frame_entry.data(), sizeof(int) * ctx->frame_entry.size()));
@@ -1005,7 +1013,7 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
 }
 
 pba_status precompute_core(pba_ctx* ctx, const LaunchCtx& L, const BundleSet& bs,
-                           const unsigned char* todo = nullptr);
+                           const unsigned char* todo = nullptr, const unsigned char* tile_todo = nullptr);
 
 // The IC precompute's launches (Sec. 3.5): p_0 from the current parameters,
 // J, W_0 and the H blocks per entry, the frame sums, the Schur complement, S
@@ -1025,13 +1033,16 @@ pba_status precompute_body(pba_ctx* ctx)
 }
 
 // The precompute after the FP32 depths of the new p_0 are in place; with
-// todo, the entries of the frames flagged there only (a window update).
-pba_status precompute_core(pba_ctx* ctx, const LaunchCtx& L, const BundleSet& bs, const unsigned char* todo)
+// todo, the entries of the frames flagged there only, and with tile_todo the
+// Schur chunks of the tiles flagged there only (a window update: the other
+// chunks' sums are kept from the last precompute, their inputs unchanged).
+pba_status precompute_core(pba_ctx* ctx, const LaunchCtx& L, const BundleSet& bs, const unsigned char* todo,
+                           const unsigned char* tile_todo)
 {
     LAUNCH(TS_PRE, launch_ic_precompute(L, todo));
     LAUNCH(TS_PRE, launch_frame_reduce(L, 0, 21, ctx->d.red_ic, -1, -1, true, -1, 0, ctx->d.ic_part));
-    LAUNCHN(TS_PRE, launch_schur_sparse(L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, schur_lists(ctx), ctx->d.schur_part,
-                                        ctx->d.Soff, ctx->stream, &nl));
+    LAUNCHN(TS_PRE, launch_schur_sparse(L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, schur_lists(ctx),
+                                        ctx->d.ic_schur_part, ctx->d.Soff, ctx->stream, &nl, tile_todo));
     LAUNCH(TS_PRE, launch_assemble_S(bs, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64, ctx->cfg.gauge_anchor_w,
                                      ctx->cfg.damping, ctx->d.S_ic, ctx->d.active_ic, ctx->stream, ctx->d.A2,
                                      ctx->d.cmap_ic));
@@ -1127,6 +1138,7 @@ pba_status pba_precompute_ic(pba_ctx* ctx)
         ctx->ic_ready = true;
         ctx->window_dirty = false;
         std::fill(ctx->frame_todo.begin(), ctx->frame_todo.end(), 0);
+        std::fill(ctx->frame_changed.begin(), ctx->frame_changed.end(), 0);
     }
     return s;
 }
@@ -1148,6 +1160,7 @@ pba_status pba_set_window(pba_ctx* ctx, int bundle, const uint8_t* in_window)
         changed = true;
         ctx->frame_on[g] = on;
         ctx->frame_todo[g] = on;
+        ctx->frame_changed[g] = 1;
         if (!on) {  // the frame's stored H_ff sums leave the frame reduction
             const int s0 = ctx->frame_entry[g], s1 = ctx->frame_entry[g + 1];
             if (s1 > s0)
@@ -1178,12 +1191,19 @@ pba_status pba_update_ic(pba_ctx* ctx)
             CK(cudaMemcpyAsync(ctx->d.poses0_64 + 12 * (size_t)f, ctx->d.poses64 + 12 * (size_t)f,
                                sizeof(double) * 12, cudaMemcpyDeviceToDevice, ctx->stream));
     CK(h2d(ctx, ctx->d.todo, ctx->frame_todo.data(), ctx->frame_todo.size()));
-    pba_status s = precompute_core(ctx, L, bs, ctx->d.todo);
+    // tiles with an entry (in or out of the window) for a frame that entered
+    // or left: their points' H_dd and Schur terms change
+    std::vector<unsigned char> tile_todo(ctx->T, 0);
+    for (const Entry& e : ctx->entries)
+        if (e.mask && ctx->frame_changed[e.f]) tile_todo[e.tile] = 1;
+    CK(h2d(ctx, ctx->d.tile_todo, tile_todo.data(), tile_todo.size()));
+    pba_status s = precompute_core(ctx, L, bs, ctx->d.todo, ctx->d.tile_todo);
     if (s != PBA_OK) return s;
     s = check_device_error(ctx);
     if (s == PBA_OK || s == PBA_ERR_NOT_PD) {
         ctx->window_dirty = false;
         std::fill(ctx->frame_todo.begin(), ctx->frame_todo.end(), 0);
+        std::fill(ctx->frame_changed.begin(), ctx->frame_changed.end(), 0);
     }
     return s;
 }
@@ -1277,6 +1297,7 @@ pba_status pba_solve_ic(pba_ctx* ctx, int n_iters, int reanchor_every, pba_iter_
         ctx->ic_ready = true;
         ctx->window_dirty = false;
         std::fill(ctx->frame_todo.begin(), ctx->frame_todo.end(), 0);
+        std::fill(ctx->frame_changed.begin(), ctx->frame_changed.end(), 0);
     }
     return s;
 }

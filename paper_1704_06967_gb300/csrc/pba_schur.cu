@@ -108,15 +108,22 @@ __device__ __forceinline__ void warp_reduce_36(float (&s)[36], float (&c)[36], i
 }
 
 // chunk c covers items [chunk_start[c], chunk_start[c+1]) of one frame pair;
-// it writes 36 unevaluated pairs (s, c) to part[c].
+// it writes 36 unevaluated pairs (s, c) to part[c]. With tile_todo, a chunk
+// none of whose items lies in a flagged tile keeps part[c] as it is.
 __global__ void __launch_bounds__(32 * kSchurWarps)
 schur_chunk_kernel(DevProblem pb, const float* Hfd, const float* Hnn, const int* chunk_start,
-                   const int2* items, float2* part)
+                   const int2* items, float2* part, const unsigned char* tile_todo)
 {
     __shared__ float2 red[kSchurWarps][36];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ch = blockIdx.x;
     const int i0 = chunk_start[ch], i1 = chunk_start[ch + 1];
+    if (tile_todo) {
+        bool todo = false;
+        for (int it = i0 + (int)threadIdx.x; it < i1; it += blockDim.x)
+            todo |= tile_todo[pb.entries[items[it].x].tile] != 0;
+        if (!__syncthreads_or(todo)) return;
+    }
     float s[36], c[36];
 #pragma unroll
     for (int k = 0; k < 36; ++k) s[k] = c[k] = 0.0f;
@@ -193,12 +200,12 @@ __global__ void schur_pair_reduce_kernel(const int* pair_fg, const int* pair_chu
 
 cudaError_t launch_schur_sparse(const DevProblem& pb, const float* Hfd, const float* Hnn,
                                 const SchurLists& sl, float2* part, double* Soff,
-                                cudaStream_t st, int* launches)
+                                cudaStream_t st, int* launches, const unsigned char* tile_todo)
 {
     if (sl.n_pairs == 0) return cudaSuccess;
     if (sl.n_chunks > 0) {
         schur_chunk_kernel<<<sl.n_chunks, 32 * kSchurWarps, 0, st>>>(
-            pb, Hfd, Hnn, sl.chunk_start, sl.items, part);
+            pb, Hfd, Hnn, sl.chunk_start, sl.items, part, tile_todo);
         ++*launches;
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -498,6 +498,37 @@ def test_window_update_equals_a_full_precompute_with_the_same_anchors(torch_cuda
     b.close()
 
 
+def test_window_update_after_a_frame_leaves_keeps_the_untouched_schur_chunks(torch_cuda):
+    """Frame 2 leaves after FC steps (which form their own Schur complement
+    every iteration): the update forms again only the Schur chunks of the
+    tiles that saw frame 2 and keeps the rest from the IC precompute; the
+    system equals a full precompute without frame 2, bit for bit."""
+    sc = synth.make_scene("small")
+    a = _bundle(sc)
+    a.precompute_ic()
+    a.solve_fc(2)
+    a.set_window([1, 1, 0, 1, 1, 1])
+    a.update_ic()
+    b = _bundle(sc)
+    b.set_window([1, 1, 0, 1, 1, 1])
+    b.precompute_ic()
+    sa, sb = a.system(fc=False), b.system(fc=False)
+    for key in ("Hff", "Hdd", "S"):
+        assert np.array_equal(sa[key], sb[key]), key
+    # and back in at its p_0 pose: the chunks of frame 2's tiles are formed
+    # again
+    a.set_params(sc.poses0, sc.depths0)
+    a.set_window([1, 1, 1, 1, 1, 1])
+    a.update_ic()
+    c = _bundle(sc)
+    c.precompute_ic()
+    sa, sc_ = a.system(fc=False), c.system(fc=False)
+    for key in ("Hff", "Hdd", "S"):
+        assert np.array_equal(sa[key], sc_[key]), key
+    for x in (a, b, c):
+        x.close()
+
+
 # ----------------------------------------------------------------------------
 # affine brightness per frame (cfg.photometric)
 # ----------------------------------------------------------------------------
