@@ -319,6 +319,35 @@ def test_ragged_tile_single_pixel_pattern_and_empty_rows(torch_cuda):
         assert st[0, 2] == o_st[oracle.ST_COUNT]
 
 
+_PATTERN16 = np.concatenate([synth.PATTERN8, np.array([(-2, -2), (2, -2), (-2, 2), (2, 2), (-1, 0), (1, 0),
+                                                        (0, -1), (0, 1)], np.int32)])
+
+
+@pytest.mark.parametrize("P", [9, 16])
+def test_large_patterns_match_oracle(torch_cuda, P):
+    """Patterns above eight pixels take the 16-pixel kernels: P = 16 is the
+    largest the library accepts, P = 9 leaves a ragged last group of J
+    chunks. One IC step and one FC step against the oracle."""
+    sc = synth.make_scene("small")
+    sc.pattern = _PATTERN16[:P] if P == 16 else np.concatenate([synth.PATTERN8, np.zeros((1, 2), np.int32)])
+    pb = oracle.Problem.from_scene(sc)
+    pre = oracle.ic_precompute(pb, sc.poses0, sc.depths0)
+    b = _bundle(sc)
+    b.precompute_ic()
+    b.iterate(1)
+    dth, dd = b.last_update()
+    o_dth, o_dd, _, _, _ = oracle.ic_step(pb, pre, sc.poses0, sc.depths0, sc.poses0, sc.depths0)
+    ref0 = np.linalg.norm(np.concatenate([o_dth[1:].ravel(), o_dd]))
+    assert _step_err(dth, dd, o_dth, o_dd, ref0) <= STEP_TOL
+    b.set_params(sc.poses0, sc.depths0)
+    b.solve_fc(1)
+    dth, dd = b.last_update()
+    o_dth, o_dd, _, _, _ = oracle.fc_step(pb, sc.poses0, sc.depths0)
+    ref0 = np.linalg.norm(np.concatenate([o_dth[1:].ravel(), o_dd]))
+    assert _step_err(dth, dd, o_dth, o_dd, ref0) <= STEP_TOL
+    b.close()
+
+
 # ----------------------------------------------------------------------------
 # Levenberg-Marquardt damping (an option beyond the paper's Gauss-Newton)
 # ----------------------------------------------------------------------------
