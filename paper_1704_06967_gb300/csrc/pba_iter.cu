@@ -33,6 +33,21 @@ __device__ __forceinline__ int rank_of(unsigned mask, int lane)
     return __popc(mask & ((1u << lane) - 1u));
 }
 
+// One reduce-scatter level over the lanes at stride o: a lane keeps values
+// [0, M) (lane bit o clear) or [M, 2M) (set) of v, moved to v[0 .. M), and
+// adds its partner's copy of them.
+template <int M>
+__device__ __forceinline__ void scatter_level(float (&v)[8], int lane, int o)
+{
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+        const float send = up ? v[q] : v[q + M];
+        const float keep = up ? v[q + M] : v[q];
+        v[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+}
+
 // (s, c) += h (t.x + t.y): h t.x split exactly by TwoProduct (Ogita, Rump
 // and Oishi 2005), the sum carried by Knuth's two-sum; t = (hi, lo) is an
 // FP64 value as an unevaluated pair of floats.
@@ -654,16 +669,20 @@ point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __rest
             const bool vis = (mask >> lane) & 1u;
             const int nvis = __popc(mask);
             const float* h = Hfd + (size_t)po * 6 + (vis ? rank_of(mask, lane) : 0);
-            float corr[6];
+            float v[8];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) corr[q] = vis ? (hv ? hv[q] : h[q * nvis]) * sn : 0.0f;
-            warp_sum<6>(corr);
-            if (lane < 6) {
-                float v = corr[0];
-#pragma unroll
-                for (int q = 1; q < 6; ++q) v = lane == q ? corr[q] : v;
-                ent_part[(size_t)sl * kEntryPartial + coff + lane] = v;
-            }
+            for (int q = 0; q < 6; ++q) v[q] = vis ? (hv ? hv[q] : h[q * nvis]) * sn : 0.0f;
+            v[6] = v[7] = 0.0f;
+            // sums over the lanes by reduce-scatter (nine exchanges instead
+            // of thirty): at strides 16, 8, 4 a lane keeps half of its values
+            // and adds its partner's copy of them, then two butterfly levels;
+            // value q ends on lanes 4q .. 4q + 3
+            scatter_level<4>(v, lane, 16);
+            scatter_level<2>(v, lane, 8);
+            scatter_level<1>(v, lane, 4);
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+            if ((lane & 3) == 0 && lane < 24) ent_part[(size_t)sl * kEntryPartial + coff + (lane >> 2)] = v[0];
         };
         int i = warp;
         if (!kFc) {
