@@ -638,21 +638,35 @@ point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __rest
     }
     pdl_wait();
     if (kAccum) {
+        // g_n (FC: and H_dd): warp w adds the tile's entries w, w + 4, ...,
+        // then every warp adds the four partial sums in warp order
         const int stride = kFc ? 2 * kTile : kTile;
-        float g = 0.0f;
-        for (int e = e0; e < e1; e += 8) {
+        __shared__ float red_g[kTileWarps][kTile], red_h[kTileWarps][kTile];
+        float g = 0.0f, hsum = 0.0f;
+        for (int e = e0 + warp; e < e1; e += 8 * kTileWarps) {
             float v[8], h[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const bool in = e + u < e1;
-                v[u] = in ? gpart[(size_t)(e + u) * stride + lane] : 0.0f;
-                h[u] = (kFc && in) ? gpart[(size_t)(e + u) * stride + kTile + lane] : 0.0f;
+                const int eu = e + u * kTileWarps;
+                const bool in = eu < e1;
+                v[u] = in ? gpart[(size_t)eu * stride + lane] : 0.0f;
+                h[u] = (kFc && in) ? gpart[(size_t)eu * stride + kTile + lane] : 0.0f;
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 g += v[u];
-                if (kFc) hnn += h[u];
+                if (kFc) hsum += h[u];
             }
+        }
+        red_g[warp][lane] = g;
+        if (kFc) red_h[warp][lane] = hsum;
+        __syncthreads();
+        g = red_g[0][lane];
+        if (kFc) hnn = red_h[0][lane];
+#pragma unroll
+        for (int w = 1; w < kTileWarps; ++w) {
+            g += red_g[w][lane];
+            if (kFc) hnn += red_h[w][lane];
         }
         const bool ok = valid && hnn > 0.0f;
         const float sn = ok ? g / (hnn * pb.damp1) : 0.0f;
