@@ -1089,7 +1089,7 @@ pba_status autotune(pba_ctx* ctx)
     const BundleSet bs = bundle_set(ctx);
     int best_c = ctx->ldl_cluster;
     best = 0.0f;
-    for (int C = 4; s == PBA_OK && C <= ldl_max_cluster(); C *= 2) {
+    for (int C = 1; s == PBA_OK && C <= ldl_max_cluster(); C *= 2) {
         float ms = 0.0f;
         auto once = [&]() -> cudaError_t {
             cudaError_t e = launch_assemble_S(bs, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64,
@@ -1100,7 +1100,7 @@ pba_status autotune(pba_ctx* ctx)
                               ctx->d.err, ctx->stream, C);
         };
         s = elapsed(once, 3, &ms);
-        if (s == PBA_OK && (C == 4 || ms < best)) {
+        if (s == PBA_OK && (C == 1 || ms < best)) {
             best = ms;
             best_c = C;
         }
