@@ -476,6 +476,41 @@ def test_ic_update_at_p0_is_boxplus_of_minus_dp():
     assert np.allclose(D1, depths0 - dd, atol=1e-15)
 
 
+def _first_step_gap(eps):
+    """Relative gaps between the parameters one IC step and one FC step reach
+    from the same p_0 (rotation, translation, inverse depth blocks), on
+    noise-free cards perturbed by eps times (0.5 deg, 0.005, 1 %)."""
+    from scipy.spatial.transform import Rotation
+    sc = synth.make_scene("cards", noise_free=True, rot_deg=0.5 * eps, trans=0.005 * eps, sigma_d=0.01 * eps)
+    pb = oracle.Problem.from_scene(sc)
+    pre = oracle.ic_precompute(pb, sc.poses0, sc.depths0)
+    _, _, Pi, Di, _ = oracle.ic_step(pb, pre, sc.poses0, sc.depths0, sc.poses0, sc.depths0)
+    _, _, Pf, Df, _ = oracle.fc_step(pb, sc.poses0, sc.depths0)
+    P0 = sc.poses0
+    blocks = {"rot": ([], []), "trans": ([], [])}
+    for f in range(1, sc.F):
+        R0t = P0[f, :9].reshape(3, 3).T
+        for P, k in ((Pi, 0), (Pf, 1)):
+            blocks["rot"][k].append(Rotation.from_matrix(P[f, :9].reshape(3, 3) @ R0t).as_rotvec())
+            blocks["trans"][k].append(P[f, 9:] - P0[f, 9:])
+    blocks["depth"] = ([Di - sc.depths0], [Df - sc.depths0])
+    return {k: np.linalg.norm(np.concatenate(a) - np.concatenate(b)) / np.linalg.norm(np.concatenate(b))
+            for k, (a, b) in blocks.items()}
+
+
+def test_ic_and_fc_first_steps_agree_to_first_order():
+    """Baker and Matthews' equivalence of the inverse and forwards
+    compositional updates (cited in Sec. 2): from the same p_0 on exact data
+    the two first steps differ by a term of second order in the
+    perturbation, so their relative gap shrinks in proportion to it. A wrong
+    sign or a swapped column in either Jacobian, or in either update rule,
+    leaves a gap of order one."""
+    g1, g2 = _first_step_gap(0.25), _first_step_gap(0.0625)
+    for k in ("rot", "trans", "depth"):
+        assert g2[k] < 0.15, (k, g1, g2)
+        assert g1[k] / g2[k] > 2.5, (k, g1, g2)  # 4x smaller perturbation
+
+
 # ----------------------------------------------------------------------------
 # whole solves on noise-free data where the model is exact
 # ----------------------------------------------------------------------------
