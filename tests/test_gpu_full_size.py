@@ -1,7 +1,7 @@
 """Full-size precision workload (orbit101: reference + 100 frames, 1280x720
 BF16 images, 200,000 points x 8-pixel pattern, 33.6 M residuals, a 600 x 600
 reduced camera system): one teacher-forced IC step and one FC step against
-the FP64 oracle at the benchmark spec's tolerance.
+the FP64 oracle at the step tolerance (relative error 1e-4).
 
 The oracle needs ~2.5 minutes for this (its precompute, and the dense
 600 x 600 Schur solves of its IC and FC steps), so the test runs only when
