@@ -147,7 +147,7 @@ def test_autotuned_shapes_leave_results_unchanged(torch_cuda):
         ctx.precompute_ic()
         ctx.iterate(4)
         w, c = ctx.tuning()
-        assert w in (4, 8, 16) and c in (4, 8, 16)
+        assert w in (4, 8, 16) and c in (1, 2, 4, 8, 16)
         res.append([ctx.params(b) for b in range(len(scenes))])
         ctx.close()
     for (P1, D1), (P2, D2) in zip(*res):
