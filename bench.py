@@ -467,7 +467,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         eb = Bundle(host_imgs, sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis,
-                    pattern=sc.pattern, huber_k=sc.huber_k, autotune=args.autotune)
+                    pattern=sc.pattern, huber_k=sc.huber_k)
+        eb.set_tuning(*b.tuning())  # the shapes found above: no autotuning per context
         eb.precompute_ic()
         eb.iterate(iters, stats=False)
         P, D = eb.params()

@@ -97,9 +97,9 @@ typedef struct {
                                 launch shapes on this problem and keeps the fastest: warps
                                 per CTA of the IC residual pass (4, 8, 16: the number of
                                 (tile, frame) entries a CTA takes) and CTAs per bundle of
-                                the cluster that factors the reduced camera system (4, 8,
-                                16). Results do not depend on the choice (every sum keeps
-                                its order); see pba_get_tuning. */
+                                the cluster that factors the reduced camera system (1, 2,
+                                4, 8, 16). Results do not depend on the choice (every sum
+                                keeps its order); see pba_get_tuning / pba_set_tuning. */
     double damping;          /* Levenberg-Marquardt lambda >= 0; 0 = Gauss-Newton as in the
                                 paper (Sec. 3.5). lambda > 0 scales every diagonal entry of
                                 the frame blocks H_ff and of H_dd by 1 + lambda in the
@@ -279,6 +279,15 @@ pba_status pba_set_brightness(pba_ctx* ctx, int bundle, const double* ab);
  * residual pass, ldl_cluster = CTAs per bundle of the factorisation. Host,
  * nullable each. */
 pba_status pba_get_tuning(pba_ctx* ctx, int* res_warps, int* ldl_cluster);
+
+/* Sets the launch shapes (e.g. those pba_get_tuning returned for another
+ * context of the same shape, so that a fresh context need not autotune):
+ * res_warps in {4, 8, 16}; ldl_cluster a power of two from 1 to the largest
+ * cluster the device co-schedules (16, else 8). Results do not depend on
+ * them. PBA_ERR_ARG for other values (nothing changes). The captured graphs
+ * are discarded, and a context with cfg.autotune keeps these shapes (its
+ * first precompute times no candidates). Needs the CUDA device. */
+pba_status pba_set_tuning(pba_ctx* ctx, int res_warps, int ldl_cluster);
 
 /* Bytes this context copied host->device and device->host since it was
  * created (uploads of images, points, structure and parameters; downloads of

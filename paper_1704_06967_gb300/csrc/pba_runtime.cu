@@ -1543,6 +1543,21 @@ pba_status pba_get_tuning(pba_ctx* ctx, int* res_warps, int* ldl_cluster)
     return PBA_OK;
 }
 
+pba_status pba_set_tuning(pba_ctx* ctx, int res_warps, int ldl_cluster)
+{
+    if (!ctx) return PBA_ERR_ARG;
+    CK(ldl_setup());  // the largest co-schedulable cluster
+    if (res_warps != 4 && res_warps != 8 && res_warps != 16)
+        return fail(ctx, PBA_ERR_ARG, "res_warps must be 4, 8 or 16");
+    if (ldl_cluster < 1 || ldl_cluster > ldl_max_cluster() || (ldl_cluster & (ldl_cluster - 1)))
+        return fail(ctx, PBA_ERR_ARG, "ldl_cluster must be a power of two in [1, %d]", ldl_max_cluster());
+    destroy_graphs(ctx);  // captured with the previous shapes
+    ctx->res_warps = res_warps;
+    ctx->ldl_cluster = ldl_cluster;
+    ctx->tuned = true;
+    return PBA_OK;
+}
+
 pba_status pba_transfer_bytes(pba_ctx* ctx, int64_t* h2d_out, int64_t* d2h_out)
 {
     if (!ctx) return PBA_ERR_ARG;

@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pba_last_timing": ([vp, vp], i),
         "pba_transfer_bytes": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], i),
         "pba_get_tuning": ([vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
+        "pba_set_tuning": ([vp, i, i], i),
         "pba_bundle_errors": ([vp, vp], i),
         "pba_depth_features": ([vp, i, vp], i),
         "pba_mlp_pack": ([vp, vp, vp], i),
@@ -335,6 +336,11 @@ class Batch:
         w, c = ctypes.c_int(), ctypes.c_int()
         self._check(self.lib.pba_get_tuning(self.h, ctypes.byref(w), ctypes.byref(c)))
         return int(w.value), int(c.value)
+
+    def set_tuning(self, res_warps, ldl_cluster):
+        """Sets the launch shapes (as tuning() returns them); results do not
+        depend on them."""
+        self._check(self.lib.pba_set_tuning(self.h, int(res_warps), int(ldl_cluster)))
 
     def transfer_bytes(self):
         a, b = ctypes.c_int64(), ctypes.c_int64()

@@ -152,3 +152,27 @@ def test_autotuned_shapes_leave_results_unchanged(torch_cuda):
         ctx.close()
     for (P1, D1), (P2, D2) in zip(*res):
         assert np.array_equal(P1, P2) and np.array_equal(D1, D2)
+
+
+def test_set_launch_shapes_leave_results_unchanged(torch_cuda):
+    """Shapes set by hand (as one context's autotuning would hand them to
+    another) change no result; values outside the candidates are refused."""
+    from paper_1704_06967_gb300 import Batch, PbaError
+    scenes = _scenes()
+    res = []
+    for shape in (None, (4, 1), (16, 2)):
+        ctx = Batch.from_scenes(scenes)
+        if shape is not None:
+            ctx.set_tuning(*shape)
+            assert ctx.tuning() == shape
+        ctx.precompute_ic()
+        ctx.iterate(3)
+        res.append([ctx.params(b) for b in range(len(scenes))])
+        for bad in ((5, 1), (8, 3), (8, 0), (8, 64)):
+            with pytest.raises(PbaError):
+                ctx.set_tuning(*bad)
+        ctx.close()
+    for other in res[1:]:
+        for (P1, D1), (P2, D2) in zip(res[0], other):
+            assert np.array_equal(P1, P2) and np.array_equal(D1, D2)
+
