@@ -194,10 +194,13 @@ pba_status pba_set_window(pba_ctx* ctx, int bundle, const uint8_t* in_window);
 /* Brings the IC system up to date with the window without a full
  * precompute: the Jacobian rows and H products of the entering frames are
  * formed (anchored at their current poses; every point keeps its d_0),
- * those of the frames already in are reused from the workspace, and H_dd,
- * the frame blocks, S, its factor and S^-1 are formed again from the stored
- * products. The result equals a full pba_precompute_ic whose p_0 holds the
- * same anchors. Before any precompute it runs the full one. */
+ * those of the frames already in are reused from the workspace, H_dd and
+ * the frame blocks are formed again from the stored products, the sums of
+ * the Schur complement are formed again only for the points of tiles that
+ * see a frame that entered or left (the rest are kept), and S, its factor
+ * and S^-1 follow. The result equals a full pba_precompute_ic whose p_0
+ * holds the same anchors, bit for bit. Before any precompute it runs the
+ * full one. */
 pba_status pba_update_ic(pba_ctx* ctx);
 
 /* Runs n_iters IC iterations (Sec. 3.5 steps 1-4 with the Sec. 3.6 update):
