@@ -71,6 +71,15 @@ pba_status pba_mlp_pack(const float* params, void* packed, void* cuda_stream);
 pba_status pba_mlp_infer(const void* packed, int n, const float* features, float* out, int* dev_flag,
                          void* cuda_stream);
 
+/* Exercises the give-up path that every bounded device wait of the library
+ * takes (the tensor-core completion waits above): one warp waits on a
+ * barrier phase that nothing completes, gives up after its bound (a few
+ * milliseconds at most), sets the error bit in dev_flag (one device int,
+ * cleared first) and exits normally, leaving the context usable.
+ * Synchronises the stream; returns PBA_ERR_TIMEOUT when the give-up reached
+ * the host (the expected result), PBA_ERR_CUDA on a launch or copy error. */
+pba_status pba_wait_selftest(int* dev_flag, void* cuda_stream);
+
 /* Training scratch for a batch of n samples, in floats. */
 size_t pba_mlp_scratch_floats(int n);
 

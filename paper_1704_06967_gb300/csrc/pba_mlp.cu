@@ -199,6 +199,27 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
     return false;
 }
 
+// The give-up path of the bounded waits, exercised on purpose: one warp
+// waits on a barrier phase that nothing completes (no arrival is ever
+// made), gives up after the bound, reports kErrTimeout through the flag and
+// exits normally.
+__global__ void wait_selftest_kernel(int* err)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t mbar = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(mbar, 0);
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        if (!ok) atomicOr(err, kErrTimeout);
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mbar) : "memory");
+    }
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
 {
     uint32_t r[32];
@@ -658,6 +679,20 @@ pba_status pba_mlp_infer(const void* packed, int n, const float* features, float
 }
 
 size_t pba_mlp_scratch_floats(int n) { return n > 0 ? pba::mlp_grad_scratch_floats(n) : 0; }
+
+pba_status pba_wait_selftest(int* dev_flag, void* cuda_stream)
+{
+    if (!dev_flag) return PBA_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaMemsetAsync(dev_flag, 0, sizeof(int), st) != cudaSuccess) return PBA_ERR_CUDA;
+    pba::wait_selftest_kernel<<<1, 32, 0, st>>>(dev_flag);
+    int flag = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&flag, dev_flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return PBA_ERR_CUDA;
+    return flag ? PBA_ERR_TIMEOUT : PBA_OK;
+}
 
 pba_status pba_mlp_grad(const float* params, int n, const float* features, const float* targets, float* grad,
                         float* loss, float* scratch, void* cuda_stream)

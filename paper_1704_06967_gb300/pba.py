@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pba_mlp_pack": ([vp, vp, vp], i),
         "pba_mlp_infer": ([vp, i, vp, vp, vp, vp], i),
         "pba_mlp_scratch_floats": ([i], ctypes.c_size_t),
+        "pba_wait_selftest": ([vp, vp], i),
         "pba_mlp_grad": ([vp, i, vp, vp, vp, vp, vp, vp], i),
         "pba_mlp_train_step": ([vp, vp, vp, i, ctypes.c_float, i, vp, vp, vp, vp, vp], i),
         "pba_propose_depths": ([vp, i, vp, vp], i),

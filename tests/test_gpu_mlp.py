@@ -201,3 +201,21 @@ def test_trained_proposal_beats_constant_depth(torch_cuda):
 def synth_images(sc):
     from paper_1704_06967_gb300.pba import _scene_images
     return _scene_images(sc)
+
+
+def test_bounded_wait_gives_up_and_reports_a_timeout(torch_cuda):
+    """The bounded waits' give-up path, run on purpose: a wait on a barrier
+    phase that nothing completes ends after its bound, the kernel exits
+    normally, the host gets PBA_ERR_TIMEOUT, and the context keeps working."""
+    import ctypes
+    torch = torch_cuda
+    from paper_1704_06967_gb300 import load
+    lib = load()
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    rc = lib.pba_wait_selftest(ctypes.c_void_p(flag.data_ptr()), ctypes.c_void_p(st))
+    assert rc == 7  # PBA_ERR_TIMEOUT
+    assert int(flag.item()) != 0
+    x = torch.arange(1024, dtype=torch.float32, device="cuda")
+    assert float((x * 2).sum().item()) == 2 * 1023 * 1024 / 2  # the context still runs kernels
+
