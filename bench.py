@@ -580,7 +580,8 @@ def run_batch(args):
     imgs = [_scene_images(sc) for sc in scenes]
     s0 = scenes[0]
     items = [(imgs[i], sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis) for i, sc in enumerate(scenes)]
-    batch = Batch(items, pattern=s0.pattern, huber_k=s0.huber_k, stream=stream, use_graphs=True)
+    batch = Batch(items, pattern=s0.pattern, huber_k=s0.huber_k, stream=stream, use_graphs=True,
+                  autotune=args.autotune)
     singles = [Bundle(imgs[i], sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis, pattern=sc.pattern,
                       huber_k=sc.huber_k, stream=stream, use_graphs=True) for i, sc in enumerate(scenes)]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -641,6 +642,10 @@ def run_batch(args):
         batch.enable_timing(1 << 1)
         timed(batch_ic, i)
         batch.enable_timing(0)
+        if i == 0 and args.autotune:
+            # the per-bundle loop runs the shapes the batch's first precompute chose
+            for b in singles:
+                b.set_tuning(*batch.tuning())
         timed(loop_ic, i + 1)
         timed(batch_fc, i + 2)
     torch.cuda.synchronize()
@@ -712,6 +717,7 @@ def run_batch(args):
         t0 = time.perf_counter()
         eb = Batch([(host[j], sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis)
                     for j, sc in enumerate(scenes)], pattern=s0.pattern, huber_k=s0.huber_k)
+        eb.set_tuning(*batch.tuning())  # the shapes found above
         flagged(eb.precompute_ic, eb, set())
         flagged(lambda: eb.iterate(iters, stats=False), eb, set())
         for j in range(B):
@@ -737,7 +743,10 @@ def run_batch(args):
                           "points_total": N, "points_min_max": [min(Ns), max(Ns)],
                           "residuals_per_iter": R, "iterations_per_step": iters,
                           "submission": "one CUDA graph replay per library call",
-                          "l2": "flushed (512 MB write) between timed steps"},
+                          "l2": "flushed (512 MB write) between timed steps",
+                          "launch_shapes": dict(zip(("residual_warps_per_cta", "ldl_ctas_per_bundle"),
+                                                    batch.tuning()),
+                                                chosen_by="autotuner" if args.autotune else "defaults")},
                "e2e": {"value": e2e_value, "unit": "bundle-iterations/s", "h2d_bytes_per_step": h2d_b,
                        "d2h_bytes_per_step": d2h_b},
                "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": None, "clocks": clk,
