@@ -430,54 +430,85 @@ void build_structure(pba_ctx* c)
         b.fo = c->F;
         b.to = c->T;
         b.e0 = (int)c->entries.size();
-        std::vector<std::pair<uint64_t, int>> key(N);
+        // Morton order of the pixels, ties in caller order: a stable LSD
+        // radix sort of the 32-bit codes, eight bits per pass
+        std::vector<uint32_t> code(N);
         for (int n = 0; n < N; ++n) {
-            uint32_t u = (uint32_t)b.uv[2 * n], v = (uint32_t)b.uv[2 * n + 1];
-            key[n] = {((uint64_t)(spread16(u) | (spread16(v) << 1)) << 32) | (uint32_t)n, n};
+            const uint32_t u = (uint32_t)b.uv[2 * n], v = (uint32_t)b.uv[2 * n + 1];
+            code[n] = spread16(u) | (spread16(v) << 1);
         }
-        std::sort(key.begin(), key.end());
+        std::vector<int> order(N), tmp(N);
+        for (int n = 0; n < N; ++n) order[n] = n;
+        for (int shift = 0; shift < 32; shift += 8) {
+            int count[257] = {0};
+            for (int i = 0; i < N; ++i) ++count[((code[order[i]] >> shift) & 255u) + 1];
+            for (int k = 0; k < 256; ++k) count[k + 1] += count[k];
+            for (int i = 0; i < N; ++i) tmp[count[(code[order[i]] >> shift) & 255u]++] = order[i];
+            order.swap(tmp);
+        }
         b.T = (N + kTile - 1) / kTile;
         b.perm.assign((size_t)b.T * kTile, -1);
-        for (int i = 0; i < N; ++i) b.perm[i] = key[i].second;
-        std::vector<int> ent_of((size_t)b.T * F, -1);  // local (tile, frame) -> entry
+        for (int i = 0; i < N; ++i) b.perm[i] = order[i];
+        // (tile, frame) entries, frames in order within a tile: each point's
+        // visibility row is read once, in order
+        std::vector<int> tile_ent0((size_t)b.T + 1, 0);  // the tile's first entry (local)
+        std::vector<unsigned> mask(F);
         const int64_t pairs0 = pairs;
         for (int t = 0; t < b.T; ++t) {
             c->tile_entry.push_back((int)c->entries.size());
             c->tile_f0.push_back(b.fo);
+            tile_ent0[t] = (int)c->entries.size() - b.e0;
+            std::fill(mask.begin(), mask.end(), 0u);
+            for (int l = 0; l < kTile; ++l) {
+                const int n = b.perm[t * kTile + l];
+                if (n < 0) continue;
+                const uint8_t* vr = b.vis.data() + (size_t)n * F;
+                const unsigned bit = 1u << l;
+                for (int f = 1; f < F; ++f) mask[f] |= vr[f] ? bit : 0u;
+            }
             for (int f = 1; f < F; ++f) {
-                unsigned mask = 0;
-                for (int l = 0; l < kTile; ++l) {
-                    const int n = b.perm[t * kTile + l];
-                    if (n >= 0 && b.vis[(size_t)n * F + f]) mask |= 1u << l;
-                }
-                if (!mask) continue;
-                ent_of[(size_t)t * F + f] = (int)c->entries.size();
-                c->entries.push_back(Entry{b.fo + f, mask, (int)pairs, b.to + t});
-                pairs += __builtin_popcount(mask);
+                if (!mask[f]) continue;
+                c->entries.push_back(Entry{b.fo + f, mask[f], (int)pairs, b.to + t});
+                pairs += __builtin_popcount(mask[f]);
             }
         }
+        tile_ent0[b.T] = (int)c->entries.size() - b.e0;
         b.e1 = (int)c->entries.size();
         b.V = pairs - pairs0;
         // frame pairs f <= g of the bundle with the (entry, entry) items of
-        // the tiles that see both (tile order: the sparse Schur kernel's
-        // fixed summation order), cut into chunks of at most kSchurChunk items
+        // the tiles that see both, in tile order (the sparse Schur kernel's
+        // fixed summation order), cut into chunks of at most kSchurChunk
+        // items. Items are counted and placed per pair from each tile's own
+        // entry pairs (a counting sort), not by scanning every tile per pair.
+        std::vector<int64_t> pbase((size_t)F + 1, 0);  // first pair index of frame f
+        for (int f = 1; f < F; ++f) pbase[f + 1] = pbase[f] + (F - f);
+        const int64_t npairs = pbase[F];
+        std::vector<int64_t> cnt((size_t)npairs + 1, 0);
+        auto each_item = [&](auto&& fn) {
+            for (int t = 0; t < b.T; ++t)
+                for (int i = tile_ent0[t]; i < tile_ent0[t + 1]; ++i) {
+                    const Entry& A = c->entries[b.e0 + i];
+                    const int fa = A.f - b.fo;
+                    for (int j = i; j < tile_ent0[t + 1]; ++j) {
+                        const Entry& Bj = c->entries[b.e0 + j];
+                        if (!(A.mask & Bj.mask)) continue;
+                        fn(pbase[fa] + (Bj.f - b.fo - fa), b.e0 + i, b.e0 + j);
+                    }
+                }
+        };
+        each_item([&](int64_t pid, int, int) { ++cnt[pid + 1]; });
+        for (int64_t q = 0; q < npairs; ++q) cnt[q + 1] += cnt[q];
+        const size_t item0 = c->pair_items.size();
+        c->pair_items.resize(item0 + (size_t)cnt[npairs]);
+        std::vector<int64_t> put(cnt.begin(), cnt.end() - 1);
+        each_item([&](int64_t pid, int ea, int eb) { c->pair_items[item0 + put[pid]++] = make_int2(ea, eb); });
         for (int f = 1; f < F; ++f)
             for (int g = f; g < F; ++g) {
                 const int p = (int)c->pair_fg.size() / 2;
-                size_t n_in_chunk = 0;
-                for (int t = 0; t < b.T; ++t) {
-                    const int ea = ent_of[(size_t)t * F + f], eb = ent_of[(size_t)t * F + g];
-                    if (!(ea >= 0 && eb >= 0 && (c->entries[ea].mask & c->entries[eb].mask))) continue;
-                    c->pair_items.push_back(make_int2(ea, eb));
-                    if (++n_in_chunk == (size_t)kSchurChunk) {
-                        c->chunk_pair.push_back(p);
-                        c->chunk_start.push_back((int)c->pair_items.size());
-                        n_in_chunk = 0;
-                    }
-                }
-                if (n_in_chunk > 0) {
+                const int64_t pid = pbase[f] + (g - f);
+                for (int64_t i0 = cnt[pid]; i0 < cnt[pid + 1]; i0 += kSchurChunk) {
                     c->chunk_pair.push_back(p);
-                    c->chunk_start.push_back((int)c->pair_items.size());
+                    c->chunk_start.push_back((int)(item0 + std::min(i0 + kSchurChunk, cnt[pid + 1])));
                 }
                 c->pair_fg.push_back(b.fo + f);
                 c->pair_fg.push_back(b.fo + g);
