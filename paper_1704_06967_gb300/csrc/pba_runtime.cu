@@ -432,23 +432,21 @@ void build_structure(pba_ctx* c)
         b.e0 = (int)c->entries.size();
         // Morton order of the pixels, ties in caller order: a stable LSD
         // radix sort of the 32-bit codes, eight bits per pass
-        std::vector<uint32_t> code(N);
+        std::vector<uint64_t> key(N), tmp(N);  // code in the high half, caller index in the low
         for (int n = 0; n < N; ++n) {
             const uint32_t u = (uint32_t)b.uv[2 * n], v = (uint32_t)b.uv[2 * n + 1];
-            code[n] = spread16(u) | (spread16(v) << 1);
+            key[n] = ((uint64_t)(spread16(u) | (spread16(v) << 1)) << 32) | (uint32_t)n;
         }
-        std::vector<int> order(N), tmp(N);
-        for (int n = 0; n < N; ++n) order[n] = n;
-        for (int shift = 0; shift < 32; shift += 8) {
+        for (int shift = 32; shift < 64; shift += 8) {
             int count[257] = {0};
-            for (int i = 0; i < N; ++i) ++count[((code[order[i]] >> shift) & 255u) + 1];
+            for (int i = 0; i < N; ++i) ++count[((key[i] >> shift) & 255u) + 1];
             for (int k = 0; k < 256; ++k) count[k + 1] += count[k];
-            for (int i = 0; i < N; ++i) tmp[count[(code[order[i]] >> shift) & 255u]++] = order[i];
-            order.swap(tmp);
+            for (int i = 0; i < N; ++i) tmp[count[(key[i] >> shift) & 255u]++] = key[i];
+            key.swap(tmp);
         }
         b.T = (N + kTile - 1) / kTile;
         b.perm.assign((size_t)b.T * kTile, -1);
-        for (int i = 0; i < N; ++i) b.perm[i] = order[i];
+        for (int i = 0; i < N; ++i) b.perm[i] = (int)(uint32_t)key[i];
         // (tile, frame) entries, frames in order within a tile: each point's
         // visibility row is read once, in order
         std::vector<int> tile_ent0((size_t)b.T + 1, 0);  // the tile's first entry (local)
@@ -459,12 +457,13 @@ void build_structure(pba_ctx* c)
             c->tile_f0.push_back(b.fo);
             tile_ent0[t] = (int)c->entries.size() - b.e0;
             std::fill(mask.begin(), mask.end(), 0u);
+            unsigned* __restrict__ mk = mask.data();
             for (int l = 0; l < kTile; ++l) {
                 const int n = b.perm[t * kTile + l];
                 if (n < 0) continue;
-                const uint8_t* vr = b.vis.data() + (size_t)n * F;
+                const uint8_t* __restrict__ vr = b.vis.data() + (size_t)n * F;
                 const unsigned bit = 1u << l;
-                for (int f = 1; f < F; ++f) mask[f] |= vr[f] ? bit : 0u;
+                for (int f = 1; f < F; ++f) mk[f] |= (unsigned)(vr[f] != 0) * bit;
             }
             for (int f = 1; f < F; ++f) {
                 if (!mask[f]) continue;
