@@ -1101,25 +1101,37 @@ pba_status autotune(pba_ctx* ctx)
         return PBA_OK;
     };
     pba_status s = PBA_OK;
-    // warps per CTA of the accumulating IC residual pass
+    // A candidate replaces the current shape only when it is faster by more
+    // than kMargin: shapes within the timing noise of each other would
+    // otherwise flip from run to run.
+    constexpr float kMargin = 0.97f;
+    // warps per CTA of the accumulating IC residual pass (the current shape
+    // is timed first)
     float best = 0.0f;
     int best_w = ctx->res_warps;
-    for (int w : {4, 8, 16}) {
+    for (int w : {ctx->res_warps, 4, 8, 16}) {
+        if (w == ctx->res_warps && best > 0.0f) continue;
         LaunchCtx L = make_launch(ctx);
         L.res_warps = w;
         float ms = 0.0f;
         s = elapsed([&]() { return launch_ic_residual(L, true, 0); }, 5, &ms);
         if (s != PBA_OK) break;
-        if (w == 4 || ms < best) {
+        if (best == 0.0f || ms < kMargin * best) {
             best = ms;
             best_w = w;
         }
     }
-    // CTAs per bundle of the factorisation (each trial re-forms A from S)
+    // CTAs per bundle of the factorisation (each trial re-forms A from S);
+    // the current cluster first
     const BundleSet bs = bundle_set(ctx);
-    int best_c = ctx->ldl_cluster;
+    const int c0 = ctx->ldl_cluster > 0 ? ctx->ldl_cluster : ldl_max_cluster();
+    int best_c = c0;
     best = 0.0f;
-    for (int C = 1; s == PBA_OK && C <= ldl_max_cluster(); C *= 2) {
+    std::vector<int> cands{c0};
+    for (int C = 1; C <= ldl_max_cluster(); C *= 2)
+        if (C != c0) cands.push_back(C);
+    for (int C : cands) {
+        if (s != PBA_OK) break;
         float ms = 0.0f;
         auto once = [&]() -> cudaError_t {
             cudaError_t e = launch_assemble_S(bs, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64,
@@ -1130,7 +1142,7 @@ pba_status autotune(pba_ctx* ctx)
                               ctx->d.err, ctx->stream, C);
         };
         s = elapsed(once, 3, &ms);
-        if (s == PBA_OK && (C == 1 || ms < best)) {
+        if (s == PBA_OK && (best == 0.0f || ms < kMargin * best)) {
             best = ms;
             best_c = C;
         }
