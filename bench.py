@@ -74,6 +74,9 @@ def parse():
                    help="keep the library's default launch shapes instead of letting it time its "
                         "candidates (residual-pass CTA size, factorisation cluster size) at the "
                         "first precompute and keep the fastest")
+    p.add_argument("--res-warps", type=int, default=0, choices=[0, 4, 8, 16],
+                   help="fix the residual pass at this many warps (entries) per CTA instead of "
+                        "autotuning it (0: autotune, or the default with --no-autotune)")
     p.add_argument("--no-graphs", action="store_true",
                    help="submit every kernel with its own launch instead of replaying CUDA graphs")
     p.add_argument("--bundles", type=int, default=256,
@@ -316,6 +319,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     b = Bundle.from_scene(sc, stream=stream, use_graphs=not args.no_graphs, autotune=args.autotune)
+    if args.res_warps:
+        b.set_tuning(args.res_warps, b.tuning()[1])  # fixed shape: no autotuning
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
     def l2_flush(k):
@@ -452,10 +457,12 @@ def run_ours(args):
     traffic_file = os.path.join(ROOT, "profiles", "ic_residual_helix30_traffic.txt")
     if os.path.exists(traffic_file):
         try:
-            tr = json.load(open(traffic_file))
-            if (tr.get("kernel_sha") == kernel_sha() and tr.get("residuals") == R
-                    and tr.get("residual_warps_per_cta") == b.tuning()[0]):
-                roofline["traffic"] = tr["dram_bytes_per_launch"]
+            # one JSON record per line, one per launch shape
+            for line in open(traffic_file):
+                tr = json.loads(line) if line.strip() else {}
+                if (tr.get("kernel_sha") == kernel_sha() and tr.get("residuals") == R
+                        and tr.get("residual_warps_per_cta") == b.tuning()[0]):
+                    roofline["traffic"] = tr["dram_bytes_per_launch"]
         except Exception:
             pass
 
@@ -499,7 +506,8 @@ def run_ours(args):
                               else "one CUDA graph replay per library call",
                               launch_shapes=dict(zip(("residual_warps_per_cta", "ldl_ctas_per_bundle"),
                                                      b.tuning()),
-                                                 chosen_by="autotuner" if args.autotune else "defaults")),
+                                                 chosen_by="fixed (--res-warps)" if args.res_warps
+                                                 else "autotuner" if args.autotune else "defaults")),
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_b,
                        "d2h_bytes_per_step": d2h_b},
                "gpu_launches": int(ic_launches), "roofline": roofline,
