@@ -98,8 +98,10 @@ typedef struct {
                                 per CTA of the IC residual pass (4, 8, 16: the number of
                                 (tile, frame) entries a CTA takes) and CTAs per bundle of
                                 the cluster that factors the reduced camera system (1, 2,
-                                4, 8, 16). Results do not depend on the choice (every sum
-                                keeps its order); see pba_get_tuning / pba_set_tuning. */
+                                4, 8, 16); a candidate replaces the current shape only when
+                                more than 3 % faster. Results do not depend on the choice
+                                (every sum keeps its order); see pba_get_tuning /
+                                pba_set_tuning. */
     double damping;          /* Levenberg-Marquardt lambda >= 0; 0 = Gauss-Newton as in the
                                 paper (Sec. 3.5). lambda > 0 scales every diagonal entry of
                                 the frame blocks H_ff and of H_dd by 1 + lambda in the
