@@ -566,3 +566,73 @@ def test_ic_contracts_linearly_from_a_modest_perturbation():
     d = hist[:-1, oracle.ST_MAXDISP]
     ratios = d[9:15] / d[8:14]
     assert (ratios < 0.9).all() and (ratios > 0.05).all()
+
+
+# ----------------------------------------------------------------------------
+# the convergence measure of Sec. 4.1: the largest pattern-centre
+# reprojection displacement between two parameter sets
+# ----------------------------------------------------------------------------
+def _disp_problem(F=4, N=7, seed=5):
+    rng = np.random.default_rng(seed)
+    W, H = 64, 48
+    fx, fy, cx, cy = 300.0, 200.0, 31.5, 23.5
+    uv = np.stack([rng.integers(4, W - 4, N), rng.integers(4, H - 4, N)], 1).astype(np.int32)
+    vis = np.ones((N, F), np.uint8)
+    pb = oracle.Problem(np.zeros((F, H, W)), uv, np.zeros((1, 2), np.int32), vis, (fx, fy, cx, cy), 0.1)
+    depths = rng.uniform(0.5, 2.0, N)
+    poses = np.tile(np.r_[np.eye(3).ravel(), 0.0, 0.0, 0.0], (F, 1))
+    return pb, poses, depths
+
+
+def test_max_reprojection_displacement_of_a_translation_is_f_d_delta():
+    """With R = I and t_z = 0 the warp is x + d t, so shifting one frame's
+    translation by (dx, dy, 0) moves every point it sees by
+    d (f_x dx, f_y dy) pixels; the measure is that length at the largest
+    inverse depth. Shifts along each axis separate f_x from f_y."""
+    pb, poses, depths = _disp_problem()
+    for delta, f_axis in (((1e-3, 0.0), pb.fx), ((0.0, 1e-3), pb.fy)):
+        shifted = poses.copy()
+        shifted[2, 9:11] += delta
+        got = oracle.max_reproj_disp(pb, poses, depths, shifted, depths)
+        assert got == pytest.approx(f_axis * depths.max() * 1e-3, rel=1e-12)
+    # both axes at once: the Euclidean length of the pixel displacement
+    shifted = poses.copy()
+    shifted[1, 9:11] += (3e-4, 4e-4)
+    got = oracle.max_reproj_disp(pb, poses, depths, shifted, depths)
+    assert got == pytest.approx(depths.max() * math.hypot(pb.fx * 3e-4, pb.fy * 4e-4), rel=1e-12)
+
+
+def test_max_reprojection_displacement_skips_unseen_pairs_and_the_reference():
+    pb, poses, depths = _disp_problem()
+    n_far = int(np.argmax(depths))
+    shifted = poses.copy()
+    shifted[0, 9] += 1.0      # the reference frame has no residuals
+    shifted[3, 9] += 1e-3
+    vis = pb.vis.copy()
+    vis[n_far, 3] = 0         # the largest inverse depth is not seen in frame 3
+    pb2 = oracle.Problem(pb.img, pb.uv, pb.pat, vis, (pb.fx, pb.fy, pb.cx, pb.cy), 0.1)
+    got = oracle.max_reproj_disp(pb2, poses, depths, shifted, depths)
+    second = np.sort(depths)[-2]
+    assert got == pytest.approx(pb.fx * second * 1e-3, rel=1e-12)
+
+
+def test_max_reprojection_displacement_of_a_depth_change_and_a_roll():
+    pb, poses, depths = _disp_problem()
+    # a depth change with t = (t_x, 0, 0): the point moves f_x t_x |Dd| pixels
+    poses_t = poses.copy()
+    poses_t[1:, 9] = 0.1
+    dd = np.linspace(-2e-3, 3e-3, pb.N)
+    got = oracle.max_reproj_disp(pb, poses_t, depths, poses_t, depths + dd)
+    assert got == pytest.approx(pb.fx * 0.1 * np.abs(dd).max(), rel=1e-9)
+    # a roll by theta about the optical axis at t = 0: the normalised centre
+    # (x, y) turns in its plane, the pixel displacement scales by (f_x, f_y)
+    th = 0.01
+    rolled = poses.copy()
+    c, s = math.cos(th), math.sin(th)
+    rolled[2, :9] = [c, -s, 0, s, c, 0, 0, 0, 1]
+    x = (pb.uv[:, 0] - pb.cx) / pb.fx
+    y = (pb.uv[:, 1] - pb.cy) / pb.fy
+    du = pb.fx * ((c - 1) * x - s * y)
+    dv = pb.fy * (s * x + (c - 1) * y)
+    got = oracle.max_reproj_disp(pb, poses, depths, rolled, depths)
+    assert got == pytest.approx(np.hypot(du, dv).max(), rel=1e-9)
