@@ -1,16 +1,26 @@
 #!/usr/bin/env python3
 """Benchmark: IC-PBA iterations/s and residuals/s against FC on one GB300.
 
-Workload: the 30-frame, 2-turn helix bundle around a textured sphere
-(640x480 FP32 images, f = 525, 20,000 points with an 8-pixel pattern,
-reduced camera system 174 x 174), perturbed by 2 deg / 0.02 / 5 %.
+Workload (default): the 100-frame orbit bundle of the precision configuration
+-- a reference frame and 100 target frames on a 30 deg orbit around a
+textured sphere on a textured ground plane, 1280x720 BF16 images, f = 900,
+200,000 points with an 8-pixel pattern (33.6 M residuals per iteration), a
+600 x 600 reduced camera system -- perturbed by 2 deg / 0.02 / 5 %.
 A step is one complete IC solve of the bundle from p_0 with the inputs
-resident in HBM: precompute (J, H, Schur complement, FP64 Cholesky and
-inverse) + 20 IC iterations. `value` = IC iterations per second over the
-timed steps (precompute amortised over the 20 iterations). FC solves of the
-same bundle (20 iterations each, Hessian and Cholesky rebuilt every
-iteration) are timed the same way beside it. L2 is flushed (512 MB write)
-between timed steps, outside the per-step CUDA events.
+resident in HBM: precompute (J, H, Schur complement, factorisation and
+inverse of the reduced system) + 20 IC iterations. `value` = IC iterations
+per second over the timed steps (precompute amortised over the 20
+iterations). FC solves of the same bundle (20 iterations each, Hessian,
+Schur complement and factorisation rebuilt every iteration) are timed the
+same way beside it. The working set (0.94 GB of stored Jacobian rows, 186 MB
+of images) is far larger than L2; L2 is also flushed (512 MB write) between
+timed steps, outside the per-step CUDA events. The other workloads
+(helix30, ring5, batch256, learned, mlp) run with --workload.
+
+The per-result error of the GPU path against the FP64 oracle (one IC step,
+one FC step, the reduced camera system, the parameters after the step) is
+measured on a point subset of the workload (every 16th point, all frames),
+where the oracle also gives the CPU baseline.
 
 --gpus N under torchrun runs N independent replicas (one bundle per rank,
 seeded by rank; no collective on the data path) and reports the aggregate.
@@ -34,7 +44,11 @@ if ROOT not in sys.path:
 
 METRIC = "IC-PBA iterations/s & residuals/s vs FC on same GB300 at equal final RMS error"
 UNIT = "iterations/s"
-SCENE = "helix30"
+SCENE = "orbit101"
+# point-subset stride of the oracle samples: the precision check and CPU
+# baseline (ours), and each step of the reference arm
+SAMPLE_STRIDE = {"orbit101": 16}
+REFERENCE_STRIDE = {"orbit101": 32}
 
 
 def log(*a):
@@ -68,8 +82,8 @@ def parse():
     p.add_argument("--iters", type=int, default=20, help="IC / FC iterations per solve")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", choices=sorted(WORKLOAD_TEXT), default=SCENE,
-                   help="helix30 (the benchmark workload), ring5 (the 5-frame case), orbit101 (the "
-                        "100-frame BF16 precision workload), batch256, learned or mlp")
+                   help="orbit101 (the benchmark workload: 100 target frames, BF16 images), helix30 "
+                        "(30 frames), ring5 (the 5-frame case), batch256, learned or mlp")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep the library's default launch shapes instead of letting it time its "
                         "candidates (residual-pass CTA size, factorisation cluster size) at the "
@@ -184,21 +198,77 @@ def measured_peaks():
 
 
 # ----------------------------------------------------------------------------
-# CPU baseline: the FP64 oracle as it stands, on a bounded sample
+# the FP64 oracle on a bounded sample: per-result errors of the GPU path and
+# the CPU baseline
 # ----------------------------------------------------------------------------
-def oracle_sample(sc, iters, n_steps=2):
+def _pose_errors(Pa, Pb):
+    import numpy as np
+    rot, tr = 0.0, 0.0
+    for f in range(1, Pa.shape[0]):
+        Ra, Rb = Pa[f, :9].reshape(3, 3), Pb[f, :9].reshape(3, 3)
+        c = float(np.clip((np.trace(Ra @ Rb.T) - 1) / 2, -1, 1))
+        rot = max(rot, math.degrees(math.acos(c)))
+        tr = max(tr, float(np.abs(Pa[f, 9:] - Pb[f, 9:]).max()))
+    return rot, tr
+
+
+def precision_sample(sc, iters, stride, stream, tuning):
+    """The GPU path against the FP64 oracle on the bundle restricted to every
+    `stride`-th point (all frames and images): one IC step and one FC step
+    from p_0 (relative error of the whole update), the anchored reduced
+    camera system S (largest entry error over the largest entry), the poses
+    and inverse depths after the IC step. The oracle's precompute and IC
+    iteration times there, scaled by `stride` (its work is linear in the
+    points), give the CPU baseline."""
+    import numpy as np
     import oracle
-    pb = oracle.Problem.from_scene(sc)
+    import synth
+    from paper_1704_06967_gb300 import Bundle
+    sub = synth.point_subset(sc, stride) if stride > 1 else sc
+    pb = oracle.Problem.from_scene(sub)
     t0 = time.perf_counter()
-    pre = oracle.ic_precompute(pb, sc.poses0, sc.depths0)
-    t_pre = time.perf_counter() - t0
-    poses, depths = sc.poses0, sc.depths0
-    t0 = time.perf_counter()
-    for _ in range(n_steps):
-        _, _, poses, depths, _ = oracle.ic_step(pb, pre, sc.poses0, sc.depths0, poses, depths)
-    t_it = (time.perf_counter() - t0) / n_steps
+    pre = oracle.ic_precompute(pb, sub.poses0, sub.depths0)
+    t1 = time.perf_counter()
+    o_dth, o_dd, o_P, o_D, o_st = oracle.ic_step(pb, pre, sub.poses0, sub.depths0, sub.poses0, sub.depths0)
+    t2 = time.perf_counter()
+    g_theta, g_d, _ = oracle.ic_gradient(pb, pre, sub.poses0, sub.depths0)
+    _, _, S_or = oracle.schur_solve(pb.F, pb.N, pre.Hff, pre.Hfd, pre.Hdd, g_theta, g_d, sub.poses0[:, 9:],
+                                    want_S=True)
+    f_dth, f_dd, _, _, _ = oracle.fc_step(pb, sub.poses0, sub.depths0)
+
+    def rel(dth, dd, r_dth, r_dd):
+        got = np.concatenate([dth[1:].ravel(), dd])
+        ref = np.concatenate([r_dth[1:].ravel(), r_dd])
+        return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+    b = Bundle.from_scene(sub, stream=stream)
+    b.set_tuning(*tuning)
+    b.precompute_ic()
+    S_gpu = b.system(fc=False)["S"]
+    b.iterate(1, stats=False)
+    dth, dd = b.last_update()
+    P1, D1 = b.params()
+    rot, tr = _pose_errors(P1, o_P)
+    drel = np.abs(D1 / o_D - 1)
+    b.set_params(sub.poses0, sub.depths0)
+    b.solve_fc(1, stats=False)
+    fdth, fdd = b.last_update()
+    b.close()
+    errors = {"sample": f"every {stride}th point ({sub.N} points, {sub.n_residuals()} residuals), all "
+                        f"{sub.F} frames, the same images; one step from p_0",
+              "ic_step_rel_err": rel(dth, dd, o_dth, o_dd),
+              "fc_step_rel_err": rel(fdth, fdd, f_dth, f_dd),
+              "S_max_err_over_max": float(np.abs(S_gpu - S_or).max() / np.abs(S_or).max()),
+              "poses_after_ic_step": {"rot_deg": rot, "trans": tr},
+              "inv_depth_after_ic_step": {"max_rel": float(drel.max()), "median_rel": float(np.median(drel))},
+              "tolerance": {"step": 1e-4, "rot_deg": 1e-3, "trans": 1e-5}}
+    t_pre, t_it = (t1 - t0) * stride, (t2 - t1) * stride
     value = iters / (t_pre + iters * t_it)
-    return value, t_pre, t_it
+    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"FP64 oracle IC precompute ({t1 - t0:.2f} s) + one IC iteration ({t2 - t1:.2f} s) on "
+                     f"every {stride}th point of the {SCENE} bundle ({sub.N} points, all frames), scaled by "
+                     f"{stride} to the whole bundle and to a {iters}-iteration solve; single thread"}
+    return errors, cpu
 
 
 # ----------------------------------------------------------------------------
@@ -257,22 +327,26 @@ def run_reference(args):
     import oracle
     import synth
     sc = synth.make_scene(SCENE)
-    pb = oracle.Problem.from_scene(sc)
+    stride = REFERENCE_STRIDE.get(SCENE, 1)
+    sub = synth.point_subset(sc, stride) if stride > 1 else sc
+    pb = oracle.Problem.from_scene(sub)
     t0 = time.perf_counter()
-    pre = oracle.ic_precompute(pb, sc.poses0, sc.depths0)
-    t_pre = time.perf_counter() - t0
-    poses, depths = sc.poses0, sc.depths0
+    pre = oracle.ic_precompute(pb, sub.poses0, sub.depths0)
+    t_pre = (time.perf_counter() - t0) * stride
+    poses, depths = sub.poses0, sub.depths0
     for _ in range(args.warmup):
-        _, _, poses, depths, _ = oracle.ic_step(pb, pre, sc.poses0, sc.depths0, poses, depths)
+        _, _, poses, depths, _ = oracle.ic_step(pb, pre, sub.poses0, sub.depths0, poses, depths)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        _, _, poses, depths, _ = oracle.ic_step(pb, pre, sc.poses0, sc.depths0, poses, depths)
-        times.append(time.perf_counter() - t0)
+        _, _, poses, depths, _ = oracle.ic_step(pb, pre, sub.poses0, sub.depths0, poses, depths)
+        times.append((time.perf_counter() - t0) * stride)
     t_it = float(np.mean(times))
     value = args.iters / (t_pre + args.iters * t_it)
-    sample = (f"one FP64 oracle IC iteration per step on the full {SCENE} bundle, precompute "
-              f"({t_pre:.2f} s) timed once and amortised over {args.iters} iterations")
+    where = (f"every {stride}th point of the {SCENE} bundle ({sub.N} points, all frames), times scaled by "
+             f"{stride} to the whole bundle" if stride > 1 else f"the full {SCENE} bundle")
+    sample = (f"one FP64 oracle IC iteration per step on {where}; precompute ({t_pre:.2f} s) timed once and "
+              f"amortised over {args.iters} iterations")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * t_it, "higher_is_better": True, "scaling": "weak",
@@ -454,7 +528,7 @@ def run_ours(args):
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
                 "traffic": None, "algorithmic_bytes_per_launch": alg_bytes,
                 "avg_launch_ms": pass_ms, "launches": int(kcounts["pass"])}
-    traffic_file = os.path.join(ROOT, "profiles", "ic_residual_helix30_traffic.txt")
+    traffic_file = os.path.join(ROOT, "profiles", f"ic_residual_{SCENE}_traffic.txt")
     if os.path.exists(traffic_file):
         try:
             # one JSON record per line, one per launch shape
@@ -488,13 +562,9 @@ def run_ours(args):
     (e2e_total,) = max_over_ranks([sum(e2e_t)], dist)
     e2e_value = aggregate_rate(iters * args.steps, world, 1e3 * e2e_total)
 
-    cpu = None
+    cpu, precision = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cv, ct_pre, ct_it = oracle_sample(sc, iters)
-        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"FP64 oracle on the full {SCENE} bundle: IC precompute ({ct_pre:.2f} s) "
-                         f"+ 2 IC iterations ({ct_it:.2f} s each), extrapolated to a "
-                         f"{iters}-iteration solve; single thread"}
+        precision, cpu = precision_sample(sc, iters, SAMPLE_STRIDE.get(SCENE, 1), stream, b.tuning())
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -523,7 +593,8 @@ def run_ours(args):
                              "fc_iterations": k_fc, "ic_ms": t_ic, "fc_ms": t_fc,
                              "fc_over_ic_time": (t_fc / t_ic) if t_ic > 0 else None},
                "kernel_ms_per_solve": {"ic": ic_break, "fc": fc_break},
-               "sliding_window": window}
+               "sliding_window": window,
+               "error_vs_fp64_oracle": precision}
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.barrier()

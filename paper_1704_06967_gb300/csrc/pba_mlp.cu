@@ -20,6 +20,7 @@
 
 #include "pba_kernels.cuh"
 #include "pba_mlp.cuh"
+#include "pba_tc.cuh"
 
 namespace pba {
 
@@ -139,64 +140,13 @@ __global__ void mlp_propose_kernel(const int* __restrict__ slot_caller, int slot
 // ---------------------------------------------------------------------------
 // tensor-core inference
 // ---------------------------------------------------------------------------
-// Operands in shared memory use the canonical K-major layout without
-// swizzle: 8 x 8 BF16 core matrices (8 rows of 16 bytes, 128 contiguous
-// bytes), core matrices adjacent along K 128 bytes apart (leading-dimension
-// byte offset) and 8-row groups (K / 8) * 128 bytes apart (stride-dimension
-// byte offset). Element (r, k) of an R x K operand sits at byte
-//   (r / 8) * (K / 8) * 128 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2.
-__host__ __device__ constexpr uint32_t canon_offset(int r, int k, int K)
-{
-    return (uint32_t)((r >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-
-// Shared-memory matrix descriptor (tcgen05): start address, leading- and
-// stride-dimension byte offsets (all >> 4), descriptor version 1 (bits
-// 46-47), no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
-}
-
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N = 128, M = 128.
-constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kMlpHidden >> 3) << 17) |
-                                ((uint32_t)(kMlpTileM >> 4) << 24);
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
+// Instruction descriptor of the layers: FP32 accumulator, BF16 A and B,
+// both K-major, N = 128, M = 128.
+constexpr uint32_t kIdescBf16 = idesc_bf16(kMlpTileM, kMlpHidden);
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate)
 {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(kIdescBf16), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-                 : "memory");
-}
-
-// bounded wait on an mbarrier phase (false: gave up)
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
-{
-    for (int i = 0; i < (1 << 16); ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
+    mma_bf16_id(tmem_d, a, b, kIdescBf16, accumulate);
 }
 
 // The give-up path of the bounded waits, exercised on purpose: one warp
@@ -220,34 +170,7 @@ __global__ void wait_selftest_kernel(int* err)
     }
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
-{
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-          "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
-{
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<const uint32_t*>(&h);
-}
 
 // Shared-memory plan of the inference kernel (bytes).
 constexpr uint32_t kOffW1 = 0;
@@ -364,10 +287,18 @@ mlp_infer_tc_kernel(const uint8_t* __restrict__ packed, int n, const float* __re
         __syncthreads();
         fence_after_sync();
     }
-    if (!ok && tid == 0) atomicOr(err, kErrTimeout);
+    if (!ok) {
+        // a wait gave up: the outputs of this CTA are undefined (the host
+        // sees kErrTimeout). The committed MMAs may still be running and
+        // writing this CTA's tensor memory, so wait for that phase again
+        // (bounded, longer) before the memory is freed.
+        if (tid == 0) atomicOr(err, kErrTimeout);
+        mbar_wait(mbar, phase ^ 1u, 1 << 20);
+        fence_after_sync();
+    }
     __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMlpHidden) : "memory");
+    if (warp == 0) tmem_dealloc(tmem, kMlpHidden);
+    if (tid == 0) mbar_inval(mbar);
 }
 
 // FP32 masters -> the inference layout (BF16 weights in the canonical

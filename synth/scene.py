@@ -442,3 +442,12 @@ def make_scene(name_or_cfg, seed_offset: int = 0, noise_free: bool = False,
                  pattern=pattern, uv=uv, vis=vis,
                  poses_gt=pack(Rrel, trel), depths_gt=d_gt,
                  poses0=pack(R0p, t0p), depths0=d0, huber_k=cfg.huber_k)
+
+
+def point_subset(scene: Scene, stride: int, offset: int = 0) -> Scene:
+    """The same bundle (frames, images, poses) with every `stride`-th point
+    only, starting at `offset`: a bounded sample of a large workload."""
+    idx = np.arange(offset, scene.N, stride)
+    return dataclasses.replace(scene, uv=np.ascontiguousarray(scene.uv[idx]),
+                               vis=np.ascontiguousarray(scene.vis[idx]),
+                               depths_gt=scene.depths_gt[idx].copy(), depths0=scene.depths0[idx].copy())
