@@ -294,6 +294,78 @@ pba_status pba_get_tuning(pba_ctx* ctx, int* res_warps, int* ldl_cluster);
  * first precompute times no candidates). Needs the CUDA device. */
 pba_status pba_set_tuning(pba_ctx* ctx, int res_warps, int ldl_cluster);
 
+/* ------------------------------------------------------------------------
+ * Point sharding of one bundle across processes, one GPU each. Every rank
+ * creates a context of the whole bundle's frames, images and poses with its
+ * own share of the points (n_bundles = 1, cfg.photometric = 0). A point's
+ * residuals, H_fd, H_dd, g_d and depth update never leave its rank; the
+ * quantities that couple the points are sums over points (Sec. 3.5: the
+ * H_ff blocks, S_off = H_pd H_dd^-1 H_dp and the right-hand side
+ * g_theta - H_pd H_dd^-1 g_d), so each call below has two halves and the
+ * caller sums the named buffers over the ranks in between (an all-reduce):
+ *
+ *   pba_shard_ic_precompute(ctx, 0)   J, W_0, H blocks at p_0 = the current
+ *       parameters; fills PBA_SHARD_IC_FRAME_SUMS and PBA_SHARD_SOFF with
+ *       this rank's sums.
+ *   pba_shard_ic_precompute(ctx, 1)   S (with the gauge prior), its factor
+ *       and S^-1 from the summed buffers (identical on every rank).
+ *   pba_shard_ic_step(ctx, k, 0)      IC iteration k: (k > 0) the update of
+ *       iteration k - 1 applied, J^T W r of this rank's residuals; fills
+ *       PBA_SHARD_IC_RHS (frame sums of the Schur right-hand side).
+ *   pba_shard_ic_step(ctx, k, 1)      the update from the summed right-hand
+ *       side (identical frame updates on every rank).
+ *   pba_shard_fc_step(ctx, k, 0)      FC iteration k: (k > 0) the last update
+ *       applied, the linearisation of this rank's residuals; fills
+ *       PBA_SHARD_FC_FRAME_SUMS (H_ff, g_theta and the Schur corrections per
+ *       frame) and PBA_SHARD_SOFF.
+ *   pba_shard_fc_step(ctx, k, 1)      S, its factorisation and the update.
+ *   pba_shard_eval(ctx, fc, n)        after n iterations: the last update
+ *       applied and the statistics of slot n (IC with fc = 0, FC with 1).
+ *
+ * k counts iterations from 0 (k <= cfg.max_stats_iters); the statistics of
+ * iteration k land in slot k (pba_shard_stats). The buffers are FP64 device
+ * arrays inside the workspace: pba_shard_count gives their length,
+ * pba_shard_export copies one to a caller device array (dev_dst, count
+ * doubles, on the context's stream) and pba_shard_import copies the summed
+ * array back. Errors: PBA_ERR_ARG (several bundles, brightness model on,
+ * bad half, k or buffer), PBA_ERR_STATE (no workspace, step before the
+ * precompute), and the statuses of the solves. */
+#define PBA_SHARD_IC_FRAME_SUMS 0  /* F x 21 packed H_ff blocks of the IC precompute */
+#define PBA_SHARD_SOFF 1           /* (6 (F - 1))^2 S_off, both triangles */
+#define PBA_SHARD_IC_RHS 2         /* F x 6 Schur right-hand side of an IC iteration */
+#define PBA_SHARD_FC_FRAME_SUMS 3  /* F x 27: 21 packed H_ff, 6 right-hand side of an FC iteration */
+pba_status pba_shard_ic_precompute(pba_ctx* ctx, int half);
+pba_status pba_shard_ic_step(pba_ctx* ctx, int k, int half);
+pba_status pba_shard_fc_step(pba_ctx* ctx, int k, int half);
+pba_status pba_shard_eval(pba_ctx* ctx, int fc, int k);
+pba_status pba_shard_count(pba_ctx* ctx, int which, int64_t* count);
+pba_status pba_shard_export(pba_ctx* ctx, int which, double* dev_dst);
+pba_status pba_shard_import(pba_ctx* ctx, int which, const double* dev_src);
+/* Raw statistics of slots 0 .. n_slots - 1 of this rank's residuals, 6
+ * doubles per slot: energy (sum of Huber rho), sum r^2, valid residual
+ * count, largest pattern-centre displacement of the step (px), |Dtheta|^2
+ * (the same on every rank), sum Dd^2. Sum over ranks, except the
+ * displacement (max) and |Dtheta|^2 (any rank). raw: host. Synchronises. */
+pba_status pba_shard_stats(pba_ctx* ctx, int n_slots, double* raw);
+
+/* How the Schur complement S_off = H_pd H_dd^-1 H_dp of the reduced camera
+ * system (Sec. 3.5 step 3) is formed, once per pba_precompute_ic and every
+ * FC iteration:
+ *  PBA_SCHUR_TENSOR (default): on the tensor cores (tcgen05.mma) over
+ *    super-tiles of 128 points, with every H_fd row and every product
+ *    H_fd / H_dd split exactly into BF16 digit slices whose FP32
+ *    accumulation is exact; the sums are added as 64-bit fixed-point
+ *    integers, so the result does not depend on the order of the work.
+ *  PBA_SCHUR_SIMT: exact FP32 products (TwoProduct) with compensated sums on
+ *    the SIMT pipes, over the co-visible (tile, frame pair) items.
+ * Both form sum_n H_fd H_fd^T w_n of the FP32 blocks with the same FP32
+ * w_n = 1 / (H_dd (1 + lambda)); they agree to ~1e-14 of the largest entry
+ * and each is deterministic run to run. The captured graphs are discarded.
+ * PBA_ERR_ARG for another value. */
+#define PBA_SCHUR_TENSOR 0
+#define PBA_SCHUR_SIMT 1
+pba_status pba_set_schur_path(pba_ctx* ctx, int path);
+
 /* Bytes this context copied host->device and device->host since it was
  * created (uploads of images, points, structure and parameters; downloads of
  * statistics, parameters, updates and systems). Host, nullable each. */

@@ -181,6 +181,36 @@ constexpr int kSchurChunk = 32;
 cudaError_t launch_schur_sparse(const DevProblem& pb, const float* Hfd, const float* Hnn,
                                 const SchurLists& sl, float2* part, double* Soff,
                                 cudaStream_t st, int* launches, const unsigned char* tile_todo = nullptr);
+
+// Schur complement on the tensor cores (pba_schur_tc.cu). Tiles are grouped
+// into super-tiles of kStTiles consecutive tiles of one bundle (K = 128
+// points); a super-tile's rows are 6 per frame that any of its tiles sees.
+constexpr int kStTiles = 4;
+constexpr int kSchurTcM = 128;  // rows of an output block (tensor-memory lanes)
+constexpr int kSchurTcN = 80;   // columns of an output block
+struct StRow {
+    int f;               // global frame
+    int e[kStTiles];     // the frame's entry in each tile of the super-tile (-1: none)
+};
+struct SchurTcLists {
+    const int4* st;      // per super-tile: (first row, frames, first tile, tiles)
+    const StRow* rows;   // the super-tiles' frames, in frame order within a super-tile
+    const int4* items;   // output blocks: (super-tile, 128-row block, 80-column block, 0)
+    short* ea;           // 6 per row: exponent bounding |H_fd| over the super-tile's points
+    short* eb;           // 6 per row: the same for |H_fd / H_dd|
+    long long* acc;      // fixed-point sums of S_off (per bundle at so, n6 x n6); zero between formations
+    int n_st, n_items;
+};
+// S_off[f][g] = sum_n H_fd(n,f) H_fd(n,g)^T / H_dd(n) for f <= g with the
+// operands split into exact BF16 slices (tcgen05.mma), written like
+// launch_schur_sparse. red: the frame sums whose first 21 components per
+// frame (stride red_stride) are the packed H_ff blocks (their diagonals
+// bound the fixed-point scale).
+cudaError_t launch_schur_tc(const DevProblem& pb, const float* Hfd, const float* Hnn, const SchurTcLists& tl,
+                            const SchurLists& sl, const double* red, int red_stride, double* Soff, int* err,
+                            cudaStream_t st, int* launches);
+// once per process and device, before any capture
+cudaError_t schur_tc_setup();
 // Per bundle (arrays at the bundle's offsets; Hff, anchor_t, rhs and active
 // indexed by global frame): S (FP64) and, when S2 is given, its double-float
 // copy over the active frames only (compact order, cmap[f] = compact index

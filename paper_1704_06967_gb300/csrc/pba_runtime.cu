@@ -101,6 +101,12 @@ struct pba_ctx {
     int n_po = 0, n_cmap = 0;
     std::vector<int> pair_fg, pair_chunk, chunk_pair, chunk_start;  // sparse Schur lists
     std::vector<int2> pair_items;
+    // tensor-core Schur complement: super-tiles (first row, frames, first
+    // tile, tiles), their frame rows and the output blocks
+    std::vector<int4> st_info, st_items;
+    std::vector<StRow> st_rows;
+    int schur_path = PBA_SCHUR_TENSOR;
+    bool ic_chunks_valid = false;  // ic_schur_part holds every chunk of the last IC formation
 
     // workspace
     bool ws_ready = false, ic_ready = false;
@@ -140,6 +146,10 @@ struct pba_ctx {
         int2* pair_items;
         float2* schur_part;     // FC: chunk sums of the Schur complement (every iteration)
         float2* ic_schur_part;  // IC: chunk sums at p_0, kept for window updates
+        int4 *st_info, *st_items;
+        StRow* st_rows;
+        short *st_ea, *st_eb;
+        long long* schur_acc;   // fixed-point S_off sums of the tensor-core path (zero between formations)
         int *active_ic, *active_fc, *cmap_ic, *cmap_fc;
         int* err;
         double* stats;
@@ -386,6 +396,12 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.pair_items, c->pair_items.size() * sizeof(int2));
     take(c->d.schur_part, c->chunk_pair.size() * 36 * sizeof(float2));
     take(c->d.ic_schur_part, c->chunk_pair.size() * 36 * sizeof(float2));
+    take(c->d.st_info, c->st_info.size() * sizeof(int4));
+    take(c->d.st_items, c->st_items.size() * sizeof(int4));
+    take(c->d.st_rows, c->st_rows.size() * sizeof(StRow));
+    take(c->d.st_ea, c->st_rows.size() * 6 * sizeof(short));
+    take(c->d.st_eb, c->st_rows.size() * 6 * sizeof(short));
+    take(c->d.schur_acc, (size_t)c->n_so * sizeof(long long));
     take(c->d.active_ic, F * 4);
     take(c->d.active_fc, F * 4);
     take(c->d.cmap_ic, (size_t)c->n_cmap * 4);
@@ -422,6 +438,9 @@ void build_structure(pba_ctx* c)
     c->chunk_pair.clear();
     c->chunk_start.assign(1, 0);
     c->pair_items.clear();
+    c->st_info.clear();
+    c->st_items.clear();
+    c->st_rows.clear();
     c->NC = (7 * (int)(c->pattern.size() / 2) + 3) / 4;
     int64_t pairs = 0;
     for (int bi = 0; bi < c->B; ++bi) {
@@ -513,6 +532,41 @@ void build_structure(pba_ctx* c)
                 c->pair_fg.push_back(b.fo + g);
                 c->pair_chunk.push_back((int)c->chunk_pair.size());
             }
+        // super-tiles of kStTiles consecutive tiles for the tensor-core Schur
+        // complement: the frames any of their tiles sees, in frame order,
+        // with each tile's entry of the frame, and the output blocks (128
+        // rows x 80 columns of the super-tile's 6-per-frame rows) that reach
+        // the upper block triangle
+        {
+            std::vector<int> frow(F, -1);
+            for (int t0 = 0; t0 < b.T; t0 += kStTiles) {
+                const int nt = std::min(kStTiles, b.T - t0);
+                const int row0 = (int)c->st_rows.size();
+                for (int j = 0; j < nt; ++j)
+                    for (int i = tile_ent0[t0 + j]; i < tile_ent0[t0 + j + 1]; ++i)
+                        frow[c->entries[b.e0 + i].f - b.fo] = 0;
+                for (int f = 1; f < F; ++f)
+                    if (frow[f] == 0) {
+                        frow[f] = (int)c->st_rows.size() - row0;
+                        c->st_rows.push_back(StRow{b.fo + f, {-1, -1, -1, -1}});
+                    }
+                for (int j = 0; j < nt; ++j)
+                    for (int i = tile_ent0[t0 + j]; i < tile_ent0[t0 + j + 1]; ++i) {
+                        const int f = c->entries[b.e0 + i].f - b.fo;
+                        c->st_rows[row0 + frow[f]].e[j] = b.e0 + i;
+                    }
+                const int nfr = (int)c->st_rows.size() - row0;
+                for (int f = 1; f < F; ++f) frow[f] = -1;
+                if (nfr == 0) continue;
+                const int sidx = (int)c->st_info.size();
+                c->st_info.push_back(make_int4(row0, nfr, b.to + t0, nt));
+                const int nr = 6 * nfr;
+                for (int mt = 0; mt * kSchurTcM < nr; ++mt)
+                    for (int nb = 0; nb * kSchurTcN < nr; ++nb)
+                        if ((mt * kSchurTcM) / 6 <= (std::min(nr, (nb + 1) * kSchurTcN) - 1) / 6)
+                            c->st_items.push_back(make_int4(sidx, mt, nb, 0));
+            }
+        }
         const int64_t n6 = 6 * (F - 1);
         BundleDesc bd{};
         bd.fo = b.fo;
@@ -668,6 +722,24 @@ SchurLists schur_lists(pba_ctx* c)
 {
     return SchurLists{c->d.pair_fg, c->d.pair_chunk, c->d.chunk_pair, c->d.chunk_start,
                       c->d.pair_items, (int)c->pair_fg.size() / 2, (int)c->chunk_pair.size()};
+}
+
+SchurTcLists schur_tc_lists(pba_ctx* c)
+{
+    return SchurTcLists{c->d.st_info, c->d.st_rows, c->d.st_items, c->d.st_ea, c->d.st_eb, c->d.schur_acc,
+                        (int)c->st_info.size(), (int)c->st_items.size()};
+}
+
+// S_off from the H_fd and H_dd of a system (red: its frame sums, H_ff
+// first) by the selected path; part / tile_todo: the SIMT path's chunk sums
+// and, for a window update, the tiles whose chunks are formed again
+cudaError_t launch_schur(pba_ctx* c, const DevProblem& pb, const float* Hfd, const float* Hnn, const double* red,
+                         int red_stride, float2* part, const unsigned char* tile_todo, int* launches)
+{
+    if (c->schur_path == PBA_SCHUR_TENSOR)
+        return launch_schur_tc(pb, Hfd, Hnn, schur_tc_lists(c), schur_lists(c), red, red_stride, c->d.Soff,
+                               c->d.err, c->stream, launches);
+    return launch_schur_sparse(pb, Hfd, Hnn, schur_lists(c), part, c->d.Soff, c->stream, launches, tile_todo);
 }
 
 SolveArgs make_solve(pba_ctx* c)
@@ -1026,6 +1098,10 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     CK(h2d(ctx, ctx->d.chunk_pair, ctx->chunk_pair.data(), sizeof(int) * ctx->chunk_pair.size()));
     CK(h2d(ctx, ctx->d.chunk_start, ctx->chunk_start.data(), sizeof(int) * ctx->chunk_start.size()));
     CK(h2d(ctx, ctx->d.pair_items, ctx->pair_items.data(), sizeof(int2) * ctx->pair_items.size()));
+    CK(h2d(ctx, ctx->d.st_info, ctx->st_info.data(), sizeof(int4) * ctx->st_info.size()));
+    CK(h2d(ctx, ctx->d.st_items, ctx->st_items.data(), sizeof(int4) * ctx->st_items.size()));
+    CK(h2d(ctx, ctx->d.st_rows, ctx->st_rows.data(), sizeof(StRow) * ctx->st_rows.size()));
+    ctx->ic_chunks_valid = false;
     for (int bi = 0; bi < ctx->B; ++bi) {
         const BundleIn& b = ctx->bun[bi];
         pba_status s = upload_params(ctx, bi, b.poses_init.data(), b.d_init.data(), 1);
@@ -1036,6 +1112,7 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     CK(ldl_setup());
     CK(iter_setup());
     CK(linalg_setup());
+    CK(schur_tc_setup());
     LAUNCH(TS_PRE, launch_setup(L.pb, ctx->d.tile_f0, ctx->d.gx, ctx->d.gy, ctx->d.I0p, ctx->d.G0p, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->ws_ready = true;
@@ -1071,8 +1148,13 @@ pba_status precompute_core(pba_ctx* ctx, const LaunchCtx& L, const BundleSet& bs
 {
     LAUNCH(TS_PRE, launch_ic_precompute(L, todo));
     LAUNCH(TS_PRE, launch_frame_reduce(L, 0, 21, ctx->d.red_ic, -1, -1, true, -1, 0, ctx->d.ic_part));
-    LAUNCHN(TS_PRE, launch_schur_sparse(L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, schur_lists(ctx),
-                                        ctx->d.ic_schur_part, ctx->d.Soff, ctx->stream, &nl, tile_todo));
+    // the SIMT path keeps its chunk sums for window updates; after a
+    // formation by the other path they are formed again in full
+    const bool simt = ctx->schur_path == PBA_SCHUR_SIMT;
+    if (simt && !ctx->ic_chunks_valid) tile_todo = nullptr;
+    LAUNCHN(TS_PRE, launch_schur(ctx, L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, ctx->d.red_ic, 21, ctx->d.ic_schur_part,
+                                 tile_todo, &nl));
+    ctx->ic_chunks_valid = simt;
     LAUNCH(TS_PRE, launch_assemble_S(bs, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64, ctx->cfg.gauge_anchor_w,
                                      ctx->cfg.damping, ctx->d.S_ic, ctx->d.active_ic, ctx->stream, ctx->d.A2,
                                      ctx->d.cmap_ic));
@@ -1285,6 +1367,199 @@ pba_status pba_iterate(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     return copy_stats(ctx, n_iters, stats);
 }
 
+// ---------------------------------------------------------------------------
+// Point sharding of one bundle (each rank a context of all frames and a share
+// of the points): the halves of the IC precompute, an IC iteration and an FC
+// iteration, between which the caller sums the frame sums and S_off over the
+// ranks (pba_shard_export / pba_shard_import). Direct launches on the
+// context's stream.
+// ---------------------------------------------------------------------------
+static pba_status shard_check(pba_ctx* ctx, int half)
+{
+    if (!ctx) return PBA_ERR_ARG;
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    if (ctx->B != 1) return fail(ctx, PBA_ERR_ARG, "point sharding takes one bundle per context");
+    if (ctx->cfg.photometric) return fail(ctx, PBA_ERR_ARG, "point sharding without the brightness model");
+    if (half != 0 && half != 1) return fail(ctx, PBA_ERR_ARG, "half must be 0 or 1");
+    return PBA_OK;
+}
+
+pba_status pba_shard_ic_precompute(pba_ctx* ctx, int half)
+{
+    pba_status s = shard_check(ctx, half);
+    if (s != PBA_OK) return s;
+    LaunchCtx L = make_launch(ctx);
+    const BundleSet bs = bundle_set(ctx);
+    if (half == 0) {
+        const int F = ctx->F;
+        CK(cudaMemcpyAsync(ctx->d.poses0_64, ctx->d.poses64, sizeof(double) * 12 * F, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d.d0_64, ctx->d.d64, sizeof(double) * ctx->Npad, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        LAUNCH(TS_PRE, launch_depth_update(L, make_solve(ctx), true, 0));
+        LAUNCH(TS_PRE, launch_ic_precompute(L));
+        LAUNCH(TS_PRE, launch_frame_reduce(L, 0, 21, ctx->d.red_ic, -1, -1, true, -1, 0, ctx->d.ic_part));
+        LAUNCHN(TS_PRE, launch_schur(ctx, L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, ctx->d.red_ic, 21,
+                                     ctx->d.ic_schur_part, nullptr, &nl));
+        ctx->ic_chunks_valid = false;  // the kept chunk sums are this rank's only
+        ctx->ic_ready = false;
+        return check_device_error(ctx);
+    }
+    LAUNCH(TS_PRE, launch_assemble_S(bs, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64, ctx->cfg.gauge_anchor_w,
+                                     ctx->cfg.damping, ctx->d.S_ic, ctx->d.active_ic, ctx->stream, ctx->d.A2,
+                                     ctx->d.cmap_ic));
+    LAUNCH(TS_PRE, launch_ldl(bs, ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv, ctx->d.cmap_ic, 0,
+                              ctx->d.err, ctx->stream, ctx->ldl_cluster));
+    LAUNCH(TS_PRE, launch_ldl_inverse(bs, ctx->d.L2, ctx->d.Linv, ctx->d.rpiv, ctx->d.cmap_ic, ctx->d.Sinv2,
+                                      ctx->stream));
+    s = check_device_error(ctx);
+    if (s == PBA_OK || s == PBA_ERR_NOT_PD) ctx->ic_ready = true;
+    return s;
+}
+
+pba_status pba_shard_ic_step(pba_ctx* ctx, int k, int half)
+{
+    pba_status s = shard_check(ctx, half);
+    if (s != PBA_OK) return s;
+    if (!ctx->ic_ready) return fail(ctx, PBA_ERR_STATE, "pba_shard_ic_precompute must come first");
+    if (k < 0 || k >= ctx->cfg.max_stats_iters + 1)
+        return fail(ctx, PBA_ERR_ARG, "k must be in [0, %d]", ctx->cfg.max_stats_iters);
+    LaunchCtx L = make_launch(ctx);
+    SolveArgs sa = make_solve(ctx);
+    sa.active = ctx->d.active_ic;
+    sa.tanchor = ctx->d.poses0_64;
+    sa.cmap = ctx->d.cmap_ic;
+    if (half == 0) {
+        LAUNCH(TS_POINT, launch_depth_update(L, sa, true, k > 0));
+        LAUNCH(TS_PASS, launch_ic_residual(L, true, k > 0));
+        LAUNCH(TS_POINT, launch_ic_point(L, true));
+        LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 6, ctx->d.red_y, k, k - 1, true, 6));
+    } else {
+        LAUNCH(TS_SOLVE, launch_ic_solve(sa, ctx->d.Sinv2, ctx->d.red_y, ctx->stream));
+        ctx->last_fc = 0;
+    }
+    return PBA_OK;
+}
+
+pba_status pba_shard_fc_step(pba_ctx* ctx, int k, int half)
+{
+    pba_status s = shard_check(ctx, half);
+    if (s != PBA_OK) return s;
+    if (k < 0 || k >= ctx->cfg.max_stats_iters + 1)
+        return fail(ctx, PBA_ERR_ARG, "k must be in [0, %d]", ctx->cfg.max_stats_iters);
+    LaunchCtx L = make_launch(ctx);
+    const BundleSet bs = bundle_set(ctx);
+    SolveArgs sa = make_solve(ctx);
+    sa.active = ctx->d.active_fc;
+    sa.tanchor = ctx->d.poses64;
+    sa.cmap = ctx->d.cmap_fc;
+    if (half == 0) {
+        LAUNCH(TS_POINT, launch_depth_update(L, sa, false, k > 0));
+        LAUNCH(TS_PASS, launch_fc_residual(L, true, k > 0));
+        LAUNCH(TS_POINT, launch_fc_point(L, true));
+        LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 27, ctx->d.red_y, k, k - 1, true, 27, 21));
+        LAUNCHN(TS_SCHUR, launch_schur(ctx, L.pb, ctx->d.Hfd_fc, ctx->d.Hnn_fc, ctx->d.red_y, 27,
+                                       ctx->d.schur_part, nullptr, &nl));
+        return PBA_OK;
+    }
+    LAUNCH(TS_SCHUR, launch_assemble_S(bs, ctx->d.red_y, 27, ctx->d.Soff, ctx->d.poses64, ctx->cfg.gauge_anchor_w,
+                                       ctx->cfg.damping, ctx->d.S_fc, ctx->d.active_fc, ctx->stream, ctx->d.A2,
+                                       ctx->d.cmap_fc, ctx->d.red_y, 27, 21));
+    LAUNCH(TS_SOLVE, launch_ldl(bs, ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv, ctx->d.cmap_fc, 1,
+                                ctx->d.err, ctx->stream, ctx->ldl_cluster));
+    LAUNCH(TS_SOLVE, launch_fc_solve_update(sa, ctx->d.L2, ctx->d.Linv, ctx->stream));
+    ctx->last_fc = 1;
+    return check_device_error(ctx);
+}
+
+pba_status pba_shard_eval(pba_ctx* ctx, int fc, int k)
+{
+    pba_status s = shard_check(ctx, 0);
+    if (s != PBA_OK) return s;
+    if (k < 0 || k >= ctx->cfg.max_stats_iters + 1)
+        return fail(ctx, PBA_ERR_ARG, "k must be in [0, %d]", ctx->cfg.max_stats_iters);
+    LaunchCtx L = make_launch(ctx);
+    SolveArgs sa = make_solve(ctx);
+    if (fc) {
+        sa.active = ctx->d.active_fc;
+        sa.tanchor = ctx->d.poses64;
+        sa.cmap = ctx->d.cmap_fc;
+        LAUNCH(TS_EVAL, launch_depth_update(L, sa, false, k > 0));
+        LAUNCH(TS_EVAL, launch_fc_residual(L, false, k > 0));
+        LAUNCH(TS_EVAL, launch_fc_point(L, false));
+    } else {
+        if (!ctx->ic_ready) return fail(ctx, PBA_ERR_STATE, "pba_shard_ic_precompute must come first");
+        sa.active = ctx->d.active_ic;
+        sa.tanchor = ctx->d.poses0_64;
+        sa.cmap = ctx->d.cmap_ic;
+        LAUNCH(TS_EVAL, launch_depth_update(L, sa, true, k > 0));
+        LAUNCH(TS_EVAL, launch_ic_residual(L, false, k > 0));
+        LAUNCH(TS_EVAL, launch_ic_point(L, false));
+    }
+    LAUNCH(TS_EVAL, launch_frame_reduce(L, 0, 0, nullptr, k, k - 1, false));
+    return check_device_error(ctx);
+}
+
+static pba_status shard_buffer(pba_ctx* ctx, int which, double** ptr, size_t* count)
+{
+    const size_t F = ctx->F;
+    switch (which) {
+    case PBA_SHARD_IC_FRAME_SUMS: *ptr = ctx->d.red_ic; *count = F * 21; return PBA_OK;
+    case PBA_SHARD_SOFF: *ptr = ctx->d.Soff; *count = (size_t)ctx->n_so; return PBA_OK;
+    case PBA_SHARD_IC_RHS: *ptr = ctx->d.red_y; *count = F * 6; return PBA_OK;
+    case PBA_SHARD_FC_FRAME_SUMS: *ptr = ctx->d.red_y; *count = F * 27; return PBA_OK;
+    default: return fail(ctx, PBA_ERR_ARG, "unknown shard buffer %d", which);
+    }
+}
+
+pba_status pba_shard_count(pba_ctx* ctx, int which, int64_t* count)
+{
+    if (!ctx || !count) return PBA_ERR_ARG;
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    double* p = nullptr;
+    size_t n = 0;
+    pba_status s = shard_buffer(ctx, which, &p, &n);
+    *count = (int64_t)n;
+    return s;
+}
+
+pba_status pba_shard_export(pba_ctx* ctx, int which, double* dev_dst)
+{
+    if (!ctx || !dev_dst) return PBA_ERR_ARG;
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    double* p = nullptr;
+    size_t n = 0;
+    pba_status s = shard_buffer(ctx, which, &p, &n);
+    if (s != PBA_OK) return s;
+    CK(cudaMemcpyAsync(dev_dst, p, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    return PBA_OK;
+}
+
+pba_status pba_shard_import(pba_ctx* ctx, int which, const double* dev_src)
+{
+    if (!ctx || !dev_src) return PBA_ERR_ARG;
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    double* p = nullptr;
+    size_t n = 0;
+    pba_status s = shard_buffer(ctx, which, &p, &n);
+    if (s != PBA_OK) return s;
+    CK(cudaMemcpyAsync(p, dev_src, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    return PBA_OK;
+}
+
+pba_status pba_shard_stats(pba_ctx* ctx, int n_slots, double* raw)
+{
+    if (!ctx || !raw) return PBA_ERR_ARG;
+    if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    if (n_slots < 1 || n_slots > ctx->stats_slots)
+        return fail(ctx, PBA_ERR_ARG, "n_slots must be in [1, %d]", ctx->stats_slots);
+    std::vector<double> h((size_t)n_slots * kStats);
+    CK(d2h(ctx, h.data(), ctx->d.stats, sizeof(double) * h.size()));
+    for (int k = 0; k < n_slots; ++k)
+        for (int q = 0; q < 6; ++q) raw[(size_t)k * 6 + q] = h[(size_t)k * kStats + q];
+    return PBA_OK;
+}
+
 pba_status pba_solve_ic(pba_ctx* ctx, int n_iters, int reanchor_every, pba_iter_stats* stats)
 {
     if (!ctx) return PBA_ERR_ARG;
@@ -1366,8 +1641,8 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
             if (ctx->cfg.photometric)
                 LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 5, ctx->d.red_photo, -1, -1, true, -1, 0,
                                                       ctx->d.ent_part + kPhotoColFc));
-            LAUNCHN(TS_SCHUR, launch_schur_sparse(L.pb, ctx->d.Hfd_fc, ctx->d.Hnn_fc, schur_lists(ctx),
-                                                  ctx->d.schur_part, ctx->d.Soff, ctx->stream, &nl));
+            LAUNCHN(TS_SCHUR, launch_schur(ctx, L.pb, ctx->d.Hfd_fc, ctx->d.Hnn_fc, ctx->d.red_y, 27,
+                                           ctx->d.schur_part, nullptr, &nl));
             LAUNCH(TS_SCHUR, launch_assemble_S(bs, ctx->d.red_y, 27, ctx->d.Soff, ctx->d.poses64,
                                                ctx->cfg.gauge_anchor_w, ctx->cfg.damping, ctx->d.S_fc,
                                                ctx->d.active_fc,
@@ -1582,6 +1857,19 @@ pba_status pba_get_tuning(pba_ctx* ctx, int* res_warps, int* ldl_cluster)
     if (!ctx) return PBA_ERR_ARG;
     if (res_warps) *res_warps = ctx->res_warps;
     if (ldl_cluster) *ldl_cluster = ctx->ldl_cluster > 0 ? ctx->ldl_cluster : ldl_max_cluster();
+    return PBA_OK;
+}
+
+pba_status pba_set_schur_path(pba_ctx* ctx, int path)
+{
+    if (!ctx) return PBA_ERR_ARG;
+    if (path != PBA_SCHUR_TENSOR && path != PBA_SCHUR_SIMT)
+        return fail(ctx, PBA_ERR_ARG, "Schur path must be PBA_SCHUR_TENSOR or PBA_SCHUR_SIMT");
+    if (path != ctx->schur_path) {
+        destroy_graphs(ctx);
+        ctx->schur_path = path;
+        ctx->ic_chunks_valid = false;
+    }
     return PBA_OK;
 }
 

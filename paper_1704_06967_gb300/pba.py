@@ -19,6 +19,7 @@ HEADERS = [os.path.join(os.path.dirname(HERE), "include", h) for h in ("pba.h", 
 
 PBA_F32, PBA_F16, PBA_BF16 = 0, 1, 2
 PBA_MEM_DEVICE, PBA_MEM_HOST = 0, 1
+PBA_SCHUR_TENSOR, PBA_SCHUR_SIMT = 0, 1
 TIMING_SLOTS = 7
 TIMING_NAMES = ["precompute", "pass", "reduce", "schur", "solve", "eval", "point"]
 STATUS = {0: "PBA_OK", 1: "PBA_ERR_ARG", 2: "PBA_ERR_STATE", 3: "PBA_ERR_CUDA",
@@ -90,6 +91,15 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pba_transfer_bytes": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], i),
         "pba_get_tuning": ([vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "pba_set_tuning": ([vp, i, i], i),
+        "pba_set_schur_path": ([vp, i], i),
+        "pba_shard_ic_precompute": ([vp, i], i),
+        "pba_shard_ic_step": ([vp, i, i], i),
+        "pba_shard_fc_step": ([vp, i, i], i),
+        "pba_shard_eval": ([vp, i, i], i),
+        "pba_shard_count": ([vp, i, ctypes.POINTER(i64)], i),
+        "pba_shard_export": ([vp, i, vp], i),
+        "pba_shard_import": ([vp, i, vp], i),
+        "pba_shard_stats": ([vp, i, vp], i),
         "pba_bundle_errors": ([vp, vp], i),
         "pba_depth_features": ([vp, i, vp], i),
         "pba_mlp_pack": ([vp, vp, vp], i),
@@ -342,6 +352,11 @@ class Batch:
         """Sets the launch shapes (as tuning() returns them); results do not
         depend on them."""
         self._check(self.lib.pba_set_tuning(self.h, int(res_warps), int(ldl_cluster)))
+
+    def set_schur_path(self, path):
+        """How the Schur complement is formed: PBA_SCHUR_TENSOR (tensor cores,
+        the default) or PBA_SCHUR_SIMT (exact products on the SIMT pipes)."""
+        self._check(self.lib.pba_set_schur_path(self.h, int(path)))
 
     def transfer_bytes(self):
         a, b = ctypes.c_int64(), ctypes.c_int64()

@@ -94,6 +94,40 @@ def test_ic_precompute_blocks_match_oracle(torch_cuda, name):
 
 
 # ----------------------------------------------------------------------------
+# the Schur complement on the tensor cores against the exact SIMT products
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["tiny", "small", "ring5", "helix30"])
+def test_tensor_core_schur_matches_exact_simt_products(torch_cuda, name):
+    """Both paths form sum_n H_fd H_fd^T / H_dd of the same FP32 blocks: the
+    tensor-core path with exact BF16 digit slices and fixed-point sums, the
+    SIMT path with exact products and compensated sums. They agree to the
+    final rounding of each (1e-12 of the largest entry is the bound), and
+    each repeats itself bit for bit. IC (S at p_0) and FC (S of the first
+    linearisation)."""
+    from paper_1704_06967_gb300.pba import PBA_SCHUR_SIMT, PBA_SCHUR_TENSOR
+    sc = synth.make_scene(name)
+    b = _bundle(sc)
+    got = {}
+    for path in (PBA_SCHUR_TENSOR, PBA_SCHUR_SIMT, PBA_SCHUR_TENSOR):
+        b.set_schur_path(path)
+        b.set_params(sc.poses0, sc.depths0)
+        b.precompute_ic()
+        S_ic = b.system(fc=False)["S"]
+        b.solve_fc(1, stats=False)
+        S_fc = b.system(fc=True)["S"]
+        if path in got:
+            assert np.array_equal(got[path][0], S_ic) and np.array_equal(got[path][1], S_fc)
+        got[path] = (S_ic, S_fc)
+    b.close()
+    for k, what in enumerate(("IC", "FC")):
+        St, Ss = got[PBA_SCHUR_TENSOR][k], got[PBA_SCHUR_SIMT][k]
+        assert np.array_equal(St, St.T)
+        err = np.abs(St - Ss).max() / np.abs(Ss).max()
+        print(f"{name} {what}: tensor-core vs SIMT Schur complement {err:.2e} of the largest entry")
+        assert err <= 1e-12, (what, err)
+
+
+# ----------------------------------------------------------------------------
 # teacher-forced single steps
 # ----------------------------------------------------------------------------
 @pytest.mark.parametrize("name", ["tiny", "small", "ring5"])
