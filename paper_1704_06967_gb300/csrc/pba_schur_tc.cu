@@ -42,9 +42,10 @@ namespace {
 
 constexpr int kTcM = kSchurTcM;                    // output rows per block (TMEM lanes)
 constexpr int kTcN = kSchurTcN;                    // output columns per block
+constexpr int kTcRows = kTcM + kTcN;               // operand rows of a block (A then B)
 constexpr int kTcSl = 6;                           // digits (slices) per operand
 constexpr int kTcKc = kTile;                       // points per K chunk (one tile)
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
 constexpr int kTcCols = 512;                       // tensor-memory columns allocated (6 x 80 used)
 constexpr uint32_t kTcASlice = kTcM * kTcKc * 2;   // bytes of one BF16 slice of A (8 KB)
 constexpr uint32_t kTcBSlice = kTcN * kTcKc * 2;   // of B (5 KB)
@@ -52,7 +53,10 @@ constexpr uint32_t kTcStage = kTcSl * (kTcASlice + kTcBSlice);
 constexpr uint32_t kTcSbo = (kTcKc / 8) * 128;     // stride between 8-row core-matrix groups
 constexpr int kTcNoRow = -1;
 constexpr short kTcZeroExp = -32768;               // exponent of a row that is zero on the super-tile
+constexpr int kTcExpLo = -80, kTcExpHi = 100;      // row exponents the FP32 splitting covers
 constexpr uint32_t kTcIdesc = idesc_bf16(kTcM, kTcN);
+// frames a block's rows can touch: 128 rows span at most 23 frames, 80 at most 15
+constexpr int kTcMFrames = 23, kTcNFrames = 15, kTcSlots = kTcMFrames + kTcNFrames;
 
 // row metadata of an output block (shared memory)
 struct TcRow {
@@ -62,10 +66,14 @@ struct TcRow {
     int fl;   // frame position within the super-tile (upper-triangle test)
 };
 
-constexpr uint32_t kTcOffW = 2 * kTcStage;                          // 128 floats: w of the points
-constexpr uint32_t kTcOffRows = kTcOffW + kStTiles * kTile * 4;     // TcRow[kTcM + kTcN]
-constexpr uint32_t kTcOffBar = kTcOffRows + (kTcM + kTcN) * sizeof(TcRow);
-constexpr uint32_t kTcSmem = kTcOffBar + 3 * 8 + 8;                 // two barriers, tmem slot, pad
+// shared-memory plan (bytes)
+constexpr uint32_t kTcStg = kTcRows * kTcKc * 4;                        // FP32 staging of one chunk
+constexpr uint32_t kTcOffStg = 2 * kTcStage;                           // two staging buffers
+constexpr uint32_t kTcOffW = kTcOffStg + 2 * kTcStg;                   // 128 floats: w of the points
+constexpr uint32_t kTcOffRows = kTcOffW + kStTiles * kTile * 4;        // TcRow[kTcRows]
+constexpr uint32_t kTcOffTab = kTcOffRows + kTcRows * sizeof(TcRow);   // int2[kTcSlots][kStTiles]
+constexpr uint32_t kTcOffBar = kTcOffTab + kTcSlots * kStTiles * 8;
+constexpr uint32_t kTcSmem = kTcOffBar + 3 * 8 + 8;                    // two barriers, tmem slot, pad
 
 // the exponent E with m < 2^E of a non-negative FP32 m (zero and
 // subnormals: the zero-row mark)
@@ -89,48 +97,64 @@ __device__ __forceinline__ int tc_global_exp(double h, bool* ok)
     return ((eh + 1) >> 1) + 1;
 }
 
-// X = round(u 2^(47 - E)) for an FP32 u with |u| < 2^E (subnormals as zero)
-__device__ __forceinline__ long long tc_fix_a(float u, int E)
+__device__ __forceinline__ float tc_pow2(int e) { return __int_as_float((e + 127) << 23); }  // e in [-126, 127]
+
+// Digits of an FP32 u with |u| < 2^E (E in [kTcExpLo, kTcExpHi]): slice s
+// is u's residual rounded to a multiple of 2^(E - 7 - 8 s) by the addition
+// of 1.5 * 2^(E + 16 - 8 s) (exact: the residual stays below that scale),
+// the residual updated exactly, the digit q 2^(7 + 8 s - E) an integer with
+// |q| <= 128.
+__device__ __forceinline__ void tc_split_a(float u, int E, float (&d)[kTcSl])
 {
-    const uint32_t b = __float_as_uint(u);
-    const int e = (int)((b >> 23) & 255u);
-    if (e == 0) return 0;
-    const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);  // u = m 2^(e - 150)
-    const int sh = 103 + E - e;                                      // X = m 2^-sh, sh >= -23
-    long long X;
-    if (sh <= 0) X = m << (-sh);
-    else if (sh >= 40) X = 0;  // m < 2^24: rounds to 0 from sh = 26
-    else X = (m + (1ll << (sh - 1))) >> sh;
-    return (b >> 31) ? -X : X;
+#pragma unroll
+    for (int s = 0; s < kTcSl; ++s) {
+        const float sig = 1.5f * tc_pow2(E + 16 - 8 * s);
+        const float q = (u + sig) - sig;
+        u -= q;
+        d[s] = q * tc_pow2(7 + 8 * s - E);
+    }
 }
 
-// X = round(u w 2^(47 - E)) of the exact product (48-bit integer mantissa)
-__device__ __forceinline__ long long tc_fix_b(float u, float w, int E)
+// Digits of the exact product u w (48-bit integer mantissa) with
+// |u w| < 2^E: X = round(u w 2^(47 - E)) as a 64-bit integer, cut into a
+// high and a balanced low 24-bit half (both exact in FP32), each split into
+// three digits by the same rounding additions (units 2^16, 2^8, 1).
+__device__ __forceinline__ void tc_split_b(float u, float w, int E, float (&d)[kTcSl])
 {
     const uint32_t bu = __float_as_uint(u), bw = __float_as_uint(w);
     const int eu = (int)((bu >> 23) & 255u), ew = (int)((bw >> 23) & 255u);
-    if (eu == 0 || ew == 0) return 0;
-    const unsigned long long m = (unsigned long long)((bu & 0x7FFFFFu) | 0x800000u) *
-                                 (unsigned long long)((bw & 0x7FFFFFu) | 0x800000u);  // [2^46, 2^48)
-    const int sh = 253 + E - eu - ew;  // X = m 2^-sh, sh >= 0 when |u w| < 2^E
-    long long X;
-    if (sh >= 50) X = 0;
-    else if (sh <= 0) X = (long long)(m << (-sh));  // sh < 0 is not reached for a valid E
-    else X = (long long)((m + (1ull << (sh - 1))) >> sh);
-    return ((bu ^ bw) >> 31) ? -X : X;
+    long long X = 0;
+    if (eu != 0 && ew != 0) {
+        const unsigned long long m = (unsigned long long)((bu & 0x7FFFFFu) | 0x800000u) *
+                                     (unsigned long long)((bw & 0x7FFFFFu) | 0x800000u);  // [2^46, 2^48)
+        const int sh = 253 + E - eu - ew;  // X = m 2^-sh, sh >= 0 when |u w| < 2^E
+        if (sh <= 0) X = (long long)(m << (-sh));
+        else if (sh < 50) X = (long long)((m + (1ull << (sh - 1))) >> sh);
+        if ((bu ^ bw) >> 31) X = -X;
+    }
+    const long long hi = (X + (1ll << 23)) >> 24;  // |hi| <= 2^23
+    float fh = (float)(int)hi;
+    float fl = (float)(int)(X - (hi << 24));       // in [-2^23, 2^23)
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const float sig = 1.5f * tc_pow2(39 - 8 * s);  // unit 2^(16 - 8 s)
+        float q = (fh + sig) - sig;
+        fh -= q;
+        d[s] = q * tc_pow2(8 * s - 16);
+        q = (fl + sig) - sig;
+        fl -= q;
+        d[s + 3] = q * tc_pow2(8 * s - 16);
+    }
 }
 
-// balanced base-256 digits of |X| <= 2^47, most significant first
-__device__ __forceinline__ void tc_digits(long long X, int (&q)[kTcSl])
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, bool valid)
 {
-#pragma unroll
-    for (int i = kTcSl - 1; i > 0; --i) {
-        const int d = (int)((X + 128) & 255) - 128;
-        q[i] = d;
-        X = (X - d) >> 8;
-    }
-    q[0] = (int)X;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 }  // namespace
 
@@ -192,8 +216,8 @@ schur_tc_kernel(DevProblem pb, const float* __restrict__ Hfd, const float* __res
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float* wsm = reinterpret_cast<float*>(sm + kTcOffW);
-    TcRow* mrow = reinterpret_cast<TcRow*>(sm + kTcOffRows);
-    TcRow* nrow = mrow + kTcM;
+    TcRow* meta = reinterpret_cast<TcRow*>(sm + kTcOffRows);  // A rows, then B rows
+    int2* tab = reinterpret_cast<int2*>(sm + kTcOffTab);      // (first H_fd float, mask) per frame slot and tile
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kTcOffBar);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
     const uint32_t mbar[2] = {smem_u32(bar), smem_u32(bar + 1)};
@@ -217,7 +241,8 @@ schur_tc_kernel(DevProblem pb, const float* __restrict__ Hfd, const float* __res
         const int nrows = 6 * info.y;
         const BundleDesc bd = pb.bund[pb.frame_bundle[rows[info.x].f]];
         const int n6 = 6 * (bd.F - 1);
-        // weights of the super-tile's points and the block's row metadata
+        const int flm0 = (item.y * kTcM) / 6, fln0 = (item.z * kTcN) / 6;  // first frames of the blocks
+        // weights of the points, row metadata, each frame slot's entries
         if (tid < kStTiles * kTile) {
             float w = 0.0f;
             if (tid < info.w * kTile) {
@@ -225,10 +250,10 @@ schur_tc_kernel(DevProblem pb, const float* __restrict__ Hfd, const float* __res
                 w = h > 0.0f ? 1.0f / (h * pb.damp1) : 0.0f;
             }
             wsm[tid] = w;
-        }
-        if (tid < kTcM + kTcN) {
-            const bool is_m = tid < kTcM;
-            const int rr = is_m ? item.y * kTcM + tid : item.z * kTcN + (tid - kTcM);
+        } else if (tid < kStTiles * kTile + kTcRows) {
+            const int r = tid - kStTiles * kTile;
+            const bool is_m = r < kTcM;
+            const int rr = is_m ? item.y * kTcM + r : item.z * kTcN + (r - kTcM);
             TcRow m{kTcNoRow, 0, 0, 0};
             if (rr < nrows) {
                 const int fl = rr / 6, a = rr - 6 * fl;
@@ -237,63 +262,100 @@ schur_tc_kernel(DevProblem pb, const float* __restrict__ Hfd, const float* __res
                 const int q = a * 6 - (a * (a - 1)) / 2;  // packed H_ff diagonal (a, a)
                 const int eg = tc_global_exp(red[(size_t)f * red_stride + q], &have);
                 const short e = (is_m ? ea : eb)[(size_t)info.x * 6 + rr];
-                if (have && e != kTcZeroExp) m = TcRow{6 * (f - bd.fo - 1) + a, eg, (int)e, fl};
+                if (have && e != kTcZeroExp) {
+                    if (e < kTcExpLo || e > kTcExpHi) atomicOr(err, kErrNonFinite);  // beyond the FP32 splitting
+                    else m = TcRow{6 * (f - bd.fo - 1) + a, eg, (int)e, fl};
+                }
             }
-            (is_m ? mrow[tid] : nrow[tid - kTcM]) = m;
+            meta[r] = m;
+        } else if (tid < kStTiles * kTile + kTcRows + kTcSlots * kStTiles) {
+            const int j = tid - kStTiles * kTile - kTcRows, slot = j / kStTiles, c = j % kStTiles;
+            const int fl = slot < kTcMFrames ? flm0 + slot : fln0 + slot - kTcMFrames;
+            int2 t = make_int2(0, 0);
+            if (fl < info.y && c < info.w) {
+                const int e = rows[info.x + fl].e[c];
+                if (e >= 0) {
+                    const Entry en = pb.entries[e];
+                    t = make_int2(en.pair_off * 6, (int)en.mask);
+                }
+            }
+            tab[j] = t;
         }
         __syncthreads();
 
-        // K chunks (the super-tile's tiles): slices into buffer c & 1, then
-        // one thread issues the chunk's MMAs
+        // FP32 staging of chunk c (one tile): element (row, lane) of the
+        // block's operand rows, zero where the lane does not see the frame
+        auto stage = [&](int c) {
+            float* stg = reinterpret_cast<float*>(sm + kTcOffStg + (c & 1) * kTcStg);
+            const uint32_t sdst = smem_u32(stg);
+            for (int i = tid; i < kTcRows * kTile; i += kTcThreads) {
+                const int r = i >> 5, l = i & 31;
+                const TcRow mr = meta[r];
+                const float* src = Hfd;
+                bool valid = false;
+                if (mr.g != kTcNoRow) {
+                    const int rr = r < kTcM ? item.y * kTcM + r : item.z * kTcN + (r - kTcM);
+                    const int fl = rr / 6, a = rr - 6 * fl;
+                    const int slot = r < kTcM ? fl - flm0 : kTcMFrames + fl - fln0;
+                    const int2 t = tab[slot * kStTiles + c];
+                    const unsigned mask = (unsigned)t.y;
+                    if ((mask >> l) & 1u) {
+                        src = Hfd + t.x + a * __popc(mask) + __popc(mask & ((1u << l) - 1u));
+                        valid = true;
+                    }
+                }
+                cp_async4(sdst + 4u * i, src, valid);
+            }
+            cp_async_commit();
+        };
+        // K chunks (the super-tile's tiles): chunk c + 1 is staged while
+        // chunk c's digits are formed into buffer c & 1; then one thread
+        // issues chunk c's MMAs
+        stage(0);
         for (int c = 0; c < info.w; ++c) {
             const int buf = c & 1;
+            if (c + 1 < info.w) {
+                stage(c + 1);
+                cp_async_wait_one();
+            } else {
+                cp_async_wait_all();
+            }
             if (c >= 2) {
                 ok = __syncthreads_and(mbar_wait(mbar[buf], phase[buf]));
                 phase[buf] ^= 1u;
                 if (!ok) break;
+            } else {
+                __syncthreads();
             }
+            const float* stg = reinterpret_cast<const float*>(sm + kTcOffStg + buf * kTcStg);
             uint8_t* sA = sm + buf * kTcStage;
             uint8_t* sB = sA + kTcSl * kTcASlice;
-            for (int task = tid; task < (kTcM + kTcN) * 4; task += kTcThreads) {
-                const bool is_a = task < kTcM * 4;
-                const int tt = is_a ? task : task - kTcM * 4;
-                const int r = tt >> 2, g = tt & 3;  // operand row, group of 8 points
-                const int rr = is_a ? item.y * kTcM + r : item.z * kTcN + r;
-                int q[8][kTcSl];
+            for (int task = tid; task < kTcRows * 4; task += kTcThreads) {
+                const int r = task >> 2, g = task & 3;  // operand row, group of 8 points
+                const bool is_a = r < kTcM;
+                const int e = meta[r].e;
+                const float4* sp = reinterpret_cast<const float4*>(stg + r * kTile + 8 * g);
+                const float4 u0 = sp[0], u1 = sp[1];
+                const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+                float d[8][kTcSl];
+                if (is_a) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
+                    for (int j = 0; j < 8; ++j) tc_split_a(u[j], e, d[j]);
+                } else {
+                    const float4* wp = reinterpret_cast<const float4*>(wsm + c * kTile + 8 * g);
+                    const float4 w0 = wp[0], w1 = wp[1];
+                    const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-                    for (int s = 0; s < kTcSl; ++s) q[j][s] = 0;
-                const TcRow meta = is_a ? mrow[r] : nrow[r];
-                if (meta.g != kTcNoRow) {
-                    const int fl = rr / 6, a = rr - 6 * fl;
-                    const int e = rows[info.x + fl].e[c];
-                    if (e >= 0) {
-                        const Entry en = pb.entries[e];
-                        const int nvis = __popc(en.mask);
-                        const float* hp = Hfd + (size_t)en.pair_off * 6 + (size_t)a * nvis;
-                        const unsigned below = en.mask & ((1u << (8 * g)) - 1u);
-                        int rank = __popc(below);
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int l = 8 * g + j;
-                            if ((en.mask >> l) & 1u) {
-                                const float u = __ldg(hp + rank);
-                                ++rank;
-                                const long long X = is_a ? tc_fix_a(u, meta.e)
-                                                         : tc_fix_b(u, wsm[c * kTile + l], meta.e);
-                                tc_digits(X, q[j]);
-                            }
-                        }
-                    }
+                    for (int j = 0; j < 8; ++j) tc_split_b(u[j], w[j], e, d[j]);
                 }
-                uint8_t* dst = (is_a ? sA : sB) + (r >> 3) * kTcSbo + g * 128 + (r & 7) * 16;
+                const int rl = is_a ? r : r - kTcM;
+                uint8_t* dst = (is_a ? sA : sB) + (rl >> 3) * kTcSbo + g * 128 + (rl & 7) * 16;
                 const uint32_t sl = is_a ? kTcASlice : kTcBSlice;
 #pragma unroll
                 for (int s = 0; s < kTcSl; ++s)
                     *reinterpret_cast<uint4*>(dst + s * sl) =
-                        make_uint4(pack_bf16x2((float)q[0][s], (float)q[1][s]), pack_bf16x2((float)q[2][s], (float)q[3][s]),
-                                   pack_bf16x2((float)q[4][s], (float)q[5][s]), pack_bf16x2((float)q[6][s], (float)q[7][s]));
+                        make_uint4(pack_bf16x2(d[0][s], d[1][s]), pack_bf16x2(d[2][s], d[3][s]),
+                                   pack_bf16x2(d[4][s], d[5][s]), pack_bf16x2(d[6][s], d[7][s]));
             }
             fence_async_smem();
             fence_before_sync();
@@ -315,6 +377,10 @@ schur_tc_kernel(DevProblem pb, const float* __restrict__ Hfd, const float* __res
                 mma_commit(mbar[buf]);
             }
         }
+        if (!ok) {
+            cp_async_wait_all();
+            break;
+        }
         // every outstanding commit (the last chunk's, and the one before it)
         for (int c = (info.w >= 2 ? info.w - 2 : 0); c < info.w && ok; ++c) {
             const int buf = c & 1;
@@ -325,22 +391,22 @@ schur_tc_kernel(DevProblem pb, const float* __restrict__ Hfd, const float* __res
         fence_after_sync();
 
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (the block's
-        // rows) and the 16-column groups w / 4, w / 4 + 2, ...
+        // rows) and the 8-column groups w / 4, w / 4 + 4, ...
         {
             const int r = 32 * (warp & 3) + lane;
-            const TcRow mr = mrow[r];
+            const TcRow mr = meta[r];
             const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
 #pragma unroll 1
-            for (int cg = warp >> 2; cg < kTcN / 16; cg += 2) {
-                const int col0 = 16 * cg;
-                float D[kTcSl][16];
+            for (int cg = warp >> 2; cg < kTcN / 8; cg += kTcThreads / 128) {
+                const int col0 = 8 * cg;
+                float D[kTcSl][8];
 #pragma unroll
-                for (int k = 0; k < kTcSl; ++k) tmem_ld16(trow + k * kTcN + col0, D[k]);
+                for (int k = 0; k < kTcSl; ++k) tmem_ld8(trow + k * kTcN + col0, D[k]);
                 tmem_wait_ld();
                 if (mr.g == kTcNoRow) continue;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const TcRow nc = nrow[col0 + j];
+                for (int j = 0; j < 8; ++j) {
+                    const TcRow nc = meta[kTcM + col0 + j];
                     if (nc.g == kTcNoRow) continue;
                     // upper block triangle; in a diagonal block a <= b
                     if (mr.fl > nc.fl || (mr.fl == nc.fl && mr.g > nc.g)) continue;
@@ -384,7 +450,6 @@ schur_tc_kernel(DevProblem pb, const float* __restrict__ Hfd, const float* __res
         mbar_inval(mbar[1]);
     }
 }
-
 // S_off of every frame pair f <= g from the fixed-point sums (both
 // triangles), which are reset to zero for the next formation.
 __global__ void schur_tc_finish_kernel(const int* __restrict__ pair_fg, int n_pairs,
