@@ -403,8 +403,10 @@ pba_status pba_downsample(const void* src, pba_dtype dtype, int n_frames, int w,
  * PBA_NOALLOC_MAX_FRAMES (about 1.2 MB, held by every GPU that loads the
  * library until exit); larger problems return PBA_ERR_TOO_LARGE without
  * touching the GPU. The function calls no cudaMalloc/cudaFree. Its first
- * call on a device looks up the array's device address (make that first
- * call before any stream capture). Every call on a device shares the array:
+ * call in a CUDA context of a device looks up the array's device address in
+ * that context (make that first call before any stream capture; a later
+ * context on the device, e.g. after cudaDeviceReset, gets its own lookup on
+ * its first call). Every call on a device shares the array:
  * calls that overlap on the GPU (concurrent streams) race and must be
  * serialised by the caller. Returns PBA_ERR_ARG for invalid arguments and
  * PBA_ERR_CUDA when a launch fails. */

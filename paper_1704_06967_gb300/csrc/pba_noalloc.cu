@@ -13,8 +13,12 @@
 // The array is a file-scope __device__ symbol: every GPU that loads the
 // library holds it until the process exits, and every call on a device
 // shares it. In host code its name is only a host-side stand-in, so the
-// device address is looked up once per device with cudaGetSymbolAddress and
-// cached; kernels receive that address.
+// device address is looked up with cudaGetSymbolAddress and cached per
+// device together with the identity of the CUDA context it belongs to; a
+// call from another context on that device (after cudaDeviceReset, or with
+// a context the caller made current) looks the address up again.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "pba_kernels.cuh"
@@ -35,9 +39,38 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // context id the address belongs to
 
-// Device address of the scratch array on the current device (looked up on
-// the first call per device).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Identity of the calling thread's current context (0: none current). The
+// two driver functions are reached through the runtime's entry-point query,
+// so the library needs no link against the driver library.
+unsigned long long current_context_id()
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+            qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess)
+            return 0;
+        get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+        get_id = reinterpret_cast<CtxGetIdFn>(b);
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the scratch array in the current context of the
+// current device (looked up again whenever that context changes).
 cudaError_t scratch_address(void** out)
 {
     int dev = 0;
@@ -45,11 +78,13 @@ cudaError_t scratch_address(void** out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // makes the device's context current if none is
         if (e != cudaSuccess) return e;
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = current_context_id();
     }
     *out = g_scratch_addr[dev];
     return cudaSuccess;
