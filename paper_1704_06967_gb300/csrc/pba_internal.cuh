@@ -110,6 +110,28 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
+// a 16-byte read-only load of data streamed once per pass (the stored J
+// rows): not allocated in L1 and, with an evict-first L2 policy
+// (l2_evict_first_policy()), the first to leave L2, so that it does not push
+// the image lines the gathers reuse out of either cache
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t l2_evict_first_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ float4 ld_stream4(const float4* p, uint64_t pol)
+{
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
+// ---------------------------------------------------------------------------
 // image access (offsets are unsigned 32-bit: the host checks that the whole
 // stack, F * H * pitch elements over all bundles, stays below 2^32)
 // ---------------------------------------------------------------------------

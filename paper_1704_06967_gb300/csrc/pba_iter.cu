@@ -333,6 +333,7 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
         if (kAccum) {
             const int NC = (7 * P + 3) / 4, nvis = __popc(en.mask);
             const float4* src = J4 + (size_t)en.pair_off * NC + rank_of(en.mask, lane);
+            const uint64_t pol = l2_evict_first_policy();
             // rows of four pattern pixels (seven float4 chunks) at a time,
             // loaded after the taps are consumed (register pressure)
 #pragma unroll
@@ -343,7 +344,7 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
 #pragma unroll
                     for (int q = 0; q < 7; ++q) {
                         float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                        if (7 * g + q < NC) v = __ldg(src + (size_t)(7 * g + q) * nvis);
+                        if (7 * g + q < NC) v = ld_stream4(src + (size_t)(7 * g + q) * nvis, pol);
                         Jr[4 * q] = v.x;
                         Jr[4 * q + 1] = v.y;
                         Jr[4 * q + 2] = v.z;

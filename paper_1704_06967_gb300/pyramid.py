@@ -46,10 +46,14 @@ def level_points(uv, level, W, H, pattern):
 
 
 def solve_coarse_to_fine(images, poses0, intrinsics, uv, inv_depth, vis, *, pattern, huber_k, levels=3,
-                         iters=(10, 10, 20), method="ic", reanchor_every=3, damping=0.0, stream=None):
+                         iters=(10, 10, 20), method="ic", reanchor_every=3, damping=0.0, stream=None,
+                         level_ms=None):
     """Solves from the coarsest level (levels - 1) to the full resolution.
     images: [F, H, W] CUDA tensor; the rest as for Bundle. iters: iterations
-    per level, coarsest first. Returns (poses, inv_depth, [stats per level])."""
+    per level, coarsest first. Returns (poses, inv_depth, [stats per level]).
+    level_ms: a list that receives, per level, the device time (ms, CUDA
+    events on the stream) of the level's solve call (the image reduction and
+    the context set-up excluded)."""
     poses = np.array(poses0, dtype=np.float64)
     depth = np.array(inv_depth, dtype=np.float64)
     K = np.asarray(intrinsics, dtype=np.float64)
@@ -66,10 +70,19 @@ def solve_coarse_to_fine(images, poses0, intrinsics, uv, inv_depth, vis, *, patt
         b = Bundle(img, poses, Kl, uvl[keep], depth[keep], None if vis is None else vis[keep], pattern=pattern,
                    huber_k=huber_k, stream=stream, damping=damping)
         n = iters[levels - 1 - lvl]
+        if level_ms is not None:
+            import torch
+            s_ = b.stream
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s_)
         if method == "ic":
             st = b.solve_ic(n, reanchor_every=reanchor_every)
         else:
             st = b.solve_fc(n)
+        if level_ms is not None:
+            e1.record(s_)
+            e1.synchronize()
+            level_ms.append(e0.elapsed_time(e1))
         p, d = b.params()
         b.close()
         poses = p
