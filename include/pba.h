@@ -351,7 +351,11 @@ pba_status pba_shard_stats(pba_ctx* ctx, int n_slots, double* raw);
 /* How the Schur complement S_off = H_pd H_dd^-1 H_dp of the reduced camera
  * system (Sec. 3.5 step 3) is formed, once per pba_precompute_ic and every
  * FC iteration:
- *  PBA_SCHUR_TENSOR (default): on the tensor cores (tcgen05.mma) over
+ *  PBA_SCHUR_AUTO (default): the tensor cores when the bundle set has at
+ *    least four of the tensor path's 128 x 80 output blocks per SM, else the
+ *    SIMT products (the faster of the two on small bundles); the choice
+ *    depends only on the problem's structure and the device's SM count.
+ *  PBA_SCHUR_TENSOR: on the tensor cores (tcgen05.mma) over
  *    super-tiles of 128 points, with every H_fd row and every product
  *    H_fd / H_dd split exactly into BF16 digit slices whose FP32
  *    accumulation is exact; the sums are added as 64-bit fixed-point
@@ -364,6 +368,7 @@ pba_status pba_shard_stats(pba_ctx* ctx, int n_slots, double* raw);
  * PBA_ERR_ARG for another value. */
 #define PBA_SCHUR_TENSOR 0
 #define PBA_SCHUR_SIMT 1
+#define PBA_SCHUR_AUTO 2
 pba_status pba_set_schur_path(pba_ctx* ctx, int path);
 
 /* Bytes this context copied host->device and device->host since it was

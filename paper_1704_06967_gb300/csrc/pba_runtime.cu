@@ -105,7 +105,8 @@ struct pba_ctx {
     // tile, tiles), their frame rows and the output blocks
     std::vector<int4> st_info, st_items;
     std::vector<StRow> st_rows;
-    int schur_path = PBA_SCHUR_TENSOR;
+    int schur_path = PBA_SCHUR_AUTO;
+    int n_sm = 0;  // SMs of the context's device (the automatic Schur path choice)
     bool ic_chunks_valid = false;  // ic_schur_part holds every chunk of the last IC formation
 
     // workspace
@@ -724,6 +725,19 @@ SchurLists schur_lists(pba_ctx* c)
                       c->d.pair_items, (int)c->pair_fg.size() / 2, (int)c->chunk_pair.size()};
 }
 
+// The automatic choice: the tensor cores once the bundle set has at least
+// four output blocks of the tensor-core formation per SM (below that the
+// SIMT former's co-visible items are fewer than the tensor path's fixed
+// per-block work: helix30, 30 frames, 20,000 points, forms S in 23 us on
+// the SIMT pipes against 40 us; orbit101 in 1.17 ms on the tensor cores
+// against 1.91 ms)
+int effective_schur_path(const pba_ctx* c)
+{
+    if (c->schur_path != PBA_SCHUR_AUTO) return c->schur_path;
+    return (int64_t)c->st_items.size() >= 4 * (int64_t)(c->n_sm > 0 ? c->n_sm : 152) ? PBA_SCHUR_TENSOR
+                                                                                    : PBA_SCHUR_SIMT;
+}
+
 SchurTcLists schur_tc_lists(pba_ctx* c)
 {
     return SchurTcLists{c->d.st_info, c->d.st_rows, c->d.st_items, c->d.st_ea, c->d.st_eb, c->d.schur_acc,
@@ -736,7 +750,7 @@ SchurTcLists schur_tc_lists(pba_ctx* c)
 cudaError_t launch_schur(pba_ctx* c, const DevProblem& pb, const float* Hfd, const float* Hnn, const double* red,
                          int red_stride, float2* part, const unsigned char* tile_todo, int* launches)
 {
-    if (c->schur_path == PBA_SCHUR_TENSOR)
+    if (effective_schur_path(c) == PBA_SCHUR_TENSOR)
         return launch_schur_tc(pb, Hfd, Hnn, schur_tc_lists(c), schur_lists(c), red, red_stride, c->d.Soff,
                                c->d.err, c->stream, launches);
     return launch_schur_sparse(pb, Hfd, Hnn, schur_lists(c), part, c->d.Soff, c->stream, launches, tile_todo);
@@ -1113,6 +1127,11 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     CK(iter_setup());
     CK(linalg_setup());
     CK(schur_tc_setup());
+    {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev));
+    }
     LAUNCH(TS_PRE, launch_setup(L.pb, ctx->d.tile_f0, ctx->d.gx, ctx->d.gy, ctx->d.I0p, ctx->d.G0p, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->ws_ready = true;
@@ -1150,7 +1169,7 @@ pba_status precompute_core(pba_ctx* ctx, const LaunchCtx& L, const BundleSet& bs
     LAUNCH(TS_PRE, launch_frame_reduce(L, 0, 21, ctx->d.red_ic, -1, -1, true, -1, 0, ctx->d.ic_part));
     // the SIMT path keeps its chunk sums for window updates; after a
     // formation by the other path they are formed again in full
-    const bool simt = ctx->schur_path == PBA_SCHUR_SIMT;
+    const bool simt = effective_schur_path(ctx) == PBA_SCHUR_SIMT;
     if (simt && !ctx->ic_chunks_valid) tile_todo = nullptr;
     LAUNCHN(TS_PRE, launch_schur(ctx, L.pb, ctx->d.Hfd_ic, ctx->d.Hnn_ic, ctx->d.red_ic, 21, ctx->d.ic_schur_part,
                                  tile_todo, &nl));
@@ -1863,8 +1882,8 @@ pba_status pba_get_tuning(pba_ctx* ctx, int* res_warps, int* ldl_cluster)
 pba_status pba_set_schur_path(pba_ctx* ctx, int path)
 {
     if (!ctx) return PBA_ERR_ARG;
-    if (path != PBA_SCHUR_TENSOR && path != PBA_SCHUR_SIMT)
-        return fail(ctx, PBA_ERR_ARG, "Schur path must be PBA_SCHUR_TENSOR or PBA_SCHUR_SIMT");
+    if (path != PBA_SCHUR_TENSOR && path != PBA_SCHUR_SIMT && path != PBA_SCHUR_AUTO)
+        return fail(ctx, PBA_ERR_ARG, "Schur path must be PBA_SCHUR_TENSOR, PBA_SCHUR_SIMT or PBA_SCHUR_AUTO");
     if (path != ctx->schur_path) {
         destroy_graphs(ctx);
         ctx->schur_path = path;

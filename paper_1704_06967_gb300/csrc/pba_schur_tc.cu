@@ -73,7 +73,7 @@ constexpr uint32_t kTcOffW = kTcOffStg + 2 * kTcStg;                   // 128 fl
 constexpr uint32_t kTcOffRows = kTcOffW + kStTiles * kTile * 4;        // TcRow[kTcRows]
 constexpr uint32_t kTcOffTab = kTcOffRows + kTcRows * sizeof(TcRow);   // int2[kTcSlots][kStTiles]
 constexpr uint32_t kTcOffBar = kTcOffTab + kTcSlots * kStTiles * 8;
-constexpr uint32_t kTcSmem = kTcOffBar + 3 * 8 + 8;                    // two barriers, tmem slot, pad
+constexpr uint32_t kTcSmem = kTcOffBar + 8 * 8;                        // six barriers, tmem slot, abort flag
 
 // the exponent E with m < 2^E of a non-negative FP32 m (zero and
 // subnormals: the zero-row mark)
@@ -206,7 +206,32 @@ schur_tc_scale_kernel(DevProblem pb, const float* __restrict__ Hfd, const float*
     }
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+// Converter warps: all but the last warp of the CTA. The last warp issues
+// the MMAs (its lane 0) and owns the tensor memory.
+constexpr int kTcConv = kTcThreads;  // converter threads (16 warps)
+constexpr int kTcMmaWarp = kTcConv / 32;
+
+__device__ __forceinline__ void conv_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kTcConv) : "memory"); }
+
+// converter barrier that also ANDs a flag over the converter threads
+__device__ __forceinline__ bool conv_sync_and(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kTcConv)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads + 32, 1)
 schur_tc_kernel(DevProblem pb, const float* __restrict__ Hfd, const float* __restrict__ Hnn,
                 const int4* __restrict__ st, const StRow* __restrict__ rows, const int4* __restrict__ items,
                 int n_items, const short* __restrict__ ea, const short* __restrict__ eb,
@@ -219,12 +244,22 @@ schur_tc_kernel(DevProblem pb, const float* __restrict__ Hfd, const float* __res
     TcRow* meta = reinterpret_cast<TcRow*>(sm + kTcOffRows);  // A rows, then B rows
     int2* tab = reinterpret_cast<int2*>(sm + kTcOffTab);      // (first H_fd float, mask) per frame slot and tile
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kTcOffBar);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
-    const uint32_t mbar[2] = {smem_u32(bar), smem_u32(bar + 1)};
-    if (warp == 0) tmem_alloc(tmem_slot, kTcCols);
+    // full[b]: chunk in buffer b formed (one arrival per converter warp);
+    // empty[b]: its MMAs done (commit); tfree: the epilogue has read the
+    // accumulators (one arrival per converter warp); fin: every MMA done
+    const uint32_t full0 = smem_u32(bar), empty0 = smem_u32(bar + 2), tfree = smem_u32(bar + 4),
+                   fin = smem_u32(bar + 5);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 6);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + 7);
+    if (warp == kTcMmaWarp) tmem_alloc(tmem_slot, kTcCols);
     if (tid == 0) {
-        mbar_init(mbar[0], 1);
-        mbar_init(mbar[1], 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(full0 + 8 * b, kTcConv / 32);
+            mbar_init(empty0 + 8 * b, 1);
+        }
+        mbar_init(tfree, kTcConv / 32);
+        mbar_init(fin, 1);
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fence_before_sync();
@@ -232,224 +267,259 @@ schur_tc_kernel(DevProblem pb, const float* __restrict__ Hfd, const float* __res
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
     const uint32_t sbase = smem_u32(sm);
-    uint32_t phase[2] = {0u, 0u};
-    bool ok = true;
 
-    for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
-        const int4 item = items[it];
-        const int4 info = st[item.x];  // first row, frames, first tile, tiles
-        const int nrows = 6 * info.y;
-        const BundleDesc bd = pb.bund[pb.frame_bundle[rows[info.x].f]];
-        const int n6 = 6 * (bd.F - 1);
-        const int flm0 = (item.y * kTcM) / 6, fln0 = (item.z * kTcN) / 6;  // first frames of the blocks
-        // weights of the points, row metadata, each frame slot's entries
-        if (tid < kStTiles * kTile) {
-            float w = 0.0f;
-            if (tid < info.w * kTile) {
-                const float h = Hnn[(size_t)(info.z + tid / kTile) * kTile + (tid % kTile)];
-                w = h > 0.0f ? 1.0f / (h * pb.damp1) : 0.0f;
-            }
-            wsm[tid] = w;
-        } else if (tid < kStTiles * kTile + kTcRows) {
-            const int r = tid - kStTiles * kTile;
-            const bool is_m = r < kTcM;
-            const int rr = is_m ? item.y * kTcM + r : item.z * kTcN + (r - kTcM);
-            TcRow m{kTcNoRow, 0, 0, 0};
-            if (rr < nrows) {
-                const int fl = rr / 6, a = rr - 6 * fl;
-                const int f = rows[info.x + fl].f;
-                bool have;
-                const int q = a * 6 - (a * (a - 1)) / 2;  // packed H_ff diagonal (a, a)
-                const int eg = tc_global_exp(red[(size_t)f * red_stride + q], &have);
-                const short e = (is_m ? ea : eb)[(size_t)info.x * 6 + rr];
-                if (have && e != kTcZeroExp) {
-                    if (e < kTcExpLo || e > kTcExpHi) atomicOr(err, kErrNonFinite);  // beyond the FP32 splitting
-                    else m = TcRow{6 * (f - bd.fo - 1) + a, eg, (int)e, fl};
+    if (warp == kTcMmaWarp) {
+        // MMA issuer: per chunk q (counted over this CTA's items) wait until
+        // buffer q & 1 holds it, before an item's first chunk until the
+        // previous item's accumulators were read, then 42 MMAs and a commit
+        if (lane == 0) {
+            int q = 0, k = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++k) {
+                const int nt = st[items[it].x].w;
+                for (int c = 0; c < nt && ok; ++c, ++q) {
+                    const int buf = q & 1;
+                    ok = mbar_wait(full0 + 8 * buf, (uint32_t)((q >> 1) & 1), 1 << 22) && !*abort_flag;
+                    if (ok && c == 0 && k > 0) ok = mbar_wait(tfree, (uint32_t)((k - 1) & 1), 1 << 22) && !*abort_flag;
+                    if (!ok) break;
+                    fence_after_sync();
+                    const uint32_t a0 = sbase + buf * kTcStage, b0 = a0 + kTcSl * kTcASlice;
+#pragma unroll
+                    for (int ks = 0; ks < kTcKc / 16; ++ks)
+#pragma unroll
+                        for (int kk = 0; kk < kTcSl; ++kk)
+#pragma unroll
+                            for (int s = 0; s <= kk; ++s) {
+                                const int t = kk - s;
+                                mma_bf16_id(tmem + kk * kTcN,
+                                            smem_desc(a0 + s * kTcASlice + ks * 256, 128, kTcSbo),
+                                            smem_desc(b0 + t * kTcBSlice + ks * 256, 128, kTcSbo), kTcIdesc,
+                                            (c > 0 || ks > 0 || s > 0) ? 1u : 0u);
+                            }
+                    mma_commit(empty0 + 8 * buf);
                 }
             }
-            meta[r] = m;
-        } else if (tid < kStTiles * kTile + kTcRows + kTcSlots * kStTiles) {
-            const int j = tid - kStTiles * kTile - kTcRows, slot = j / kStTiles, c = j % kStTiles;
-            const int fl = slot < kTcMFrames ? flm0 + slot : fln0 + slot - kTcMFrames;
-            int2 t = make_int2(0, 0);
-            if (fl < info.y && c < info.w) {
-                const int e = rows[info.x + fl].e[c];
-                if (e >= 0) {
-                    const Entry en = pb.entries[e];
-                    t = make_int2(en.pair_off * 6, (int)en.mask);
-                }
+            if (!ok) {
+                atomicOr(err, kErrTimeout);
+                *abort_flag = 1;
             }
-            tab[j] = t;
+            // every MMA issued has finished before the tensor memory is freed
+            mma_commit(fin);
+            mbar_wait(fin, 0u, 1 << 22);
         }
-        __syncthreads();
-
-        // FP32 staging of chunk c (one tile): element (row, lane) of the
-        // block's operand rows, zero where the lane does not see the frame
-        auto stage = [&](int c) {
-            float* stg = reinterpret_cast<float*>(sm + kTcOffStg + (c & 1) * kTcStg);
-            const uint32_t sdst = smem_u32(stg);
-            for (int i = tid; i < kTcRows * kTile; i += kTcThreads) {
-                const int r = i >> 5, l = i & 31;
-                const TcRow mr = meta[r];
-                const float* src = Hfd;
-                bool valid = false;
-                if (mr.g != kTcNoRow) {
-                    const int rr = r < kTcM ? item.y * kTcM + r : item.z * kTcN + (r - kTcM);
-                    const int fl = rr / 6, a = rr - 6 * fl;
-                    const int slot = r < kTcM ? fl - flm0 : kTcMFrames + fl - fln0;
-                    const int2 t = tab[slot * kStTiles + c];
-                    const unsigned mask = (unsigned)t.y;
-                    if ((mask >> l) & 1u) {
-                        src = Hfd + t.x + a * __popc(mask) + __popc(mask & ((1u << l) - 1u));
-                        valid = true;
-                    }
-                }
-                cp_async4(sdst + 4u * i, src, valid);
+        __syncwarp();
+    } else {
+        // converters: stage, form the digit slices, read the accumulators
+        int q0 = 0;                  // this item's first chunk, counted over the CTA's items
+        uint32_t consumed[2] = {0u, 0u};  // commits on empty[b] waited for
+        bool ok = true;
+        // chunk j's MMAs are done (its commit is number j >> 1 on empty[j & 1])
+        auto ensure_done = [&](int j) -> bool {
+            const int b = j & 1;
+            while ((int)consumed[b] <= (j >> 1)) {
+                const bool w = mbar_wait(empty0 + 8 * b, consumed[b] & 1u, 1 << 22) && !*abort_flag;
+                if (!w) return false;
+                ++consumed[b];
             }
-            cp_async_commit();
+            return true;
         };
-        // K chunks (the super-tile's tiles): chunk c + 1 is staged while
-        // chunk c's digits are formed into buffer c & 1; then one thread
-        // issues chunk c's MMAs
-        stage(0);
-        for (int c = 0; c < info.w; ++c) {
-            const int buf = c & 1;
-            if (c + 1 < info.w) {
-                stage(c + 1);
-                cp_async_wait_one();
-            } else {
-                cp_async_wait_all();
-            }
-            if (c >= 2) {
-                ok = __syncthreads_and(mbar_wait(mbar[buf], phase[buf]));
-                phase[buf] ^= 1u;
-                if (!ok) break;
-            } else {
-                __syncthreads();
-            }
-            const float* stg = reinterpret_cast<const float*>(sm + kTcOffStg + buf * kTcStg);
-            uint8_t* sA = sm + buf * kTcStage;
-            uint8_t* sB = sA + kTcSl * kTcASlice;
-            for (int task = tid; task < kTcRows * 4; task += kTcThreads) {
-                const int r = task >> 2, g = task & 3;  // operand row, group of 8 points
-                const bool is_a = r < kTcM;
-                const int e = meta[r].e;
-                const float4* sp = reinterpret_cast<const float4*>(stg + r * kTile + 8 * g);
-                const float4 u0 = sp[0], u1 = sp[1];
-                const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-                float d[8][kTcSl];
-                if (is_a) {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) tc_split_a(u[j], e, d[j]);
-                } else {
-                    const float4* wp = reinterpret_cast<const float4*>(wsm + c * kTile + 8 * g);
-                    const float4 w0 = wp[0], w1 = wp[1];
-                    const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) tc_split_b(u[j], w[j], e, d[j]);
+        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+            const int4 item = items[it];
+            const int4 info = st[item.x];  // first row, frames, first tile, tiles
+            const int nrows = 6 * info.y;
+            const BundleDesc bd = pb.bund[pb.frame_bundle[rows[info.x].f]];
+            const int n6 = 6 * (bd.F - 1);
+            const int flm0 = (item.y * kTcM) / 6, fln0 = (item.z * kTcN) / 6;  // first frames of the blocks
+            // weights of the points, row metadata, each frame slot's entries
+            if (tid < kStTiles * kTile) {
+                float w = 0.0f;
+                if (tid < info.w * kTile) {
+                    const float h = Hnn[(size_t)(info.z + tid / kTile) * kTile + (tid % kTile)];
+                    w = h > 0.0f ? 1.0f / (h * pb.damp1) : 0.0f;
                 }
-                const int rl = is_a ? r : r - kTcM;
-                uint8_t* dst = (is_a ? sA : sB) + (rl >> 3) * kTcSbo + g * 128 + (rl & 7) * 16;
-                const uint32_t sl = is_a ? kTcASlice : kTcBSlice;
-#pragma unroll
-                for (int s = 0; s < kTcSl; ++s)
-                    *reinterpret_cast<uint4*>(dst + s * sl) =
-                        make_uint4(pack_bf16x2(d[0][s], d[1][s]), pack_bf16x2(d[2][s], d[3][s]),
-                                   pack_bf16x2(d[4][s], d[5][s]), pack_bf16x2(d[6][s], d[7][s]));
-            }
-            fence_async_smem();
-            fence_before_sync();
-            __syncthreads();
-            fence_after_sync();
-            if (tid == 0) {
-                const uint32_t a0 = sbase + buf * kTcStage, b0 = a0 + kTcSl * kTcASlice;
-#pragma unroll
-                for (int ks = 0; ks < kTcKc / 16; ++ks)
-#pragma unroll
-                    for (int k = 0; k < kTcSl; ++k)
-#pragma unroll
-                        for (int s = 0; s <= k; ++s) {
-                            const int t = k - s;
-                            mma_bf16_id(tmem + k * kTcN, smem_desc(a0 + s * kTcASlice + ks * 256, 128, kTcSbo),
-                                        smem_desc(b0 + t * kTcBSlice + ks * 256, 128, kTcSbo), kTcIdesc,
-                                        (c > 0 || ks > 0 || s > 0) ? 1u : 0u);
-                        }
-                mma_commit(mbar[buf]);
-            }
-        }
-        if (!ok) {
-            cp_async_wait_all();
-            break;
-        }
-        // every outstanding commit (the last chunk's, and the one before it)
-        for (int c = (info.w >= 2 ? info.w - 2 : 0); c < info.w && ok; ++c) {
-            const int buf = c & 1;
-            ok = __syncthreads_and(mbar_wait(mbar[buf], phase[buf]));
-            phase[buf] ^= 1u;
-        }
-        if (!ok) break;
-        fence_after_sync();
-
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (the block's
-        // rows) and the 8-column groups w / 4, w / 4 + 4, ...
-        {
-            const int r = 32 * (warp & 3) + lane;
-            const TcRow mr = meta[r];
-            const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-#pragma unroll 1
-            for (int cg = warp >> 2; cg < kTcN / 8; cg += kTcThreads / 128) {
-                const int col0 = 8 * cg;
-                float D[kTcSl][8];
-#pragma unroll
-                for (int k = 0; k < kTcSl; ++k) tmem_ld8(trow + k * kTcN + col0, D[k]);
-                tmem_wait_ld();
-                if (mr.g == kTcNoRow) continue;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const TcRow nc = meta[kTcM + col0 + j];
-                    if (nc.g == kTcNoRow) continue;
-                    // upper block triangle; in a diagonal block a <= b
-                    if (mr.fl > nc.fl || (mr.fl == nc.fl && mr.g > nc.g)) continue;
-                    long long V = (long long)__float2int_rn(D[0][j]);
-#pragma unroll
-                    for (int k = 1; k < kTcSl; ++k) V = V * 256 + (long long)__float2int_rn(D[k][j]);
-                    if (V == 0) continue;
-                    const int dl = mr.e + nc.e - mr.eg - nc.eg + 8;  // V 2^dl in units 2^(G_i + G_j - 62)
-                    long long I;
-                    if (dl >= 0) {
-                        const long long lim = dl >= 62 ? 0 : (1ll << (62 - dl));
-                        if (!(V < lim && V > -lim)) {
-                            atomicOr(err, kErrNonFinite);  // the scale bound does not hold
-                            continue;
-                        }
-                        I = V << dl;
-                    } else {
-                        const int n = -dl;
-                        I = n >= 62 ? 0 : ((V + (1ll << (n - 1))) >> n);
+                wsm[tid] = w;
+            } else if (tid < kStTiles * kTile + kTcRows) {
+                const int r = tid - kStTiles * kTile;
+                const bool is_m = r < kTcM;
+                const int rr = is_m ? item.y * kTcM + r : item.z * kTcN + (r - kTcM);
+                TcRow m{kTcNoRow, 0, 0, 0};
+                if (rr < nrows) {
+                    const int fl = rr / 6, a = rr - 6 * fl;
+                    const int f = rows[info.x + fl].f;
+                    bool have;
+                    const int qd = a * 6 - (a * (a - 1)) / 2;  // packed H_ff diagonal (a, a)
+                    const int eg = tc_global_exp(red[(size_t)f * red_stride + qd], &have);
+                    const short e = (is_m ? ea : eb)[(size_t)info.x * 6 + rr];
+                    if (have && e != kTcZeroExp) {
+                        if (e < kTcExpLo || e > kTcExpHi) atomicOr(err, kErrNonFinite);  // beyond the FP32 splitting
+                        else m = TcRow{6 * (f - bd.fo - 1) + a, eg, (int)e, fl};
                     }
-                    if (I != 0)
-                        atomicAdd(acc + bd.so + (size_t)mr.g * n6 + nc.g, (unsigned long long)I);
+                }
+                meta[r] = m;
+            } else if (tid < kStTiles * kTile + kTcRows + kTcSlots * kStTiles) {
+                const int j = tid - kStTiles * kTile - kTcRows, slot = j / kStTiles, c = j % kStTiles;
+                const int fl = slot < kTcMFrames ? flm0 + slot : fln0 + slot - kTcMFrames;
+                int2 t = make_int2(0, 0);
+                if (fl < info.y && c < info.w) {
+                    const int e = rows[info.x + fl].e[c];
+                    if (e >= 0) {
+                        const Entry en = pb.entries[e];
+                        t = make_int2(en.pair_off * 6, (int)en.mask);
+                    }
+                }
+                tab[j] = t;
+            }
+            conv_sync();
+
+            // FP32 staging of chunk c (one tile): element (row, lane) of the
+            // block's operand rows, zero where the lane does not see the frame
+            auto stage = [&](int c) {
+                float* stg = reinterpret_cast<float*>(sm + kTcOffStg + (c & 1) * kTcStg);
+                const uint32_t sdst = smem_u32(stg);
+                for (int i = tid; i < kTcRows * kTile; i += kTcConv) {
+                    const int r = i >> 5, l = i & 31;
+                    const TcRow mr = meta[r];
+                    const float* src = Hfd;
+                    bool valid = false;
+                    if (mr.g != kTcNoRow) {
+                        const int rr = r < kTcM ? item.y * kTcM + r : item.z * kTcN + (r - kTcM);
+                        const int fl = rr / 6, a = rr - 6 * fl;
+                        const int slot = r < kTcM ? fl - flm0 : kTcMFrames + fl - fln0;
+                        const int2 t = tab[slot * kStTiles + c];
+                        const unsigned mask = (unsigned)t.y;
+                        if ((mask >> l) & 1u) {
+                            src = Hfd + t.x + a * __popc(mask) + __popc(mask & ((1u << l) - 1u));
+                            valid = true;
+                        }
+                    }
+                    cp_async4(sdst + 4u * i, src, valid);
+                }
+                cp_async_commit();
+            };
+            // chunk c + 1 is staged while chunk c's digits are formed into
+            // buffer (q0 + c) & 1, once that buffer's previous MMAs are done;
+            // one converter barrier per chunk (after it, chunk c's staging is
+            // visible and staging buffer (c + 1) & 1 is free)
+            stage(0);
+            for (int c = 0; c < info.w && ok; ++c) {
+                const int q = q0 + c, buf = q & 1;
+                cp_async_wait_all();
+                bool w = true;
+                if (q >= 2) w = ensure_done(q - 2);
+                if (!conv_sync_and(w)) {
+                    ok = false;
+                    break;
+                }
+                if (c + 1 < info.w) stage(c + 1);
+                const float* stg = reinterpret_cast<const float*>(sm + kTcOffStg + (c & 1) * kTcStg);
+                uint8_t* sA = sm + buf * kTcStage;
+                uint8_t* sB = sA + kTcSl * kTcASlice;
+                for (int task = tid; task < kTcRows * 4; task += kTcConv) {
+                    const int r = task >> 2, g = task & 3;  // operand row, group of 8 points
+                    const bool is_a = r < kTcM;
+                    const int e = meta[r].e;
+                    const float4* sp = reinterpret_cast<const float4*>(stg + r * kTile + 8 * g);
+                    const float4 u0 = sp[0], u1 = sp[1];
+                    const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+                    float d[8][kTcSl];
+                    if (is_a) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) tc_split_a(u[j], e, d[j]);
+                    } else {
+                        const float4* wp = reinterpret_cast<const float4*>(wsm + c * kTile + 8 * g);
+                        const float4 w0 = wp[0], w1 = wp[1];
+                        const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) tc_split_b(u[j], w[j], e, d[j]);
+                    }
+                    const int rl = is_a ? r : r - kTcM;
+                    uint8_t* dst = (is_a ? sA : sB) + (rl >> 3) * kTcSbo + g * 128 + (rl & 7) * 16;
+                    const uint32_t sl = is_a ? kTcASlice : kTcBSlice;
+#pragma unroll
+                    for (int s = 0; s < kTcSl; ++s)
+                        *reinterpret_cast<uint4*>(dst + s * sl) =
+                            make_uint4(pack_bf16x2(d[0][s], d[1][s]), pack_bf16x2(d[2][s], d[3][s]),
+                                       pack_bf16x2(d[4][s], d[5][s]), pack_bf16x2(d[6][s], d[7][s]));
+                }
+                // the slices are visible to the tensor cores, then the MMA
+                // warp is told (one arrival per warp)
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(full0 + 8 * buf);
+            }
+            if (ok) ok = conv_sync_and(ensure_done(q0 + info.w - 1));  // the item's MMAs are done
+            if (!ok) {
+                cp_async_wait_all();
+                break;
+            }
+            q0 += info.w;
+            fence_after_sync();
+
+            // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (the block's
+            // rows) and the 8-column groups w / 4, w / 4 + 4, ...
+            {
+                const int r = 32 * (warp & 3) + lane;
+                const TcRow mr = meta[r];
+                const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+#pragma unroll 1
+                for (int cg = warp >> 2; cg < kTcN / 8; cg += kTcConv / 128) {
+                    const int col0 = 8 * cg;
+                    float D[kTcSl][8];
+#pragma unroll
+                    for (int k = 0; k < kTcSl; ++k) tmem_ld8(trow + k * kTcN + col0, D[k]);
+                    tmem_wait_ld();
+                    if (mr.g == kTcNoRow) continue;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const TcRow nc = meta[kTcM + col0 + j];
+                        if (nc.g == kTcNoRow) continue;
+                        // upper block triangle; in a diagonal block a <= b
+                        if (mr.fl > nc.fl || (mr.fl == nc.fl && mr.g > nc.g)) continue;
+                        long long V = (long long)__float2int_rn(D[0][j]);
+#pragma unroll
+                        for (int k = 1; k < kTcSl; ++k) V = V * 256 + (long long)__float2int_rn(D[k][j]);
+                        if (V == 0) continue;
+                        const int dl = mr.e + nc.e - mr.eg - nc.eg + 8;  // V 2^dl in units 2^(G_i + G_j - 62)
+                        long long I;
+                        if (dl >= 0) {
+                            const long long lim = dl >= 62 ? 0 : (1ll << (62 - dl));
+                            if (!(V < lim && V > -lim)) {
+                                atomicOr(err, kErrNonFinite);  // the scale bound does not hold
+                                continue;
+                            }
+                            I = V << dl;
+                        } else {
+                            const int n = -dl;
+                            I = n >= 62 ? 0 : ((V + (1ll << (n - 1))) >> n);
+                        }
+                        if (I != 0)
+                            atomicAdd(acc + bd.so + (size_t)mr.g * n6 + nc.g, (unsigned long long)I);
+                    }
                 }
             }
+            // the accumulators are read: the MMA warp may start the next item
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tfree);
+            conv_sync();
         }
-        fence_before_sync();
-        __syncthreads();
-    }
-    if (!ok) {
-        // a wait gave up: report it and let the MMAs in flight finish (a
-        // second, longer bound) before the tensor memory is freed
-        if (tid == 0) atomicOr(err, kErrTimeout);
-        mbar_wait(mbar[0], phase[0], 1 << 20);
-        mbar_wait(mbar[1], phase[1], 1 << 20);
-        fence_after_sync();
+        if (!ok && tid == 0) {
+            atomicOr(err, kErrTimeout);
+            *abort_flag = 1;
+        }
     }
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kTcCols);
+    if (warp == kTcMmaWarp) tmem_dealloc(tmem, kTcCols);
     if (tid == 0) {
-        mbar_inval(mbar[0]);
-        mbar_inval(mbar[1]);
+        for (int b = 0; b < 2; ++b) {
+            mbar_inval(full0 + 8 * b);
+            mbar_inval(empty0 + 8 * b);
+        }
+        mbar_inval(tfree);
+        mbar_inval(fin);
     }
 }
+
 // S_off of every frame pair f <= g from the fixed-point sums (both
 // triangles), which are reset to zero for the next formation.
 __global__ void schur_tc_finish_kernel(const int* __restrict__ pair_fg, int n_pairs,
@@ -509,7 +579,7 @@ cudaError_t launch_schur_tc(const DevProblem& pb, const float* Hfd, const float*
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const int grid = tl.n_items < nsm ? tl.n_items : nsm;
-        schur_tc_kernel<<<grid, kTcThreads, kTcSmem, st>>>(pb, Hfd, Hnn, tl.st, tl.rows, tl.items, tl.n_items,
+        schur_tc_kernel<<<grid, kTcThreads + 32, kTcSmem, st>>>(pb, Hfd, Hnn, tl.st, tl.rows, tl.items, tl.n_items,
                                                           tl.ea, tl.eb, red, red_stride,
                                                           reinterpret_cast<unsigned long long*>(tl.acc), err);
         ++*launches;

@@ -19,7 +19,7 @@ HEADERS = [os.path.join(os.path.dirname(HERE), "include", h) for h in ("pba.h", 
 
 PBA_F32, PBA_F16, PBA_BF16 = 0, 1, 2
 PBA_MEM_DEVICE, PBA_MEM_HOST = 0, 1
-PBA_SCHUR_TENSOR, PBA_SCHUR_SIMT = 0, 1
+PBA_SCHUR_TENSOR, PBA_SCHUR_SIMT, PBA_SCHUR_AUTO = 0, 1, 2
 TIMING_SLOTS = 7
 TIMING_NAMES = ["precompute", "pass", "reduce", "schur", "solve", "eval", "point"]
 STATUS = {0: "PBA_OK", 1: "PBA_ERR_ARG", 2: "PBA_ERR_STATE", 3: "PBA_ERR_CUDA",
@@ -354,8 +354,9 @@ class Batch:
         self._check(self.lib.pba_set_tuning(self.h, int(res_warps), int(ldl_cluster)))
 
     def set_schur_path(self, path):
-        """How the Schur complement is formed: PBA_SCHUR_TENSOR (tensor cores,
-        the default) or PBA_SCHUR_SIMT (exact products on the SIMT pipes)."""
+        """How the Schur complement is formed: PBA_SCHUR_AUTO (the default: by
+        the problem's size), PBA_SCHUR_TENSOR (tensor cores) or PBA_SCHUR_SIMT
+        (exact products on the SIMT pipes)."""
         self._check(self.lib.pba_set_schur_path(self.h, int(path)))
 
     def transfer_bytes(self):

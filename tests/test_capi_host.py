@@ -74,6 +74,9 @@ def test_call_order_and_argument_checks(lib):
                                   K.ctypes.data) == 1
         assert lib.pba_set_frames(h, 0, 1, W, H, W, 0, 1, img.ctypes.data, poses.ctypes.data,
                                   K.ctypes.data) == 1
+        # a device image pointer off the element size (checked without touching it)
+        assert lib.pba_set_frames(h, 0, F, W, H, W, 0, 0, 0x10002, poses.ctypes.data, K.ctypes.data) == 1
+        assert b"misaligned" in lib.pba_last_error(h)
         assert lib.pba_set_frames(h, 0, *args) == 0
         # points: pattern footprint inside the reference, positive depths
         uv_bad = uv.copy()
