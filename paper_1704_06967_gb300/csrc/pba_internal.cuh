@@ -188,6 +188,14 @@ __device__ __forceinline__ void warp_sum(float (&v)[K])
         for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
 }
 
+// 1 / x by the hardware approximation (rcp.approx.ftz: within 1 ulp)
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ float warp_sum1(float v)
 {
 #pragma unroll

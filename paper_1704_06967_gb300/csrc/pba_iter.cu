@@ -48,6 +48,19 @@ __device__ __forceinline__ void scatter_level(float (&v)[8], int lane, int o)
     }
 }
 
+// Sums of v[0 .. 7] over the warp's lanes by reduce-scatter (nine exchanges
+// instead of forty): at strides 16, 8, 4 a lane keeps half of its values and
+// adds its partner's copy of them, then two butterfly levels; sum q ends in
+// v[0] of lanes 4q .. 4q + 3.
+__device__ __forceinline__ void lane_sums8(float (&v)[8], int lane)
+{
+    scatter_level<4>(v, lane, 16);
+    scatter_level<2>(v, lane, 8);
+    scatter_level<1>(v, lane, 4);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 // (s, c) += h (t.x + t.y): h t.x split exactly by TwoProduct (Ogita, Rump
 // and Oishi 2005), the sum carried by Knuth's two-sum; t = (hi, lo) is an
 // FP64 value as an unevaluated pair of floats.
@@ -262,7 +275,8 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
     const Entry en = pb.entries[e];
     const int P = pb.P;
     const float k = pb.huber_k;
-    float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // g_f (6), energy, r^2, count
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // g_f (6), energy, r^2
+    float cnt = 0.0f;
     float ph[5] = {0, 0, 0, 0, 0};               // brightness fit sums (w, w v, w v^2, w I_0, w I_0^2)
     float gp = 0.0f, disp = 0.0f;
     if ((en.mask >> lane) & 1u) {
@@ -286,7 +300,7 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
         for (int j = 0; j < PMAX; ++j) {
             if (j < P) {
                 const float qx = qcx + c[12 + 3 * j], qy = qcy + c[13 + 3 * j], qz = qcz + c[14 + 3 * j];
-                const float iz = 1.0f / qz;
+                const float iz = rcp_approx(qz);
                 const float u = fmaf(pb.fx * qx, iz, pb.cx), v = fmaf(pb.fy * qy, iz, pb.cy);
                 const float fu = floorf(u), fv = floorf(v);
                 // (a NaN coordinate fails the test and clamps to 1)
@@ -318,7 +332,7 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
                 const float r = I0[j] - fmaf(alpha, val[j], beta);
                 acc[6] += huber_rho(r, k);
                 acc[7] = fmaf(r, r, acc[7]);
-                acc[8] += 1.0f;
+                cnt += 1.0f;
                 wr[j] = fabsf(r) <= k ? r : copysignf(k, r);
                 if (kAccum && photo) {
                     const float w = huber_w(r, k);
@@ -370,32 +384,36 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
             const float px = fmaf(cp[0], xc.x, fmaf(cp[1], xc.y, fmaf(dp, cp[9], cp[2])));
             const float py = fmaf(cp[3], xc.x, fmaf(cp[4], xc.y, fmaf(dp, cp[10], cp[5])));
             const float pz = fmaf(cp[6], xc.x, fmaf(cp[7], xc.y, fmaf(dp, cp[11], cp[8])));
-            const float du = pb.fx * (qcx / qcz - px / pz), dv = pb.fy * (qcy / qcz - py / pz);
-            disp = sqrtf(du * du + dv * dv);
+            const float iq = rcp_approx(qcz), ip = rcp_approx(pz);
+            const float du = pb.fx * fmaf(qcx, iq, -px * ip), dv = pb.fy * fmaf(qcy, iq, -py * ip);
+            disp = fmaf(du, du, dv * dv);  // squared: the square root of the warp's maximum is taken once
         }
     }
+    disp = sqrtf(warp_max1(disp));
     if (kAccum) {
         gpart[(size_t)e * kTile + lane] = gp;
-        warp_sum<9>(acc);
+        // g_f (6), energy and r^2 by reduce-scatter (sum q on lanes 4q ..
+        // 4q + 3), the count by a butterfly
+        lane_sums8(acc, lane);
+        cnt = warp_sum1(cnt);
         if (photo) warp_sum<5>(ph);
-    } else {
-        float st[3] = {acc[6], acc[7], acc[8]};
-        warp_sum<3>(st);
-        acc[6] = st[0];
-        acc[7] = st[1];
-        acc[8] = st[2];
-    }
-    disp = warp_max1(disp);
-    if (lane == 0) {
-        if (kAccum) {
-            float* o = ent_part + (size_t)pb.entry_slot[e] * kEntryPartial;
-#pragma unroll
-            for (int a = 0; a < 6; ++a) o[a] = acc[a];
+        float* o = ent_part + (size_t)pb.entry_slot[e] * kEntryPartial;
+        float* es = reinterpret_cast<float*>(estats + e);
+        if ((lane & 3) == 0) {
+            if (lane < 24) o[lane >> 2] = acc[0];
+            else es[(lane - 24) >> 2] = acc[0];  // energy, r^2
+        }
+        if (lane == 0) {
+            es[2] = cnt;
+            es[3] = disp;
             if (photo)
 #pragma unroll
                 for (int a = 0; a < 5; ++a) o[kPhotoColIc + a] = ph[a];
         }
-        estats[e] = make_float4(acc[6], acc[7], acc[8], disp);
+    } else {
+        float st[3] = {acc[6], acc[7], cnt};
+        warp_sum<3>(st);
+        if (lane == 0) estats[e] = make_float4(st[0], st[1], st[2], disp);
     }
 }
 
