@@ -127,7 +127,8 @@ def training_pairs(scene, iters: int = 20, stream=None, damping: float = 0.01, r
     """(features at p_0, converged inverse depths, mask of usable points) of
     one generated bundle, or None when the method cannot solve it: the
     bundle is solved with IC (damped, re-anchored) from its own
-    initialisation; points that no target frame observes are not usable."""
+    initialisation; points that no target frame observes, or whose converged
+    inverse depth lies outside [0.05, 20], are not usable."""
     from .pba import Bundle
     b = Bundle.from_scene(scene, stream=stream, damping=damping, **kw)
     X = b.depth_features()
@@ -138,5 +139,8 @@ def training_pairs(scene, iters: int = 20, stream=None, damping: float = 0.01, r
         return None  # a bundle the method cannot solve gives no targets
     _, d = b.params()
     b.close()
-    usable = (scene.vis[:, 1:].sum(1) > 0) & np.isfinite(d) & (d > 0)
+    # points no target frame observes, and converged values outside the
+    # range a proposal can take (pba_propose_depths clamps to [0.05, 20]:
+    # points the solve drove away), give no targets
+    usable = (scene.vis[:, 1:].sum(1) > 0) & np.isfinite(d) & (d >= 0.05) & (d <= 20.0)
     return X, d, usable
