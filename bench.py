@@ -653,8 +653,8 @@ def run_ours(args):
             # one JSON record per line, one per launch shape
             for line in open(traffic_file):
                 tr = json.loads(line) if line.strip() else {}
-                if (tr.get("kernel_sha") == kernel_sha() and tr.get("residuals") == R
-                        and tr.get("residual_warps_per_cta") == b.tuning()[0]):
+                # (the traffic of a launch does not depend on its CTA size)
+                if tr.get("kernel_sha") == kernel_sha() and tr.get("residuals") == R:
                     roofline["traffic"] = tr["dram_bytes_per_launch"]
         except Exception:
             pass
@@ -1081,12 +1081,16 @@ def run_learned(args):
             except PbaError:
                 st = None
             _, d = b.params()
-            conv = np.flatnonzero(st[:-1, 3] < 0.01) if st is not None else np.zeros(0)
+            conv = np.flatnonzero(st[:-1, 3] < 5e-3) if st is not None else np.zeros(0)
             seen = sc.vis[:, 1:].any(1)  # the points the bundle adjustment estimates
+            ratio = d[seen] / sc.depths_gt[seen]
+            # the monocular scale is a gauge freedom: the depth error after
+            # the solve is taken with the median ratio divided out
+            scale = float(np.median(ratio)) if np.isfinite(ratio).all() else float("nan")
             out[mode] = (float(st[-1, 0]) if st is not None else float("nan"),
                          float(st[-1, 1]) if st is not None else float("nan"),
-                         int(conv[0]) + 1 if conv.size else iters,
-                         float(np.median(np.abs(d[seen] / sc.depths_gt[seen] - 1.0))),
+                         int(conv[0]) + 1 if conv.size else None,
+                         float(np.median(np.abs(ratio / scale - 1.0))),
                          float(np.median(np.abs(dinit[seen] / sc.depths_gt[seen] - 1.0))),
                          float(st[-1, 2]) if st is not None else 0.0)
             b.close()
@@ -1094,8 +1098,8 @@ def run_learned(args):
     ec = np.array([r["constant"][3] for r in rows])
     ep = np.array([r["proposal"][3] for r in rows])
     res = {"metric": "learned inverse-depth proposal vs constant-depth initialisation: median inverse-depth "
-                     f"error against the truth after {iters} IC iterations on held-out bundles "
-                     "(mean ratio constant / proposal)",
+                     f"error against the truth after {iters} IC iterations on held-out bundles, the monocular "
+                     "scale (median ratio) divided out (mean ratio constant / proposal)",
            "value": float(np.mean(ec / ep)), "unit": "error ratio", "higher_is_better": True,
            "n_gpus": 1, "dtype": "bf16 inference (FP32 accumulation), f32 training", "data": "synthetic",
            "config": {"workload": f"learned: {WORKLOAD_TEXT['learned']}; {ntr} training and {nev} held-out "
@@ -1114,9 +1118,10 @@ def run_learned(args):
                         "rms_proposal": [r["proposal"][1] for r in rows],
                         "iterations_to_convergence_constant": [r["constant"][2] for r in rows],
                         "iterations_to_convergence_proposal": [r["proposal"][2] for r in rows],
-                        "median_depth_error_constant": [r["constant"][3] for r in rows],
-                        "median_depth_error_proposal": [r["proposal"][3] for r in rows],
-                        "convergence_rule": "max pattern-centre displacement of a step < 0.01 px"},
+                        "scale_aligned_median_depth_error_constant": [r["constant"][3] for r in rows],
+                        "scale_aligned_median_depth_error_proposal": [r["proposal"][3] for r in rows],
+                        "convergence_rule": "max pattern-centre displacement of a step < 5e-3 px (Sec. 4.1); "
+                                            "null: not reached"},
            "training": {"loss_per_epoch": hist, "ms": train_ms, "samples_per_s": n_samples / (train_ms / 1e3)},
            "inference": {"points": int(Fe.shape[0]), "ms": infer_ms, "points_per_s": Fe.shape[0] / (infer_ms / 1e3),
                          "tflops": flops / (infer_ms * 1e-3) / 1e12, "kernel": "mlp_infer_tc_kernel (tcgen05)"}}

@@ -10,6 +10,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -33,6 +34,31 @@ uint32_t spread16(uint32_t x)
     x = (x | (x << 2)) & 0x33333333u;
     x = (x | (x << 1)) & 0x55555555u;
     return x;
+}
+
+// Host parallelism of the structure build: up to 16 threads (at most
+// max_parts) over [0, n) in contiguous ranges of at least `grain` items.
+int parallel_parts(int64_t n, int64_t grain, int max_parts = 16)
+{
+    const int hw = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+    return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)hw, (int64_t)max_parts,
+                                                        n / std::max<int64_t>(1, grain)}));
+}
+
+// fn(k, begin, end) for the parallel_parts(n, grain, max_parts) ranges, in
+// order of k, each on its own thread
+template <class Fn>
+void parallel_ranges(int64_t n, int64_t grain, int max_parts, Fn&& fn)
+{
+    const int k = parallel_parts(n, grain, max_parts);
+    if (k == 1) {
+        fn(0, (int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(k);
+    for (int i = 0; i < k; ++i) th.emplace_back([&fn, i, n, k]() { fn(i, n * i / k, n * (i + 1) / k); });
+    for (std::thread& t : th) t.join();
 }
 
 // Timing slots (pba_last_timing): precompute, residual pass, reduce,
@@ -66,11 +92,18 @@ struct BundleIn {
     int N = 0;
     std::vector<int32_t> uv;
     std::vector<double> d_init;
-    std::vector<uint8_t> vis;  // N*F
+    // set by pba_set_points from the caller's visibility (which is not
+    // kept): the bundle's tiles of 32 points in Morton order and its
+    // (tile, frame) entries, frames in order within a tile
+    int F_pts = 0;                    // frame count the entries were formed for
+    int T = 0;
+    std::vector<int> perm;            // slot (within the bundle's tiles) -> caller index, -1 for pads
+    std::vector<int> tile_ent;        // T + 1 offsets of each tile's local entries
+    std::vector<int> ent_f;           // local frame of each local entry
+    std::vector<unsigned> ent_mask;   // lanes (points of the tile) the entry's frame sees
     // set by build_structure
-    int fo = 0, to = 0, T = 0, e0 = 0, e1 = 0;
+    int fo = 0, to = 0, e0 = 0, e1 = 0;
     int64_t V = 0;
-    std::vector<int> perm;  // slot (within the bundle's tiles) -> caller index, -1 for pads
 };
 
 struct pba_ctx {
@@ -422,6 +455,74 @@ bool all_set(const pba_ctx* c)
 // Sorted point order, tiles, (tile, frame) entries, frame pairs and the
 // per-bundle system offsets, bundle after bundle (frames, tiles and entries
 // of bundle b follow those of bundle b - 1).
+// The bundle's tiles (32 points in Morton order of their pixels, ties in
+// caller order) and its (tile, frame) entries, frames in order within a
+// tile, from the caller's visibility (N x F bytes, null: every point in
+// every frame; frame 0 is the reference and is no entry's frame). Each
+// point's visibility row is read once.
+void form_tiles(BundleIn& b, const uint8_t* vis)
+{
+    const int N = b.N, F = b.F;
+    // a stable LSD radix sort of the 32-bit codes, eight bits per pass
+    std::vector<uint64_t> key(N), tmp(N);  // code in the high half, caller index in the low
+    for (int n = 0; n < N; ++n) {
+        const uint32_t u = (uint32_t)b.uv[2 * n], v = (uint32_t)b.uv[2 * n + 1];
+        key[n] = ((uint64_t)(spread16(u) | (spread16(v) << 1)) << 32) | (uint32_t)n;
+    }
+    for (int shift = 32; shift < 64; shift += 8) {
+        int count[257] = {0};
+        for (int i = 0; i < N; ++i) ++count[((key[i] >> shift) & 255u) + 1];
+        for (int k = 0; k < 256; ++k) count[k + 1] += count[k];
+        for (int i = 0; i < N; ++i) tmp[count[(key[i] >> shift) & 255u]++] = key[i];
+        key.swap(tmp);
+    }
+    const int T = (N + kTile - 1) / kTile;
+    b.T = T;
+    b.F_pts = F;
+    b.perm.assign((size_t)T * kTile, -1);
+    for (int i = 0; i < N; ++i) b.perm[i] = (int)(uint32_t)key[i];
+    // each tile's frame masks, then the entries (the frames with a nonzero
+    // mask) at the tile's offset
+    std::vector<unsigned> masks((size_t)T * F);
+    std::vector<int> cnt((size_t)T + 1, 0);
+    parallel_ranges(T, 64, 16, [&](int, int64_t t0, int64_t t1) {
+        for (int64_t t = t0; t < t1; ++t) {
+            unsigned* __restrict__ mk = masks.data() + (size_t)t * F;
+            std::fill(mk, mk + F, 0u);
+            for (int l = 0; l < kTile; ++l) {
+                const int n = b.perm[t * kTile + l];
+                if (n < 0) continue;
+                const unsigned bit = 1u << l;
+                if (!vis) {
+                    for (int f = 1; f < F; ++f) mk[f] |= bit;
+                    continue;
+                }
+                const uint8_t* __restrict__ vr = vis + (size_t)n * F;
+                for (int f = 1; f < F; ++f) mk[f] |= (unsigned)(vr[f] != 0) * bit;
+            }
+            int c = 0;
+            for (int f = 1; f < F; ++f) c += mk[f] != 0u;
+            cnt[t + 1] = c;
+        }
+    });
+    for (int t = 0; t < T; ++t) cnt[t + 1] += cnt[t];
+    b.ent_f.resize(cnt[T]);
+    b.ent_mask.resize(cnt[T]);
+    parallel_ranges(T, 64, 16, [&](int, int64_t t0, int64_t t1) {
+        for (int64_t t = t0; t < t1; ++t) {
+            const unsigned* mk = masks.data() + (size_t)t * F;
+            int o = cnt[t];
+            for (int f = 1; f < F; ++f)
+                if (mk[f]) {
+                    b.ent_f[o] = f;
+                    b.ent_mask[o] = mk[f];
+                    ++o;
+                }
+        }
+    });
+    b.tile_ent.swap(cnt);
+}
+
 void build_structure(pba_ctx* c)
 {
     c->F = c->N = c->T = 0;
@@ -444,83 +545,76 @@ void build_structure(pba_ctx* c)
     c->st_rows.clear();
     c->NC = (7 * (int)(c->pattern.size() / 2) + 3) / 4;
     int64_t pairs = 0;
+    {
+        size_t total = 0;
+        for (const BundleIn& b : c->bun) total += b.ent_f.size();
+        c->entries.reserve(total);
+    }
     for (int bi = 0; bi < c->B; ++bi) {
         BundleIn& b = c->bun[bi];
         const int N = b.N, F = b.F;
         b.fo = c->F;
         b.to = c->T;
         b.e0 = (int)c->entries.size();
-        // Morton order of the pixels, ties in caller order: a stable LSD
-        // radix sort of the 32-bit codes, eight bits per pass
-        std::vector<uint64_t> key(N), tmp(N);  // code in the high half, caller index in the low
-        for (int n = 0; n < N; ++n) {
-            const uint32_t u = (uint32_t)b.uv[2 * n], v = (uint32_t)b.uv[2 * n + 1];
-            key[n] = ((uint64_t)(spread16(u) | (spread16(v) << 1)) << 32) | (uint32_t)n;
-        }
-        for (int shift = 32; shift < 64; shift += 8) {
-            int count[257] = {0};
-            for (int i = 0; i < N; ++i) ++count[((key[i] >> shift) & 255u) + 1];
-            for (int k = 0; k < 256; ++k) count[k + 1] += count[k];
-            for (int i = 0; i < N; ++i) tmp[count[(key[i] >> shift) & 255u]++] = key[i];
-            key.swap(tmp);
-        }
-        b.T = (N + kTile - 1) / kTile;
-        b.perm.assign((size_t)b.T * kTile, -1);
-        for (int i = 0; i < N; ++i) b.perm[i] = (int)(uint32_t)key[i];
-        // (tile, frame) entries, frames in order within a tile: each point's
-        // visibility row is read once, in order
-        std::vector<int> tile_ent0((size_t)b.T + 1, 0);  // the tile's first entry (local)
-        std::vector<unsigned> mask(F);
+        // the bundle's entries (formed by pba_set_points) at the global
+        // frame, tile and pair offsets
+        const std::vector<int>& tile_ent0 = b.tile_ent;  // the tile's first entry (local)
         const int64_t pairs0 = pairs;
         for (int t = 0; t < b.T; ++t) {
             c->tile_entry.push_back((int)c->entries.size());
             c->tile_f0.push_back(b.fo);
-            tile_ent0[t] = (int)c->entries.size() - b.e0;
-            std::fill(mask.begin(), mask.end(), 0u);
-            unsigned* __restrict__ mk = mask.data();
-            for (int l = 0; l < kTile; ++l) {
-                const int n = b.perm[t * kTile + l];
-                if (n < 0) continue;
-                const uint8_t* __restrict__ vr = b.vis.data() + (size_t)n * F;
-                const unsigned bit = 1u << l;
-                for (int f = 1; f < F; ++f) mk[f] |= (unsigned)(vr[f] != 0) * bit;
-            }
-            for (int f = 1; f < F; ++f) {
-                if (!mask[f]) continue;
-                c->entries.push_back(Entry{b.fo + f, mask[f], (int)pairs, b.to + t});
-                pairs += __builtin_popcount(mask[f]);
+            for (int i = tile_ent0[t]; i < tile_ent0[t + 1]; ++i) {
+                c->entries.push_back(Entry{b.fo + b.ent_f[i], b.ent_mask[i], (int)pairs, b.to + t});
+                pairs += __builtin_popcount(b.ent_mask[i]);
             }
         }
-        tile_ent0[b.T] = (int)c->entries.size() - b.e0;
         b.e1 = (int)c->entries.size();
         b.V = pairs - pairs0;
         // frame pairs f <= g of the bundle with the (entry, entry) items of
         // the tiles that see both, in tile order (the sparse Schur kernel's
         // fixed summation order), cut into chunks of at most kSchurChunk
         // items. Items are counted and placed per pair from each tile's own
-        // entry pairs (a counting sort), not by scanning every tile per pair.
+        // entry pairs (a counting sort over contiguous tile ranges, one
+        // host thread each, the ranges' counts placed in range order).
         std::vector<int64_t> pbase((size_t)F + 1, 0);  // first pair index of frame f
         for (int f = 1; f < F; ++f) pbase[f + 1] = pbase[f] + (F - f);
         const int64_t npairs = pbase[F];
-        std::vector<int64_t> cnt((size_t)npairs + 1, 0);
-        auto each_item = [&](auto&& fn) {
-            for (int t = 0; t < b.T; ++t)
-                for (int i = tile_ent0[t]; i < tile_ent0[t + 1]; ++i) {
-                    const Entry& A = c->entries[b.e0 + i];
-                    const int fa = A.f - b.fo;
-                    for (int j = i; j < tile_ent0[t + 1]; ++j) {
-                        const Entry& Bj = c->entries[b.e0 + j];
-                        if (!(A.mask & Bj.mask)) continue;
-                        fn(pbase[fa] + (Bj.f - b.fo - fa), b.e0 + i, b.e0 + j);
-                    }
+        auto tile_items = [&](int64_t t, auto&& fn) {
+            for (int i = tile_ent0[t]; i < tile_ent0[t + 1]; ++i) {
+                const Entry& A = c->entries[b.e0 + i];
+                const int fa = A.f - b.fo;
+                for (int j = i; j < tile_ent0[t + 1]; ++j) {
+                    const Entry& Bj = c->entries[b.e0 + j];
+                    if (!(A.mask & Bj.mask)) continue;
+                    fn(pbase[fa] + (Bj.f - b.fo - fa), b.e0 + i, b.e0 + j);
                 }
+            }
         };
-        each_item([&](int64_t pid, int, int) { ++cnt[pid + 1]; });
-        for (int64_t q = 0; q < npairs; ++q) cnt[q + 1] += cnt[q];
+        const int max_parts = (int)std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)(1 << 22) / std::max<int64_t>(1, npairs)));
+        const int parts = parallel_parts(b.T, 64, max_parts);
+        std::vector<int64_t> pc((size_t)parts * npairs, 0);  // per range: items per pair
+        parallel_ranges(b.T, 64, max_parts, [&](int k, int64_t t0, int64_t t1) {
+            int64_t* ck = pc.data() + (size_t)k * npairs;
+            for (int64_t t = t0; t < t1; ++t) tile_items(t, [&](int64_t pid, int, int) { ++ck[pid]; });
+        });
+        std::vector<int64_t> cnt((size_t)npairs + 1, 0);
+        for (int64_t q = 0; q < npairs; ++q) {
+            int64_t o = cnt[q];
+            for (int k = 0; k < parts; ++k) {
+                const int64_t n_k = pc[(size_t)k * npairs + q];
+                pc[(size_t)k * npairs + q] = o;  // the range's first slot of the pair
+                o += n_k;
+            }
+            cnt[q + 1] = o;
+        }
         const size_t item0 = c->pair_items.size();
         c->pair_items.resize(item0 + (size_t)cnt[npairs]);
-        std::vector<int64_t> put(cnt.begin(), cnt.end() - 1);
-        each_item([&](int64_t pid, int ea, int eb) { c->pair_items[item0 + put[pid]++] = make_int2(ea, eb); });
+        int2* items = c->pair_items.data() + item0;
+        parallel_ranges(b.T, 64, max_parts, [&](int k, int64_t t0, int64_t t1) {
+            int64_t* put = pc.data() + (size_t)k * npairs;
+            for (int64_t t = t0; t < t1; ++t)
+                tile_items(t, [&](int64_t pid, int ea, int eb) { items[put[pid]++] = make_int2(ea, eb); });
+        });
         for (int f = 1; f < F; ++f)
             for (int g = f; g < F; ++g) {
                 const int p = (int)c->pair_fg.size() / 2;
@@ -994,7 +1088,7 @@ pba_status pba_set_frames(pba_ctx* ctx, int bundle, int n_frames, int w, int h, 
     b.images = images;
     b.poses_init.assign(poses, poses + 12 * n_frames);
     b.have_frames = true;
-    if (b.have_points && b.vis.size() != (size_t)b.N * n_frames) b.have_points = false;
+    if (b.have_points && b.F_pts != n_frames) b.have_points = false;  // entries formed for another F
     ctx->W = w;
     ctx->H = h;
     ctx->pitch = pitch_elems;
@@ -1028,11 +1122,7 @@ pba_status pba_set_points(pba_ctx* ctx, int bundle, int n_points, const int32_t*
     b.N = n_points;
     b.uv.assign(uv, uv + 2 * n_points);
     b.d_init.assign(inv_depth, inv_depth + n_points);
-    if (vis)
-        b.vis.assign(vis, vis + (size_t)n_points * b.F);
-    else
-        b.vis.assign((size_t)n_points * b.F, 1);
-    for (int n = 0; n < n_points; ++n) b.vis[(size_t)n * b.F] = 0;
+    form_tiles(b, vis);
     b.have_points = true;
     ctx->built = false;
     ctx->ws_ready = ctx->ic_ready = false;
