@@ -11,6 +11,10 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <atomic>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <tuple>
 #include <vector>
 
@@ -36,17 +40,116 @@ uint32_t spread16(uint32_t x)
     return x;
 }
 
-// Host parallelism of the structure build: up to 16 threads (at most
-// max_parts) over [0, n) in contiguous ranges of at least `grain` items.
+// Host parallelism of the structure build: a fixed set of worker threads
+// (up to 15 beside the caller, created on first use and kept for the
+// process), so that a build over many small bundles does not pay a thread
+// start per range. run(k, fn) calls fn(i) for every i < k, the caller
+// taking part, and returns when all have returned; one run at a time.
+class HostPool {
+  public:
+    static HostPool& get()
+    {
+        static HostPool pool;
+        return pool;
+    }
+    int threads() const { return (int)workers_.size() + 1; }
+
+    void run(int k, const std::function<void(int)>& fn)
+    {
+        if (k <= 1 || workers_.empty()) {
+            for (int i = 0; i < k; ++i) fn(i);
+            return;
+        }
+        std::lock_guard<std::mutex> one(run_m_);
+        uint64_t g;
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            g = ++gen_;
+            job_ = &fn;
+            k_ = k;
+            left_ = k;
+            next_.store((g & 0xffffffffu) << 32);  // this run's generation, index 0
+        }
+        cv_.notify_all();
+        work(g, &fn, k);
+        std::unique_lock<std::mutex> lk(m_);
+        done_cv_.wait(lk, [this]() { return left_ == 0; });
+        job_ = nullptr;
+    }
+
+    ~HostPool()
+    {
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            stop_ = true;
+            ++gen_;
+        }
+        cv_.notify_all();
+        for (std::thread& t : workers_) t.join();
+    }
+
+  private:
+    HostPool()
+    {
+        const int hw = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+        for (int i = 1; i < hw; ++i) workers_.emplace_back([this]() { loop(); });
+    }
+    // Takes indices of run g until none is left. An index is taken by
+    // advancing the counter only while it still holds run g's generation,
+    // so a thread that arrives late never takes a later run's index.
+    void work(uint64_t g, const std::function<void(int)>* job, int k)
+    {
+        const uint64_t tag = (g & 0xffffffffu) << 32;
+        for (;;) {
+            uint64_t v = next_.load();
+            for (;;) {
+                if ((v & ~0xffffffffull) != tag || (int)(v & 0xffffffffu) >= k) return;
+                if (next_.compare_exchange_weak(v, v + 1)) break;
+            }
+            (*job)((int)(v & 0xffffffffu));
+            std::lock_guard<std::mutex> lk(m_);
+            if (--left_ == 0) done_cv_.notify_one();
+        }
+    }
+    void loop()
+    {
+        uint64_t seen = 0;
+        for (;;) {
+            uint64_t g;
+            const std::function<void(int)>* job;
+            int k;
+            {
+                std::unique_lock<std::mutex> lk(m_);
+                cv_.wait(lk, [&]() { return gen_ != seen; });
+                seen = g = gen_;
+                if (stop_) return;
+                job = job_;
+                k = k_;
+            }
+            if (job) work(g, job, k);
+        }
+    }
+    std::vector<std::thread> workers_;
+    std::mutex m_, run_m_;
+    std::condition_variable cv_, done_cv_;
+    const std::function<void(int)>* job_ = nullptr;
+    int k_ = 0, left_ = 0;
+    std::atomic<uint64_t> next_{0};
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+};
+
+// The number of contiguous ranges of at least `grain` of n items the
+// structure build splits a loop into (at most max_parts and the pool's
+// threads).
 int parallel_parts(int64_t n, int64_t grain, int max_parts = 16)
 {
-    const int hw = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
-    return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)hw, (int64_t)max_parts,
+    return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)HostPool::get().threads(), (int64_t)max_parts,
                                                         n / std::max<int64_t>(1, grain)}));
 }
 
-// fn(k, begin, end) for the parallel_parts(n, grain, max_parts) ranges, in
-// order of k, each on its own thread
+// fn(k, begin, end) for the parallel_parts(n, grain, max_parts) ranges
+// (range k = [n k / parts, n (k + 1) / parts)), on the pool's threads
 template <class Fn>
 void parallel_ranges(int64_t n, int64_t grain, int max_parts, Fn&& fn)
 {
@@ -55,10 +158,7 @@ void parallel_ranges(int64_t n, int64_t grain, int max_parts, Fn&& fn)
         fn(0, (int64_t)0, n);
         return;
     }
-    std::vector<std::thread> th;
-    th.reserve(k);
-    for (int i = 0; i < k; ++i) th.emplace_back([&fn, i, n, k]() { fn(i, n * i / k, n * (i + 1) / k); });
-    for (std::thread& t : th) t.join();
+    HostPool::get().run(k, [&](int i) { fn(i, n * i / k, n * (i + 1) / k); });
 }
 
 // Timing slots (pba_last_timing): precompute, residual pass, reduce,
@@ -463,17 +563,36 @@ bool all_set(const pba_ctx* c)
 void form_tiles(BundleIn& b, const uint8_t* vis)
 {
     const int N = b.N, F = b.F;
-    // a stable LSD radix sort of the 32-bit codes, eight bits per pass
+    // a stable LSD radix sort of the 32-bit codes, eight bits per pass;
+    // each pass counts the digits of contiguous ranges of keys in parallel
+    // and places each range's keys at its offsets (digit-major, then range
+    // order: stable)
     std::vector<uint64_t> key(N), tmp(N);  // code in the high half, caller index in the low
-    for (int n = 0; n < N; ++n) {
-        const uint32_t u = (uint32_t)b.uv[2 * n], v = (uint32_t)b.uv[2 * n + 1];
-        key[n] = ((uint64_t)(spread16(u) | (spread16(v) << 1)) << 32) | (uint32_t)n;
-    }
+    parallel_ranges(N, 4096, 16, [&](int, int64_t i0, int64_t i1) {
+        for (int64_t n = i0; n < i1; ++n) {
+            const uint32_t u = (uint32_t)b.uv[2 * n], v = (uint32_t)b.uv[2 * n + 1];
+            key[n] = ((uint64_t)(spread16(u) | (spread16(v) << 1)) << 32) | (uint32_t)n;
+        }
+    });
+    const int parts = parallel_parts(N, 4096);
+    std::vector<int64_t> hist((size_t)parts * 256);
     for (int shift = 32; shift < 64; shift += 8) {
-        int count[257] = {0};
-        for (int i = 0; i < N; ++i) ++count[((key[i] >> shift) & 255u) + 1];
-        for (int k = 0; k < 256; ++k) count[k + 1] += count[k];
-        for (int i = 0; i < N; ++i) tmp[count[(key[i] >> shift) & 255u]++] = key[i];
+        std::fill(hist.begin(), hist.end(), 0);
+        parallel_ranges(N, 4096, 16, [&](int k, int64_t i0, int64_t i1) {
+            int64_t* h = hist.data() + (size_t)k * 256;
+            for (int64_t i = i0; i < i1; ++i) ++h[(key[i] >> shift) & 255u];
+        });
+        int64_t o = 0;
+        for (int d = 0; d < 256; ++d)
+            for (int k = 0; k < parts; ++k) {
+                const int64_t c = hist[(size_t)k * 256 + d];
+                hist[(size_t)k * 256 + d] = o;
+                o += c;
+            }
+        parallel_ranges(N, 4096, 16, [&](int k, int64_t i0, int64_t i1) {
+            int64_t* h = hist.data() + (size_t)k * 256;
+            for (int64_t i = i0; i < i1; ++i) tmp[h[(key[i] >> shift) & 255u]++] = key[i];
+        });
         key.swap(tmp);
     }
     const int T = (N + kTile - 1) / kTile;
