@@ -76,7 +76,7 @@ def aggregate_rate(units_per_rank, world, total_ms):
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--iters", type=int, default=20, help="IC / FC iterations per solve")
@@ -272,6 +272,57 @@ def precision_sample(sc, iters, stride, stream, tuning):
                      f"every {stride}th point of the {SCENE} bundle ({sub.N} points, all frames), scaled by "
                      f"{stride} to the whole bundle and to a {iters}-iteration solve; single thread"}
     return errors, cpu
+
+
+# The all-core leg of the CPU baseline: worker processes forked before the
+# first CUDA call, each running the oracle as it stands on its own share of
+# the point sample (the scene is shared with the parent copy-on-write).
+_FORK_SCENE = None
+
+
+def _oracle_share(args):
+    """(precompute s, one IC iteration s, points) of the oracle on every
+    `step`-th point from `offset` of the forked scene."""
+    import oracle
+    import synth
+    step, offset = args
+    sub = synth.point_subset(_FORK_SCENE, step, offset=offset)
+    pb = oracle.Problem.from_scene(sub)
+    t0 = time.perf_counter()
+    pre = oracle.ic_precompute(pb, sub.poses0, sub.depths0)
+    t1 = time.perf_counter()
+    oracle.ic_step(pb, pre, sub.poses0, sub.depths0, sub.poses0, sub.depths0)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1, sub.N
+
+
+def fork_oracle_pool(sc):
+    """A pool of min(16, host cores) oracle workers forked now, before any
+    CUDA call (a process forked after CUDA is initialised can hang)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    global _FORK_SCENE
+    _FORK_SCENE = sc
+    parts = max(1, min(16, os.cpu_count() or 1))
+    pool = cf.ProcessPoolExecutor(max_workers=parts, mp_context=mp.get_context("fork"))
+    list(pool.map(time.sleep, [0.05] * parts))  # start every worker now
+    return pool, parts
+
+
+def oracle_all_cores(pool, parts, stride, iters):
+    """The oracle on every `stride`-th point split over `parts` processes at
+    once; the slowest share's times, scaled by `stride`, estimate a solve of
+    the whole bundle on all of them."""
+    shares = list(pool.map(_oracle_share, [(stride * parts, stride * k) for k in range(parts)]))
+    t_pre = max(x[0] for x in shares) * stride
+    t_it = max(x[1] for x in shares) * stride
+    value = iters / (t_pre + iters * t_it)
+    return {"value": value, "unit": UNIT, "cores": parts, "kind": "oracle",
+            "sample": f"FP64 oracle IC precompute + one IC iteration on every {stride}th point of the {SCENE} "
+                      f"bundle ({sum(x[2] for x in shares)} points, all frames) split over {parts} processes "
+                      f"running at once (every {stride * parts}th point each); the slowest process's times, "
+                      f"scaled by {stride} to the whole bundle and to a {iters}-iteration solve (each process "
+                      f"also solves the whole reduced system)"}
 
 
 # ----------------------------------------------------------------------------
@@ -493,6 +544,13 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world != args.gpus:
         log(f"warning: --gpus {args.gpus} but WORLD_SIZE {world}")
+    iters = args.iters
+    sc = synth.make_scene(SCENE, seed_offset=rank)
+    if args.point_stride > 1:
+        sc = synth.point_subset(sc, args.point_stride)
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool, parts = fork_oracle_pool(sc)  # before the first CUDA call
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -503,10 +561,6 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
 
-    iters = args.iters
-    sc = synth.make_scene(SCENE, seed_offset=rank)
-    if args.point_stride > 1:
-        sc = synth.point_subset(sc, args.point_stride)
     # a stream of our own (the legacy stream cannot be captured): every
     # library call, L2 flush and timing event below is ordered on it
     stream = torch.cuda.Stream()
@@ -692,9 +746,14 @@ def run_ours(args):
         except Exception as ex:  # a diagnostic, as above
             small = {"error": f"{type(ex).__name__}: {ex}"}
 
-    cpu, precision = None, None
+    cpu, precision, cpu_all = None, None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         precision, cpu = precision_sample(sc, iters, SAMPLE_STRIDE.get(SCENE, 1), stream, b.tuning())
+        try:
+            cpu_all = oracle_all_cores(pool, parts, SAMPLE_STRIDE.get(SCENE, 1), iters)
+        except Exception as ex:  # a reported baseline, not the measurement
+            cpu_all = {"error": f"{type(ex).__name__}: {ex}"}
+        pool.shutdown()
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -711,7 +770,7 @@ def run_ours(args):
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_b,
                        "d2h_bytes_per_step": d2h_b},
                "gpu_launches": int(ic_launches), "roofline": roofline,
-               "cpu_baseline": cpu, "clocks": clk,
+               "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "clocks": clk,
                "residuals_per_s": value * R,
                "ic": {"precompute_ms": pre_avg, "iteration_ms": it_ic,
                       "final_rms": float(st_ic[-1, 1])},
@@ -883,7 +942,13 @@ def run_batch(args):
     loop_value = aggregate_rate(B * iters * args.steps, world, total_loop)
     fc_value = aggregate_rate(B * iters * args.steps, world, total_fc)
 
-    # the batch and the loop must agree exactly (each bundle's sums keep their order)
+    # the batch and the loop must agree exactly (each bundle's sums keep their
+    # order) on the same Schur path: the automatic choice goes by the size of
+    # the whole context, so it is fixed to the exact-product SIMT path here
+    from paper_1704_06967_gb300.pba import PBA_SCHUR_AUTO, PBA_SCHUR_SIMT
+    batch.set_schur_path(PBA_SCHUR_SIMT)
+    for sb in singles:
+        sb.set_schur_path(PBA_SCHUR_SIMT)
     reset()
     batch_ic()
     loop_ic()
@@ -895,6 +960,7 @@ def run_batch(args):
         P1, D1 = batch.params(i)
         P2, D2 = singles[i].params()
         mismatch += int(not (np.array_equal(P1, P2) and np.array_equal(D1, D2)))
+    batch.set_schur_path(PBA_SCHUR_AUTO)
     # final RMS of the batch's IC and FC solves (sums over the bundles)
     reset()
     flagged(batch.precompute_ic, batch, ic_failed)
@@ -972,7 +1038,8 @@ def run_batch(args):
                "ic_final_rms": float(st_ic[-1, 1]) if st_ic is not None else None,
                "ic_bundles_not_positive_definite": sorted(ic_failed),
                "ic_over_fc_iterations_per_s": value / fc_value,
-               "batch_equals_loop": {"bundles_checked": len(range(0, B, max(1, B // 16))),
+               "batch_equals_loop": {"schur_path": "SIMT (exact products) on both",
+                                     "bundles_checked": len(range(0, B, max(1, B // 16))),
                                      "mismatches": mismatch}}
         print(json.dumps(out), flush=True)
     for b in singles:
