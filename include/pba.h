@@ -386,6 +386,49 @@ pba_status pba_transfer_bytes(pba_ctx* ctx, int64_t* h2d, int64_t* d2h);
 pba_status pba_downsample(const void* src, pba_dtype dtype, int n_frames, int w, int h, int pitch_elems,
                           float* dst, void* cuda_stream);
 
+/* Coarse-to-fine solve of one bundle over an image pyramid (an addition
+ * beyond the paper: a direct method's basin widens at coarse levels). Level
+ * l (0 = full resolution) halves the images l times (pba_downsample, FP32)
+ * with intrinsics f / 2^l and (c + 0.5) / 2^l - 0.5. A point keeps its
+ * inverse depth at every level and takes the nearest level pixel, (u + 0.5)
+ * / 2^l - 0.5 rounded to nearest (ties to even); a point whose pattern (and
+ * the pattern's central-difference neighbours) would leave a level's
+ * reference image sits that level out. From the coarsest level to level 0,
+ * a context of the level (cfg with one bundle) solves iters[i] iterations
+ * (i = 0 for the coarsest), method 0 = IC (pba_solve_ic with
+ * reanchor_every) or 1 = FC (pba_solve_fc); the poses and inverse depths it
+ * reaches start the next level (a point driven to a non-positive or
+ * non-finite inverse depth keeps the one it entered the level with).
+ *
+ * levels: 1..8, every level at least 4 x 4 pixels and with at least one
+ * point. images: device, n_frames x h rows of pitch_elems elements of dtype.
+ * poses (n_frames x 12, R row-major then t) and inv_depth (n_points): host,
+ * in: the initial values, out: the result. intrinsics, uv (n_points x 2),
+ * vis (n_points x n_frames, nullable = all visible): host, as for
+ * pba_set_frames / pba_set_points. workspace: device, 256-byte aligned, at
+ * least the size pba_pyramid_workspace_size gives for the same problem (the
+ * coarser levels' images, then the region each level's context uses in
+ * turn); its contents are scratch. stats: host, nullable, sum(iters[i] + 1)
+ * entries, each level's pba_solve_ic / pba_solve_fc statistics in turn.
+ * level_ms: host, nullable, `levels` entries (coarsest first): the device
+ * time of each level's solve call (CUDA events on the stream around it; the
+ * level's image reduction and context set-up excluded). Runs on
+ * cfg->cuda_stream and returns when the result is on the host.
+ * Errors: PBA_ERR_ARG (invalid arguments, cfg with several bundles, a level
+ * too small or without points) and PBA_ERR_NOMEM (workspace smaller than
+ * the size query's), both before anything is solved, and any status of a
+ * level's calls (the solve stops at that level; poses and inv_depth then
+ * hold the last completed level's result). */
+pba_status pba_pyramid_workspace_size(const pba_config* cfg, int levels, int n_frames, int w, int h,
+                                      const double* poses, const double* intrinsics, int n_points,
+                                      const int32_t* uv, const double* inv_depth, const uint8_t* vis,
+                                      size_t* bytes);
+pba_status pba_solve_pyramid(const pba_config* cfg, int levels, const int* iters, int method, int reanchor_every,
+                             const void* images, pba_dtype dtype, int n_frames, int w, int h, int pitch_elems,
+                             double* poses, const double* intrinsics, int n_points, const int32_t* uv,
+                             double* inv_depth, const uint8_t* vis, void* workspace, size_t ws_bytes,
+                             pba_iter_stats* stats, double* level_ms);
+
 /* Reduced camera system without any allocation, for callers that cannot
  * allocate device memory (code running inside a fixed pre-reserved memory
  * arena, runtimes that forbid cudaMalloc after start-up, frameworks that

@@ -78,6 +78,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pba_solve_ic": ([vp, i, i, vp], i),
         "pba_set_window": ([vp, i, vp], i),
         "pba_downsample": ([vp, i, i, i, i, i, vp, vp], i),
+        "pba_pyramid_workspace_size": ([ctypes.POINTER(Config), i, i, i, i, vp, vp, i, vp, vp, vp,
+                                        ctypes.POINTER(ctypes.c_size_t)], i),
+        "pba_solve_pyramid": ([ctypes.POINTER(Config), i, vp, i, i, vp, i, i, i, i, i, vp, vp, i, vp, vp, vp, vp,
+                               ctypes.c_size_t, vp, vp], i),
         "pba_get_brightness": ([vp, i, vp], i),
         "pba_set_brightness": ([vp, i, vp], i),
         "pba_update_ic": ([vp], i),
