@@ -1072,21 +1072,23 @@ namespace pba {
 
 // Setup: central-difference gradient images (FC) and the template
 // intensities of every (point, pattern pixel).
+template <int DT>
 __global__ void gradient_images_kernel(DevProblem pb, float* gx, float* gy)
 {
-    const size_t total = (size_t)pb.F * pb.H * pb.W;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % pb.W);
-        const size_t fy = i / pb.W;
-        const int y = (int)(fy % pb.H);
-        const size_t row = fy * pb.pitch;
+    // blockIdx.z = frame (strided over gridDim.z), blockIdx.y = row, threads
+    // along the row: no index divisions, coalesced rows
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= pb.W) return;
+    for (int f = blockIdx.z; f < pb.F; f += gridDim.z) {
+        const size_t row = ((size_t)f * pb.H + y) * pb.pitch;
         float a = 0.0f, b = 0.0f;
         if (x >= 1 && x <= pb.W - 2)
-            a = 0.5f * (load_px(pb.img, pb.dtype, row + x + 1) - load_px(pb.img, pb.dtype, row + x - 1));
+            a = 0.5f * (load_px_t<DT>(pb.img, (unsigned)(row + x + 1)) -
+                        load_px_t<DT>(pb.img, (unsigned)(row + x - 1)));
         if (y >= 1 && y <= pb.H - 2)
-            b = 0.5f * (load_px(pb.img, pb.dtype, row + pb.pitch + x) -
-                        load_px(pb.img, pb.dtype, row - pb.pitch + x));
+            b = 0.5f * (load_px_t<DT>(pb.img, (unsigned)(row + pb.pitch + x)) -
+                        load_px_t<DT>(pb.img, (unsigned)(row - pb.pitch + x)));
+        const size_t i = ((size_t)f * pb.H + y) * pb.W + x;
         gx[i] = a;
         gy[i] = b;
     }
@@ -1112,7 +1114,10 @@ __global__ void template_gather_kernel(DevProblem pb, const int* tile_f0, float*
 cudaError_t launch_setup(const DevProblem& pb, const int* tile_f0, float* gx, float* gy, float* I0p,
                          float2* G0p, cudaStream_t st)
 {
-    gradient_images_kernel<<<1024, 256, 0, st>>>(pb, gx, gy);
+    const dim3 grid((pb.W + 255) / 256, pb.H, std::min(pb.F, 65535));
+    if (pb.dtype == PBA_F32) gradient_images_kernel<PBA_F32><<<grid, 256, 0, st>>>(pb, gx, gy);
+    else if (pb.dtype == PBA_F16) gradient_images_kernel<PBA_F16><<<grid, 256, 0, st>>>(pb, gx, gy);
+    else gradient_images_kernel<PBA_BF16><<<grid, 256, 0, st>>>(pb, gx, gy);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     template_gather_kernel<<<256, 256, 0, st>>>(pb, tile_f0, I0p, G0p);
