@@ -204,6 +204,7 @@ struct BundleIn {
     // set by build_structure
     int fo = 0, to = 0, e0 = 0, e1 = 0;
     int64_t V = 0;
+    int64_t item0 = 0;  // the bundle's first Schur pair item
 };
 
 struct pba_ctx {
@@ -233,7 +234,9 @@ struct pba_ctx {
     int64_t n_so = 0, n_ao = 0, n_lo = 0;  // sizes of the per-bundle system arrays
     int n_po = 0, n_cmap = 0;
     std::vector<int> pair_fg, pair_chunk, chunk_pair, chunk_start;  // sparse Schur lists
-    std::vector<int2> pair_items;
+    std::vector<int2> pair_items;  // placed only for the SIMT path (fill_pair_items)
+    int64_t n_pair_items = 0;
+    bool items_ready = false;
     // tensor-core Schur complement: super-tiles (first row, frames, first
     // tile, tiles), their frame rows and the output blocks
     std::vector<int4> st_info, st_items;
@@ -527,7 +530,7 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.pair_chunk, c->pair_chunk.size() * sizeof(int));
     take(c->d.chunk_pair, c->chunk_pair.size() * sizeof(int));
     take(c->d.chunk_start, c->chunk_start.size() * sizeof(int));
-    take(c->d.pair_items, c->pair_items.size() * sizeof(int2));
+    take(c->d.pair_items, (size_t)c->n_pair_items * sizeof(int2));
     take(c->d.schur_part, c->chunk_pair.size() * 36 * sizeof(float2));
     take(c->d.ic_schur_part, c->chunk_pair.size() * 36 * sizeof(float2));
     take(c->d.st_info, c->st_info.size() * sizeof(int4));
@@ -642,6 +645,57 @@ void form_tiles(BundleIn& b, const uint8_t* vis)
     b.tile_ent.swap(cnt);
 }
 
+// The (entry, entry) items of bundle b's tiles per frame pair f <= g: cnt
+// (resized to npairs + 1) receives the prefix sums of the counts per pair
+// (pair index of (f, g) = first pair of f + g - f), and with items non-null
+// every item is placed at items[cnt[pair] + its rank in tile order] as
+// (global entry of f, global entry of g). A counting sort over contiguous
+// tile ranges, one host thread each, the ranges' counts placed in range
+// order, so the order is the serial one.
+void bundle_pair_items(const pba_ctx* c, const BundleIn& b, std::vector<int64_t>& cnt, int2* items)
+{
+    const int F = b.F;
+    const std::vector<int>& tile_ent0 = b.tile_ent;
+    std::vector<int64_t> pbase((size_t)F + 1, 0);
+    for (int f = 1; f < F; ++f) pbase[f + 1] = pbase[f] + (F - f);
+    const int64_t npairs = pbase[F];
+    auto tile_items = [&](int64_t t, auto&& fn) {
+        for (int i = tile_ent0[t]; i < tile_ent0[t + 1]; ++i) {
+            const Entry& A = c->entries[b.e0 + i];
+            const int fa = A.f - b.fo;
+            for (int j = i; j < tile_ent0[t + 1]; ++j) {
+                const Entry& Bj = c->entries[b.e0 + j];
+                if (!(A.mask & Bj.mask)) continue;
+                fn(pbase[fa] + (Bj.f - b.fo - fa), b.e0 + i, b.e0 + j);
+            }
+        }
+    };
+    const int max_parts =
+        (int)std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)(1 << 22) / std::max<int64_t>(1, npairs)));
+    const int parts = parallel_parts(b.T, 64, max_parts);
+    std::vector<int64_t> pc((size_t)parts * npairs, 0);  // per range: items per pair
+    parallel_ranges(b.T, 64, max_parts, [&](int k, int64_t t0, int64_t t1) {
+        int64_t* ck = pc.data() + (size_t)k * npairs;
+        for (int64_t t = t0; t < t1; ++t) tile_items(t, [&](int64_t pid, int, int) { ++ck[pid]; });
+    });
+    cnt.assign((size_t)npairs + 1, 0);
+    for (int64_t q = 0; q < npairs; ++q) {
+        int64_t o = cnt[q];
+        for (int k = 0; k < parts; ++k) {
+            const int64_t n_k = pc[(size_t)k * npairs + q];
+            pc[(size_t)k * npairs + q] = o;  // the range's first slot of the pair
+            o += n_k;
+        }
+        cnt[q + 1] = o;
+    }
+    if (!items) return;
+    parallel_ranges(b.T, 64, max_parts, [&](int k, int64_t t0, int64_t t1) {
+        int64_t* put = pc.data() + (size_t)k * npairs;
+        for (int64_t t = t0; t < t1; ++t)
+            tile_items(t, [&](int64_t pid, int ea, int eb) { items[put[pid]++] = make_int2(ea, eb); });
+    });
+}
+
 void build_structure(pba_ctx* c)
 {
     c->F = c->N = c->T = 0;
@@ -659,6 +713,8 @@ void build_structure(pba_ctx* c)
     c->chunk_pair.clear();
     c->chunk_start.assign(1, 0);
     c->pair_items.clear();
+    c->n_pair_items = 0;
+    c->items_ready = false;
     c->st_info.clear();
     c->st_items.clear();
     c->st_rows.clear();
@@ -692,48 +748,15 @@ void build_structure(pba_ctx* c)
         // frame pairs f <= g of the bundle with the (entry, entry) items of
         // the tiles that see both, in tile order (the sparse Schur kernel's
         // fixed summation order), cut into chunks of at most kSchurChunk
-        // items. Items are counted and placed per pair from each tile's own
-        // entry pairs (a counting sort over contiguous tile ranges, one
-        // host thread each, the ranges' counts placed in range order).
+        // items: counted here, placed by fill_pair_items when the SIMT path
+        // is in use (the tensor-core path does not read them)
         std::vector<int64_t> pbase((size_t)F + 1, 0);  // first pair index of frame f
         for (int f = 1; f < F; ++f) pbase[f + 1] = pbase[f] + (F - f);
-        const int64_t npairs = pbase[F];
-        auto tile_items = [&](int64_t t, auto&& fn) {
-            for (int i = tile_ent0[t]; i < tile_ent0[t + 1]; ++i) {
-                const Entry& A = c->entries[b.e0 + i];
-                const int fa = A.f - b.fo;
-                for (int j = i; j < tile_ent0[t + 1]; ++j) {
-                    const Entry& Bj = c->entries[b.e0 + j];
-                    if (!(A.mask & Bj.mask)) continue;
-                    fn(pbase[fa] + (Bj.f - b.fo - fa), b.e0 + i, b.e0 + j);
-                }
-            }
-        };
-        const int max_parts = (int)std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)(1 << 22) / std::max<int64_t>(1, npairs)));
-        const int parts = parallel_parts(b.T, 64, max_parts);
-        std::vector<int64_t> pc((size_t)parts * npairs, 0);  // per range: items per pair
-        parallel_ranges(b.T, 64, max_parts, [&](int k, int64_t t0, int64_t t1) {
-            int64_t* ck = pc.data() + (size_t)k * npairs;
-            for (int64_t t = t0; t < t1; ++t) tile_items(t, [&](int64_t pid, int, int) { ++ck[pid]; });
-        });
-        std::vector<int64_t> cnt((size_t)npairs + 1, 0);
-        for (int64_t q = 0; q < npairs; ++q) {
-            int64_t o = cnt[q];
-            for (int k = 0; k < parts; ++k) {
-                const int64_t n_k = pc[(size_t)k * npairs + q];
-                pc[(size_t)k * npairs + q] = o;  // the range's first slot of the pair
-                o += n_k;
-            }
-            cnt[q + 1] = o;
-        }
-        const size_t item0 = c->pair_items.size();
-        c->pair_items.resize(item0 + (size_t)cnt[npairs]);
-        int2* items = c->pair_items.data() + item0;
-        parallel_ranges(b.T, 64, max_parts, [&](int k, int64_t t0, int64_t t1) {
-            int64_t* put = pc.data() + (size_t)k * npairs;
-            for (int64_t t = t0; t < t1; ++t)
-                tile_items(t, [&](int64_t pid, int ea, int eb) { items[put[pid]++] = make_int2(ea, eb); });
-        });
+        std::vector<int64_t> cnt;
+        bundle_pair_items(c, b, cnt, nullptr);
+        const size_t item0 = (size_t)c->n_pair_items;
+        b.item0 = c->n_pair_items;
+        c->n_pair_items += cnt.back();
         for (int f = 1; f < F; ++f)
             for (int g = f; g < F; ++g) {
                 const int p = (int)c->pair_fg.size() / 2;
@@ -967,6 +990,21 @@ cudaError_t launch_schur(pba_ctx* c, const DevProblem& pb, const float* Hfd, con
         return launch_schur_tc(pb, Hfd, Hnn, schur_tc_lists(c), schur_lists(c), red, red_stride, c->d.Soff,
                                c->d.err, c->stream, launches);
     return launch_schur_sparse(pb, Hfd, Hnn, schur_lists(c), part, c->d.Soff, c->stream, launches, tile_todo);
+}
+
+// Places the Schur pair items of every bundle (bundle_pair_items; once per
+// structure) and uploads them into the workspace: before the SIMT path
+// first runs on a workspace (the tensor-core path does not read them).
+pba_status fill_pair_items(pba_ctx* ctx)
+{
+    if (!ctx->items_ready) {
+        ctx->pair_items.resize((size_t)ctx->n_pair_items);
+        std::vector<int64_t> cnt;
+        for (const BundleIn& b : ctx->bun) bundle_pair_items(ctx, b, cnt, ctx->pair_items.data() + b.item0);
+        ctx->items_ready = true;
+    }
+    CK(h2d(ctx, ctx->d.pair_items, ctx->pair_items.data(), sizeof(int2) * ctx->pair_items.size()));
+    return PBA_OK;
 }
 
 SolveArgs make_solve(pba_ctx* c)
@@ -1325,7 +1363,6 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     CK(h2d(ctx, ctx->d.pair_chunk, ctx->pair_chunk.data(), sizeof(int) * ctx->pair_chunk.size()));
     CK(h2d(ctx, ctx->d.chunk_pair, ctx->chunk_pair.data(), sizeof(int) * ctx->chunk_pair.size()));
     CK(h2d(ctx, ctx->d.chunk_start, ctx->chunk_start.data(), sizeof(int) * ctx->chunk_start.size()));
-    CK(h2d(ctx, ctx->d.pair_items, ctx->pair_items.data(), sizeof(int2) * ctx->pair_items.size()));
     CK(h2d(ctx, ctx->d.st_info, ctx->st_info.data(), sizeof(int4) * ctx->st_info.size()));
     CK(h2d(ctx, ctx->d.st_items, ctx->st_items.data(), sizeof(int4) * ctx->st_items.size()));
     CK(h2d(ctx, ctx->d.st_rows, ctx->st_rows.data(), sizeof(StRow) * ctx->st_rows.size()));
@@ -1347,6 +1384,10 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
         CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev));
     }
     LAUNCH(TS_PRE, launch_setup(L.pb, ctx->d.tile_f0, ctx->d.gx, ctx->d.gy, ctx->d.I0p, ctx->d.G0p, ctx->stream));
+    if (effective_schur_path(ctx) == PBA_SCHUR_SIMT) {
+        pba_status s = fill_pair_items(ctx);
+        if (s != PBA_OK) return s;
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->ws_ready = true;
     return PBA_OK;
@@ -2102,6 +2143,13 @@ pba_status pba_set_schur_path(pba_ctx* ctx, int path)
         destroy_graphs(ctx);
         ctx->schur_path = path;
         ctx->ic_chunks_valid = false;
+    }
+    // the SIMT path reads the pair items: placed now if the workspace is
+    // set (else pba_set_workspace places them)
+    if (ctx->ws_ready && effective_schur_path(ctx) == PBA_SCHUR_SIMT) {
+        pba_status s = fill_pair_items(ctx);
+        if (s != PBA_OK) return s;
+        CK(cudaStreamSynchronize(ctx->stream));
     }
     return PBA_OK;
 }
