@@ -196,6 +196,22 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
+// One reduce-scatter level over the lanes at stride o: a lane keeps values
+// [0, M) (lane bit o clear) or [M, 2M) (set) of v, moved to v[0 .. M), and
+// adds its partner's copy of them.
+template <int M, int N>
+__device__ __forceinline__ void scatter_level(float (&v)[N], int lane, int o)
+{
+    static_assert(2 * M <= N, "scatter level");
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+        const float send = up ? v[q] : v[q + M];
+        const float keep = up ? v[q + M] : v[q];
+        v[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+}
+
 __device__ __forceinline__ float warp_sum1(float v)
 {
 #pragma unroll

@@ -33,21 +33,6 @@ __device__ __forceinline__ int rank_of(unsigned mask, int lane)
     return __popc(mask & ((1u << lane) - 1u));
 }
 
-// One reduce-scatter level over the lanes at stride o: a lane keeps values
-// [0, M) (lane bit o clear) or [M, 2M) (set) of v, moved to v[0 .. M), and
-// adds its partner's copy of them.
-template <int M>
-__device__ __forceinline__ void scatter_level(float (&v)[8], int lane, int o)
-{
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int q = 0; q < M; ++q) {
-        const float send = up ? v[q] : v[q + M];
-        const float keep = up ? v[q + M] : v[q];
-        v[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
-}
-
 // Sums of v[0 .. 7] over the warp's lanes by reduce-scatter (nine exchanges
 // instead of forty): at strides 16, 8, 4 a lane keeps half of its values and
 // adds its partner's copy of them, then two butterfly levels; sum q ends in

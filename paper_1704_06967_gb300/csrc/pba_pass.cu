@@ -170,12 +170,27 @@ ic_precompute_kernel(DevProblem pb, const float* __restrict__ fconst, const doub
         for (int a = 0; a < 6; ++a) hd[a * nvis] = hfd[a];
     }
     hpart[(size_t)e * kTile + lane] = hnn;
-    warp_sum<21>(hff);
-    if (lane == 0) {
-        float* o = ent_part + (size_t)pb.entry_slot[e] * kEntryPartial;
+    // the entry's 21 H_ff sums over the lanes by reduce-scatter (25
+    // exchanges instead of 105): sums 0-15 end on lanes 2q, 2q + 1, sums
+    // 16-20 on lanes 4q .. 4q + 3
+    float a[16], b[8];
 #pragma unroll
-        for (int q = 0; q < 21; ++q) o[q] = hff[q];
-    }
+    for (int q = 0; q < 16; ++q) a[q] = hff[q];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) b[q] = q < 5 ? hff[16 + q] : 0.0f;
+    scatter_level<8>(a, lane, 16);
+    scatter_level<4>(a, lane, 8);
+    scatter_level<2>(a, lane, 4);
+    scatter_level<1>(a, lane, 2);
+    a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+    scatter_level<4>(b, lane, 16);
+    scatter_level<2>(b, lane, 8);
+    scatter_level<1>(b, lane, 4);
+    b[0] += __shfl_xor_sync(0xffffffffu, b[0], 2);
+    b[0] += __shfl_xor_sync(0xffffffffu, b[0], 1);
+    float* o = ent_part + (size_t)pb.entry_slot[e] * kEntryPartial;
+    if ((lane & 1) == 0) o[lane >> 1] = a[0];
+    if ((lane & 3) == 0 && lane < 20) o[16 + (lane >> 2)] = b[0];
 }
 
 // H_dd per point (entries of its tile added in order; entries of frames
