@@ -867,9 +867,10 @@ pba_status upload_params(pba_ctx* ctx, int bi, const double* poses, const double
     CK(h2d(ctx, ctx->d.poses64 + (size_t)12 * b.fo, poses, sizeof(double) * 12 * b.F));
     CK(launch_frame_consts(make_solve(ctx), b.fo, b.F, ctx->stream, init_photo));
     if (depth) {
-        std::vector<double> ds(b.perm.size(), 1.0);
-        for (size_t i = 0; i < ds.size(); ++i)
-            if (b.perm[i] >= 0) ds[i] = depth[b.perm[i]];
+        std::vector<double> ds(b.perm.size());
+        parallel_ranges((int64_t)ds.size(), 8192, 16, [&](int, int64_t i0, int64_t i1) {
+            for (int64_t i = i0; i < i1; ++i) ds[i] = b.perm[i] >= 0 ? depth[b.perm[i]] : 1.0;
+        });
         CK(h2d(ctx, ctx->d.d64 + (size_t)kTile * b.to, ds.data(), sizeof(double) * ds.size()));
     }
     // all host staging above is pageable: the copies have consumed it on return
@@ -1329,18 +1330,22 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     std::vector<unsigned char> valid(Np, 0);
     std::vector<int> slot_caller(Np, -1);
     for (const BundleIn& b : ctx->bun) {
-        int last = b.perm[0];
-        for (size_t k = 0; k < b.perm.size(); ++k) {
-            const size_t i = (size_t)kTile * b.to + k;
-            const int n = b.perm[k] >= 0 ? b.perm[k] : last;
-            if (b.perm[k] >= 0) last = b.perm[k];
-            uvs[2 * i] = b.uv[2 * n];
-            uvs[2 * i + 1] = b.uv[2 * n + 1];
-            xn[i] = make_float2((float)((uvs[2 * i] - ctx->K[2]) / ctx->K[0]),
-                                (float)((uvs[2 * i + 1] - ctx->K[3]) / ctx->K[1]));
-            valid[i] = b.perm[k] >= 0;
-            slot_caller[i] = b.perm[k];
-        }
+        // the real points fill the first N slots; a pad copies the last real
+        // point (ranges of slots on the host pool)
+        if (b.perm.empty()) continue;
+        const int last = b.perm[b.N - 1];
+        parallel_ranges((int64_t)b.perm.size(), 8192, 16, [&](int, int64_t k0, int64_t k1) {
+            for (int64_t k = k0; k < k1; ++k) {
+                const size_t i = (size_t)kTile * b.to + k;
+                const int n = b.perm[k] >= 0 ? b.perm[k] : last;
+                uvs[2 * i] = b.uv[2 * n];
+                uvs[2 * i + 1] = b.uv[2 * n + 1];
+                xn[i] = make_float2((float)((uvs[2 * i] - ctx->K[2]) / ctx->K[0]),
+                                    (float)((uvs[2 * i + 1] - ctx->K[3]) / ctx->K[1]));
+                valid[i] = b.perm[k] >= 0;
+                slot_caller[i] = b.perm[k];
+            }
+        });
     }
     std::vector<int> pat(ctx->pattern.begin(), ctx->pattern.end());
     CK(h2d(ctx, ctx->d.pat, pat.data(), sizeof(int) * pat.size()));
@@ -1940,16 +1945,21 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
 static pba_status gather_points(pba_ctx* ctx, const BundleIn& b, const void* dev, bool fp32, double* out)
 {
     const size_t n = b.perm.size(), off = (size_t)kTile * b.to;
+    // (the scatter into caller order runs in ranges on the host pool)
     if (fp32) {
         std::vector<float> h(n);
         CK(d2h(ctx, h.data(), static_cast<const float*>(dev) + off, sizeof(float) * n));
-        for (size_t i = 0; i < n; ++i)
-            if (b.perm[i] >= 0) out[b.perm[i]] = h[i];
+        parallel_ranges((int64_t)n, 8192, 16, [&](int, int64_t i0, int64_t i1) {
+            for (int64_t i = i0; i < i1; ++i)
+                if (b.perm[i] >= 0) out[b.perm[i]] = h[i];
+        });
     } else {
         std::vector<double> h(n);
         CK(d2h(ctx, h.data(), static_cast<const double*>(dev) + off, sizeof(double) * n));
-        for (size_t i = 0; i < n; ++i)
-            if (b.perm[i] >= 0) out[b.perm[i]] = h[i];
+        parallel_ranges((int64_t)n, 8192, 16, [&](int, int64_t i0, int64_t i1) {
+            for (int64_t i = i0; i < i1; ++i)
+                if (b.perm[i] >= 0) out[b.perm[i]] = h[i];
+        });
     }
     return PBA_OK;
 }
