@@ -88,6 +88,8 @@ def _L():
             "or_fc_step": ([pp, vp, vp, vp, vp, vp, vp, vp], i),
             "or_eval": ([pp, vp, vp, vp], None),
             "or_photo_update": ([pp, vp, vp], None),
+            "or_photo_compose": ([vp, vp, vp], None),
+            "or_ic_step_joint": ([pp, ctypes.POINTER(_IcPre), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -298,6 +300,41 @@ def ic_step(pb: Problem, pre: IcPre, poses0, depths0, poses, depths):
     if st != 0:
         raise np.linalg.LinAlgError("reduced camera system not positive definite")
     return dtheta.reshape(pb.F, 6), dd, po, do, stats
+
+
+def photo_compose(ab, dab):
+    """The brightness pair after a template-side increment (da, db)."""
+    ab, dab, out = _f64(ab), _f64(dab), np.zeros(2)
+    _L().or_photo_compose(_p(ab), _p(dab), _p(out))
+    return out
+
+
+def ic_step_joint(pb: Problem, pre: IcPre, poses0, depths0, poses, depths):
+    """One IC iteration with the brightness pairs (pb.photo, updated in
+    place) as Gauss-Newton unknowns; returns (dtheta [F,6], dab [F,2], dd
+    [N], poses', depths', stats)."""
+    if pb.photo is None:
+        raise ValueError("the joint brightness step needs a problem with photometric=True")
+    poses0, depths0, poses, depths = _f64(poses0), _f64(depths0), _f64(poses), _f64(depths)
+    dtheta, dab, dd = np.zeros(6 * pb.F), np.zeros(2 * pb.F), np.zeros(pb.N)
+    po, do, stats = np.empty_like(poses), np.empty_like(depths), np.zeros(N_STATS)
+    st = _L().or_ic_step_joint(pb.ref(), pre.ref(), _p(poses0), _p(depths0), _p(poses), _p(depths),
+                               _p(dtheta), _p(dab), _p(dd), _p(po), _p(do), _p(stats))
+    if st != 0:
+        raise np.linalg.LinAlgError("reduced camera system not positive definite")
+    return dtheta.reshape(pb.F, 6), dab.reshape(pb.F, 2), dd, po, do, stats
+
+
+def ic_run_joint(pb: Problem, poses0, depths0, iters: int):
+    """IC-PBA with the brightness pairs as unknowns (same return layout as
+    ic_run; pb.photo holds the final pairs)."""
+    pre = ic_precompute(pb, poses0, depths0)
+    poses, depths = _f64(poses0).copy(), _f64(depths0).copy()
+    hist = np.zeros((iters + 1, N_STATS))
+    for k in range(iters):
+        _, _, _, poses, depths, hist[k] = ic_step_joint(pb, pre, poses0, depths0, poses, depths)
+    hist[iters] = evaluate(pb, poses, depths)
+    return poses, depths, hist
 
 
 def fc_linearize(pb: Problem, poses, depths):

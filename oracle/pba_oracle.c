@@ -763,6 +763,222 @@ int or_ic_step(const or_problem* pb, const or_ic_pre* pre, const double* poses0,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Affine brightness as Gauss-Newton unknowns (IC; an option beyond the      */
+/* paper, whose Sec. 2 notes that direct methods must model lighting)        */
+/* ------------------------------------------------------------------------ */
+/* Each target frame f carries (alpha_f, beta_f) with r = I_0 - (alpha_f I_f +
+ * beta_f). In the inverse compositional form the increment acts on the
+ * template, as it does for the pose (Sec. 3.5): the template intensities
+ * become (1 + da_f) I_0 + db_f, so to first order
+ *     r(Delta) = r + J_theta Delta theta_f + J_d Delta d_n + I_0 da_f + db_f,
+ * and the two new Jacobian columns, I_0(x) and 1, do not depend on the
+ * parameters: H stays fixed at p_0 like the rest of the IC system. The frame
+ * blocks become 8 x 8 ([Delta t, omega, da, db]), H_fd 8-vectors. After the
+ * solve, (1 + da) I_0 + db = alpha I_f + beta is solved for I_0, which
+ * composes the increment into the pair:
+ *     alpha' = alpha / (1 + da),  beta' = (beta - db) / (1 + da). */
+void or_photo_compose(const double* ab, const double* dab, double* out)
+{
+    const double s = 1.0 + dab[0];
+    out[0] = ab[0] / s;
+    out[1] = (ab[1] - dab[1]) / s;
+}
+
+/* Schur-complement solve with nb unknowns per frame block (nb = 8: the pose
+ * and the brightness pair), otherwise as or_schur_solve: S = Hpp - Hpd
+ * Hdd^-1 Hdp, frames without residuals get an identity block, the scale
+ * prior mu that that^T (mu = mean diagonal over the pose rows of the active
+ * frames) goes on the translation rows of the first active frame (damping =
+ * 0), damping scales every diagonal entry of Hpp and Hdd by 1 + lambda and
+ * then moves the translations along the scale null vector. Hff: F*nb*nb,
+ * Hfd: N*F*nb, g_theta: F*nb; dtheta: F*nb out. */
+static int schur_solve_nb(int nb, int F, int N, const double* Hff, const double* Hfd, const double* Hdd,
+                          const double* g_theta, const double* g_d, const double* t_anchor, double damping,
+                          double* dtheta, double* dd)
+{
+    int Fp = F - 1, n = nb * Fp;
+    const double ld = 1.0 + damping;
+    double* S = (double*)calloc((size_t)n * n, sizeof(double));
+    double* b = (double*)calloc(n, sizeof(double));
+    int* active = (int*)calloc(F, sizeof(int));
+    for (int f = 1; f < F; ++f) {
+        double tr = 0.0;
+        for (int a = 0; a < 6; ++a) tr += Hff[((size_t)f * nb + a) * nb + a];
+        active[f] = tr > 0.0;
+        for (int a = 0; a < nb; ++a) {
+            for (int c = 0; c < nb; ++c)
+                S[(size_t)(nb * (f - 1) + a) * n + nb * (f - 1) + c] =
+                    Hff[((size_t)f * nb + a) * nb + c] * (a == c ? ld : 1.0);
+            b[nb * (f - 1) + a] = -g_theta[nb * f + a];
+        }
+    }
+    for (int p = 0; p < N; ++p) {
+        if (!(Hdd[p] > 0.0)) continue;
+        const double hd = Hdd[p] * ld;
+        for (int f = 1; f < F; ++f) {
+            const double* hf = Hfd + nb * ((size_t)p * F + f);
+            for (int a = 0; a < nb; ++a) b[nb * (f - 1) + a] += hf[a] * g_d[p] / hd;
+            for (int g = 1; g < F; ++g) {
+                const double* hg = Hfd + nb * ((size_t)p * F + g);
+                for (int a = 0; a < nb; ++a)
+                    for (int c = 0; c < nb; ++c)
+                        S[(size_t)(nb * (f - 1) + a) * n + nb * (g - 1) + c] -= hf[a] * hg[c] / hd;
+            }
+        }
+    }
+    double mu = 0.0;
+    int n_act = 0, anchor = -1;
+    for (int f = 1; f < F; ++f) {
+        if (!active[f]) continue;
+        if (anchor < 0) anchor = f;
+        for (int a = 0; a < 6; ++a) mu += S[(size_t)(nb * (f - 1) + a) * n + nb * (f - 1) + a];
+        n_act += 6;
+    }
+    if (n_act > 0) mu /= n_act;
+    for (int f = 1; f < F; ++f) {
+        if (active[f]) continue;
+        for (int a = 0; a < nb; ++a) {
+            for (int c = 0; c < n; ++c) {
+                S[(size_t)(nb * (f - 1) + a) * n + c] = 0.0;
+                S[(size_t)c * n + nb * (f - 1) + a] = 0.0;
+            }
+            S[(size_t)(nb * (f - 1) + a) * n + nb * (f - 1) + a] = 1.0;
+            b[nb * (f - 1) + a] = 0.0;
+        }
+    }
+    if (anchor > 0 && damping == 0.0) {
+        const double* ta = t_anchor + 3 * anchor;
+        double nt = sqrt(ta[0] * ta[0] + ta[1] * ta[1] + ta[2] * ta[2]);
+        if (nt > 0.0) {
+            double th[3] = {ta[0] / nt, ta[1] / nt, ta[2] / nt};
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 3; ++c)
+                    S[(size_t)(nb * (anchor - 1) + a) * n + nb * (anchor - 1) + c] += mu * th[a] * th[c];
+        }
+    }
+    int st = cholesky_inplace(S, n);
+    if (st == OR_OK) {
+        cholesky_solve(S, n, b);
+        memset(dtheta, 0, sizeof(double) * nb * F);
+        for (int f = 1; f < F; ++f)
+            for (int a = 0; a < nb; ++a) dtheta[nb * f + a] = b[nb * (f - 1) + a];
+        if (damping > 0.0 && anchor > 0) {
+            const double* ta = t_anchor + 3 * anchor;
+            const double* da = dtheta + nb * anchor;
+            const double n2 = ta[0] * ta[0] + ta[1] * ta[1] + ta[2] * ta[2];
+            const double alpha = n2 > 0.0 ? (ta[0] * da[0] + ta[1] * da[1] + ta[2] * da[2]) / n2 : 0.0;
+            for (int f = 1; f < F; ++f)
+                if (active[f])
+                    for (int a = 0; a < 3; ++a) dtheta[nb * f + a] -= alpha * t_anchor[3 * f + a];
+        }
+        for (int p = 0; p < N; ++p) {
+            if (!(Hdd[p] > 0.0)) { dd[p] = 0.0; continue; }
+            double s = g_d[p];
+            for (int f = 1; f < F; ++f) {
+                const double* hf = Hfd + nb * ((size_t)p * F + f);
+                for (int a = 0; a < nb; ++a) s += hf[a] * dtheta[nb * f + a];
+            }
+            dd[p] = -s / (Hdd[p] * ld);
+        }
+    }
+    free(S);
+    free(b);
+    free(active);
+    return st;
+}
+
+/* One IC iteration with the brightness pairs pb->photo as unknowns (steps
+ * 1-4 of Sec. 3.5 over the 8-parameter frame blocks; the pose and depth
+ * updates of Sec. 3.6; the pairs by or_photo_compose). H comes from the
+ * precompute's rows and W_0 (valid at p_0), extended by the columns I_0 and
+ * 1; g = J^T W r over the residuals valid now and at p_0, with the weights
+ * of the current residuals. dtheta: F*6, dab: F*2 (frame 0: zero). */
+int or_ic_step_joint(const or_problem* pb, const or_ic_pre* pre, const double* poses0,
+                     const double* depths0, const double* poses, const double* depths,
+                     double* dtheta, double* dab, double* dd, double* poses_out, double* depths_out,
+                     double* stats)
+{
+    int F = pb->F, N = pb->N, P = pb->P;
+    if (!pb->photo) return OR_ERR_NOT_PD;
+    double* Hff = (double*)calloc((size_t)64 * F, sizeof(double));
+    double* Hfd = (double*)calloc((size_t)8 * N * F, sizeof(double));
+    double* g8 = (double*)calloc((size_t)8 * F, sizeof(double));
+    double* g_d = (double*)calloc(N, sizeof(double));
+    double* d8 = (double*)calloc((size_t)8 * F, sizeof(double));
+    double* t_anchor = (double*)malloc(sizeof(double) * 3 * F);
+    double energy = 0.0, sq = 0.0, cnt = 0.0;
+    for (int n = 0; n < N; ++n) {
+        for (int f = 1; f < F; ++f) {
+            if (!pb->vis[(size_t)n * F + f]) continue;
+            const double* R = poses + 12 * f;
+            for (int j = 0; j < P; ++j) {
+                size_t id = rid(pb, n, f, j);
+                int px, py;
+                double x, y;
+                pattern_pixel(pb, n, j, &px, &py, &x, &y);
+                /* the frame-block row [J_theta, I_0, 1] and the depth column */
+                double Jf[8];
+                const double* J = pre->J + 7 * id;
+                for (int a = 0; a < 6; ++a) Jf[a] = J[a];
+                Jf[6] = pix(frame_img(pb, 0), pb->W, px, py);
+                Jf[7] = 1.0;
+                if (pre->valid0[id]) {
+                    const double w0 = pre->w0[id];
+                    double* hff = Hff + 64 * f;
+                    double* hfd = Hfd + 8 * ((size_t)n * F + f);
+                    for (int a = 0; a < 8; ++a) {
+                        for (int b = 0; b < 8; ++b) hff[8 * a + b] += w0 * (Jf[a] * Jf[b]);
+                        hfd[a] += w0 * Jf[a] * J[6];
+                    }
+                }
+                double r, u[2], q[3];
+                if (!residual_at(pb, n, f, j, R, R + 9, depths[n], &r, u, q)) continue;
+                energy += or_huber_rho(r, pb->huber_k);
+                sq += r * r;
+                cnt += 1.0;
+                if (!pre->valid0[id]) continue;
+                const double w = or_huber_weight(r, pb->huber_k);
+                for (int a = 0; a < 8; ++a) g8[8 * f + a] += Jf[a] * w * r;
+                g_d[n] += J[6] * w * r;
+            }
+        }
+    }
+    stats[ST_ENERGY] = energy;
+    stats[ST_RMS] = cnt > 0 ? sqrt(sq / cnt) : 0.0;
+    stats[ST_COUNT] = cnt;
+    for (int f = 0; f < F; ++f)
+        for (int i = 0; i < 3; ++i) t_anchor[3 * f + i] = poses0[12 * f + 9 + i];
+    int st = schur_solve_nb(8, F, N, Hff, Hfd, pre->Hdd, g8, g_d, t_anchor, pb->damping, d8, dd);
+    if (st == OR_OK) {
+        for (int f = 0; f < F; ++f) {
+            for (int a = 0; a < 6; ++a) dtheta[6 * f + a] = d8[8 * f + a];
+            dab[2 * f] = d8[8 * f + 6];
+            dab[2 * f + 1] = d8[8 * f + 7];
+        }
+        or_ic_update(F, N, poses0, depths0, poses, depths, dtheta, dd, poses_out, depths_out);
+        stats[ST_MAXDISP] = or_max_reproj_disp(pb, poses, depths, poses_out, depths_out);
+        for (int f = 1; f < F; ++f) {
+            double ab[2];
+            or_photo_compose(pb->photo + 2 * f, dab + 2 * f, ab);
+            pb->photo[2 * f] = ab[0];
+            pb->photo[2 * f + 1] = ab[1];
+        }
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < 6 * F; ++i) a += dtheta[i] * dtheta[i];
+        for (int n = 0; n < N; ++n) b += dd[n] * dd[n];
+        stats[ST_DTHETA] = sqrt(a);
+        stats[ST_DD] = sqrt(b);
+    }
+    free(Hff);
+    free(Hfd);
+    free(g8);
+    free(g_d);
+    free(d8);
+    free(t_anchor);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
 /* FC iteration (the plain method: Jacobians and Hessian every iteration)    */
 /* ------------------------------------------------------------------------ */
 void or_fc_linearize(const or_problem* pb, const double* poses, const double* depths,
