@@ -48,7 +48,8 @@ class _Problem(ctypes.Structure):
                 ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double),
                 ("cy", ctypes.c_double), ("huber_k", ctypes.c_double),
                 ("img", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("pat", ctypes.c_void_p),
-                ("vis", ctypes.c_void_p), ("damping", ctypes.c_double), ("photo", ctypes.c_void_p)]
+                ("vis", ctypes.c_void_p), ("damping", ctypes.c_double), ("photo", ctypes.c_void_p),
+                ("photo_prior", ctypes.c_double)]
 
 
 class _IcPre(ctypes.Structure):
@@ -181,7 +182,8 @@ class Problem:
     """A bundle as the oracle sees it: FP64 copies of the (dequantised) images,
     integer point pixels, pattern, visibility, intrinsics and Huber k."""
 
-    def __init__(self, images, uv, pattern, vis, intrinsics, huber_k, damping=0.0, photometric=False):
+    def __init__(self, images, uv, pattern, vis, intrinsics, huber_k, damping=0.0, photometric=False,
+                 photo_prior=0.0):
         self.img = _f64(images)
         self.F, self.H, self.W = self.img.shape
         self.uv = np.ascontiguousarray(uv, dtype=np.int32)
@@ -197,12 +199,12 @@ class Problem:
         self.photo = np.tile([1.0, 0.0], self.F) if photometric else None
         self.c = _Problem(self.W, self.H, self.F, self.N, self.P, fx, fy, cx, cy,
                           self.huber_k, _p(self.img), _p(self.uv), _p(self.pat), _p(self.vis),
-                          self.damping, _p(self.photo) if photometric else None)
+                          self.damping, _p(self.photo) if photometric else None, float(photo_prior))
 
     @classmethod
-    def from_scene(cls, scene, damping=0.0, photometric=False):
+    def from_scene(cls, scene, damping=0.0, photometric=False, photo_prior=0.0):
         return cls(scene.images_f32, scene.uv, scene.pattern, scene.vis, scene.intrinsics,
-                   scene.huber_k, damping, photometric)
+                   scene.huber_k, damping, photometric, photo_prior)
 
     def ref(self):
         return ctypes.byref(self.c)

@@ -56,6 +56,7 @@ typedef struct {
     const unsigned char* vis;   /* N*F visibility, vis[n*F+f] */
     double damping;             /* Levenberg-Marquardt lambda (0: Gauss-Newton) */
     double* photo;              /* F*2 affine brightness (alpha_f, beta_f) or NULL (model off) */
+    double photo_prior;         /* joint brightness step: prior weight lambda >= 0 (0: none) */
 } or_problem;
 
 /* IC precompute (Sec. 3.5), indexed by residual id ((n*F + f)*P + j). */
@@ -892,14 +893,15 @@ static int schur_solve_nb(int nb, int F, int N, const double* Hff, const double*
  * updates of Sec. 3.6; the pairs by or_photo_compose). H comes from the
  * precompute's rows and W_0 (valid at p_0), extended by the columns I_0 and
  * 1; g = J^T W r over the residuals valid now and at p_0, with the weights
- * of the current residuals. dtheta: F*6, dab: F*2 (frame 0: zero). */
+ * of the current residuals; with pb->photo_prior > 0 a prior pulls the pairs
+ * toward (1, 0). dtheta: F*6, dab: F*2 (frame 0: zero). */
 int or_ic_step_joint(const or_problem* pb, const or_ic_pre* pre, const double* poses0,
                      const double* depths0, const double* poses, const double* depths,
                      double* dtheta, double* dab, double* dd, double* poses_out, double* depths_out,
                      double* stats)
 {
     int F = pb->F, N = pb->N, P = pb->P;
-    if (!pb->photo) return OR_ERR_NOT_PD;
+    if (!pb->photo || F < 2) return OR_ERR_NOT_PD;
     double* Hff = (double*)calloc((size_t)64 * F, sizeof(double));
     double* Hfd = (double*)calloc((size_t)8 * N * F, sizeof(double));
     double* g8 = (double*)calloc((size_t)8 * F, sizeof(double));
@@ -946,6 +948,18 @@ int or_ic_step_joint(const or_problem* pb, const or_ic_pre* pre, const double* p
     stats[ST_ENERGY] = energy;
     stats[ST_RMS] = cnt > 0 ? sqrt(sq / cnt) : 0.0;
     stats[ST_COUNT] = cnt;
+    /* prior on the pairs: lambda W_f ((ln alpha_f)^2 + beta_f^2) / 2 with W_f =
+     * sum w0 of the frame (its H_bb); to first order in the increment ln
+     * alpha' = ln alpha - da and beta' = beta - db, i.e. residuals (ln alpha,
+     * beta) with Jacobian -I on (da, db): H += W I, g -= W (ln alpha, beta) */
+    if (pb->photo_prior > 0.0)
+        for (int f = 1; f < F; ++f) {
+            const double w = pb->photo_prior * Hff[64 * f + 63];
+            Hff[64 * f + 54] += w;
+            Hff[64 * f + 63] += w;
+            g8[8 * f + 6] -= w * log(pb->photo[2 * f]);
+            g8[8 * f + 7] -= w * pb->photo[2 * f + 1];
+        }
     for (int f = 0; f < F; ++f)
         for (int i = 0; i < 3; ++i) t_anchor[3 * f + i] = poses0[12 * f + 9 + i];
     int st = schur_solve_nb(8, F, N, Hff, Hfd, pre->Hdd, g8, g_d, t_anchor, pb->damping, d8, dd);

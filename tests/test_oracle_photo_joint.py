@@ -19,7 +19,7 @@ import oracle
 import synth
 
 
-def _identity_warp_problem(alphas, betas, huber_k=None):
+def _identity_warp_problem(alphas, betas, huber_k=None, photo_prior=0.0):
     """Every frame sees the template through the identity pose; frame f is
     the template mapped so that alpha_f I_f + beta_f = I_0."""
     sc = synth.make_scene("small", noise_free=True)
@@ -29,7 +29,8 @@ def _identity_warp_problem(alphas, betas, huber_k=None):
     poses[:, [0, 4, 8]] = 1.0
     vis = np.ones((sc.N, sc.F), np.uint8)
     k = sc.huber_k if huber_k is None else huber_k
-    pb = oracle.Problem(imgs, sc.uv, sc.pattern, vis, sc.intrinsics, k, photometric=True)
+    pb = oracle.Problem(imgs, sc.uv, sc.pattern, vis, sc.intrinsics, k, photometric=True,
+                        photo_prior=photo_prior)
     return sc, pb, poses
 
 
@@ -56,14 +57,25 @@ def test_joint_step_recovers_affine_brightness_exactly():
     assert st[oracle.ST_RMS] < 1e-9
 
 
-def _dense_first_step(sc, pb, pre):
+def _dense_first_step(sc, pb, pre, prior=0.0):
     """Minimiser of sum w0 (r0 + J Delta)^2 over [per frame: Delta t, omega,
     da, db | per point: Delta d] from the precompute's rows (the step at p_0,
-    where the current weights are W_0), by numpy least squares."""
+    where the current weights are W_0), by numpy least squares; with prior,
+    also the rows sqrt(W_f) (ln alpha_f - da_f), sqrt(W_f) (beta_f - db_f),
+    W_f = prior * sum of the frame's w0."""
     F, N, P = pb.F, pb.N, pb.P
     I0 = pb.img[0]
     rows, rhs = [], []
     nf = 8 * (F - 1)
+    if prior > 0.0:
+        for f in range(1, F):
+            W = prior * sum(pre.w0[pre.rid(pb, n, f, j)] for n in range(N) for j in range(P)
+                            if pre.valid0[pre.rid(pb, n, f, j)])
+            for b, target in ((0, np.log(pb.photo[2 * f])), (1, pb.photo[2 * f + 1])):
+                row = np.zeros(nf + N)
+                row[8 * (f - 1) + 6 + b] = -np.sqrt(W)
+                rows.append(row)
+                rhs.append(-np.sqrt(W) * target)
     for n in range(N):
         for f in range(1, F):
             if not pb.vis[n, f]:
@@ -133,3 +145,29 @@ def test_composed_update_moves_the_residual_by_the_template_increment(da, db):
         # exactly r1 = (I_0 da + db) / (1 + da): the model up to O(da (|da| + |db|))
         assert abs(r1 - model) <= 2.0 * abs(da) * (abs(da) + abs(db)) + 1e-14, (r1, model)
         assert abs(r1 - model) <= 1e-5 * abs(model)
+
+
+def test_prior_step_is_the_dense_minimiser_with_the_prior_rows():
+    """At pairs off the truth (identity warp, zero depth coupling), the step
+    with the prior is the dense minimiser of the linearised data cost plus
+    the prior rows; without the prior it is the exact recovery."""
+    rng = np.random.default_rng(4)
+    F = synth.make_scene("small", noise_free=True).F
+    alphas = np.r_[1.0, rng.uniform(0.7, 1.3, F - 1)]
+    betas = np.r_[0.0, rng.uniform(-0.1, 0.1, F - 1)]
+    sc, pb, poses = _identity_warp_problem(alphas, betas, photo_prior=0.3)
+    start = np.r_[1.0, 0.0, np.c_[rng.uniform(0.8, 1.2, F - 1), rng.uniform(-0.05, 0.05, F - 1)].ravel()]
+    pb.photo[:] = start
+    d = sc.depths_gt
+    pre = oracle.ic_precompute(pb, poses, d)
+    dense, _ = _dense_first_step(sc, pb, pre, prior=0.3)
+    dth, dab, _, _, _, _ = oracle.ic_step_joint(pb, pre, poses, d, poses, d)
+    assert np.abs(dab[1:] - dense[:, 6:]).max() <= 1e-8 * np.abs(dense[:, 6:]).max()
+    assert np.abs(dth[1:] - dense[:, :6]).max() <= 1e-8 * max(np.abs(dense[:, :6]).max(), 1e-12)
+    # the prior changes the step (without it the step lands on the truth)
+    pb0 = _identity_warp_problem(alphas, betas)[1]
+    pb0.photo[:] = start
+    pre0 = oracle.ic_precompute(pb0, poses, d)
+    _, dab0, _, _, _, _ = oracle.ic_step_joint(pb0, pre0, poses, d, poses, d)
+    assert np.abs(dab0 - dab).max() > 1e-2
+    assert np.abs(pb0.photo.reshape(F, 2)[1:] - np.c_[alphas, betas][1:]).max() < 1e-9
