@@ -110,14 +110,33 @@ typedef struct {
                                 system is definite) and keeps the exact gauge constraint
                                 t_a . Delta t_a = 0. pba_get_system returns the undamped
                                 blocks and the S that was factorised. */
-    int photometric;         /* non-zero: affine brightness per target frame (an option
-                                beyond the paper, whose Sec. 2 notes that direct methods
-                                must model lighting): residual r = I_0 - (alpha_f I_f +
-                                beta_f); after every IC/FC step each frame's pair is set
-                                from that step's residuals so that the warped samples
-                                take the template's Huber-weighted mean and spread
-                                (alpha = sqrt(var I_0 / var v), beta = mean I_0 - alpha
-                                mean v). Pairs start at (1, 0); see pba_get_brightness. */
+    int photometric;         /* affine brightness per target frame (an option beyond the
+                                paper, whose Sec. 2 notes that direct methods must model
+                                lighting): residual r = I_0 - (alpha_f I_f + beta_f),
+                                pairs starting at (1, 0); see pba_get_brightness.
+                                1: after every IC/FC step each frame's pair is set from
+                                that step's residuals so that the warped samples take the
+                                template's Huber-weighted mean and spread (alpha =
+                                sqrt(var I_0 / var v), beta = mean I_0 - alpha mean v).
+                                2: the pairs are unknowns of the IC Gauss-Newton system:
+                                the template-side increment (1 + da) I_0 + db adds the
+                                fixed columns I_0 and 1 to each frame block (8 x 8 blocks,
+                                an 8 (F - 1) reduced system formed and inverted once at
+                                p_0 with the rest of the IC system, Sec. 3.5), and a
+                                step composes alpha' = alpha / (1 + da), beta' = (beta -
+                                db) / (1 + da). One bundle per context; IC only
+                                (pba_solve_fc, pba_set_window and the sharded steps
+                                return PBA_ERR_ARG). Other values: PBA_ERR_ARG. */
+    double photo_prior;      /* photometric = 2: weight lambda >= 0 of a prior that pulls
+                                the pairs toward (1, 0), lambda W_f ((ln alpha_f)^2 +
+                                beta_f^2) / 2 with W_f the sum of the frame's Huber
+                                weights at p_0 (fixed with the IC system: lambda W_f on
+                                the pair's diagonal, its gradient at the current pair
+                                every step). The template-side pairs are exact at zero
+                                residual but, far from alignment, move toward
+                                var(I_0) / cov(I_0, I_f) and can drift; 0.01 keeps them
+                                bounded. 0: no prior. Negative or non-finite:
+                                PBA_ERR_ARG. */
 } pba_config;
 
 /* Statistics of one iteration (Sec. 4.1): Huber energy, RMS and count of the

@@ -81,7 +81,7 @@ ldl_cluster_kernel(BundleSet bs, dfloat* A, dfloat* L, dfloat* Linv, dfloat* dpi
     Linv += bd.lo;
     dpiv += bd.po;
     rpiv += bd.po;
-    const int n = 6 * cmap[bd.co + bd.F];  // active frames only (the same value in every CTA)
+    const int n = bs.nb * cmap[bd.co + bd.F];  // active frames only (the same value in every CTA)
     const int tid = threadIdx.x, wi = tid >> 5, lm = tid & 31;
     const int nrow = n + aug;  // rows of A / L (the last one is b^T when aug)
     const int nblk = (n + kNB - 1) / kNB;
@@ -230,7 +230,7 @@ ldl_inverse_kernel(BundleSet bs, const dfloat* L, const dfloat* Linv, const dflo
     extern __shared__ dfloat xs[];
     __shared__ dfloat t[kLdlBlock];
     const BundleDesc bd = bundle_at(bs, blockIdx.y);
-    const int nc = 6 * cmap[bd.co + bd.F], c = blockIdx.x;
+    const int nc = bs.nb * cmap[bd.co + bd.F], c = blockIdx.x;
     if (c >= nc) return;
     L += bd.ao;
     Linv += bd.lo;
@@ -251,7 +251,7 @@ cudaError_t launch_ldl(const BundleSet& bs, dfloat* A, dfloat* L, dfloat* Linv, 
                        const int* cmap, int aug, int* err, cudaStream_t st, int cluster)
 {
     const int C = cluster > 0 ? cluster : g_chol_cluster;
-    if (C > g_chol_cluster || (C & (C - 1)) || bs.B < 1) return cudaErrorInvalidValue;
+    if (C > g_chol_cluster || (C & (C - 1)) || bs.B < 1 || (bs.nb != 6 && bs.nb != 8)) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C * bs.B);
     cfg.blockDim = dim3(kCholThreads);
@@ -293,9 +293,10 @@ cudaError_t ldl_setup()
 cudaError_t launch_ldl_inverse(const BundleSet& bs, const dfloat* L, const dfloat* Linv, const dfloat* rpiv,
                                const int* cmap, dfloat* Sinv, cudaStream_t st)
 {
-    const int n6 = bs.n6max;
-    if (n6 > 6 * 1023 || n6 < 1 || bs.B < 1 || bs.B > 65535) return cudaErrorInvalidValue;
-    ldl_inverse_kernel<<<dim3(n6, bs.B), 256, sizeof(dfloat) * n6, st>>>(bs, L, Linv, rpiv, cmap, Sinv);
+    if (bs.nb != 6 && bs.nb != 8) return cudaErrorInvalidValue;
+    const int n = bs.n6max / 6 * bs.nb;
+    if (n > 8 * 1023 || n < 1 || bs.B < 1 || bs.B > 65535) return cudaErrorInvalidValue;
+    ldl_inverse_kernel<<<dim3(n, bs.B), 256, sizeof(dfloat) * n, st>>>(bs, L, Linv, rpiv, cmap, Sinv);
     return cudaGetLastError();
 }
 

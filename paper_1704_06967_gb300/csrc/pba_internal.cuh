@@ -32,6 +32,8 @@ constexpr int kEntryPartial = 44;     // floats of partial sums per entry (FC: 2
 constexpr int kPhotoColIc = 12;       // brightness fit sums of an entry (IC), 5 floats, 16-byte aligned
 constexpr int kPhotoColFc = 36;       // the same for FC
 constexpr int kFrameAlpha = 60;       // frame constants [60], [61]: affine brightness alpha, beta
+constexpr int kAffCol = 24;           // IC precompute rows, joint brightness: 12 H_pa, 3 H_aa sums
+constexpr int kAffComp = 15;
 constexpr int kStats = 8;             // doubles per statistics slot
 
 // device error word values (bit flags); the error words are err[0] for the
@@ -91,6 +93,9 @@ struct DevProblem {
     const float2* xn;           // Npad normalised centre coordinates
     const float* I0p;           // T*P*32 template intensities [tile][j][lane]
     unsigned char* valid_pt;    // Npad (1 = real point)
+    // joint brightness unknowns (IC, cfg.photometric = 2; null otherwise):
+    const unsigned* vmask0;     // per pair: bit j set when pattern pixel j was valid at p_0
+    const float* Had;           // per pair, 2 values (compact like H_fd): J_d^T W_0 [I_0, 1]
 };
 
 // ---------------------------------------------------------------------------

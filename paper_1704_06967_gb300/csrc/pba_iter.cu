@@ -64,7 +64,8 @@ __device__ __forceinline__ void dot_pair_add(float& s, float& c, float h, float2
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Depth back-substitution: Dd_n = -(g_n + sum_f H_fd^T Dtheta_f) / H_dd.
+// Depth back-substitution: Dd_n = -(g_n + sum_f H_fd^T Dtheta_f) / H_dd
+// (with the brightness pairs as unknowns, + sum_f H_a^T (da_f, db_f)).
 // g_n + sum H_fd^T Dtheta nearly cancels for well-determined points, so the
 // dot products are carried as unevaluated FP32 pairs (about 48 bits) and the
 // quotient and the depth rule are FP64 (IC: 1/H_dd and 1/d_0 come from the
@@ -75,7 +76,7 @@ __device__ __forceinline__ void dot_pair_add(float& s, float& c, float h, float2
 // update (dprev) and the tile's sum of Dd^2. apply = 0 only refreshes
 // dcur/dprev from the FP64 depths.
 // ---------------------------------------------------------------------------
-template <bool kIcRule>
+template <bool kIcRule, bool kAff = false>
 __global__ void __launch_bounds__(kTileWarps * 32)
 depth_update_kernel(DevProblem pb, DepthState ds, const float2* __restrict__ dth2,
                     const double* __restrict__ inv_hnn, const double* __restrict__ inv_d0,
@@ -93,6 +94,17 @@ depth_update_kernel(DevProblem pb, DepthState ds, const float2* __restrict__ dth
         const int f = t - pb.T + 1;
         if (warp != 0) return;
         if (lane < 6) d[lane] = a.dtheta64[6 * f + lane];
+        if (kAff && lane == 0) {
+            // the brightness pair: alpha' = alpha / (1 + da), beta' = (beta - db) / (1 + da)
+            const double da = a.dab64[2 * f], db = a.dab64[2 * f + 1];
+            if (da != 0.0 || db != 0.0) {
+                float* fcf = a.fc + (size_t)f * kFrameConst + kFrameAlpha;
+                const double s = 1.0 + da;
+                const double al = (double)fcf[0], be = (double)fcf[1];
+                fcf[0] = (float)(al / s);
+                fcf[1] = (float)((be - db) / s);
+            }
+        }
         __syncwarp();
         // a zero update (a bundle's reference frame, a frame without
         // residuals) leaves the pose exactly as it is
@@ -162,6 +174,13 @@ depth_update_kernel(DevProblem pb, DepthState ds, const float2* __restrict__ dth
             const float2* th = dth2 + 6 * f;
 #pragma unroll
             for (int k = 0; k < 6; ++k) dot_pair_add(s, c, vis ? (hv ? hv[k] : h[k * nvis]) : 0.0f, th[k]);
+            if (kAff) {
+                // joint brightness: + H_a^T (da, db) of the frame
+                const float* ha = ds.Had + (size_t)po * 2 + (vis ? rank_of(mask, lane) : 0);
+                const float2* tb = a.dab2 + 2 * f;
+                dot_pair_add(s, c, vis ? ha[0] : 0.0f, tb[0]);
+                dot_pair_add(s, c, vis ? ha[nvis] : 0.0f, tb[1]);
+            }
         };
         int i = warp;
         if (kIcRule) {
@@ -245,7 +264,7 @@ __device__ __forceinline__ void tile_stats_from_entries(const DevProblem& pb, co
 // w r (r, or k sign r: exact, no division); phase 4 streams the stored rows
 // J and adds J_theta w r into the frame sum and J_d w r into the point's.
 // ---------------------------------------------------------------------------
-template <int PMAX, bool kAccum, int DT, int WARPS>
+template <int PMAX, bool kAccum, int DT, int WARPS, bool kJoint = false>
 __global__ void __launch_bounds__(WARPS * 32, (PMAX <= 8 ? 32 : 16) / WARPS)
 ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float* __restrict__ fprev,
                    const float* __restrict__ dcur, const float* __restrict__ dprev,
@@ -262,10 +281,12 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
     const float k = pb.huber_k;
     float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // g_f (6), energy, r^2
     float cnt = 0.0f;
-    float ph[5] = {0, 0, 0, 0, 0};               // brightness fit sums (w, w v, w v^2, w I_0, w I_0^2)
+    float ph[5] = {0, 0, 0, 0, 0};  // photo: brightness fit sums (w, w v, w v^2, w I_0, w I_0^2);
+                                    // kJoint: g_a = (sum I_0 w r, sum w r) over the rows valid at p_0
     float gp = 0.0f, disp = 0.0f;
     if ((en.mask >> lane) & 1u) {
         const int n = en.tile * kTile + lane;
+        const unsigned vm0 = (kAccum && kJoint) ? pb.vmask0[en.pair_off + rank_of(en.mask, lane)] : 0u;
         const float* c = fconst + (size_t)en.f * kFrameConst;
         const float alpha = c[kFrameAlpha], beta = c[kFrameAlpha + 1];
         const float d = dcur[n];
@@ -319,7 +340,12 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
                 acc[7] = fmaf(r, r, acc[7]);
                 cnt += 1.0f;
                 wr[j] = fabsf(r) <= k ? r : copysignf(k, r);
-                if (kAccum && photo) {
+                if (kAccum && kJoint) {
+                    if ((vm0 >> j) & 1u) {
+                        ph[0] = fmaf(I0[j], wr[j], ph[0]);
+                        ph[1] += wr[j];
+                    }
+                } else if (kAccum && photo) {
                     const float w = huber_w(r, k);
                     ph[0] += w;
                     ph[1] = fmaf(w, val[j], ph[1]);
@@ -381,7 +407,14 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
         // 4q + 3), the count by a butterfly
         lane_sums8(acc, lane);
         cnt = warp_sum1(cnt);
-        if (photo) warp_sum<5>(ph);
+        if (kJoint) {
+            float g2[2] = {ph[0], ph[1]};
+            warp_sum(g2);
+            ph[0] = g2[0];
+            ph[1] = g2[1];
+        } else if (photo) {
+            warp_sum<5>(ph);
+        }
         float* o = ent_part + (size_t)pb.entry_slot[e] * kEntryPartial;
         float* es = reinterpret_cast<float*>(estats + e);
         if ((lane & 3) == 0) {
@@ -391,9 +424,13 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
         if (lane == 0) {
             es[2] = cnt;
             es[3] = disp;
-            if (photo)
+            if (kJoint) {
+                o[kPhotoColIc] = ph[0];
+                o[kPhotoColIc + 1] = ph[1];
+            } else if (photo) {
 #pragma unroll
                 for (int a = 0; a < 5; ++a) o[kPhotoColIc + a] = ph[a];
+            }
         }
     } else {
         float st[3] = {acc[6], acc[7], cnt};
@@ -607,7 +644,7 @@ __global__ void __launch_bounds__(kTileWarps * 32)
 point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __restrict__ Hfd,
              float* __restrict__ Hnn, float* __restrict__ gn, float* __restrict__ ent_part, int coff,
              const float4* __restrict__ estats, const float* __restrict__ ddsq_t,
-             TileStats* __restrict__ tstats)
+             TileStats* __restrict__ tstats, const float* __restrict__ Had)
 {
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     pdl_trigger();
@@ -691,6 +728,12 @@ point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __rest
 #pragma unroll
             for (int q = 0; q < 6; ++q) v[q] = vis ? (hv ? hv[q] : h[q * nvis]) * sn : 0.0f;
             v[6] = v[7] = 0.0f;
+            if (Had && vis) {
+                // joint brightness: the pair's correction sum_n H_a g_n / H_dd
+                const float* ha = Had + (size_t)po * 2 + rank_of(mask, lane);
+                v[6] = ha[0] * sn;
+                v[7] = ha[nvis] * sn;
+            }
             // sums over the lanes by reduce-scatter (nine exchanges instead
             // of thirty): at strides 16, 8, 4 a lane keeps half of its values
             // and adds its partner's copy of them, then two butterfly levels;
@@ -701,6 +744,8 @@ point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __rest
             v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
             v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
             if ((lane & 3) == 0 && lane < 24) ent_part[(size_t)sl * kEntryPartial + coff + (lane >> 2)] = v[0];
+            else if ((lane & 3) == 0 && Had)
+                ent_part[(size_t)sl * kEntryPartial + kPhotoColIc + 2 + ((lane - 24) >> 2)] = v[0];
         };
         int i = warp;
         if (!kFc) {
@@ -823,8 +868,9 @@ cudaError_t launch_depth_update(const LaunchCtx& L, const SolveArgs& a, bool ic_
     const DepthState& ds = ic_rule ? L.ds_ic : L.ds_fc;
     const int grid = L.pb.T + (apply ? L.pb.F - 1 : 0);  // + one CTA per frame's pose update
     if (ic_rule)
-        return launch_pdl(depth_update_kernel<true>, grid, kTileWarps * 32, 0, L.stream, L.pb, ds, L.fs.dth2,
-                          L.ic.inv_hnn, L.ic.inv_d0, L.it.dcur, L.it.dprev, L.it.ddsq_t, apply, a);
+        return launch_pdl(ds.Had ? depth_update_kernel<true, true> : depth_update_kernel<true, false>, grid,
+                          kTileWarps * 32, 0, L.stream, L.pb, ds, L.fs.dth2, L.ic.inv_hnn, L.ic.inv_d0, L.it.dcur,
+                          L.it.dprev, L.it.ddsq_t, apply, a);
     else
         return launch_pdl(depth_update_kernel<false>, grid, kTileWarps * 32, 0, L.stream, L.pb, ds, L.fs.dth2,
                           (const double*)nullptr, (const double*)nullptr, L.it.dcur, L.it.dprev, L.it.ddsq_t,
@@ -832,11 +878,11 @@ cudaError_t launch_depth_update(const LaunchCtx& L, const SolveArgs& a, bool ic_
     return cudaGetLastError();
 }
 
-template <int PMAX, bool A, int DT, int WARPS>
+template <int PMAX, bool A, int DT, int WARPS, bool J = false>
 static cudaError_t ic_residual_w(const LaunchCtx& L, int have_prev)
 {
     const int blocks = (L.pb.E + WARPS - 1) / WARPS;
-    return launch_pdl(ic_residual_kernel<PMAX, A, DT, WARPS>, blocks, WARPS * 32, 0, L.stream, L.pb, L.fs.fc,
+    return launch_pdl(ic_residual_kernel<PMAX, A, DT, WARPS, J>, blocks, WARPS * 32, 0, L.stream, L.pb, L.fs.fc,
                       L.fs.fc_prev, L.it.dcur, L.it.dprev, L.ic.J4, L.ent_part, L.it.gpart, L.it.estats,
                       have_prev, L.photo);
 }
@@ -846,6 +892,8 @@ static cudaError_t ic_residual_w(const LaunchCtx& L, int have_prev)
 template <int PMAX, bool A, int DT>
 static cudaError_t ic_residual_p(const LaunchCtx& L, int have_prev)
 {
+    // the brightness pairs as unknowns: their own instance, 8 warps
+    if (A && L.photo == 2) return ic_residual_w<PMAX, A, DT, kResWarps, A>(L, have_prev);
     if (A && L.res_warps == 4) return ic_residual_w<PMAX, A, DT, 4>(L, have_prev);
     if (A && L.res_warps == 16) return ic_residual_w<PMAX, A, DT, 16>(L, have_prev);
     return ic_residual_w<PMAX, A, DT, kResWarps>(L, have_prev);
@@ -896,14 +944,15 @@ cudaError_t launch_ic_point(const LaunchCtx& L, bool accum)
 {
     auto k = accum ? point_kernel<true, false> : point_kernel<false, false>;
     return launch_pdl(k, L.pb.T, kTileWarps * 32, 0, L.stream, L.pb, L.it.gpart, L.ic.Hfd, L.ic.Hnn,
-                      L.ds_ic.gn, L.ent_part, 6, L.it.estats, L.it.ddsq_t, L.tstats);
+                      L.ds_ic.gn, L.ent_part, 6, L.it.estats, L.it.ddsq_t, L.tstats,
+                      (const float*)(L.photo == 2 ? L.ic.Had : nullptr));
 }
 
 cudaError_t launch_fc_point(const LaunchCtx& L, bool accum)
 {
     auto k = accum ? point_kernel<true, true> : point_kernel<false, true>;
     return launch_pdl(k, L.pb.T, kTileWarps * 32, 0, L.stream, L.pb, L.it.gpart, L.Hfd_fc, L.ds_fc.Hnn,
-                      L.ds_fc.gn, L.ent_part, 27, L.it.estats, L.it.ddsq_t, L.tstats);
+                      L.ds_fc.gn, L.ent_part, 27, L.it.estats, L.it.ddsq_t, L.tstats, (const float*)nullptr);
 }
 
 // FP32 pass constants and previous R|t of frames [f0, f0 + nf) from their

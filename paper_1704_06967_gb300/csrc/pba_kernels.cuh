@@ -53,6 +53,7 @@ struct DepthState {
     float* gn;            // g_d of the last linearisation / pass
     float* Hnn;           // H_dd of the system in use
     const float* Hfd;     // H_fd of the system in use (compact pairs)
+    const float* Had;     // joint brightness (IC): J_d^T W_0 [I_0, 1] per pair; null otherwise
     double* dd_last;      // last applied depth update
     int* err;
 };
@@ -66,6 +67,8 @@ struct IcStore {
     double* inv_d0;   // Npad 1 / d_0
     float* part;      // E rows of kEntryPartial: the entry's 21 H_ff sums (kept for window updates)
     float* hpart;     // E * 32 per-(entry, lane) J_d^T W_0 J_d (kept for window updates)
+    float* Had;       // joint brightness: pairs * 2 (J_d^T W_0 [I_0, 1]); null otherwise
+    unsigned* vmask0; // joint brightness: pairs, pattern pixels valid at p_0
 };
 
 struct LaunchCtx {
@@ -82,7 +85,8 @@ struct LaunchCtx {
     const double* poses0;  // F*12 FP64 poses at p_0
     cudaStream_t stream;
     int res_warps;         // warps per CTA of the accumulating IC residual pass (4, 8, 16)
-    int photo;             // affine brightness fit on: the residual passes write its sums
+    int photo;             // affine brightness: 0 off, 1 moment fit (the residual passes write its
+                           // sums), 2 joint unknowns (IC: g_a sums and the Schur corrections)
 };
 
 // IC precompute of the entries of the frames with todo[f] != 0 (all when
@@ -103,6 +107,7 @@ struct BundleSet {
     const BundleDesc* bund;
     BundleDesc one;
     int n6max;  // largest 6 (F - 1) of the bundles
+    int nb;     // unknowns per frame of the factorised system (6, or 8 with the brightness pair)
 };
 
 __device__ __forceinline__ BundleDesc bundle_at(const BundleSet& s, int b)
@@ -132,6 +137,13 @@ struct SolveArgs {
                             // [F_b] their number
     const double* tanchor;  // F*12 poses whose t define the gauge direction
     const double* photo_sums;  // F*5 brightness fit sums of the step (null: model off)
+    // joint brightness unknowns (IC): the last increments (da, db) per frame
+    // (composed into the pairs by the pose-update CTAs of the next depth
+    // update), the frame sums H_pa / H_aa and the prior weight
+    double* dab64;          // F*2
+    float2* dab2;           // F*2 (hi, lo) pairs
+    const double* red_aff;  // F*kAffComp
+    double photo_prior;
 };
 
 // Affine brightness of frame f from its fit sums (w, w v, w v^2, w I_0,
@@ -237,6 +249,29 @@ int ldl_max_cluster();    // the largest cluster size ldl_setup found usable (8 
 // S^-1 over the active frames (compact nc x nc, nc = 6 cmap[F_b]) per bundle
 cudaError_t launch_ldl_inverse(const BundleSet& bs, const dfloat* L, const dfloat* Linv, const dfloat* rpiv,
                                const int* cmap, dfloat* Sinv, cudaStream_t st);
+// Joint brightness unknowns (pba_affine.cu; IC, one bundle). Sums over the
+// points of H_fd(n,f) H_a(n,g)^T / H_dd(n) (6 x 2 per frame pair, S_pa) and
+// H_a(n,f) H_a(n,g)^T / H_dd(n) (2 x 2, S_aa) as fixed-point integers (acc:
+// n6 * n2 then n2 * n2, zero on entry); the scale comes from the frame
+// sums (red_ic: 21 per frame, red_aff: 15 per frame).
+cudaError_t launch_affine_schur(const DevProblem& pb, const float* Hfd, const float* Had,
+                                const double* inv_hnn, const double* red_ic, const double* red_aff,
+                                long long* acc, int F, cudaStream_t st);
+// The factorisation's working matrix of the 8 (F - 1) system over the
+// active frames, poses first (6 per active frame, the order of S) then the
+// pairs (2 per active frame): S (FP64, assembled), H_pa and H_aa from
+// red_aff, minus the fixed-point sums of launch_affine_schur.
+cudaError_t launch_assemble_affine(const double* S, const double* red_ic, const double* red_aff,
+                                   const long long* acc, const int* cmap, int F, double damping, double prior,
+                                   dfloat* A8, cudaStream_t st);
+// Delta = -S8^-1 [y_theta; y_a] per target frame (y_a from the brightness
+// columns of the frame reduction and the prior), the gauge constraint on the
+// translations, the pose update written like launch_ic_solve and (da, db)
+cudaError_t launch_ic_solve_affine(const SolveArgs& a, const dfloat* Sinv8, const double* y,
+                                   const double* yph, cudaStream_t st);
+// once per process and device, before any capture
+cudaError_t affine_setup();
+
 // one CTA per bundle
 cudaError_t launch_fc_solve_update(const SolveArgs& a, const dfloat* L, const dfloat* Linv,
                                    cudaStream_t st);

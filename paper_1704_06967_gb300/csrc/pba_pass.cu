@@ -40,8 +40,14 @@ __device__ __forceinline__ int rank_in(unsigned mask, int lane)
 // stored rows, so H = J^T W_0 J holds for the J the iterations use. Pattern
 // pixels go in groups of four: their taps are issued together and their
 // rows are exactly seven float4 chunks, stored as soon as they are formed.
+// kAff (the brightness pairs as unknowns): the frame block gains the columns
+// I_0 and 1 (the template-side increment (1 + da) I_0 + db), so per entry
+// also H_pa (12 sums: sum w0 J_a I_0, sum w0 J_a), H_aa (sum w0 I_0^2,
+// sum w0 I_0, sum w0) and per pair J_d^T W_0 [I_0, 1] and the mask of the
+// pattern pixels valid at p_0 (the iterations' brightness gradient keeps
+// the residual set of p_0, like the stored rows).
 // ---------------------------------------------------------------------------
-template <int PMAX, int DT>
+template <int PMAX, int DT, bool kAff>
 __global__ void __launch_bounds__(kPreWarps * 32, 2)
 ic_precompute_kernel(DevProblem pb, const float* __restrict__ fconst, const double* __restrict__ d0_64,
                      const float2* __restrict__ G0p, IcStore ic, const unsigned char* __restrict__ todo)
@@ -59,9 +65,14 @@ ic_precompute_kernel(DevProblem pb, const float* __restrict__ fconst, const doub
 #pragma unroll
     for (int q = 0; q < 21; ++q) hff[q] = 0.0f;
     float hnn = 0.0f;
+    float aff[kAffComp];  // kAff: H_pa (a-major: [a][I_0, 1]), H_aa (I_0^2, I_0, 1)
+#pragma unroll
+    for (int q = 0; q < kAffComp; ++q) aff[q] = 0.0f;
     if ((en.mask >> lane) & 1u) {
         const int n = en.tile * kTile + lane;
         const int nvis = __popc(en.mask), rank = rank_in(en.mask, lane);
+        float had[2] = {0.0f, 0.0f};
+        unsigned vm = 0u;
         const float* c = fconst + (size_t)en.f * kFrameConst;
         const float d0 = (float)d0_64[n];
         const float2 xc = pb.xn[n];
@@ -153,6 +164,20 @@ ic_precompute_kernel(DevProblem pb, const float* __restrict__ fconst, const doub
                             hfd[a] = fmaf(wja, J[6], hfd[a]);
                         }
                         hnn = fmaf(w0 * J[6], J[6], hnn);
+                        if (kAff) {
+                            const float wi = w0 * I0[jj];
+#pragma unroll
+                            for (int a = 0; a < 6; ++a) {
+                                aff[2 * a] = fmaf(wi, J[a], aff[2 * a]);
+                                aff[2 * a + 1] = fmaf(w0, J[a], aff[2 * a + 1]);
+                            }
+                            aff[12] = fmaf(wi, I0[jj], aff[12]);
+                            aff[13] += wi;
+                            aff[14] += w0;
+                            had[0] = fmaf(wi, J[6], had[0]);
+                            had[1] = fmaf(w0, J[6], had[1]);
+                            vm |= 1u << j;
+                        }
                     }
 #pragma unroll
                     for (int a = 0; a < 7; ++a) Jr[7 * jj + a] = J[a];
@@ -168,6 +193,12 @@ ic_precompute_kernel(DevProblem pb, const float* __restrict__ fconst, const doub
         float* hd = ic.Hfd + (size_t)en.pair_off * 6 + rank;
 #pragma unroll
         for (int a = 0; a < 6; ++a) hd[a * nvis] = hfd[a];
+        if (kAff) {
+            float* ha = ic.Had + (size_t)en.pair_off * 2 + rank;
+            ha[0] = had[0];
+            ha[nvis] = had[1];
+            ic.vmask0[en.pair_off + rank] = vm;
+        }
     }
     hpart[(size_t)e * kTile + lane] = hnn;
     // the entry's 21 H_ff sums over the lanes by reduce-scatter (25
@@ -191,6 +222,12 @@ ic_precompute_kernel(DevProblem pb, const float* __restrict__ fconst, const doub
     float* o = ent_part + (size_t)pb.entry_slot[e] * kEntryPartial;
     if ((lane & 1) == 0) o[lane >> 1] = a[0];
     if ((lane & 3) == 0 && lane < 20) o[16 + (lane >> 2)] = b[0];
+    if (kAff) {
+        warp_sum<kAffComp>(aff);
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < kAffComp; ++q) o[kAffCol + q] = aff[q];
+    }
 }
 
 // H_dd per point (entries of its tile added in order; entries of frames
@@ -260,8 +297,12 @@ template <int PMAX, int DT>
 static cudaError_t ic_precompute_p(const LaunchCtx& L, const unsigned char* todo)
 {
     const int blocks = (L.pb.E + kPreWarps - 1) / kPreWarps;
-    ic_precompute_kernel<PMAX, DT><<<blocks, kPreWarps * 32, 0, L.stream>>>(L.pb, L.fs.fc, L.ds_ic.d0_64,
-                                                                            L.it.G0p, L.ic, todo);
+    if (L.ic.Had)
+        ic_precompute_kernel<PMAX, DT, true><<<blocks, kPreWarps * 32, 0, L.stream>>>(
+            L.pb, L.fs.fc, L.ds_ic.d0_64, L.it.G0p, L.ic, todo);
+    else
+        ic_precompute_kernel<PMAX, DT, false><<<blocks, kPreWarps * 32, 0, L.stream>>>(
+            L.pb, L.fs.fc, L.ds_ic.d0_64, L.it.G0p, L.ic, todo);
     return cudaGetLastError();
 }
 
@@ -294,6 +335,7 @@ cudaError_t launch_frame_reduce(const LaunchCtx& L, int off, int ncomp, double* 
     if (!frames || (ncomp == 6 && sub == 6 && sub_from == 0)) return PBA_R(6, 6, 0);
     if (ncomp == 21 && sub < 0) return PBA_R(21, -1, 0);
     if (ncomp == 5 && sub < 0) return PBA_R(5, -1, 0);
+    if (ncomp == kAffComp && sub < 0) return PBA_R(kAffComp, -1, 0);
     if (ncomp == 27 && sub == 27 && sub_from == 21) return PBA_R(27, 27, 21);
     return cudaErrorInvalidValue;
 #undef PBA_R

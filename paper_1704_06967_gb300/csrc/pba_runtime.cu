@@ -287,6 +287,16 @@ struct pba_ctx {
         StRow* st_rows;
         short *st_ea, *st_eb;
         long long* schur_acc;   // fixed-point S_off sums of the tensor-core path (zero between formations)
+        // joint brightness unknowns (cfg.photometric = 2, one bundle): the
+        // per-pair H_a and p_0 masks, the H_pa / H_aa frame sums, the border
+        // sums of S, and the 8 (F - 1) system's factorisation and inverse
+        float* Had;
+        unsigned* vmask0;
+        double* red_aff;
+        long long* aff_acc;
+        dfloat *A8, *L8, *Linv8, *dpiv8, *rpiv8, *Sinv8;
+        double* dab64;
+        float2* dab2;
         int *active_ic, *active_fc, *cmap_ic, *cmap_fc;
         int* err;
         double* stats;
@@ -452,6 +462,9 @@ cudaError_t d2h(pba_ctx* ctx, void* dst, const void* src, size_t bytes)
 // made one contiguous array.
 bool own_images(const pba_ctx* c) { return c->mem == PBA_MEM_HOST || c->B > 1; }
 
+// The affine brightness pairs as unknowns of the IC system (cfg.photometric = 2).
+bool joint_brightness(const pba_ctx* c) { return c->cfg.photometric == 2; }
+
 // Lays out (and optionally assigns) the workspace; returns its size.
 size_t layout(pba_ctx* c, char* base)
 {
@@ -539,6 +552,23 @@ size_t layout(pba_ctx* c, char* base)
     take(c->d.st_ea, c->st_rows.size() * 6 * sizeof(short));
     take(c->d.st_eb, c->st_rows.size() * 6 * sizeof(short));
     take(c->d.schur_acc, (size_t)c->n_so * sizeof(long long));
+    {
+        // joint brightness unknowns (zero-sized otherwise)
+        const bool jb = joint_brightness(c);
+        const size_t n8 = jb ? 8 * (F - 1) : 0, n2 = jb ? 2 * (F - 1) : 0, n6 = jb ? 6 * (F - 1) : 0;
+        take(c->d.Had, jb ? (size_t)c->V * 2 * 4 : 0);
+        take(c->d.vmask0, jb ? (size_t)c->V * 4 : 0);
+        take(c->d.red_aff, jb ? F * kAffComp * 8 : 0);
+        take(c->d.aff_acc, (n6 * n2 + n2 * n2) * sizeof(long long));
+        take(c->d.A8, (n8 + 1) * n8 * sizeof(dfloat));
+        take(c->d.L8, (n8 + 1) * n8 * sizeof(dfloat));
+        take(c->d.Linv8, (n8 + kLdlBlock - 1) / kLdlBlock * kLinvStride * sizeof(dfloat));
+        take(c->d.dpiv8, n8 * sizeof(dfloat));
+        take(c->d.rpiv8, n8 * sizeof(dfloat));
+        take(c->d.Sinv8, n8 * n8 * sizeof(dfloat));
+        take(c->d.dab64, jb ? F * 2 * 8 : 0);
+        take(c->d.dab2, jb ? F * 2 * sizeof(float2) : 0);
+    }
     take(c->d.active_ic, F * 4);
     take(c->d.active_fc, F * 4);
     take(c->d.cmap_ic, (size_t)c->n_cmap * 4);
@@ -941,9 +971,12 @@ LaunchCtx make_launch(pba_ctx* c)
     pb.valid_pt = c->d.valid_pt;
     L.fs = FrameState{c->d.fc, c->d.fc_prev, c->d.dth2, c->d.dtheta64};
     L.it = IterBufs{c->d.dcur, c->d.dprev, c->d.gpart, c->d.estats, c->d.ddsq_t, c->d.G0p};
-    L.ds_ic = DepthState{c->d.d64, c->d.d0_64, c->d.gn_ic, c->d.Hnn_ic, c->d.Hfd_ic, c->d.dd_last, c->d.err};
-    L.ds_fc = DepthState{c->d.d64, c->d.d0_64, c->d.gn_fc, c->d.Hnn_fc, c->d.Hfd_fc, c->d.dd_last, c->d.err};
-    L.ic = IcStore{c->d.J4, c->d.Hfd_ic, c->d.Hnn_ic, c->d.inv_hnn, c->d.inv_d0, c->d.ic_part, c->d.ic_hpart};
+    L.ds_ic = DepthState{c->d.d64, c->d.d0_64, c->d.gn_ic, c->d.Hnn_ic, c->d.Hfd_ic, nullptr, c->d.dd_last,
+                         c->d.err};
+    L.ds_fc = DepthState{c->d.d64, c->d.d0_64, c->d.gn_fc, c->d.Hnn_fc, c->d.Hfd_fc, nullptr, c->d.dd_last,
+                         c->d.err};
+    L.ic = IcStore{c->d.J4, c->d.Hfd_ic, c->d.Hnn_ic, c->d.inv_hnn, c->d.inv_d0, c->d.ic_part, c->d.ic_hpart,
+                   nullptr, nullptr};
     L.Hfd_fc = c->d.Hfd_fc;
     L.ent_part = c->d.ent_part;
     L.tstats = c->d.tstats;
@@ -952,7 +985,14 @@ LaunchCtx make_launch(pba_ctx* c)
     L.poses0 = c->d.poses0_64;
     L.stream = c->stream;
     L.res_warps = c->res_warps;
-    L.photo = c->cfg.photometric != 0;
+    L.photo = c->cfg.photometric;
+    if (joint_brightness(c)) {
+        L.ic.Had = c->d.Had;
+        L.ic.vmask0 = c->d.vmask0;
+        L.ds_ic.Had = c->d.Had;
+        L.pb.vmask0 = c->d.vmask0;
+        L.pb.Had = c->d.Had;
+    }
     return L;
 }
 
@@ -1031,6 +1071,12 @@ SolveArgs make_solve(pba_ctx* c)
     a.fc_prev = c->d.fc_prev;
     a.dthsq = c->d.dthsq;
     a.err = c->d.err;
+    if (joint_brightness(c)) {
+        a.dab64 = c->d.dab64;
+        a.dab2 = c->d.dab2;
+        a.red_aff = c->d.red_aff;
+        a.photo_prior = c->cfg.photo_prior;
+    }
     return a;
 }
 
@@ -1040,6 +1086,7 @@ BundleSet bundle_set(pba_ctx* c)
     bs.B = c->B;
     bs.bund = c->d.bund;
     bs.n6max = c->n6max;
+    bs.nb = 6;
     return bs;
 }
 
@@ -1178,7 +1225,9 @@ pba_status pba_create(const pba_config* cfg, pba_ctx** out)
         cfg->pattern_size > PBA_MAX_PATTERN || !cfg->pattern || cfg->n_bundles < 0 ||
         cfg->n_bundles > PBA_MAX_BUNDLES ||
         cfg->gauge_anchor_w < 0.0 || cfg->max_stats_iters < 0 || !(cfg->damping >= 0.0) ||
-        !(cfg->damping < 1e6))
+        !(cfg->damping < 1e6) || cfg->photometric < 0 || cfg->photometric > 2 ||
+        !(cfg->photo_prior >= 0.0) || !(cfg->photo_prior < 1e12) ||
+        (cfg->photometric == 2 && cfg->n_bundles > 1))
         return PBA_ERR_ARG;
     for (int j = 0; j < 2 * cfg->pattern_size; ++j)
         if (cfg->pattern[j] < -32 || cfg->pattern[j] > 32) return PBA_ERR_ARG;
@@ -1382,6 +1431,7 @@ pba_status pba_set_workspace(pba_ctx* ctx, void* dev_ptr, size_t bytes)
     CK(ldl_setup());
     CK(iter_setup());
     CK(linalg_setup());
+    if (joint_brightness(ctx)) CK(affine_setup());
     CK(schur_tc_setup());
     {
         int dev = 0;
@@ -1437,11 +1487,46 @@ pba_status precompute_core(pba_ctx* ctx, const LaunchCtx& L, const BundleSet& bs
     LAUNCH(TS_PRE, launch_assemble_S(bs, ctx->d.red_ic, 21, ctx->d.Soff, ctx->d.poses0_64, ctx->cfg.gauge_anchor_w,
                                      ctx->cfg.damping, ctx->d.S_ic, ctx->d.active_ic, ctx->stream, ctx->d.A2,
                                      ctx->d.cmap_ic));
+    if (joint_brightness(ctx)) {
+        // the border of the 8 (F - 1) system, its factorisation and inverse
+        // (the pose block S is the one assembled above)
+        const int F = ctx->F;
+        const size_t n2 = 2 * (size_t)(F - 1), n6 = 6 * (size_t)(F - 1);
+        LAUNCH(TS_PRE, launch_frame_reduce(L, 0, kAffComp, ctx->d.red_aff, -1, -1, true, -1, 0,
+                                           ctx->d.ic_part + kAffCol));
+        CK(cudaMemsetAsync(ctx->d.aff_acc, 0, (n6 * n2 + n2 * n2) * sizeof(long long), ctx->stream));
+        LAUNCH(TS_PRE, launch_affine_schur(L.pb, ctx->d.Hfd_ic, ctx->d.Had, ctx->d.inv_hnn, ctx->d.red_ic,
+                                           ctx->d.red_aff, ctx->d.aff_acc, F, ctx->stream));
+        LAUNCH(TS_PRE, launch_assemble_affine(ctx->d.S_ic, ctx->d.red_ic, ctx->d.red_aff, ctx->d.aff_acc,
+                                              ctx->d.cmap_ic, F, ctx->cfg.damping, ctx->cfg.photo_prior,
+                                              ctx->d.A8, ctx->stream));
+        BundleSet b8{};
+        b8.B = 1;
+        b8.one = ctx->bdesc[0];
+        b8.one.so = b8.one.ao = b8.one.lo = 0;
+        b8.one.po = 0;
+        b8.n6max = ctx->n6max;
+        b8.nb = 8;
+        LAUNCH(TS_PRE, launch_ldl(b8, ctx->d.A8, ctx->d.L8, ctx->d.Linv8, ctx->d.dpiv8, ctx->d.rpiv8,
+                                  ctx->d.cmap_ic, 0, ctx->d.err, ctx->stream, ctx->ldl_cluster));
+        LAUNCH(TS_PRE, launch_ldl_inverse(b8, ctx->d.L8, ctx->d.Linv8, ctx->d.rpiv8, ctx->d.cmap_ic, ctx->d.Sinv8,
+                                          ctx->stream));
+        return PBA_OK;
+    }
     LAUNCH(TS_PRE, launch_ldl(bs, ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv, ctx->d.cmap_ic, 0,
                               ctx->d.err, ctx->stream, ctx->ldl_cluster));
     LAUNCH(TS_PRE, launch_ldl_inverse(bs, ctx->d.L2, ctx->d.Linv, ctx->d.rpiv, ctx->d.cmap_ic, ctx->d.Sinv2,
                                       ctx->stream));
     return PBA_OK;
+}
+
+// The IC solve of an iteration: Dtheta = -S^-1 y, or with the brightness
+// pairs as unknowns the 8 (F - 1) system's solve and the pair update.
+cudaError_t launch_ic_solve_any(pba_ctx* ctx, const SolveArgs& sa)
+{
+    if (joint_brightness(ctx))
+        return launch_ic_solve_affine(sa, ctx->d.Sinv8, ctx->d.red_y, ctx->d.red_photo, ctx->stream);
+    return launch_ic_solve(sa, ctx->d.Sinv2, ctx->d.red_y, ctx->stream);
 }
 
 // Autotuner: with the precompute's state in place, times each candidate
@@ -1553,6 +1638,7 @@ pba_status pba_set_window(pba_ctx* ctx, int bundle, const uint8_t* in_window)
 {
     CHECK_BUNDLE();
     if (!in_window) return fail(ctx, PBA_ERR_ARG, "null window flags");
+    if (joint_brightness(ctx)) return fail(ctx, PBA_ERR_ARG, "sliding windows without the brightness unknowns");
     if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
     const BundleIn& b = ctx->bun[bundle];
     bool changed = false;
@@ -1623,7 +1709,7 @@ pba_status pba_iterate(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     sa.active = ctx->d.active_ic;
     sa.tanchor = ctx->d.poses0_64;
     sa.cmap = ctx->d.cmap_ic;
-    sa.photo_sums = ctx->cfg.photometric ? ctx->d.red_photo : nullptr;
+    sa.photo_sums = ctx->cfg.photometric == 1 ? ctx->d.red_photo : nullptr;
     pba_status s = run_enqueued(ctx, GraphKey{G_ITERATE, n_iters, ctx->timing}, [&]() -> pba_status {
         for (int k = 0; k < n_iters; ++k) {
             LAUNCH(TS_POINT, launch_depth_update(L, sa, true, k > 0));
@@ -1633,7 +1719,7 @@ pba_status pba_iterate(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
             if (ctx->cfg.photometric)
                 LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 5, ctx->d.red_photo, -1, -1, true, -1, 0,
                                                       ctx->d.ent_part + kPhotoColIc));
-            LAUNCH(TS_SOLVE, launch_ic_solve(sa, ctx->d.Sinv2, ctx->d.red_y, ctx->stream));
+            LAUNCH(TS_SOLVE, launch_ic_solve_any(ctx, sa));
         }
         LAUNCH(TS_EVAL, launch_depth_update(L, sa, true, n_iters > 0));
         LAUNCH(TS_EVAL, launch_ic_residual(L, false, n_iters > 0));
@@ -1854,7 +1940,7 @@ pba_status pba_solve_ic(pba_ctx* ctx, int n_iters, int reanchor_every, pba_iter_
     sa.active = ctx->d.active_ic;
     sa.tanchor = ctx->d.poses0_64;
     sa.cmap = ctx->d.cmap_ic;
-    sa.photo_sums = ctx->cfg.photometric ? ctx->d.red_photo : nullptr;
+    sa.photo_sums = ctx->cfg.photometric == 1 ? ctx->d.red_photo : nullptr;
     pba_status s = run_enqueued(ctx, GraphKey{G_SOLVE, n_iters | (m << 16), ctx->timing}, [&]() -> pba_status {
         pba_status q = precompute_body(ctx);
         if (q != PBA_OK) return q;
@@ -1878,7 +1964,7 @@ pba_status pba_solve_ic(pba_ctx* ctx, int n_iters, int reanchor_every, pba_iter_
             if (ctx->cfg.photometric)
                 LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 5, ctx->d.red_photo, -1, -1, true, -1, 0,
                                                       ctx->d.ent_part + kPhotoColIc));
-            LAUNCH(TS_SOLVE, launch_ic_solve(sa, ctx->d.Sinv2, ctx->d.red_y, ctx->stream));
+            LAUNCH(TS_SOLVE, launch_ic_solve_any(ctx, sa));
         }
         LAUNCH(TS_EVAL, launch_depth_update(L, sa, true, n_iters > 0));
         LAUNCH(TS_EVAL, launch_ic_residual(L, false, n_iters > 0));
@@ -1902,6 +1988,8 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
 {
     if (!ctx) return PBA_ERR_ARG;
     if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
+    if (joint_brightness(ctx))
+        return fail(ctx, PBA_ERR_ARG, "the brightness pairs as unknowns are an IC option (photometric = 2)");
     if (n_iters < 0 || n_iters > ctx->cfg.max_stats_iters)
         return fail(ctx, PBA_ERR_ARG, "n_iters must be in [0, %d]", ctx->cfg.max_stats_iters);
     LaunchCtx L = make_launch(ctx);
@@ -1910,7 +1998,7 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
     sa.active = ctx->d.active_fc;
     sa.tanchor = ctx->d.poses64;
     sa.cmap = ctx->d.cmap_fc;
-    sa.photo_sums = ctx->cfg.photometric ? ctx->d.red_photo : nullptr;
+    sa.photo_sums = ctx->cfg.photometric == 1 ? ctx->d.red_photo : nullptr;
     pba_status s = run_enqueued(ctx, GraphKey{G_FC, n_iters, ctx->timing}, [&]() -> pba_status {
         for (int k = 0; k < n_iters; ++k) {
             LAUNCH(TS_POINT, launch_depth_update(L, sa, false, k > 0));

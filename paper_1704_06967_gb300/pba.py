@@ -41,7 +41,7 @@ class Config(ctypes.Structure):
                 ("conv_px", ctypes.c_double), ("n_bundles", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("use_graphs", ctypes.c_int),
                 ("max_stats_iters", ctypes.c_int), ("autotune", ctypes.c_int), ("damping", ctypes.c_double),
-                ("photometric", ctypes.c_int)]
+                ("photometric", ctypes.c_int), ("photo_prior", ctypes.c_double)]
 
 
 class IterStats(ctypes.Structure):
@@ -126,6 +126,21 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+def _photo_mode(photometric) -> int:
+    """cfg.photometric from the binding's argument: False/0 off, True/1 or
+    "fit" the per-step moment fit, 2 or "joint" the pairs as unknowns of the
+    IC system."""
+    if isinstance(photometric, str):
+        modes = {"off": 0, "fit": 1, "joint": 2}
+        if photometric not in modes:
+            raise ValueError(f"photometric must be one of {sorted(modes)}")
+        return modes[photometric]
+    v = int(photometric)
+    if v not in (0, 1, 2):
+        raise ValueError("photometric must be 0, 1 or 2")
+    return v
+
+
 def _scene_images(scene, device_images=True):
     """A synth.Scene's image stack as a CUDA tensor (or the host array)."""
     import torch
@@ -153,7 +168,7 @@ class Batch:
     """
 
     def __init__(self, items, *, pattern, huber_k, stream=None, gauge_anchor_w=1.0, max_stats_iters=256,
-                 use_graphs=False, autotune=False, damping=0.0, photometric=False):
+                 use_graphs=False, autotune=False, damping=0.0, photometric=False, photo_prior=0.0):
         import torch
         self.torch = torch
         lib = load()
@@ -168,7 +183,8 @@ class Batch:
         cfg = Config(float(huber_k), pat.shape[0],
                      pat.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), float(gauge_anchor_w),
                      0.0, self.B, ctypes.c_void_p(stream.cuda_stream), int(bool(use_graphs)),
-                     int(max_stats_iters), int(bool(autotune)), float(damping), int(bool(photometric)))
+                     int(max_stats_iters), int(bool(autotune)), float(damping), _photo_mode(photometric),
+                     float(photo_prior))
         h = ctypes.c_void_p()
         self.h = None
         self._check(lib.pba_create(ctypes.byref(cfg), ctypes.byref(h)), None)

@@ -1,0 +1,182 @@
+"""The affine brightness pairs as unknowns of the IC system (photometric =
+"joint"; an option beyond the paper, whose Sec. 2 notes that direct methods
+must model lighting) against the oracle's or_ic_step_joint, through the C
+ABI: single steps, a short trajectory, exact recovery of known brightness
+changes, and the calls that refuse the mode."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 1e-4        # relative error of the joint step (poses and depths), as for the plain IC step
+PAIR_TOL = 1e-4        # brightness pairs after a step, relative to their largest entry
+
+_ALPHAS = np.r_[1.0, 0.75, 1.25, 0.8, 1.2, 0.9]
+_BETAS = np.r_[0.0, 0.06, -0.05, 0.04, -0.06, 0.03]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_06967_gb300 import build
+    build.build()
+    return torch
+
+
+def _relit_small():
+    sc = synth.make_scene("small")
+    imgs = sc.images_f32.astype(np.float64).copy()
+    for f in range(1, sc.F):
+        imgs[f] = (imgs[f] - _BETAS[f]) / _ALPHAS[f]
+    return sc, imgs.astype(np.float32)
+
+
+def _step_err(dth, dd, o_dth, o_dd):
+    got = np.concatenate([dth[1:].ravel(), dd])
+    ref = np.concatenate([o_dth[1:].ravel(), o_dd])
+    return np.linalg.norm(got - ref) / np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("prior", [0.0, 0.05])
+def test_joint_steps_match_oracle(torch_cuda, prior):
+    torch = torch_cuda
+    from paper_1704_06967_gb300 import Bundle
+    sc, imgs = _relit_small()
+    pb = oracle.Problem(imgs, sc.uv, sc.pattern, sc.vis, sc.intrinsics, sc.huber_k, photometric=True,
+                        photo_prior=prior)
+    b = Bundle(torch.tensor(imgs, device="cuda"), sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis,
+               pattern=sc.pattern, huber_k=sc.huber_k, photometric="joint", photo_prior=prior)
+    b.precompute_ic()
+    pre = oracle.ic_precompute(pb, sc.poses0, sc.depths0)
+    P, D = sc.poses0.copy(), sc.depths0.copy()
+    for k in range(3):
+        pb.photo[:] = b.brightness().ravel()  # FP32 on the device: give the oracle the same pairs
+        b.set_params(P, D)
+        b.iterate(1)
+        o_dth, o_dab, o_dd, P1, D1, _ = oracle.ic_step_joint(pb, pre, sc.poses0, sc.depths0, P, D)
+        dth, dd = b.last_update()
+        assert _step_err(dth, dd, o_dth, o_dd) <= STEP_TOL, k
+        got = b.brightness().ravel()
+        assert np.abs(got - pb.photo).max() <= PAIR_TOL * np.abs(pb.photo).max(), (k, got, pb.photo)
+        assert np.abs(o_dab[1:]).max() > 1e-3  # the pairs move: the test sees their update
+        P, D = P1, D1
+    b.close()
+
+
+def test_joint_trajectory_matches_oracle(torch_cuda):
+    """Ten iterations from p_0 on each side (each its own FP32 / FP64
+    trajectory): final poses, pairs and photometric RMS agree."""
+    torch = torch_cuda
+    from paper_1704_06967_gb300 import Bundle
+    sc, imgs = _relit_small()
+    pb = oracle.Problem(imgs, sc.uv, sc.pattern, sc.vis, sc.intrinsics, sc.huber_k, photometric=True)
+    Po, Do, ho = oracle.ic_run_joint(pb, sc.poses0, sc.depths0, 10)
+    b = Bundle(torch.tensor(imgs, device="cuda"), sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis,
+               pattern=sc.pattern, huber_k=sc.huber_k, photometric="joint")
+    st = b.solve_ic(10)
+    P, D = b.params()
+    ab = b.brightness()
+    b.close()
+    assert abs(st[-1, 1] - ho[-1, oracle.ST_RMS]) <= 1e-3 * ho[-1, oracle.ST_RMS], (st[-1], ho[-1])
+    assert np.abs(ab.ravel() - pb.photo).max() <= 1e-3, (ab, pb.photo)
+    assert np.abs(P[1:, 9:] - Po[1:, 9:]).max() <= 1e-3 * np.abs(Po[1:, 9:]).max()
+
+
+def test_joint_unknowns_lower_the_cost_under_relighting(torch_cuda):
+    """The relit 5-frame bundle from its 2-degree perturbation: H and W_0
+    fixed at a p_0 with the wrong brightness keep IC from settling, so the
+    solve re-anchors every 3 iterations (p_0, with the current pairs, is
+    moved to the current parameters); with the pairs as unknowns the final
+    RMS is far below the plain model's and the gains are close to the
+    relighting (the oracle's trajectory: RMS 0.021 against 0.098, largest
+    gain error 0.06)."""
+    torch = torch_cuda
+    from paper_1704_06967_gb300 import Bundle
+    sc, imgs = _relit_small()
+    rms, ab = {}, None
+    for mode in ("off", "joint"):
+        b = Bundle(torch.tensor(imgs, device="cuda"), sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis,
+                   pattern=sc.pattern, huber_k=sc.huber_k, photometric=mode)
+        rms[mode] = b.solve_ic(20, reanchor_every=3 if mode == "joint" else 0)[-1, 1]
+        if mode == "joint":
+            ab = b.brightness()
+        b.close()
+    assert rms["joint"] < 0.5 * rms["off"], rms
+    assert np.abs(ab[1:, 0] - _ALPHAS[1:]).max() < 0.15, ab
+
+
+def test_joint_step_recovers_affine_brightness(torch_cuda):
+    """Identity warp, targets that are affine images of the template: one
+    step lands on the true pairs and leaves the geometry (the exact
+    recovery the oracle is pinned to, at FP32)."""
+    torch = torch_cuda
+    from paper_1704_06967_gb300 import Bundle
+    rng = np.random.default_rng(3)
+    sc = synth.make_scene("small", noise_free=True)
+    alphas = np.r_[1.0, rng.uniform(0.7, 1.3, sc.F - 1)]
+    betas = np.r_[0.0, rng.uniform(-0.1, 0.1, sc.F - 1)]
+    I0 = sc.images_f32[0].astype(np.float64)
+    imgs = np.stack([I0] + [(I0 - betas[f]) / alphas[f] for f in range(1, sc.F)]).astype(np.float32)
+    poses = np.zeros((sc.F, 12))
+    poses[:, [0, 4, 8]] = 1.0
+    vis = np.ones((sc.N, sc.F), np.uint8)
+    b = Bundle(torch.tensor(imgs, device="cuda"), poses, sc.intrinsics, sc.uv, sc.depths_gt, vis,
+               pattern=sc.pattern, huber_k=sc.huber_k, photometric="joint")
+    b.precompute_ic()
+    b.iterate(1)
+    ab = b.brightness()
+    dth, dd = b.last_update()
+    b.close()
+    # the template-side form of the pairs: alpha I_f + beta = I_0 with
+    # I_f = (I_0 - beta) / alpha (FP32 images and sums)
+    assert np.abs(ab[1:, 0] - alphas[1:]).max() < 2e-4, (ab, alphas)
+    assert np.abs(ab[1:, 1] - betas[1:]).max() < 2e-4, (ab, betas)
+    assert np.array_equal(ab[0], [1.0, 0.0])
+    assert np.abs(dth).max() < 1e-5 and np.abs(dd).max() == 0.0
+
+
+def test_joint_mode_refusals(torch_cuda):
+    torch = torch_cuda
+    from paper_1704_06967_gb300 import Batch, Bundle, PbaError
+    sc, imgs = _relit_small()
+    t = torch.tensor(imgs, device="cuda")
+    b = Bundle(t, sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis, pattern=sc.pattern,
+               huber_k=sc.huber_k, photometric="joint")
+    with pytest.raises(PbaError):
+        b.solve_fc(1)
+    with pytest.raises(PbaError):
+        b.set_window(np.ones(sc.F, np.uint8))
+    b.close()
+    item = (t, sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis)
+    with pytest.raises(PbaError):
+        Batch([item, item], pattern=sc.pattern, huber_k=sc.huber_k, photometric="joint")
+    with pytest.raises(ValueError):
+        Bundle(t, sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis, pattern=sc.pattern,
+               huber_k=sc.huber_k, photometric=3)
+    with pytest.raises(PbaError):
+        Bundle(t, sc.poses0, sc.intrinsics, sc.uv, sc.depths0, sc.vis, pattern=sc.pattern,
+               huber_k=sc.huber_k, photometric="joint", photo_prior=-1.0)
+
+
+def test_prior_keeps_the_pairs_bounded_on_helix30(torch_cuda):
+    """helix30 from its perturbation, where IC stops short of alignment: the
+    template-side pairs drift without the prior (the oracle on a point subset:
+    gains up to 47 after 20 iterations) and stay near 1 with lambda = 0.01,
+    at the plain model's RMS."""
+    torch = torch_cuda
+    from paper_1704_06967_gb300 import Bundle
+    sc = synth.make_scene("helix30")
+    rms = {}
+    for mode, prior in (("off", 0.0), ("joint", 0.01)):
+        b = Bundle.from_scene(sc, photometric=mode, photo_prior=prior)
+        rms[mode] = b.solve_ic(20)[-1, 1]
+        if mode == "joint":
+            ab = b.brightness()
+        b.close()
+    assert np.abs(ab[1:, 0] - 1.0).max() < 0.5 and np.abs(ab[1:, 1]).max() < 0.3, ab
+    assert rms["joint"] <= 1.05 * rms["off"], rms
