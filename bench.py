@@ -95,8 +95,10 @@ def parse():
                    help="submit every kernel with its own launch instead of replaying CUDA graphs")
     p.add_argument("--bundles", type=int, default=256,
                    help="batch workload: number of bundles (default 256)")
-    p.add_argument("--train-bundles", type=int, default=48, help="learned workload: training bundles")
-    p.add_argument("--eval-bundles", type=int, default=16, help="learned workload: held-out bundles")
+    p.add_argument("--train-bundles", type=int, default=2000, help="learned workload: training bundles")
+    p.add_argument("--eval-bundles", type=int, default=64, help="learned workload: held-out bundles")
+    p.add_argument("--render", choices=("gpu", "host"), default="gpu",
+                   help="learned workload: scenes by the CUDA ray caster or the host renderer")
     p.add_argument("--epochs", type=int, default=20, help="learned workload: training epochs")
     p.add_argument("--points", type=int, default=262144, help="mlp workload: feature rows per inference")
     p.add_argument("--point-stride", type=int, default=1,
@@ -1054,17 +1056,17 @@ def run_batch(args):
 # ----------------------------------------------------------------------------
 # learned workload: depth proposal trained on the method's own solutions
 # ----------------------------------------------------------------------------
-def learned_scene(i):
+def learned_scene(i, device=None):
     """30-frame 640x480 FP16 helix bundle around a sphere (radius uniform
     0.7-1.5) on a ground plane, poses known to 0.1 deg / 0.001: the
     proposal's setting, new points of tracked frames whose depths are
-    unknown."""
+    unknown. device="cuda": rendered by the CUDA ray caster."""
     import synth
     rng = __import__("numpy").random.default_rng(synth.BATCH_SEED + 7 + i)
     cfg = synth.SceneConfig(f"learned{i}", 640, 480, 525.0, 5000, "helix", n_frames=30, spacing=1,
                             sphere_r=float(rng.uniform(0.7, 1.5)), plane=True, dtype="f16", rot_deg=0.1,
                             trans=0.001, allow_fewer_points=True)
-    return synth.make_scene(cfg, seed_offset=5000 + i)
+    return synth.make_scene(cfg, seed_offset=5000 + i, device=device)
 
 
 def _learned_scene_star(i):
@@ -1088,21 +1090,34 @@ def run_learned(args):
     pkg_build.build()
     ntr, nev, iters = args.train_bundles, args.eval_bundles, args.iters
     t0 = time.perf_counter()
-    with cf.ProcessPoolExecutor(max_workers=max(1, min(8, (os.cpu_count() or 2) // 2)),
-                                mp_context=mp.get_context("spawn")) as ex:
-        scenes = list(ex.map(_learned_scene_star, range(ntr + nev)))
-    log(f"generated {len(scenes)} bundles in {time.perf_counter() - t0:.1f} s")
-    train, held = scenes[:ntr], scenes[ntr:]
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     Xs, Ts = [], []
-    for sc in train:
+
+    def add_pairs(sc):
         tp = training_pairs(sc, iters=iters, stream=stream)
-        if tp is None:
-            continue
-        X, d, use = tp
-        Xs.append(X[torch.tensor(use, device="cuda")])
-        Ts.append(torch.tensor(d[use], dtype=torch.float32, device="cuda"))
+        if tp is not None:
+            X, d, use = tp
+            Xs.append(X[torch.tensor(use, device="cuda")])
+            Ts.append(torch.tensor(d[use], dtype=torch.float32, device="cuda"))
+
+    if args.render == "gpu":
+        # rendered on the device one bundle at a time (the CUDA ray caster);
+        # each training bundle is solved and dropped
+        import synth
+        synth.build_renderer_gpu()
+        for i in range(ntr):
+            add_pairs(learned_scene(i, device="cuda"))
+        held = [learned_scene(i, device="cuda") for i in range(ntr, ntr + nev)]
+    else:
+        with cf.ProcessPoolExecutor(max_workers=max(1, min(8, (os.cpu_count() or 2) // 2)),
+                                    mp_context=mp.get_context("spawn")) as ex:
+            scenes = list(ex.map(_learned_scene_star, range(ntr + nev)))
+        held = scenes[ntr:]
+        for sc in scenes[:ntr]:
+            add_pairs(sc)
+    gen_s = time.perf_counter() - t0
+    log(f"generated and solved {ntr + nev} bundles ({args.render} rendering) in {gen_s:.1f} s")
     X, T = torch.cat(Xs).contiguous(), torch.cat(Ts).contiguous()
     net = DepthMLP(seed=0, stream=stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1174,7 +1189,10 @@ def run_learned(args):
                                   f"poses known to 0.1 deg / 0.001), targets from {iters} IC iterations, "
                                   f"{args.epochs} epochs of Adam (batch 1024, lr 2e-3); held-out solves: IC "
                                   f"with damping 0.01, re-anchored every 3 iterations",
-                      "training_samples": int(X.shape[0])},
+                      "training_samples": int(X.shape[0]),
+                      "scene_generation": {"renderer": "CUDA ray caster (synth/render_gpu.cu)" if args.render == "gpu"
+                                           else "host renderer (synth/render.c)",
+                                           "seconds_with_training_solves": gen_s}},
            "held_out": {"energy_constant": [r["constant"][0] for r in rows],
                         "energy_proposal": [r["proposal"][0] for r in rows],
                         "valid_residuals_constant": [r["constant"][5] for r in rows],

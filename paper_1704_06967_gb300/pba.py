@@ -144,9 +144,14 @@ def _photo_mode(photometric) -> int:
 def _scene_images(scene, device_images=True):
     """A synth.Scene's image stack as a CUDA tensor (or the host array)."""
     import torch
-    if not device_images:
-        return scene.images_store
     store = scene.images_store
+    if isinstance(store, torch.Tensor):  # rendered on the device (synth.make_scene(device="cuda"))
+        if device_images:
+            return store.contiguous()
+        return store.view(torch.int16).cpu().numpy().view(np.uint16) if store.dtype == torch.bfloat16 \
+            else store.cpu().numpy()
+    if not device_images:
+        return store
     if scene.dtype == "bf16":
         t = torch.from_numpy(store.view(np.int16)).cuda().view(torch.bfloat16)
     else:

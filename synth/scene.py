@@ -46,8 +46,11 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "render.c")
 _LIB = os.path.join(_HERE, "librender.so")
+_SRC_GPU = os.path.join(_HERE, "render_gpu.cu")
+_LIB_GPU = os.path.join(_HERE, "librender_gpu.so")
 _lock = threading.Lock()
 _lib = None
+_lib_gpu = None
 
 # 8-pixel pattern around each point; the point's own pixel is not part of it.
 PATTERN8 = np.array([(-1, -1), (1, -1), (-1, 1), (1, 1), (-2, 0), (2, 0), (0, -2), (0, 2)],
@@ -62,10 +65,40 @@ def build_renderer(force: bool = False) -> str:
         stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
         if force or stale:
             tmp = _LIB + f".tmp{os.getpid()}"
+            # no multiply-add contraction: the same images on x86 and Arm,
+            # and bit for bit those of the CUDA renderer
             subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c99",
-                                   _SRC, "-o", tmp, "-lm"])
+                                   "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
             os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_renderer_gpu(force: bool = False) -> str:
+    """Compile render_gpu.cu into librender_gpu.so (nvcc, sm_103a, no
+    multiply-add contraction) if missing or stale."""
+    import shutil
+    with _lock:
+        stale = (not os.path.exists(_LIB_GPU)) or os.path.getmtime(_LIB_GPU) < os.path.getmtime(_SRC_GPU)
+        if force or stale:
+            nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+            tmp = _LIB_GPU + f".tmp{os.getpid()}"
+            subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-fmad=false",
+                                   "-lineinfo", "-shared", "-Xcompiler", "-fPIC", _SRC_GPU, "-o", tmp])
+            os.replace(tmp, _LIB_GPU)
+    return _LIB_GPU
+
+
+def _renderer_gpu():
+    global _lib_gpu
+    if _lib_gpu is None:
+        build_renderer_gpu()
+        lib = ctypes.CDLL(_LIB_GPU)
+        d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+        lib.synth_render_gpu.argtypes = [i, i, i, i, d, d, d, d, vp, d, i, vp, d, i, ctypes.c_uint64, d, vp, vp,
+                                         vp]
+        lib.synth_render_gpu.restype = i
+        _lib_gpu = lib
+    return _lib_gpu
 
 
 def _renderer():
@@ -309,9 +342,33 @@ def _select_points(I0: np.ndarray, hit: np.ndarray, pattern: np.ndarray, n: int,
     return np.array(pts, dtype=np.int32)
 
 
-def make_scene(name_or_cfg, seed_offset: int = 0, noise_free: bool = False,
+def _render_frames_gpu(cfg, W, H, fx, fy, cx, cy, Rw, centres, rects, sphere_r, base_freq, tex_seed):
+    """Every frame by the CUDA renderer (the same images as synth_render):
+    a float32 torch tensor [F, H, W] on the current CUDA device and frame
+    0's object ids (host)."""
+    import torch
+    F = centres.shape[0]
+    RC = torch.tensor(np.concatenate([Rw.reshape(F, 9), centres], axis=1), dtype=torch.float64, device="cuda")
+    out = torch.empty((F, H, W), dtype=torch.float32, device="cuda")
+    hit = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    rc = _renderer_gpu().synth_render_gpu(F, W, H, cfg.ss, fx, fy, cx, cy, RC.data_ptr(), sphere_r,
+                                          rects.shape[0], rects.ctypes.data, base_freq, cfg.octaves, tex_seed,
+                                          0.5, out.data_ptr(), hit.data_ptr(), ctypes.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise RuntimeError(f"synth_render_gpu failed ({rc})")
+    return out, hit.cpu().numpy()
+
+
+def make_scene(name_or_cfg, seed_offset: int = 0, noise_free: bool = False, device: str | None = None,
                **overrides) -> Scene:
-    """Generate a bundle. `overrides` replace SceneConfig fields."""
+    """Generate a bundle. `overrides` replace SceneConfig fields.
+
+    device="cuda": the frames are rendered by the CUDA ray caster (the same
+    noise-free images as the host renderer, bit for bit), the image noise is
+    drawn on the device (torch's Philox generator seeded like the host's
+    NOISE_SEED + seed_offset: other values than the host path's) and the
+    scene's images_f32 / images_store are torch tensors on the device."""
     cfg = CONFIGS[name_or_cfg] if isinstance(name_or_cfg, str) else name_or_cfg
     if overrides:
         cfg = dataclasses.replace(cfg, **overrides)
@@ -329,6 +386,9 @@ def make_scene(name_or_cfg, seed_offset: int = 0, noise_free: bool = False,
     sphere_r = cfg.sphere_r
     tex_seed = SCENE_SEED + seed_offset
 
+    if device is not None:
+        return _finish_scene_gpu(cfg, seed_offset, noise_free, W, H, fx, fy, cx, cy, centres, Rw, rects,
+                                 near, base_freq, sphere_r, tex_seed, lib)
     images = np.empty((F, H, W), np.float32)
     hit0 = np.empty((H, W), np.uint8)
     for f in range(F):
@@ -355,10 +415,44 @@ def make_scene(name_or_cfg, seed_offset: int = 0, noise_free: bool = False,
     else:
         raise ValueError(cfg.dtype)
 
+    return _geometry(cfg, seed_offset, W, H, fx, fy, cx, cy, centres, Rw, rects, sphere_r, lib,
+                     deq[0], hit0, np.ascontiguousarray(deq, dtype=np.float32), np.ascontiguousarray(store))
+
+
+def _finish_scene_gpu(cfg, seed_offset, noise_free, W, H, fx, fy, cx, cy, centres, Rw, rects, near, base_freq,
+                      sphere_r, tex_seed, lib):
+    import torch
+    images, hit0 = _render_frames_gpu(cfg, W, H, fx, fy, cx, cy, Rw, centres, rects, sphere_r, base_freq,
+                                      tex_seed)
+    if not noise_free and cfg.noise > 0:
+        g = torch.Generator(device=images.device)
+        g.manual_seed(NOISE_SEED + seed_offset)
+        images = images + cfg.noise * torch.randn(images.shape, generator=g, device=images.device,
+                                                  dtype=torch.float32)
+    if cfg.dtype == "f32":
+        store = images
+    elif cfg.dtype == "f16":
+        store = images.half()
+    elif cfg.dtype == "bf16":
+        store = images.bfloat16()  # round to nearest even, as bf16_round
+    else:
+        raise ValueError(cfg.dtype)
+    deq = store.float()
+    return _geometry(cfg, seed_offset, W, H, fx, fy, cx, cy, centres, Rw, rects, sphere_r, lib,
+                     deq[0].cpu().numpy(), hit0, deq.contiguous(), store.contiguous())
+
+
+def _geometry(cfg, seed_offset, W, H, fx, fy, cx, cy, centres, Rw, rects, sphere_r, lib, deq0, hit0,
+              images_f32, images_store) -> Scene:
+    """Points, ground truth, perturbation and visibility of a rendered
+    bundle (frame 0's dequantised image deq0 and object ids hit0)."""
+    F = centres.shape[0]
+    n_rects = rects.shape[0]
+    rects_p = _dp(rects)
     pattern = PATTERN8.copy()
     prad = int(np.abs(pattern).max())
     border = prad + 2 + int(math.ceil(cfg.margin_px))
-    uv = _select_points(deq[0], hit0, pattern, cfg.n_points, cfg.spacing, border, cfg.edge_px,
+    uv = _select_points(deq0, hit0, pattern, cfg.n_points, cfg.spacing, border, cfg.edge_px,
                         cfg.allow_fewer_points)
     N = uv.shape[0]
 
@@ -437,8 +531,8 @@ def make_scene(name_or_cfg, seed_offset: int = 0, noise_free: bool = False,
         return out
 
     return Scene(cfg=cfg, W=W, H=H, fx=fx, fy=fy, cx=cx, cy=cy,
-                 images_f32=np.ascontiguousarray(deq, dtype=np.float32),
-                 images_store=np.ascontiguousarray(store), dtype=cfg.dtype,
+                 images_f32=images_f32,
+                 images_store=images_store, dtype=cfg.dtype,
                  pattern=pattern, uv=uv, vis=vis,
                  poses_gt=pack(Rrel, trel), depths_gt=d_gt,
                  poses0=pack(R0p, t0p), depths0=d0, huber_k=cfg.huber_k)
