@@ -91,6 +91,8 @@ def _L():
             "or_photo_update": ([pp, vp, vp], None),
             "or_photo_compose": ([vp, vp, vp], None),
             "or_ic_step_joint": ([pp, ctypes.POINTER(_IcPre), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], i),
+            "or_fc_residual_joint": ([pp, vp, vp, i, i, i, vp, vp], i),
+            "or_fc_step_joint": ([pp, vp, vp, vp, vp, vp, vp, vp, vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -337,6 +339,31 @@ def ic_run_joint(pb: Problem, poses0, depths0, iters: int):
         _, _, _, poses, depths, hist[k] = ic_step_joint(pb, pre, poses0, depths0, poses, depths)
     hist[iters] = evaluate(pb, poses, depths)
     return poses, depths, hist
+
+
+def fc_residual_joint(pb: Problem, poses, depths, n, f, j):
+    """FC residual with the brightness columns: (J [9]: pose 6, -v, -1,
+    depth; r; valid)."""
+    poses, depths = _f64(poses), _f64(depths)
+    J, r = np.empty(9), np.empty(1)
+    ok = _L().or_fc_residual_joint(pb.ref(), _p(poses), _p(depths), n, f, j, _p(J), _p(r))
+    return J, float(r[0]), bool(ok)
+
+
+def fc_step_joint(pb: Problem, poses, depths):
+    """One FC iteration with the brightness pairs (pb.photo, updated in
+    place) as unknowns; returns (dtheta [F,6], dab [F,2], dd [N], poses',
+    depths', stats)."""
+    if pb.photo is None:
+        raise ValueError("the joint brightness step needs a problem with photometric=True")
+    poses, depths = _f64(poses), _f64(depths)
+    dtheta, dab, dd = np.zeros(6 * pb.F), np.zeros(2 * pb.F), np.zeros(pb.N)
+    po, do, stats = np.empty_like(poses), np.empty_like(depths), np.zeros(N_STATS)
+    st = _L().or_fc_step_joint(pb.ref(), _p(poses), _p(depths), _p(dtheta), _p(dab), _p(dd), _p(po), _p(do),
+                               _p(stats))
+    if st != 0:
+        raise np.linalg.LinAlgError("reduced camera system not positive definite")
+    return dtheta.reshape(pb.F, 6), dab.reshape(pb.F, 2), dd, po, do, stats
 
 
 def fc_linearize(pb: Problem, poses, depths):

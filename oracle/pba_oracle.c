@@ -1082,6 +1082,102 @@ int or_fc_step(const or_problem* pb, const double* poses, const double* depths, 
     return st;
 }
 
+/* FC with the brightness pairs as unknowns (an option beyond the paper): the
+ * residual r = I_0 - (alpha_f v + beta_f), v = I_f(W(x; p)), is linearised at
+ * the current parameters in all of them, so the frame block's two new
+ * columns are dr/dalpha = -v and dr/dbeta = -1 and the pairs are updated
+ * additively. Jrow (9): [dr/d(upsilon, omega) (6), -v, -1, dr/dd]. */
+int or_fc_residual_joint(const or_problem* pb, const double* poses, const double* depths, int n, int f,
+                         int j, double* Jrow, double* r)
+{
+    double J7[7], u[2], q[3], v = 0.0;
+    const double* R = poses + 12 * f;
+    for (int k = 0; k < 9; ++k) Jrow[k] = 0.0;
+    if (!or_fc_residual(pb, poses, depths, n, f, j, J7, r)) return 0;
+    residual_at(pb, n, f, j, R, R + 9, depths[n], r, u, q);
+    or_bilinear(frame_img(pb, f), pb->W, pb->H, u[0], u[1], &v);
+    for (int k = 0; k < 6; ++k) Jrow[k] = J7[k];
+    Jrow[6] = -v;
+    Jrow[7] = -1.0;
+    Jrow[8] = J7[6];
+    return 1;
+}
+
+/* One FC iteration with the pairs pb->photo as unknowns: H = J^T W J and
+ * g = J^T W r over the 8-parameter frame blocks at the current parameters,
+ * the 8 (F - 1) Schur solve (or_schur_solve's gauge and damping), the
+ * boxplus pose update, d <- d + dd and (alpha, beta) += (da, db). dtheta:
+ * F*6, dab: F*2. (No prior: or_ic_step_joint's prior belongs to the IC
+ * form.) */
+int or_fc_step_joint(const or_problem* pb, const double* poses, const double* depths, double* dtheta,
+                     double* dab, double* dd, double* poses_out, double* depths_out, double* stats)
+{
+    int F = pb->F, N = pb->N, P = pb->P;
+    if (!pb->photo || F < 2) return OR_ERR_NOT_PD;
+    double* Hff = (double*)calloc((size_t)64 * F, sizeof(double));
+    double* Hfd = (double*)calloc((size_t)8 * N * F, sizeof(double));
+    double* Hdd = (double*)calloc(N, sizeof(double));
+    double* g8 = (double*)calloc((size_t)8 * F, sizeof(double));
+    double* g_d = (double*)calloc(N, sizeof(double));
+    double* d8 = (double*)calloc((size_t)8 * F, sizeof(double));
+    double* t_anchor = (double*)malloc(sizeof(double) * 3 * F);
+    double energy = 0.0, sq = 0.0, cnt = 0.0;
+    for (int n = 0; n < N; ++n) {
+        for (int f = 1; f < F; ++f) {
+            if (!pb->vis[(size_t)n * F + f]) continue;
+            for (int j = 0; j < P; ++j) {
+                double J[9], r;
+                if (!or_fc_residual_joint(pb, poses, depths, n, f, j, J, &r)) continue;
+                const double w = or_huber_weight(r, pb->huber_k);
+                energy += or_huber_rho(r, pb->huber_k);
+                sq += r * r;
+                cnt += 1.0;
+                double* hff = Hff + 64 * f;
+                double* hfd = Hfd + 8 * ((size_t)n * F + f);
+                for (int a = 0; a < 8; ++a) {
+                    for (int b = 0; b < 8; ++b) hff[8 * a + b] += w * (J[a] * J[b]);
+                    hfd[a] += w * J[a] * J[8];
+                    g8[8 * f + a] += w * J[a] * r;
+                }
+                Hdd[n] += w * J[8] * J[8];
+                g_d[n] += w * J[8] * r;
+            }
+        }
+    }
+    stats[ST_ENERGY] = energy;
+    stats[ST_RMS] = cnt > 0 ? sqrt(sq / cnt) : 0.0;
+    stats[ST_COUNT] = cnt;
+    for (int f = 0; f < F; ++f)
+        for (int i = 0; i < 3; ++i) t_anchor[3 * f + i] = poses[12 * f + 9 + i];
+    int st = schur_solve_nb(8, F, N, Hff, Hfd, Hdd, g8, g_d, t_anchor, pb->damping, d8, dd);
+    if (st == OR_OK) {
+        for (int f = 0; f < F; ++f) {
+            for (int a = 0; a < 6; ++a) dtheta[6 * f + a] = d8[8 * f + a];
+            dab[2 * f] = d8[8 * f + 6];
+            dab[2 * f + 1] = d8[8 * f + 7];
+        }
+        or_fc_update(F, N, poses, depths, dtheta, dd, poses_out, depths_out);
+        stats[ST_MAXDISP] = or_max_reproj_disp(pb, poses, depths, poses_out, depths_out);
+        for (int f = 1; f < F; ++f) {
+            pb->photo[2 * f] += dab[2 * f];
+            pb->photo[2 * f + 1] += dab[2 * f + 1];
+        }
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < 6 * F; ++i) a += dtheta[i] * dtheta[i];
+        for (int n = 0; n < N; ++n) b += dd[n] * dd[n];
+        stats[ST_DTHETA] = sqrt(a);
+        stats[ST_DD] = sqrt(b);
+    }
+    free(Hff);
+    free(Hfd);
+    free(Hdd);
+    free(g8);
+    free(g_d);
+    free(d8);
+    free(t_anchor);
+    return st;
+}
+
 /* Residual statistics only (energy, RMS, count) at a parameter set. */
 void or_eval(const or_problem* pb, const double* poses, const double* depths, double* stats)
 {

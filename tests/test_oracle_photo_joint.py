@@ -171,3 +171,90 @@ def test_prior_step_is_the_dense_minimiser_with_the_prior_rows():
     _, dab0, _, _, _, _ = oracle.ic_step_joint(pb0, pre0, poses, d, poses, d)
     assert np.abs(dab0 - dab).max() > 1e-2
     assert np.abs(pb0.photo.reshape(F, 2)[1:] - np.c_[alphas, betas][1:]).max() < 1e-9
+
+
+# ----------------------------------------------------------------------------
+# FC with the pairs as unknowns (or_fc_step_joint): target-side columns
+# -I_f and -1 at the current parameters, additive pair update
+# ----------------------------------------------------------------------------
+def _relit_tiny(seed=5):
+    sc = synth.make_scene("tiny")
+    rng = np.random.default_rng(seed)
+    alphas = np.r_[1.0, rng.uniform(0.8, 1.2, sc.F - 1)]
+    betas = np.r_[0.0, rng.uniform(-0.05, 0.05, sc.F - 1)]
+    imgs = sc.images_f32.astype(np.float64).copy()
+    for f in range(1, sc.F):
+        imgs[f] = (imgs[f] - betas[f]) / alphas[f]
+    return sc, imgs
+
+
+def test_fc_joint_columns_are_finite_differences_of_the_residual():
+    sc, imgs = _relit_tiny()
+    pb = oracle.Problem(imgs, sc.uv, sc.pattern, sc.vis, sc.intrinsics, sc.huber_k, photometric=True)
+    pb.photo[2:] = np.c_[np.linspace(0.9, 1.1, sc.F - 1), np.linspace(-0.02, 0.03, sc.F - 1)].ravel()
+    P, D = sc.poses0, sc.depths0
+    checked = 0
+    for n in range(0, sc.N, 7):
+        for f in range(1, sc.F):
+            if not sc.vis[n, f]:
+                continue
+            J, r, ok = oracle.fc_residual_joint(pb, P, D, n, f, 3)
+            if not ok:
+                continue
+            for k, idx in ((6, 2 * f), (7, 2 * f + 1)):
+                h = 1e-6
+                keep = pb.photo[idx]
+                pb.photo[idx] = keep + h
+                rp = oracle.fc_residual_joint(pb, P, D, n, f, 3)[1]
+                pb.photo[idx] = keep - h
+                rm = oracle.fc_residual_joint(pb, P, D, n, f, 3)[1]
+                pb.photo[idx] = keep
+                assert abs((rp - rm) / (2 * h) - J[k]) <= 1e-7, (n, f, k)
+            # (the pose and depth columns use the central-difference image
+            # gradient, pinned with or_fc_residual; they are not the
+            # derivative of the bilinear sample)
+            assert np.array_equal(J[[0, 1, 2, 3, 4, 5, 8]], oracle.fc_residual(pb, P, D, n, f, 3)[0])
+            checked += 1
+    assert checked > 20
+
+
+def test_fc_joint_step_recovers_affine_brightness_exactly():
+    rng = np.random.default_rng(7)
+    F = synth.make_scene("small", noise_free=True).F
+    alphas = np.r_[1.0, rng.uniform(0.7, 1.3, F - 1)]
+    betas = np.r_[0.0, rng.uniform(-0.1, 0.1, F - 1)]
+    sc, pb, poses = _identity_warp_problem(alphas, betas)
+    d = sc.depths_gt
+    dth, dab, dd, _, _, _ = oracle.fc_step_joint(pb, poses, d)
+    got = pb.photo.reshape(F, 2)
+    assert np.abs(got[1:, 0] - alphas[1:]).max() < 1e-9, (got, alphas)
+    assert np.abs(got[1:, 1] - betas[1:]).max() < 1e-9, (got, betas)
+    assert np.abs(dth).max() < 1e-9 and np.abs(dd).max() == 0.0
+
+
+def test_fc_joint_step_is_the_dense_least_squares_minimiser():
+    sc, imgs = _relit_tiny()
+    pb = oracle.Problem(imgs, sc.uv, sc.pattern, sc.vis, sc.intrinsics, sc.huber_k, photometric=True)
+    P, D = sc.poses0, sc.depths0
+    F, N = pb.F, pb.N
+    nf = 8 * (F - 1)
+    rows, rhs = [], []
+    for n in range(N):
+        for f in range(1, F):
+            if not pb.vis[n, f]:
+                continue
+            for j in range(pb.P):
+                J, r, ok = oracle.fc_residual_joint(pb, P, D, n, f, j)
+                if not ok:
+                    continue
+                w = oracle.huber_weight(r, pb.huber_k)
+                row = np.zeros(nf + N)
+                row[8 * (f - 1):8 * f] = J[:8]
+                row[nf + n] = J[8]
+                rows.append(np.sqrt(w) * row)
+                rhs.append(-np.sqrt(w) * r)
+    x = np.linalg.lstsq(np.array(rows), np.array(rhs), rcond=None)[0]
+    dense = x[:nf].reshape(F - 1, 8)
+    dth, dab, _, _, _, _ = oracle.fc_step_joint(pb, P, D)
+    assert np.abs(dth[1:, 3:] - dense[:, 3:6]).max() <= 1e-6 * np.abs(dense[:, 3:6]).max()
+    assert np.abs(dab[1:] - dense[:, 6:]).max() <= 1e-6 * np.abs(dense[:, 6:]).max()
