@@ -118,16 +118,18 @@ typedef struct {
                                 that step's residuals so that the warped samples take the
                                 template's Huber-weighted mean and spread (alpha =
                                 sqrt(var I_0 / var v), beta = mean I_0 - alpha mean v).
-                                2: the pairs are unknowns of the IC Gauss-Newton system:
-                                the template-side increment (1 + da) I_0 + db adds the
-                                fixed columns I_0 and 1 to each frame block (8 x 8 blocks,
-                                an 8 (F - 1) reduced system formed and inverted once at
-                                p_0 with the rest of the IC system, Sec. 3.5), and a
-                                step composes alpha' = alpha / (1 + da), beta' = (beta -
-                                db) / (1 + da). One bundle per context; IC only
-                                (pba_solve_fc, pba_set_window and the sharded steps
-                                return PBA_ERR_ARG). Other values: PBA_ERR_ARG. */
-    double photo_prior;      /* photometric = 2: weight lambda >= 0 of a prior that pulls
+                                2: the pairs are unknowns of the Gauss-Newton system
+                                (8 x 8 frame blocks, an 8 (F - 1) reduced system). IC: the
+                                template-side increment (1 + da) I_0 + db adds the fixed
+                                columns I_0 and 1, formed and inverted once at p_0 with
+                                the rest of the IC system (Sec. 3.5), and a step composes
+                                alpha' = alpha / (1 + da), beta' = (beta - db) / (1 +
+                                da). FC: the columns -I_f and -1 at the current
+                                parameters, every iteration, and (alpha, beta) += (da,
+                                db). One bundle per context (pba_set_window and the
+                                sharded steps return PBA_ERR_ARG). Other values:
+                                PBA_ERR_ARG. */
+    double photo_prior;      /* photometric = 2, IC: weight lambda >= 0 of a prior that pulls
                                 the pairs toward (1, 0), lambda W_f ((ln alpha_f)^2 +
                                 beta_f^2) / 2 with W_f the sum of the frame's Huber
                                 weights at p_0 (fixed with the IC system: lambda W_f on

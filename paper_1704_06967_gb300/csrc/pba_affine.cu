@@ -1,6 +1,9 @@
-// Affine brightness pairs as unknowns of the IC Gauss-Newton system (an
-// option beyond the paper, whose Sec. 2 notes that direct methods must model
-// lighting; cfg.photometric = 2, one bundle per context).
+// Affine brightness pairs as unknowns of the Gauss-Newton system (an option
+// beyond the paper, whose Sec. 2 notes that direct methods must model
+// lighting; cfg.photometric = 2, one bundle per context). IC and FC share
+// the border formation and the 8 (F - 1) assembly below; FC's columns are
+// -I_f and -1 at the current parameters, re-formed every iteration, and its
+// pairs are updated additively.
 //
 // Each target frame's block gains (da, db): the template-side increment
 // (1 + da) I_0 + db, whose Jacobian columns I_0 and 1 are fixed like the
@@ -20,6 +23,7 @@
 // -lambda W_f (ln alpha, beta) to its gradient.
 #include <algorithm>
 
+#include "pba_chol.cuh"
 #include "pba_kernels.cuh"
 #include "pba_pose.cuh"
 #include "pba_reduce.cuh"
@@ -41,11 +45,11 @@ __device__ __forceinline__ int lane_rank(unsigned mask, int lane)
 // least the frame's share), so by m = the largest diagonal entry of the
 // frame blocks; the sums are kept as integers of 2^(58 - e) units, 2^e > m.
 // Every caller computes the same value from the same frame sums.
-__device__ inline double affine_scale(const double* red_ic, const double* red_aff, int F)
+__device__ inline double affine_scale(const double* red_ff, int ff_stride, const double* red_aff, int F)
 {
     double m = 0.0;
     for (int f = 1; f < F; ++f) {
-        for (int a = 0; a < 6; ++a) m = fmax(m, red_ic[(size_t)f * 21 + a * 6 - a * (a - 1) / 2]);
+        for (int a = 0; a < 6; ++a) m = fmax(m, red_ff[(size_t)f * ff_stride + a * 6 - a * (a - 1) / 2]);
         m = fmax(m, red_aff[(size_t)f * kAffComp + 12]);
         m = fmax(m, red_aff[(size_t)f * kAffComp + 14]);
     }
@@ -63,12 +67,12 @@ __device__ inline double affine_scale(const double* red_ic, const double* red_af
 // so the result is the same run to run).
 __global__ void __launch_bounds__(kAffWarps * 32)
 affine_schur_kernel(DevProblem pb, const float* __restrict__ Hfd, const float* __restrict__ Had,
-                    const double* __restrict__ inv_hnn, const double* __restrict__ red_ic,
+                    const float* __restrict__ Hnn, const double* __restrict__ red_ff, int ff_stride,
                     const double* __restrict__ red_aff, long long* __restrict__ acc, int F)
 {
     __shared__ double s_scale;
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_scale = affine_scale(red_ic, red_aff, F);
+    if (threadIdx.x == 0) s_scale = affine_scale(red_ff, ff_stride, red_aff, F);
     __syncthreads();
     const double scale = s_scale;
     if (scale == 0.0 || t >= pb.T) return;
@@ -77,7 +81,9 @@ affine_schur_kernel(DevProblem pb, const float* __restrict__ Hfd, const float* _
     unsigned long long* aa = pa + (size_t)n6 * n2;
     const int e0 = pb.tile_entry[t], e1 = pb.tile_entry[t + 1];
     const int n = t * kTile + lane;
-    const float ih = (float)inv_hnn[n];
+    // 1 / H_dd of the solved system (H_dd = 0: a point without residuals)
+    const float hn = Hnn[n];
+    const float ih = hn > 0.0f ? 1.0f / (hn * pb.damp1) : 0.0f;
     for (int i = e0 + warp; i < e1; i += kAffWarps) {
         const Entry ei = pb.entries[i];
         const bool vi = (ei.mask >> lane) & 1u;
@@ -120,17 +126,18 @@ affine_schur_kernel(DevProblem pb, const float* __restrict__ Hfd, const float* _
 // assembled S over the active frames (compact order, as the 6 (F - 1)
 // system's working copy), then the pair rows; grid-stride over elements.
 __global__ void __launch_bounds__(256)
-assemble_affine_kernel(const double* __restrict__ S, const double* __restrict__ red_ic,
+assemble_affine_kernel(const double* __restrict__ S, const double* __restrict__ red_ff, int ff_stride,
                        const double* __restrict__ red_aff, const long long* __restrict__ acc,
                        const int* __restrict__ cmap, int F, double damping, double prior,
-                       dfloat* __restrict__ A8)
+                       dfloat* __restrict__ A8, const double* __restrict__ rhs, int rhs_stride, int rhs_off,
+                       const double* __restrict__ yph)
 {
     __shared__ int frame_of[1024];
     __shared__ double s_scale;
     const int nact = cmap[F], n6 = 6 * (F - 1), n2 = 2 * (F - 1), nc = 8 * nact, np = 6 * nact;
     for (int f = 1 + threadIdx.x; f < F; f += blockDim.x)
         if (cmap[f] >= 0) frame_of[cmap[f]] = f;
-    if (threadIdx.x == 0) s_scale = affine_scale(red_ic, red_aff, F);
+    if (threadIdx.x == 0) s_scale = affine_scale(red_ff, ff_stride, red_aff, F);
     __syncthreads();
     const double inv = s_scale > 0.0 ? 1.0 / s_scale : 0.0;  // a power of two: exact
     const long long* pa = acc;
@@ -163,6 +170,18 @@ assemble_affine_kernel(const double* __restrict__ S, const double* __restrict__ 
         }
         A8[idx] = df_from_double(v);
     }
+    // FC: augmented row nc, b = -[y_theta; y_a], eliminated with the matrix
+    if (rhs)
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nc; j += gridDim.x * blockDim.x) {
+            double y;
+            if (j < np) {
+                y = rhs[(size_t)frame_of[j / 6] * rhs_stride + rhs_off + j % 6];
+            } else {
+                const int g = frame_of[(j - np) / 2], b = (j - np) % 2;
+                y = yph[(size_t)g * 5 + b] - yph[(size_t)g * 5 + 2 + b];
+            }
+            A8[(size_t)nc * nc + j] = df_from_double(-y);
+        }
 }
 
 // One CTA per target frame (one bundle): warps 0-5 its pose rows of S8^-1,
@@ -253,23 +272,96 @@ ic_solve_affine_kernel(SolveArgs a, const dfloat* __restrict__ Sinv, const doubl
     }
 }
 
-cudaError_t launch_affine_schur(const DevProblem& pb, const float* Hfd, const float* Had, const double* inv_hnn,
-                                const double* red_ic, const double* red_aff, long long* acc, int F,
-                                cudaStream_t st)
+cudaError_t launch_affine_schur(const DevProblem& pb, const float* Hfd, const float* Had, const float* Hnn,
+                                const double* red_ff, int ff_stride, const double* red_aff, long long* acc,
+                                int F, cudaStream_t st)
 {
     if (F < 2 || F > 1024 || pb.T < 1) return cudaErrorInvalidValue;
-    affine_schur_kernel<<<pb.T, kAffWarps * 32, 0, st>>>(pb, Hfd, Had, inv_hnn, red_ic, red_aff, acc, F);
+    affine_schur_kernel<<<pb.T, kAffWarps * 32, 0, st>>>(pb, Hfd, Had, Hnn, red_ff, ff_stride, red_aff, acc, F);
     return cudaGetLastError();
 }
 
-cudaError_t launch_assemble_affine(const double* S, const double* red_ic, const double* red_aff,
+cudaError_t launch_assemble_affine(const double* S, const double* red_ff, int ff_stride, const double* red_aff,
                                    const long long* acc, const int* cmap, int F, double damping, double prior,
-                                   dfloat* A8, cudaStream_t st)
+                                   dfloat* A8, cudaStream_t st, const double* rhs, int rhs_stride, int rhs_off,
+                                   const double* yph)
 {
-    if (F < 2 || F > 1024) return cudaErrorInvalidValue;
+    if (F < 2 || F > 1024 || (rhs && !yph)) return cudaErrorInvalidValue;
     const int n8 = 8 * (F - 1);
     const int blocks = std::max(1, std::min(148, (n8 * n8 + 255) / 256));
-    assemble_affine_kernel<<<blocks, 256, 0, st>>>(S, red_ic, red_aff, acc, cmap, F, damping, prior, A8);
+    assemble_affine_kernel<<<blocks, 256, 0, st>>>(S, red_ff, ff_stride, red_aff, acc, cmap, F, damping, prior,
+                                                   A8, rhs, rhs_stride, rhs_off, yph);
+    return cudaGetLastError();
+}
+
+// FC: row nc of L8 holds D^-1 L^-1 b (b = -y), so the backward
+// substitution gives Delta = -S8^-1 y; then the pose part takes the exact
+// gauge constraint and every frame's update is written (warp per frame),
+// the pair part (da, db) for the depth back-substitution and the additive
+// pair update of the next depth update. One CTA.
+constexpr int kFcAffWarps = 32;
+
+__global__ void __launch_bounds__(kFcAffWarps * 32)
+fc_solve_affine_kernel(SolveArgs a, const dfloat* __restrict__ L, const dfloat* __restrict__ Linv)
+{
+    extern __shared__ dfloat xs[];  // nc, then 8 (F - 1) doubles
+    __shared__ dfloat tb[kLdlBlock];
+    __shared__ double s_alpha;
+    __shared__ double dsh[kFcAffWarps][6];
+    const int F = a.F;
+    const int* cmap = a.cmap;
+    const int nact = cmap[F], nc = 8 * nact, np = 6 * nact, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double* x = reinterpret_cast<double*>(xs + 8 * (F - 1));
+    for (int i = tid; i < nc; i += blockDim.x) xs[i] = L[(size_t)nc * nc + i];
+    __syncthreads();
+    ldl_backward_smem(L, Linv, nc, xs, tb);
+    // back to frame order, 8 per frame [pose 6, pair 2]; frames left out of
+    // the system get no update
+    for (int i = tid; i < 8 * (F - 1); i += blockDim.x) {
+        const int f = i / 8 + 1, q = i % 8, k = cmap[f];
+        x[i] = k < 0 ? 0.0 : df_to_double(q < 6 ? xs[6 * k + q] : xs[np + 2 * k + q - 6]);
+    }
+    __syncthreads();
+    const int anchor = a.active[0];
+    const double* tanchor = a.tanchor;
+    if (tid == 0) {
+        double dta[3] = {0.0, 0.0, 0.0};
+        if (anchor > 0)
+            for (int q = 0; q < 3; ++q) dta[q] = x[8 * (anchor - 1) + q];
+        s_alpha = anchor > 0 ? gauge_alpha(tanchor + 12 * anchor + 9, dta) : 0.0;
+    }
+    __syncthreads();
+    for (int f = warp; f < F; f += blockDim.x >> 5) {
+        double* d = dsh[warp];
+        if (lane < 6) {
+            double v = f > 0 ? x[8 * (f - 1) + lane] : 0.0;
+            if (lane < 3 && f > 0 && a.active[f]) v = fma(-s_alpha, tanchor[12 * f + 9 + lane], v);
+            d[lane] = v;
+        }
+        __syncwarp();
+        double dab = (f > 0 && lane < 2) ? x[8 * (f - 1) + 6 + lane] : 0.0;
+        const bool ok = __all_sync(0xffffffffu, (lane >= 6 || isfinite(d[lane])) && isfinite(dab));
+        if (!ok) {
+            if (lane == 0) flag_error(a.err, 0, kErrNonFinite);
+            if (lane < 6) d[lane] = 0.0;
+            dab = 0.0;
+            __syncwarp();
+        }
+        write_update_lanes(a, f, d, lane);
+        if (lane < 2) {
+            const float hi = (float)dab;
+            a.dab64[2 * f + lane] = dab;
+            a.dab2[2 * f + lane] = make_float2(hi, (float)(dab - (double)hi));
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_fc_solve_affine(const SolveArgs& a, const dfloat* L8, const dfloat* Linv8, cudaStream_t st)
+{
+    if (a.F < 2 || a.F > 1024 || a.B != 1) return cudaErrorInvalidValue;
+    const size_t smem = (sizeof(dfloat) + sizeof(double)) * 8 * (a.F - 1);
+    fc_solve_affine_kernel<<<1, kFcAffWarps * 32, smem, st>>>(a, L8, Linv8);
     return cudaGetLastError();
 }
 
@@ -283,9 +375,13 @@ cudaError_t launch_ic_solve_affine(const SolveArgs& a, const dfloat* Sinv8, cons
 
 cudaError_t affine_setup()
 {
-    // up to 1023 target frames: 8 * 1023 double-float values + the frame map
-    return cudaFuncSetAttribute(ic_solve_affine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(dfloat) * 8 * 1023 + sizeof(int) * 1024));
+    // up to 1023 target frames: 8 * 1023 double-float values + the frame
+    // map, or + as many doubles
+    cudaError_t e = cudaFuncSetAttribute(ic_solve_affine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(dfloat) * 8 * 1023 + sizeof(int) * 1024));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fc_solve_affine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((sizeof(dfloat) + sizeof(double)) * 8 * 1023));
 }
 
 }  // namespace pba

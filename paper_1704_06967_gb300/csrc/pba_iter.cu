@@ -95,14 +95,20 @@ depth_update_kernel(DevProblem pb, DepthState ds, const float2* __restrict__ dth
         if (warp != 0) return;
         if (lane < 6) d[lane] = a.dtheta64[6 * f + lane];
         if (kAff && lane == 0) {
-            // the brightness pair: alpha' = alpha / (1 + da), beta' = (beta - db) / (1 + da)
+            // the brightness pair: IC composes alpha' = alpha / (1 + da),
+            // beta' = (beta - db) / (1 + da); FC adds (da, db)
             const double da = a.dab64[2 * f], db = a.dab64[2 * f + 1];
             if (da != 0.0 || db != 0.0) {
                 float* fcf = a.fc + (size_t)f * kFrameConst + kFrameAlpha;
-                const double s = 1.0 + da;
                 const double al = (double)fcf[0], be = (double)fcf[1];
-                fcf[0] = (float)(al / s);
-                fcf[1] = (float)((be - db) / s);
+                if (kIcRule) {
+                    const double s = 1.0 + da;
+                    fcf[0] = (float)(al / s);
+                    fcf[1] = (float)((be - db) / s);
+                } else {
+                    fcf[0] = (float)(al + da);
+                    fcf[1] = (float)(be + db);
+                }
             }
         }
         __syncwarp();
@@ -175,7 +181,8 @@ depth_update_kernel(DevProblem pb, DepthState ds, const float2* __restrict__ dth
 #pragma unroll
             for (int k = 0; k < 6; ++k) dot_pair_add(s, c, vis ? (hv ? hv[k] : h[k * nvis]) : 0.0f, th[k]);
             if (kAff) {
-                // joint brightness: + H_a^T (da, db) of the frame
+                // joint brightness: + H_a^T (da, db) of the frame (H_a: the
+                // IC or FC system's, ds.Had)
                 const float* ha = ds.Had + (size_t)po * 2 + (vis ? rank_of(mask, lane) : 0);
                 const float2* tb = a.dab2 + 2 * f;
                 dot_pair_add(s, c, vis ? ha[0] : 0.0f, tb[0]);
@@ -452,12 +459,13 @@ ic_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
 // ---------------------------------------------------------------------------
 constexpr int kFcGroup = 2;
 
-template <int PMAX, bool kAccum, int DT>
+template <int PMAX, bool kAccum, int DT, bool kJoint = false>
 __global__ void __launch_bounds__(kResWarps * 32, 2)
 fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float* __restrict__ fprev,
                    const float* __restrict__ dcur, const float* __restrict__ dprev,
                    float* __restrict__ Hfd_out, float* __restrict__ ent_part,
-                   float* __restrict__ gpart, float4* __restrict__ estats, int have_prev, int photo)
+                   float* __restrict__ gpart, float4* __restrict__ estats, int have_prev, int photo,
+                   float* __restrict__ Had_out, float* __restrict__ aff_part)
 {
     const int lane = threadIdx.x & 31;
     const int e = blockIdx.x * kResWarps + (threadIdx.x >> 5);
@@ -472,7 +480,13 @@ fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
     for (int q = 0; q < 27; ++q) acc[q] = 0.0f;
     float hfd[6] = {0, 0, 0, 0, 0, 0};
     float st[3] = {0, 0, 0};
-    float ph[5] = {0, 0, 0, 0, 0};  // brightness fit sums (w, w v, w v^2, w I_0, w I_0^2)
+    float ph[5] = {0, 0, 0, 0, 0};  // brightness fit sums (w, w v, w v^2, w I_0, w I_0^2);
+                                    // kJoint: g_a = (sum -v w r, sum -w r)
+    // kJoint (the pairs as unknowns, columns -v and -1): H_pa ([a][alpha,
+    // beta]), H_aa (v^2, v, 1) weighted sums, and the pair's J_d^T W [-v, -1]
+    float aff[kAffComp], had[2] = {0.0f, 0.0f};
+#pragma unroll
+    for (int q = 0; q < kAffComp; ++q) aff[q] = 0.0f;
     float gp = 0.0f, hnn = 0.0f, disp = 0.0f;
     if ((en.mask >> lane) & 1u) {
         const int n = en.tile * kTile + lane;
@@ -546,7 +560,7 @@ fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
                         st[0] += huber_rho(r, k);
                         st[1] = fmaf(r, r, st[1]);
                         st[2] += 1.0f;
-                        if (kAccum && photo) {
+                        if (kAccum && !kJoint && photo) {
                             const float w = huber_w(r, k);
                             ph[0] += w;
                             ph[1] = fmaf(w, val[jj], ph[1]);
@@ -581,6 +595,21 @@ fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
                             }
                             hnn = fmaf(w * J[6], J[6], hnn);
                             gp = fmaf(J[6], wr, gp);
+                            if (kJoint) {
+                                const float wv = w * val[jj];
+#pragma unroll
+                                for (int a = 0; a < 6; ++a) {
+                                    aff[2 * a] = fmaf(-wv, J[a], aff[2 * a]);
+                                    aff[2 * a + 1] = fmaf(-w, J[a], aff[2 * a + 1]);
+                                }
+                                aff[12] = fmaf(wv, val[jj], aff[12]);
+                                aff[13] += wv;
+                                aff[14] += w;
+                                ph[0] = fmaf(-val[jj], wr, ph[0]);
+                                ph[1] -= wr;
+                                had[0] = fmaf(-wv, J[6], had[0]);
+                                had[1] = fmaf(-w, J[6], had[1]);
+                            }
                         }
                     }
                 }
@@ -591,6 +620,11 @@ fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
             float* hd = Hfd_out + (size_t)en.pair_off * 6 + rank_of(en.mask, lane);
 #pragma unroll
             for (int a = 0; a < 6; ++a) hd[a * nvis] = hfd[a];
+            if (kJoint) {
+                float* ha = Had_out + (size_t)en.pair_off * 2 + rank_of(en.mask, lane);
+                ha[0] = had[0];
+                ha[nvis] = had[1];
+            }
         }
         if (have_prev) {
             const float* cp = fprev + 12 * en.f;
@@ -607,6 +641,7 @@ fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
         gpart[(size_t)e * 2 * kTile + kTile + lane] = hnn;
         warp_sum<27>(acc);
         if (photo) warp_sum<5>(ph);
+        if (kJoint) warp_sum<kAffComp>(aff);
     }
     warp_sum<3>(st);
     disp = warp_max1(disp);
@@ -618,6 +653,11 @@ fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
             if (photo)
 #pragma unroll
                 for (int a = 0; a < 5; ++a) o[kPhotoColFc + a] = ph[a];
+            if (kJoint) {
+                float* oa = aff_part + (size_t)pb.entry_slot[e] * kEntryPartial;
+#pragma unroll
+                for (int q = 0; q < kAffComp; ++q) oa[q] = aff[q];
+            }
         }
         estats[e] = make_float4(st[0], st[1], st[2], disp);
     }
@@ -644,7 +684,7 @@ __global__ void __launch_bounds__(kTileWarps * 32)
 point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __restrict__ Hfd,
              float* __restrict__ Hnn, float* __restrict__ gn, float* __restrict__ ent_part, int coff,
              const float4* __restrict__ estats, const float* __restrict__ ddsq_t,
-             TileStats* __restrict__ tstats, const float* __restrict__ Had)
+             TileStats* __restrict__ tstats, const float* __restrict__ Had, int acol)
 {
     const int t = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     pdl_trigger();
@@ -745,7 +785,7 @@ point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __rest
             v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
             if ((lane & 3) == 0 && lane < 24) ent_part[(size_t)sl * kEntryPartial + coff + (lane >> 2)] = v[0];
             else if ((lane & 3) == 0 && Had)
-                ent_part[(size_t)sl * kEntryPartial + kPhotoColIc + 2 + ((lane - 24) >> 2)] = v[0];
+                ent_part[(size_t)sl * kEntryPartial + acol + ((lane - 24) >> 2)] = v[0];
         };
         int i = warp;
         if (!kFc) {
@@ -872,9 +912,9 @@ cudaError_t launch_depth_update(const LaunchCtx& L, const SolveArgs& a, bool ic_
                           kTileWarps * 32, 0, L.stream, L.pb, ds, L.fs.dth2, L.ic.inv_hnn, L.ic.inv_d0, L.it.dcur,
                           L.it.dprev, L.it.ddsq_t, apply, a);
     else
-        return launch_pdl(depth_update_kernel<false>, grid, kTileWarps * 32, 0, L.stream, L.pb, ds, L.fs.dth2,
-                          (const double*)nullptr, (const double*)nullptr, L.it.dcur, L.it.dprev, L.it.ddsq_t,
-                          apply, a);
+        return launch_pdl(ds.Had ? depth_update_kernel<false, true> : depth_update_kernel<false, false>, grid,
+                          kTileWarps * 32, 0, L.stream, L.pb, ds, L.fs.dth2, (const double*)nullptr,
+                          (const double*)nullptr, L.it.dcur, L.it.dprev, L.it.ddsq_t, apply, a);
     return cudaGetLastError();
 }
 
@@ -919,9 +959,10 @@ template <int PMAX, bool A, int DT>
 static cudaError_t fc_residual_p(const LaunchCtx& L, int have_prev)
 {
     const int blocks = (L.pb.E + kResWarps - 1) / kResWarps;
-    return launch_pdl(fc_residual_kernel<PMAX, A, DT>, blocks, kResWarps * 32, 0, L.stream, L.pb, L.fs.fc,
-                      L.fs.fc_prev, L.it.dcur, L.it.dprev, L.Hfd_fc, L.ent_part, L.it.gpart, L.it.estats,
-                      have_prev, L.photo);
+    // the brightness pairs as unknowns: their own instance
+    auto k = (A && L.photo == 2) ? fc_residual_kernel<PMAX, A, DT, A> : fc_residual_kernel<PMAX, A, DT, false>;
+    return launch_pdl(k, blocks, kResWarps * 32, 0, L.stream, L.pb, L.fs.fc, L.fs.fc_prev, L.it.dcur, L.it.dprev,
+                      L.Hfd_fc, L.ent_part, L.it.gpart, L.it.estats, have_prev, L.photo, L.Had_fc, L.aff_part);
 }
 
 cudaError_t launch_fc_residual(const LaunchCtx& L, bool accum, int have_prev)
@@ -945,14 +986,15 @@ cudaError_t launch_ic_point(const LaunchCtx& L, bool accum)
     auto k = accum ? point_kernel<true, false> : point_kernel<false, false>;
     return launch_pdl(k, L.pb.T, kTileWarps * 32, 0, L.stream, L.pb, L.it.gpart, L.ic.Hfd, L.ic.Hnn,
                       L.ds_ic.gn, L.ent_part, 6, L.it.estats, L.it.ddsq_t, L.tstats,
-                      (const float*)(L.photo == 2 ? L.ic.Had : nullptr));
+                      (const float*)(L.photo == 2 ? L.ic.Had : nullptr), kPhotoColIc + 2);
 }
 
 cudaError_t launch_fc_point(const LaunchCtx& L, bool accum)
 {
     auto k = accum ? point_kernel<true, true> : point_kernel<false, true>;
     return launch_pdl(k, L.pb.T, kTileWarps * 32, 0, L.stream, L.pb, L.it.gpart, L.Hfd_fc, L.ds_fc.Hnn,
-                      L.ds_fc.gn, L.ent_part, 27, L.it.estats, L.it.ddsq_t, L.tstats, (const float*)nullptr);
+                      L.ds_fc.gn, L.ent_part, 27, L.it.estats, L.it.ddsq_t, L.tstats,
+                      (const float*)(L.photo == 2 ? L.Had_fc : nullptr), kPhotoColFc + 2);
 }
 
 // FP32 pass constants and previous R|t of frames [f0, f0 + nf) from their

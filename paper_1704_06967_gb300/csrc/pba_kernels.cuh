@@ -77,6 +77,8 @@ struct LaunchCtx {
     DepthState ds_ic, ds_fc;
     IcStore ic;
     float* Hfd_fc;
+    float* Had_fc;    // joint brightness (FC): pairs * 2, J_d^T W [-v, -1]
+    float* aff_part;  // joint brightness (FC): E rows of kEntryPartial, the 15 H_pa / H_aa sums
     float* ent_part;
     TileStats* tstats;
     IterBufs it;
@@ -254,16 +256,21 @@ cudaError_t launch_ldl_inverse(const BundleSet& bs, const dfloat* L, const dfloa
 // H_a(n,f) H_a(n,g)^T / H_dd(n) (2 x 2, S_aa) as fixed-point integers (acc:
 // n6 * n2 then n2 * n2, zero on entry); the scale comes from the frame
 // sums (red_ic: 21 per frame, red_aff: 15 per frame).
-cudaError_t launch_affine_schur(const DevProblem& pb, const float* Hfd, const float* Had,
-                                const double* inv_hnn, const double* red_ic, const double* red_aff,
-                                long long* acc, int F, cudaStream_t st);
+cudaError_t launch_affine_schur(const DevProblem& pb, const float* Hfd, const float* Had, const float* Hnn,
+                                const double* red_ff, int ff_stride, const double* red_aff, long long* acc,
+                                int F, cudaStream_t st);
 // The factorisation's working matrix of the 8 (F - 1) system over the
 // active frames, poses first (6 per active frame, the order of S) then the
 // pairs (2 per active frame): S (FP64, assembled), H_pa and H_aa from
 // red_aff, minus the fixed-point sums of launch_affine_schur.
-cudaError_t launch_assemble_affine(const double* S, const double* red_ic, const double* red_aff,
+cudaError_t launch_assemble_affine(const double* S, const double* red_ff, int ff_stride, const double* red_aff,
                                    const long long* acc, const int* cmap, int F, double damping, double prior,
-                                   dfloat* A8, cudaStream_t st);
+                                   dfloat* A8, cudaStream_t st, const double* rhs = nullptr, int rhs_stride = 0,
+                                   int rhs_off = 0, const double* yph = nullptr);
+// FC with the pairs as unknowns: the backward substitution of the factorised
+// 8 (F - 1) system (its augmented row), the gauge constraint on the
+// translations, every frame's pose update and (da, db) (one CTA)
+cudaError_t launch_fc_solve_affine(const SolveArgs& a, const dfloat* L8, const dfloat* Linv8, cudaStream_t st);
 // Delta = -S8^-1 [y_theta; y_a] per target frame (y_a from the brightness
 // columns of the frame reduction and the prior), the gauge constraint on the
 // translations, the pose update written like launch_ic_solve and (da, db)

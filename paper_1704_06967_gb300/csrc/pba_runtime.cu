@@ -293,6 +293,9 @@ struct pba_ctx {
         float* Had;
         unsigned* vmask0;
         double* red_aff;
+        float* Had_fc;     // FC: per pair J_d^T W [-v, -1]
+        float* aff_part;   // FC: E rows of kEntryPartial (the 15 H_pa / H_aa sums)
+        double* red_aff_fc;
         long long* aff_acc;
         dfloat *A8, *L8, *Linv8, *dpiv8, *rpiv8, *Sinv8;
         double* dab64;
@@ -559,6 +562,9 @@ size_t layout(pba_ctx* c, char* base)
         take(c->d.Had, jb ? (size_t)c->V * 2 * 4 : 0);
         take(c->d.vmask0, jb ? (size_t)c->V * 4 : 0);
         take(c->d.red_aff, jb ? F * kAffComp * 8 : 0);
+        take(c->d.Had_fc, jb ? (size_t)c->V * 2 * 4 : 0);
+        take(c->d.aff_part, jb ? (size_t)c->E * kEntryPartial * 4 : 0);
+        take(c->d.red_aff_fc, jb ? F * kAffComp * 8 : 0);
         take(c->d.aff_acc, (n6 * n2 + n2 * n2) * sizeof(long long));
         take(c->d.A8, (n8 + 1) * n8 * sizeof(dfloat));
         take(c->d.L8, (n8 + 1) * n8 * sizeof(dfloat));
@@ -992,6 +998,9 @@ LaunchCtx make_launch(pba_ctx* c)
         L.ds_ic.Had = c->d.Had;
         L.pb.vmask0 = c->d.vmask0;
         L.pb.Had = c->d.Had;
+        L.Had_fc = c->d.Had_fc;
+        L.aff_part = c->d.aff_part;
+        L.ds_fc.Had = c->d.Had_fc;
     }
     return L;
 }
@@ -1088,6 +1097,20 @@ BundleSet bundle_set(pba_ctx* c)
     bs.n6max = c->n6max;
     bs.nb = 6;
     return bs;
+}
+
+// The 8 (F - 1) system of the brightness pairs as unknowns (one bundle; its
+// arrays start at offset 0 of the A8 / L8 / Linv8 / pivot / S8^-1 buffers).
+BundleSet bundle_set8(pba_ctx* c)
+{
+    BundleSet b8{};
+    b8.B = 1;
+    b8.one = c->bdesc[0];
+    b8.one.so = b8.one.ao = b8.one.lo = 0;
+    b8.one.po = 0;
+    b8.n6max = c->n6max;
+    b8.nb = 8;
+    return b8;
 }
 
 pba_status copy_stats(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
@@ -1495,18 +1518,12 @@ pba_status precompute_core(pba_ctx* ctx, const LaunchCtx& L, const BundleSet& bs
         LAUNCH(TS_PRE, launch_frame_reduce(L, 0, kAffComp, ctx->d.red_aff, -1, -1, true, -1, 0,
                                            ctx->d.ic_part + kAffCol));
         CK(cudaMemsetAsync(ctx->d.aff_acc, 0, (n6 * n2 + n2 * n2) * sizeof(long long), ctx->stream));
-        LAUNCH(TS_PRE, launch_affine_schur(L.pb, ctx->d.Hfd_ic, ctx->d.Had, ctx->d.inv_hnn, ctx->d.red_ic,
+        LAUNCH(TS_PRE, launch_affine_schur(L.pb, ctx->d.Hfd_ic, ctx->d.Had, ctx->d.Hnn_ic, ctx->d.red_ic, 21,
                                            ctx->d.red_aff, ctx->d.aff_acc, F, ctx->stream));
-        LAUNCH(TS_PRE, launch_assemble_affine(ctx->d.S_ic, ctx->d.red_ic, ctx->d.red_aff, ctx->d.aff_acc,
+        LAUNCH(TS_PRE, launch_assemble_affine(ctx->d.S_ic, ctx->d.red_ic, 21, ctx->d.red_aff, ctx->d.aff_acc,
                                               ctx->d.cmap_ic, F, ctx->cfg.damping, ctx->cfg.photo_prior,
                                               ctx->d.A8, ctx->stream));
-        BundleSet b8{};
-        b8.B = 1;
-        b8.one = ctx->bdesc[0];
-        b8.one.so = b8.one.ao = b8.one.lo = 0;
-        b8.one.po = 0;
-        b8.n6max = ctx->n6max;
-        b8.nb = 8;
+        const BundleSet b8 = bundle_set8(ctx);
         LAUNCH(TS_PRE, launch_ldl(b8, ctx->d.A8, ctx->d.L8, ctx->d.Linv8, ctx->d.dpiv8, ctx->d.rpiv8,
                                   ctx->d.cmap_ic, 0, ctx->d.err, ctx->stream, ctx->ldl_cluster));
         LAUNCH(TS_PRE, launch_ldl_inverse(b8, ctx->d.L8, ctx->d.Linv8, ctx->d.rpiv8, ctx->d.cmap_ic, ctx->d.Sinv8,
@@ -1517,6 +1534,26 @@ pba_status precompute_core(pba_ctx* ctx, const LaunchCtx& L, const BundleSet& bs
                               ctx->d.err, ctx->stream, ctx->ldl_cluster));
     LAUNCH(TS_PRE, launch_ldl_inverse(bs, ctx->d.L2, ctx->d.Linv, ctx->d.rpiv, ctx->d.cmap_ic, ctx->d.Sinv2,
                                       ctx->stream));
+    return PBA_OK;
+}
+
+// FC with the brightness pairs as unknowns, after the pose system S_fc is
+// assembled: the border from this iteration's H_a, the augmented 8 (F - 1)
+// system, its factorisation and the backward substitution with the updates.
+pba_status fc_affine_solve(pba_ctx* ctx, const LaunchCtx& L, const SolveArgs& sa)
+{
+    const int F = ctx->F;
+    const size_t n2 = 2 * (size_t)(F - 1), n6 = 6 * (size_t)(F - 1);
+    CK(cudaMemsetAsync(ctx->d.aff_acc, 0, (n6 * n2 + n2 * n2) * sizeof(long long), ctx->stream));
+    LAUNCH(TS_SCHUR, launch_affine_schur(L.pb, ctx->d.Hfd_fc, ctx->d.Had_fc, ctx->d.Hnn_fc, ctx->d.red_y, 27,
+                                         ctx->d.red_aff_fc, ctx->d.aff_acc, F, ctx->stream));
+    LAUNCH(TS_SCHUR, launch_assemble_affine(ctx->d.S_fc, ctx->d.red_y, 27, ctx->d.red_aff_fc, ctx->d.aff_acc,
+                                            ctx->d.cmap_fc, F, ctx->cfg.damping, 0.0, ctx->d.A8, ctx->stream,
+                                            ctx->d.red_y, 27, 21, ctx->d.red_photo));
+    const BundleSet b8 = bundle_set8(ctx);
+    LAUNCH(TS_SOLVE, launch_ldl(b8, ctx->d.A8, ctx->d.L8, ctx->d.Linv8, ctx->d.dpiv8, ctx->d.rpiv8, ctx->d.cmap_fc,
+                                1, ctx->d.err, ctx->stream, ctx->ldl_cluster));
+    LAUNCH(TS_SOLVE, launch_fc_solve_affine(sa, ctx->d.L8, ctx->d.Linv8, ctx->stream));
     return PBA_OK;
 }
 
@@ -1988,8 +2025,6 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
 {
     if (!ctx) return PBA_ERR_ARG;
     if (!ctx->ws_ready) return fail(ctx, PBA_ERR_STATE, "workspace not set");
-    if (joint_brightness(ctx))
-        return fail(ctx, PBA_ERR_ARG, "the brightness pairs as unknowns are an IC option (photometric = 2)");
     if (n_iters < 0 || n_iters > ctx->cfg.max_stats_iters)
         return fail(ctx, PBA_ERR_ARG, "n_iters must be in [0, %d]", ctx->cfg.max_stats_iters);
     LaunchCtx L = make_launch(ctx);
@@ -2008,12 +2043,20 @@ pba_status pba_solve_fc(pba_ctx* ctx, int n_iters, pba_iter_stats* stats)
             if (ctx->cfg.photometric)
                 LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, 5, ctx->d.red_photo, -1, -1, true, -1, 0,
                                                       ctx->d.ent_part + kPhotoColFc));
+            if (joint_brightness(ctx))
+                LAUNCH(TS_REDUCE, launch_frame_reduce(L, 0, kAffComp, ctx->d.red_aff_fc, -1, -1, true, -1, 0,
+                                                      ctx->d.aff_part));
             LAUNCHN(TS_SCHUR, launch_schur(ctx, L.pb, ctx->d.Hfd_fc, ctx->d.Hnn_fc, ctx->d.red_y, 27,
                                            ctx->d.schur_part, nullptr, &nl));
             LAUNCH(TS_SCHUR, launch_assemble_S(bs, ctx->d.red_y, 27, ctx->d.Soff, ctx->d.poses64,
                                                ctx->cfg.gauge_anchor_w, ctx->cfg.damping, ctx->d.S_fc,
                                                ctx->d.active_fc,
                                                ctx->stream, ctx->d.A2, ctx->d.cmap_fc, ctx->d.red_y, 27, 21));
+            if (joint_brightness(ctx)) {
+                pba_status q = fc_affine_solve(ctx, L, sa);
+                if (q != PBA_OK) return q;
+                continue;
+            }
             LAUNCH(TS_SOLVE, launch_ldl(bs, ctx->d.A2, ctx->d.L2, ctx->d.Linv, ctx->d.dpiv, ctx->d.rpiv,
                                         ctx->d.cmap_fc, 1, ctx->d.err, ctx->stream, ctx->ldl_cluster));
             LAUNCH(TS_SOLVE, launch_fc_solve_update(sa, ctx->d.L2, ctx->d.Linv, ctx->stream));
