@@ -679,7 +679,7 @@ fc_residual_kernel(DevProblem pb, const float* __restrict__ fconst, const float*
 // ---------------------------------------------------------------------------
 constexpr int kPointPre = 4;
 
-template <bool kAccum, bool kFc>
+template <bool kAccum, bool kFc, bool kAff = false>
 __global__ void __launch_bounds__(kTileWarps * 32)
 point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __restrict__ Hfd,
              float* __restrict__ Hnn, float* __restrict__ gn, float* __restrict__ ent_part, int coff,
@@ -768,7 +768,7 @@ point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __rest
 #pragma unroll
             for (int q = 0; q < 6; ++q) v[q] = vis ? (hv ? hv[q] : h[q * nvis]) * sn : 0.0f;
             v[6] = v[7] = 0.0f;
-            if (Had && vis) {
+            if (kAff && vis) {
                 // joint brightness: the pair's correction sum_n H_a g_n / H_dd
                 const float* ha = Had + (size_t)po * 2 + rank_of(mask, lane);
                 v[6] = ha[0] * sn;
@@ -784,7 +784,7 @@ point_kernel(DevProblem pb, const float* __restrict__ gpart, const float* __rest
             v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
             v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
             if ((lane & 3) == 0 && lane < 24) ent_part[(size_t)sl * kEntryPartial + coff + (lane >> 2)] = v[0];
-            else if ((lane & 3) == 0 && Had)
+            else if (kAff && (lane & 3) == 0)
                 ent_part[(size_t)sl * kEntryPartial + acol + ((lane - 24) >> 2)] = v[0];
         };
         int i = warp;
@@ -983,7 +983,8 @@ cudaError_t launch_fc_residual(const LaunchCtx& L, bool accum, int have_prev)
 
 cudaError_t launch_ic_point(const LaunchCtx& L, bool accum)
 {
-    auto k = accum ? point_kernel<true, false> : point_kernel<false, false>;
+    const bool aff = accum && L.photo == 2;
+    auto k = aff ? point_kernel<true, false, true> : accum ? point_kernel<true, false> : point_kernel<false, false>;
     return launch_pdl(k, L.pb.T, kTileWarps * 32, 0, L.stream, L.pb, L.it.gpart, L.ic.Hfd, L.ic.Hnn,
                       L.ds_ic.gn, L.ent_part, 6, L.it.estats, L.it.ddsq_t, L.tstats,
                       (const float*)(L.photo == 2 ? L.ic.Had : nullptr), kPhotoColIc + 2);
@@ -991,7 +992,8 @@ cudaError_t launch_ic_point(const LaunchCtx& L, bool accum)
 
 cudaError_t launch_fc_point(const LaunchCtx& L, bool accum)
 {
-    auto k = accum ? point_kernel<true, true> : point_kernel<false, true>;
+    const bool aff = accum && L.photo == 2;
+    auto k = aff ? point_kernel<true, true, true> : accum ? point_kernel<true, true> : point_kernel<false, true>;
     return launch_pdl(k, L.pb.T, kTileWarps * 32, 0, L.stream, L.pb, L.it.gpart, L.Hfd_fc, L.ds_fc.Hnn,
                       L.ds_fc.gn, L.ent_part, 27, L.it.estats, L.it.ddsq_t, L.tstats,
                       (const float*)(L.photo == 2 ? L.Had_fc : nullptr), kPhotoColFc + 2);
