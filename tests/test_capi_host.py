@@ -45,6 +45,23 @@ def test_create_rejects_bad_configs(lib):
     assert lib.pba_create(None, ctypes.byref(h)) == 1
 
 
+def test_create_checks_the_brightness_options(lib):
+    """photometric in {0, 1, 2}; the pairs as unknowns take one bundle per
+    context; the prior weight is finite and >= 0."""
+    h = ctypes.c_void_p()
+    for mode, nb, prior, want in ((3, 1, 0.0, 1), (-1, 1, 0.0, 1), (2, 2, 0.0, 1), (2, 1, -0.5, 1),
+                                  (2, 1, float("nan"), 1), (2, 1, float("inf"), 1), (1, 2, 0.0, 0),
+                                  (2, 1, 0.01, 0), (2, 1, 0.0, 0), (0, 1, 0.0, 0)):
+        cfg, pat = _cfg()
+        cfg.n_bundles = nb
+        cfg.photometric = mode
+        cfg.photo_prior = prior
+        st = lib.pba_create(ctypes.byref(cfg), ctypes.byref(h))
+        assert st == want, (mode, nb, prior, st)
+        if st == 0:
+            lib.pba_destroy(h)
+
+
 def test_call_order_and_argument_checks(lib):
     cfg, pat = _cfg()
     h = ctypes.c_void_p()
