@@ -296,7 +296,11 @@ pba_status pba_bundle_errors(pba_ctx* ctx, int* flags);
 /* Affine brightness pairs of a bundle's frames: ab host, F_b x 2 doubles
  * (alpha_f, beta_f; frame 0 is (1, 0)), stored as FP32 on the device. They
  * are used in every residual (an identity pair changes nothing) and fitted
- * by the steps when cfg.photometric is set. */
+ * (photometric = 1) or solved for (photometric = 2) by the steps when
+ * cfg.photometric is set. With photometric = 2 a step's pair update is
+ * applied with its pose update (at the next iteration's start or at the end
+ * of the call), so the pairs read after a call belong to its final
+ * parameters. */
 pba_status pba_get_brightness(pba_ctx* ctx, int bundle, double* ab);
 pba_status pba_set_brightness(pba_ctx* ctx, int bundle, const double* ab);
 
