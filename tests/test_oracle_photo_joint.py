@@ -258,3 +258,42 @@ def test_fc_joint_step_is_the_dense_least_squares_minimiser():
     dth, dab, _, _, _, _ = oracle.fc_step_joint(pb, P, D)
     assert np.abs(dth[1:, 3:] - dense[:, 3:6]).max() <= 1e-6 * np.abs(dense[:, 3:6]).max()
     assert np.abs(dab[1:] - dense[:, 6:]).max() <= 1e-6 * np.abs(dense[:, 6:]).max()
+
+
+@pytest.mark.parametrize("lam", [0.1, 1.0])
+def test_damped_joint_step_is_the_damped_dense_solution(lam):
+    """Levenberg-Marquardt damping of the 8-block system (every diagonal
+    entry of H_pp and H_dd times 1 + lambda): the rotations and the pair
+    increments equal those of the damped dense normal equations over all
+    unknowns (numpy solve); the translations then take the scale-gauge
+    projection, which leaves those components alone."""
+    sc, imgs = _relit_tiny()
+    pb = oracle.Problem(imgs, sc.uv, sc.pattern, sc.vis, sc.intrinsics, sc.huber_k, damping=lam,
+                        photometric=True)
+    P, D = sc.poses0, sc.depths0
+    F, N = pb.F, pb.N
+    nf = 8 * (F - 1)
+    H = np.zeros((nf + N, nf + N))
+    g = np.zeros(nf + N)
+    for n in range(N):
+        for f in range(1, F):
+            if not pb.vis[n, f]:
+                continue
+            for j in range(pb.P):
+                J, r, ok = oracle.fc_residual_joint(pb, P, D, n, f, j)
+                if not ok:
+                    continue
+                w = oracle.huber_weight(r, pb.huber_k)
+                row = np.zeros(nf + N)
+                row[8 * (f - 1):8 * f] = J[:8]
+                row[nf + n] = J[8]
+                H += w * np.outer(row, row)
+                g += w * r * row
+    live = np.diag(H) > 0
+    Hd = H + lam * np.diag(np.diag(H))
+    x = np.zeros(nf + N)
+    x[live] = np.linalg.solve(Hd[np.ix_(live, live)], -g[live])
+    dense = x[:nf].reshape(F - 1, 8)
+    dth, dab, _, _, _, _ = oracle.fc_step_joint(pb, P, D)
+    assert np.abs(dth[1:, 3:] - dense[:, 3:6]).max() <= 1e-8 * np.abs(dense[:, 3:6]).max()
+    assert np.abs(dab[1:] - dense[:, 6:]).max() <= 1e-8 * np.abs(dense[:, 6:]).max()
