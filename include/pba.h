@@ -264,7 +264,9 @@ pba_status pba_get_last_update(pba_ctx* ctx, int bundle, double* dtheta, double*
 /* The last linear system: Hff F*36 (row-major 6x6 per frame, frame 0 zero),
  * Hfd N*F*6 (caller point order), Hdd N, and S (6(F-1))^2 row-major as
  * factorised (with the gauge prior). fc != 0 selects the last FC system.
- * Host arrays, nullable each. */
+ * Host arrays, nullable each. With the brightness pairs as unknowns
+ * (photometric = 2) these are the pose blocks of the 8-per-frame system;
+ * its brightness border is not returned. */
 pba_status pba_get_system(pba_ctx* ctx, int bundle, int fc, double* Hff, double* Hfd,
                           double* Hdd, double* S);
 
